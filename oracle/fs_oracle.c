@@ -1,0 +1,170 @@
+/*
+ * CPU oracle: short-characteristics formal solution in plain FP64 loops.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or
+ * calls this file; only the tests, the package's smoke check and the bench's
+ * CPU-baseline leg do.  It shares no code with the CUDA path.
+ *
+ * What it computes (Sec. 3, "Computational setup"; Eq. 1): the transfer
+ * equation dI/dtau = S - I is integrated cell by cell with the short
+ * characteristics method of Kunasz & Auer (1988) with linear interpolation.
+ * For a node on plane k and a ray with direction (mux, muy, muz) the short
+ * characteristic runs back to the neighbouring plane upwind (k-1 for muz > 0,
+ * k+1 for muz < 0).  Where it crosses that plane, I, chi and S are taken by
+ * bilinear interpolation between the four surrounding nodes, periodic in x and
+ * y (Sec. 4.2).  Along the characteristic of length s = |dz|/|muz| the optical
+ * depth is the trapezoid dtau = (chi_up + chi_0) s / 2 and S is linear in tau,
+ * which gives
+ *     I_0 = I_up exp(-dtau) + w_up S_up + w_0 S_0,
+ *     w_0  = 1 - (1 - exp(-dtau))/dtau,   w_up = (1 - exp(-dtau))/dtau - exp(-dtau).
+ * Boundary conditions (Sec. 4.2): rays entering through the bottom plane
+ * start with the given I_bottom (the Planck function at the local gas
+ * temperature), rays entering through the top start with I_top (zero).
+ *
+ * Accumulated per node, with the quadrature weight w_r of each ray and the
+ * per-node frequency weight wphi (frequency quadrature weight times line
+ * profile):
+ *     Jbar  = sum w_r wphi I                 (mean intensity, profile-averaged)
+ *     Jeff  = sum w_r wphi (I - w_0 S_0)     (Jbar minus the local part)
+ *     U     = sum w_r wphi (1 - w_0)         (so that the diagonal operator
+ *                                             Lambda* = sum w_r wphi w_0 = sum w_r wphi - U)
+ * The diagonal of the Lambda operator is exactly w_0 at each node and ray,
+ * because the upwind intensity depends only on nodes of other planes.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+static long node_index(long x, long y, long k, long nx, long ny)
+{
+    return (k * ny + y) * nx + x;
+}
+
+static long periodic(long i, long n)
+{
+    long r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+/* Weights of the linear short-characteristics step.  For small dtau the
+ * closed forms lose digits to cancellation, so below 1e-3 the Taylor series
+ * of w_0 and w_up (five terms each) are used instead. */
+static void sc_weights(double dtau, double *ex, double *w0, double *wup)
+{
+    double e = exp(-dtau);
+    *ex = e;
+    if (dtau < 1e-3) {
+        double t = dtau;
+        *w0 = t * (0.5 - t * (1.0 / 6.0 - t * (1.0 / 24.0 - t * (1.0 / 120.0 - t / 720.0))));
+        *wup = t * (0.5 - t * (1.0 / 3.0 - t * (1.0 / 8.0 - t * (1.0 / 30.0 - t / 144.0))));
+    } else {
+        double u = (1.0 - e) / dtau;
+        *w0 = 1.0 - u;
+        *wup = u - e;
+    }
+}
+
+static double bilinear(const double *plane, long nx, long ny, double xu, double yu)
+{
+    double fx0 = floor(xu), fy0 = floor(yu);
+    double tx = xu - fx0, ty = yu - fy0;
+    long x0 = periodic((long)fx0, nx), x1 = periodic((long)fx0 + 1, nx);
+    long y0 = periodic((long)fy0, ny), y1 = periodic((long)fy0 + 1, ny);
+    double f00 = plane[y0 * nx + x0], f10 = plane[y0 * nx + x1];
+    double f01 = plane[y1 * nx + x0], f11 = plane[y1 * nx + x1];
+    return (1.0 - tx) * (1.0 - ty) * f00 + tx * (1.0 - ty) * f10
+         + (1.0 - tx) * ty * f01 + tx * ty * f11;
+}
+
+/*
+ * Formal solution for all rays and frequencies.
+ *   chi, S, wphi : [nfreq][nz][ny][nx]
+ *   I_bottom, I_top : [nfreq][ny][nx]
+ *   mu : [nrays][3] direction cosines, wray : [nrays]
+ * Outputs (zeroed here) Jbar, Jeff, U : [nz][ny][nx]; I_out, if not NULL,
+ * receives every intensity as [nrays][nfreq][nz][ny][nx].
+ * Returns 0, or -1 on a bad argument.
+ */
+int orc_formal_solution(long nx, long ny, long nz, double dx, double dy,
+                        const double *z, long nrays, const double *mu,
+                        const double *wray, long nfreq, const double *chi,
+                        const double *S, const double *wphi,
+                        const double *I_bottom, const double *I_top,
+                        double *Jbar, double *Jeff, double *U, double *I_out)
+{
+    if (nx < 1 || ny < 1 || nz < 2 || nrays < 1 || nfreq < 1 || dx <= 0 || dy <= 0)
+        return -1;
+    long nplane = nx * ny, nvox = nplane * nz;
+    memset(Jbar, 0, sizeof(double) * nvox);
+    memset(Jeff, 0, sizeof(double) * nvox);
+    memset(U, 0, sizeof(double) * nvox);
+    double *Iprev = malloc(sizeof(double) * nplane);
+    double *Icur = malloc(sizeof(double) * nplane);
+    double *W0 = malloc(sizeof(double) * nplane);
+    if (!Iprev || !Icur || !W0) {
+        free(Iprev);
+        free(Icur);
+        free(W0);
+        return -1;
+    }
+    for (long r = 0; r < nrays; ++r) {
+        double mx = mu[3 * r], my = mu[3 * r + 1], mz = mu[3 * r + 2];
+        int up = mz > 0.0;
+        for (long f = 0; f < nfreq; ++f) {
+            const double *chif = chi + f * nvox, *Sf = S + f * nvox, *wf = wphi + f * nvox;
+            for (long step = 0; step < nz; ++step) {
+                long k = up ? step : nz - 1 - step;
+                if (step == 0) {
+                    /* entering boundary: the intensity is prescribed, so the
+                     * node's own source function does not enter (w_0 = 0) */
+                    const double *bc = (up ? I_bottom : I_top) + f * nplane;
+                    for (long y = 0; y < ny; ++y)
+                        for (long x = 0; x < nx; ++x) {
+                            Icur[y * nx + x] = bc[y * nx + x];
+                            W0[y * nx + x] = 0.0;
+                        }
+                } else {
+                    long kp = up ? k - 1 : k + 1;
+                    double s = fabs(z[k] - z[kp]) / fabs(mz);
+                    const double *chip = chif + kp * nplane, *Sp = Sf + kp * nplane;
+                    for (long y = 0; y < ny; ++y) {
+                        for (long x = 0; x < nx; ++x) {
+                            /* upwind crossing point, in units of cells */
+                            double xu = (double)x - s * mx / dx;
+                            double yu = (double)y - s * my / dy;
+                            double I_up = bilinear(Iprev, nx, ny, xu, yu);
+                            double chi_up = bilinear(chip, nx, ny, xu, yu);
+                            double S_up = bilinear(Sp, nx, ny, xu, yu);
+                            long v = node_index(x, y, k, nx, ny);
+                            double dtau = 0.5 * (chi_up + chif[v]) * s;
+                            double ex, w0, wup;
+                            sc_weights(dtau, &ex, &w0, &wup);
+                            Icur[y * nx + x] = I_up * ex + wup * S_up + w0 * Sf[v];
+                            W0[y * nx + x] = w0;
+                        }
+                    }
+                }
+                /* accumulate this plane */
+                for (long y = 0; y < ny; ++y) {
+                    for (long x = 0; x < nx; ++x) {
+                        long v = node_index(x, y, k, nx, ny);
+                        double I = Icur[y * nx + x], w0 = W0[y * nx + x];
+                        double w = wray[r] * wf[v];
+                        Jbar[v] += w * I;
+                        Jeff[v] += w * (I - w0 * Sf[v]);
+                        U[v] += w * (1.0 - w0);
+                        if (I_out)
+                            I_out[((r * nfreq + f) * nz + k) * nplane + y * nx + x] = I;
+                    }
+                }
+                double *t = Iprev;
+                Iprev = Icur;
+                Icur = t;
+            }
+        }
+    }
+    free(Iprev);
+    free(Icur);
+    free(W0);
+    return 0;
+}

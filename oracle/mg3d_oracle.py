@@ -1,0 +1,525 @@
+"""CPU oracle for the multigrid non-LTE 3D radiative-transfer hot path (FP64).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py`` may import this module.  It shares
+no code with the CUDA library: the formal solution is the plain C loop nest in
+``oracle/fs_oracle.c`` and everything else is written out here in numpy.  The
+only thing both sides consume in common is the seeded input generator
+``paper_1701_01607_gb300.synth`` (atmosphere arrays and atom parameters).
+
+What each function follows in the paper (Bjorgen & Leenaarts 2017):
+
+* ``a4_quadrature``     -- the 24-direction Carlson A4 set (Sec. 3).  The paper
+  does not print its values.  Reading: three directions per octant, the
+  permutations of (a, a, b) with 2a^2 + b^2 = 1 and equal weights 1/24; ``a``
+  is fixed by integrating mu^4 exactly, 2a^4 + b^4 = 3/5 (a = 0.3500212).
+* ``frequency_grid``    -- CRD Doppler profile sampled at equidistant offsets
+  with trapezoid weights, renormalised so that sum(w phi) = 1 (reading; the
+  paper only states CRD).
+* ``formal_solution``   -- short characteristics with linear interpolation
+  (Sec. 3) accumulating Jbar, Jeff = Jbar - Lambda* S and U = 1 - Lambda*.
+* ``rate_matrix`` / ``W`` -- statistical equilibrium (Eq. 2) with the first
+  rate equation replaced by particle conservation (Eq. 3), so that
+  W(n) = f with f = (n_tot, 0, ..., 0) (Eq. 4 and the f vector after it).
+  Radiative rates carry the diagonal-operator preconditioning of Rybicki &
+  Hummer (1991) that MALI uses (Sec. 2.1, Sec. 3).
+* ``mali_sweep``        -- one MALI (Jacobi) iteration; ``max_rel_change`` is
+  C_i of Sec. 3.3.
+* ``restrict_fw``       -- full-weighting restriction (Sec. 4.4), 27 points.
+* ``prolong_trilinear`` -- trilinear interpolation (Sec. 4.5).
+* ``vcycle``            -- FAS V-cycle, Eqs. 5-11 and the recursion of Sec. 2.2
+  with nu_1 pre-, nu_2 post-smoothing, nu_3 coarse iterations, nu_0 in the
+  first cycle (Sec. 4.10) and the 10 % fix for negative populations (Sec. 4.8).
+* ``fmg_solve``         -- full multigrid (Sec. 2.3, Fig. 1).
+
+Readings where the paper is silent (each also listed in the design doc):
+full weighting at the fixed z boundaries injects in z; n_before of Eq. 10 is
+R(n^k) as it enters level k-1; the negative fix applies per (level, node)
+whenever n_old (1 + I(e)) <= 0; W(n) on the right of Eq. 9 is evaluated in
+the preconditioned form Gamma(Jeff(n), U(n)) n, which equals the unpreconditioned
+rates at n by algebra.
+
+Parity pins: quadrature moments, closed-form slab intensities, the LTE limit,
+the sqrt(eps) law, horizontally homogeneous 3D = plane-parallel closed form,
+the dense Lambda-matrix solve, FAS fixed-point invariance, agreement of MALI,
+FAS and FMG, transfer-operator identities and particle conservation (see
+tests/test_oracle_*.py).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle/fs_oracle.c into oracle/_build/liboracle.so (plain gcc)."""
+    src = os.path.join(_HERE, "fs_oracle.c")
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(src)):
+        return _LIB_PATH
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp,
+                           src, "-lm"])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        d = ctypes.POINTER(ctypes.c_double)
+        lib.orc_formal_solution.restype = ctypes.c_int
+        lib.orc_formal_solution.argtypes = [
+            ctypes.c_long, ctypes.c_long, ctypes.c_long, ctypes.c_double, ctypes.c_double,
+            d, ctypes.c_long, d, d, ctypes.c_long, d, d, d, d, d, d, d, d, d]
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# --------------------------------------------------------------------------
+# Angle and frequency quadrature
+# --------------------------------------------------------------------------
+
+def a4_quadrature(a: float | None = None):
+    """Carlson A4 set: 24 unit vectors and weights (Sec. 3).
+
+    Three directions per octant, the permutations of (a, a, b) with
+    2a^2 + b^2 = 1.  By default a^2 is the root of 6a^4 - 4a^2 + 2/5 = 0
+    (from 2a^4 + b^4 = 3/5) that keeps b real.  Rays 0-11 point up (mu_z > 0).
+    """
+    if a is None:
+        a = math.sqrt((4.0 - math.sqrt(6.4)) / 12.0)
+    b = math.sqrt(1.0 - 2.0 * a * a)
+    dirs = []
+    for sz in (1.0, -1.0):
+        for sy in (1.0, -1.0):
+            for sx in (1.0, -1.0):
+                for (cx, cy, cz) in ((b, a, a), (a, b, a), (a, a, b)):
+                    dirs.append((sx * cx, sy * cy, sz * cz))
+    mu = np.array(dirs, dtype=np.float64)
+    w = np.full(len(dirs), 1.0 / len(dirs))
+    return mu, w
+
+
+def frequency_grid(n_freq: int, x_max: float):
+    """Doppler-profile frequency grid: offsets x, profile phi(x), weights.
+
+    phi(x) = exp(-x^2)/sqrt(pi) per unit Doppler width; weights are the
+    trapezoid rule on equidistant x in [-x_max, x_max], scaled so that
+    sum_nu w phi = 1 exactly.  Returns (x, phi, wphi) with wphi = w * phi.
+    """
+    if n_freq == 1:
+        x = np.zeros(1)
+        phi = np.ones(1) / math.sqrt(math.pi)
+        w = np.ones(1)
+    else:
+        x = np.linspace(-x_max, x_max, n_freq)
+        h = x[1] - x[0]
+        w = np.full(n_freq, h)
+        w[0] *= 0.5
+        w[-1] *= 0.5
+        phi = np.exp(-x * x) / math.sqrt(math.pi)
+    wphi = w * phi
+    wphi = wphi / wphi.sum()
+    return x, phi, wphi
+
+
+def formal_solution_raw(z, dx, dy, mu, wray, chi, S, wphi, I_bottom, I_top,
+                        want_intensity=False):
+    """Formal solution for given chi, S [nfreq, nz, ny, nx] (Sec. 3).
+
+    ``wphi`` [nfreq, nz, ny, nx] weights the frequency sum; ``I_bottom`` and
+    ``I_top`` [nfreq, ny, nx] are the entering intensities.  Returns
+    (Jbar, Jeff, U) [nz, ny, nx] and, if asked, I [nrays, nfreq, nz, ny, nx].
+    """
+    chi = np.ascontiguousarray(chi, dtype=np.float64)
+    nf, nz, ny, nx = chi.shape
+    S = np.ascontiguousarray(np.broadcast_to(S, chi.shape), dtype=np.float64)
+    wphi = np.ascontiguousarray(np.broadcast_to(wphi, chi.shape), dtype=np.float64)
+    Ib = np.ascontiguousarray(np.broadcast_to(I_bottom, (nf, ny, nx)), dtype=np.float64)
+    It = np.ascontiguousarray(np.broadcast_to(I_top, (nf, ny, nx)), dtype=np.float64)
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    wray = np.ascontiguousarray(wray, dtype=np.float64)
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    Jbar = np.empty((nz, ny, nx))
+    Jeff = np.empty((nz, ny, nx))
+    U = np.empty((nz, ny, nx))
+    I = np.empty((len(wray), nf, nz, ny, nx)) if want_intensity else None
+    rc = _load().orc_formal_solution(nx, ny, nz, float(dx), float(dy), _ptr(z), len(wray),
+                                     _ptr(mu), _ptr(wray), nf, _ptr(chi), _ptr(S),
+                                     _ptr(wphi), _ptr(Ib), _ptr(It), _ptr(Jbar), _ptr(Jeff),
+                                     _ptr(U), _ptr(I))
+    if rc != 0:
+        raise RuntimeError("oracle formal solution failed")
+    if want_intensity:
+        return Jbar, Jeff, U, I
+    return Jbar, Jeff, U
+
+
+# --------------------------------------------------------------------------
+# One grid level
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Level:
+    nx: int
+    ny: int
+    nz: int
+    dx: float
+    dy: float
+    z: np.ndarray
+    T: np.ndarray
+    n_tot: np.ndarray
+    c_ul: np.ndarray
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+
+class TwoLevelProblem:
+    """The problem W(n) = f on a hierarchy of grids (finest = index ``n_grids``).
+
+    ``levels[k]`` for k = 1 (coarsest) .. n_grids (finest), as in the paper.
+    Populations are arrays [2, nz, ny, nx]: index 0 lower, 1 upper level.
+    """
+
+    def __init__(self, atm, atom, n_grids: int = 1, quad_a: float | None = None):
+        self.atom = atom
+        self.n_grids = n_grids
+        self.mu, self.wray = a4_quadrature(quad_a)
+        self.x, self.phi, self.wphi = frequency_grid(atom.n_freq, atom.x_max)
+        fine = Level(atm.nx, atm.ny, atm.nz, atm.dx, atm.dy, np.asarray(atm.z, float),
+                     np.asarray(atm.T, float), np.asarray(atm.n_tot, float),
+                     np.asarray(atm.c_ul, float))
+        self.levels = {n_grids: fine}
+        for k in range(n_grids - 1, 0, -1):
+            self.levels[k] = coarsen_level(self.levels[k + 1])
+        self.fs_count = {k: 0 for k in self.levels}
+        self.sweep_count = {k: 0 for k in self.levels}
+        self.negatives = 0
+
+    # ---- opacity and source function (Eq. 1, CRD two-level atom) ----
+    def planck(self, T):
+        """B(T) at line centre in units of 2 h nu0^3/c^2."""
+        return 1.0 / np.expm1(self.atom.theta / T)
+
+    def opacity_source(self, lev: Level, n):
+        """chi_nu [nfreq, nvox] and S [nvox] from populations.
+
+        chi_nu = kappa (n_l g_u/g_l - n_u) phi(x_nu);  S = n_u/(n_l g_u/g_l - n_u),
+        the ratio of line emissivity n_u A_ul to line opacity, with
+        B_lu = (g_u/g_l) B_ul and B_ul = A_ul in these intensity units.
+        """
+        g = self.atom.g_ratio
+        nl = n[0].reshape(-1)
+        nu = n[1].reshape(-1)
+        diff = nl * g - nu
+        chi = self.atom.kappa * diff[None, :] * self.phi[:, None]
+        S = nu / diff
+        return chi, S
+
+    def formal_solution(self, k: int, n):
+        """One formal solution on level k with populations n: (Jbar, Jeff, U)."""
+        lev = self.levels[k]
+        nvox = lev.nx * lev.ny * lev.nz
+        nf = len(self.phi)
+        chi, S = self.opacity_source(lev, n)
+        chi = np.ascontiguousarray(chi)
+        Sf = np.ascontiguousarray(np.broadcast_to(S[None, :], (nf, nvox)))
+        wphi = np.ascontiguousarray(np.broadcast_to(self.wphi[:, None], (nf, nvox)))
+        Ib = np.ascontiguousarray(np.broadcast_to(
+            self.planck(lev.T[0]).reshape(1, -1), (nf, lev.nx * lev.ny)))
+        It = np.zeros((nf, lev.nx * lev.ny))
+        Jbar = np.empty(nvox)
+        Jeff = np.empty(nvox)
+        U = np.empty(nvox)
+        mu = np.ascontiguousarray(self.mu)
+        rc = _load().orc_formal_solution(
+            lev.nx, lev.ny, lev.nz, lev.dx, lev.dy, _ptr(np.ascontiguousarray(lev.z)),
+            len(self.wray), _ptr(mu), _ptr(self.wray), nf, _ptr(chi), _ptr(Sf),
+            _ptr(wphi), _ptr(Ib), _ptr(It), _ptr(Jbar), _ptr(Jeff), _ptr(U), None)
+        if rc != 0:
+            raise RuntimeError("oracle formal solution failed")
+        self.fs_count[k] += 1
+        return (Jbar.reshape(lev.shape), Jeff.reshape(lev.shape), U.reshape(lev.shape))
+
+    # ---- statistical equilibrium (Eqs. 2-4) ----
+    def rate_matrix(self, k: int, Jeff, U):
+        """Matrix M [nvox, 2, 2] with W(n) = M n (rows: conservation, level u).
+
+        Row 0 is particle conservation (Eq. 3).  Row 1 is the rate equation of
+        the upper level in the sign convention of Eq. 2: n_u sum P_uj - sum n_j P_ju.
+        Preconditioned radiative rates (Rybicki & Hummer 1991):
+            P_lu = B_lu Jeff + C_lu,   P_ul = A_ul U + B_ul Jeff + C_ul,
+        with U = 1 - Lambda*.  For Jeff = Jbar - Lambda* S(n) evaluated at the
+        same n these equal the plain rates B_lu Jbar + C_lu and A_ul + B_ul
+        Jbar + C_ul applied to n.
+        """
+        lev = self.levels[k]
+        A = self.atom.a_ul
+        g = self.atom.g_ratio
+        c_ul = lev.c_ul.reshape(-1)
+        c_lu = c_ul * g * np.exp(-self.atom.theta / lev.T.reshape(-1))
+        je = Jeff.reshape(-1)
+        uu = U.reshape(-1)
+        P_lu = g * A * je + c_lu
+        P_ul = A * uu + A * je + c_ul
+        M = np.empty((je.size, 2, 2))
+        M[:, 0, 0] = 1.0
+        M[:, 0, 1] = 1.0
+        M[:, 1, 0] = -P_lu
+        M[:, 1, 1] = P_ul
+        return M
+
+    def default_rhs(self, k: int):
+        lev = self.levels[k]
+        f = np.zeros((2,) + lev.shape)
+        f[0] = lev.n_tot
+        return f
+
+    def apply(self, M, n):
+        nv = n.reshape(2, -1).T                      # [nvox, 2]
+        out = np.einsum("vij,vj->vi", M, nv)
+        return out.T.reshape(n.shape)
+
+    def solve(self, M, f):
+        fv = f.reshape(2, -1).T[:, :, None]
+        x = np.linalg.solve(M, fv)[:, :, 0]
+        return x.T.reshape(f.shape)
+
+    def W(self, k: int, n):
+        """W^k_*(n): rates from an extra formal solution with n (Eq. 5)."""
+        _, Jeff, U = self.formal_solution(k, n)
+        return self.apply(self.rate_matrix(k, Jeff, U), n)
+
+    def zero_radiation(self, k: int):
+        """Populations from statistical equilibrium with J = 0 (Sec. 4.9)."""
+        lev = self.levels[k]
+        zeros = np.zeros(lev.shape)
+        ones = np.ones(lev.shape)
+        return self.solve(self.rate_matrix(k, zeros, ones), self.default_rhs(k))
+
+    def mali_sweep(self, k: int, n, f=None):
+        """One MALI iteration on level k solving W(n) = f; returns (n_new, C)."""
+        if f is None:
+            f = self.default_rhs(k)
+        _, Jeff, U = self.formal_solution(k, n)
+        n_new = self.solve(self.rate_matrix(k, Jeff, U), f)
+        self.sweep_count[k] += 1
+        return n_new, max_rel_change(n_new, n)
+
+    # ---- multigrid (Secs. 2.2-2.3) ----
+    def restrict(self, k_fine: int, a):
+        return restrict_fw(a)
+
+    def prolong(self, k_fine: int, a_coarse):
+        return prolong_trilinear(a_coarse, self.levels[k_fine].z)
+
+    def vcycle(self, k: int, n: dict, f: dict, first: bool, params):
+        """One FAS V-cycle from level k down to level 1; updates n[k] in place."""
+        nu_pre = params["nu0"] if (first and k == self.n_grids) else params["nu1"]
+        for _ in range(nu_pre):
+            n[k], _ = self.mali_sweep(k, n[k], f[k])
+        # residual with an extra formal solution (Eq. 5)
+        r = f[k] - self.W(k, n[k])
+        # coarse-grid equation (Eq. 9)
+        n[k - 1] = self.restrict(k, n[k])
+        n_before = n[k - 1].copy()
+        f[k - 1] = self.restrict(k, r) + self.W(k - 1, n[k - 1])
+        if k - 1 == 1:
+            for _ in range(params["nu3"]):
+                n[1], _ = self.mali_sweep(1, n[1], f[1])
+        else:
+            self.vcycle(k - 1, n, f, False, params)
+        # relative correction (Eq. 10) and its interpolation (Eq. 11)
+        e = (n[k - 1] - n_before) / n_before
+        n_old = n[k]
+        n_new = n_old * (1.0 + self.prolong(k, e))
+        bad = n_new <= 0.0
+        self.negatives += int(bad.sum())
+        n_new[bad] = 0.1 * n_old[bad]
+        n[k] = n_new
+        for _ in range(params["nu2"]):
+            n[k], _ = self.mali_sweep(k, n[k], f[k])
+
+    def fas_cycle(self, n_fine, first: bool, params):
+        L = self.n_grids
+        n = {L: n_fine.copy()}
+        f = {L: self.default_rhs(L)}
+        self.vcycle(L, n, f, first, params)
+        return n[L], max_rel_change(n[L], n_fine)
+
+
+def max_rel_change(n_new, n_old):
+    """C = max |n_new - n_old| / |n_new| over all levels and nodes (Sec. 3.3)."""
+    return float(np.max(np.abs(n_new - n_old) / np.abs(n_new)))
+
+
+def max_rel_error(n, n_ref):
+    """E_inf = max |n - n_ref| / |n_ref| (Sec. 3.3)."""
+    return float(np.max(np.abs(n - n_ref) / np.abs(n_ref)))
+
+
+# --------------------------------------------------------------------------
+# Grid transfer (Sec. 4.1, 4.4-4.7)
+# --------------------------------------------------------------------------
+
+def restrict_fw(a):
+    """Full weighting of [..., nz, ny, nx] onto every second node.
+
+    Coarse node (K, J, I) sits on fine node (2K, 2J, 2I).  Its value is the
+    sum over the 27 fine nodes (2K+c, 2J+b, 2I+a), a, b, c in {-1, 0, 1}, with
+    weights w_a w_b w_c, w_0 = 1/2 and w_{+-1} = 1/4; x and y are periodic.  On
+    the two fixed boundary planes (K = 0 and the top) the z stencil is the
+    single fine plane 2K (weight 1): the boundary heights are kept.
+    """
+    a = np.asarray(a, dtype=np.float64)
+    nz, ny, nx = a.shape[-3:]
+    if nz % 2 != 1 or ny % 2 or nx % 2:
+        raise ValueError("grid does not coarsen")
+    nzc, nyc, nxc = (nz + 1) // 2, ny // 2, nx // 2
+    wts = {-1: 0.25, 0: 0.5, 1: 0.25}
+    out = np.zeros(a.shape[:-3] + (nzc, nyc, nxc))
+    K = np.arange(nzc)
+    interior = (K > 0) & (K < nzc - 1)
+    for c in (-1, 0, 1):
+        zi = np.clip(2 * K + c, 0, nz - 1)
+        wz = np.where(interior, wts[c], 1.0 if c == 0 else 0.0)
+        for b in (-1, 0, 1):
+            yi = (2 * np.arange(nyc) + b) % ny
+            for aa in (-1, 0, 1):
+                xi = (2 * np.arange(nxc) + aa) % nx
+                block = a[..., zi[:, None, None], yi[None, :, None], xi[None, None, :]]
+                out += (wz[:, None, None] * wts[b] * wts[aa]) * block
+    return out
+
+
+def prolong_trilinear(ac, z_fine):
+    """Trilinear interpolation of [..., nzc, nyc, nxc] onto the finer grid.
+
+    Fine node i on an even index coincides with coarse node i/2; on an odd
+    index it lies half-way (x, y: uniform spacing, periodic) or, in z, at the
+    physical height z_fine[k] between the coarse planes at z_fine[k-1] and
+    z_fine[k+1].  The value is the sum over the 8 surrounding coarse nodes of
+    the product of the three 1D linear weights.
+    """
+    ac = np.asarray(ac, dtype=np.float64)
+    nzc, nyc, nxc = ac.shape[-3:]
+    nz, ny, nx = 2 * nzc - 1, 2 * nyc, 2 * nxc
+
+    def axis_periodic(n, nc):
+        i = np.arange(n)
+        i0 = (i // 2) % nc
+        i1 = np.where(i % 2 == 1, (i // 2 + 1) % nc, i0)
+        w1 = np.where(i % 2 == 1, 0.5, 0.0)
+        return i0, i1, 1.0 - w1, w1
+
+    k = np.arange(nz)
+    k0 = k // 2
+    k1 = np.where(k % 2 == 1, k0 + 1, k0)
+    zf = np.asarray(z_fine, dtype=np.float64)
+    t = np.zeros(nz)
+    odd = k % 2 == 1
+    t[odd] = (zf[k[odd]] - zf[k[odd] - 1]) / (zf[k[odd] + 1] - zf[k[odd] - 1])
+    zsets = ((k0, 1.0 - t), (k1, t))
+    y0, y1, wy0, wy1 = axis_periodic(ny, nyc)
+    x0, x1, wx0, wx1 = axis_periodic(nx, nxc)
+    out = np.zeros(ac.shape[:-3] + (nz, ny, nx))
+    for (zi, wz) in zsets:
+        for (yi, wy) in ((y0, wy0), (y1, wy1)):
+            for (xi, wx) in ((x0, wx0), (x1, wx1)):
+                block = ac[..., zi[:, None, None], yi[None, :, None], xi[None, None, :]]
+                out += (wz[:, None, None] * wy[None, :, None] * wx[None, None, :]) * block
+    return out
+
+
+def coarsen_level(lev: Level) -> Level:
+    """Atmosphere on the next coarser grid (Sec. 4.1, 4.7).
+
+    The grid keeps every second node (z coordinates by dropping nodes, so the
+    boundary heights stay fixed); T, n_tot and the collisional rate are
+    carried over by full weighting.
+    """
+    return Level(lev.nx // 2, lev.ny // 2, (lev.nz + 1) // 2, 2 * lev.dx, 2 * lev.dy,
+                 lev.z[::2].copy(), restrict_fw(lev.T), restrict_fw(lev.n_tot),
+                 restrict_fw(lev.c_ul))
+
+
+# --------------------------------------------------------------------------
+# Drivers
+# --------------------------------------------------------------------------
+
+def mali_solve(prob: TwoLevelProblem, tol: float, max_iter: int = 100000, n0=None,
+               history=None):
+    """Plain MALI on the finest grid from the zero-radiation start."""
+    L = prob.n_grids
+    n = prob.zero_radiation(L) if n0 is None else n0.copy()
+    for it in range(1, max_iter + 1):
+        n, C = prob.mali_sweep(L, n)
+        if history is not None:
+            history.append(C)
+        if C < tol:
+            return n, it
+    raise RuntimeError("MALI did not converge")
+
+
+def fas_solve(prob: TwoLevelProblem, tol: float, params, max_cycles: int = 1000,
+              n0=None, history=None):
+    """FAS V-cycles on the finest grid from the zero-radiation start."""
+    L = prob.n_grids
+    n = prob.zero_radiation(L) if n0 is None else n0.copy()
+    for cyc in range(1, max_cycles + 1):
+        n, C = prob.fas_cycle(n, cyc == 1, params)
+        if history is not None:
+            history.append(C)
+        if C < tol:
+            return n, cyc
+    raise RuntimeError("FAS did not converge")
+
+
+def fmg_solve(prob: TwoLevelProblem, tol: float, params, max_cycles: int = 1000,
+              history=None):
+    """Full multigrid (Sec. 2.3): solve on level 1, interpolate the full
+    approximation upward with one V-cycle per intermediate level, then
+    regular V-cycles on the finest grid until C < tol."""
+    L = prob.n_grids
+    n1 = prob.zero_radiation(1)
+    for _ in range(params["nu_fmg"]):
+        n1, _ = prob.mali_sweep(1, n1)
+    n_k = n1
+    for k in range(2, L + 1):
+        n_k = prob.prolong(k, n_k)
+        if k < L:
+            n = {k: n_k}
+            f = {k: prob.default_rhs(k)}
+            prob.vcycle(k, n, f, False, params)
+            n_k = n[k]
+    n = n_k
+    for cyc in range(1, max_cycles + 1):
+        n, C = prob.fas_cycle(n, cyc == 1, params)
+        if history is not None:
+            history.append(C)
+        if C < tol:
+            return n, cyc
+    raise RuntimeError("FMG did not converge")
