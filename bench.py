@@ -1,0 +1,365 @@
+"""Benchmark: formal-solution throughput of FAS V-cycles on one GB300.
+
+Workload: the two-level atom (CRD, 9 Doppler frequencies, A4 rays) in a
+64x64x128-cell box (129 nodes in z), eps = 1e-4, exponentially stratified
+line-centre optical depth 1e-4..1e4 with seeded log-normal perturbations
+(sigma 0.3, k^-5/3 spectrum); 3-grid FAS V-cycles with
+(nu0, nu1, nu2, nu3) = (0, 2, 2, 32), FP64 throughout.
+
+One step is one V-cycle, which runs every part of the hot path: formal
+solutions on all grids (plane sweeps), MALI rate updates, residuals,
+full-weighting restriction, the tau-corrected right-hand side, coarse-grid
+iterations, the interpolated relative correction and the convergence check.
+value = (nodes x rays x frequencies swept by all formal solutions of the
+timed steps) / (summed device time of the steps), in G units/s.
+
+Under torchrun each rank solves its own independently seeded atmosphere
+(replicas; no collective touches the solve), and the slowest rank's time
+counts.  --impl reference times the FP64 CPU oracle on the host instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "two-level atom, 64x64x129 nodes, eps=1e-4, lognormal sigma=0.3, 3-grid FAS"
+GRID = (64, 64, 129)
+NU = dict(nu_fmg=16, nu0=0, nu1=2, nu2=2, nu3=32)
+N_GRIDS = 3
+METRIC = "FS Gvoxel*ray*freq/s (3-grid FAS V-cycle step)"
+UNIT = "Gunit/s"
+FS_UNITS_PER_FINE = GRID[0] * GRID[1] * GRID[2] * 24 * 9
+# FP64 floating-point operations per (node, ray, frequency) of the sweep as
+# the method states it (bilinear I_up 7, optical path 1, exp 1, u 2, w0 1,
+# w_up 1, new I 5, two accumulations 4, plus 16 per node and ray shared by
+# the 9 frequencies for the chi/S interpolation and dtau), exp and the
+# division counted as one operation each.
+ALG_FLOPS_PER_UNIT = 7 + 1 + 1 + 2 + 1 + 1 + 5 + 4 + 16.0 / 9.0
+FP64_NOMINAL_TFLOPS = 1.25      # GB300, at the 2070 MHz maximum SM clock
+SM_MAX_MHZ = 2070.0
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def build_problem(seed):
+    from paper_1701_01607_gb300 import synth
+    return synth.stratified_two_level(GRID[0], GRID[1], GRID[2], eps=1e-4, sigma=0.3,
+                                      seed=seed)
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import torch
+
+    from paper_1701_01607_gb300 import mg3d as m
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    m.load(build_if_missing=True)
+    atm, atom = build_problem(seed=1 + rank)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def make(prec):
+        h = m.mg3d_create(atm, atom, n_grids=N_GRIDS, fs_prec=prec, **NU)
+        m.mg3d_set_stream(h, stream.cuda_stream)
+        return h
+
+    def timed_cycles(h, steps, warmup, timing):
+        for i in range(warmup):
+            m.mg3d_fas_vcycle(h, i == 0)
+        m.mg3d_set_timing(h, timing)
+        m.mg3d_reset_counters(h)
+        ms = []
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            m.mg3d_fas_vcycle(h, False)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms, m.mg3d_get_counters(h)
+
+    # ---- main measurement: FP64 V-cycles
+    h = make(m.MG3D_PREC_F64)
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ms, cnt = timed_cycles(h, args.steps, args.warmup, timing=True)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = sum(ms)
+    units = cnt["fs_units"]
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        u = torch.tensor([units], device="cuda", dtype=torch.float64)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        units = float(u.item())
+    value = units / (total_ms * 1e-3) / 1e9
+    fine = N_GRIDS
+    fine_ms = cnt["level_fs_kernel_ms"][fine] / max(1, cnt["level_fs_timed_launches"][fine])
+    fine_units = cnt["level_fs_units"][fine] / max(1, cnt["level_fs_launches"][fine])
+
+    # ---- end to end: host populations in, V-cycle, host populations out
+    nx, ny, nz = GRID
+    pinned_in = torch.empty((2, nz, ny, nx), dtype=torch.float64, pin_memory=True).numpy()
+    pinned_out = torch.empty((2, nz, ny, nx), dtype=torch.float64, pin_memory=True).numpy()
+    pinned_in[...] = m.mg3d_get_populations(h, fine)
+    m.mg3d_set_timing(h, False)
+    m.mg3d_reset_counters(h)
+    e2e_ms = []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m.mg3d_set_populations(h, fine, pinned_in)
+        m.mg3d_fas_vcycle(h, False)
+        m.mg3d_get_populations(h, fine, pinned_out)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_units = m.mg3d_get_counters(h)["fs_units"]
+    launches = cnt["kernel_launches"]
+    m.mg3d_destroy(h)
+
+    # ---- mixed precision (FP32 formal solution, FP64 rates): same step
+    h32 = make(m.MG3D_PREC_F32)
+    ms32, cnt32 = timed_cycles(h32, args.steps, args.warmup, timing=True)
+    m.mg3d_destroy(h32)
+    fine_ms32 = cnt32["level_fs_kernel_ms"][fine] / max(1, cnt32["level_fs_timed_launches"][fine])
+
+    result = None
+    if rank == 0:
+        sm_mhz = clk.get("sm_mhz") or SM_MAX_MHZ
+        peak = FP64_NOMINAL_TFLOPS * sm_mhz / SM_MAX_MHZ
+        achieved = ALG_FLOPS_PER_UNIT * fine_units / (fine_ms * 1e-3) / 1e12
+        result = {
+            "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(total_ms / args.steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": list(GRID), "n_grids": N_GRIDS,
+                       "n_freq": 9, "rays": 24, **NU, "fs_precision": "f64",
+                       "parallelism": f"replicas x{world}",
+                       "l2": "256 MB buffer written between timed steps"},
+            "roofline": {"kernel": "sweep_kernel<double> (finest grid)", "bound": "alu",
+                         "achieved": round(achieved, 4), "peak": round(peak, 4),
+                         "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                         "traffic": None,
+                         "peak_source": "nominal FP64 1.25 TFLOP/s x median SM clock / 2070 MHz",
+                         "alg_flops_per_unit": round(ALG_FLOPS_PER_UNIT, 3),
+                         "units_per_launch": fine_units,
+                         "ms_per_launch": round(fine_ms, 4)},
+            "e2e": {"value": round(e2e_units / (sum(e2e_ms) * 1e-3) / 1e9, 4), "unit": UNIT,
+                    "h2d_bytes_per_step": int(pinned_in.nbytes),
+                    "d2h_bytes_per_step": int(pinned_out.nbytes)},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "mixed_precision": {
+                "fs_precision": "f32 (rates f64)",
+                "value": round(cnt32["fs_units"] / (sum(ms32) * 1e-3) / 1e9, 4),
+                "ms_per_step": round(sum(ms32) / args.steps, 4),
+                "fine_sweep_ms": round(fine_ms32, 4),
+                "fine_sweep_gunits_s": round(fine_units / (fine_ms32 * 1e-3) / 1e9, 3)},
+            "fine_sweep_gunits_s": round(fine_units / (fine_ms * 1e-3) / 1e9, 3),
+        }
+        if not args.no_tts and world == 1:
+            result["time_to_solution"] = time_to_solution(m, atm, atom, stream)
+        if world == 1 and not args.no_cpu:
+            result["cpu_baseline"] = cpu_baseline(atm, atom, samples=2)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return result
+
+
+def time_to_solution(m, atm, atom, stream, tol=1e-3):
+    """MALI, FAS and FMG from the zero-radiation start to C < tol (FP64), with
+    their true error E_inf against a FAS solution converged to C < 1e-9."""
+    out = {}
+    ref_h = m.mg3d_create(atm, atom, n_grids=N_GRIDS, fs_prec=m.MG3D_PREC_F64, **NU)
+    m.mg3d_set_stream(ref_h, stream.cuda_stream)
+    m.mg3d_fas_solve(ref_h, 1e-9, 400, n_grids=N_GRIDS)
+    n_ref = m.mg3d_get_populations(ref_h, N_GRIDS)
+    m.mg3d_destroy(ref_h)
+    for method, fn, grids, cap in (("mali", m.mg3d_mali_solve, 1, 200000),
+                                   ("fas", m.mg3d_fas_solve, N_GRIDS, 400),
+                                   ("fmg", m.mg3d_fmg_solve, N_GRIDS, 400)):
+        h = m.mg3d_create(atm, atom, n_grids=grids, fs_prec=m.MG3D_PREC_F64, **NU)
+        m.mg3d_set_stream(h, stream.cuda_stream)
+        st = fn(h, tol, cap, n_grids=grids)
+        n = m.mg3d_get_populations(h, grids)
+        m.mg3d_destroy(h)
+        out[method] = {"seconds": round(st["seconds"], 4), "iterations": st["iterations"],
+                       "fine_fs_equivalents": round(st["fine_fs_equivalents"], 3),
+                       "e_inf": float(np.max(np.abs(n - n_ref) / np.abs(n_ref))),
+                       "negatives": st["negatives"]}
+    out["tol"] = tol
+    out["speedup_fas"] = round(out["mali"]["seconds"] / out["fas"]["seconds"], 3)
+    out["speedup_fmg"] = round(out["mali"]["seconds"] / out["fmg"]["seconds"], 3)
+    return out
+
+
+
+def cpu_baseline(atm, atom, samples=2):
+    """The FP64 CPU oracle as it stands: fine-grid formal solutions."""
+    from oracle import mg3d_oracle as O
+    prob = O.TwoLevelProblem(atm, atom, n_grids=1)
+    n = prob.zero_radiation(1)
+    t0 = time.perf_counter()
+    for _ in range(samples):
+        prob.formal_solution(1, n)
+    dt = time.perf_counter() - t0
+    return {"value": round(samples * FS_UNITS_PER_FINE / dt / 1e9, 6), "unit": UNIT,
+            "cores": 1, "kind": "oracle",
+            "sample": f"{samples} fine-grid formal solutions of the 64x64x129 box "
+                      f"({samples * FS_UNITS_PER_FINE:.3g} units, {dt:.1f} s, 1 thread)"}
+
+
+# ---------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return None
+    atm, atom = build_problem(seed=1)
+    from oracle import mg3d_oracle as O
+    prob = O.TwoLevelProblem(atm, atom, n_grids=1)
+    n = prob.zero_radiation(1)
+    for _ in range(args.warmup):
+        prob.formal_solution(1, n)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        prob.formal_solution(1, n)
+    dt = time.perf_counter() - t0
+    value = args.steps * FS_UNITS_PER_FINE / dt / 1e9
+    sample = (f"{args.steps} fine-grid formal solutions of the 64x64x129 box per run, "
+              f"one per step, FP64 C oracle, 1 thread")
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": list(GRID), "fs_precision": "f64"},
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def run_profile_case(prec_name, launches):
+    """A few finest-grid formal solutions of the bench workload, for ncu."""
+    from paper_1701_01607_gb300 import mg3d as m
+    m.load(build_if_missing=True)
+    atm, atom = build_problem(seed=1)
+    prec = m.MG3D_PREC_F64 if prec_name == "f64" else m.MG3D_PREC_F32
+    h = m.mg3d_create(atm, atom, n_grids=N_GRIDS, fs_prec=prec, **NU)
+    try:
+        for _ in range(launches):
+            m.mg3d_formal_solve(h, N_GRIDS, want=False)
+        print("profile case:", prec_name, m.mg3d_get_fs_config(h, N_GRIDS), flush=True)
+    finally:
+        m.mg3d_destroy(h)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--no-tts", action="store_true", help="skip time-to-solution runs")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--profile-sweep", choices=["f64", "f32"],
+                    help="only run a few finest-grid formal solutions (for ncu)")
+    ap.add_argument("--profile-launches", type=int, default=3)
+    args = ap.parse_args()
+    if args.profile_sweep:
+        run_profile_case(args.profile_sweep, args.profile_launches)
+        return
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    res = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

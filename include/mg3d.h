@@ -1,0 +1,226 @@
+/*
+ * mg3d.h -- C ABI of a GB300 (sm_103a) library for non-LTE 3D radiative
+ * transfer with a non-linear multigrid method (Bjorgen & Leenaarts 2017).
+ *
+ * The problem (Sec. 2.1): find atomic level populations n on a Cartesian grid
+ * such that the transfer equation dI/dtau = S(n) - I (Eq. 1) and statistical
+ * equilibrium (Eq. 2), with the first rate equation replaced by particle
+ * conservation (Eq. 3), hold everywhere: W(n) = f with f = (n_tot, 0) per node
+ * (Eq. 4).  The library solves it with MALI (Jacobi iteration with the
+ * diagonal approximate operator), FAS V-cycles (Sec. 2.2, Eqs. 5-11) and full
+ * multigrid (Sec. 2.3) on one GPU.
+ *
+ * Model supported: a static two-level atom in complete redistribution with a
+ * Doppler line profile sampled at n_freq points, no background continuum.
+ *
+ * Conventions for every entry point:
+ *  - returns MG3D_OK (0) or a negative MG3D_E_* code; no exception crosses the
+ *    ABI; mg3d_last_error() then gives a message (per calling thread);
+ *  - arrays are C-ordered: a field is [nz][ny][nx] (x fastest) and a set of
+ *    populations is [2][nz][ny][nx] with index 0 the lower and 1 the upper
+ *    level; z[0] is the bottom boundary plane;
+ *  - pointers named *_host are host memory owned by the caller; the library
+ *    reads them during the call (or writes them before returning) and keeps
+ *    no reference.  All other state lives in device memory that the handle
+ *    owns and frees in mg3d_destroy;
+ *  - "level" numbers grids as the paper does: 1 is the coarsest and
+ *    n_grids the finest;
+ *  - work is ordered on the handle's CUDA stream; calls that return host data
+ *    or a convergence measure synchronise that stream; a handle must not be
+ *    used from two threads at once.
+ */
+#ifndef MG3D_H
+#define MG3D_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MG3D_OK 0
+#define MG3D_E_ARG (-1)       /* bad argument (null pointer, out of range) */
+#define MG3D_E_GRID (-2)      /* grid does not coarsen n_grids - 1 times */
+#define MG3D_E_CUDA (-3)      /* a CUDA call failed */
+#define MG3D_E_OOM (-4)       /* device or host allocation failed */
+#define MG3D_E_DIVERGED (-5)  /* a solve produced non-finite populations */
+#define MG3D_E_MAXITER (-6)   /* iteration or cycle cap reached before tol */
+#define MG3D_E_STATE (-8)     /* call not valid in the handle's current state */
+
+#define MG3D_MAX_GRIDS 8
+
+/* Precision of the formal solution (interpolation, opacities, intensities).
+ * Rate equations, residuals and grid transfer are always FP64. */
+#define MG3D_PREC_F64 0
+#define MG3D_PREC_F32 1
+
+typedef struct mg3d_handle mg3d_handle;
+
+/* Input atmosphere on the finest grid (Sec. 3.1, 4.1-4.2). */
+typedef struct {
+    int nx, ny, nz;        /* nodes; x, y periodic, z bounded (nz odd) */
+    double dx, dy;         /* constant horizontal spacing */
+    const double *z;       /* [nz] node heights, strictly increasing */
+    const double *T;       /* [nz][ny][nx] gas temperature, K */
+    const double *n_tot;   /* [nz][ny][nx] total number density of the atom */
+    const double *c_ul;    /* [nz][ny][nx] collisional de-excitation rate */
+} mg3d_atmosphere;
+
+/* Two-level model atom (Sec. 3.2).  Intensities are in units of
+ * 2 h nu0^3 / c^2, so B_ul = A_ul and B_lu = g_ratio A_ul.  The line opacity
+ * at normalised offset x is kappa (n_l g_ratio - n_u) exp(-x^2)/sqrt(pi) and
+ * the source function n_u / (n_l g_ratio - n_u).  The frequency grid is
+ * n_freq equidistant offsets in [-x_max, x_max] with trapezoid weights,
+ * renormalised so that the weighted profile sums to one. */
+typedef struct {
+    double a_ul;     /* Einstein A_ul, the rate unit */
+    double g_ratio;  /* g_u / g_l */
+    double theta;    /* h nu0 / k in K; B(T) = 1/(exp(theta/T) - 1) */
+    double kappa;    /* line opacity constant */
+    int n_freq;      /* frequency points across the line, >= 1 */
+    double x_max;    /* half width of the grid in Doppler widths */
+} mg3d_atom;
+
+/* Angle quadrature: the 24-direction A4 set of Carlson (Sec. 3): per octant
+ * the permutations of (a, a, b), b = sqrt(1 - 2a^2), weights 1/24.
+ * a <= 0 selects a = sqrt((4 - sqrt(6.4))/12) = 0.3500212..., which
+ * integrates mu^4 exactly. */
+typedef struct {
+    double a;
+} mg3d_quadrature;
+
+/* Multigrid schedule (Sec. 2.2-2.3, 4.10, Table 1). */
+typedef struct {
+    int n_grids;   /* number of grids l, 1..MG3D_MAX_GRIDS */
+    int nu_fmg;    /* MALI iterations on the coarsest grid in FMG */
+    int nu0;       /* pre-smoothing on the finest grid in the first V-cycle */
+    int nu1;       /* pre-smoothing iterations */
+    int nu2;       /* post-smoothing iterations */
+    int nu3;       /* iterations on the coarsest grid */
+    int fs_prec;   /* MG3D_PREC_F64 or MG3D_PREC_F32 */
+} mg3d_params;
+
+/* Outcome of a solve. */
+typedef struct {
+    int iterations;              /* MALI sweeps (mali) or V-cycles (fas, fmg) */
+    int sweeps[MG3D_MAX_GRIDS + 1];            /* MALI sweeps per level */
+    int formal_solutions[MG3D_MAX_GRIDS + 1];  /* formal solutions per level */
+    double last_change;          /* C of the last iteration or cycle */
+    long long negatives;         /* populations reset by the 10 % rule */
+    double seconds;              /* wall time of the solve */
+    double fine_fs_equivalents;  /* sum over levels of FS count x 8^(k - l) */
+} mg3d_stats;
+
+/* Counters of the handle since creation (or the last reset).  The level_*
+ * arrays split the sweep counters by grid level (index = level). */
+typedef struct {
+    long long kernel_launches;   /* launches of this library's kernels */
+    long long fs_launches;       /* formal-solution sweep launches */
+    double fs_units;             /* nodes x rays x frequencies swept */
+    double fs_kernel_ms;         /* summed device time of the sweep kernel,
+                                    valid only while timing is enabled */
+    long long fs_timed_launches; /* sweeps included in fs_kernel_ms */
+    long long level_fs_launches[MG3D_MAX_GRIDS + 1];
+    double level_fs_units[MG3D_MAX_GRIDS + 1];
+    double level_fs_kernel_ms[MG3D_MAX_GRIDS + 1];
+    long long level_fs_timed_launches[MG3D_MAX_GRIDS + 1];
+} mg3d_counters;
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *mg3d_last_error(void);
+
+/* Create a solver: validates the grid (Sec. 4.2; MG3D_E_GRID unless every
+ * coarsening keeps nz odd and nx, ny even, i.e. nz = A 2^(l-1) + 1 and
+ * nx, ny = B 2^(l-1) with A, B >= 1 for l = n_grids), checks dx, dy > 0 and z
+ * increasing (MG3D_E_ARG), copies the atmosphere to device memory, builds the
+ * coarser grids by
+ * dropping every second node and full-weighting T, n_tot and c_ul (Sec. 4.1,
+ * 4.7), and precomputes the per-plane upwind geometry of every ray.
+ * Populations start at zero-radiation equilibrium (Sec. 4.9) on every grid.
+ * On success *out holds the handle; on failure *out is NULL. */
+int mg3d_create(const mg3d_atmosphere *atm, const mg3d_atom *atom,
+                const mg3d_quadrature *quad, const mg3d_params *params,
+                mg3d_handle **out);
+
+/* Free every device and host resource of the handle (NULL is accepted). */
+int mg3d_destroy(mg3d_handle *h);
+
+/* Order the handle's work on an existing CUDA stream (a cudaStream_t passed
+ * as void*; NULL restores the handle's own stream).  The caller keeps
+ * ownership of the stream and must keep it alive while the handle uses it. */
+int mg3d_set_stream(mg3d_handle *h, void *cuda_stream);
+
+/* Shape of a level's grid. */
+int mg3d_level_shape(const mg3d_handle *h, int level, int *nx, int *ny, int *nz);
+
+/* Copy a level's populations [2][nz][ny][nx] out to, or in from, host memory. */
+int mg3d_get_populations(mg3d_handle *h, int level, double *n_host);
+int mg3d_set_populations(mg3d_handle *h, int level, const double *n_host);
+
+/* Reset a level's populations to the zero-radiation solution of statistical
+ * equilibrium (all radiative rates from J = 0; Sec. 4.9) and its right-hand
+ * side to f = (n_tot, 0). */
+int mg3d_init_zero_radiation(mg3d_handle *h, int level);
+
+/* One formal solution on a level with its current populations (Sec. 3:
+ * short characteristics, linear interpolation, A4 rays, CRD).  Optional host
+ * outputs [nz][ny][nx]: Jeff = Jbar - Lambda* S (the profile-averaged mean
+ * intensity minus its local part) and U = 1 - Lambda* (Lambda* the diagonal
+ * of the Lambda operator).  Either pointer may be NULL. */
+int mg3d_formal_solve(mg3d_handle *h, int level, double *jeff_host, double *u_host);
+
+/* n_sweeps MALI iterations on a level solving W(n) = f for that level's f
+ * (f = (n_tot, 0) on the finest grid, the tau-corrected f of Eq. 9 on a
+ * coarser one).  *max_rel_change (nullable) receives C of the last sweep:
+ * max |n_new - n_old| / |n_new| over levels and nodes (Sec. 3.3). */
+int mg3d_mali_sweep(mg3d_handle *h, int level, int n_sweeps, double *max_rel_change);
+
+/* Residual r = f - W_*(n) of a level (Eq. 5), with an extra formal solution
+ * for the current populations; r_host is [2][nz][ny][nx]. */
+int mg3d_residual(mg3d_handle *h, int level, double *r_host);
+
+/* One FAS V-cycle from the finest grid (Sec. 2.2).  is_first selects nu0
+ * instead of nu1 for the finest-grid pre-smoothing (Sec. 4.10).
+ * *max_rel_change (nullable) receives C over the whole cycle. */
+int mg3d_fas_vcycle(mg3d_handle *h, int is_first, double *max_rel_change);
+
+/* Plain MALI on the finest grid from the zero-radiation start until C < tol
+ * (MG3D_E_MAXITER after max_sweeps).  stats is nullable. */
+int mg3d_mali_solve(mg3d_handle *h, double tol, int max_sweeps, mg3d_stats *stats);
+
+/* FAS V-cycles from the zero-radiation start until C(cycle) < tol. */
+int mg3d_fas_solve(mg3d_handle *h, double tol, int max_cycles, mg3d_stats *stats);
+
+/* Full multigrid (Sec. 2.3): nu_fmg MALI iterations on grid 1 from the
+ * zero-radiation start, trilinear interpolation of the full approximation to
+ * each finer grid with one V-cycle there, then V-cycles on the finest grid
+ * until C(cycle) < tol. */
+int mg3d_fmg_solve(mg3d_handle *h, double tol, int max_cycles, mg3d_stats *stats);
+
+/* Grid-transfer operators on host arrays of ncomp fields, for checking.
+ * mg3d_restrict: full weighting (Sec. 4.4) from level_fine to level_fine-1,
+ * fine_host [ncomp][fine nodes] -> coarse_host [ncomp][coarse nodes].
+ * mg3d_prolong: trilinear interpolation (Sec. 4.5) from level_fine-1 to
+ * level_fine.  1 <= ncomp <= 4. */
+int mg3d_restrict(mg3d_handle *h, int level_fine, int ncomp, const double *fine_host,
+                  double *coarse_host);
+int mg3d_prolong(mg3d_handle *h, int level_fine, int ncomp, const double *coarse_host,
+                 double *fine_host);
+
+/* Sweep launch shape of a level: freq_per_block frequencies per thread block,
+ * bands = thread blocks (one cluster) sharing each horizontal plane, threads
+ * per block.  The library picks one at creation; this overrides it.
+ * Returns MG3D_E_ARG if the shape does not fit in shared memory. */
+int mg3d_set_fs_config(mg3d_handle *h, int level, int freq_per_block, int bands,
+                       int threads);
+int mg3d_get_fs_config(const mg3d_handle *h, int level, int *freq_per_block, int *bands,
+                       int *threads);
+
+/* Per-launch device timing of the sweep kernel (CUDA events on the handle's
+ * stream) on or off, counters and their reset. */
+int mg3d_set_timing(mg3d_handle *h, int enable);
+int mg3d_get_counters(mg3d_handle *h, mg3d_counters *out);
+int mg3d_reset_counters(mg3d_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MG3D_H */

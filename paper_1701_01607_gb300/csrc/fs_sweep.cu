@@ -1,0 +1,264 @@
+// Formal solution: opacity/source kernel and the plane-sweep kernel.
+//
+// The transfer equation (Eq. 1) is solved with short characteristics and
+// linear interpolation (Sec. 3, Kunasz & Auer 1988) for the 24 rays of the A4
+// set.  For a ray going up, plane k depends only on plane k-1: the short
+// characteristic of each node crosses plane k-1 at the same horizontal offset
+// for all nodes of the plane (periodic in x and y, Sec. 4.2), so a whole plane
+// is one parallel step and the sweep is a chain of nz dependent steps.
+//
+// GPU layout: one thread-block cluster per (ray, frequency group).  The
+// cluster holds the intensity planes of that ray and group in shared memory,
+// split in horizontal bands of rows, one band per block, double buffered
+// (plane k-1 is read while plane k is written).  A block reads the upwind
+// intensities of rows owned by another block of its cluster through
+// distributed shared memory.  One cluster barrier per plane orders the steps;
+// no global synchronisation is needed, and the intensities never leave the
+// chip.  Opacity and source function of the two planes involved come from
+// global memory (L2-resident at these sizes); their upwind interpolation is
+// shared by all frequencies of the group, because for the two-level atom the
+// opacity factorises as chi0(node) phi(nu) and S does not depend on nu.
+//
+// Each block accumulates, per node, the frequency sum of its group for
+//   Jeff = sum w phi (I - w0 S)    and    U = sum w phi (1 - w0)
+// and stores it into a partial slot (ray, group); the rate kernel adds the
+// slots in a fixed order, so results are deterministic.
+#include <cooperative_groups.h>
+
+#include "mg3d_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace mg3d {
+
+// Linear short-characteristics weights for optical path x:
+//   I = I_up exp(-x) + w_up S_up + w_0 S_0,
+//   u = (1 - exp(-x))/x, w_0 = 1 - u, w_up = u - exp(-x).
+// Below a threshold the closed forms cancel, so Taylor series are used.
+template <typename T>
+struct ScWeights;
+
+template <>
+struct ScWeights<double> {
+    static __device__ __forceinline__ void eval(double x, double &ex, double &w0,
+                                                double &wup, double &u) {
+        ex = exp(-x);
+        if (x < 1e-3) {
+            w0 = x * (0.5 - x * (1.0 / 6.0 - x * (1.0 / 24.0 - x * (1.0 / 120.0 - x / 720.0))));
+            wup = x * (0.5 - x * (1.0 / 3.0 - x * (1.0 / 8.0 - x * (1.0 / 30.0 - x / 144.0))));
+            u = 1.0 - w0;
+        } else {
+            u = (1.0 - ex) / x;
+            w0 = 1.0 - u;
+            wup = u - ex;
+        }
+    }
+};
+
+template <>
+struct ScWeights<float> {
+    static __device__ __forceinline__ void eval(float x, float &ex, float &w0, float &wup,
+                                                float &u) {
+        ex = expf(-x);
+        if (x < 0.1f) {
+            w0 = x * (0.5f - x * (1.0f / 6.0f - x * (1.0f / 24.0f - x * (1.0f / 120.0f - x / 720.0f))));
+            wup = x * (0.5f - x * (1.0f / 3.0f - x * (1.0f / 8.0f - x * (1.0f / 30.0f - x / 144.0f))));
+            u = 1.0f - w0;
+        } else {
+            u = (1.0f - ex) / x;
+            w0 = 1.0f - u;
+            wup = u - ex;
+        }
+    }
+};
+
+template <typename T>
+__global__ void opacity_kernel(long nvox, double g_ratio, double kappa,
+                               const double *__restrict__ n, T *__restrict__ chi0,
+                               T *__restrict__ S) {
+    for (long v = blockIdx.x * (long)blockDim.x + threadIdx.x; v < nvox;
+         v += (long)gridDim.x * blockDim.x) {
+        double nl = n[v], nu = n[nvox + v];
+        double diff = nl * g_ratio - nu;
+        chi0[v] = (T)(kappa * diff);
+        S[v] = (T)(nu / diff);
+    }
+}
+
+template <typename T>
+__global__ void planck_bottom_kernel(long nplane, double theta, const double *__restrict__ Tgas,
+                                     T *__restrict__ bbot) {
+    for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < nplane;
+         p += (long)gridDim.x * blockDim.x)
+        bbot[p] = (T)(1.0 / expm1(theta / Tgas[p]));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs<T> a) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int g = blockIdx.y;
+    const int r = blockIdx.z;
+    const int nx = a.nx, ny = a.ny, nz = a.nz, rows = a.rows;
+    const int y0 = rank * rows;
+    const int myrows = max(0, min(rows, ny - y0));
+    const int band = myrows * nx;
+    const int f0 = g * a.ng;
+    const int nf = min(a.ng, a.nfreq - f0);
+    const bool up = (a.up_mask >> r) & 1u;
+    const long nplane = (long)nx * ny;
+    const long nvox = nplane * nz;
+    const long slot = (long)r * a.ngroups + g;
+    T *__restrict__ pj = a.pj + slot * nvox;
+    T *__restrict__ pu = a.pu + slot * nvox;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *buf = reinterpret_cast<T *>(smem_raw);
+    const long bufstride = (long)a.ng * rows * nx;
+
+    for (int t = 0; t < nz; ++t) {
+        const int k = up ? t : nz - 1 - t;
+        T *cur = buf + (t & 1) * bufstride;
+        if (t == 0) {
+            // entering boundary: I prescribed (bottom: Planck at the local
+            // temperature; top: zero), so w0 = 0 and 1 - w0 = 1
+            for (int q = threadIdx.x; q < band; q += blockDim.x) {
+                const int yl = q / nx, x = q - yl * nx;
+                const int y = y0 + yl;
+                const T Ib = up ? a.bbot[(long)y * nx + x] : T(0);
+                T cj = 0, cu = 0;
+                for (int f = 0; f < nf; ++f) {
+                    cur[((long)f * rows + yl) * nx + x] = Ib;
+                    const T w = a.wphi[f0 + f];
+                    cj += w * Ib;
+                    cu += w;
+                }
+                const long v = (long)k * nplane + (long)y * nx + x;
+                pj[v] = cj;
+                pu[v] = cu;
+            }
+        } else {
+            const T *prev = buf + ((t - 1) & 1) * bufstride;
+            const StepGeom o = a.geom[(long)r * nz + t];
+            const int kp = up ? k - 1 : k + 1;
+            const T tx = (T)o.tx, ty = (T)o.ty;
+            const T half_s = (T)(0.5 * o.s);
+            const T w00 = (T(1) - tx) * (T(1) - ty), w10 = tx * (T(1) - ty);
+            const T w01 = (T(1) - tx) * ty, w11 = tx * ty;
+            const T *__restrict__ chip = a.chi0 + (long)kp * nplane;
+            const T *__restrict__ Sp = a.S + (long)kp * nplane;
+            for (int q = threadIdx.x; q < band; q += blockDim.x) {
+                const int yl = q / nx, x = q - yl * nx;
+                const int y = y0 + yl;
+                int xa = x + o.ix0;
+                if (xa >= nx) xa -= nx;
+                const int xb = (xa + 1 == nx) ? 0 : xa + 1;
+                int ya = y + o.iy0;
+                if (ya >= ny) ya -= ny;
+                const int yb = (ya + 1 == ny) ? 0 : ya + 1;
+                const long ra = (long)ya * nx, rb = (long)yb * nx;
+                const T chi_up = w00 * chip[ra + xa] + w10 * chip[ra + xb] +
+                                 w01 * chip[rb + xa] + w11 * chip[rb + xb];
+                const T S_up = w00 * Sp[ra + xa] + w10 * Sp[ra + xb] + w01 * Sp[rb + xa] +
+                               w11 * Sp[rb + xb];
+                const long v = (long)k * nplane + (long)y * nx + x;
+                const T chi_loc = a.chi0[v];
+                const T S_loc = a.S[v];
+                const T dtau0 = (chi_up + chi_loc) * half_s;
+                // upwind rows of the intensity planes: local or in a peer block
+                const int ba = ya / rows, bb = yb / rows;
+                const T *Pa = (ba == rank) ? prev : cluster.map_shared_rank(prev, ba);
+                const T *Pb = (bb == rank) ? prev : cluster.map_shared_rank(prev, bb);
+                Pa += (long)(ya - ba * rows) * nx;
+                Pb += (long)(yb - bb * rows) * nx;
+                T cj = 0, cu = 0;
+                for (int f = 0; f < nf; ++f) {
+                    const long off = (long)f * rows * nx;
+                    const T I_up = w00 * Pa[off + xa] + w10 * Pa[off + xb] +
+                                   w01 * Pb[off + xa] + w11 * Pb[off + xb];
+                    T ex, w0, wup, u;
+                    ScWeights<T>::eval(dtau0 * a.phi[f0 + f], ex, w0, wup, u);
+                    const T part = I_up * ex + wup * S_up;
+                    cur[((long)f * rows + yl) * nx + x] = part + w0 * S_loc;
+                    const T w = a.wphi[f0 + f];
+                    cj += w * part;
+                    cu += w * u;
+                }
+                pj[v] = cj;
+                pu[v] = cu;
+            }
+        }
+        // plane t complete in every block before any block reads it, and no
+        // block overwrites plane t-1 (written again at t+1) while it is read
+        cluster.sync();
+    }
+}
+
+size_t sweep_smem_bytes(int prec, const SweepShape &s, int nx) {
+    size_t elem = prec == 0 ? sizeof(double) : sizeof(float);
+    return 2ull * s.ng * s.rows * nx * elem;
+}
+
+template <typename T>
+static cudaError_t launch_sweep_t(const SweepArgs<T> &a, const SweepShape &s,
+                                  cudaStream_t st) {
+    size_t smem = sweep_smem_bytes(sizeof(T) == 8 ? 0 : 1, s, a.nx);
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(s.bands, s.ngroups, kRays);
+    cfg.blockDim = dim3(s.threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = s.bands;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, sweep_kernel<T>, a);
+}
+
+cudaError_t launch_sweep_f64(const SweepArgs<double> &a, const SweepShape &s, cudaStream_t st) {
+    return launch_sweep_t<double>(a, s, st);
+}
+
+cudaError_t launch_sweep_f32(const SweepArgs<float> &a, const SweepShape &s, cudaStream_t st) {
+    return launch_sweep_t<float>(a, s, st);
+}
+
+static int grid_for(long n, int threads) {
+    long b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 152L * 32) b = 152L * 32;
+    return (int)b;
+}
+
+cudaError_t launch_opacity(int prec, long nvox, double g_ratio, double kappa,
+                           const double *n, void *chi0, void *S, cudaStream_t st) {
+    const int th = 256;
+    if (prec == 0)
+        opacity_kernel<double><<<grid_for(nvox, th), th, 0, st>>>(
+            nvox, g_ratio, kappa, n, (double *)chi0, (double *)S);
+    else
+        opacity_kernel<float><<<grid_for(nvox, th), th, 0, st>>>(
+            nvox, g_ratio, kappa, n, (float *)chi0, (float *)S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_planck_bottom(int prec, long nplane, double theta, const double *T,
+                                 void *bbot, cudaStream_t st) {
+    const int th = 256;
+    if (prec == 0)
+        planck_bottom_kernel<double><<<grid_for(nplane, th), th, 0, st>>>(nplane, theta, T,
+                                                                          (double *)bbot);
+    else
+        planck_bottom_kernel<float><<<grid_for(nplane, th), th, 0, st>>>(nplane, theta, T,
+                                                                         (float *)bbot);
+    return cudaGetLastError();
+}
+
+}  // namespace mg3d

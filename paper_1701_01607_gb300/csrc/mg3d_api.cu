@@ -1,0 +1,916 @@
+// C ABI and host driver: handle, grid hierarchy, MALI, FAS V-cycle and FMG.
+//
+// The driver follows Sec. 2.2-2.3 of Bjorgen & Leenaarts (2017):
+//   V-cycle(k):  nu1 MALI sweeps (nu0 on the finest grid in the first cycle)
+//                r^k = f^k - W^k_*(n^k)                     (Eq. 5, extra FS)
+//                n^{k-1} = R n^k,  n_before = n^{k-1}
+//                f^{k-1} = R r^k + W^{k-1}_*(R n^k)         (Eq. 9, extra FS)
+//                k-1 == 1 ? nu3 MALI sweeps : V-cycle(k-1)
+//                e = (n_after - n_before)/n_before           (Eq. 10)
+//                n^k <- n^k (1 + I e), <= 0 -> 0.1 n^k       (Eq. 11, Sec. 4.8)
+//                nu2 MALI sweeps
+//   FMG:         nu_fmg sweeps on grid 1, then for k = 2..l: n^k = I n^{k-1}
+//                and one V-cycle on grid k (k < l); V-cycles on grid l until
+//                the change over a cycle falls below the tolerance.
+// Every step runs in the library's kernels on the handle's stream; the host
+// only sequences launches and reads one scalar at convergence checks.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "mg3d.h"
+#include "mg3d_internal.h"
+
+using namespace mg3d;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+#define MG_CUDA(call)                                                                  \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return fail(MG3D_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define MG_TRY(call)             \
+    do {                                 \
+        int rc_ = (call);                \
+        if (rc_ != MG3D_OK) return rc_;  \
+    } while (0)
+
+struct Level {
+    int nx = 0, ny = 0, nz = 0;
+    long nplane = 0, nvox = 0;
+    double dx = 0, dy = 0;
+    std::vector<double> z;
+    double *T = nullptr, *n_tot = nullptr, *c_ul = nullptr, *c_lu = nullptr;
+    double *tz = nullptr;        // [nz] prolongation weight of the upper coarse plane
+    double *n = nullptr;         // [2][nvox]
+    double *f = nullptr;         // [2][nvox]
+    bool f_default = true;       // f = (n_tot, 0)
+    double *n_before = nullptr;  // [2][nvox]
+    double *r = nullptr;         // [2][nvox] residual / scratch
+    void *chi0 = nullptr, *S = nullptr, *bbot = nullptr;
+    StepGeom *geom = nullptr;    // [kRays][nz]
+    SweepShape shape{};
+};
+
+struct TimedLaunch {
+    cudaEvent_t a, b;
+    int level;
+};
+
+}  // namespace
+
+struct mg3d_handle {
+    int L = 0;
+    int prec = 0;
+    mg3d_atom atom{};
+    mg3d_params params{};
+    double mu[kRays][3];
+    double wray[kRays];
+    unsigned up_mask = 0;
+    Level lev[MG3D_MAX_GRIDS + 1];
+    std::vector<double> phi, wphi;
+    void *d_phi = nullptr, *d_wphi = nullptr;
+    void *pj = nullptr, *pu = nullptr;
+    size_t partial_elems = 0;
+    unsigned long long *scal = nullptr;  // [0] C bits, [1] negative after a sweep,
+                                         // [2] non-finite, [3] reset by the 10 % rule
+    double *scratch = nullptr;           // [4][finest nvox]
+    cudaStream_t own_stream = nullptr, stream = nullptr;
+    // counters
+    long long launches = 0, fs_launches = 0;
+    double fs_units = 0;
+    long long level_launches[MG3D_MAX_GRIDS + 1] = {};
+    double level_units[MG3D_MAX_GRIDS + 1] = {};
+    bool timing = false;
+    std::vector<TimedLaunch> timed;
+    std::vector<cudaEvent_t> event_pool;
+    // per-solve statistics
+    int sweeps[MG3D_MAX_GRIDS + 1] = {};
+    int fss[MG3D_MAX_GRIDS + 1] = {};
+    long long negatives = 0;
+};
+
+namespace {
+
+size_t elem_size(int prec) { return prec == MG3D_PREC_F64 ? sizeof(double) : sizeof(float); }
+
+// A4 set (Sec. 3): per octant the permutations of (a, a, b), weights 1/24;
+// rays 0-11 point up.
+void build_quadrature(mg3d_handle *h, double a) {
+    if (!(a > 0.0)) a = std::sqrt((4.0 - std::sqrt(6.4)) / 12.0);
+    const double b = std::sqrt(1.0 - 2.0 * a * a);
+    const double perm[3][3] = {{b, a, a}, {a, b, a}, {a, a, b}};
+    int r = 0;
+    for (int oz = 0; oz < 2; ++oz)
+        for (int oy = 0; oy < 2; ++oy)
+            for (int ox = 0; ox < 2; ++ox)
+                for (int p = 0; p < 3; ++p) {
+                    h->mu[r][0] = (ox ? -1.0 : 1.0) * perm[p][0];
+                    h->mu[r][1] = (oy ? -1.0 : 1.0) * perm[p][1];
+                    h->mu[r][2] = (oz ? -1.0 : 1.0) * perm[p][2];
+                    h->wray[r] = 1.0 / kRays;
+                    if (h->mu[r][2] > 0) h->up_mask |= 1u << r;
+                    ++r;
+                }
+}
+
+// Doppler profile phi(x) = exp(-x^2)/sqrt(pi) on equidistant x in
+// [-x_max, x_max], trapezoid weights, renormalised to sum(w phi) = 1.
+void build_frequencies(mg3d_handle *h) {
+    const int nf = h->atom.n_freq;
+    h->phi.assign(nf, 0.0);
+    h->wphi.assign(nf, 0.0);
+    double sum = 0.0;
+    for (int i = 0; i < nf; ++i) {
+        double x = nf == 1 ? 0.0 : -h->atom.x_max + 2.0 * h->atom.x_max * i / (nf - 1);
+        double w = nf == 1 ? 1.0 : 2.0 * h->atom.x_max / (nf - 1);
+        if (nf > 1 && (i == 0 || i == nf - 1)) w *= 0.5;
+        h->phi[i] = std::exp(-x * x) / std::sqrt(M_PI);
+        h->wphi[i] = w * h->phi[i];
+        sum += h->wphi[i];
+    }
+    for (int i = 0; i < nf; ++i) h->wphi[i] /= sum;
+}
+
+// Upwind crossing of every (ray, sweep step): for step t the plane is
+// k = t (up) or nz-1-t (down), the upwind plane kp = k-1 or k+1, the path
+// s = |z_k - z_kp| / |mu_z|, and the crossing lies at x - s mu_x/dx cells.
+void build_geometry(const mg3d_handle *h, const Level &L, std::vector<StepGeom> &g) {
+    g.assign((size_t)kRays * L.nz, StepGeom{0, 0, 0.0, 0.0, 0.0});
+    for (int r = 0; r < kRays; ++r) {
+        const bool up = h->mu[r][2] > 0;
+        for (int t = 1; t < L.nz; ++t) {
+            const int k = up ? t : L.nz - 1 - t;
+            const int kp = up ? k - 1 : k + 1;
+            const double s = std::fabs(L.z[k] - L.z[kp]) / std::fabs(h->mu[r][2]);
+            const double sx = -s * h->mu[r][0] / L.dx;
+            const double sy = -s * h->mu[r][1] / L.dy;
+            const double fx = std::floor(sx), fy = std::floor(sy);
+            long ix = (long)fx % L.nx, iy = (long)fy % L.ny;
+            if (ix < 0) ix += L.nx;
+            if (iy < 0) iy += L.ny;
+            StepGeom &e = g[(size_t)r * L.nz + t];
+            e.ix0 = (int)ix;
+            e.iy0 = (int)iy;
+            e.tx = sx - fx;
+            e.ty = sy - fy;
+            e.s = s;
+        }
+    }
+}
+
+// Sweep shape: spread the 24 x ceil(nfreq/ng) x bands blocks evenly over the
+// 152 SMs; cost = blocks per SM x nodes-frequencies per block; ties prefer
+// fewer partial slots, then fewer bands.
+SweepShape choose_shape(int prec, int nx, int ny, int nfreq) {
+    SweepShape best{};
+    double best_cost = 1e300;
+    for (int ng = 1; ng <= nfreq; ++ng) {
+        const int ngroups = (nfreq + ng - 1) / ng;
+        for (int bands = 1; bands <= kMaxBands && bands <= ny; ++bands) {
+            const int rows = (ny + bands - 1) / bands;
+            if ((long)(bands - 1) * rows >= ny) continue;
+            SweepShape s{ng, ngroups, bands, rows, 256};
+            if (sweep_smem_bytes(prec, s, nx) > kMaxSweepSmem) continue;
+            const long blocks = (long)kRays * ngroups * bands;
+            const double per_sm = (double)((blocks + 151) / 152);
+            const double cost = per_sm * ng * rows * nx + 1e-3 * ngroups + 1e-6 * bands;
+            if (cost < best_cost) {
+                best_cost = cost;
+                best = s;
+            }
+        }
+    }
+    const int band = best.rows * nx;
+    int th = ((band + 31) / 32) * 32;
+    if (th > 256) th = 256;
+    if (th < 32) th = 32;
+    best.threads = th;
+    return best;
+}
+
+int dev_alloc(void **p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(MG3D_E_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    return MG3D_OK;
+}
+
+template <typename P>
+int dalloc(P **p, size_t count) {
+    return dev_alloc((void **)p, count * sizeof(P));
+}
+
+void free_level(Level &L) {
+    void *ptrs[] = {L.T, L.n_tot, L.c_ul, L.c_lu, L.tz, L.n, L.f, L.n_before, L.r,
+                    L.chi0, L.S, L.bbot, L.geom};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    L = Level{};
+}
+
+int check_level(const mg3d_handle *h, int level) {
+    if (!h) return fail(MG3D_E_ARG, "null handle");
+    if (level < 1 || level > h->L) return fail(MG3D_E_ARG, "level out of range");
+    return MG3D_OK;
+}
+
+int launched(mg3d_handle *h, cudaError_t e, const char *what) {
+    ++h->launches;
+    if (e != cudaSuccess) return fail(MG3D_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return MG3D_OK;
+}
+
+cudaEvent_t pool_event(mg3d_handle *h) {
+    if (!h->event_pool.empty()) {
+        cudaEvent_t e = h->event_pool.back();
+        h->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// ------------------------------------------------------------- operations
+
+// Formal solution on level k with its populations: partial sums into pj/pu.
+int formal_solution(mg3d_handle *h, int k) {
+    Level &L = h->lev[k];
+    MG_TRY(launched(h, launch_opacity(h->prec, L.nvox, h->atom.g_ratio, h->atom.kappa, L.n,
+                                      L.chi0, L.S, h->stream),
+                    "opacity"));
+    TimedLaunch tl{nullptr, nullptr, k};
+    if (h->timing) {
+        tl.a = pool_event(h);
+        tl.b = pool_event(h);
+        MG_CUDA(cudaEventRecord(tl.a, h->stream));
+    }
+    cudaError_t e;
+    if (h->prec == MG3D_PREC_F64) {
+        SweepArgs<double> a{L.nx, L.ny, L.nz, h->atom.n_freq, L.shape.ng, L.shape.ngroups,
+                            L.shape.rows, h->up_mask, (const double *)L.chi0,
+                            (const double *)L.S, (const double *)L.bbot, L.geom,
+                            (const double *)h->d_phi, (const double *)h->d_wphi,
+                            (double *)h->pj, (double *)h->pu};
+        e = launch_sweep_f64(a, L.shape, h->stream);
+    } else {
+        SweepArgs<float> a{L.nx, L.ny, L.nz, h->atom.n_freq, L.shape.ng, L.shape.ngroups,
+                           L.shape.rows, h->up_mask, (const float *)L.chi0,
+                           (const float *)L.S, (const float *)L.bbot, L.geom,
+                           (const float *)h->d_phi, (const float *)h->d_wphi,
+                           (float *)h->pj, (float *)h->pu};
+        e = launch_sweep_f32(a, L.shape, h->stream);
+    }
+    MG_TRY(launched(h, e, "sweep"));
+    if (h->timing) {
+        MG_CUDA(cudaEventRecord(tl.b, h->stream));
+        h->timed.push_back(tl);
+    }
+    ++h->fs_launches;
+    h->fs_units += (double)L.nvox * kRays * h->atom.n_freq;
+    ++h->level_launches[k];
+    h->level_units[k] += (double)L.nvox * kRays * h->atom.n_freq;
+    ++h->fss[k];
+    return MG3D_OK;
+}
+
+RateArgs rate_args(mg3d_handle *h, int k, int mode) {
+    Level &L = h->lev[k];
+    RateArgs a{};
+    a.nvox = L.nvox;
+    a.nslots = kRays * L.shape.ngroups;
+    a.prec = h->prec;
+    a.pj = h->pj;
+    a.pu = h->pu;
+    a.zero_radiation = 0;
+    a.a_ul = h->atom.a_ul;
+    a.g_ratio = h->atom.g_ratio;
+    a.c_ul = L.c_ul;
+    a.c_lu = L.c_lu;
+    a.n_tot = L.n_tot;
+    a.f = L.f_default ? nullptr : L.f;
+    a.n = L.n;
+    a.out = nullptr;
+    a.mode = mode;
+    a.scal = h->scal;
+    return a;
+}
+
+int sweep(mg3d_handle *h, int k) {
+    MG_TRY(formal_solution(h, k));
+    RateArgs a = rate_args(h, k, kRateSolve);
+    MG_TRY(launched(h, launch_rates(a, h->stream), "rates"));
+    ++h->sweeps[k];
+    return MG3D_OK;
+}
+
+int reset_scalars(mg3d_handle *h) {
+    MG_CUDA(cudaMemsetAsync(h->scal, 0, 4 * sizeof(unsigned long long), h->stream));
+    return MG3D_OK;
+}
+
+int read_scalars(mg3d_handle *h, double *C, long long *neg, long long *bad) {
+    unsigned long long s[4];
+    MG_CUDA(cudaMemcpyAsync(s, h->scal, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
+    MG_CUDA(cudaStreamSynchronize(h->stream));
+    double c;
+    std::memcpy(&c, &s[0], sizeof(c));
+    if (C) *C = c;
+    if (neg) *neg = (long long)s[3];
+    if (bad) *bad = (long long)s[2];
+    return MG3D_OK;
+}
+
+int zero_radiation(mg3d_handle *h, int k) {
+    Level &L = h->lev[k];
+    L.f_default = true;
+    RateArgs a = rate_args(h, k, kRateSolve);
+    a.zero_radiation = 1;
+    a.scal = nullptr;
+    MG_TRY(launched(h, launch_rates(a, h->stream), "zero radiation"));
+    return MG3D_OK;
+}
+
+// out <- f - W(n) (mode residual) or out += W(n) (mode add), one extra FS.
+int apply_W(mg3d_handle *h, int k, int mode, double *out) {
+    MG_TRY(formal_solution(h, k));
+    RateArgs a = rate_args(h, k, mode);
+    a.out = out;
+    a.scal = nullptr;
+    MG_TRY(launched(h, launch_rates(a, h->stream), "residual"));
+    return MG3D_OK;
+}
+
+int vcycle(mg3d_handle *h, int k, bool first) {
+    Level &F = h->lev[k];
+    Level &C = h->lev[k - 1];
+    const int nu_pre = (first && k == h->L) ? h->params.nu0 : h->params.nu1;
+    for (int i = 0; i < nu_pre; ++i) MG_TRY(sweep(h, k));
+    // residual with an extra formal solution (Eq. 5)
+    MG_TRY(apply_W(h, k, kRateResidual, F.r));
+    // coarse-grid equation (Eq. 9)
+    MG_TRY(launched(h, launch_restrict(2, F.nx, F.ny, F.nz, F.n, C.n, h->stream), "restrict n"));
+    MG_CUDA(cudaMemcpyAsync(C.n_before, C.n, 2 * C.nvox * sizeof(double),
+                            cudaMemcpyDeviceToDevice, h->stream));
+    MG_TRY(launched(h, launch_restrict(2, F.nx, F.ny, F.nz, F.r, C.f, h->stream), "restrict r"));
+    C.f_default = false;
+    MG_TRY(apply_W(h, k - 1, kRateAddW, C.f));
+    if (k - 1 == 1) {
+        for (int i = 0; i < h->params.nu3; ++i) MG_TRY(sweep(h, 1));
+    } else {
+        MG_TRY(vcycle(h, k - 1, false));
+    }
+    // relative correction, interpolated (Eqs. 10-11), 10 % rule (Sec. 4.8)
+    MG_TRY(launched(h, launch_prolong_correct(C.nx, C.ny, C.nz, F.tz, C.n, C.n_before, F.n,
+                                              h->scal, h->stream),
+                    "prolong correction"));
+    for (int i = 0; i < h->params.nu2; ++i) MG_TRY(sweep(h, k));
+    return MG3D_OK;
+}
+
+// One V-cycle from the finest grid; C over the cycle into *C.
+int fas_cycle(mg3d_handle *h, bool first, double *C, long long *neg) {
+    Level &F = h->lev[h->L];
+    if (h->L < 2) return fail(MG3D_E_STATE, "a V-cycle needs n_grids >= 2");
+    MG_CUDA(cudaMemcpyAsync(h->scratch, F.n, 2 * F.nvox * sizeof(double),
+                            cudaMemcpyDeviceToDevice, h->stream));
+    F.f_default = true;
+    MG_TRY(reset_scalars(h));
+    MG_TRY(vcycle(h, h->L, first));
+    long long neg_in_cycle = 0;
+    MG_TRY(read_scalars(h, nullptr, &neg_in_cycle, nullptr));
+    MG_TRY(reset_scalars(h));
+    MG_TRY(launched(h, launch_max_rel_change(2 * F.nvox, F.n, h->scratch, h->scal, h->stream),
+                    "max rel change"));
+    long long bad = 0;
+    MG_TRY(read_scalars(h, C, nullptr, &bad));
+    if (neg) *neg = neg_in_cycle;
+    if (bad) return fail(MG3D_E_DIVERGED, "non-finite populations after a V-cycle");
+    return MG3D_OK;
+}
+
+void begin_stats(mg3d_handle *h) {
+    std::memset(h->sweeps, 0, sizeof(h->sweeps));
+    std::memset(h->fss, 0, sizeof(h->fss));
+    h->negatives = 0;
+}
+
+void end_stats(mg3d_handle *h, mg3d_stats *st, int iters, double C, double secs) {
+    if (!st) return;
+    std::memset(st, 0, sizeof(*st));
+    st->iterations = iters;
+    st->last_change = C;
+    st->negatives = h->negatives;
+    st->seconds = secs;
+    double eq = 0;
+    for (int k = 1; k <= h->L; ++k) {
+        st->sweeps[k] = h->sweeps[k];
+        st->formal_solutions[k] = h->fss[k];
+        eq += h->fss[k] * std::pow(0.125, h->L - k);
+    }
+    st->fine_fs_equivalents = eq;
+}
+
+int host_to_level(mg3d_handle *h, double *dst, const double *src, size_t count) {
+    MG_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    MG_CUDA(cudaStreamSynchronize(h->stream));
+    return MG3D_OK;
+}
+
+int level_to_host(mg3d_handle *h, double *dst, const double *src, size_t count) {
+    MG_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    MG_CUDA(cudaStreamSynchronize(h->stream));
+    return MG3D_OK;
+}
+
+int create_impl(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_quadrature *quad,
+                const mg3d_params *params, mg3d_handle *h) {
+    h->L = params->n_grids;
+    h->prec = params->fs_prec;
+    h->atom = *atom;
+    h->params = *params;
+    build_quadrature(h, quad ? quad->a : 0.0);
+    build_frequencies(h);
+    MG_CUDA(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
+    h->stream = h->own_stream;
+    const size_t es = elem_size(h->prec);
+
+    // grid hierarchy
+    for (int k = h->L; k >= 1; --k) {
+        Level &L = h->lev[k];
+        if (k == h->L) {
+            L.nx = atm->nx;
+            L.ny = atm->ny;
+            L.nz = atm->nz;
+            L.dx = atm->dx;
+            L.dy = atm->dy;
+            L.z.assign(atm->z, atm->z + atm->nz);
+        } else {
+            const Level &Fn = h->lev[k + 1];
+            L.nx = Fn.nx / 2;
+            L.ny = Fn.ny / 2;
+            L.nz = (Fn.nz + 1) / 2;
+            L.dx = 2 * Fn.dx;
+            L.dy = 2 * Fn.dy;
+            L.z.clear();
+            for (int i = 0; i < Fn.nz; i += 2) L.z.push_back(Fn.z[i]);
+        }
+        L.nplane = (long)L.nx * L.ny;
+        L.nvox = L.nplane * L.nz;
+        MG_TRY(dalloc(&L.T, L.nvox));
+        MG_TRY(dalloc(&L.n_tot, L.nvox));
+        MG_TRY(dalloc(&L.c_ul, L.nvox));
+        MG_TRY(dalloc(&L.c_lu, L.nvox));
+        MG_TRY(dalloc(&L.tz, L.nz));
+        MG_TRY(dalloc(&L.n, 2 * L.nvox));
+        MG_TRY(dalloc(&L.f, 2 * L.nvox));
+        MG_TRY(dalloc(&L.n_before, 2 * L.nvox));
+        MG_TRY(dalloc(&L.r, 2 * L.nvox));
+        MG_TRY(dev_alloc(&L.chi0, L.nvox * es));
+        MG_TRY(dev_alloc(&L.S, L.nvox * es));
+        MG_TRY(dev_alloc(&L.bbot, L.nplane * es));
+        MG_TRY(dalloc(&L.geom, (size_t)kRays * L.nz));
+        std::vector<double> tz(L.nz, 0.0);
+        for (int i = 1; i + 1 < L.nz; i += 2) tz[i] = (L.z[i] - L.z[i - 1]) / (L.z[i + 1] - L.z[i - 1]);
+        MG_CUDA(cudaMemcpy(L.tz, tz.data(), L.nz * sizeof(double), cudaMemcpyHostToDevice));
+        std::vector<StepGeom> g;
+        build_geometry(h, L, g);
+        MG_CUDA(cudaMemcpy(L.geom, g.data(), g.size() * sizeof(StepGeom), cudaMemcpyHostToDevice));
+        L.shape = choose_shape(h->prec, L.nx, L.ny, atom->n_freq);
+        if (L.shape.ng == 0) return fail(MG3D_E_ARG, "no sweep shape fits in shared memory");
+        h->partial_elems = std::max(h->partial_elems,
+                                    (size_t)kRays * L.shape.ngroups * (size_t)L.nvox);
+    }
+    // atmosphere on the finest grid, then full weighting downward (Sec. 4.7)
+    Level &F = h->lev[h->L];
+    MG_CUDA(cudaMemcpy(F.T, atm->T, F.nvox * sizeof(double), cudaMemcpyHostToDevice));
+    MG_CUDA(cudaMemcpy(F.n_tot, atm->n_tot, F.nvox * sizeof(double), cudaMemcpyHostToDevice));
+    MG_CUDA(cudaMemcpy(F.c_ul, atm->c_ul, F.nvox * sizeof(double), cudaMemcpyHostToDevice));
+    MG_TRY(dalloc(&h->scratch, 4 * F.nvox));
+    for (int k = h->L; k >= 2; --k) {
+        Level &Fk = h->lev[k];
+        Level &Ck = h->lev[k - 1];
+        // pack T, n_tot, c_ul into scratch, restrict, unpack
+        MG_CUDA(cudaMemcpyAsync(h->scratch, Fk.T, Fk.nvox * 8, cudaMemcpyDeviceToDevice, h->stream));
+        MG_CUDA(cudaMemcpyAsync(h->scratch + Fk.nvox, Fk.n_tot, Fk.nvox * 8,
+                                cudaMemcpyDeviceToDevice, h->stream));
+        MG_CUDA(cudaMemcpyAsync(h->scratch + 2 * Fk.nvox, Fk.c_ul, Fk.nvox * 8,
+                                cudaMemcpyDeviceToDevice, h->stream));
+        double *coarse = h->scratch + 3 * Fk.nvox;  // 3 coarse fields fit in nvox
+        MG_TRY(launched(h, launch_restrict(3, Fk.nx, Fk.ny, Fk.nz, h->scratch, coarse, h->stream),
+                        "restrict atmosphere"));
+        MG_CUDA(cudaMemcpyAsync(Ck.T, coarse, Ck.nvox * 8, cudaMemcpyDeviceToDevice, h->stream));
+        MG_CUDA(cudaMemcpyAsync(Ck.n_tot, coarse + Ck.nvox, Ck.nvox * 8,
+                                cudaMemcpyDeviceToDevice, h->stream));
+        MG_CUDA(cudaMemcpyAsync(Ck.c_ul, coarse + 2 * Ck.nvox, Ck.nvox * 8,
+                                cudaMemcpyDeviceToDevice, h->stream));
+    }
+    for (int k = 1; k <= h->L; ++k) {
+        Level &L = h->lev[k];
+        MG_TRY(launched(h, launch_collisions_up(L.nvox, atom->g_ratio, atom->theta, L.T, L.c_ul,
+                                                L.c_lu, h->stream),
+                        "collisions"));
+        MG_TRY(launched(h, launch_planck_bottom(h->prec, L.nplane, atom->theta, L.T, L.bbot,
+                                                h->stream),
+                        "planck"));
+    }
+    // frequency tables in the formal-solution precision
+    const int nf = atom->n_freq;
+    MG_TRY(dev_alloc(&h->d_phi, nf * es));
+    MG_TRY(dev_alloc(&h->d_wphi, nf * es));
+    std::vector<double> wphi_ray(nf);
+    for (int i = 0; i < nf; ++i) wphi_ray[i] = h->wphi[i] / kRays;
+    if (h->prec == MG3D_PREC_F64) {
+        MG_CUDA(cudaMemcpy(h->d_phi, h->phi.data(), nf * es, cudaMemcpyHostToDevice));
+        MG_CUDA(cudaMemcpy(h->d_wphi, wphi_ray.data(), nf * es, cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> a(nf), b(nf);
+        for (int i = 0; i < nf; ++i) {
+            a[i] = (float)h->phi[i];
+            b[i] = (float)wphi_ray[i];
+        }
+        MG_CUDA(cudaMemcpy(h->d_phi, a.data(), nf * es, cudaMemcpyHostToDevice));
+        MG_CUDA(cudaMemcpy(h->d_wphi, b.data(), nf * es, cudaMemcpyHostToDevice));
+    }
+    MG_TRY(dev_alloc(&h->pj, h->partial_elems * es));
+    MG_TRY(dev_alloc(&h->pu, h->partial_elems * es));
+    MG_TRY(dalloc(&h->scal, 4));
+    for (int k = 1; k <= h->L; ++k) MG_TRY(zero_radiation(h, k));
+    MG_CUDA(cudaStreamSynchronize(h->stream));
+    return MG3D_OK;
+}
+
+}  // namespace
+
+// ======================================================================= ABI
+
+extern "C" {
+
+const char *mg3d_last_error(void) { return g_last_error.c_str(); }
+
+int mg3d_create(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_quadrature *quad,
+                const mg3d_params *params, mg3d_handle **out) {
+    if (!out) return fail(MG3D_E_ARG, "null output pointer");
+    *out = nullptr;
+    if (!atm || !atom || !params) return fail(MG3D_E_ARG, "null argument");
+    if (!atm->z || !atm->T || !atm->n_tot || !atm->c_ul) return fail(MG3D_E_ARG, "null array");
+    if (params->n_grids < 1 || params->n_grids > MG3D_MAX_GRIDS)
+        return fail(MG3D_E_ARG, "n_grids out of range");
+    if (params->fs_prec != MG3D_PREC_F64 && params->fs_prec != MG3D_PREC_F32)
+        return fail(MG3D_E_ARG, "fs_prec must be MG3D_PREC_F64 or MG3D_PREC_F32");
+    if (params->nu_fmg < 0 || params->nu0 < 0 || params->nu1 < 0 || params->nu2 < 0 ||
+        params->nu3 < 0)
+        return fail(MG3D_E_ARG, "negative iteration count");
+    if (atom->n_freq < 1 || atom->n_freq > 4096 || !(atom->x_max >= 0.0) ||
+        !(atom->a_ul > 0.0) || !(atom->g_ratio > 0.0) || !(atom->theta > 0.0) ||
+        !(atom->kappa > 0.0))
+        return fail(MG3D_E_ARG, "bad atom parameters");
+    if (atm->nx < 1 || atm->ny < 1 || atm->nz < 2) return fail(MG3D_E_ARG, "grid too small");
+    if (!(atm->dx > 0.0) || !(atm->dy > 0.0)) return fail(MG3D_E_ARG, "dx, dy must be > 0");
+    for (int k = 1; k < atm->nz; ++k)
+        if (!(atm->z[k] > atm->z[k - 1])) return fail(MG3D_E_ARG, "z must increase");
+    const long step = 1L << (params->n_grids - 1);
+    if ((atm->nz - 1) % step != 0 || atm->nx % step != 0 || atm->ny % step != 0 ||
+        (atm->nz - 1) / step < 1)
+        return fail(MG3D_E_GRID, "grid does not coarsen n_grids - 1 times "
+                                 "(need nz = A 2^(l-1) + 1, nx, ny = B 2^(l-1))");
+    mg3d_handle *h = new (std::nothrow) mg3d_handle();
+    if (!h) return fail(MG3D_E_OOM, "host allocation failed");
+    int rc = create_impl(atm, atom, quad, params, h);
+    if (rc != MG3D_OK) {
+        std::string msg = g_last_error;
+        mg3d_destroy(h);
+        g_last_error = msg;
+        return rc;
+    }
+    *out = h;
+    g_last_error.clear();
+    return MG3D_OK;
+}
+
+int mg3d_destroy(mg3d_handle *h) {
+    if (!h) return MG3D_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (int k = 0; k <= MG3D_MAX_GRIDS; ++k) free_level(h->lev[k]);
+    void *ptrs[] = {h->d_phi, h->d_wphi, h->pj, h->pu, h->scal, h->scratch};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (auto &t : h->timed) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    for (auto e : h->event_pool) cudaEventDestroy(e);
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    delete h;
+    return MG3D_OK;
+}
+
+int mg3d_set_stream(mg3d_handle *h, void *cuda_stream) {
+    if (!h) return fail(MG3D_E_ARG, "null handle");
+    MG_CUDA(cudaStreamSynchronize(h->stream));
+    h->stream = cuda_stream ? (cudaStream_t)cuda_stream : h->own_stream;
+    return MG3D_OK;
+}
+
+int mg3d_level_shape(const mg3d_handle *h, int level, int *nx, int *ny, int *nz) {
+    MG_TRY(check_level(h, level));
+    const Level &L = h->lev[level];
+    if (nx) *nx = L.nx;
+    if (ny) *ny = L.ny;
+    if (nz) *nz = L.nz;
+    return MG3D_OK;
+}
+
+int mg3d_get_populations(mg3d_handle *h, int level, double *n_host) {
+    MG_TRY(check_level(h, level));
+    if (!n_host) return fail(MG3D_E_ARG, "null buffer");
+    Level &L = h->lev[level];
+    return level_to_host(h, n_host, L.n, 2 * L.nvox);
+}
+
+int mg3d_set_populations(mg3d_handle *h, int level, const double *n_host) {
+    MG_TRY(check_level(h, level));
+    if (!n_host) return fail(MG3D_E_ARG, "null buffer");
+    Level &L = h->lev[level];
+    return host_to_level(h, L.n, n_host, 2 * L.nvox);
+}
+
+int mg3d_init_zero_radiation(mg3d_handle *h, int level) {
+    MG_TRY(check_level(h, level));
+    MG_TRY(zero_radiation(h, level));
+    MG_CUDA(cudaStreamSynchronize(h->stream));
+    return MG3D_OK;
+}
+
+int mg3d_formal_solve(mg3d_handle *h, int level, double *jeff_host, double *u_host) {
+    MG_TRY(check_level(h, level));
+    Level &L = h->lev[level];
+    MG_TRY(formal_solution(h, level));
+    RateArgs a = rate_args(h, level, kRateReduce);
+    a.out = h->scratch;
+    a.scal = nullptr;
+    MG_TRY(launched(h, launch_rates(a, h->stream), "reduce"));
+    if (jeff_host) MG_CUDA(cudaMemcpyAsync(jeff_host, h->scratch, L.nvox * 8,
+                                           cudaMemcpyDeviceToHost, h->stream));
+    if (u_host) MG_CUDA(cudaMemcpyAsync(u_host, h->scratch + L.nvox, L.nvox * 8,
+                                        cudaMemcpyDeviceToHost, h->stream));
+    MG_CUDA(cudaStreamSynchronize(h->stream));
+    return MG3D_OK;
+}
+
+int mg3d_mali_sweep(mg3d_handle *h, int level, int n_sweeps, double *max_rel_change) {
+    MG_TRY(check_level(h, level));
+    if (n_sweeps < 0) return fail(MG3D_E_ARG, "negative sweep count");
+    double C = 0.0;
+    long long bad = 0;
+    for (int i = 0; i < n_sweeps; ++i) {
+        if (i == n_sweeps - 1) MG_TRY(reset_scalars(h));
+        MG_TRY(sweep(h, level));
+    }
+    if (n_sweeps > 0) MG_TRY(read_scalars(h, &C, nullptr, &bad));
+    if (max_rel_change) *max_rel_change = C;
+    if (bad) return fail(MG3D_E_DIVERGED, "non-finite populations");
+    return MG3D_OK;
+}
+
+int mg3d_residual(mg3d_handle *h, int level, double *r_host) {
+    MG_TRY(check_level(h, level));
+    if (!r_host) return fail(MG3D_E_ARG, "null buffer");
+    Level &L = h->lev[level];
+    MG_TRY(apply_W(h, level, kRateResidual, L.r));
+    return level_to_host(h, r_host, L.r, 2 * L.nvox);
+}
+
+int mg3d_fas_vcycle(mg3d_handle *h, int is_first, double *max_rel_change) {
+    if (!h) return fail(MG3D_E_ARG, "null handle");
+    long long neg = 0;
+    MG_TRY(fas_cycle(h, is_first != 0, max_rel_change, &neg));
+    h->negatives += neg;
+    return MG3D_OK;
+}
+
+int mg3d_mali_solve(mg3d_handle *h, double tol, int max_sweeps, mg3d_stats *stats) {
+    if (!h) return fail(MG3D_E_ARG, "null handle");
+    if (!(tol > 0.0) || max_sweeps < 1) return fail(MG3D_E_ARG, "bad tol or max_sweeps");
+    auto t0 = std::chrono::steady_clock::now();
+    begin_stats(h);
+    MG_TRY(zero_radiation(h, h->L));
+    double C = 1.0;
+    int it = 0;
+    while (it < max_sweeps) {
+        MG_TRY(reset_scalars(h));
+        MG_TRY(sweep(h, h->L));
+        ++it;
+        long long bad = 0;
+        MG_TRY(read_scalars(h, &C, nullptr, &bad));
+        if (bad) return fail(MG3D_E_DIVERGED, "non-finite populations");
+        if (C < tol) break;
+    }
+    double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    end_stats(h, stats, it, C, secs);
+    if (!(C < tol)) return fail(MG3D_E_MAXITER, "MALI did not reach tol");
+    return MG3D_OK;
+}
+
+int mg3d_fas_solve(mg3d_handle *h, double tol, int max_cycles, mg3d_stats *stats) {
+    if (!h) return fail(MG3D_E_ARG, "null handle");
+    if (!(tol > 0.0) || max_cycles < 1) return fail(MG3D_E_ARG, "bad tol or max_cycles");
+    auto t0 = std::chrono::steady_clock::now();
+    begin_stats(h);
+    MG_TRY(zero_radiation(h, h->L));
+    double C = 1.0;
+    int cyc = 0;
+    while (cyc < max_cycles) {
+        long long neg = 0;
+        MG_TRY(fas_cycle(h, cyc == 0, &C, &neg));
+        h->negatives += neg;
+        ++cyc;
+        if (C < tol) break;
+    }
+    double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    end_stats(h, stats, cyc, C, secs);
+    if (!(C < tol)) return fail(MG3D_E_MAXITER, "FAS did not reach tol");
+    return MG3D_OK;
+}
+
+int mg3d_fmg_solve(mg3d_handle *h, double tol, int max_cycles, mg3d_stats *stats) {
+    if (!h) return fail(MG3D_E_ARG, "null handle");
+    if (!(tol > 0.0) || max_cycles < 1) return fail(MG3D_E_ARG, "bad tol or max_cycles");
+    if (h->L < 2) return fail(MG3D_E_STATE, "FMG needs n_grids >= 2");
+    auto t0 = std::chrono::steady_clock::now();
+    begin_stats(h);
+    MG_TRY(zero_radiation(h, 1));
+    for (int i = 0; i < h->params.nu_fmg; ++i) MG_TRY(sweep(h, 1));
+    for (int k = 2; k <= h->L; ++k) {
+        Level &Fk = h->lev[k];
+        Level &Ck = h->lev[k - 1];
+        MG_TRY(launched(h, launch_prolong(2, Ck.nx, Ck.ny, Ck.nz, Fk.tz, Ck.n, Fk.n, h->stream),
+                        "prolong full approximation"));
+        Fk.f_default = true;
+        if (k < h->L) {
+            MG_TRY(reset_scalars(h));
+            MG_TRY(vcycle(h, k, false));
+            long long neg = 0;
+            MG_TRY(read_scalars(h, nullptr, &neg, nullptr));
+            h->negatives += neg;
+        }
+    }
+    double C = 1.0;
+    int cyc = 0;
+    while (cyc < max_cycles) {
+        long long neg = 0;
+        MG_TRY(fas_cycle(h, cyc == 0, &C, &neg));
+        h->negatives += neg;
+        ++cyc;
+        if (C < tol) break;
+    }
+    double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    end_stats(h, stats, cyc, C, secs);
+    if (!(C < tol)) return fail(MG3D_E_MAXITER, "FMG did not reach tol");
+    return MG3D_OK;
+}
+
+int mg3d_restrict(mg3d_handle *h, int level_fine, int ncomp, const double *fine_host,
+                  double *coarse_host) {
+    MG_TRY(check_level(h, level_fine));
+    if (level_fine < 2) return fail(MG3D_E_ARG, "level_fine must be >= 2");
+    if (ncomp < 1 || ncomp > 4 || !fine_host || !coarse_host) return fail(MG3D_E_ARG, "bad args");
+    Level &F = h->lev[level_fine];
+    Level &C = h->lev[level_fine - 1];
+    double *dfine = nullptr, *dcoarse = nullptr;
+    MG_TRY(dalloc(&dfine, (size_t)ncomp * F.nvox));
+    int rc = dalloc(&dcoarse, (size_t)ncomp * C.nvox);
+    if (rc == MG3D_OK) rc = host_to_level(h, dfine, fine_host, (size_t)ncomp * F.nvox);
+    if (rc == MG3D_OK)
+        rc = launched(h, launch_restrict(ncomp, F.nx, F.ny, F.nz, dfine, dcoarse, h->stream),
+                      "restrict");
+    if (rc == MG3D_OK) rc = level_to_host(h, coarse_host, dcoarse, (size_t)ncomp * C.nvox);
+    cudaFree(dfine);
+    if (dcoarse) cudaFree(dcoarse);
+    return rc;
+}
+
+int mg3d_prolong(mg3d_handle *h, int level_fine, int ncomp, const double *coarse_host,
+                 double *fine_host) {
+    MG_TRY(check_level(h, level_fine));
+    if (level_fine < 2) return fail(MG3D_E_ARG, "level_fine must be >= 2");
+    if (ncomp < 1 || ncomp > 4 || !fine_host || !coarse_host) return fail(MG3D_E_ARG, "bad args");
+    Level &F = h->lev[level_fine];
+    Level &C = h->lev[level_fine - 1];
+    double *dfine = nullptr, *dcoarse = nullptr;
+    MG_TRY(dalloc(&dcoarse, (size_t)ncomp * C.nvox));
+    int rc = dalloc(&dfine, (size_t)ncomp * F.nvox);
+    if (rc == MG3D_OK) rc = host_to_level(h, dcoarse, coarse_host, (size_t)ncomp * C.nvox);
+    if (rc == MG3D_OK)
+        rc = launched(h, launch_prolong(ncomp, C.nx, C.ny, C.nz, F.tz, dcoarse, dfine, h->stream),
+                      "prolong");
+    if (rc == MG3D_OK) rc = level_to_host(h, fine_host, dfine, (size_t)ncomp * F.nvox);
+    cudaFree(dcoarse);
+    if (dfine) cudaFree(dfine);
+    return rc;
+}
+
+int mg3d_set_fs_config(mg3d_handle *h, int level, int freq_per_block, int bands, int threads) {
+    MG_TRY(check_level(h, level));
+    Level &L = h->lev[level];
+    const int nf = h->atom.n_freq;
+    if (freq_per_block < 1 || freq_per_block > nf || bands < 1 || bands > kMaxBands ||
+        bands > L.ny || threads < 32 || threads > 256 || threads % 32)
+        return fail(MG3D_E_ARG, "bad sweep shape");
+    SweepShape s{freq_per_block, (nf + freq_per_block - 1) / freq_per_block, bands,
+                 (L.ny + bands - 1) / bands, threads};
+    if ((long)(bands - 1) * s.rows >= L.ny) return fail(MG3D_E_ARG, "empty band");
+    if (sweep_smem_bytes(h->prec, s, L.nx) > kMaxSweepSmem)
+        return fail(MG3D_E_ARG, "sweep shape exceeds shared memory");
+    MG_CUDA(cudaStreamSynchronize(h->stream));
+    const size_t need = (size_t)kRays * s.ngroups * (size_t)L.nvox;
+    if (need > h->partial_elems) {
+        // more partial slots than any level needed so far: grow the buffers
+        const size_t es = elem_size(h->prec);
+        cudaFree(h->pj);
+        cudaFree(h->pu);
+        h->pj = h->pu = nullptr;
+        h->partial_elems = 0;
+        MG_TRY(dev_alloc(&h->pj, need * es));
+        MG_TRY(dev_alloc(&h->pu, need * es));
+        h->partial_elems = need;
+    }
+    L.shape = s;
+    return MG3D_OK;
+}
+
+int mg3d_get_fs_config(const mg3d_handle *h, int level, int *freq_per_block, int *bands,
+                       int *threads) {
+    MG_TRY(check_level(h, level));
+    const Level &L = h->lev[level];
+    if (freq_per_block) *freq_per_block = L.shape.ng;
+    if (bands) *bands = L.shape.bands;
+    if (threads) *threads = L.shape.threads;
+    return MG3D_OK;
+}
+
+int mg3d_set_timing(mg3d_handle *h, int enable) {
+    if (!h) return fail(MG3D_E_ARG, "null handle");
+    h->timing = enable != 0;
+    return MG3D_OK;
+}
+
+int mg3d_get_counters(mg3d_handle *h, mg3d_counters *out) {
+    if (!h || !out) return fail(MG3D_E_ARG, "null argument");
+    MG_CUDA(cudaStreamSynchronize(h->stream));
+    std::memset(out, 0, sizeof(*out));
+    for (auto &t : h->timed) {
+        float ms = 0.f;
+        MG_CUDA(cudaEventElapsedTime(&ms, t.a, t.b));
+        out->fs_kernel_ms += ms;
+        ++out->fs_timed_launches;
+        out->level_fs_kernel_ms[t.level] += ms;
+        ++out->level_fs_timed_launches[t.level];
+    }
+    out->kernel_launches = h->launches;
+    out->fs_launches = h->fs_launches;
+    out->fs_units = h->fs_units;
+    for (int k = 0; k <= MG3D_MAX_GRIDS; ++k) {
+        out->level_fs_launches[k] = h->level_launches[k];
+        out->level_fs_units[k] = h->level_units[k];
+    }
+    return MG3D_OK;
+}
+
+int mg3d_reset_counters(mg3d_handle *h) {
+    if (!h) return fail(MG3D_E_ARG, "null handle");
+    MG_CUDA(cudaStreamSynchronize(h->stream));
+    for (auto &t : h->timed) {
+        h->event_pool.push_back(t.a);
+        h->event_pool.push_back(t.b);
+    }
+    h->timed.clear();
+    h->launches = 0;
+    h->fs_launches = 0;
+    h->fs_units = 0;
+    std::memset(h->level_launches, 0, sizeof(h->level_launches));
+    std::memset(h->level_units, 0, sizeof(h->level_units));
+    return MG3D_OK;
+}
+
+}  // extern "C"

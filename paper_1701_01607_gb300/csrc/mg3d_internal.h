@@ -1,0 +1,96 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+namespace mg3d {
+
+constexpr int kRays = 24;          // A4 quadrature, 12 up and 12 down
+constexpr int kMaxBands = 8;       // thread blocks per cluster sharing a plane
+constexpr size_t kMaxSweepSmem = 200 * 1024;
+
+// Upwind geometry of one sweep step of one ray.  The short characteristic of
+// every node on the plane crosses the upwind plane at the same horizontal
+// offset, so the bilinear weights and the integer corner offsets are
+// constants of (ray, step).  ix0/iy0 are already reduced modulo nx/ny.
+struct StepGeom {
+    int ix0, iy0;
+    double tx, ty;   // fractional position inside the upwind cell, [0, 1)
+    double s;        // path length of the short characteristic
+};
+
+// Launch shape of the sweep on one level.
+struct SweepShape {
+    int ng;       // frequencies per thread block
+    int ngroups;  // ceil(nfreq / ng)
+    int bands;    // thread blocks per cluster; each holds `rows` rows
+    int rows;     // ceil(ny / bands)
+    int threads;  // threads per block
+};
+
+// Arguments of the sweep kernel.  T is the formal-solution precision.
+template <typename T>
+struct SweepArgs {
+    int nx, ny, nz, nfreq;
+    int ng, ngroups, rows;
+    unsigned up_mask;        // bit r set when ray r points up
+    const T *chi0;           // [nvox] line opacity at unit profile
+    const T *S;              // [nvox] line source function
+    const T *bbot;           // [nx*ny] intensity entering at the bottom
+    const StepGeom *geom;    // [kRays][nz], entry t = 1..nz-1 used
+    const T *phi;            // [nfreq] profile
+    const T *wphi;           // [nfreq] ray weight x frequency weight x profile
+    T *pj, *pu;              // [kRays*ngroups][nvox] partial Jeff and U
+};
+
+size_t sweep_smem_bytes(int prec, const SweepShape &s, int nx);
+
+// Kernel launchers; each returns the launch error.
+cudaError_t launch_opacity(int prec, long nvox, double g_ratio, double kappa,
+                           const double *n, void *chi0, void *S, cudaStream_t st);
+cudaError_t launch_planck_bottom(int prec, long nplane, double theta, const double *T,
+                                 void *bbot, cudaStream_t st);
+cudaError_t launch_sweep_f64(const SweepArgs<double> &a, const SweepShape &s, cudaStream_t st);
+cudaError_t launch_sweep_f32(const SweepArgs<float> &a, const SweepShape &s, cudaStream_t st);
+
+// Rate kernel modes.
+enum RateMode {
+    kRateSolve = 0,      // n <- solution of Gamma(Jeff, U) n = f; C, counts
+    kRateResidual = 1,   // out <- f - Gamma(Jeff, U) n
+    kRateAddW = 2,       // out <- out + Gamma(Jeff, U) n
+    kRateReduce = 3,     // out[0] <- Jeff, out[1] <- U
+};
+
+struct RateArgs {
+    long nvox;
+    int nslots;
+    int prec;                  // type of pj/pu
+    const void *pj, *pu;       // [nslots][nvox]
+    int zero_radiation;        // Jeff = 0, U = 1 instead of the partials
+    double a_ul, g_ratio;
+    const double *c_ul, *c_lu, *n_tot;
+    const double *f;           // [2][nvox] or nullptr for (n_tot, 0)
+    double *n;                 // [2][nvox]
+    double *out;               // [2][nvox]
+    int mode;
+    unsigned long long *scal;  // [0] max rel change bits, [1] negatives, [2] non-finite,
+                               // [3] populations reset by the 10 % rule
+};
+cudaError_t launch_rates(const RateArgs &a, cudaStream_t st);
+
+cudaError_t launch_collisions_up(long nvox, double g_ratio, double theta, const double *T,
+                                 const double *c_ul, double *c_lu, cudaStream_t st);
+cudaError_t launch_restrict(int ncomp, int nxf, int nyf, int nzf, const double *fine,
+                            double *coarse, cudaStream_t st);
+cudaError_t launch_prolong(int ncomp, int nxc, int nyc, int nzc, const double *tz,
+                           const double *coarse, double *fine, cudaStream_t st);
+cudaError_t launch_prolong_correct(int nxc, int nyc, int nzc, const double *tz,
+                                   const double *n_after, const double *n_before,
+                                   double *n_fine, unsigned long long *scal,
+                                   cudaStream_t st);
+cudaError_t launch_max_rel_change(long len, const double *n_new, const double *n_old,
+                                  unsigned long long *scal, cudaStream_t st);
+
+}  // namespace mg3d

@@ -1,0 +1,307 @@
+"""Thin ctypes binding of the C ABI in include/mg3d.h (same names).
+
+Only argument marshalling lives here: every step of the solver runs in the
+CUDA library.  Loading fails loudly if the library has not been built; there
+is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MG3D_OK = 0
+MG3D_E_ARG = -1
+MG3D_E_GRID = -2
+MG3D_E_CUDA = -3
+MG3D_E_OOM = -4
+MG3D_E_DIVERGED = -5
+MG3D_E_MAXITER = -6
+MG3D_E_STATE = -8
+MG3D_MAX_GRIDS = 8
+MG3D_PREC_F64 = 0
+MG3D_PREC_F32 = 1
+
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+class mg3d_atmosphere(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+                ("z", _D), ("T", _D), ("n_tot", _D), ("c_ul", _D)]
+
+
+class mg3d_atom(ctypes.Structure):
+    _fields_ = [("a_ul", ctypes.c_double), ("g_ratio", ctypes.c_double),
+                ("theta", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("n_freq", ctypes.c_int), ("x_max", ctypes.c_double)]
+
+
+class mg3d_quadrature(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_double)]
+
+
+class mg3d_params(ctypes.Structure):
+    _fields_ = [("n_grids", ctypes.c_int), ("nu_fmg", ctypes.c_int), ("nu0", ctypes.c_int),
+                ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("nu3", ctypes.c_int),
+                ("fs_prec", ctypes.c_int)]
+
+
+class mg3d_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int),
+                ("sweeps", ctypes.c_int * (MG3D_MAX_GRIDS + 1)),
+                ("formal_solutions", ctypes.c_int * (MG3D_MAX_GRIDS + 1)),
+                ("last_change", ctypes.c_double), ("negatives", ctypes.c_longlong),
+                ("seconds", ctypes.c_double), ("fine_fs_equivalents", ctypes.c_double)]
+
+
+class mg3d_counters(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_longlong), ("fs_launches", ctypes.c_longlong),
+                ("fs_units", ctypes.c_double), ("fs_kernel_ms", ctypes.c_double),
+                ("fs_timed_launches", ctypes.c_longlong),
+                ("level_fs_launches", ctypes.c_longlong * (MG3D_MAX_GRIDS + 1)),
+                ("level_fs_units", ctypes.c_double * (MG3D_MAX_GRIDS + 1)),
+                ("level_fs_kernel_ms", ctypes.c_double * (MG3D_MAX_GRIDS + 1)),
+                ("level_fs_timed_launches", ctypes.c_longlong * (MG3D_MAX_GRIDS + 1))]
+
+
+_H = ctypes.c_void_p
+_I = ctypes.c_int
+_SIGNATURES = {
+    "mg3d_last_error": (ctypes.c_char_p, []),
+    "mg3d_create": (_I, [ctypes.POINTER(mg3d_atmosphere), ctypes.POINTER(mg3d_atom),
+                         ctypes.POINTER(mg3d_quadrature), ctypes.POINTER(mg3d_params),
+                         ctypes.POINTER(_H)]),
+    "mg3d_destroy": (_I, [_H]),
+    "mg3d_set_stream": (_I, [_H, ctypes.c_void_p]),
+    "mg3d_level_shape": (_I, [_H, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                              ctypes.POINTER(_I)]),
+    "mg3d_get_populations": (_I, [_H, _I, _D]),
+    "mg3d_set_populations": (_I, [_H, _I, _D]),
+    "mg3d_init_zero_radiation": (_I, [_H, _I]),
+    "mg3d_formal_solve": (_I, [_H, _I, _D, _D]),
+    "mg3d_mali_sweep": (_I, [_H, _I, _I, _D]),
+    "mg3d_residual": (_I, [_H, _I, _D]),
+    "mg3d_fas_vcycle": (_I, [_H, _I, _D]),
+    "mg3d_mali_solve": (_I, [_H, ctypes.c_double, _I, ctypes.POINTER(mg3d_stats)]),
+    "mg3d_fas_solve": (_I, [_H, ctypes.c_double, _I, ctypes.POINTER(mg3d_stats)]),
+    "mg3d_fmg_solve": (_I, [_H, ctypes.c_double, _I, ctypes.POINTER(mg3d_stats)]),
+    "mg3d_restrict": (_I, [_H, _I, _I, _D, _D]),
+    "mg3d_prolong": (_I, [_H, _I, _I, _D, _D]),
+    "mg3d_set_fs_config": (_I, [_H, _I, _I, _I, _I]),
+    "mg3d_get_fs_config": (_I, [_H, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                ctypes.POINTER(_I)]),
+    "mg3d_set_timing": (_I, [_H, _I]),
+    "mg3d_get_counters": (_I, [_H, ctypes.POINTER(mg3d_counters)]),
+    "mg3d_reset_counters": (_I, [_H]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libmg3d.so; raise if it is missing (no fallback of any kind)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class MG3DError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"mg3d error {code}: {msg}")
+        self.code = code
+
+
+def _check(rc):
+    if rc != MG3D_OK:
+        raise MG3DError(rc, load().mg3d_last_error().decode())
+    return rc
+
+
+def _dptr(a):
+    if a is None:
+        return None
+    if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("expected a C-contiguous float64 array")
+    return a.ctypes.data_as(_D)
+
+
+# ---------------------------------------------------------------- same names
+
+def mg3d_last_error() -> str:
+    return load().mg3d_last_error().decode()
+
+
+def mg3d_create(atm, atom, quad_a: float = 0.0, n_grids: int = 1, nu_fmg: int = 16,
+                nu0: int = 0, nu1: int = 2, nu2: int = 2, nu3: int = 32,
+                fs_prec: int = MG3D_PREC_F64):
+    """mg3d_create from a synth.Atmosphere and TwoLevelAtom; returns the handle."""
+    lib = load()
+    z = np.ascontiguousarray(atm.z, dtype=np.float64)
+    T = np.ascontiguousarray(atm.T, dtype=np.float64)
+    n_tot = np.ascontiguousarray(atm.n_tot, dtype=np.float64)
+    c_ul = np.ascontiguousarray(atm.c_ul, dtype=np.float64)
+    a = mg3d_atmosphere(atm.nx, atm.ny, atm.nz, atm.dx, atm.dy, _dptr(z), _dptr(T),
+                        _dptr(n_tot), _dptr(c_ul))
+    at = mg3d_atom(atom.a_ul, atom.g_ratio, atom.theta, atom.kappa, atom.n_freq, atom.x_max)
+    q = mg3d_quadrature(quad_a)
+    p = mg3d_params(n_grids, nu_fmg, nu0, nu1, nu2, nu3, fs_prec)
+    h = _H()
+    _check(lib.mg3d_create(ctypes.byref(a), ctypes.byref(at), ctypes.byref(q),
+                           ctypes.byref(p), ctypes.byref(h)))
+    return h
+
+
+def mg3d_destroy(h):
+    return _check(load().mg3d_destroy(h))
+
+
+def mg3d_set_stream(h, stream_ptr: int | None):
+    return _check(load().mg3d_set_stream(h, ctypes.c_void_p(stream_ptr or 0)))
+
+
+def mg3d_level_shape(h, level: int):
+    nx, ny, nz = _I(), _I(), _I()
+    _check(load().mg3d_level_shape(h, level, ctypes.byref(nx), ctypes.byref(ny),
+                                   ctypes.byref(nz)))
+    return nx.value, ny.value, nz.value
+
+
+def mg3d_get_populations(h, level: int, out=None):
+    nx, ny, nz = mg3d_level_shape(h, level)
+    if out is None:
+        out = np.empty((2, nz, ny, nx))
+    _check(load().mg3d_get_populations(h, level, _dptr(out)))
+    return out
+
+
+def mg3d_set_populations(h, level: int, n):
+    n = np.ascontiguousarray(n, dtype=np.float64)
+    return _check(load().mg3d_set_populations(h, level, _dptr(n)))
+
+
+def mg3d_init_zero_radiation(h, level: int):
+    return _check(load().mg3d_init_zero_radiation(h, level))
+
+
+def mg3d_formal_solve(h, level: int, want: bool = True):
+    nx, ny, nz = mg3d_level_shape(h, level)
+    jeff = np.empty((nz, ny, nx)) if want else None
+    u = np.empty((nz, ny, nx)) if want else None
+    _check(load().mg3d_formal_solve(h, level, _dptr(jeff), _dptr(u)))
+    return jeff, u
+
+
+def mg3d_mali_sweep(h, level: int, n_sweeps: int = 1) -> float:
+    c = ctypes.c_double()
+    _check(load().mg3d_mali_sweep(h, level, n_sweeps, ctypes.byref(c)))
+    return c.value
+
+
+def mg3d_residual(h, level: int):
+    nx, ny, nz = mg3d_level_shape(h, level)
+    r = np.empty((2, nz, ny, nx))
+    _check(load().mg3d_residual(h, level, _dptr(r)))
+    return r
+
+
+def mg3d_fas_vcycle(h, is_first: bool = False) -> float:
+    c = ctypes.c_double()
+    _check(load().mg3d_fas_vcycle(h, int(bool(is_first)), ctypes.byref(c)))
+    return c.value
+
+
+def _stats_dict(st: mg3d_stats, n_grids: int):
+    return {"iterations": st.iterations,
+            "sweeps": {k: st.sweeps[k] for k in range(1, n_grids + 1)},
+            "formal_solutions": {k: st.formal_solutions[k] for k in range(1, n_grids + 1)},
+            "last_change": st.last_change, "negatives": st.negatives,
+            "seconds": st.seconds, "fine_fs_equivalents": st.fine_fs_equivalents}
+
+
+def _solve(fn, h, tol, cap, n_grids):
+    st = mg3d_stats()
+    _check(fn(h, tol, cap, ctypes.byref(st)))
+    return _stats_dict(st, n_grids)
+
+
+def mg3d_mali_solve(h, tol: float, max_sweeps: int = 100000, n_grids: int = 1):
+    return _solve(load().mg3d_mali_solve, h, tol, max_sweeps, n_grids)
+
+
+def mg3d_fas_solve(h, tol: float, max_cycles: int = 1000, n_grids: int = 1):
+    return _solve(load().mg3d_fas_solve, h, tol, max_cycles, n_grids)
+
+
+def mg3d_fmg_solve(h, tol: float, max_cycles: int = 1000, n_grids: int = 1):
+    return _solve(load().mg3d_fmg_solve, h, tol, max_cycles, n_grids)
+
+
+def mg3d_restrict(h, level_fine: int, fine):
+    fine = np.ascontiguousarray(fine, dtype=np.float64)
+    ncomp = fine.shape[0] if fine.ndim == 4 else 1
+    nx, ny, nz = mg3d_level_shape(h, level_fine - 1)
+    out = np.empty((ncomp, nz, ny, nx))
+    _check(load().mg3d_restrict(h, level_fine, ncomp, _dptr(fine), _dptr(out)))
+    return out if fine.ndim == 4 else out[0]
+
+
+def mg3d_prolong(h, level_fine: int, coarse):
+    coarse = np.ascontiguousarray(coarse, dtype=np.float64)
+    ncomp = coarse.shape[0] if coarse.ndim == 4 else 1
+    nx, ny, nz = mg3d_level_shape(h, level_fine)
+    out = np.empty((ncomp, nz, ny, nx))
+    _check(load().mg3d_prolong(h, level_fine, ncomp, _dptr(coarse), _dptr(out)))
+    return out if coarse.ndim == 4 else out[0]
+
+
+def mg3d_set_fs_config(h, level: int, freq_per_block: int, bands: int, threads: int = 256):
+    return _check(load().mg3d_set_fs_config(h, level, freq_per_block, bands, threads))
+
+
+def mg3d_get_fs_config(h, level: int):
+    a, b, c = _I(), _I(), _I()
+    _check(load().mg3d_get_fs_config(h, level, ctypes.byref(a), ctypes.byref(b),
+                                     ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def mg3d_set_timing(h, enable: bool):
+    return _check(load().mg3d_set_timing(h, int(bool(enable))))
+
+
+def mg3d_get_counters(h):
+    c = mg3d_counters()
+    _check(load().mg3d_get_counters(h, ctypes.byref(c)))
+    lv = range(MG3D_MAX_GRIDS + 1)
+    return {"kernel_launches": c.kernel_launches, "fs_launches": c.fs_launches,
+            "fs_units": c.fs_units, "fs_kernel_ms": c.fs_kernel_ms,
+            "fs_timed_launches": c.fs_timed_launches,
+            "level_fs_launches": [c.level_fs_launches[k] for k in lv],
+            "level_fs_units": [c.level_fs_units[k] for k in lv],
+            "level_fs_kernel_ms": [c.level_fs_kernel_ms[k] for k in lv],
+            "level_fs_timed_launches": [c.level_fs_timed_launches[k] for k in lv]}
+
+
+def mg3d_reset_counters(h):
+    return _check(load().mg3d_reset_counters(h))
