@@ -34,21 +34,25 @@ namespace mg3d {
 // Linear short-characteristics weights for optical path x:
 //   I = I_up exp(-x) + w_up S_up + w_0 S_0,
 //   u = (1 - exp(-x))/x, w_0 = 1 - u, w_up = u - exp(-x).
-// Below a threshold the closed forms cancel, so Taylor series are used.
+// Below a threshold the closed forms cancel, so Taylor series are used.  The
+// FP32 variant uses the hardware exp2 approximation (__expf): its error grows
+// with x, but exp(-x) then multiplies a term that is already negligible.
 template <typename T>
 struct ScWeights;
 
 template <>
 struct ScWeights<double> {
-    static __device__ __forceinline__ void eval(double x, double &ex, double &w0,
-                                                double &wup, double &u) {
+    // inv_x = 1/x, formed by the caller as (1/dtau0)(1/phi): one division per
+    // node and ray instead of one per frequency.
+    static __device__ __forceinline__ void eval(double x, double inv_x, double &ex,
+                                                double &w0, double &wup, double &u) {
         ex = exp(-x);
         if (x < 1e-3) {
             w0 = x * (0.5 - x * (1.0 / 6.0 - x * (1.0 / 24.0 - x * (1.0 / 120.0 - x / 720.0))));
             wup = x * (0.5 - x * (1.0 / 3.0 - x * (1.0 / 8.0 - x * (1.0 / 30.0 - x / 144.0))));
             u = 1.0 - w0;
         } else {
-            u = (1.0 - ex) / x;
+            u = (1.0 - ex) * inv_x;
             w0 = 1.0 - u;
             wup = u - ex;
         }
@@ -57,15 +61,15 @@ struct ScWeights<double> {
 
 template <>
 struct ScWeights<float> {
-    static __device__ __forceinline__ void eval(float x, float &ex, float &w0, float &wup,
-                                                float &u) {
-        ex = expf(-x);
+    static __device__ __forceinline__ void eval(float x, float inv_x, float &ex, float &w0,
+                                                float &wup, float &u) {
+        ex = __expf(-x);
         if (x < 0.1f) {
             w0 = x * (0.5f - x * (1.0f / 6.0f - x * (1.0f / 24.0f - x * (1.0f / 120.0f - x / 720.0f))));
             wup = x * (0.5f - x * (1.0f / 3.0f - x * (1.0f / 8.0f - x * (1.0f / 30.0f - x / 144.0f))));
             u = 1.0f - w0;
         } else {
-            u = (1.0f - ex) / x;
+            u = (1.0f - ex) * inv_x;
             w0 = 1.0f - u;
             wup = u - ex;
         }
@@ -94,7 +98,7 @@ __global__ void planck_bottom_kernel(long nplane, double theta, const double *__
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs<T> a) {
+__global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs<T> a) {
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int g = blockIdx.y;
@@ -165,6 +169,9 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs<T> a) {
                 const T chi_loc = a.chi0[v];
                 const T S_loc = a.S[v];
                 const T dtau0 = (chi_up + chi_loc) * half_s;
+                // 1/dtau0 is only used where dtau0 phi >= the series threshold,
+                // so dtau0 > 0 there
+                const T inv_dtau0 = T(1) / dtau0;
                 // upwind rows of the intensity planes: local or in a peer block
                 const int ba = ya / rows, bb = yb / rows;
                 const T *Pa = (ba == rank) ? prev : cluster.map_shared_rank(prev, ba);
@@ -177,7 +184,8 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs<T> a) {
                     const T I_up = w00 * Pa[off + xa] + w10 * Pa[off + xb] +
                                    w01 * Pb[off + xa] + w11 * Pb[off + xb];
                     T ex, w0, wup, u;
-                    ScWeights<T>::eval(dtau0 * a.phi[f0 + f], ex, w0, wup, u);
+                    ScWeights<T>::eval(dtau0 * a.phi[f0 + f], inv_dtau0 * a.inv_phi[f0 + f],
+                                       ex, w0, wup, u);
                     const T part = I_up * ex + wup * S_up;
                     cur[((long)f * rows + yl) * nx + x] = part + w0 * S_loc;
                     const T w = a.wphi[f0 + f];

@@ -86,7 +86,7 @@ struct mg3d_handle {
     unsigned up_mask = 0;
     Level lev[MG3D_MAX_GRIDS + 1];
     std::vector<double> phi, wphi;
-    void *d_phi = nullptr, *d_wphi = nullptr;
+    void *d_phi = nullptr, *d_wphi = nullptr, *d_inv_phi = nullptr;
     void *pj = nullptr, *pu = nullptr;
     size_t partial_elems = 0;
     unsigned long long *scal = nullptr;  // [0] C bits, [1] negative after a sweep,
@@ -176,12 +176,24 @@ void build_geometry(const mg3d_handle *h, const Level &L, std::vector<StepGeom> 
     }
 }
 
+// Threads per block for a band of `band` nodes: as few passes of at most
+// kMaxSweepThreads threads as possible, split evenly, rounded to warps.
+int threads_for_band(int band) {
+    const int passes = (band + kMaxSweepThreads - 1) / kMaxSweepThreads;
+    int th = (band + passes - 1) / passes;
+    th = ((th + 31) / 32) * 32;
+    return th < 32 ? 32 : (th > kMaxSweepThreads ? kMaxSweepThreads : th);
+}
+
 // Sweep shape: spread the 24 x ceil(nfreq/ng) x bands blocks evenly over the
-// 152 SMs; cost = blocks per SM x nodes-frequencies per block; ties prefer
-// fewer partial slots, then fewer bands.
+// 152 SMs.  Cost = blocks per SM x nodes per block x (ng + c_node), where
+// c_node is the per-(node, ray) work shared by a group's frequencies (upwind
+// chi/S interpolation, 1/dtau) relative to one frequency; ties prefer fewer
+// partial slots, then fewer bands.
 SweepShape choose_shape(int prec, int nx, int ny, int nfreq) {
     SweepShape best{};
     double best_cost = 1e300;
+    const double c_node = 0.3;
     for (int ng = 1; ng <= nfreq; ++ng) {
         const int ngroups = (nfreq + ng - 1) / ng;
         for (int bands = 1; bands <= kMaxBands && bands <= ny; ++bands) {
@@ -191,18 +203,14 @@ SweepShape choose_shape(int prec, int nx, int ny, int nfreq) {
             if (sweep_smem_bytes(prec, s, nx) > kMaxSweepSmem) continue;
             const long blocks = (long)kRays * ngroups * bands;
             const double per_sm = (double)((blocks + 151) / 152);
-            const double cost = per_sm * ng * rows * nx + 1e-3 * ngroups + 1e-6 * bands;
+            const double cost = per_sm * rows * nx * (ng + c_node) + 1e-3 * ngroups + 1e-6 * bands;
             if (cost < best_cost) {
                 best_cost = cost;
                 best = s;
             }
         }
     }
-    const int band = best.rows * nx;
-    int th = ((band + 31) / 32) * 32;
-    if (th > 256) th = 256;
-    if (th < 32) th = 32;
-    best.threads = th;
+    best.threads = threads_for_band(best.rows * nx);
     return best;
 }
 
@@ -270,15 +278,15 @@ int formal_solution(mg3d_handle *h, int k) {
         SweepArgs<double> a{L.nx, L.ny, L.nz, h->atom.n_freq, L.shape.ng, L.shape.ngroups,
                             L.shape.rows, h->up_mask, (const double *)L.chi0,
                             (const double *)L.S, (const double *)L.bbot, L.geom,
-                            (const double *)h->d_phi, (const double *)h->d_wphi,
-                            (double *)h->pj, (double *)h->pu};
+                            (const double *)h->d_phi, (const double *)h->d_inv_phi,
+                            (const double *)h->d_wphi, (double *)h->pj, (double *)h->pu};
         e = launch_sweep_f64(a, L.shape, h->stream);
     } else {
         SweepArgs<float> a{L.nx, L.ny, L.nz, h->atom.n_freq, L.shape.ng, L.shape.ngroups,
                            L.shape.rows, h->up_mask, (const float *)L.chi0,
                            (const float *)L.S, (const float *)L.bbot, L.geom,
-                           (const float *)h->d_phi, (const float *)h->d_wphi,
-                           (float *)h->pj, (float *)h->pu};
+                           (const float *)h->d_phi, (const float *)h->d_inv_phi,
+                           (const float *)h->d_wphi, (float *)h->pj, (float *)h->pu};
         e = launch_sweep_f32(a, L.shape, h->stream);
     }
     MG_TRY(launched(h, e, "sweep"));
@@ -538,19 +546,26 @@ int create_impl(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_qu
     const int nf = atom->n_freq;
     MG_TRY(dev_alloc(&h->d_phi, nf * es));
     MG_TRY(dev_alloc(&h->d_wphi, nf * es));
-    std::vector<double> wphi_ray(nf);
-    for (int i = 0; i < nf; ++i) wphi_ray[i] = h->wphi[i] / kRays;
+    MG_TRY(dev_alloc(&h->d_inv_phi, nf * es));
+    std::vector<double> wphi_ray(nf), inv_phi(nf);
+    for (int i = 0; i < nf; ++i) {
+        wphi_ray[i] = h->wphi[i] / kRays;
+        inv_phi[i] = 1.0 / h->phi[i];
+    }
     if (h->prec == MG3D_PREC_F64) {
         MG_CUDA(cudaMemcpy(h->d_phi, h->phi.data(), nf * es, cudaMemcpyHostToDevice));
         MG_CUDA(cudaMemcpy(h->d_wphi, wphi_ray.data(), nf * es, cudaMemcpyHostToDevice));
+        MG_CUDA(cudaMemcpy(h->d_inv_phi, inv_phi.data(), nf * es, cudaMemcpyHostToDevice));
     } else {
-        std::vector<float> a(nf), b(nf);
+        std::vector<float> a(nf), b(nf), c(nf);
         for (int i = 0; i < nf; ++i) {
             a[i] = (float)h->phi[i];
             b[i] = (float)wphi_ray[i];
+            c[i] = (float)inv_phi[i];
         }
         MG_CUDA(cudaMemcpy(h->d_phi, a.data(), nf * es, cudaMemcpyHostToDevice));
         MG_CUDA(cudaMemcpy(h->d_wphi, b.data(), nf * es, cudaMemcpyHostToDevice));
+        MG_CUDA(cudaMemcpy(h->d_inv_phi, c.data(), nf * es, cudaMemcpyHostToDevice));
     }
     MG_TRY(dev_alloc(&h->pj, h->partial_elems * es));
     MG_TRY(dev_alloc(&h->pu, h->partial_elems * es));
@@ -612,7 +627,7 @@ int mg3d_destroy(mg3d_handle *h) {
     if (!h) return MG3D_OK;
     if (h->stream) cudaStreamSynchronize(h->stream);
     for (int k = 0; k <= MG3D_MAX_GRIDS; ++k) free_level(h->lev[k]);
-    void *ptrs[] = {h->d_phi, h->d_wphi, h->pj, h->pu, h->scal, h->scratch};
+    void *ptrs[] = {h->d_phi, h->d_wphi, h->d_inv_phi, h->pj, h->pu, h->scal, h->scratch};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &t : h->timed) {
@@ -835,7 +850,7 @@ int mg3d_set_fs_config(mg3d_handle *h, int level, int freq_per_block, int bands,
     Level &L = h->lev[level];
     const int nf = h->atom.n_freq;
     if (freq_per_block < 1 || freq_per_block > nf || bands < 1 || bands > kMaxBands ||
-        bands > L.ny || threads < 32 || threads > 256 || threads % 32)
+        bands > L.ny || threads < 32 || threads > kMaxSweepThreads || threads % 32)
         return fail(MG3D_E_ARG, "bad sweep shape");
     SweepShape s{freq_per_block, (nf + freq_per_block - 1) / freq_per_block, bands,
                  (L.ny + bands - 1) / bands, threads};

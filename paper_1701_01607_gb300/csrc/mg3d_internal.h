@@ -9,6 +9,7 @@ namespace mg3d {
 
 constexpr int kRays = 24;          // A4 quadrature, 12 up and 12 down
 constexpr int kMaxBands = 8;       // thread blocks per cluster sharing a plane
+constexpr int kMaxSweepThreads = 512;
 constexpr size_t kMaxSweepSmem = 200 * 1024;
 
 // Upwind geometry of one sweep step of one ray.  The short characteristic of
@@ -41,6 +42,7 @@ struct SweepArgs {
     const T *bbot;           // [nx*ny] intensity entering at the bottom
     const StepGeom *geom;    // [kRays][nz], entry t = 1..nz-1 used
     const T *phi;            // [nfreq] profile
+    const T *inv_phi;        // [nfreq] 1/profile
     const T *wphi;           // [nfreq] ray weight x frequency weight x profile
     T *pj, *pu;              // [kRays*ngroups][nvox] partial Jeff and U
 };
