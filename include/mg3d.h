@@ -220,6 +220,43 @@ int mg3d_set_timing(mg3d_handle *h, int enable);
 int mg3d_get_counters(mg3d_handle *h, mg3d_counters *out);
 int mg3d_reset_counters(mg3d_handle *h);
 
+/* Allocation-free formal solution.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory at the moment
+ * they need a formal solution -- code running under another framework's
+ * memory pool that forbids foreign cudaMalloc calls, allocation-free sections
+ * of a real-time pipeline, or a process whose device memory is all held by a
+ * caching allocator.  It allocates nothing: the caller passes device inputs
+ * and outputs, and the scratch of the sweep (partial sums per ray, upwind
+ * geometry, frequency tables) lives in one fixed array in the library's
+ * device image, about 26 MB, which every GPU that loads the library holds
+ * until the process exits.
+ *
+ * It computes what mg3d_formal_solve computes on one grid, always in FP64:
+ *   z_dev    [nz] node heights (device), strictly increasing;
+ *   chi0_dev [nz][ny][nx] line opacity at unit profile, kappa (n_l g_u/g_l - n_u);
+ *   S_dev    [nz][ny][nx] line source function n_u / (n_l g_u/g_l - n_u);
+ *   bbot_dev [ny][nx] intensity entering through the bottom plane;
+ *   jeff_dev, u_dev [nz][ny][nx] outputs Jeff and U = 1 - Lambda*;
+ *   atom gives n_freq and x_max; quad_a selects the A4 set as in
+ *   mg3d_quadrature; cuda_stream orders the work (NULL: the legacy default
+ *   stream).  The call returns once the work is enqueued.
+ * Limits: at most MG3D_NOALLOC_MAX_NODES nodes, MG3D_NOALLOC_MAX_NZ planes and
+ * MG3D_NOALLOC_MAX_FREQ frequencies; larger inputs return MG3D_E_ARG with a
+ * message naming the limit.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) while that device is current;
+ * make that first call before any stream capture.  All calls share the one
+ * array, and each call rewrites all of it that it reads: calls whose work
+ * overlaps on the GPU race, so order them on one stream or synchronise
+ * between them. */
+#define MG3D_NOALLOC_MAX_NODES 65536
+#define MG3D_NOALLOC_MAX_NZ 1024
+#define MG3D_NOALLOC_MAX_FREQ 64
+int mg3d_formal_solve_noalloc(int nx, int ny, int nz, double dx, double dy,
+                              const double *z_dev, const mg3d_atom *atom, double quad_a,
+                              const double *chi0_dev, const double *S_dev,
+                              const double *bbot_dev, double *jeff_dev, double *u_dev,
+                              void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libmg3d.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["fs_sweep.cu", "rates_transfer.cu", "mg3d_api.cu"]
+SOURCES = ["fs_sweep.cu", "rates_transfer.cu", "mg3d_api.cu", "noalloc.cu"]
 HEADERS = [os.path.join(CSRC, "mg3d_internal.h"), os.path.join(INCLUDE, "mg3d.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",

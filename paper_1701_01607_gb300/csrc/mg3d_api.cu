@@ -577,6 +577,11 @@ int create_impl(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_qu
 
 }  // namespace
 
+namespace mg3d {
+// Lets other translation units report through mg3d_last_error().
+void record_error(const std::string &msg) { g_last_error = msg; }
+}  // namespace mg3d
+
 // ======================================================================= ABI
 
 extern "C" {

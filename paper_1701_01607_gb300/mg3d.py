@@ -25,6 +25,9 @@ MG3D_E_STATE = -8
 MG3D_MAX_GRIDS = 8
 MG3D_PREC_F64 = 0
 MG3D_PREC_F32 = 1
+MG3D_NOALLOC_MAX_NODES = 65536
+MG3D_NOALLOC_MAX_NZ = 1024
+MG3D_NOALLOC_MAX_FREQ = 64
 
 _D = ctypes.POINTER(ctypes.c_double)
 
@@ -98,6 +101,11 @@ _SIGNATURES = {
     "mg3d_set_timing": (_I, [_H, _I]),
     "mg3d_get_counters": (_I, [_H, ctypes.POINTER(mg3d_counters)]),
     "mg3d_reset_counters": (_I, [_H]),
+    "mg3d_formal_solve_noalloc": (_I, [_I, _I, _I, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_void_p, ctypes.POINTER(mg3d_atom),
+                                       ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
 }
 
 _lib = None
@@ -305,3 +313,18 @@ def mg3d_get_counters(h):
 
 def mg3d_reset_counters(h):
     return _check(load().mg3d_reset_counters(h))
+
+
+def mg3d_formal_solve_noalloc(nx: int, ny: int, nz: int, dx: float, dy: float, z_dev: int,
+                              atom, quad_a: float, chi0_dev: int, S_dev: int, bbot_dev: int,
+                              jeff_dev: int, u_dev: int, stream_ptr: int | None = None) -> int:
+    """Allocation-free formal solution on caller-owned device buffers.
+
+    All buffer arguments are device addresses (e.g. a torch tensor's
+    data_ptr()); returns the library's status code without raising, so that
+    callers can inspect limit errors.
+    """
+    at = mg3d_atom(atom.a_ul, atom.g_ratio, atom.theta, atom.kappa, atom.n_freq, atom.x_max)
+    return load().mg3d_formal_solve_noalloc(nx, ny, nz, dx, dy, z_dev, ctypes.byref(at),
+                                            quad_a, chi0_dev, S_dev, bbot_dev, jeff_dev,
+                                            u_dev, stream_ptr)
