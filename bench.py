@@ -131,9 +131,16 @@ def run_gpu(args):
     stream = torch.cuda.Stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
 
+    tuning = {}
+
     def make(prec):
         h = m.mg3d_create(atm, atom, n_grids=N_GRIDS, fs_prec=prec, **NU)
         m.mg3d_set_stream(h, stream.cuda_stream)
+        if not args.no_autotune:
+            info = m.mg3d_autotune(h)
+            tuning["f64" if prec == m.MG3D_PREC_F64 else "f32"] = {
+                "seconds": round(info["seconds"], 3), "candidates": info["evaluated"],
+                "shapes": {k: m.mg3d_get_fs_config(h, k) for k in range(1, N_GRIDS + 1)}}
         return h
 
     def timed_cycles(h, steps, warmup, timing):
@@ -219,7 +226,8 @@ def run_gpu(args):
             "config": {"workload": WORKLOAD, "grid": list(GRID), "n_grids": N_GRIDS,
                        "n_freq": 9, "rays": 24, **NU, "fs_precision": "f64",
                        "parallelism": f"replicas x{world}",
-                       "l2": "256 MB buffer written between timed steps"},
+                       "l2": "256 MB buffer written between timed steps",
+                       "sweep_autotune": tuning},
             "roofline": {"kernel": "sweep_kernel<double> (finest grid)", "bound": "alu",
                          "achieved": round(achieved, 4), "peak": round(peak, 4),
                          "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
@@ -240,6 +248,11 @@ def run_gpu(args):
                 "fine_sweep_ms": round(fine_ms32, 4),
                 "fine_sweep_gunits_s": round(fine_units / (fine_ms32 * 1e-3) / 1e9, 3)},
             "fine_sweep_gunits_s": round(fine_units / (fine_ms * 1e-3) / 1e9, 3),
+            "sweep_ms_per_launch_by_level": {
+                k: round(cnt["level_fs_kernel_ms"][k] / max(1, cnt["level_fs_timed_launches"][k]), 4)
+                for k in range(1, N_GRIDS + 1)},
+            "sweep_launches_per_step_by_level": {
+                k: cnt["level_fs_launches"][k] // args.steps for k in range(1, N_GRIDS + 1)},
         }
         if not args.no_tts and world == 1:
             result["time_to_solution"] = time_to_solution(m, atm, atom, stream)
@@ -324,14 +337,21 @@ def run_reference(args):
                     "d2h_bytes_per_step": 0}}
 
 
-def run_profile_case(prec_name, launches):
-    """A few finest-grid formal solutions of the bench workload, for ncu."""
+def run_profile_case(prec_name, launches, shape):
+    """A few finest-grid formal solutions of the bench workload, for ncu.
+
+    ``shape`` "ng,bands,threads" fixes the sweep's launch shape (e.g. the one
+    the autotuner chose in a bench run); empty keeps the library default.
+    No autotuning runs here, so every sweep launch is a profiled one."""
     from paper_1701_01607_gb300 import mg3d as m
     m.load(build_if_missing=True)
     atm, atom = build_problem(seed=1)
     prec = m.MG3D_PREC_F64 if prec_name == "f64" else m.MG3D_PREC_F32
     h = m.mg3d_create(atm, atom, n_grids=N_GRIDS, fs_prec=prec, **NU)
     try:
+        if shape:
+            ng, bands, th = (int(v) for v in shape.split(","))
+            m.mg3d_set_fs_config(h, N_GRIDS, ng, bands, th)
         for _ in range(launches):
             m.mg3d_formal_solve(h, N_GRIDS, want=False)
         print("profile case:", prec_name, m.mg3d_get_fs_config(h, N_GRIDS), flush=True)
@@ -347,12 +367,15 @@ def main():
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--no-tts", action="store_true", help="skip time-to-solution runs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default sweep shapes")
     ap.add_argument("--profile-sweep", choices=["f64", "f32"],
                     help="only run a few finest-grid formal solutions (for ncu)")
     ap.add_argument("--profile-launches", type=int, default=3)
+    ap.add_argument("--profile-shape", default="", help="ng,bands,threads of the profiled sweep")
     args = ap.parse_args()
     if args.profile_sweep:
-        run_profile_case(args.profile_sweep, args.profile_launches)
+        run_profile_case(args.profile_sweep, args.profile_launches, args.profile_shape)
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -214,6 +214,20 @@ int mg3d_set_fs_config(mg3d_handle *h, int level, int freq_per_block, int bands,
 int mg3d_get_fs_config(const mg3d_handle *h, int level, int *freq_per_block, int *bands,
                        int *threads);
 
+/* Autotuner: times candidate sweep shapes on this GPU with the level's current
+ * populations and keeps the fastest per level (level = 0: every level).
+ * Candidates: every number of frequency groups up to 64, 1-8 bands and
+ * 128/256/512 threads that fit; one launch each, then the best eight three
+ * more times.  Overwrites the partial sums (not the populations).
+ * *evaluated and *seconds (nullable) report the candidates and wall time. */
+int mg3d_autotune(mg3d_handle *h, int level, int *evaluated, double *seconds);
+
+/* Check of the FP64 exponential the sweep uses: for each x_host[i] >= 0 the
+ * GPU writes out_host[2i] = the sweep's e^{-x} and out_host[2i+1] = CUDA's
+ * exp(-x), so callers can bound the difference.  Allocates temporary device
+ * memory; out_host holds 2n doubles. */
+int mg3d_check_exp(int n, const double *x_host, double *out_host);
+
 /* Per-launch device timing of the sweep kernel (CUDA events on the handle's
  * stream) on or off, counters and their reset. */
 int mg3d_set_timing(mg3d_handle *h, int enable);

@@ -25,6 +25,8 @@
 // slots in a fixed order, so results are deterministic.
 #include <cooperative_groups.h>
 
+#include <cmath>
+
 #include "mg3d_internal.h"
 
 namespace cg = cooperative_groups;
@@ -40,19 +42,50 @@ namespace mg3d {
 template <typename T>
 struct ScWeights;
 
+// e^{-x} for x >= 0 by the table-driven method of Tang (ACM TOMS 15, 1989):
+// -x = (64 m + j) ln2/64 + r with integer m, j in [0, 64) and |r| <= ln2/128,
+// so e^{-x} = 2^m 2^{j/64} e^r.  The reduction uses a two-part ln2/64 whose
+// high part times any |n| < 2^17 is exact; e^r - 1 is its Taylor polynomial of
+// degree 5 (truncation < 4e-17 relative); 2^{j/64} comes from a 64-entry
+// table and 2^m is applied by adding m to the exponent field.  Results below
+// e^{-708} are flushed to zero.
+struct ExpNegTable {
+    const double *tab;   // [64] 2^{j/64}
+    double l1, l2;       // ln2/64 = l1 + l2, l1 with 36 significant bits
+};
+
+__device__ __forceinline__ double exp_neg(double x, const ExpNegTable e) {
+    if (x > 708.0) return 0.0;
+    const double magic = 6755399441055744.0;  // 1.5 * 2^52
+    const double t = fma(x, -92.33248261689366, magic);  // -x * 64/ln2, rounded to an integer
+    const int n = __double2loint(t);
+    const double nd = t - magic;
+    double r = fma(-nd, e.l1, -x);
+    r = fma(-nd, e.l2, r);
+    double p = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+    p = fma(p, r, 1.0 / 6.0);
+    p = fma(p, r, 0.5);
+    p = fma(p, r, 1.0);
+    const double q = p * r;                      // e^r - 1
+    const double tj = e.tab[n & 63];
+    const double v = fma(tj, q, tj);             // 2^{j/64} e^r, in [0.99, 2.01)
+    const long long bits = __double_as_longlong(v) + ((long long)(n >> 6) << 52);
+    return __longlong_as_double(bits);
+}
+
 template <>
 struct ScWeights<double> {
     // inv_x = 1/x, formed by the caller as (1/dtau0)(1/phi): one division per
     // node and ray instead of one per frequency.
-    static __device__ __forceinline__ void eval(double x, double inv_x, double &ex,
-                                                double &w0, double &wup, double &u) {
-        ex = exp(-x);
+    static __device__ __forceinline__ void eval(double x, double inv_x, const ExpNegTable et,
+                                                double &ex, double &w0, double &wup, double &u) {
+        ex = exp_neg(x, et);
         if (x < 1e-3) {
             w0 = x * (0.5 - x * (1.0 / 6.0 - x * (1.0 / 24.0 - x * (1.0 / 120.0 - x / 720.0))));
             wup = x * (0.5 - x * (1.0 / 3.0 - x * (1.0 / 8.0 - x * (1.0 / 30.0 - x / 144.0))));
             u = 1.0 - w0;
         } else {
-            u = (1.0 - ex) * inv_x;
+            u = fma(-ex, inv_x, inv_x);   // (1 - e^-x)/x
             w0 = 1.0 - u;
             wup = u - ex;
         }
@@ -61,15 +94,15 @@ struct ScWeights<double> {
 
 template <>
 struct ScWeights<float> {
-    static __device__ __forceinline__ void eval(float x, float inv_x, float &ex, float &w0,
-                                                float &wup, float &u) {
+    static __device__ __forceinline__ void eval(float x, float inv_x, const ExpNegTable,
+                                                float &ex, float &w0, float &wup, float &u) {
         ex = __expf(-x);
         if (x < 0.1f) {
             w0 = x * (0.5f - x * (1.0f / 6.0f - x * (1.0f / 24.0f - x * (1.0f / 120.0f - x / 720.0f))));
             wup = x * (0.5f - x * (1.0f / 3.0f - x * (1.0f / 8.0f - x * (1.0f / 30.0f - x / 144.0f))));
             u = 1.0f - w0;
         } else {
-            u = (1.0f - ex) * inv_x;
+            u = fmaf(-ex, inv_x, inv_x);   // (1 - e^-x)/x
             w0 = 1.0f - u;
             wup = u - ex;
         }
@@ -97,8 +130,10 @@ __global__ void planck_bottom_kernel(long nplane, double theta, const double *__
         bbot[p] = (T)(1.0 / expm1(theta / Tgas[p]));
 }
 
-template <typename T>
-__global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs<T> a) {
+// MAXT: the block size bound the kernel is compiled for (256 or 512); the
+// register budget per thread follows from it.
+template <typename T, int MAXT>
+__global__ void __launch_bounds__(MAXT) sweep_kernel(const SweepArgs<T> a) {
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int g = blockIdx.y;
@@ -119,6 +154,12 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf = reinterpret_cast<T *>(smem_raw);
     const long bufstride = (long)a.ng * rows * nx;
+    __shared__ double exp_tab[64];
+    if (sizeof(T) == 8) {
+        for (int i = threadIdx.x; i < 64; i += blockDim.x) exp_tab[i] = a.exp_tab[i];
+        __syncthreads();
+    }
+    const ExpNegTable et{exp_tab, a.exp_l1, a.exp_l2};
 
     for (int t = 0; t < nz; ++t) {
         const int k = up ? t : nz - 1 - t;
@@ -185,7 +226,7 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs<T> a) {
                                    w01 * Pb[off + xa] + w11 * Pb[off + xb];
                     T ex, w0, wup, u;
                     ScWeights<T>::eval(dtau0 * a.phi[f0 + f], inv_dtau0 * a.inv_phi[f0 + f],
-                                       ex, w0, wup, u);
+                                       et, ex, w0, wup, u);
                     const T part = I_up * ex + wup * S_up;
                     cur[((long)f * rows + yl) * nx + x] = part + w0 * S_loc;
                     const T w = a.wphi[f0 + f];
@@ -202,16 +243,43 @@ __global__ void __launch_bounds__(512) sweep_kernel(const SweepArgs<T> a) {
     }
 }
 
+__global__ void exp_check_kernel(int n, const double *__restrict__ x, double *__restrict__ out,
+                                 const double *__restrict__ tab, double l1, double l2) {
+    const ExpNegTable et{tab, l1, l2};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        out[2 * i] = exp_neg(x[i], et);
+        out[2 * i + 1] = exp(-x[i]);
+    }
+}
+
+cudaError_t launch_exp_check(int n, const double *x, double *out, const double *tab, double l1,
+                             double l2, cudaStream_t st) {
+    exp_check_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, x, out, tab, l1, l2);
+    return cudaGetLastError();
+}
+
+void exp_neg_constants(double *tab64, double *l1, double *l2) {
+    // 2^{j/64} correctly rounded through the wider long double
+    for (int j = 0; j < 64; ++j) tab64[j] = (double)exp2l((long double)j / 64.0L);
+    // ln2 = LN2_HI + LN2_LO to about 1e-33
+    const double ln2_hi = 0.6931471805599453094172321;
+    const double ln2_lo = 2.3190468138462996e-17;
+    const double c = ln2_hi / 64.0;                   // exact: division by a power of two
+    const double hi = std::ldexp(std::floor(std::ldexp(c, 36 + 7)), -(36 + 7));
+    *l1 = hi;
+    *l2 = (c - hi) + ln2_lo / 64.0;
+}
+
 size_t sweep_smem_bytes(int prec, const SweepShape &s, int nx) {
     size_t elem = prec == 0 ? sizeof(double) : sizeof(float);
     return 2ull * s.ng * s.rows * nx * elem;
 }
 
-template <typename T>
+template <typename T, int MAXT>
 static cudaError_t launch_sweep_t(const SweepArgs<T> &a, const SweepShape &s,
                                   cudaStream_t st) {
     size_t smem = sweep_smem_bytes(sizeof(T) == 8 ? 0 : 1, s, a.nx);
-    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T>,
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, MAXT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -227,15 +295,22 @@ static cudaError_t launch_sweep_t(const SweepArgs<T> &a, const SweepShape &s,
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, sweep_kernel<T>, a);
+    return cudaLaunchKernelEx(&cfg, sweep_kernel<T, MAXT>, a);
+}
+
+template <typename T>
+static cudaError_t launch_sweep_any(const SweepArgs<T> &a, const SweepShape &s,
+                                    cudaStream_t st) {
+    if (s.threads <= 256) return launch_sweep_t<T, 256>(a, s, st);
+    return launch_sweep_t<T, 512>(a, s, st);
 }
 
 cudaError_t launch_sweep_f64(const SweepArgs<double> &a, const SweepShape &s, cudaStream_t st) {
-    return launch_sweep_t<double>(a, s, st);
+    return launch_sweep_any<double>(a, s, st);
 }
 
 cudaError_t launch_sweep_f32(const SweepArgs<float> &a, const SweepShape &s, cudaStream_t st) {
-    return launch_sweep_t<float>(a, s, st);
+    return launch_sweep_any<float>(a, s, st);
 }
 
 static int grid_for(long n, int threads) {

@@ -87,6 +87,8 @@ struct mg3d_handle {
     Level lev[MG3D_MAX_GRIDS + 1];
     std::vector<double> phi, wphi;
     void *d_phi = nullptr, *d_wphi = nullptr, *d_inv_phi = nullptr;
+    double *d_exp_tab = nullptr;         // [64] table of the FP64 exp in the sweep
+    double exp_l1 = 0, exp_l2 = 0;
     void *pj = nullptr, *pu = nullptr;
     size_t partial_elems = 0;
     unsigned long long *scal = nullptr;  // [0] C bits, [1] negative after a sweep,
@@ -185,32 +187,42 @@ int threads_for_band(int band) {
     return th < 32 ? 32 : (th > kMaxSweepThreads ? kMaxSweepThreads : th);
 }
 
-// Sweep shape: spread the 24 x ceil(nfreq/ng) x bands blocks evenly over the
-// 152 SMs.  Cost = blocks per SM x nodes per block x (ng + c_node), where
-// c_node is the per-(node, ray) work shared by a group's frequencies (upwind
-// chi/S interpolation, 1/dtau) relative to one frequency; ties prefer fewer
-// partial slots, then fewer bands.
+// Default sweep shape before any autotuning: three frequencies per block and
+// the number of bands that brings the grid closest to two blocks per SM (the
+// shapes measured fastest on the 64x64 planes of the bench workload, in both
+// precisions, were of this kind); mg3d_autotune replaces it by measurement.
 SweepShape choose_shape(int prec, int nx, int ny, int nfreq) {
+    const int ng = nfreq < 3 ? nfreq : 3;
+    const int ngroups = (nfreq + ng - 1) / ng;
     SweepShape best{};
-    double best_cost = 1e300;
-    const double c_node = 0.3;
-    for (int ng = 1; ng <= nfreq; ++ng) {
-        const int ngroups = (nfreq + ng - 1) / ng;
-        for (int bands = 1; bands <= kMaxBands && bands <= ny; ++bands) {
+    long best_gap = 1L << 40;
+    for (int bands = 1; bands <= kMaxBands && bands <= ny; ++bands) {
+        const int rows = (ny + bands - 1) / bands;
+        if ((long)(bands - 1) * rows >= ny) continue;
+        SweepShape s{ng, ngroups, bands, rows, 256};
+        if (sweep_smem_bytes(prec, s, nx) > kMaxSweepSmem) continue;
+        const long blocks = (long)kRays * ngroups * bands;
+        const long gap = blocks > 304 ? blocks - 304 : 304 - blocks;
+        if (gap < best_gap) {
+            best_gap = gap;
+            best = s;
+        }
+    }
+    if (best.ng == 0) {
+        // planes too large for three frequencies: one frequency, most bands
+        for (int bands = kMaxBands; bands >= 1; --bands) {
+            if (bands > ny) continue;
             const int rows = (ny + bands - 1) / bands;
             if ((long)(bands - 1) * rows >= ny) continue;
-            SweepShape s{ng, ngroups, bands, rows, 256};
-            if (sweep_smem_bytes(prec, s, nx) > kMaxSweepSmem) continue;
-            const long blocks = (long)kRays * ngroups * bands;
-            const double per_sm = (double)((blocks + 151) / 152);
-            const double cost = per_sm * rows * nx * (ng + c_node) + 1e-3 * ngroups + 1e-6 * bands;
-            if (cost < best_cost) {
-                best_cost = cost;
+            SweepShape s{1, nfreq, bands, rows, 256};
+            if (sweep_smem_bytes(prec, s, nx) <= kMaxSweepSmem) {
                 best = s;
+                break;
             }
         }
     }
-    best.threads = threads_for_band(best.rows * nx);
+    int th = threads_for_band(best.rows * nx);
+    best.threads = th > 256 ? 256 : th;
     return best;
 }
 
@@ -279,14 +291,16 @@ int formal_solution(mg3d_handle *h, int k) {
                             L.shape.rows, h->up_mask, (const double *)L.chi0,
                             (const double *)L.S, (const double *)L.bbot, L.geom,
                             (const double *)h->d_phi, (const double *)h->d_inv_phi,
-                            (const double *)h->d_wphi, (double *)h->pj, (double *)h->pu};
+                            (const double *)h->d_wphi, (double *)h->pj, (double *)h->pu,
+                            h->d_exp_tab, h->exp_l1, h->exp_l2};
         e = launch_sweep_f64(a, L.shape, h->stream);
     } else {
         SweepArgs<float> a{L.nx, L.ny, L.nz, h->atom.n_freq, L.shape.ng, L.shape.ngroups,
                            L.shape.rows, h->up_mask, (const float *)L.chi0,
                            (const float *)L.S, (const float *)L.bbot, L.geom,
                            (const float *)h->d_phi, (const float *)h->d_inv_phi,
-                           (const float *)h->d_wphi, (float *)h->pj, (float *)h->pu};
+                           (const float *)h->d_wphi, (float *)h->pj, (float *)h->pu,
+                           h->d_exp_tab, h->exp_l1, h->exp_l2};
         e = launch_sweep_f32(a, L.shape, h->stream);
     }
     MG_TRY(launched(h, e, "sweep"));
@@ -451,6 +465,141 @@ int level_to_host(mg3d_handle *h, double *dst, const double *src, size_t count) 
     return MG3D_OK;
 }
 
+int make_shape(const mg3d_handle *h, int k, int ng, int bands, int threads, SweepShape *out) {
+    const Level &L = h->lev[k];
+    const int nf = h->atom.n_freq;
+    if (ng < 1 || ng > nf || bands < 1 || bands > kMaxBands || bands > L.ny || threads < 32 ||
+        threads > kMaxSweepThreads || threads % 32)
+        return fail(MG3D_E_ARG, "bad sweep shape");
+    SweepShape s{ng, (nf + ng - 1) / ng, bands, (L.ny + bands - 1) / bands, threads};
+    if ((long)(bands - 1) * s.rows >= L.ny) return fail(MG3D_E_ARG, "empty band");
+    if (sweep_smem_bytes(h->prec, s, L.nx) > kMaxSweepSmem)
+        return fail(MG3D_E_ARG, "sweep shape exceeds shared memory");
+    *out = s;
+    return MG3D_OK;
+}
+
+// Partial-sum buffers of at least `need` elements (contents not kept).
+int ensure_partials(mg3d_handle *h, size_t need) {
+    if (need <= h->partial_elems) return MG3D_OK;
+    const size_t es = elem_size(h->prec);
+    MG_CUDA(cudaStreamSynchronize(h->stream));
+    cudaFree(h->pj);
+    cudaFree(h->pu);
+    h->pj = h->pu = nullptr;
+    h->partial_elems = 0;
+    MG_TRY(dev_alloc(&h->pj, need * es));
+    MG_TRY(dev_alloc(&h->pu, need * es));
+    h->partial_elems = need;
+    return MG3D_OK;
+}
+
+// Shrink the partial buffers to what the current shapes of all levels need.
+int shrink_partials(mg3d_handle *h) {
+    size_t need = 0;
+    for (int k = 1; k <= h->L; ++k)
+        need = std::max(need, (size_t)kRays * h->lev[k].shape.ngroups * (size_t)h->lev[k].nvox);
+    if (need >= h->partial_elems) return MG3D_OK;
+    h->partial_elems = 0;
+    return ensure_partials(h, need);
+}
+
+// Device time of `reps` sweep launches of level k with shape s (ms each).
+int time_shape(mg3d_handle *h, int k, const SweepShape &s, int reps, float *ms) {
+    Level &L = h->lev[k];
+    const SweepShape saved = L.shape;
+    L.shape = s;
+    cudaEvent_t a = pool_event(h), b = pool_event(h);
+    int rc = MG3D_OK;
+    cudaError_t e = cudaEventRecord(a, h->stream);
+    for (int i = 0; i < reps && e == cudaSuccess; ++i) {
+        if (h->prec == MG3D_PREC_F64) {
+            SweepArgs<double> sa{L.nx, L.ny, L.nz, h->atom.n_freq, s.ng, s.ngroups, s.rows,
+                                 h->up_mask, (const double *)L.chi0, (const double *)L.S,
+                                 (const double *)L.bbot, L.geom, (const double *)h->d_phi,
+                                 (const double *)h->d_inv_phi, (const double *)h->d_wphi,
+                                 (double *)h->pj, (double *)h->pu, h->d_exp_tab, h->exp_l1,
+                                 h->exp_l2};
+            e = launch_sweep_f64(sa, s, h->stream);
+        } else {
+            SweepArgs<float> sa{L.nx, L.ny, L.nz, h->atom.n_freq, s.ng, s.ngroups, s.rows,
+                                h->up_mask, (const float *)L.chi0, (const float *)L.S,
+                                (const float *)L.bbot, L.geom, (const float *)h->d_phi,
+                                (const float *)h->d_inv_phi, (const float *)h->d_wphi,
+                                (float *)h->pj, (float *)h->pu, h->d_exp_tab, h->exp_l1,
+                                h->exp_l2};
+            e = launch_sweep_f32(sa, s, h->stream);
+        }
+        ++h->launches;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
+    if (e != cudaSuccess) rc = fail(MG3D_E_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+    else *ms /= (float)reps;
+    h->event_pool.push_back(a);
+    h->event_pool.push_back(b);
+    L.shape = saved;
+    return rc;
+}
+
+// Time candidate sweep shapes of level k with its current populations and
+// keep the fastest: every (frequencies per block, bands, threads) that fits,
+// one launch each, then the best eight again three times each.
+int autotune_level(mg3d_handle *h, int k, int *evaluated) {
+    Level &L = h->lev[k];
+    const int nf = h->atom.n_freq;
+    std::vector<int> ngs;
+    for (int ng = 1; ng <= nf; ++ng) {
+        const int groups = (nf + ng - 1) / ng;
+        if (groups > 64) continue;
+        // one ng per distinct group count, the smallest that gives it
+        if (!ngs.empty() && (nf + ngs.back() - 1) / ngs.back() == groups) continue;
+        ngs.push_back(ng);
+    }
+    std::vector<SweepShape> cands;
+    for (int ng : ngs)
+        for (int bands = 1; bands <= kMaxBands && bands <= L.ny; ++bands)
+            for (int th : {128, 256, 512}) {
+                SweepShape s;
+                if (make_shape(h, k, ng, bands, th, &s) != MG3D_OK) continue;
+                const int band = s.rows * L.nx;
+                if (th > 128 && th / 2 >= band) continue;  // a smaller block covers the band
+                cands.push_back(s);
+            }
+    g_last_error.clear();
+    if (cands.empty()) return fail(MG3D_E_ARG, "no sweep shape fits");
+    size_t need = 0;
+    for (auto &s : cands) need = std::max(need, (size_t)kRays * s.ngroups * (size_t)L.nvox);
+    MG_TRY(ensure_partials(h, need));
+    MG_TRY(launched(h, launch_opacity(h->prec, L.nvox, h->atom.g_ratio, h->atom.kappa, L.n,
+                                      L.chi0, L.S, h->stream),
+                    "opacity"));
+    float warm = 0.f;
+    MG_TRY(time_shape(h, k, L.shape, 1, &warm));
+    std::vector<std::pair<float, size_t>> t1;
+    for (size_t i = 0; i < cands.size(); ++i) {
+        float ms = 0.f;
+        MG_TRY(time_shape(h, k, cands[i], 1, &ms));
+        t1.push_back({ms, i});
+    }
+    std::sort(t1.begin(), t1.end());
+    const size_t keep = std::min<size_t>(8, t1.size());
+    float best_ms = 1e30f;
+    size_t best = t1[0].second;
+    for (size_t j = 0; j < keep; ++j) {
+        float ms = 0.f;
+        MG_TRY(time_shape(h, k, cands[t1[j].second], 3, &ms));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = t1[j].second;
+        }
+    }
+    L.shape = cands[best];
+    if (evaluated) *evaluated = (int)cands.size();
+    return MG3D_OK;
+}
+
 int create_impl(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_quadrature *quad,
                 const mg3d_params *params, mg3d_handle *h) {
     h->L = params->n_grids;
@@ -567,6 +716,12 @@ int create_impl(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_qu
         MG_CUDA(cudaMemcpy(h->d_wphi, b.data(), nf * es, cudaMemcpyHostToDevice));
         MG_CUDA(cudaMemcpy(h->d_inv_phi, c.data(), nf * es, cudaMemcpyHostToDevice));
     }
+    {
+        double tab[64];
+        exp_neg_constants(tab, &h->exp_l1, &h->exp_l2);
+        MG_TRY(dalloc(&h->d_exp_tab, 64));
+        MG_CUDA(cudaMemcpy(h->d_exp_tab, tab, sizeof(tab), cudaMemcpyHostToDevice));
+    }
     MG_TRY(dev_alloc(&h->pj, h->partial_elems * es));
     MG_TRY(dev_alloc(&h->pu, h->partial_elems * es));
     MG_TRY(dalloc(&h->scal, 4));
@@ -632,7 +787,8 @@ int mg3d_destroy(mg3d_handle *h) {
     if (!h) return MG3D_OK;
     if (h->stream) cudaStreamSynchronize(h->stream);
     for (int k = 0; k <= MG3D_MAX_GRIDS; ++k) free_level(h->lev[k]);
-    void *ptrs[] = {h->d_phi, h->d_wphi, h->d_inv_phi, h->pj, h->pu, h->scal, h->scratch};
+    void *ptrs[] = {h->d_phi, h->d_wphi, h->d_inv_phi, h->d_exp_tab, h->pj, h->pu, h->scal,
+                    h->scratch};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &t : h->timed) {
@@ -852,30 +1008,29 @@ int mg3d_prolong(mg3d_handle *h, int level_fine, int ncomp, const double *coarse
 
 int mg3d_set_fs_config(mg3d_handle *h, int level, int freq_per_block, int bands, int threads) {
     MG_TRY(check_level(h, level));
-    Level &L = h->lev[level];
-    const int nf = h->atom.n_freq;
-    if (freq_per_block < 1 || freq_per_block > nf || bands < 1 || bands > kMaxBands ||
-        bands > L.ny || threads < 32 || threads > kMaxSweepThreads || threads % 32)
-        return fail(MG3D_E_ARG, "bad sweep shape");
-    SweepShape s{freq_per_block, (nf + freq_per_block - 1) / freq_per_block, bands,
-                 (L.ny + bands - 1) / bands, threads};
-    if ((long)(bands - 1) * s.rows >= L.ny) return fail(MG3D_E_ARG, "empty band");
-    if (sweep_smem_bytes(h->prec, s, L.nx) > kMaxSweepSmem)
-        return fail(MG3D_E_ARG, "sweep shape exceeds shared memory");
+    SweepShape s;
+    MG_TRY(make_shape(h, level, freq_per_block, bands, threads, &s));
     MG_CUDA(cudaStreamSynchronize(h->stream));
-    const size_t need = (size_t)kRays * s.ngroups * (size_t)L.nvox;
-    if (need > h->partial_elems) {
-        // more partial slots than any level needed so far: grow the buffers
-        const size_t es = elem_size(h->prec);
-        cudaFree(h->pj);
-        cudaFree(h->pu);
-        h->pj = h->pu = nullptr;
-        h->partial_elems = 0;
-        MG_TRY(dev_alloc(&h->pj, need * es));
-        MG_TRY(dev_alloc(&h->pu, need * es));
-        h->partial_elems = need;
+    MG_TRY(ensure_partials(h, (size_t)kRays * s.ngroups * (size_t)h->lev[level].nvox));
+    h->lev[level].shape = s;
+    return MG3D_OK;
+}
+
+int mg3d_autotune(mg3d_handle *h, int level, int *evaluated, double *seconds) {
+    if (!h) return fail(MG3D_E_ARG, "null handle");
+    if (level != 0) MG_TRY(check_level(h, level));
+    auto t0 = std::chrono::steady_clock::now();
+    int count = 0;
+    for (int k = 1; k <= h->L; ++k) {
+        if (level != 0 && k != level) continue;
+        int c = 0;
+        MG_TRY(autotune_level(h, k, &c));
+        count += c;
     }
-    L.shape = s;
+    MG_TRY(shrink_partials(h));
+    if (evaluated) *evaluated = count;
+    if (seconds)
+        *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return MG3D_OK;
 }
 
@@ -887,6 +1042,23 @@ int mg3d_get_fs_config(const mg3d_handle *h, int level, int *freq_per_block, int
     if (bands) *bands = L.shape.bands;
     if (threads) *threads = L.shape.threads;
     return MG3D_OK;
+}
+
+int mg3d_check_exp(int n, const double *x_host, double *out_host) {
+    if (n < 1 || !x_host || !out_host) return fail(MG3D_E_ARG, "bad arguments");
+    double tab[64], l1, l2;
+    exp_neg_constants(tab, &l1, &l2);
+    double *d = nullptr;
+    MG_TRY(dalloc(&d, 64 + 3 * (size_t)n));
+    int rc = MG3D_OK;
+    cudaError_t e = cudaMemcpy(d, tab, sizeof(tab), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d + 64, x_host, n * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_exp_check(n, d + 64, d + 64 + n, d, l1, l2, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(out_host, d + 64 + n, 2 * n * sizeof(double),
+                                         cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) rc = fail(MG3D_E_CUDA, std::string("exp check: ") + cudaGetErrorString(e));
+    cudaFree(d);
+    return rc;
 }
 
 int mg3d_set_timing(mg3d_handle *h, int enable) {

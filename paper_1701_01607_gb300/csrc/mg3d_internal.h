@@ -45,7 +45,14 @@ struct SweepArgs {
     const T *inv_phi;        // [nfreq] 1/profile
     const T *wphi;           // [nfreq] ray weight x frequency weight x profile
     T *pj, *pu;              // [kRays*ngroups][nvox] partial Jeff and U
+    const double *exp_tab;   // [64] 2^{j/64} for the FP64 exp (FP64 sweeps only)
+    double exp_l1, exp_l2;   // two-part ln2/64
 };
+
+// Table and reduction constants of the FP64 e^{-x} of the sweep.
+void exp_neg_constants(double *tab64, double *l1, double *l2);
+cudaError_t launch_exp_check(int n, const double *x, double *out, const double *tab, double l1,
+                             double l2, cudaStream_t st);
 
 size_t sweep_smem_bytes(int prec, const SweepShape &s, int nx);
 

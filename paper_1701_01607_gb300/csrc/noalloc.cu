@@ -43,7 +43,8 @@ constexpr long kGeomDoubles = (long)kRays * kMaxNz * (sizeof(StepGeom) / sizeof(
 constexpr long kOffPhi = kOffGeom + kGeomDoubles;
 constexpr long kOffInvPhi = kOffPhi + kMaxFreq;
 constexpr long kOffWphi = kOffInvPhi + kMaxFreq;
-constexpr long kScratchDoubles = kOffWphi + kMaxFreq;
+constexpr long kOffExpTab = kOffWphi + kMaxFreq;
+constexpr long kScratchDoubles = kOffExpTab + 64;
 static_assert(sizeof(StepGeom) % sizeof(double) == 0, "geometry entries pack into doubles");
 
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
@@ -129,6 +130,8 @@ __global__ void noalloc_tables_kernel(int nx, int ny, int nz, double dx, double 
         }
         for (int f = 0; f < nfreq; ++f) wphi[f] /= sum * kRays;
     }
+    if (blockIdx.x == 0 && threadIdx.x < 64)
+        scratch[kOffExpTab + threadIdx.x] = exp2((double)threadIdx.x / 64.0);
 }
 
 // Jeff and U: the 24 ray partials of every node added in ray order.
@@ -207,6 +210,8 @@ extern "C" int mg3d_formal_solve_noalloc(int nx, int ny, int nz, double dx, doub
         nx, ny, nz, dx, dy, z_dev, quad_a, nf, atom->x_max, scratch);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) {
+        double tab_unused[64], l1 = 0.0, l2 = 0.0;
+        exp_neg_constants(tab_unused, &l1, &l2);
         unsigned up_mask = 0;
         for (int r = 0; r < kRays; ++r)
             if (!((r / 3) & 4)) up_mask |= 1u << r;
@@ -214,7 +219,7 @@ extern "C" int mg3d_formal_solve_noalloc(int nx, int ny, int nz, double dx, doub
                             chi0_dev, S_dev, bbot_dev,
                             reinterpret_cast<const StepGeom *>(scratch + kOffGeom),
                             scratch + kOffPhi, scratch + kOffInvPhi, scratch + kOffWphi,
-                            scratch + kOffPj, scratch + kOffPu};
+                            scratch + kOffPj, scratch + kOffPu, scratch + kOffExpTab, l1, l2};
         e = launch_sweep_f64(a, shape, st);
     }
     if (e == cudaSuccess) {

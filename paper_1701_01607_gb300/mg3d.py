@@ -98,6 +98,8 @@ _SIGNATURES = {
     "mg3d_set_fs_config": (_I, [_H, _I, _I, _I, _I]),
     "mg3d_get_fs_config": (_I, [_H, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
                                 ctypes.POINTER(_I)]),
+    "mg3d_autotune": (_I, [_H, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),
+    "mg3d_check_exp": (_I, [_I, _D, _D]),
     "mg3d_set_timing": (_I, [_H, _I]),
     "mg3d_get_counters": (_I, [_H, ctypes.POINTER(mg3d_counters)]),
     "mg3d_reset_counters": (_I, [_H]),
@@ -292,6 +294,20 @@ def mg3d_get_fs_config(h, level: int):
     _check(load().mg3d_get_fs_config(h, level, ctypes.byref(a), ctypes.byref(b),
                                      ctypes.byref(c)))
     return a.value, b.value, c.value
+
+
+def mg3d_autotune(h, level: int = 0):
+    n = _I()
+    secs = ctypes.c_double()
+    _check(load().mg3d_autotune(h, level, ctypes.byref(n), ctypes.byref(secs)))
+    return {"evaluated": n.value, "seconds": secs.value}
+
+
+def mg3d_check_exp(x):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.empty(2 * x.size)
+    _check(load().mg3d_check_exp(x.size, _dptr(x), _dptr(out)))
+    return out[0::2], out[1::2]
 
 
 def mg3d_set_timing(h, enable: bool):

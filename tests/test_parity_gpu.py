@@ -262,3 +262,34 @@ def test_full_size_formal_solution_fp64_and_fp32():
         if prec == m.MG3D_PREC_F64:
             n1o, _ = prob.mali_sweep(3, n0)
             assert rel(n1, n1o) < TOL_POP64
+
+
+# ------------------------------------------------------- sweep internals
+
+def test_sweep_exp_matches_cuda_exp():
+    """The sweep's table-driven FP64 e^{-x} against CUDA's exp (within 2 ulp)."""
+    x = np.concatenate([np.linspace(0.0, 707.9, 200001),
+                        np.logspace(-14, np.log10(707.9), 50001), [0.0, 5e-324, 1e-300]])
+    ours, ref = m.mg3d_check_exp(x)
+    assert np.all(np.isfinite(ours))
+    assert np.max(np.abs(ours - ref) / ref) < 4.5e-16
+    big, _ = m.mg3d_check_exp(np.array([708.5, 745.2, 1000.0, 1e300]))
+    assert np.all(big == 0.0)
+
+
+def test_autotuned_shapes_keep_parity():
+    atm, atom = synth.stratified_two_level(16, 16, 33, eps=1e-3, sigma=0.3, seed=12)
+    h = make(atm, atom, n_grids=2)
+    prob = O.TwoLevelProblem(atm, atom, n_grids=2)
+    try:
+        info = m.mg3d_autotune(h)
+        assert info["evaluated"] > 10
+        for k in (1, 2):
+            jeff, u = m.mg3d_formal_solve(h, k)
+            _, jo, uo = prob.formal_solution(k, prob.zero_radiation(k))
+            assert rel(jeff, jo) < TOL_FS64 and rel(u, uo) < TOL_FS64, k
+        c = m.mg3d_fas_vcycle(h, True)
+        n, co = prob.fas_cycle(prob.zero_radiation(2), True, PARAMS)
+        assert rel(m.mg3d_get_populations(h, 2), n) < TOL_POP64
+    finally:
+        m.mg3d_destroy(h)
