@@ -168,3 +168,90 @@ int orc_formal_solution(long nx, long ny, long nz, double dx, double dy,
     free(W0);
     return 0;
 }
+
+/*
+ * Formal solution with per-frequency angle sums, for atoms with several
+ * transitions and a background continuum (Sec. 2.1; MALI with the diagonal
+ * operator of Rybicki & Hummer 1992).  Each frequency belongs to one
+ * transition t; at every node and frequency the total opacity chi and
+ * source function S drive the transfer, while the transition's own share
+ * enters the preconditioning:
+ *     sl = eta_t / chi   (the part of S the transition's new populations set)
+ *     fl = chi_t / chi   (the transition's share of the opacity)
+ * Returned per frequency and node (zeroed here):
+ *     Jx = sum_r w_r (I - w_0 sl),     Ux = sum_r w_r (1 - w_0 fl).
+ * Shapes: chi, S, sl, fl, Jx, Ux [nfreq][nz][ny][nx]; I_bottom, I_top
+ * [nfreq][ny][nx].  Returns 0, or -1 on a bad argument.
+ */
+int orc_formal_solution_nu(long nx, long ny, long nz, double dx, double dy,
+                           const double *z, long nrays, const double *mu,
+                           const double *wray, long nfreq, const double *chi,
+                           const double *S, const double *sl, const double *fl,
+                           const double *I_bottom, const double *I_top,
+                           double *Jx, double *Ux)
+{
+    if (nx < 1 || ny < 1 || nz < 2 || nrays < 1 || nfreq < 1 || dx <= 0 || dy <= 0)
+        return -1;
+    long nplane = nx * ny, nvox = nplane * nz;
+    memset(Jx, 0, sizeof(double) * nvox * nfreq);
+    memset(Ux, 0, sizeof(double) * nvox * nfreq);
+    double *Iprev = malloc(sizeof(double) * nplane);
+    double *Icur = malloc(sizeof(double) * nplane);
+    double *W0 = malloc(sizeof(double) * nplane);
+    if (!Iprev || !Icur || !W0) {
+        free(Iprev);
+        free(Icur);
+        free(W0);
+        return -1;
+    }
+    for (long r = 0; r < nrays; ++r) {
+        double mx = mu[3 * r], my = mu[3 * r + 1], mz = mu[3 * r + 2];
+        int up = mz > 0.0;
+        for (long f = 0; f < nfreq; ++f) {
+            const double *chif = chi + f * nvox, *Sf = S + f * nvox;
+            const double *slf = sl + f * nvox, *flf = fl + f * nvox;
+            double *Jf = Jx + f * nvox, *Uf = Ux + f * nvox;
+            for (long step = 0; step < nz; ++step) {
+                long k = up ? step : nz - 1 - step;
+                if (step == 0) {
+                    const double *bc = (up ? I_bottom : I_top) + f * nplane;
+                    for (long q = 0; q < nplane; ++q) {
+                        Icur[q] = bc[q];
+                        W0[q] = 0.0;
+                    }
+                } else {
+                    long kp = up ? k - 1 : k + 1;
+                    double s = fabs(z[k] - z[kp]) / fabs(mz);
+                    const double *chip = chif + kp * nplane, *Sp = Sf + kp * nplane;
+                    for (long y = 0; y < ny; ++y) {
+                        for (long x = 0; x < nx; ++x) {
+                            double xu = (double)x - s * mx / dx;
+                            double yu = (double)y - s * my / dy;
+                            double I_up = bilinear(Iprev, nx, ny, xu, yu);
+                            double chi_up = bilinear(chip, nx, ny, xu, yu);
+                            double S_up = bilinear(Sp, nx, ny, xu, yu);
+                            long v = node_index(x, y, k, nx, ny);
+                            double dtau = 0.5 * (chi_up + chif[v]) * s;
+                            double ex, w0, wup;
+                            sc_weights(dtau, &ex, &w0, &wup);
+                            Icur[y * nx + x] = I_up * ex + wup * S_up + w0 * Sf[v];
+                            W0[y * nx + x] = w0;
+                        }
+                    }
+                }
+                for (long q = 0; q < nplane; ++q) {
+                    long v = k * nplane + q;
+                    Jf[v] += wray[r] * (Icur[q] - W0[q] * slf[v]);
+                    Uf[v] += wray[r] * (1.0 - W0[q] * flf[v]);
+                }
+                double *t = Iprev;
+                Iprev = Icur;
+                Icur = t;
+            }
+        }
+    }
+    free(Iprev);
+    free(Icur);
+    free(W0);
+    return 0;
+}

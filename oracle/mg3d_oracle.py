@@ -85,6 +85,10 @@ def _load():
         lib.orc_formal_solution.argtypes = [
             ctypes.c_long, ctypes.c_long, ctypes.c_long, ctypes.c_double, ctypes.c_double,
             d, ctypes.c_long, d, d, ctypes.c_long, d, d, d, d, d, d, d, d, d]
+        lib.orc_formal_solution_nu.restype = ctypes.c_int
+        lib.orc_formal_solution_nu.argtypes = [
+            ctypes.c_long, ctypes.c_long, ctypes.c_long, ctypes.c_double, ctypes.c_double,
+            d, ctypes.c_long, d, d, ctypes.c_long, d, d, d, d, d, d, d, d]
         _lib = lib
     return _lib
 
@@ -299,12 +303,12 @@ class TwoLevelProblem:
         return f
 
     def apply(self, M, n):
-        nv = n.reshape(2, -1).T                      # [nvox, 2]
+        nv = n.reshape(n.shape[0], -1).T             # [nvox, N]
         out = np.einsum("vij,vj->vi", M, nv)
         return out.T.reshape(n.shape)
 
     def solve(self, M, f):
-        fv = f.reshape(2, -1).T[:, :, None]
+        fv = f.reshape(f.shape[0], -1).T[:, :, None]
         x = np.linalg.solve(M, fv)[:, :, 0]
         return x.T.reshape(f.shape)
 
@@ -479,6 +483,8 @@ def mali_solve(prob: TwoLevelProblem, tol: float, max_iter: int = 100000, n0=Non
         n, C = prob.mali_sweep(L, n)
         if history is not None:
             history.append(C)
+        if not math.isfinite(C):
+            raise FloatingPointError("MALI produced non-finite populations")
         if C < tol:
             return n, it
     raise RuntimeError("MALI did not converge")
@@ -493,6 +499,8 @@ def fas_solve(prob: TwoLevelProblem, tol: float, params, max_cycles: int = 1000,
         n, C = prob.fas_cycle(n, cyc == 1, params)
         if history is not None:
             history.append(C)
+        if not math.isfinite(C):
+            raise FloatingPointError("FAS produced non-finite populations")
         if C < tol:
             return n, cyc
     raise RuntimeError("FAS did not converge")
@@ -520,6 +528,261 @@ def fmg_solve(prob: TwoLevelProblem, tol: float, params, max_cycles: int = 1000,
         n, C = prob.fas_cycle(n, cyc == 1, params)
         if history is not None:
             history.append(C)
+        if not math.isfinite(C):
+            raise FloatingPointError("FMG produced non-finite populations")
         if C < tol:
             return n, cyc
     raise RuntimeError("FMG did not converge")
+
+
+# --------------------------------------------------------------------------
+# Multi-level atom: lines, bound-free continua, grey background continuum
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class MLLevel:
+    nx: int
+    ny: int
+    nz: int
+    dx: float
+    dy: float
+    z: np.ndarray
+    T: np.ndarray
+    n_tot: np.ndarray
+    chi_c: np.ndarray
+    c: np.ndarray       # [N, N, nz, ny, nx]
+    saha: np.ndarray    # [N, nz, ny, nx]
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+
+def coarsen_ml_level(lev: MLLevel) -> MLLevel:
+    """Coarser grid (Sec. 4.1, 4.7): every second node, full weighting of every
+    atmospheric field (T, n_tot, background opacity, collisional rates, LTE
+    ratios)."""
+    return MLLevel(lev.nx // 2, lev.ny // 2, (lev.nz + 1) // 2, 2 * lev.dx, 2 * lev.dy,
+                   lev.z[::2].copy(), restrict_fw(lev.T), restrict_fw(lev.n_tot),
+                   restrict_fw(lev.chi_c), restrict_fw(lev.c), restrict_fw(lev.saha))
+
+
+def formal_solution_nu_raw(z, dx, dy, mu, wray, chi, S, sl, fl, I_bottom, I_top):
+    """Per-frequency angle sums Jx, Ux [nfreq, nz, ny, nx] (see fs_oracle.c)."""
+    chi = np.ascontiguousarray(chi, dtype=np.float64)
+    nf, nz, ny, nx = chi.shape
+    arrs = [np.ascontiguousarray(np.broadcast_to(a, chi.shape), dtype=np.float64)
+            for a in (S, sl, fl)]
+    Ib = np.ascontiguousarray(np.broadcast_to(I_bottom, (nf, ny, nx)), dtype=np.float64)
+    It = np.ascontiguousarray(np.broadcast_to(I_top, (nf, ny, nx)), dtype=np.float64)
+    Jx = np.empty(chi.shape)
+    Ux = np.empty(chi.shape)
+    rc = _load().orc_formal_solution_nu(nx, ny, nz, float(dx), float(dy),
+                                        _ptr(np.ascontiguousarray(z, dtype=np.float64)),
+                                        len(wray), _ptr(np.ascontiguousarray(mu)),
+                                        _ptr(np.ascontiguousarray(wray)), nf, _ptr(chi),
+                                        _ptr(arrs[0]), _ptr(arrs[1]), _ptr(arrs[2]), _ptr(Ib),
+                                        _ptr(It), _ptr(Jx), _ptr(Ux))
+    if rc != 0:
+        raise RuntimeError("oracle formal solution failed")
+    return Jx, Ux
+
+
+def trapezoid_weights(x):
+    w = np.zeros_like(x)
+    if len(x) == 1:
+        w[0] = 1.0
+        return w
+    d = np.diff(x)
+    w[:-1] += 0.5 * d
+    w[1:] += 0.5 * d
+    return w
+
+
+class MultiLevelProblem(TwoLevelProblem):
+    """W(n) = f for an N-level atom (Eqs. 2-4) with lines, bound-free continua
+    and a grey LTE background continuum, on a hierarchy of grids.
+
+    Per frequency of transition t (lower l, upper u) and node:
+        chi_t = n_l a - n_u b,   eta_t = n_u e        (line or bound-free)
+        chi = chi_t + chi_c,     S = (eta_t + chi_c B_nu)/chi,
+        sl = eta_t / chi,        fl = chi_t / chi.
+    Lines: a = kappa (g_u/g_l) phi, b = kappa phi, e = kappa rho^3 phi with the
+    Doppler profile phi(x) = exp(-(x/d)^2)/(sqrt(pi) d), d = sqrt(T/t_ref).
+    Bound-free (l -> continuum u): a = kappa y^-3, b = kappa y^-3 G E,
+    e = kappa y^-3 G E (rho y)^3 with y = nu/nu_threshold, G = n_l*/n_u* and
+    E = exp(-theta_ref rho y / T).  B_nu = (rho y)^3 / (exp(theta_ref rho y/T) - 1)
+    (rho y -> rho for lines: one Planck value per line).
+    Preconditioned radiative rates (Rybicki & Hummer 1992, diagonal operator),
+    with Jx = sum_r w_r (I - w0 sl), Ux = sum_r w_r (1 - w0 fl) per frequency:
+        R_lu = sum_nu qa Jx,   R_ul = sum_nu (qe Ux + qb Jx),
+    lines: qa = B_lu wphi, qb = B_ul wphi, qe = A_ul wphi (wphi: trapezoid x
+    profile, normalised per node to sum 1; B_ul = A_ul/rho^3,
+    B_lu = (g_u/g_l) B_ul); bound-free: qa = beta w_y y^-4, qb = qa G E,
+    qe = qa G E (rho y)^3.
+    """
+
+    def __init__(self, atm, atom, n_grids: int = 1, quad_a: float | None = None):
+        self.atom = atom
+        self.N = atom.n_levels
+        self.n_grids = n_grids
+        self.mu, self.wray = a4_quadrature(quad_a)
+        fine = MLLevel(atm.nx, atm.ny, atm.nz, atm.dx, atm.dy, np.asarray(atm.z, float),
+                       np.asarray(atm.T, float), np.asarray(atm.n_tot, float),
+                       np.asarray(atm.chi_c, float), np.asarray(atm.c, float),
+                       np.asarray(atm.saha, float))
+        self.levels = {n_grids: fine}
+        for k in range(n_grids - 1, 0, -1):
+            self.levels[k] = coarsen_ml_level(self.levels[k + 1])
+        # frequency points: (kind, transition index, abscissa, weight)
+        self.freqs = []
+        for ti, ln in enumerate(atom.lines):
+            x = np.linspace(-ln.x_max, ln.x_max, ln.n_freq) if ln.n_freq > 1 else np.zeros(1)
+            for xv, wv in zip(x, trapezoid_weights(x)):
+                self.freqs.append(("line", ti, float(xv), float(wv)))
+        for ti, ct in enumerate(atom.continua):
+            y = np.linspace(1.0, ct.y_max, ct.n_freq) if ct.n_freq > 1 else np.ones(1)
+            for yv, wv in zip(y, trapezoid_weights(y)):
+                self.freqs.append(("cont", ti, float(yv), float(wv)))
+        self.fs_count = {k: 0 for k in self.levels}
+        self.sweep_count = {k: 0 for k in self.levels}
+        self.negatives = 0
+
+    def planck_rho(self, rho, T):
+        return rho ** 3 / np.expm1(self.atom.theta_ref * rho / T)
+
+    def transition_terms(self, k: int, n):
+        """Per frequency: chi, S, sl, fl and the rate weights qa, qb, qe, all
+        [nfreq, nvox], plus the bottom intensity [nfreq, nx*ny]."""
+        lev = self.levels[k]
+        at = self.atom
+        T = lev.T.reshape(-1)
+        nvox = T.size
+        nf = len(self.freqs)
+        out = {key: np.empty((nf, nvox)) for key in ("chi", "S", "sl", "fl", "qa", "qb", "qe")}
+        Ib = np.empty((nf, lev.nx * lev.ny))
+        chi_c = lev.chi_c.reshape(-1)
+        nn = n.reshape(self.N, -1)
+        # line profile normalisation per node and line
+        d = np.sqrt(T / at.t_ref)
+        norm = {}
+        for (kind, ti, xv, wv) in self.freqs:
+            if kind == "line":
+                phi = np.exp(-(xv / d) ** 2) / (math.sqrt(math.pi) * d)
+                norm[ti] = norm.get(ti, 0.0) + wv * phi
+        for f, (kind, ti, xv, wv) in enumerate(self.freqs):
+            if kind == "line":
+                ln = at.lines[ti]
+                lo, up = ln.lower, ln.upper
+                phi = np.exp(-(xv / d) ** 2) / (math.sqrt(math.pi) * d)
+                gr = at.g[up] / at.g[lo]
+                a = ln.kappa * gr * phi
+                b = ln.kappa * phi
+                e = ln.kappa * ln.rho ** 3 * phi
+                B = self.planck_rho(ln.rho, T)
+                wphi = wv * phi / norm[ti]
+                b_ul = ln.a_ul / ln.rho ** 3
+                out["qa"][f] = gr * b_ul * wphi
+                out["qb"][f] = b_ul * wphi
+                out["qe"][f] = ln.a_ul * wphi
+                Ib[f] = self.planck_rho(ln.rho, lev.T[0].reshape(-1))
+            else:
+                ct = at.continua[ti]
+                lo, up = ct.lower, self.N - 1
+                G = lev.saha[lo].reshape(-1)
+                E = np.exp(-at.theta_ref * ct.rho * xv / T)
+                alpha = xv ** -3
+                a = ct.kappa * alpha * np.ones_like(T)
+                b = ct.kappa * alpha * G * E
+                e = b * (ct.rho * xv) ** 3
+                B = self.planck_rho(ct.rho * xv, T)
+                qa = ct.beta * wv * xv ** -4
+                out["qa"][f] = qa
+                out["qb"][f] = qa * G * E
+                out["qe"][f] = qa * G * E * (ct.rho * xv) ** 3
+                Ib[f] = self.planck_rho(ct.rho * xv, lev.T[0].reshape(-1))
+            chi_t = nn[lo] * a - nn[up] * b
+            eta_t = nn[up] * e
+            chi = chi_t + chi_c
+            out["chi"][f] = chi
+            out["S"][f] = (eta_t + chi_c * B) / chi
+            out["sl"][f] = eta_t / chi
+            out["fl"][f] = chi_t / chi
+        return out, Ib
+
+    def formal_solution(self, k: int, n):
+        """Per-frequency (Jx, Ux) [nfreq, nz, ny, nx] and the rate weights."""
+        lev = self.levels[k]
+        terms, Ib = self.transition_terms(k, n)
+        nf = len(self.freqs)
+        shp = (nf,) + lev.shape
+        Jx, Ux = formal_solution_nu_raw(lev.z, lev.dx, lev.dy, self.mu, self.wray,
+                                        terms["chi"].reshape(shp), terms["S"].reshape(shp),
+                                        terms["sl"].reshape(shp), terms["fl"].reshape(shp),
+                                        Ib.reshape((nf, lev.ny, lev.nx)), 0.0)
+        self.fs_count[k] += 1
+        return Jx.reshape(nf, -1), Ux.reshape(nf, -1), terms
+
+    def rate_matrix_from(self, k: int, Jx, Ux, terms):
+        """M [nvox, N, N] with W(n) = M n: row 0 particle conservation (Eq. 3),
+        row i the rate equation of level i in the sign convention of Eq. 2."""
+        lev = self.levels[k]
+        N = self.N
+        nvox = lev.nx * lev.ny * lev.nz
+        P = lev.c.reshape(N, N, nvox).copy()
+        for f, (kind, ti, xv, wv) in enumerate(self.freqs):
+            if kind == "line":
+                lo, up = self.atom.lines[ti].lower, self.atom.lines[ti].upper
+            else:
+                lo, up = self.atom.continua[ti].lower, N - 1
+            P[lo, up] += terms["qa"][f] * Jx[f]
+            P[up, lo] += terms["qe"][f] * Ux[f] + terms["qb"][f] * Jx[f]
+        M = np.zeros((nvox, N, N))
+        M[:, 0, :] = 1.0
+        for i in range(1, N):
+            for j in range(N):
+                if j == i:
+                    M[:, i, i] = sum(P[i, jj] for jj in range(N) if jj != i)
+                else:
+                    M[:, i, j] = -P[j, i]
+        return M
+
+    def default_rhs(self, k: int):
+        lev = self.levels[k]
+        f = np.zeros((self.N,) + lev.shape)
+        f[0] = lev.n_tot
+        return f
+
+    def W(self, k: int, n):
+        Jx, Ux, terms = self.formal_solution(k, n)
+        return self.apply(self.rate_matrix_from(k, Jx, Ux, terms), n)
+
+    def zero_radiation(self, k: int):
+        """Statistical equilibrium with J = 0 (Sec. 4.9): Jx = 0, Ux = 1."""
+        lev = self.levels[k]
+        nvox = lev.nx * lev.ny * lev.nz
+        nf = len(self.freqs)
+        n_any = np.ones((self.N,) + lev.shape)   # weights do not depend on n
+        terms, _ = self.transition_terms(k, n_any)
+        M = self.rate_matrix_from(k, np.zeros((nf, nvox)), np.ones((nf, nvox)), terms)
+        return self.solve(M, self.default_rhs(k))
+
+    def mali_sweep(self, k: int, n, f=None):
+        if f is None:
+            f = self.default_rhs(k)
+        Jx, Ux, terms = self.formal_solution(k, n)
+        n_new = self.solve(self.rate_matrix_from(k, Jx, Ux, terms), f)
+        self.sweep_count[k] += 1
+        return n_new, max_rel_change(n_new, n)
+
+    def lte_populations(self, k: int):
+        """Saha-Boltzmann populations of the level's atmosphere (for checks)."""
+        lev = self.levels[k]
+        at = self.atom
+        N = self.N
+        rel = np.empty((N,) + lev.shape)
+        rel[0] = 1.0
+        for i in range(1, N - 1):
+            rel[i] = at.g[i] / at.g[0] * np.exp(-(at.theta[i] - at.theta[0]) / lev.T)
+        rel[N - 1] = 1.0 / lev.saha[0]          # n_c*/n_0*
+        return rel / rel.sum(axis=0) * lev.n_tot

@@ -170,3 +170,169 @@ def box_64x64x129_lognormal(seed: int = 1):
 
 def zero_populations_like(atm: Atmosphere, n_levels: int = 2):
     return np.zeros((n_levels,) + atm.shape)
+
+
+# ---------------------------------------------------------------------------
+# Multi-level atom (hydrogen-like, seeded) and a chromosphere-like atmosphere
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Line:
+    lower: int
+    upper: int
+    rho: float          # nu / nu_ref
+    a_ul: float         # Einstein A (rate units)
+    kappa: float        # opacity per unit (n_l g_u/g_l - n_u) at unit profile
+    n_freq: int
+    x_max: float        # half width in reference Doppler widths
+
+
+@dataclasses.dataclass
+class Continuum:
+    lower: int          # bound level; the upper level is the continuum level
+    rho: float          # threshold nu / nu_ref
+    beta: float         # photoionisation rate per unit J at threshold (rate units)
+    kappa: float        # opacity per unit population at threshold (1/length)
+    n_freq: int
+    y_max: float        # frequencies nu/nu_threshold in [1, y_max]
+
+
+@dataclasses.dataclass
+class MultiLevelAtom:
+    """N levels (the last may be a continuum), lines and bound-free continua.
+
+    theta[i] is the energy of level i over k (K), measured from level 0;
+    theta_ref = h nu_ref / k.  Intensities are in units of 2 h nu_ref^3/c^2,
+    so B_ul = A_ul / rho^3 and B_lu = (g_u/g_l) B_ul for a line.
+    """
+    g: np.ndarray
+    theta: np.ndarray
+    theta_ref: float
+    lines: list
+    continua: list
+    t_ref: float = 5000.0   # Doppler widths scale as sqrt(T / t_ref)
+
+    @property
+    def n_levels(self):
+        return len(self.g)
+
+
+@dataclasses.dataclass
+class MultiLevelAtmosphere:
+    """Cartesian atmosphere for a multi-level atom; arrays [nz][ny][nx].
+
+    c[i, j] is the collisional rate from level i to level j (i != j);
+    saha[i] is the LTE ratio n_i*/n_c* of bound level i to the continuum
+    level (used by bound-free transitions); chi_c is the grey background
+    opacity, whose source function is the Planck function.
+    """
+    nx: int
+    ny: int
+    nz: int
+    dx: float
+    dy: float
+    z: np.ndarray
+    T: np.ndarray
+    n_tot: np.ndarray
+    chi_c: np.ndarray
+    c: np.ndarray        # [N, N, nz, ny, nx]
+    saha: np.ndarray     # [N, nz, ny, nx] (0 for levels without a continuum)
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+
+def hydrogen_like_atom(n_bound: int = 5, line_freq: int = 100, cont_freq: int = 20,
+                       seed: int = 2, theta_ref: float = 40000.0, x_max: float = 4.0,
+                       y_max: float = 2.5, kappa_line: float = 10.0,
+                       kappa_cont: float = 1e-3, beta_cont: float = 0.05,
+                       jitter: float = 0.2) -> MultiLevelAtom:
+    """A seeded hydrogen-like atom: n_bound bound levels plus a continuum.
+
+    Level n (1-based) has g = 2 n^2 and energy theta_ref (1 - 1/n^2)/(3/4)
+    (so that the 1-2 line has h nu/k = theta_ref); the continuum sits at
+    theta_ref/(3/4).  Lines 1-2, 2-3, ..., (n_bound-1)-n_bound and 1-3 with
+    Kramers-like oscillator strengths; one bound-free continuum per bound
+    level with a nu^-3 cross-section.  Strengths carry a seeded +-jitter.
+    """
+    rng = np.random.default_rng(seed)
+    nl = n_bound + 1
+    n = np.arange(1, n_bound + 1, dtype=np.float64)
+    g = np.r_[2.0 * n * n, 1.0]
+    theta_ion = theta_ref / 0.75
+    theta = np.r_[theta_ion * (1.0 - 1.0 / (n * n)), theta_ion]
+
+    def jit():
+        return 1.0 + jitter * (2.0 * rng.random() - 1.0)
+
+    pairs = [(i, i + 1) for i in range(n_bound - 1)] + ([(0, 2)] if n_bound >= 3 else [])
+
+    def kramers_f(nlo, nup):
+        # Kramers' oscillator strength ~ 1/(l^5 u^3 (1/l^2 - 1/u^2)^3), scaled to
+        # the hydrogen Lyman-alpha value 0.4162 for the 1-2 line
+        raw = lambda a, b: 1.0 / (a ** 5 * b ** 3 * (1.0 / a ** 2 - 1.0 / b ** 2) ** 3)
+        return 0.4162 * raw(nlo, nup) / raw(1.0, 2.0)
+
+    f12 = kramers_f(1.0, 2.0)
+    lines = []
+    for (lo, up) in pairs:
+        nlo, nup = lo + 1.0, up + 1.0
+        rho = (1.0 / nlo ** 2 - 1.0 / nup ** 2) / 0.75
+        f_lu = kramers_f(nlo, nup)
+        # A_ul ~ f_lu (g_l/g_u) nu^2, in units where the 1-2 line has A = 1
+        a_ul = (f_lu / f12) * (g[lo] / g[up]) / (g[0] / g[1]) * rho ** 2
+        lines.append(Line(lo, up, rho, a_ul * jit(), kappa_line * (f_lu / f12) * jit(),
+                          line_freq, x_max))
+    continua = []
+    for lo in range(n_bound):
+        rho = (theta_ion - theta[lo]) / theta_ref
+        continua.append(Continuum(lo, rho, beta_cont * (lo + 1) * jit(),
+                                  kappa_cont * (lo + 1) * jit(), cont_freq, y_max))
+    return MultiLevelAtom(g=g, theta=theta, theta_ref=theta_ref, lines=lines,
+                          continua=continua)
+
+
+def chromosphere(nx: int, ny: int, nz: int, atom: MultiLevelAtom, seed: int = 2,
+                 t_min: float = 4000.0, t_max: float = 10000.0, scale_heights: float = 8.0,
+                 n_bottom: float = 1e4, sigma_t: float = 0.1, ionisation: float = 1e-3,
+                 saha_scale: float = 10.0, c_strength: float = 1e-3, chi_c0: float = 1e-2,
+                 dx: float = 1.0, z=None) -> MultiLevelAtmosphere:
+    """Chromosphere-like box: T rises from t_min to t_max with height (with
+    seeded 3D perturbations of relative size sigma_t), the density falls by
+    e^scale_heights from bottom to top; electron density = ionisation x
+    density; collisional rates from a van Regemorter-like n_e T^-1/2 law with
+    seeded strengths and detailed balance; Saha-like LTE ratios
+    saha_i = saha_scale n_e T^-3/2 (g_i/g_c) exp(theta_ion_i / T)."""
+    rng = np.random.default_rng(seed)
+    if z is None:
+        z = np.arange(nz, dtype=np.float64) * dx
+    z = np.asarray(z, dtype=np.float64)
+    h = (z - z[0]) / (z[-1] - z[0])
+    T1 = t_min + (t_max - t_min) * h ** 2
+    G = gaussian_random_field((nz, ny, nx), seed)
+    T = T1[:, None, None] * (1.0 + sigma_t * np.tanh(G))
+    rho = n_bottom * np.exp(-scale_heights * h)
+    n_tot = np.broadcast_to(rho[:, None, None], (nz, ny, nx)).copy()
+    n_e = ionisation * n_tot * (T / t_min)
+    chi_c = chi_c0 * n_tot / n_bottom * (T / t_min) ** 2
+    N = atom.n_levels
+    c = np.zeros((N, N, nz, ny, nx))
+    cont = N - 1
+    saha = np.zeros((N, nz, ny, nx))
+    for i in range(N - 1):
+        th_ion = atom.theta[cont] - atom.theta[i]
+        saha[i] = saha_scale * n_e * T ** -1.5 * (atom.g[i] / atom.g[cont]) * np.exp(th_ion / T)
+    for i in range(N):
+        for j in range(i + 1, N):
+            s = c_strength * (1.0 + 0.2 * (2.0 * rng.random() - 1.0)) / (1.0 + (j - i))
+            down = s * n_e * (T / 5000.0) ** -0.5          # j -> i
+            if j == cont:
+                # detailed balance with the LTE ratio n_i*/n_c* = saha_i
+                up = down / saha[i]
+            else:
+                up = down * (atom.g[j] / atom.g[i]) * np.exp(-(atom.theta[j] - atom.theta[i]) / T)
+            c[j, i] = down
+            c[i, j] = up
+    return MultiLevelAtmosphere(nx=nx, ny=ny, nz=nz, dx=dx, dy=dx, z=z, T=T, n_tot=n_tot,
+                                chi_c=chi_c, c=c, saha=saha)

@@ -1,0 +1,104 @@
+"""Pins of the multi-level oracle (lines, bound-free continua, background).
+
+* with one line, no continuum and no background it must reproduce the
+  two-level oracle (itself pinned to closed forms in test_oracle_pins.py);
+* with collisions dominating it must give Saha-Boltzmann populations;
+* with the radiation field set to the Planck function (and no local
+  operator) the radiative rates alone must be in detailed balance with the
+  Saha-Boltzmann populations, transition by transition;
+* particle conservation, the FAS fixed point, and MALI/FAS/FMG agreement.
+"""
+
+import math
+
+import numpy as np
+
+from oracle import mg3d_oracle as O
+from paper_1701_01607_gb300 import synth
+
+
+def ml_box(nx=8, nz=17, seed=2, **kw):
+    atom = synth.hydrogen_like_atom(line_freq=7, cont_freq=4, seed=seed)
+    atm = synth.chromosphere(nx, nx, nz, atom, seed=seed, **kw)
+    return atm, atom
+
+
+def test_ml_reduces_to_two_level():
+    atm2, atom2 = synth.stratified_two_level(8, 8, 17, eps=1e-2, sigma=0.3, seed=4)
+    line = synth.Line(0, 1, 1.0, atom2.a_ul, atom2.kappa, atom2.n_freq, atom2.x_max)
+    ml_atom = synth.MultiLevelAtom(g=np.array([1.0, 1.0]), theta=np.array([0.0, atom2.theta]),
+                                   theta_ref=atom2.theta, lines=[line], continua=[],
+                                   t_ref=5000.0)
+    c = np.zeros((2, 2) + atm2.shape)
+    c[1, 0] = atm2.c_ul
+    c[0, 1] = atm2.c_ul * np.exp(-atom2.theta / atm2.T)
+    ml_atm = synth.MultiLevelAtmosphere(atm2.nx, atm2.ny, atm2.nz, atm2.dx, atm2.dy, atm2.z,
+                                        atm2.T, atm2.n_tot, np.zeros(atm2.shape), c,
+                                        np.zeros((2,) + atm2.shape))
+    p2 = O.TwoLevelProblem(atm2, atom2)
+    pm = O.MultiLevelProblem(ml_atm, ml_atom)
+    n2 = p2.zero_radiation(1)
+    nm = pm.zero_radiation(1)
+    assert np.allclose(nm, n2, rtol=1e-13)
+    for _ in range(4):
+        n2, c2 = p2.mali_sweep(1, n2)
+        nm, cm = pm.mali_sweep(1, nm)
+    assert np.allclose(nm, n2, rtol=1e-12)
+    assert abs(cm - c2) < 1e-10
+
+
+def test_ml_lte_limit():
+    atm, atom = ml_box()
+    atm.c = atm.c * 1e12
+    p = O.MultiLevelProblem(atm, atom)
+    n = p.zero_radiation(1)
+    n, _ = p.mali_sweep(1, n)
+    lte = p.lte_populations(1)
+    assert np.allclose(n, lte, rtol=1e-9)
+
+
+def test_ml_radiative_detailed_balance():
+    atm, atom = ml_box(nx=2, nz=5)
+    atm.c[:] = 0.0
+    p = O.MultiLevelProblem(atm, atom)
+    lte = p.lte_populations(1)
+    terms, _ = p.transition_terms(1, lte)
+    nvox = atm.T.size
+    B = np.empty((len(p.freqs), nvox))
+    T = atm.T.reshape(-1)
+    for f, (kind, ti, xv, wv) in enumerate(p.freqs):
+        rho = atom.lines[ti].rho if kind == "line" else atom.continua[ti].rho * xv
+        B[f] = rho ** 3 / np.expm1(atom.theta_ref * rho / T)
+    M = p.rate_matrix_from(1, B, np.ones_like(B), terms)
+    W = p.apply(M, lte)
+    # rows 1..N-1 vanish; compare with the size of the individual rates
+    scale = np.abs(np.einsum("vij,jv->vi", np.abs(M), lte.reshape(p.N, -1))).T
+    assert np.max(np.abs(W[1:].reshape(p.N - 1, -1)) / scale[1:]) < 1e-12
+    assert np.allclose(W[0], atm.n_tot, rtol=1e-13)
+
+
+def test_ml_conservation_and_positivity():
+    atm, atom = ml_box()
+    p = O.MultiLevelProblem(atm, atom)
+    n = p.zero_radiation(1)
+    for _ in range(3):
+        n, _ = p.mali_sweep(1, n)
+        assert np.allclose(n.sum(axis=0), atm.n_tot, rtol=1e-13)
+        assert np.all(n > 0)
+
+
+def test_ml_fas_fixed_point_and_agreement():
+    atm, atom = ml_box(nx=8, nz=17)
+    # the first cycle needs pre-smoothing from the zero-radiation start, as
+    # the paper found for its hydrogen atom (nu0 >= 15, Table 1)
+    params = dict(nu_fmg=8, nu0=10, nu1=2, nu2=4, nu3=16)
+    p = O.MultiLevelProblem(atm, atom, n_grids=2)
+    n_mali, it = O.mali_solve(p, 1e-11)
+    n2, c2 = p.fas_cycle(n_mali, False, params)
+    assert c2 < 1e-9
+    p2 = O.MultiLevelProblem(atm, atom, n_grids=2)
+    n_fas, cyc = O.fas_solve(p2, 1e-10, params)
+    p3 = O.MultiLevelProblem(atm, atom, n_grids=2)
+    n_fmg, cyc3 = O.fmg_solve(p3, 1e-10, params)
+    assert O.max_rel_error(n_fas, n_mali) < 1e-8
+    assert O.max_rel_error(n_fmg, n_mali) < 1e-8
