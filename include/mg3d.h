@@ -10,15 +10,17 @@
  * diagonal approximate operator), FAS V-cycles (Sec. 2.2, Eqs. 5-11) and full
  * multigrid (Sec. 2.3) on one GPU.
  *
- * Model supported: a static two-level atom in complete redistribution with a
- * Doppler line profile sampled at n_freq points, no background continuum.
+ * Models supported: a static two-level atom in complete redistribution with a
+ * Doppler line profile sampled at n_freq points and no background continuum
+ * (mg3d_create, the fast path), and multi-level atoms with lines, bound-free
+ * continua and a grey background continuum (mg3d_create_ml).
  *
  * Conventions for every entry point:
  *  - returns MG3D_OK (0) or a negative MG3D_E_* code; no exception crosses the
  *    ABI; mg3d_last_error() then gives a message (per calling thread);
  *  - arrays are C-ordered: a field is [nz][ny][nx] (x fastest) and a set of
- *    populations is [2][nz][ny][nx] with index 0 the lower and 1 the upper
- *    level; z[0] is the bottom boundary plane;
+ *    populations is [n_levels][nz][ny][nx] (two-level atom: index 0 the lower
+ *    and 1 the upper level); z[0] is the bottom boundary plane;
  *  - pointers named *_host are host memory owned by the caller; the library
  *    reads them during the call (or writes them before returning) and keeps
  *    no reference.  All other state lives in device memory that the handle
@@ -151,7 +153,8 @@ int mg3d_set_stream(mg3d_handle *h, void *cuda_stream);
 /* Shape of a level's grid. */
 int mg3d_level_shape(const mg3d_handle *h, int level, int *nx, int *ny, int *nz);
 
-/* Copy a level's populations [2][nz][ny][nx] out to, or in from, host memory. */
+/* Copy a level's populations [n_levels][nz][ny][nx] out to, or in from, host
+ * memory. */
 int mg3d_get_populations(mg3d_handle *h, int level, double *n_host);
 int mg3d_set_populations(mg3d_handle *h, int level, const double *n_host);
 
@@ -174,7 +177,7 @@ int mg3d_formal_solve(mg3d_handle *h, int level, double *jeff_host, double *u_ho
 int mg3d_mali_sweep(mg3d_handle *h, int level, int n_sweeps, double *max_rel_change);
 
 /* Residual r = f - W_*(n) of a level (Eq. 5), with an extra formal solution
- * for the current populations; r_host is [2][nz][ny][nx]. */
+ * for the current populations; r_host is [n_levels][nz][ny][nx]. */
 int mg3d_residual(mg3d_handle *h, int level, double *r_host);
 
 /* One FAS V-cycle from the finest grid (Sec. 2.2).  is_first selects nu0
@@ -194,6 +197,87 @@ int mg3d_fas_solve(mg3d_handle *h, double tol, int max_cycles, mg3d_stats *stats
  * each finer grid with one V-cycle there, then V-cycles on the finest grid
  * until C(cycle) < tol. */
 int mg3d_fmg_solve(mg3d_handle *h, double tol, int max_cycles, mg3d_stats *stats);
+
+/* ------------------------------------------------------------------------
+ * Multi-level atoms (Sec. 3.2: the paper's 3- and 6-level Ca II and H I atoms;
+ * here any atom of 2..8 levels with lines and bound-free continua).
+ *
+ * Each frequency point belongs to one transition.  With a grey LTE background
+ * continuum chi_c (source function B_nu), the opacity and source function at
+ * a frequency of transition t (lower l, upper u) are
+ *   chi = chi_t + chi_c,   S = (eta_t + chi_c B_nu) / chi,
+ * line:        chi_t = kappa (n_l g_u/g_l - n_u) phi,  eta_t = kappa rho^3 n_u phi,
+ *              phi = exp(-(x/d)^2)/(sqrt(pi) d), d = sqrt(T/t_ref) (thermal
+ *              Doppler width relative to t_ref), B_nu taken at line centre;
+ * bound-free:  chi_t = kappa y^-3 (n_l - n_u G E),  eta_t = kappa y^-3 n_u G E (rho y)^3,
+ *              y = nu/nu_threshold, G = (n_l/n_u) in LTE (saha input), E = exp(-theta_ref rho y/T).
+ * Intensities are in units of 2 h nu_ref^3/c^2; B_nu = (nu/nu_ref)^3 /
+ * (exp(theta_ref (nu/nu_ref)/T) - 1).  MALI uses the diagonal-operator
+ * preconditioning of Rybicki & Hummer (1992): the transition's own share of
+ * S and of chi enters the local operator; rates for a line are
+ * P_lu = B_lu Jbar + C_lu, P_ul = A_ul Ubar + B_ul Jbar + C_ul (B_ul = A_ul/rho^3,
+ * B_lu = g_u/g_l B_ul), for a continuum (qa = beta w_y y^-4)
+ * P_lc = sum qa Jx + C_lc, P_cl = G sum qa E ((rho y)^3 Ux + Jx) + C_cl.
+ * The N x N system with row 0 replaced by conservation is solved by Gaussian
+ * elimination with partial pivoting.  The frequency grid of a line is n_freq
+ * equidistant offsets in [-x_max, x_max] (reference Doppler widths), of a
+ * continuum n_freq equidistant y in [1, y_max]; both with trapezoid weights,
+ * the line profile weights renormalised per node. */
+typedef struct {
+    int lower, upper;   /* level indices, lower < upper */
+    double rho;         /* nu / nu_ref */
+    double a_ul;        /* Einstein A (rate units) */
+    double kappa;       /* opacity coefficient at unit profile */
+    int n_freq;
+    double x_max;
+} mg3d_line;
+
+typedef struct {
+    int lower;          /* bound level; the upper level is the last level */
+    double rho;         /* threshold nu / nu_ref */
+    double beta;        /* photoionisation rate per unit J at threshold */
+    double kappa;       /* opacity per unit population at threshold */
+    int n_freq;
+    double y_max;       /* frequencies nu/nu_threshold in [1, y_max] */
+} mg3d_continuum;
+
+typedef struct {
+    int n_levels;                 /* 2..8; bound-free continua end on the last */
+    const double *g;              /* [n_levels] statistical weights */
+    const double *theta;          /* [n_levels] level energies / k (K), informative */
+    double theta_ref;             /* h nu_ref / k (K) */
+    double t_ref;                 /* temperature of the reference Doppler width */
+    int n_lines;
+    const mg3d_line *lines;
+    int n_continua;
+    const mg3d_continuum *continua;
+} mg3d_ml_atom;
+
+typedef struct {
+    int nx, ny, nz;
+    double dx, dy;
+    const double *z;        /* [nz] */
+    const double *T;        /* [nz][ny][nx] */
+    const double *n_tot;    /* [nz][ny][nx] */
+    const double *chi_c;    /* [nz][ny][nx] grey background opacity */
+    const double *c;        /* [N][N][nz][ny][nx] collisional rate from i to j (i != j) */
+    const double *saha;     /* [N][nz][ny][nx] LTE ratio (n_i/n_c) to the last level */
+} mg3d_ml_atmosphere;
+
+/* Create a solver for a multi-level atom; everything else as mg3d_create.
+ * Populations are [n_levels][nz][ny][nx] in every entry point. */
+int mg3d_create_ml(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
+                   const mg3d_quadrature *quad, const mg3d_params *params,
+                   mg3d_handle **out);
+
+/* Levels of the handle's atom and its number of frequency points. */
+int mg3d_n_levels(const mg3d_handle *h, int *n_levels, int *n_freq);
+
+/* One multi-level formal solution: per frequency and node the angle sums
+ * Jx = sum_r w_r (I - w0 S_t) and Ux = sum_r w_r (1 - w0 chi_t/chi), with S_t
+ * the transition's part of the source function; host outputs
+ * [n_freq][nz][ny][nx] (nullable).  MG3D_E_STATE on a two-level handle. */
+int mg3d_formal_solve_ml(mg3d_handle *h, int level, double *jx_host, double *ux_host);
 
 /* Grid-transfer operators on host arrays of ncomp fields, for checking.
  * mg3d_restrict: full weighting (Sec. 4.4) from level_fine to level_fine-1,

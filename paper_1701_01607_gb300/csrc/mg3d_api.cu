@@ -67,6 +67,13 @@ struct Level {
     void *chi0 = nullptr, *S = nullptr, *bbot = nullptr;
     StepGeom *geom = nullptr;    // [kRays][nz]
     SweepShape shape{};
+    // multi-level atom only
+    double *chi_c = nullptr;     // [nvox] background opacity
+    double *cmat = nullptr;      // [N][N][nvox] collisional rates
+    double *saha = nullptr;      // [N][nvox] LTE ratios to the continuum
+    void *mchi = nullptr, *mS = nullptr, *msl = nullptr, *mfl = nullptr;  // [nf][nvox]
+    void *mib = nullptr;         // [nf][nplane] bottom intensity
+    int ml_bands = 0, ml_rows = 0, ml_threads = 0;
 };
 
 struct TimedLaunch {
@@ -79,6 +86,16 @@ struct TimedLaunch {
 struct mg3d_handle {
     int L = 0;
     int prec = 0;
+    int kind = 0;                // 0: two-level atom, 1: multi-level atom
+    int N = 2;                   // levels of the atom
+    // multi-level atom
+    double theta_ref = 0, t_ref = 0;
+    int nfreq_ml = 0, ntrans = 0;
+    std::vector<FreqInfo> fi;
+    std::vector<TransInfo> ti;
+    FreqInfo *d_fi = nullptr;
+    TransInfo *d_ti = nullptr;
+    void *ml_jx = nullptr, *ml_ux = nullptr;  // [2][nf][finest nvox]
     mg3d_atom atom{};
     mg3d_params params{};
     double mu[kRays][3];
@@ -241,8 +258,9 @@ int dalloc(P **p, size_t count) {
 }
 
 void free_level(Level &L) {
-    void *ptrs[] = {L.T, L.n_tot, L.c_ul, L.c_lu, L.tz, L.n, L.f, L.n_before, L.r,
-                    L.chi0, L.S, L.bbot, L.geom};
+    void *ptrs[] = {L.T,     L.n_tot, L.c_ul, L.c_lu, L.tz,   L.n,    L.f,   L.n_before,
+                    L.r,     L.chi0,  L.S,    L.bbot, L.geom, L.chi_c, L.cmat, L.saha,
+                    L.mchi,  L.mS,    L.msl,  L.mfl,  L.mib};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     L = Level{};
@@ -273,8 +291,79 @@ cudaEvent_t pool_event(mg3d_handle *h) {
 
 // ------------------------------------------------------------- operations
 
+// Multi-level formal solution on level k: per-frequency angle sums per
+// hemisphere into ml_jx/ml_ux.
+int ml_formal_solution(mg3d_handle *h, int k) {
+    Level &L = h->lev[k];
+    MlOpacityArgs oa{L.nvox, h->nfreq_ml, h->N, h->prec, h->d_fi, h->theta_ref, h->t_ref,
+                     L.n, L.T, L.chi_c, L.saha, L.mchi, L.mS, L.msl, L.mfl};
+    MG_TRY(launched(h, launch_ml_opacity(oa, h->stream), "multi-level opacity"));
+    TimedLaunch tl{nullptr, nullptr, k};
+    if (h->timing) {
+        tl.a = pool_event(h);
+        tl.b = pool_event(h);
+        MG_CUDA(cudaEventRecord(tl.a, h->stream));
+    }
+    cudaError_t e;
+    if (h->prec == MG3D_PREC_F64) {
+        MlSweepArgs<double> a{L.nx, L.ny, L.nz, h->nfreq_ml, L.ml_rows,
+                              (const double *)L.mchi, (const double *)L.mS,
+                              (const double *)L.msl, (const double *)L.mfl,
+                              (const double *)L.mib, L.geom, h->d_exp_tab, h->exp_l1, h->exp_l2,
+                              (double *)h->ml_jx, (double *)h->ml_ux};
+        e = launch_ml_sweep_f64(a, L.ml_bands, L.ml_threads, h->stream);
+    } else {
+        MlSweepArgs<float> a{L.nx, L.ny, L.nz, h->nfreq_ml, L.ml_rows,
+                             (const float *)L.mchi, (const float *)L.mS,
+                             (const float *)L.msl, (const float *)L.mfl,
+                             (const float *)L.mib, L.geom, h->d_exp_tab, h->exp_l1, h->exp_l2,
+                             (float *)h->ml_jx, (float *)h->ml_ux};
+        e = launch_ml_sweep_f32(a, L.ml_bands, L.ml_threads, h->stream);
+    }
+    MG_TRY(launched(h, e, "multi-level sweep"));
+    if (h->timing) {
+        MG_CUDA(cudaEventRecord(tl.b, h->stream));
+        h->timed.push_back(tl);
+    }
+    const double units = (double)L.nvox * kRays * h->nfreq_ml;
+    ++h->fs_launches;
+    h->fs_units += units;
+    ++h->level_launches[k];
+    h->level_units[k] += units;
+    ++h->fss[k];
+    return MG3D_OK;
+}
+
+MlRateArgs ml_rate_args(mg3d_handle *h, int k, int mode) {
+    Level &L = h->lev[k];
+    MlRateArgs a{};
+    a.nvox = L.nvox;
+    a.nfreq = h->nfreq_ml;
+    a.n_levels = h->N;
+    a.n_trans = h->ntrans;
+    a.prec = h->prec;
+    a.fi = h->d_fi;
+    a.ti = h->d_ti;
+    a.jx = h->ml_jx;
+    a.ux = h->ml_ux;
+    a.zero_radiation = 0;
+    a.theta_ref = h->theta_ref;
+    a.t_ref = h->t_ref;
+    a.T = L.T;
+    a.c = L.cmat;
+    a.saha = L.saha;
+    a.n_tot = L.n_tot;
+    a.f = L.f_default ? nullptr : L.f;
+    a.n = L.n;
+    a.out = nullptr;
+    a.mode = mode;
+    a.scal = h->scal;
+    return a;
+}
+
 // Formal solution on level k with its populations: partial sums into pj/pu.
 int formal_solution(mg3d_handle *h, int k) {
+    if (h->kind == 1) return ml_formal_solution(h, k);
     Level &L = h->lev[k];
     MG_TRY(launched(h, launch_opacity(h->prec, L.nvox, h->atom.g_ratio, h->atom.kappa, L.n,
                                       L.chi0, L.S, h->stream),
@@ -340,8 +429,13 @@ RateArgs rate_args(mg3d_handle *h, int k, int mode) {
 
 int sweep(mg3d_handle *h, int k) {
     MG_TRY(formal_solution(h, k));
-    RateArgs a = rate_args(h, k, kRateSolve);
-    MG_TRY(launched(h, launch_rates(a, h->stream), "rates"));
+    if (h->kind == 1) {
+        MlRateArgs a = ml_rate_args(h, k, kRateSolve);
+        MG_TRY(launched(h, launch_ml_rates(a, h->stream), "multi-level rates"));
+    } else {
+        RateArgs a = rate_args(h, k, kRateSolve);
+        MG_TRY(launched(h, launch_rates(a, h->stream), "rates"));
+    }
     ++h->sweeps[k];
     return MG3D_OK;
 }
@@ -366,6 +460,13 @@ int read_scalars(mg3d_handle *h, double *C, long long *neg, long long *bad) {
 int zero_radiation(mg3d_handle *h, int k) {
     Level &L = h->lev[k];
     L.f_default = true;
+    if (h->kind == 1) {
+        MlRateArgs a = ml_rate_args(h, k, kRateSolve);
+        a.zero_radiation = 1;
+        a.scal = nullptr;
+        MG_TRY(launched(h, launch_ml_rates(a, h->stream), "zero radiation"));
+        return MG3D_OK;
+    }
     RateArgs a = rate_args(h, k, kRateSolve);
     a.zero_radiation = 1;
     a.scal = nullptr;
@@ -376,6 +477,13 @@ int zero_radiation(mg3d_handle *h, int k) {
 // out <- f - W(n) (mode residual) or out += W(n) (mode add), one extra FS.
 int apply_W(mg3d_handle *h, int k, int mode, double *out) {
     MG_TRY(formal_solution(h, k));
+    if (h->kind == 1) {
+        MlRateArgs a = ml_rate_args(h, k, mode);
+        a.out = out;
+        a.scal = nullptr;
+        MG_TRY(launched(h, launch_ml_rates(a, h->stream), "multi-level residual"));
+        return MG3D_OK;
+    }
     RateArgs a = rate_args(h, k, mode);
     a.out = out;
     a.scal = nullptr;
@@ -391,10 +499,12 @@ int vcycle(mg3d_handle *h, int k, bool first) {
     // residual with an extra formal solution (Eq. 5)
     MG_TRY(apply_W(h, k, kRateResidual, F.r));
     // coarse-grid equation (Eq. 9)
-    MG_TRY(launched(h, launch_restrict(2, F.nx, F.ny, F.nz, F.n, C.n, h->stream), "restrict n"));
-    MG_CUDA(cudaMemcpyAsync(C.n_before, C.n, 2 * C.nvox * sizeof(double),
+    MG_TRY(launched(h, launch_restrict(h->N, F.nx, F.ny, F.nz, F.n, C.n, h->stream),
+                    "restrict n"));
+    MG_CUDA(cudaMemcpyAsync(C.n_before, C.n, (size_t)h->N * C.nvox * sizeof(double),
                             cudaMemcpyDeviceToDevice, h->stream));
-    MG_TRY(launched(h, launch_restrict(2, F.nx, F.ny, F.nz, F.r, C.f, h->stream), "restrict r"));
+    MG_TRY(launched(h, launch_restrict(h->N, F.nx, F.ny, F.nz, F.r, C.f, h->stream),
+                    "restrict r"));
     C.f_default = false;
     MG_TRY(apply_W(h, k - 1, kRateAddW, C.f));
     if (k - 1 == 1) {
@@ -403,7 +513,7 @@ int vcycle(mg3d_handle *h, int k, bool first) {
         MG_TRY(vcycle(h, k - 1, false));
     }
     // relative correction, interpolated (Eqs. 10-11), 10 % rule (Sec. 4.8)
-    MG_TRY(launched(h, launch_prolong_correct(C.nx, C.ny, C.nz, F.tz, C.n, C.n_before, F.n,
+    MG_TRY(launched(h, launch_prolong_correct(h->N, C.nx, C.ny, C.nz, F.tz, C.n, C.n_before, F.n,
                                               h->scal, h->stream),
                     "prolong correction"));
     for (int i = 0; i < h->params.nu2; ++i) MG_TRY(sweep(h, k));
@@ -414,7 +524,7 @@ int vcycle(mg3d_handle *h, int k, bool first) {
 int fas_cycle(mg3d_handle *h, bool first, double *C, long long *neg) {
     Level &F = h->lev[h->L];
     if (h->L < 2) return fail(MG3D_E_STATE, "a V-cycle needs n_grids >= 2");
-    MG_CUDA(cudaMemcpyAsync(h->scratch, F.n, 2 * F.nvox * sizeof(double),
+    MG_CUDA(cudaMemcpyAsync(h->scratch, F.n, (size_t)h->N * F.nvox * sizeof(double),
                             cudaMemcpyDeviceToDevice, h->stream));
     F.f_default = true;
     MG_TRY(reset_scalars(h));
@@ -422,7 +532,8 @@ int fas_cycle(mg3d_handle *h, bool first, double *C, long long *neg) {
     long long neg_in_cycle = 0;
     MG_TRY(read_scalars(h, nullptr, &neg_in_cycle, nullptr));
     MG_TRY(reset_scalars(h));
-    MG_TRY(launched(h, launch_max_rel_change(2 * F.nvox, F.n, h->scratch, h->scal, h->stream),
+    MG_TRY(launched(h, launch_max_rel_change((long)h->N * F.nvox, F.n, h->scratch, h->scal,
+                                             h->stream),
                     "max rel change"));
     long long bad = 0;
     MG_TRY(read_scalars(h, C, nullptr, &bad));
@@ -730,6 +841,198 @@ int create_impl(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_qu
     return MG3D_OK;
 }
 
+// Equidistant points on [a, b] (the last one exactly b) and trapezoid weights.
+void trapezoid_grid(double a, double b, int n, std::vector<double> &x, std::vector<double> &w) {
+    x.assign(n, a);
+    w.assign(n, n == 1 ? 1.0 : 0.0);
+    if (n == 1) return;
+    const double step = (b - a) / (n - 1);
+    for (int i = 0; i < n; ++i) x[i] = i == n - 1 ? b : a + i * step;
+    for (int i = 0; i + 1 < n; ++i) {
+        const double d = x[i + 1] - x[i];
+        w[i] += 0.5 * d;
+        w[i + 1] += 0.5 * d;
+    }
+}
+
+int create_ml_impl(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
+                   const mg3d_quadrature *quad, const mg3d_params *params, mg3d_handle *h) {
+    h->kind = 1;
+    h->N = atom->n_levels;
+    h->L = params->n_grids;
+    h->prec = params->fs_prec;
+    h->params = *params;
+    h->theta_ref = atom->theta_ref;
+    h->t_ref = atom->t_ref;
+    build_quadrature(h, quad ? quad->a : 0.0);
+    const int N = h->N;
+    // frequency table: lines, then continua, each transition contiguous
+    for (int t = 0; t < atom->n_lines; ++t) {
+        const mg3d_line &ln = atom->lines[t];
+        std::vector<double> x, w;
+        trapezoid_grid(-ln.x_max, ln.x_max, ln.n_freq, x, w);
+        if (ln.n_freq == 1) x[0] = 0.0;
+        TransInfo tr{0, ln.lower, ln.upper, (int)h->fi.size(), 0, ln.rho, ln.a_ul,
+                     atom->g[ln.upper] / atom->g[ln.lower]};
+        for (int i = 0; i < ln.n_freq; ++i)
+            h->fi.push_back(FreqInfo{0, ln.lower, ln.upper, x[i], w[i], ln.rho, ln.kappa, tr.gr});
+        tr.f_end = (int)h->fi.size();
+        h->ti.push_back(tr);
+    }
+    for (int t = 0; t < atom->n_continua; ++t) {
+        const mg3d_continuum &ct = atom->continua[t];
+        std::vector<double> y, w;
+        trapezoid_grid(1.0, ct.y_max, ct.n_freq, y, w);
+        if (ct.n_freq == 1) y[0] = 1.0;
+        TransInfo tr{1, ct.lower, N - 1, (int)h->fi.size(), 0, ct.rho, ct.beta, 1.0};
+        for (int i = 0; i < ct.n_freq; ++i)
+            h->fi.push_back(FreqInfo{1, ct.lower, N - 1, y[i], w[i], ct.rho, ct.kappa, 1.0});
+        tr.f_end = (int)h->fi.size();
+        h->ti.push_back(tr);
+    }
+    h->nfreq_ml = (int)h->fi.size();
+    h->ntrans = (int)h->ti.size();
+    MG_CUDA(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
+    h->stream = h->own_stream;
+    const size_t es = elem_size(h->prec);
+    const int nf = h->nfreq_ml;
+    for (int k = h->L; k >= 1; --k) {
+        Level &L = h->lev[k];
+        if (k == h->L) {
+            L.nx = atm->nx;
+            L.ny = atm->ny;
+            L.nz = atm->nz;
+            L.dx = atm->dx;
+            L.dy = atm->dy;
+            L.z.assign(atm->z, atm->z + atm->nz);
+        } else {
+            const Level &Fn = h->lev[k + 1];
+            L.nx = Fn.nx / 2;
+            L.ny = Fn.ny / 2;
+            L.nz = (Fn.nz + 1) / 2;
+            L.dx = 2 * Fn.dx;
+            L.dy = 2 * Fn.dy;
+            L.z.clear();
+            for (int i = 0; i < Fn.nz; i += 2) L.z.push_back(Fn.z[i]);
+        }
+        L.nplane = (long)L.nx * L.ny;
+        L.nvox = L.nplane * L.nz;
+        MG_TRY(dalloc(&L.T, L.nvox));
+        MG_TRY(dalloc(&L.n_tot, L.nvox));
+        MG_TRY(dalloc(&L.chi_c, L.nvox));
+        MG_TRY(dalloc(&L.cmat, (size_t)N * N * L.nvox));
+        MG_TRY(dalloc(&L.saha, (size_t)N * L.nvox));
+        MG_TRY(dalloc(&L.tz, L.nz));
+        MG_TRY(dalloc(&L.n, (size_t)N * L.nvox));
+        MG_TRY(dalloc(&L.f, (size_t)N * L.nvox));
+        MG_TRY(dalloc(&L.n_before, (size_t)N * L.nvox));
+        MG_TRY(dalloc(&L.r, (size_t)N * L.nvox));
+        MG_TRY(dev_alloc(&L.mchi, (size_t)nf * L.nvox * es));
+        MG_TRY(dev_alloc(&L.mS, (size_t)nf * L.nvox * es));
+        MG_TRY(dev_alloc(&L.msl, (size_t)nf * L.nvox * es));
+        MG_TRY(dev_alloc(&L.mfl, (size_t)nf * L.nvox * es));
+        MG_TRY(dev_alloc(&L.mib, (size_t)nf * L.nplane * es));
+        MG_TRY(dalloc(&L.geom, (size_t)kRays * L.nz));
+        std::vector<double> tz(L.nz, 0.0);
+        for (int i = 1; i + 1 < L.nz; i += 2) tz[i] = (L.z[i] - L.z[i - 1]) / (L.z[i + 1] - L.z[i - 1]);
+        MG_CUDA(cudaMemcpy(L.tz, tz.data(), L.nz * sizeof(double), cudaMemcpyHostToDevice));
+        std::vector<StepGeom> g;
+        build_geometry(h, L, g);
+        MG_CUDA(cudaMemcpy(L.geom, g.data(), g.size() * sizeof(StepGeom), cudaMemcpyHostToDevice));
+        // bands: the fewest that fit in shared memory and give >= 300 blocks,
+        // else the most that fit
+        int pick = 0;
+        for (int b = 1; b <= kMaxBands && b <= L.ny; ++b) {
+            const int rows = (L.ny + b - 1) / b;
+            if ((long)(b - 1) * rows >= L.ny) continue;
+            if (ml_sweep_smem_bytes(h->prec, rows, L.nx) > kMaxSweepSmem) continue;
+            pick = b;
+            if (2L * nf * b >= 300) break;
+        }
+        if (pick == 0) return fail(MG3D_E_ARG, "plane too large for the multi-level sweep");
+        L.ml_bands = pick;
+        L.ml_rows = (L.ny + pick - 1) / pick;
+        const int th = threads_for_band(L.ml_rows * L.nx);
+        L.ml_threads = th > 256 ? 256 : th;
+    }
+    Level &F = h->lev[h->L];
+    const size_t nfld = 3 + (size_t)N * N + N;   // T, n_tot, chi_c, c, saha
+    MG_CUDA(cudaMemcpy(F.T, atm->T, F.nvox * 8, cudaMemcpyHostToDevice));
+    MG_CUDA(cudaMemcpy(F.n_tot, atm->n_tot, F.nvox * 8, cudaMemcpyHostToDevice));
+    MG_CUDA(cudaMemcpy(F.chi_c, atm->chi_c, F.nvox * 8, cudaMemcpyHostToDevice));
+    MG_CUDA(cudaMemcpy(F.cmat, atm->c, (size_t)N * N * F.nvox * 8, cudaMemcpyHostToDevice));
+    MG_CUDA(cudaMemcpy(F.saha, atm->saha, (size_t)N * F.nvox * 8, cudaMemcpyHostToDevice));
+    const size_t scratch_fields = std::max<size_t>(4, (size_t)N + 2);
+    MG_TRY(dalloc(&h->scratch, scratch_fields * F.nvox));
+    if (h->L > 1) {
+        // full weighting of every atmospheric field, grid by grid (Sec. 4.7)
+        double *pack = nullptr;
+        MG_TRY(dalloc(&pack, nfld * (F.nvox + h->lev[h->L - 1].nvox)));
+        int rc = MG3D_OK;
+        for (int k = h->L; k >= 2 && rc == MG3D_OK; --k) {
+            Level &Fk = h->lev[k];
+            Level &Ck = h->lev[k - 1];
+            double *fine = pack, *coarse = pack + nfld * Fk.nvox;
+            const double *src[3] = {Fk.T, Fk.n_tot, Fk.chi_c};
+            cudaError_t e = cudaSuccess;
+            for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+                e = cudaMemcpyAsync(fine + i * Fk.nvox, src[i], Fk.nvox * 8,
+                                    cudaMemcpyDeviceToDevice, h->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(fine + 3 * Fk.nvox, Fk.cmat, (size_t)N * N * Fk.nvox * 8,
+                                    cudaMemcpyDeviceToDevice, h->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(fine + (3 + (size_t)N * N) * Fk.nvox, Fk.saha,
+                                    (size_t)N * Fk.nvox * 8, cudaMemcpyDeviceToDevice, h->stream);
+            if (e == cudaSuccess) {
+                rc = launched(h, launch_restrict((int)nfld, Fk.nx, Fk.ny, Fk.nz, fine, coarse,
+                                                 h->stream),
+                              "restrict atmosphere");
+                if (rc != MG3D_OK) break;
+            }
+            double *dst[3] = {Ck.T, Ck.n_tot, Ck.chi_c};
+            for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+                e = cudaMemcpyAsync(dst[i], coarse + i * Ck.nvox, Ck.nvox * 8,
+                                    cudaMemcpyDeviceToDevice, h->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(Ck.cmat, coarse + 3 * Ck.nvox, (size_t)N * N * Ck.nvox * 8,
+                                    cudaMemcpyDeviceToDevice, h->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(Ck.saha, coarse + (3 + (size_t)N * N) * Ck.nvox,
+                                    (size_t)N * Ck.nvox * 8, cudaMemcpyDeviceToDevice, h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+            if (e != cudaSuccess) rc = fail(MG3D_E_CUDA, std::string("coarsening: ") +
+                                                             cudaGetErrorString(e));
+        }
+        cudaFree(pack);
+        if (rc != MG3D_OK) return rc;
+    }
+    MG_TRY(dev_alloc((void **)&h->d_fi, h->fi.size() * sizeof(FreqInfo)));
+    MG_TRY(dev_alloc((void **)&h->d_ti, h->ti.size() * sizeof(TransInfo)));
+    MG_CUDA(cudaMemcpy(h->d_fi, h->fi.data(), h->fi.size() * sizeof(FreqInfo),
+                       cudaMemcpyHostToDevice));
+    MG_CUDA(cudaMemcpy(h->d_ti, h->ti.data(), h->ti.size() * sizeof(TransInfo),
+                       cudaMemcpyHostToDevice));
+    for (int k = 1; k <= h->L; ++k) {
+        Level &L = h->lev[k];
+        MG_TRY(launched(h, launch_ml_bottom(h->prec, L.nplane, nf, h->d_fi, h->theta_ref, L.T,
+                                            L.mib, h->stream),
+                        "bottom intensity"));
+    }
+    {
+        double tab[64];
+        exp_neg_constants(tab, &h->exp_l1, &h->exp_l2);
+        MG_TRY(dalloc(&h->d_exp_tab, 64));
+        MG_CUDA(cudaMemcpy(h->d_exp_tab, tab, sizeof(tab), cudaMemcpyHostToDevice));
+    }
+    MG_TRY(dev_alloc(&h->ml_jx, 2 * (size_t)nf * F.nvox * es));
+    MG_TRY(dev_alloc(&h->ml_ux, 2 * (size_t)nf * F.nvox * es));
+    MG_TRY(dalloc(&h->scal, 4));
+    for (int k = 1; k <= h->L; ++k) MG_TRY(zero_radiation(h, k));
+    MG_CUDA(cudaStreamSynchronize(h->stream));
+    return MG3D_OK;
+}
+
 }  // namespace
 
 namespace mg3d {
@@ -783,12 +1086,107 @@ int mg3d_create(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_qu
     return MG3D_OK;
 }
 
+int mg3d_create_ml(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
+                   const mg3d_quadrature *quad, const mg3d_params *params, mg3d_handle **out) {
+    if (!out) return fail(MG3D_E_ARG, "null output pointer");
+    *out = nullptr;
+    if (!atm || !atom || !params) return fail(MG3D_E_ARG, "null argument");
+    if (!atm->z || !atm->T || !atm->n_tot || !atm->chi_c || !atm->c || !atm->saha)
+        return fail(MG3D_E_ARG, "null atmosphere array");
+    const int N = atom->n_levels;
+    if (N < 2 || N > kMaxLevels || !atom->g || !atom->theta)
+        return fail(MG3D_E_ARG, "n_levels must be 2..8 with g and theta given");
+    if (!(atom->theta_ref > 0.0) || !(atom->t_ref > 0.0))
+        return fail(MG3D_E_ARG, "theta_ref and t_ref must be > 0");
+    if (atom->n_lines < 0 || atom->n_continua < 0 || atom->n_lines + atom->n_continua < 1 ||
+        (atom->n_lines && !atom->lines) || (atom->n_continua && !atom->continua))
+        return fail(MG3D_E_ARG, "no transitions");
+    long nf = 0;
+    for (int t = 0; t < atom->n_lines; ++t) {
+        const mg3d_line &ln = atom->lines[t];
+        if (ln.lower < 0 || ln.upper >= N || ln.lower >= ln.upper || ln.n_freq < 1 ||
+            !(ln.rho > 0) || !(ln.a_ul > 0) || !(ln.kappa >= 0) || !(ln.x_max >= 0))
+            return fail(MG3D_E_ARG, "bad line " + std::to_string(t));
+        nf += ln.n_freq;
+    }
+    for (int t = 0; t < atom->n_continua; ++t) {
+        const mg3d_continuum &ct = atom->continua[t];
+        if (ct.lower < 0 || ct.lower >= N - 1 || ct.n_freq < 1 || !(ct.rho > 0) ||
+            !(ct.beta >= 0) || !(ct.kappa >= 0) || !(ct.y_max >= 1.0))
+            return fail(MG3D_E_ARG, "bad continuum " + std::to_string(t));
+        nf += ct.n_freq;
+    }
+    if (nf > 65535) return fail(MG3D_E_ARG, "too many frequencies");
+    if (params->n_grids < 1 || params->n_grids > MG3D_MAX_GRIDS)
+        return fail(MG3D_E_ARG, "n_grids out of range");
+    if (params->fs_prec != MG3D_PREC_F64 && params->fs_prec != MG3D_PREC_F32)
+        return fail(MG3D_E_ARG, "fs_prec must be MG3D_PREC_F64 or MG3D_PREC_F32");
+    if (params->nu_fmg < 0 || params->nu0 < 0 || params->nu1 < 0 || params->nu2 < 0 ||
+        params->nu3 < 0)
+        return fail(MG3D_E_ARG, "negative iteration count");
+    if (atm->nx < 1 || atm->ny < 1 || atm->nz < 2) return fail(MG3D_E_ARG, "grid too small");
+    if (!(atm->dx > 0.0) || !(atm->dy > 0.0)) return fail(MG3D_E_ARG, "dx, dy must be > 0");
+    for (int k = 1; k < atm->nz; ++k)
+        if (!(atm->z[k] > atm->z[k - 1])) return fail(MG3D_E_ARG, "z must increase");
+    const long step = 1L << (params->n_grids - 1);
+    if ((atm->nz - 1) % step != 0 || atm->nx % step != 0 || atm->ny % step != 0)
+        return fail(MG3D_E_GRID, "grid does not coarsen n_grids - 1 times "
+                                 "(need nz = A 2^(l-1) + 1, nx, ny = B 2^(l-1))");
+    mg3d_handle *h = new (std::nothrow) mg3d_handle();
+    if (!h) return fail(MG3D_E_OOM, "host allocation failed");
+    int rc = create_ml_impl(atm, atom, quad, params, h);
+    if (rc != MG3D_OK) {
+        std::string msg = g_last_error;
+        mg3d_destroy(h);
+        g_last_error = msg;
+        return rc;
+    }
+    *out = h;
+    g_last_error.clear();
+    return MG3D_OK;
+}
+
+int mg3d_n_levels(const mg3d_handle *h, int *n_levels, int *n_freq) {
+    if (!h) return fail(MG3D_E_ARG, "null handle");
+    if (n_levels) *n_levels = h->N;
+    if (n_freq) *n_freq = h->kind == 1 ? h->nfreq_ml : h->atom.n_freq;
+    return MG3D_OK;
+}
+
+int mg3d_formal_solve_ml(mg3d_handle *h, int level, double *jx_host, double *ux_host) {
+    MG_TRY(check_level(h, level));
+    if (h->kind != 1) return fail(MG3D_E_STATE, "not a multi-level handle");
+    Level &L = h->lev[level];
+    MG_TRY(formal_solution(h, level));
+    MG_CUDA(cudaStreamSynchronize(h->stream));
+    const size_t cnt = (size_t)h->nfreq_ml * L.nvox;
+    const size_t es = elem_size(h->prec);
+    // both hemispheres of the per-frequency sums, added on the host
+    std::vector<unsigned char> hj(2 * cnt * es), hu(2 * cnt * es);
+    MG_CUDA(cudaMemcpy(hj.data(), h->ml_jx, 2 * cnt * es, cudaMemcpyDeviceToHost));
+    MG_CUDA(cudaMemcpy(hu.data(), h->ml_ux, 2 * cnt * es, cudaMemcpyDeviceToHost));
+    const size_t hs = (size_t)h->nfreq_ml * L.nvox;   // hemisphere stride of this level
+    for (size_t i = 0; i < cnt; ++i) {
+        double j0, j1, u0, u1;
+        if (h->prec == MG3D_PREC_F64) {
+            const double *J = (const double *)hj.data(), *U = (const double *)hu.data();
+            j0 = J[i]; j1 = J[hs + i]; u0 = U[i]; u1 = U[hs + i];
+        } else {
+            const float *J = (const float *)hj.data(), *U = (const float *)hu.data();
+            j0 = J[i]; j1 = J[hs + i]; u0 = U[i]; u1 = U[hs + i];
+        }
+        if (jx_host) jx_host[i] = j0 + j1;
+        if (ux_host) ux_host[i] = u0 + u1;
+    }
+    return MG3D_OK;
+}
+
 int mg3d_destroy(mg3d_handle *h) {
     if (!h) return MG3D_OK;
     if (h->stream) cudaStreamSynchronize(h->stream);
     for (int k = 0; k <= MG3D_MAX_GRIDS; ++k) free_level(h->lev[k]);
     void *ptrs[] = {h->d_phi, h->d_wphi, h->d_inv_phi, h->d_exp_tab, h->pj, h->pu, h->scal,
-                    h->scratch};
+                    h->scratch, h->d_fi, h->d_ti, h->ml_jx, h->ml_ux};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &t : h->timed) {
@@ -821,14 +1219,14 @@ int mg3d_get_populations(mg3d_handle *h, int level, double *n_host) {
     MG_TRY(check_level(h, level));
     if (!n_host) return fail(MG3D_E_ARG, "null buffer");
     Level &L = h->lev[level];
-    return level_to_host(h, n_host, L.n, 2 * L.nvox);
+    return level_to_host(h, n_host, L.n, (size_t)h->N * L.nvox);
 }
 
 int mg3d_set_populations(mg3d_handle *h, int level, const double *n_host) {
     MG_TRY(check_level(h, level));
     if (!n_host) return fail(MG3D_E_ARG, "null buffer");
     Level &L = h->lev[level];
-    return host_to_level(h, L.n, n_host, 2 * L.nvox);
+    return host_to_level(h, L.n, n_host, (size_t)h->N * L.nvox);
 }
 
 int mg3d_init_zero_radiation(mg3d_handle *h, int level) {
@@ -840,6 +1238,7 @@ int mg3d_init_zero_radiation(mg3d_handle *h, int level) {
 
 int mg3d_formal_solve(mg3d_handle *h, int level, double *jeff_host, double *u_host) {
     MG_TRY(check_level(h, level));
+    if (h->kind != 0) return fail(MG3D_E_STATE, "multi-level handle: use mg3d_formal_solve_ml");
     Level &L = h->lev[level];
     MG_TRY(formal_solution(h, level));
     RateArgs a = rate_args(h, level, kRateReduce);
@@ -874,7 +1273,7 @@ int mg3d_residual(mg3d_handle *h, int level, double *r_host) {
     if (!r_host) return fail(MG3D_E_ARG, "null buffer");
     Level &L = h->lev[level];
     MG_TRY(apply_W(h, level, kRateResidual, L.r));
-    return level_to_host(h, r_host, L.r, 2 * L.nvox);
+    return level_to_host(h, r_host, L.r, (size_t)h->N * L.nvox);
 }
 
 int mg3d_fas_vcycle(mg3d_handle *h, int is_first, double *max_rel_change) {
@@ -940,7 +1339,7 @@ int mg3d_fmg_solve(mg3d_handle *h, double tol, int max_cycles, mg3d_stats *stats
     for (int k = 2; k <= h->L; ++k) {
         Level &Fk = h->lev[k];
         Level &Ck = h->lev[k - 1];
-        MG_TRY(launched(h, launch_prolong(2, Ck.nx, Ck.ny, Ck.nz, Fk.tz, Ck.n, Fk.n, h->stream),
+        MG_TRY(launched(h, launch_prolong(h->N, Ck.nx, Ck.ny, Ck.nz, Fk.tz, Ck.n, Fk.n, h->stream),
                         "prolong full approximation"));
         Fk.f_default = true;
         if (k < h->L) {
@@ -1008,6 +1407,7 @@ int mg3d_prolong(mg3d_handle *h, int level_fine, int ncomp, const double *coarse
 
 int mg3d_set_fs_config(mg3d_handle *h, int level, int freq_per_block, int bands, int threads) {
     MG_TRY(check_level(h, level));
+    if (h->kind != 0) return fail(MG3D_E_STATE, "sweep shapes apply to two-level handles");
     SweepShape s;
     MG_TRY(make_shape(h, level, freq_per_block, bands, threads, &s));
     MG_CUDA(cudaStreamSynchronize(h->stream));
@@ -1021,7 +1421,7 @@ int mg3d_autotune(mg3d_handle *h, int level, int *evaluated, double *seconds) {
     if (level != 0) MG_TRY(check_level(h, level));
     auto t0 = std::chrono::steady_clock::now();
     int count = 0;
-    for (int k = 1; k <= h->L; ++k) {
+    for (int k = 1; k <= h->L && h->kind == 0; ++k) {
         if (level != 0 && k != level) continue;
         int c = 0;
         MG_TRY(autotune_level(h, k, &c));

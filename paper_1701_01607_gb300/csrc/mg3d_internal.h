@@ -95,11 +95,79 @@ cudaError_t launch_restrict(int ncomp, int nxf, int nyf, int nzf, const double *
                             double *coarse, cudaStream_t st);
 cudaError_t launch_prolong(int ncomp, int nxc, int nyc, int nzc, const double *tz,
                            const double *coarse, double *fine, cudaStream_t st);
-cudaError_t launch_prolong_correct(int nxc, int nyc, int nzc, const double *tz,
+cudaError_t launch_prolong_correct(int ncomp, int nxc, int nyc, int nzc, const double *tz,
                                    const double *n_after, const double *n_before,
                                    double *n_fine, unsigned long long *scal,
                                    cudaStream_t st);
 cudaError_t launch_max_rel_change(long len, const double *n_new, const double *n_old,
                                   unsigned long long *scal, cudaStream_t st);
+
+// ---------------------------------------------------------------- multi-level
+
+constexpr int kMaxLevels = 8;
+
+// One frequency point of a multi-level atom; each belongs to one transition.
+struct FreqInfo {
+    int kind;       // 0 line, 1 bound-free continuum
+    int lo, up;     // lower and upper level
+    double xy;      // line: offset in reference Doppler widths; continuum: nu/nu_threshold
+    double w;       // trapezoid weight in x or y
+    double rho;     // line: nu/nu_ref; continuum: threshold nu/nu_ref
+    double kappa;   // opacity coefficient
+    double gr;      // line: g_u/g_l (unused for continua)
+};
+
+// One transition: its frequencies are [f_begin, f_end) of the table.
+struct TransInfo {
+    int kind, lo, up, f_begin, f_end;
+    double rho;     // as in FreqInfo
+    double coef;    // line: A_ul; continuum: beta
+    double gr;      // line: g_u/g_l
+};
+
+template <typename T>
+struct MlSweepArgs {
+    int nx, ny, nz, nfreq, rows;
+    const T *chi, *S, *sl, *fl;   // [nfreq][nvox]
+    const T *ib;                  // [nfreq][nx*ny] intensity entering at the bottom
+    const StepGeom *geom;         // [kRays][nz]
+    const double *exp_tab;
+    double exp_l1, exp_l2;
+    T *jx, *ux;                   // [2 hemispheres][nfreq][nvox]
+};
+
+struct MlOpacityArgs {
+    long nvox;
+    int nfreq, n_levels, prec;
+    const FreqInfo *fi;
+    double theta_ref, t_ref;
+    const double *n, *T, *chi_c, *saha;
+    void *chi, *S, *sl, *fl;
+};
+
+struct MlRateArgs {
+    long nvox;
+    int nfreq, n_levels, n_trans, prec;
+    const FreqInfo *fi;
+    const TransInfo *ti;
+    const void *jx, *ux;          // [2][nfreq][nvox]
+    int zero_radiation;
+    double theta_ref, t_ref;
+    const double *T, *c, *saha, *n_tot;   // c [N][N][nvox], saha [N][nvox]
+    const double *f;              // [N][nvox] or nullptr for (n_tot, 0, ...)
+    double *n, *out;              // [N][nvox]
+    int mode;                     // RateMode (kRateReduce not used)
+    unsigned long long *scal;
+};
+
+size_t ml_sweep_smem_bytes(int prec, int rows, int nx);
+cudaError_t launch_ml_opacity(const MlOpacityArgs &a, cudaStream_t st);
+cudaError_t launch_ml_bottom(int prec, long nplane, int nfreq, const FreqInfo *fi,
+                             double theta_ref, const double *T, void *ib, cudaStream_t st);
+cudaError_t launch_ml_sweep_f64(const MlSweepArgs<double> &a, int bands, int threads,
+                                cudaStream_t st);
+cudaError_t launch_ml_sweep_f32(const MlSweepArgs<float> &a, int bands, int threads,
+                                cudaStream_t st);
+cudaError_t launch_ml_rates(const MlRateArgs &a, cudaStream_t st);
 
 }  // namespace mg3d

@@ -1,0 +1,434 @@
+// Multi-level atom: opacity per frequency and node, the plane sweep with all
+// rays of a hemisphere in one thread block, and the N x N rate equations.
+//
+// Opacity (Eq. 1, Sec. 2.1, Sec. 3).  Every frequency point belongs to one
+// transition (lower l, upper u); with the grey LTE background chi_c:
+//   chi = chi_t + chi_c,  S = (eta_t + chi_c B_nu) / chi,
+//   sl = eta_t / chi (the part of S the transition's populations set),
+//   fl = chi_t / chi (its share of the opacity).
+// Line:        chi_t = kappa (n_l g_u/g_l - n_u) phi,  eta_t = kappa rho^3 n_u phi,
+//              phi = exp(-(x/d)^2)/(sqrt(pi) d), d = sqrt(T/t_ref), B at line centre.
+// Bound-free:  chi_t = kappa y^-3 (n_l - n_u G E),  eta_t = kappa y^-3 n_u G E (rho y)^3,
+//              G = n_l*/n_u*, E = exp(-theta_ref rho y/T).
+//
+// Sweep.  One thread-block cluster per (frequency, hemisphere); its blocks
+// split the plane in row bands and each holds the 12 intensity planes of the
+// hemisphere's rays, double buffered.  A thread owns a node and walks the 12
+// rays, so the angle sums
+//   Jx = sum_r w_r (I - w0 sl),   Ux = sum_r w_r (1 - w0 fl)
+// of its node are complete in registers and written once per hemisphere.
+//
+// Rates (Rybicki & Hummer 1992, diagonal operator).  Per node, for a line:
+//   Jbar = sum wphi Jx, Ubar = sum wphi Ux (wphi: trapezoid x profile,
+//   normalised per node), P_lu += B_lu Jbar, P_ul += A_ul Ubar + B_ul Jbar;
+// for a bound-free continuum (qa = beta w_y y^-4):
+//   P_lc += sum qa Jx,   P_cl += G sum qa E ((rho y)^3 Ux + Jx);
+// plus collisions; row 0 is particle conservation (Eq. 3); the N x N system
+// is solved by Gaussian elimination with partial pivoting.
+#include <cooperative_groups.h>
+
+#include <cmath>
+
+#include "mg3d.h"
+#include "mg3d_internal.h"
+#include "sc_step.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace mg3d {
+
+static int grid_for(long n, int threads) {
+    long b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 152L * 32) b = 152L * 32;
+    return (int)b;
+}
+
+__device__ __forceinline__ double planck_rho(double rho, double theta_ref, double T) {
+    return rho * rho * rho / expm1(theta_ref * rho / T);
+}
+
+// ------------------------------------------------------------------ opacity
+
+template <typename T>
+__global__ void ml_opacity_kernel(const MlOpacityArgs a) {
+    const long total = (long)a.nfreq * a.nvox;
+    const double rsqpi = 0.5641895835477563;  // 1/sqrt(pi)
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total;
+         i += (long)gridDim.x * blockDim.x) {
+        const int f = (int)(i / a.nvox);
+        const long v = i - (long)f * a.nvox;
+        const FreqInfo q = a.fi[f];
+        const double Tg = a.T[v];
+        const double nl = a.n[(long)q.lo * a.nvox + v];
+        const double nu = a.n[(long)q.up * a.nvox + v];
+        double chi_t, eta_t, B;
+        if (q.kind == 0) {
+            const double d = sqrt(Tg / a.t_ref);
+            const double xd = q.xy / d;
+            const double phi = exp(-xd * xd) * rsqpi / d;
+            chi_t = q.kappa * phi * (q.gr * nl - nu);
+            eta_t = q.kappa * q.rho * q.rho * q.rho * nu * phi;
+            B = planck_rho(q.rho, a.theta_ref, Tg);
+        } else {
+            const double y = q.xy;
+            const double G = a.saha[(long)q.lo * a.nvox + v];
+            const double E = exp(-a.theta_ref * q.rho * y / Tg);
+            const double alpha = 1.0 / (y * y * y);
+            const double ry = q.rho * y;
+            chi_t = q.kappa * alpha * (nl - nu * G * E);
+            eta_t = q.kappa * alpha * nu * G * E * ry * ry * ry;
+            B = planck_rho(ry, a.theta_ref, Tg);
+        }
+        const double cc = a.chi_c[v];
+        const double chi = chi_t + cc;
+        const double inv = 1.0 / chi;
+        ((T *)a.chi)[i] = (T)chi;
+        ((T *)a.S)[i] = (T)((eta_t + cc * B) * inv);
+        ((T *)a.sl)[i] = (T)(eta_t * inv);
+        ((T *)a.fl)[i] = (T)(chi_t * inv);
+    }
+}
+
+template <typename T>
+__global__ void ml_bottom_kernel(long nplane, int nfreq, const FreqInfo *__restrict__ fi,
+                                 double theta_ref, const double *__restrict__ Tg,
+                                 T *__restrict__ ib) {
+    const long total = nplane * nfreq;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total;
+         i += (long)gridDim.x * blockDim.x) {
+        const int f = (int)(i / nplane);
+        const long p = i - (long)f * nplane;
+        const FreqInfo q = fi[f];
+        const double rho = q.kind == 0 ? q.rho : q.rho * q.xy;
+        ib[i] = (T)planck_rho(rho, theta_ref, Tg[p]);
+    }
+}
+
+// -------------------------------------------------------------------- sweep
+
+template <typename T, int MAXT>
+__global__ void __launch_bounds__(MAXT) ml_sweep_kernel(const MlSweepArgs<T> a) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int f = blockIdx.y;
+    const int hemi = blockIdx.z;     // 0: rays 0-11 (up), 1: rays 12-23 (down)
+    const bool up = hemi == 0;
+    const int nx = a.nx, ny = a.ny, nz = a.nz, rows = a.rows;
+    const int y0 = rank * rows;
+    const int myrows = max(0, min(rows, ny - y0));
+    const int band = myrows * nx;
+    const long nplane = (long)nx * ny;
+    const long nvox = nplane * nz;
+    const T *__restrict__ chif = a.chi + (long)f * nvox;
+    const T *__restrict__ Sf = a.S + (long)f * nvox;
+    const T *__restrict__ slf = a.sl + (long)f * nvox;
+    const T *__restrict__ flf = a.fl + (long)f * nvox;
+    T *__restrict__ jxo = a.jx + ((long)hemi * a.nfreq + f) * nvox;
+    T *__restrict__ uxo = a.ux + ((long)hemi * a.nfreq + f) * nvox;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *buf = reinterpret_cast<T *>(smem_raw);
+    const long raystride = (long)rows * nx;
+    const long bufstride = 12 * raystride;
+    __shared__ double exp_tab[64];
+    if (sizeof(T) == 8) {
+        for (int i = threadIdx.x; i < 64; i += blockDim.x) exp_tab[i] = a.exp_tab[i];
+        __syncthreads();
+    }
+    const ExpNegTable et{exp_tab, a.exp_l1, a.exp_l2};
+    const T wray = T(1.0 / kRays);
+
+    for (int t = 0; t < nz; ++t) {
+        const int k = up ? t : nz - 1 - t;
+        T *cur = buf + (t & 1) * bufstride;
+        if (t == 0) {
+            for (int q = threadIdx.x; q < band; q += blockDim.x) {
+                const int yl = q / nx, x = q - yl * nx;
+                const int y = y0 + yl;
+                const T Ib = up ? a.ib[(long)f * nplane + (long)y * nx + x] : T(0);
+                for (int j = 0; j < 12; ++j) cur[j * raystride + (long)yl * nx + x] = Ib;
+                const long v = (long)k * nplane + (long)y * nx + x;
+                jxo[v] = T(12) * wray * Ib;
+                uxo[v] = T(12) * wray;
+            }
+        } else {
+            const T *prev = buf + ((t - 1) & 1) * bufstride;
+            const int kp = up ? k - 1 : k + 1;
+            const T *__restrict__ chip = chif + (long)kp * nplane;
+            const T *__restrict__ Sp = Sf + (long)kp * nplane;
+            for (int q = threadIdx.x; q < band; q += blockDim.x) {
+                const int yl = q / nx, x = q - yl * nx;
+                const int y = y0 + yl;
+                const long v = (long)k * nplane + (long)y * nx + x;
+                const T chi_loc = chif[v], S_loc = Sf[v], sl = slf[v], fl = flf[v];
+                T jx = 0, ux = 0;
+                for (int j = 0; j < 12; ++j) {
+                    const StepGeom o = a.geom[(long)(hemi * 12 + j) * nz + t];
+                    const T tx = (T)o.tx, ty = (T)o.ty;
+                    const T w00 = (T(1) - tx) * (T(1) - ty), w10 = tx * (T(1) - ty);
+                    const T w01 = (T(1) - tx) * ty, w11 = tx * ty;
+                    int xa = x + o.ix0;
+                    if (xa >= nx) xa -= nx;
+                    const int xb = (xa + 1 == nx) ? 0 : xa + 1;
+                    int ya = y + o.iy0;
+                    if (ya >= ny) ya -= ny;
+                    const int yb = (ya + 1 == ny) ? 0 : ya + 1;
+                    const long ra = (long)ya * nx, rb = (long)yb * nx;
+                    const T chi_up = w00 * chip[ra + xa] + w10 * chip[ra + xb] +
+                                     w01 * chip[rb + xa] + w11 * chip[rb + xb];
+                    const T S_up = w00 * Sp[ra + xa] + w10 * Sp[ra + xb] +
+                                   w01 * Sp[rb + xa] + w11 * Sp[rb + xb];
+                    const int ba = ya / rows, bb = yb / rows;
+                    const T *Pa = (ba == rank) ? prev : cluster.map_shared_rank(prev, ba);
+                    const T *Pb = (bb == rank) ? prev : cluster.map_shared_rank(prev, bb);
+                    Pa += j * raystride + (long)(ya - ba * rows) * nx;
+                    Pb += j * raystride + (long)(yb - bb * rows) * nx;
+                    const T I_up = w00 * Pa[xa] + w10 * Pa[xb] + w01 * Pb[xa] + w11 * Pb[xb];
+                    const T x_tau = (chi_up + chi_loc) * (T(0.5) * (T)o.s);
+                    T ex, w0, wup, u;
+                    ScWeights<T>::eval(x_tau, T(1) / x_tau, et, ex, w0, wup, u);
+                    const T I = I_up * ex + wup * S_up + w0 * S_loc;
+                    cur[j * raystride + (long)yl * nx + x] = I;
+                    jx += I - w0 * sl;
+                    ux += T(1) - w0 * fl;
+                }
+                jxo[v] = wray * jx;
+                uxo[v] = wray * ux;
+            }
+        }
+        cluster.sync();
+    }
+}
+
+size_t ml_sweep_smem_bytes(int prec, int rows, int nx) {
+    const size_t elem = prec == MG3D_PREC_F64 ? sizeof(double) : sizeof(float);
+    return 2ull * 12 * rows * nx * elem;
+}
+
+template <typename T, int MAXT>
+static cudaError_t launch_ml_sweep_t(const MlSweepArgs<T> &a, int bands, int threads,
+                                     cudaStream_t st) {
+    const size_t smem = ml_sweep_smem_bytes(sizeof(T) == 8 ? MG3D_PREC_F64 : MG3D_PREC_F32,
+                                            a.rows, a.nx);
+    cudaError_t e = cudaFuncSetAttribute(ml_sweep_kernel<T, MAXT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(bands, a.nfreq, 2);
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = bands;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, ml_sweep_kernel<T, MAXT>, a);
+}
+
+cudaError_t launch_ml_sweep_f64(const MlSweepArgs<double> &a, int bands, int threads,
+                                cudaStream_t st) {
+    return threads <= 256 ? launch_ml_sweep_t<double, 256>(a, bands, threads, st)
+                          : launch_ml_sweep_t<double, 512>(a, bands, threads, st);
+}
+
+cudaError_t launch_ml_sweep_f32(const MlSweepArgs<float> &a, int bands, int threads,
+                                cudaStream_t st) {
+    return threads <= 256 ? launch_ml_sweep_t<float, 256>(a, bands, threads, st)
+                          : launch_ml_sweep_t<float, 512>(a, bands, threads, st);
+}
+
+// -------------------------------------------------------------------- rates
+
+__device__ __forceinline__ unsigned long long dbits_ml(double x) {
+    return (unsigned long long)__double_as_longlong(x);
+}
+
+template <typename TP>
+__global__ void __launch_bounds__(128) ml_rates_kernel(const MlRateArgs a) {
+    const TP *__restrict__ jx = (const TP *)a.jx;
+    const TP *__restrict__ ux = (const TP *)a.ux;
+    const long nvox = a.nvox;
+    const int N = a.n_levels;
+    const long hstride = (long)a.nfreq * nvox;
+    const double rsqpi = 0.5641895835477563;
+    double cmax = 0.0;
+    unsigned neg = 0, bad = 0;
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long base = (long)blockIdx.x * blockDim.x; base < nvox; base += stride) {
+        const long v = base + threadIdx.x;
+        if (v >= nvox) continue;
+        double P[kMaxLevels][kMaxLevels];
+        for (int i = 0; i < N; ++i)
+            for (int j = 0; j < N; ++j) P[i][j] = i == j ? 0.0 : a.c[((long)i * N + j) * nvox + v];
+        const double Tg = a.T[v];
+        for (int t = 0; t < a.n_trans; ++t) {
+            const TransInfo tr = a.ti[t];
+            if (tr.kind == 0) {
+                const double d = sqrt(Tg / a.t_ref);
+                double norm = 0.0, sj = 0.0, su = 0.0;
+                for (int f = tr.f_begin; f < tr.f_end; ++f) {
+                    const FreqInfo q = a.fi[f];
+                    const double xd = q.xy / d;
+                    const double wphi = q.w * exp(-xd * xd) * rsqpi / d;
+                    double J = 0.0, U = 1.0;
+                    if (!a.zero_radiation) {
+                        J = (double)jx[(long)f * nvox + v] + (double)jx[hstride + (long)f * nvox + v];
+                        U = (double)ux[(long)f * nvox + v] + (double)ux[hstride + (long)f * nvox + v];
+                    }
+                    norm += wphi;
+                    sj += wphi * J;
+                    su += wphi * U;
+                }
+                const double Jb = sj / norm, Ub = su / norm;
+                const double b_ul = tr.coef / (tr.rho * tr.rho * tr.rho);
+                P[tr.lo][tr.up] += tr.gr * b_ul * Jb;
+                P[tr.up][tr.lo] += tr.coef * Ub + b_ul * Jb;
+            } else {
+                const double G = a.saha[(long)tr.lo * nvox + v];
+                double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+                for (int f = tr.f_begin; f < tr.f_end; ++f) {
+                    const FreqInfo q = a.fi[f];
+                    const double y = q.xy;
+                    const double qa = tr.coef * q.w / (y * y * y * y);
+                    const double E = exp(-a.theta_ref * tr.rho * y / Tg);
+                    const double ry = tr.rho * y;
+                    double J = 0.0, U = 1.0;
+                    if (!a.zero_radiation) {
+                        J = (double)jx[(long)f * nvox + v] + (double)jx[hstride + (long)f * nvox + v];
+                        U = (double)ux[(long)f * nvox + v] + (double)ux[hstride + (long)f * nvox + v];
+                    }
+                    s1 += qa * J;
+                    s2 += qa * E * J;
+                    s3 += qa * E * ry * ry * ry * U;
+                }
+                P[tr.lo][tr.up] += s1;
+                P[tr.up][tr.lo] += G * (s3 + s2);
+            }
+        }
+        // W(n) = M n: row 0 conservation, row i: n_i sum_j P_ij - sum_j n_j P_ji
+        double M[kMaxLevels][kMaxLevels + 1];
+        for (int j = 0; j < N; ++j) M[0][j] = 1.0;
+        for (int i = 1; i < N; ++i) {
+            double out_i = 0.0;
+            for (int j = 0; j < N; ++j)
+                if (j != i) out_i += P[i][j];
+            for (int j = 0; j < N; ++j) M[i][j] = j == i ? out_i : -P[j][i];
+        }
+        double fv[kMaxLevels];
+        for (int i = 0; i < N; ++i)
+            fv[i] = a.f ? a.f[(long)i * nvox + v] : (i == 0 ? a.n_tot[v] : 0.0);
+        if (a.mode == kRateSolve) {
+            for (int i = 0; i < N; ++i) M[i][N] = fv[i];
+            for (int c = 0; c < N; ++c) {
+                int piv = c;
+                double best = fabs(M[c][c]);
+                for (int r = c + 1; r < N; ++r)
+                    if (fabs(M[r][c]) > best) {
+                        best = fabs(M[r][c]);
+                        piv = r;
+                    }
+                if (piv != c)
+                    for (int j = c; j <= N; ++j) {
+                        const double tmp = M[c][j];
+                        M[c][j] = M[piv][j];
+                        M[piv][j] = tmp;
+                    }
+                const double inv = 1.0 / M[c][c];
+                for (int r = c + 1; r < N; ++r) {
+                    const double fac = M[r][c] * inv;
+                    for (int j = c; j <= N; ++j) M[r][j] -= fac * M[c][j];
+                }
+            }
+            double xsol[kMaxLevels];
+            for (int i = N - 1; i >= 0; --i) {
+                double acc = M[i][N];
+                for (int j = i + 1; j < N; ++j) acc -= M[i][j] * xsol[j];
+                xsol[i] = acc / M[i][i];
+            }
+            bool finite = true;
+            double cl = 0.0;
+            for (int i = 0; i < N; ++i) {
+                const double old = a.n[(long)i * nvox + v];
+                a.n[(long)i * nvox + v] = xsol[i];
+                const double ci = fabs(xsol[i] - old) / fabs(xsol[i]);
+                if (!(isfinite(xsol[i]) && isfinite(ci))) finite = false;
+                else cl = fmax(cl, ci);
+                neg += xsol[i] <= 0.0;
+            }
+            if (finite) cmax = fmax(cmax, cl);
+            else ++bad;
+        } else {
+            for (int i = 0; i < N; ++i) {
+                double w = 0.0;
+                for (int j = 0; j < N; ++j) w += M[i][j] * a.n[(long)j * nvox + v];
+                if (a.mode == kRateResidual) a.out[(long)i * nvox + v] = fv[i] - w;
+                else a.out[(long)i * nvox + v] += w;
+            }
+        }
+    }
+    if (a.mode == kRateSolve && a.scal) {
+        __shared__ double red[32];
+        __shared__ unsigned cnt[2][32];
+        double m = cmax;
+        for (int o = 16; o > 0; o >>= 1) {
+            m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+            neg += __shfl_xor_sync(0xffffffffu, neg, o);
+            bad += __shfl_xor_sync(0xffffffffu, bad, o);
+        }
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        if (lane == 0) {
+            red[wid] = m;
+            cnt[0][wid] = neg;
+            cnt[1][wid] = bad;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int nw = (blockDim.x + 31) >> 5;
+            double mm = 0.0;
+            unsigned tn = 0, tb = 0;
+            for (int i = 0; i < nw; ++i) {
+                mm = fmax(mm, red[i]);
+                tn += cnt[0][i];
+                tb += cnt[1][i];
+            }
+            if (mm > 0.0) atomicMax(a.scal, dbits_ml(mm));
+            if (tn) atomicAdd(a.scal + 1, (unsigned long long)tn);
+            if (tb) atomicAdd(a.scal + 2, (unsigned long long)tb);
+        }
+    }
+}
+
+cudaError_t launch_ml_opacity(const MlOpacityArgs &a, cudaStream_t st) {
+    const long total = (long)a.nfreq * a.nvox;
+    if (a.prec == MG3D_PREC_F64)
+        ml_opacity_kernel<double><<<grid_for(total, 256), 256, 0, st>>>(a);
+    else
+        ml_opacity_kernel<float><<<grid_for(total, 256), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ml_bottom(int prec, long nplane, int nfreq, const FreqInfo *fi,
+                             double theta_ref, const double *T, void *ib, cudaStream_t st) {
+    const long total = nplane * nfreq;
+    if (prec == MG3D_PREC_F64)
+        ml_bottom_kernel<double><<<grid_for(total, 256), 256, 0, st>>>(nplane, nfreq, fi,
+                                                                       theta_ref, T, (double *)ib);
+    else
+        ml_bottom_kernel<float><<<grid_for(total, 256), 256, 0, st>>>(nplane, nfreq, fi,
+                                                                      theta_ref, T, (float *)ib);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ml_rates(const MlRateArgs &a, cudaStream_t st) {
+    if (a.prec == MG3D_PREC_F64)
+        ml_rates_kernel<double><<<grid_for(a.nvox, 128), 128, 0, st>>>(a);
+    else
+        ml_rates_kernel<float><<<grid_for(a.nvox, 128), 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace mg3d

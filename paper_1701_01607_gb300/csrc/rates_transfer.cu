@@ -261,7 +261,7 @@ __global__ void prolong_kernel(int ncomp, int nxc, int nyc, int nzc,
 // n_fine <- n_fine (1 + I(e)), e = (n_after - n_before)/n_before on the
 // coarse grid (Eqs. 10-11); a result <= 0 becomes 0.1 n_fine (Sec. 4.8).
 __global__ void __launch_bounds__(256) prolong_correct_kernel(
-    int nxc, int nyc, int nzc, const double *__restrict__ tz,
+    int ncomp, int nxc, int nyc, int nzc, const double *__restrict__ tz,
     const double *__restrict__ n_after, const double *__restrict__ n_before,
     double *__restrict__ n_fine, unsigned long long *scal) {
     const long nvf = (long)(2 * nxc) * (2 * nyc) * (2 * nzc - 1);
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(256) prolong_correct_kernel(
         if (f >= nvf) continue;
         Corners cr;
         corners(f, nxc, nyc, nzc, tz, cr);
-        for (int comp = 0; comp < 2; ++comp) {
+        for (int comp = 0; comp < ncomp; ++comp) {
             const double *Aa = n_after + comp * nvc;
             const double *Bb = n_before + comp * nvc;
             double ie = 0.0;
@@ -301,13 +301,14 @@ cudaError_t launch_prolong(int ncomp, int nxc, int nyc, int nzc, const double *t
     return cudaGetLastError();
 }
 
-cudaError_t launch_prolong_correct(int nxc, int nyc, int nzc, const double *tz,
+cudaError_t launch_prolong_correct(int ncomp, int nxc, int nyc, int nzc, const double *tz,
                                    const double *n_after, const double *n_before,
                                    double *n_fine, unsigned long long *scal,
                                    cudaStream_t st) {
     const long nvf = (long)(2 * nxc) * (2 * nyc) * (2 * nzc - 1);
-    prolong_correct_kernel<<<grid_for(nvf, 256), 256, 0, st>>>(nxc, nyc, nzc, tz, n_after,
-                                                                 n_before, n_fine, scal);
+    prolong_correct_kernel<<<grid_for(nvf, 256), 256, 0, st>>>(ncomp, nxc, nyc, nzc, tz,
+                                                                 n_after, n_before, n_fine,
+                                                                 scal);
     return cudaGetLastError();
 }
 

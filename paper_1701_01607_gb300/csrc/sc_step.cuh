@@ -1,0 +1,84 @@
+// Linear short-characteristics step shared by the sweep kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace mg3d {
+
+// Linear short-characteristics weights for optical path x:
+//   I = I_up exp(-x) + w_up S_up + w_0 S_0,
+//   u = (1 - exp(-x))/x, w_0 = 1 - u, w_up = u - exp(-x).
+// Below a threshold the closed forms cancel, so Taylor series are used.  The
+// FP32 variant uses the hardware exp2 approximation (__expf): its error grows
+// with x, but exp(-x) then multiplies a term that is already negligible.
+template <typename T>
+struct ScWeights;
+
+// e^{-x} for x >= 0 by the table-driven method of Tang (ACM TOMS 15, 1989):
+// -x = (64 m + j) ln2/64 + r with integer m, j in [0, 64) and |r| <= ln2/128,
+// so e^{-x} = 2^m 2^{j/64} e^r.  The reduction uses a two-part ln2/64 whose
+// high part times any |n| < 2^17 is exact; e^r - 1 is its Taylor polynomial of
+// degree 5 (truncation < 4e-17 relative); 2^{j/64} comes from a 64-entry
+// table and 2^m is applied by adding m to the exponent field.  Results below
+// e^{-708} are flushed to zero.
+struct ExpNegTable {
+    const double *tab;   // [64] 2^{j/64}
+    double l1, l2;       // ln2/64 = l1 + l2, l1 with 36 significant bits
+};
+
+__device__ __forceinline__ double exp_neg(double x, const ExpNegTable e) {
+    if (x > 708.0) return 0.0;
+    const double magic = 6755399441055744.0;  // 1.5 * 2^52
+    const double t = fma(x, -92.33248261689366, magic);  // -x * 64/ln2, rounded to an integer
+    const int n = __double2loint(t);
+    const double nd = t - magic;
+    double r = fma(-nd, e.l1, -x);
+    r = fma(-nd, e.l2, r);
+    double p = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+    p = fma(p, r, 1.0 / 6.0);
+    p = fma(p, r, 0.5);
+    p = fma(p, r, 1.0);
+    const double q = p * r;                      // e^r - 1
+    const double tj = e.tab[n & 63];
+    const double v = fma(tj, q, tj);             // 2^{j/64} e^r, in [0.99, 2.01)
+    const long long bits = __double_as_longlong(v) + ((long long)(n >> 6) << 52);
+    return __longlong_as_double(bits);
+}
+
+template <>
+struct ScWeights<double> {
+    // inv_x = 1/x, formed by the caller as (1/dtau0)(1/phi): one division per
+    // node and ray instead of one per frequency.
+    static __device__ __forceinline__ void eval(double x, double inv_x, const ExpNegTable et,
+                                                double &ex, double &w0, double &wup, double &u) {
+        ex = exp_neg(x, et);
+        if (x < 1e-3) {
+            w0 = x * (0.5 - x * (1.0 / 6.0 - x * (1.0 / 24.0 - x * (1.0 / 120.0 - x / 720.0))));
+            wup = x * (0.5 - x * (1.0 / 3.0 - x * (1.0 / 8.0 - x * (1.0 / 30.0 - x / 144.0))));
+            u = 1.0 - w0;
+        } else {
+            u = fma(-ex, inv_x, inv_x);   // (1 - e^-x)/x
+            w0 = 1.0 - u;
+            wup = u - ex;
+        }
+    }
+};
+
+template <>
+struct ScWeights<float> {
+    static __device__ __forceinline__ void eval(float x, float inv_x, const ExpNegTable,
+                                                float &ex, float &w0, float &wup, float &u) {
+        ex = __expf(-x);
+        if (x < 0.1f) {
+            w0 = x * (0.5f - x * (1.0f / 6.0f - x * (1.0f / 24.0f - x * (1.0f / 120.0f - x / 720.0f))));
+            wup = x * (0.5f - x * (1.0f / 3.0f - x * (1.0f / 8.0f - x * (1.0f / 30.0f - x / 144.0f))));
+            u = 1.0f - w0;
+        } else {
+            u = fmaf(-ex, inv_x, inv_x);   // (1 - e^-x)/x
+            w0 = 1.0f - u;
+            wup = u - ex;
+        }
+    }
+};
+
+}  // namespace mg3d

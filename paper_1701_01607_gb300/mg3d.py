@@ -54,6 +54,30 @@ class mg3d_params(ctypes.Structure):
                 ("fs_prec", ctypes.c_int)]
 
 
+class mg3d_line(ctypes.Structure):
+    _fields_ = [("lower", ctypes.c_int), ("upper", ctypes.c_int), ("rho", ctypes.c_double),
+                ("a_ul", ctypes.c_double), ("kappa", ctypes.c_double), ("n_freq", ctypes.c_int),
+                ("x_max", ctypes.c_double)]
+
+
+class mg3d_continuum(ctypes.Structure):
+    _fields_ = [("lower", ctypes.c_int), ("rho", ctypes.c_double), ("beta", ctypes.c_double),
+                ("kappa", ctypes.c_double), ("n_freq", ctypes.c_int), ("y_max", ctypes.c_double)]
+
+
+class mg3d_ml_atom(ctypes.Structure):
+    _fields_ = [("n_levels", ctypes.c_int), ("g", _D), ("theta", _D),
+                ("theta_ref", ctypes.c_double), ("t_ref", ctypes.c_double),
+                ("n_lines", ctypes.c_int), ("lines", ctypes.POINTER(mg3d_line)),
+                ("n_continua", ctypes.c_int), ("continua", ctypes.POINTER(mg3d_continuum))]
+
+
+class mg3d_ml_atmosphere(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("z", _D), ("T", _D),
+                ("n_tot", _D), ("chi_c", _D), ("c", _D), ("saha", _D)]
+
+
 class mg3d_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int),
                 ("sweeps", ctypes.c_int * (MG3D_MAX_GRIDS + 1)),
@@ -79,6 +103,11 @@ _SIGNATURES = {
     "mg3d_create": (_I, [ctypes.POINTER(mg3d_atmosphere), ctypes.POINTER(mg3d_atom),
                          ctypes.POINTER(mg3d_quadrature), ctypes.POINTER(mg3d_params),
                          ctypes.POINTER(_H)]),
+    "mg3d_create_ml": (_I, [ctypes.POINTER(mg3d_ml_atmosphere), ctypes.POINTER(mg3d_ml_atom),
+                            ctypes.POINTER(mg3d_quadrature), ctypes.POINTER(mg3d_params),
+                            ctypes.POINTER(_H)]),
+    "mg3d_n_levels": (_I, [_H, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "mg3d_formal_solve_ml": (_I, [_H, _I, _D, _D]),
     "mg3d_destroy": (_I, [_H]),
     "mg3d_set_stream": (_I, [_H, ctypes.c_void_p]),
     "mg3d_level_shape": (_I, [_H, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
@@ -182,6 +211,51 @@ def mg3d_create(atm, atom, quad_a: float = 0.0, n_grids: int = 1, nu_fmg: int = 
     return h
 
 
+def mg3d_create_ml(atm, atom, quad_a: float = 0.0, n_grids: int = 1, nu_fmg: int = 16,
+                   nu0: int = 0, nu1: int = 2, nu2: int = 2, nu3: int = 32,
+                   fs_prec: int = MG3D_PREC_F64):
+    """mg3d_create_ml from a synth.MultiLevelAtmosphere and MultiLevelAtom."""
+    lib = load()
+    keep = {}
+
+    def arr(name, a):
+        keep[name] = np.ascontiguousarray(a, dtype=np.float64)
+        return _dptr(keep[name])
+
+    a = mg3d_ml_atmosphere(atm.nx, atm.ny, atm.nz, atm.dx, atm.dy, arr("z", atm.z),
+                           arr("T", atm.T), arr("n", atm.n_tot), arr("cc", atm.chi_c),
+                           arr("c", atm.c), arr("s", atm.saha))
+    lines = (mg3d_line * max(1, len(atom.lines)))(
+        *[mg3d_line(l.lower, l.upper, l.rho, l.a_ul, l.kappa, l.n_freq, l.x_max)
+          for l in atom.lines])
+    conts = (mg3d_continuum * max(1, len(atom.continua)))(
+        *[mg3d_continuum(c.lower, c.rho, c.beta, c.kappa, c.n_freq, c.y_max)
+          for c in atom.continua])
+    at = mg3d_ml_atom(atom.n_levels, arr("g", atom.g), arr("th", atom.theta), atom.theta_ref,
+                      atom.t_ref, len(atom.lines), lines, len(atom.continua), conts)
+    q = mg3d_quadrature(quad_a)
+    p = mg3d_params(n_grids, nu_fmg, nu0, nu1, nu2, nu3, fs_prec)
+    h = _H()
+    _check(lib.mg3d_create_ml(ctypes.byref(a), ctypes.byref(at), ctypes.byref(q),
+                              ctypes.byref(p), ctypes.byref(h)))
+    return h
+
+
+def mg3d_n_levels(h):
+    n, f = _I(), _I()
+    _check(load().mg3d_n_levels(h, ctypes.byref(n), ctypes.byref(f)))
+    return n.value, f.value
+
+
+def mg3d_formal_solve_ml(h, level: int):
+    nx, ny, nz = mg3d_level_shape(h, level)
+    _, nf = mg3d_n_levels(h)
+    jx = np.empty((nf, nz, ny, nx))
+    ux = np.empty((nf, nz, ny, nx))
+    _check(load().mg3d_formal_solve_ml(h, level, _dptr(jx), _dptr(ux)))
+    return jx, ux
+
+
 def mg3d_destroy(h):
     return _check(load().mg3d_destroy(h))
 
@@ -200,7 +274,7 @@ def mg3d_level_shape(h, level: int):
 def mg3d_get_populations(h, level: int, out=None):
     nx, ny, nz = mg3d_level_shape(h, level)
     if out is None:
-        out = np.empty((2, nz, ny, nx))
+        out = np.empty((mg3d_n_levels(h)[0], nz, ny, nx))
     _check(load().mg3d_get_populations(h, level, _dptr(out)))
     return out
 
@@ -230,7 +304,7 @@ def mg3d_mali_sweep(h, level: int, n_sweeps: int = 1) -> float:
 
 def mg3d_residual(h, level: int):
     nx, ny, nz = mg3d_level_shape(h, level)
-    r = np.empty((2, nz, ny, nx))
+    r = np.empty((mg3d_n_levels(h)[0], nz, ny, nx))
     _check(load().mg3d_residual(h, level, _dptr(r)))
     return r
 

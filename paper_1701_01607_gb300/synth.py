@@ -296,14 +296,16 @@ def hydrogen_like_atom(n_bound: int = 5, line_freq: int = 100, cont_freq: int = 
 def chromosphere(nx: int, ny: int, nz: int, atom: MultiLevelAtom, seed: int = 2,
                  t_min: float = 4000.0, t_max: float = 10000.0, scale_heights: float = 8.0,
                  n_bottom: float = 1e4, sigma_t: float = 0.1, ionisation: float = 1e-3,
-                 saha_scale: float = 10.0, c_strength: float = 1e-3, chi_c0: float = 1e-2,
+                 saha_scale: float = 10.0, c_strength: float = 1e-2, chi_c0: float = 1e-2,
                  dx: float = 1.0, z=None) -> MultiLevelAtmosphere:
     """Chromosphere-like box: T rises from t_min to t_max with height (with
     seeded 3D perturbations of relative size sigma_t), the density falls by
     e^scale_heights from bottom to top; electron density = ionisation x
     density; collisional rates from a van Regemorter-like n_e T^-1/2 law with
     seeded strengths and detailed balance; Saha-like LTE ratios
-    saha_i = saha_scale n_e T^-3/2 (g_i/g_c) exp(theta_ion_i / T)."""
+    saha_i = saha_scale n_e T^-3/2 (g_i/g_c) exp(theta_ion_i / T).  With the
+    default strengths no line or continuum is inverted at the zero-radiation
+    start (ten times weaker collisions make the upper lines mase)."""
     rng = np.random.default_rng(seed)
     if z is None:
         z = np.arange(nz, dtype=np.float64) * dx
