@@ -312,6 +312,13 @@ int mg3d_autotune(mg3d_handle *h, int level, int *evaluated, double *seconds);
  * memory; out_host holds 2n doubles. */
 int mg3d_check_exp(int n, const double *x_host, double *out_host);
 
+/* Replay V-cycles from CUDA graphs (default on).  The first V-cycle of each
+ * kind (first cycle / later cycles) is captured on the handle's stream and
+ * later ones replay the graph; graphs are rebuilt after a change of stream or
+ * sweep shapes or of the timing switch; with timing on, the graphs carry
+ * the event records and each replay's sweep times are read back. */
+int mg3d_set_graphs(mg3d_handle *h, int enable);
+
 /* Per-launch device timing of the sweep kernel (CUDA events on the handle's
  * stream) on or off, counters and their reset. */
 int mg3d_set_timing(mg3d_handle *h, int enable);

@@ -39,11 +39,15 @@ int fail(int code, const std::string &msg) {
     return code;
 }
 
+// On failure the runtime's last-error state is cleared as well, so that a
+// later launch check does not report this error again.
 #define MG_CUDA(call)                                                                  \
     do {                                                                               \
         cudaError_t e_ = (call);                                                       \
-        if (e_ != cudaSuccess)                                                         \
+        if (e_ != cudaSuccess) {                                                       \
+            (void)cudaGetLastError();                                                  \
             return fail(MG3D_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+        }                                                                              \
     } while (0)
 
 #define MG_TRY(call)             \
@@ -120,6 +124,21 @@ struct mg3d_handle {
     bool timing = false;
     std::vector<TimedLaunch> timed;
     std::vector<cudaEvent_t> event_pool;
+    // CUDA graphs of the V-cycle (index: first cycle or not)
+    bool use_graphs = true;
+    cudaGraphExec_t cycle_exec[2] = {nullptr, nullptr};
+    cudaStream_t graph_stream = nullptr;     // stream the graphs were captured on
+    std::vector<TimedLaunch> cycle_timed[2]; // event pairs recorded by each graph
+    double acc_ms[MG3D_MAX_GRIDS + 1] = {};  // sweep time read back from graph replays
+    long long acc_n[MG3D_MAX_GRIDS + 1] = {};
+    struct CycleDelta {
+        long long launches = 0, fs_launches = 0;
+        double fs_units = 0;
+        long long level_launches[MG3D_MAX_GRIDS + 1] = {};
+        double level_units[MG3D_MAX_GRIDS + 1] = {};
+        int sweeps[MG3D_MAX_GRIDS + 1] = {};
+        int fss[MG3D_MAX_GRIDS + 1] = {};
+    } cycle_delta[2];
     // per-solve statistics
     int sweeps[MG3D_MAX_GRIDS + 1] = {};
     int fss[MG3D_MAX_GRIDS + 1] = {};
@@ -274,8 +293,22 @@ int check_level(const mg3d_handle *h, int level) {
 
 int launched(mg3d_handle *h, cudaError_t e, const char *what) {
     ++h->launches;
-    if (e != cudaSuccess) return fail(MG3D_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(MG3D_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    }
     return MG3D_OK;
+}
+
+// Record an event on the handle's stream; inside a stream capture it becomes
+// an event-record node of the graph, so that replays can be timed.
+cudaError_t record_event(cudaEvent_t e, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t r = cudaStreamIsCapturing(st, &cs);
+    if (r != cudaSuccess) return r;
+    if (cs == cudaStreamCaptureStatusActive)
+        return cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    return cudaEventRecord(e, st);
 }
 
 cudaEvent_t pool_event(mg3d_handle *h) {
@@ -302,7 +335,7 @@ int ml_formal_solution(mg3d_handle *h, int k) {
     if (h->timing) {
         tl.a = pool_event(h);
         tl.b = pool_event(h);
-        MG_CUDA(cudaEventRecord(tl.a, h->stream));
+        MG_CUDA(record_event(tl.a, h->stream));
     }
     cudaError_t e;
     if (h->prec == MG3D_PREC_F64) {
@@ -322,7 +355,7 @@ int ml_formal_solution(mg3d_handle *h, int k) {
     }
     MG_TRY(launched(h, e, "multi-level sweep"));
     if (h->timing) {
-        MG_CUDA(cudaEventRecord(tl.b, h->stream));
+        MG_CUDA(record_event(tl.b, h->stream));
         h->timed.push_back(tl);
     }
     const double units = (double)L.nvox * kRays * h->nfreq_ml;
@@ -372,7 +405,7 @@ int formal_solution(mg3d_handle *h, int k) {
     if (h->timing) {
         tl.a = pool_event(h);
         tl.b = pool_event(h);
-        MG_CUDA(cudaEventRecord(tl.a, h->stream));
+        MG_CUDA(record_event(tl.a, h->stream));
     }
     cudaError_t e;
     if (h->prec == MG3D_PREC_F64) {
@@ -394,7 +427,7 @@ int formal_solution(mg3d_handle *h, int k) {
     }
     MG_TRY(launched(h, e, "sweep"));
     if (h->timing) {
-        MG_CUDA(cudaEventRecord(tl.b, h->stream));
+        MG_CUDA(record_event(tl.b, h->stream));
         h->timed.push_back(tl);
     }
     ++h->fs_launches;
@@ -441,7 +474,7 @@ int sweep(mg3d_handle *h, int k) {
 }
 
 int reset_scalars(mg3d_handle *h) {
-    MG_CUDA(cudaMemsetAsync(h->scal, 0, 4 * sizeof(unsigned long long), h->stream));
+    MG_CUDA(cudaMemsetAsync(h->scal, 0, 8 * sizeof(unsigned long long), h->stream));
     return MG3D_OK;
 }
 
@@ -521,24 +554,127 @@ int vcycle(mg3d_handle *h, int k, bool first) {
 }
 
 // One V-cycle from the finest grid; C over the cycle into *C.
-int fas_cycle(mg3d_handle *h, bool first, double *C, long long *neg) {
+// The work of one V-cycle from the finest grid, with no host synchronisation:
+// copy of the starting populations, the cycle, and C over the cycle into
+// scal[4] (non-finite count into scal[6]); the 10 % rule counts into scal[3].
+int cycle_work(mg3d_handle *h, bool first) {
     Level &F = h->lev[h->L];
-    if (h->L < 2) return fail(MG3D_E_STATE, "a V-cycle needs n_grids >= 2");
     MG_CUDA(cudaMemcpyAsync(h->scratch, F.n, (size_t)h->N * F.nvox * sizeof(double),
                             cudaMemcpyDeviceToDevice, h->stream));
     F.f_default = true;
     MG_TRY(reset_scalars(h));
     MG_TRY(vcycle(h, h->L, first));
-    long long neg_in_cycle = 0;
-    MG_TRY(read_scalars(h, nullptr, &neg_in_cycle, nullptr));
-    MG_TRY(reset_scalars(h));
-    MG_TRY(launched(h, launch_max_rel_change((long)h->N * F.nvox, F.n, h->scratch, h->scal,
+    MG_TRY(launched(h, launch_max_rel_change((long)h->N * F.nvox, F.n, h->scratch, h->scal + 4,
                                              h->stream),
                     "max rel change"));
-    long long bad = 0;
-    MG_TRY(read_scalars(h, C, nullptr, &bad));
-    if (neg) *neg = neg_in_cycle;
-    if (bad) return fail(MG3D_E_DIVERGED, "non-finite populations after a V-cycle");
+    return MG3D_OK;
+}
+
+void drop_graphs(mg3d_handle *h) {
+    for (int i = 0; i < 2; ++i) {
+        if (h->cycle_exec[i]) {
+            cudaGraphExecDestroy(h->cycle_exec[i]);
+            h->cycle_exec[i] = nullptr;
+        }
+        for (auto &t : h->cycle_timed[i]) {
+            h->event_pool.push_back(t.a);
+            h->event_pool.push_back(t.b);
+        }
+        h->cycle_timed[i].clear();
+    }
+}
+
+// Capture the cycle into a graph (once per variant), then replay it; the
+// library's counters advance by what the captured cycle launched.
+int graph_cycle(mg3d_handle *h, bool first) {
+    const int idx = first ? 1 : 0;
+    if (h->graph_stream != h->stream) {
+        drop_graphs(h);
+        h->graph_stream = h->stream;
+    }
+    if (!h->cycle_exec[idx]) {
+        mg3d_handle::CycleDelta before;
+        before.launches = h->launches;
+        before.fs_launches = h->fs_launches;
+        before.fs_units = h->fs_units;
+        std::memcpy(before.level_launches, h->level_launches, sizeof(before.level_launches));
+        std::memcpy(before.level_units, h->level_units, sizeof(before.level_units));
+        std::memcpy(before.sweeps, h->sweeps, sizeof(before.sweeps));
+        std::memcpy(before.fss, h->fss, sizeof(before.fss));
+        const size_t timed_before = h->timed.size();
+        MG_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed));
+        int rc = cycle_work(h, first);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+        if (rc != MG3D_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return fail(MG3D_E_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&h->cycle_exec[idx], graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess)
+            return fail(MG3D_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        // event pairs recorded inside the graph are read after every replay
+        h->cycle_timed[idx].assign(h->timed.begin() + timed_before, h->timed.end());
+        h->timed.resize(timed_before);
+        // what one replay adds to the counters; capturing itself ran nothing
+        mg3d_handle::CycleDelta &d = h->cycle_delta[idx];
+        d.launches = h->launches - before.launches;
+        d.fs_launches = h->fs_launches - before.fs_launches;
+        d.fs_units = h->fs_units - before.fs_units;
+        for (int k = 0; k <= MG3D_MAX_GRIDS; ++k) {
+            d.level_launches[k] = h->level_launches[k] - before.level_launches[k];
+            d.level_units[k] = h->level_units[k] - before.level_units[k];
+            d.sweeps[k] = h->sweeps[k] - before.sweeps[k];
+            d.fss[k] = h->fss[k] - before.fss[k];
+        }
+        h->launches = before.launches;
+        h->fs_launches = before.fs_launches;
+        h->fs_units = before.fs_units;
+        std::memcpy(h->level_launches, before.level_launches, sizeof(before.level_launches));
+        std::memcpy(h->level_units, before.level_units, sizeof(before.level_units));
+        std::memcpy(h->sweeps, before.sweeps, sizeof(before.sweeps));
+        std::memcpy(h->fss, before.fss, sizeof(before.fss));
+    }
+    MG_CUDA(cudaGraphLaunch(h->cycle_exec[idx], h->stream));
+    const mg3d_handle::CycleDelta &d = h->cycle_delta[idx];
+    h->launches += d.launches;
+    h->fs_launches += d.fs_launches;
+    h->fs_units += d.fs_units;
+    for (int k = 0; k <= MG3D_MAX_GRIDS; ++k) {
+        h->level_launches[k] += d.level_launches[k];
+        h->level_units[k] += d.level_units[k];
+        h->sweeps[k] += d.sweeps[k];
+        h->fss[k] += d.fss[k];
+    }
+    return MG3D_OK;
+}
+
+// One V-cycle from the finest grid; C over the cycle into *C.  Replayed from
+// a CUDA graph unless graphs are off or per-launch timing is on.
+int fas_cycle(mg3d_handle *h, bool first, double *C, long long *neg) {
+    if (h->L < 2) return fail(MG3D_E_STATE, "a V-cycle needs n_grids >= 2");
+    const bool graphs = h->use_graphs;
+    if (graphs) {
+        MG_TRY(graph_cycle(h, first));
+    } else {
+        MG_TRY(cycle_work(h, first));
+    }
+    unsigned long long sc[8];
+    MG_CUDA(cudaMemcpyAsync(sc, h->scal, sizeof(sc), cudaMemcpyDeviceToHost, h->stream));
+    MG_CUDA(cudaStreamSynchronize(h->stream));
+    if (graphs) {
+        for (auto &t : h->cycle_timed[first ? 1 : 0]) {
+            float ms = 0.f;
+            MG_CUDA(cudaEventElapsedTime(&ms, t.a, t.b));
+            h->acc_ms[t.level] += ms;
+            ++h->acc_n[t.level];
+        }
+    }
+    if (C) std::memcpy(C, &sc[4], sizeof(double));
+    if (neg) *neg = (long long)sc[3];
+    if (sc[6]) return fail(MG3D_E_DIVERGED, "non-finite populations after a V-cycle");
     return MG3D_OK;
 }
 
@@ -590,6 +726,8 @@ int make_shape(const mg3d_handle *h, int k, int ng, int bands, int threads, Swee
     return MG3D_OK;
 }
 
+void drop_graphs(mg3d_handle *h);
+
 // Partial-sum buffers of at least `need` elements (contents not kept).
 int ensure_partials(mg3d_handle *h, size_t need) {
     if (need <= h->partial_elems) return MG3D_OK;
@@ -602,6 +740,7 @@ int ensure_partials(mg3d_handle *h, size_t need) {
     MG_TRY(dev_alloc(&h->pj, need * es));
     MG_TRY(dev_alloc(&h->pu, need * es));
     h->partial_elems = need;
+    drop_graphs(h);
     return MG3D_OK;
 }
 
@@ -835,7 +974,7 @@ int create_impl(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_qu
     }
     MG_TRY(dev_alloc(&h->pj, h->partial_elems * es));
     MG_TRY(dev_alloc(&h->pu, h->partial_elems * es));
-    MG_TRY(dalloc(&h->scal, 4));
+    MG_TRY(dalloc(&h->scal, 8));
     for (int k = 1; k <= h->L; ++k) MG_TRY(zero_radiation(h, k));
     MG_CUDA(cudaStreamSynchronize(h->stream));
     return MG3D_OK;
@@ -1027,7 +1166,7 @@ int create_ml_impl(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
     }
     MG_TRY(dev_alloc(&h->ml_jx, 2 * (size_t)nf * F.nvox * es));
     MG_TRY(dev_alloc(&h->ml_ux, 2 * (size_t)nf * F.nvox * es));
-    MG_TRY(dalloc(&h->scal, 4));
+    MG_TRY(dalloc(&h->scal, 8));
     for (int k = 1; k <= h->L; ++k) MG_TRY(zero_radiation(h, k));
     MG_CUDA(cudaStreamSynchronize(h->stream));
     return MG3D_OK;
@@ -1184,6 +1323,7 @@ int mg3d_formal_solve_ml(mg3d_handle *h, int level, double *jx_host, double *ux_
 int mg3d_destroy(mg3d_handle *h) {
     if (!h) return MG3D_OK;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    drop_graphs(h);
     for (int k = 0; k <= MG3D_MAX_GRIDS; ++k) free_level(h->lev[k]);
     void *ptrs[] = {h->d_phi, h->d_wphi, h->d_inv_phi, h->d_exp_tab, h->pj, h->pu, h->scal,
                     h->scratch, h->d_fi, h->d_ti, h->ml_jx, h->ml_ux};
@@ -1413,6 +1553,7 @@ int mg3d_set_fs_config(mg3d_handle *h, int level, int freq_per_block, int bands,
     MG_CUDA(cudaStreamSynchronize(h->stream));
     MG_TRY(ensure_partials(h, (size_t)kRays * s.ngroups * (size_t)h->lev[level].nvox));
     h->lev[level].shape = s;
+    drop_graphs(h);
     return MG3D_OK;
 }
 
@@ -1428,6 +1569,7 @@ int mg3d_autotune(mg3d_handle *h, int level, int *evaluated, double *seconds) {
         count += c;
     }
     MG_TRY(shrink_partials(h));
+    drop_graphs(h);
     if (evaluated) *evaluated = count;
     if (seconds)
         *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -1461,8 +1603,18 @@ int mg3d_check_exp(int n, const double *x_host, double *out_host) {
     return rc;
 }
 
+int mg3d_set_graphs(mg3d_handle *h, int enable) {
+    if (!h) return fail(MG3D_E_ARG, "null handle");
+    MG_CUDA(cudaStreamSynchronize(h->stream));
+    h->use_graphs = enable != 0;
+    if (!h->use_graphs) drop_graphs(h);
+    return MG3D_OK;
+}
+
 int mg3d_set_timing(mg3d_handle *h, int enable) {
     if (!h) return fail(MG3D_E_ARG, "null handle");
+    MG_CUDA(cudaStreamSynchronize(h->stream));
+    if ((enable != 0) != h->timing) drop_graphs(h);
     h->timing = enable != 0;
     return MG3D_OK;
 }
@@ -1478,6 +1630,12 @@ int mg3d_get_counters(mg3d_handle *h, mg3d_counters *out) {
         ++out->fs_timed_launches;
         out->level_fs_kernel_ms[t.level] += ms;
         ++out->level_fs_timed_launches[t.level];
+    }
+    for (int k = 0; k <= MG3D_MAX_GRIDS; ++k) {
+        out->fs_kernel_ms += h->acc_ms[k];
+        out->fs_timed_launches += h->acc_n[k];
+        out->level_fs_kernel_ms[k] += h->acc_ms[k];
+        out->level_fs_timed_launches[k] += h->acc_n[k];
     }
     out->kernel_launches = h->launches;
     out->fs_launches = h->fs_launches;
@@ -1502,6 +1660,8 @@ int mg3d_reset_counters(mg3d_handle *h) {
     h->fs_units = 0;
     std::memset(h->level_launches, 0, sizeof(h->level_launches));
     std::memset(h->level_units, 0, sizeof(h->level_units));
+    std::memset(h->acc_ms, 0, sizeof(h->acc_ms));
+    std::memset(h->acc_n, 0, sizeof(h->acc_n));
     return MG3D_OK;
 }
 

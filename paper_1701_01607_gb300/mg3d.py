@@ -129,6 +129,7 @@ _SIGNATURES = {
                                 ctypes.POINTER(_I)]),
     "mg3d_autotune": (_I, [_H, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),
     "mg3d_check_exp": (_I, [_I, _D, _D]),
+    "mg3d_set_graphs": (_I, [_H, _I]),
     "mg3d_set_timing": (_I, [_H, _I]),
     "mg3d_get_counters": (_I, [_H, ctypes.POINTER(mg3d_counters)]),
     "mg3d_reset_counters": (_I, [_H]),
@@ -382,6 +383,10 @@ def mg3d_check_exp(x):
     out = np.empty(2 * x.size)
     _check(load().mg3d_check_exp(x.size, _dptr(x), _dptr(out)))
     return out[0::2], out[1::2]
+
+
+def mg3d_set_graphs(h, enable: bool):
+    return _check(load().mg3d_set_graphs(h, int(bool(enable))))
 
 
 def mg3d_set_timing(h, enable: bool):

@@ -293,3 +293,28 @@ def test_autotuned_shapes_keep_parity():
         assert rel(m.mg3d_get_populations(h, 2), n) < TOL_POP64
     finally:
         m.mg3d_destroy(h)
+
+
+def test_graph_replayed_vcycles_equal_direct_launches():
+    """V-cycles replayed from CUDA graphs give bit-identical populations and
+    the same counters as the same cycles launched one kernel at a time."""
+    atm, atom = synth.stratified_two_level(16, 16, 33, eps=1e-3, sigma=0.3, seed=13)
+    hg = make(atm, atom, n_grids=3)
+    hd = make(atm, atom, n_grids=3)
+    try:
+        m.mg3d_set_graphs(hd, False)
+        m.mg3d_set_timing(hg, True)
+        for cyc in range(4):
+            cg = m.mg3d_fas_vcycle(hg, cyc == 0)
+            cd = m.mg3d_fas_vcycle(hd, cyc == 0)
+            assert cg == cd
+        assert np.array_equal(m.mg3d_get_populations(hg, 3), m.mg3d_get_populations(hd, 3))
+        ctg, ctd = m.mg3d_get_counters(hg), m.mg3d_get_counters(hd)
+        assert ctg["fs_launches"] == ctd["fs_launches"]
+        assert ctg["fs_units"] == ctd["fs_units"]
+        assert ctg["kernel_launches"] == ctd["kernel_launches"]
+        assert ctg["level_fs_timed_launches"][3] == ctg["level_fs_launches"][3]
+        assert ctg["level_fs_kernel_ms"][3] > 0
+    finally:
+        m.mg3d_destroy(hg)
+        m.mg3d_destroy(hd)
