@@ -279,6 +279,32 @@ int mg3d_n_levels(const mg3d_handle *h, int *n_levels, int *n_freq);
  * [n_freq][nz][ny][nx] (nullable).  MG3D_E_STATE on a two-level handle. */
 int mg3d_formal_solve_ml(mg3d_handle *h, int level, double *jx_host, double *ux_host);
 
+/* ------------------------------------------------------------------------
+ * Batches: many independent atmospheres of uneven size (two-level and
+ * multi-level atoms mixed) iterated in lockstep.  Every formal solution of
+ * the batch is one launch per atom kind whose thread-block clusters each
+ * take one (member, ray or hemisphere, frequency group) of a shared work
+ * table; the other per-node kernels run per member; a whole batched V-cycle
+ * is captured once into a CUDA graph and replayed.  Members must share
+ * n_grids, the formal-solution precision and the multigrid schedule; creating
+ * the batch moves them onto the batch's stream and fixes their sweep shapes
+ * (a common number of bands per level), so they should not be autotuned or
+ * used alone while the batch exists.  The batch does not own its members. */
+typedef struct mg3d_batch mg3d_batch;
+int mg3d_batch_create(int n, mg3d_handle *const *members, mg3d_batch **out);
+int mg3d_batch_destroy(mg3d_batch *b);
+/* One lockstep V-cycle; max_rel_change (nullable) receives C of each member
+ * ([n] doubles). */
+int mg3d_batch_fas_vcycle(mg3d_batch *b, int is_first, double *max_rel_change);
+/* FAS from the zero-radiation start, or full multigrid, until every member's
+ * change over a cycle is below tol; stats (nullable) is [n] (iterations: the
+ * cycle at which each member first met tol). */
+int mg3d_batch_fas_solve(mg3d_batch *b, double tol, int max_cycles, mg3d_stats *stats);
+int mg3d_batch_fmg_solve(mg3d_batch *b, double tol, int max_cycles, mg3d_stats *stats);
+/* Kernel launches and formal-solution units (nodes x rays x frequencies)
+ * of the batch so far. */
+int mg3d_batch_counters(const mg3d_batch *b, long long *kernel_launches, double *fs_units);
+
 /* Grid-transfer operators on host arrays of ncomp fields, for checking.
  * mg3d_restrict: full weighting (Sec. 4.4) from level_fine to level_fine-1,
  * fine_host [ncomp][fine nodes] -> coarse_host [ncomp][coarse nodes].

@@ -55,14 +55,11 @@ __global__ void planck_bottom_kernel(long nplane, double theta, const double *__
         bbot[p] = (T)(1.0 / expm1(theta / Tgas[p]));
 }
 
-// MAXT: the block size bound the kernel is compiled for (256 or 512); the
-// register budget per thread follows from it.
-template <typename T, int MAXT>
-__global__ void __launch_bounds__(MAXT) sweep_kernel(const SweepArgs<T> a) {
+// Body of the sweep for ray r and frequency group g of one problem.
+template <typename T>
+__device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) {
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
-    const int g = blockIdx.y;
-    const int r = blockIdx.z;
     const int nx = a.nx, ny = a.ny, nz = a.nz, rows = a.rows;
     const int y0 = rank * rows;
     const int myrows = max(0, min(rows, ny - y0));
@@ -168,6 +165,24 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(const SweepArgs<T> a) {
     }
 }
 
+// MAXT: the block size bound the kernel is compiled for (256 or 512); the
+// register budget per thread follows from it.
+template <typename T, int MAXT>
+__global__ void __launch_bounds__(MAXT) sweep_kernel(const SweepArgs<T> a) {
+    sweep_body<T>(a, blockIdx.y, blockIdx.z);
+}
+
+// Batched sweep: cluster y of the grid runs work item items[y] = (problem,
+// ray, group) of problems args[]; every problem uses the launch's number of
+// bands.
+template <typename T, int MAXT>
+__global__ void __launch_bounds__(MAXT) sweep_batch_kernel(const SweepArgs<T> *__restrict__ args,
+                                                           const BatchItem *__restrict__ items) {
+    const BatchItem it = items[blockIdx.y];
+    const SweepArgs<T> a = args[it.member];
+    sweep_body<T>(a, it.group, it.ray);
+}
+
 __global__ void exp_check_kernel(int n, const double *__restrict__ x, double *__restrict__ out,
                                  const double *__restrict__ tab, double l1, double l2) {
     const ExpNegTable et{tab, l1, l2};
@@ -228,6 +243,43 @@ static cudaError_t launch_sweep_any(const SweepArgs<T> &a, const SweepShape &s,
                                     cudaStream_t st) {
     if (s.threads <= 256) return launch_sweep_t<T, 256>(a, s, st);
     return launch_sweep_t<T, 512>(a, s, st);
+}
+
+template <typename T, int MAXT>
+static cudaError_t launch_sweep_batch_t(const SweepArgs<T> *args, const BatchItem *items,
+                                        int n_items, int bands, int threads, size_t smem,
+                                        cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(sweep_batch_kernel<T, MAXT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(bands, n_items, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = bands;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, sweep_batch_kernel<T, MAXT>, args, items);
+}
+
+cudaError_t launch_sweep_batch(int prec, const void *args, const BatchItem *items, int n_items,
+                               int bands, int threads, size_t smem, cudaStream_t st) {
+    if (prec == 0)
+        return threads <= 256
+                   ? launch_sweep_batch_t<double, 256>((const SweepArgs<double> *)args, items,
+                                                       n_items, bands, threads, smem, st)
+                   : launch_sweep_batch_t<double, 512>((const SweepArgs<double> *)args, items,
+                                                       n_items, bands, threads, smem, st);
+    return threads <= 256
+               ? launch_sweep_batch_t<float, 256>((const SweepArgs<float> *)args, items, n_items,
+                                                  bands, threads, smem, st)
+               : launch_sweep_batch_t<float, 512>((const SweepArgs<float> *)args, items, n_items,
+                                                  bands, threads, smem, st);
 }
 
 cudaError_t launch_sweep_f64(const SweepArgs<double> &a, const SweepShape &s, cudaStream_t st) {

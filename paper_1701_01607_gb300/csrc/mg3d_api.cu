@@ -1172,6 +1172,366 @@ int create_ml_impl(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
     return MG3D_OK;
 }
 
+// ------------------------------------------------------------------- batches
+
+}  // namespace
+
+struct mg3d_batch {
+    int n = 0, L = 0, prec = 0;
+    mg3d_params params{};
+    std::vector<mg3d_handle *> m;
+    cudaStream_t stream = nullptr;
+    struct KindLevel {
+        std::vector<int> members;          // batch indices of this kind
+        int n_items = 0, bands = 0, threads = 0;
+        size_t smem = 0;
+        BatchItem *d_items = nullptr;
+        void *d_args = nullptr;
+    } two[MG3D_MAX_GRIDS + 1], ml[MG3D_MAX_GRIDS + 1];
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    long long launches = 0, delta_launches[2] = {0, 0};
+    double fs_units = 0, delta_units[2] = {0, 0};
+    // per member and level: sweeps and formal solutions one replay performs
+    std::vector<std::vector<int>> delta_sweeps[2], delta_fss[2];
+};
+
+namespace {
+
+int batch_launched(mg3d_batch *b, cudaError_t e, const char *what) {
+    ++b->launches;
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(MG3D_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    }
+    return MG3D_OK;
+}
+
+// Formal solution of level k for every member: per-member opacity, then one
+// batched sweep launch per atom kind.
+int batch_fs(mg3d_batch *b, int k) {
+    for (mg3d_handle *h : b->m) {
+        Level &L = h->lev[k];
+        if (h->kind == 1) {
+            MlOpacityArgs oa{L.nvox, h->nfreq_ml, h->N, h->prec, h->d_fi, h->theta_ref, h->t_ref,
+                             L.n, L.T, L.chi_c, L.saha, L.mchi, L.mS, L.msl, L.mfl};
+            MG_TRY(batch_launched(b, launch_ml_opacity(oa, b->stream), "batch opacity"));
+            b->fs_units += (double)L.nvox * kRays * h->nfreq_ml;
+        } else {
+            MG_TRY(batch_launched(b, launch_opacity(h->prec, L.nvox, h->atom.g_ratio,
+                                                    h->atom.kappa, L.n, L.chi0, L.S, b->stream),
+                                  "batch opacity"));
+            b->fs_units += (double)L.nvox * kRays * h->atom.n_freq;
+        }
+        ++h->fss[k];
+    }
+    mg3d_batch::KindLevel &t = b->two[k];
+    if (t.n_items)
+        MG_TRY(batch_launched(b, launch_sweep_batch(b->prec, t.d_args, t.d_items, t.n_items,
+                                                    t.bands, t.threads, t.smem, b->stream),
+                              "batched sweep"));
+    mg3d_batch::KindLevel &q = b->ml[k];
+    if (q.n_items)
+        MG_TRY(batch_launched(b, launch_ml_sweep_batch(b->prec, q.d_args, q.d_items, q.n_items,
+                                                       q.bands, q.threads, q.smem, b->stream),
+                              "batched multi-level sweep"));
+    return MG3D_OK;
+}
+
+int member_rates(mg3d_batch *b, mg3d_handle *h, int k, int mode, double *out, bool zero_rad,
+                 unsigned long long *scal) {
+    if (h->kind == 1) {
+        MlRateArgs a = ml_rate_args(h, k, mode);
+        a.out = out;
+        a.zero_radiation = zero_rad;
+        a.scal = scal;
+        return batch_launched(b, launch_ml_rates(a, b->stream), "batch rates");
+    }
+    RateArgs a = rate_args(h, k, mode);
+    a.out = out;
+    a.zero_radiation = zero_rad;
+    a.scal = scal;
+    return batch_launched(b, launch_rates(a, b->stream), "batch rates");
+}
+
+int batch_sweep(mg3d_batch *b, int k) {
+    MG_TRY(batch_fs(b, k));
+    for (mg3d_handle *h : b->m) {
+        MG_TRY(member_rates(b, h, k, kRateSolve, nullptr, false, h->scal));
+        ++h->sweeps[k];
+    }
+    return MG3D_OK;
+}
+
+int batch_vcycle(mg3d_batch *b, int k, bool first) {
+    const int nu_pre = (first && k == b->L) ? b->params.nu0 : b->params.nu1;
+    for (int i = 0; i < nu_pre; ++i) MG_TRY(batch_sweep(b, k));
+    MG_TRY(batch_fs(b, k));
+    for (mg3d_handle *h : b->m)
+        MG_TRY(member_rates(b, h, k, kRateResidual, h->lev[k].r, false, nullptr));
+    for (mg3d_handle *h : b->m) {
+        Level &F = h->lev[k];
+        Level &C = h->lev[k - 1];
+        MG_TRY(batch_launched(b, launch_restrict(h->N, F.nx, F.ny, F.nz, F.n, C.n, b->stream),
+                              "restrict n"));
+        MG_CUDA(cudaMemcpyAsync(C.n_before, C.n, (size_t)h->N * C.nvox * sizeof(double),
+                                cudaMemcpyDeviceToDevice, b->stream));
+        MG_TRY(batch_launched(b, launch_restrict(h->N, F.nx, F.ny, F.nz, F.r, C.f, b->stream),
+                              "restrict r"));
+        C.f_default = false;
+    }
+    MG_TRY(batch_fs(b, k - 1));
+    for (mg3d_handle *h : b->m)
+        MG_TRY(member_rates(b, h, k - 1, kRateAddW, h->lev[k - 1].f, false, nullptr));
+    if (k - 1 == 1) {
+        for (int i = 0; i < b->params.nu3; ++i) MG_TRY(batch_sweep(b, 1));
+    } else {
+        MG_TRY(batch_vcycle(b, k - 1, false));
+    }
+    for (mg3d_handle *h : b->m) {
+        Level &F = h->lev[k];
+        Level &C = h->lev[k - 1];
+        MG_TRY(batch_launched(b, launch_prolong_correct(h->N, C.nx, C.ny, C.nz, F.tz, C.n,
+                                                        C.n_before, F.n, h->scal, b->stream),
+                              "prolong correction"));
+    }
+    for (int i = 0; i < b->params.nu2; ++i) MG_TRY(batch_sweep(b, k));
+    return MG3D_OK;
+}
+
+int batch_cycle_work(mg3d_batch *b, bool first) {
+    for (mg3d_handle *h : b->m) {
+        Level &F = h->lev[h->L];
+        MG_CUDA(cudaMemcpyAsync(h->scratch, F.n, (size_t)h->N * F.nvox * sizeof(double),
+                                cudaMemcpyDeviceToDevice, b->stream));
+        F.f_default = true;
+        MG_CUDA(cudaMemsetAsync(h->scal, 0, 8 * sizeof(unsigned long long), b->stream));
+    }
+    MG_TRY(batch_vcycle(b, b->L, first));
+    for (mg3d_handle *h : b->m) {
+        Level &F = h->lev[h->L];
+        MG_TRY(batch_launched(b, launch_max_rel_change((long)h->N * F.nvox, F.n, h->scratch,
+                                                       h->scal + 4, b->stream),
+                              "max rel change"));
+    }
+    return MG3D_OK;
+}
+
+void batch_drop_graphs(mg3d_batch *b) {
+    for (auto &g : b->exec)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+// One batched V-cycle (captured once per variant, then replayed); C per
+// member into C[i] and the 10 % rule counts into neg[i].
+int batch_cycle(mg3d_batch *b, bool first, double *C, long long *neg) {
+    const int idx = first ? 1 : 0;
+    if (!b->exec[idx]) {
+        const long long l0 = b->launches;
+        const double u0 = b->fs_units;
+        std::vector<std::vector<int>> sw0(b->n), fs0(b->n);
+        for (int i = 0; i < b->n; ++i) {
+            sw0[i].assign(b->m[i]->sweeps, b->m[i]->sweeps + MG3D_MAX_GRIDS + 1);
+            fs0[i].assign(b->m[i]->fss, b->m[i]->fss + MG3D_MAX_GRIDS + 1);
+        }
+        MG_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed));
+        int rc = batch_cycle_work(b, first);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+        if (rc != MG3D_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return fail(MG3D_E_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&b->exec[idx], graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess)
+            return fail(MG3D_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        b->delta_launches[idx] = b->launches - l0;
+        b->delta_units[idx] = b->fs_units - u0;
+        b->launches = l0;
+        b->fs_units = u0;
+        b->delta_sweeps[idx].assign(b->n, std::vector<int>(MG3D_MAX_GRIDS + 1, 0));
+        b->delta_fss[idx].assign(b->n, std::vector<int>(MG3D_MAX_GRIDS + 1, 0));
+        for (int i = 0; i < b->n; ++i)
+            for (int k = 0; k <= MG3D_MAX_GRIDS; ++k) {
+                b->delta_sweeps[idx][i][k] = b->m[i]->sweeps[k] - sw0[i][k];
+                b->delta_fss[idx][i][k] = b->m[i]->fss[k] - fs0[i][k];
+                b->m[i]->sweeps[k] = sw0[i][k];
+                b->m[i]->fss[k] = fs0[i][k];
+            }
+    }
+    MG_CUDA(cudaGraphLaunch(b->exec[idx], b->stream));
+    b->launches += b->delta_launches[idx];
+    b->fs_units += b->delta_units[idx];
+    for (int i = 0; i < b->n; ++i)
+        for (int k = 0; k <= MG3D_MAX_GRIDS; ++k) {
+            b->m[i]->sweeps[k] += b->delta_sweeps[idx][i][k];
+            b->m[i]->fss[k] += b->delta_fss[idx][i][k];
+        }
+    MG_CUDA(cudaStreamSynchronize(b->stream));
+    bool bad = false;
+    for (int i = 0; i < b->n; ++i) {
+        unsigned long long sc[8];
+        MG_CUDA(cudaMemcpy(sc, b->m[i]->scal, sizeof(sc), cudaMemcpyDeviceToHost));
+        if (C) std::memcpy(&C[i], &sc[4], sizeof(double));
+        if (neg) neg[i] = (long long)sc[3];
+        if (sc[6]) bad = true;
+    }
+    if (bad) return fail(MG3D_E_DIVERGED, "non-finite populations after a batched V-cycle");
+    return MG3D_OK;
+}
+
+// Launch tables of level k: common bands and block size per kind, each
+// member's frequency grouping chosen to fit.
+int batch_build_level(mg3d_batch *b, int k) {
+    // two-level members
+    {
+        mg3d_batch::KindLevel &t = b->two[k];
+        int bands = kMaxBands;
+        for (int i : t.members) {
+            const Level &L = b->m[i]->lev[k];
+            int bmax = 0;
+            for (int bb = 1; bb <= kMaxBands && bb <= L.ny; ++bb) {
+                const int rows = (L.ny + bb - 1) / bb;
+                if ((long)(bb - 1) * rows < L.ny) bmax = bb;
+            }
+            bands = std::min(bands, bmax);
+        }
+        std::vector<BatchItem> items;
+        std::vector<unsigned char> args;
+        const size_t asz = b->prec == MG3D_PREC_F64 ? sizeof(SweepArgs<double>)
+                                                    : sizeof(SweepArgs<float>);
+        int threads = 32;
+        size_t smem = 0;
+        for (size_t j = 0; j < t.members.size(); ++j) {
+            mg3d_handle *h = b->m[t.members[j]];
+            Level &L = h->lev[k];
+            const int nf = h->atom.n_freq;
+            SweepShape s{};
+            for (int ng = std::min(nf, 3); ng >= 1; --ng) {
+                SweepShape c{ng, (nf + ng - 1) / ng, bands, (L.ny + bands - 1) / bands, 0};
+                if (sweep_smem_bytes(h->prec, c, L.nx) <= kMaxSweepSmem) {
+                    s = c;
+                    break;
+                }
+            }
+            if (s.ng == 0) return fail(MG3D_E_ARG, "batch member plane too large for the sweep");
+            s.threads = std::min(256, threads_for_band(s.rows * L.nx));
+            threads = std::max(threads, s.threads);
+            smem = std::max(smem, sweep_smem_bytes(h->prec, s, L.nx));
+            // partial buffers were sized for every level's shape before any
+            // table was built (see mg3d_batch_create)
+            if ((size_t)kRays * s.ngroups * (size_t)L.nvox > h->partial_elems)
+                return fail(MG3D_E_STATE, "batch member partial buffers too small");
+            L.shape = s;
+            drop_graphs(h);
+            for (int r = 0; r < kRays; ++r)
+                for (int g = 0; g < s.ngroups; ++g) items.push_back(BatchItem{(int)j, r, g});
+            args.resize(args.size() + asz);
+            unsigned char *dst = args.data() + args.size() - asz;
+            if (b->prec == MG3D_PREC_F64) {
+                SweepArgs<double> a{L.nx, L.ny, L.nz, nf, s.ng, s.ngroups, s.rows, h->up_mask,
+                                    (const double *)L.chi0, (const double *)L.S,
+                                    (const double *)L.bbot, L.geom, (const double *)h->d_phi,
+                                    (const double *)h->d_inv_phi, (const double *)h->d_wphi,
+                                    (double *)h->pj, (double *)h->pu, h->d_exp_tab, h->exp_l1,
+                                    h->exp_l2};
+                std::memcpy(dst, &a, asz);
+            } else {
+                SweepArgs<float> a{L.nx, L.ny, L.nz, nf, s.ng, s.ngroups, s.rows, h->up_mask,
+                                   (const float *)L.chi0, (const float *)L.S,
+                                   (const float *)L.bbot, L.geom, (const float *)h->d_phi,
+                                   (const float *)h->d_inv_phi, (const float *)h->d_wphi,
+                                   (float *)h->pj, (float *)h->pu, h->d_exp_tab, h->exp_l1,
+                                   h->exp_l2};
+                std::memcpy(dst, &a, asz);
+            }
+        }
+        if (items.size() > 65535) return fail(MG3D_E_ARG, "batch too large for one launch");
+        t.n_items = (int)items.size();
+        t.bands = bands;
+        t.threads = threads;
+        t.smem = smem;
+        if (t.n_items) {
+            MG_TRY(dev_alloc((void **)&t.d_items, items.size() * sizeof(BatchItem)));
+            MG_TRY(dev_alloc(&t.d_args, args.size()));
+            MG_CUDA(cudaMemcpy(t.d_items, items.data(), items.size() * sizeof(BatchItem),
+                               cudaMemcpyHostToDevice));
+            MG_CUDA(cudaMemcpy(t.d_args, args.data(), args.size(), cudaMemcpyHostToDevice));
+        }
+    }
+    // multi-level members
+    {
+        mg3d_batch::KindLevel &q = b->ml[k];
+        int bands = 0;
+        for (int bb = kMaxBands; bb >= 1 && !bands && !q.members.empty(); --bb) {
+            bool ok = true;
+            for (int i : q.members) {
+                const Level &L = b->m[i]->lev[k];
+                const int rows = (L.ny + bb - 1) / bb;
+                if (bb > L.ny || (long)(bb - 1) * rows >= L.ny ||
+                    ml_sweep_smem_bytes(b->prec, rows, L.nx) > kMaxSweepSmem)
+                    ok = false;
+            }
+            if (ok) bands = bb;
+        }
+        if (!q.members.empty() && !bands)
+            return fail(MG3D_E_ARG, "multi-level batch members need a common band count");
+        std::vector<BatchItem> items;
+        std::vector<unsigned char> args;
+        const size_t asz = b->prec == MG3D_PREC_F64 ? sizeof(MlSweepArgs<double>)
+                                                    : sizeof(MlSweepArgs<float>);
+        int threads = 32;
+        size_t smem = 0;
+        for (size_t j = 0; j < q.members.size(); ++j) {
+            mg3d_handle *h = b->m[q.members[j]];
+            Level &L = h->lev[k];
+            const int rows = (L.ny + bands - 1) / bands;
+            L.ml_bands = bands;
+            L.ml_rows = rows;
+            L.ml_threads = std::min(256, threads_for_band(rows * L.nx));
+            threads = std::max(threads, L.ml_threads);
+            smem = std::max(smem, ml_sweep_smem_bytes(h->prec, rows, L.nx));
+            drop_graphs(h);
+            for (int hemi = 0; hemi < 2; ++hemi)
+                for (int f = 0; f < h->nfreq_ml; ++f) items.push_back(BatchItem{(int)j, hemi, f});
+            args.resize(args.size() + asz);
+            unsigned char *dst = args.data() + args.size() - asz;
+            if (b->prec == MG3D_PREC_F64) {
+                MlSweepArgs<double> a{L.nx, L.ny, L.nz, h->nfreq_ml, rows,
+                                      (const double *)L.mchi, (const double *)L.mS,
+                                      (const double *)L.msl, (const double *)L.mfl,
+                                      (const double *)L.mib, L.geom, h->d_exp_tab, h->exp_l1,
+                                      h->exp_l2, (double *)h->ml_jx, (double *)h->ml_ux};
+                std::memcpy(dst, &a, asz);
+            } else {
+                MlSweepArgs<float> a{L.nx, L.ny, L.nz, h->nfreq_ml, rows,
+                                     (const float *)L.mchi, (const float *)L.mS,
+                                     (const float *)L.msl, (const float *)L.mfl,
+                                     (const float *)L.mib, L.geom, h->d_exp_tab, h->exp_l1,
+                                     h->exp_l2, (float *)h->ml_jx, (float *)h->ml_ux};
+                std::memcpy(dst, &a, asz);
+            }
+        }
+        if (items.size() > 65535) return fail(MG3D_E_ARG, "batch too large for one launch");
+        q.n_items = (int)items.size();
+        q.bands = bands;
+        q.threads = threads;
+        q.smem = smem;
+        if (q.n_items) {
+            MG_TRY(dev_alloc((void **)&q.d_items, items.size() * sizeof(BatchItem)));
+            MG_TRY(dev_alloc(&q.d_args, args.size()));
+            MG_CUDA(cudaMemcpy(q.d_items, items.data(), items.size() * sizeof(BatchItem),
+                               cudaMemcpyHostToDevice));
+            MG_CUDA(cudaMemcpy(q.d_args, args.data(), args.size(), cudaMemcpyHostToDevice));
+        }
+    }
+    return MG3D_OK;
+}
+
 }  // namespace
 
 namespace mg3d {
@@ -1317,6 +1677,170 @@ int mg3d_formal_solve_ml(mg3d_handle *h, int level, double *jx_host, double *ux_
         if (jx_host) jx_host[i] = j0 + j1;
         if (ux_host) ux_host[i] = u0 + u1;
     }
+    return MG3D_OK;
+}
+
+int mg3d_batch_create(int n, mg3d_handle *const *members, mg3d_batch **out) {
+    if (!out) return fail(MG3D_E_ARG, "null output pointer");
+    *out = nullptr;
+    if (n < 1 || !members) return fail(MG3D_E_ARG, "empty batch");
+    for (int i = 0; i < n; ++i) {
+        if (!members[i]) return fail(MG3D_E_ARG, "null member");
+        for (int j = 0; j < i; ++j)
+            if (members[j] == members[i]) return fail(MG3D_E_ARG, "member listed twice");
+    }
+    const mg3d_handle *h0 = members[0];
+    for (int i = 1; i < n; ++i) {
+        const mg3d_handle *h = members[i];
+        const mg3d_params &p = h->params, &q = h0->params;
+        if (h->L != h0->L || h->prec != h0->prec || p.nu0 != q.nu0 || p.nu1 != q.nu1 ||
+            p.nu2 != q.nu2 || p.nu3 != q.nu3 || p.nu_fmg != q.nu_fmg)
+            return fail(MG3D_E_ARG, "batch members need equal n_grids, precision and schedule");
+    }
+    mg3d_batch *b = new (std::nothrow) mg3d_batch();
+    if (!b) return fail(MG3D_E_OOM, "host allocation failed");
+    b->n = n;
+    b->L = h0->L;
+    b->prec = h0->prec;
+    b->params = h0->params;
+    b->m.assign(members, members + n);
+    int rc = MG3D_OK;
+    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) rc = fail(MG3D_E_CUDA, std::string("stream: ") + cudaGetErrorString(e));
+    for (int i = 0; i < n && rc == MG3D_OK; ++i) {
+        rc = mg3d_set_stream(b->m[i], b->stream);
+        for (int k = 1; k <= b->L; ++k)
+            (b->m[i]->kind == 1 ? b->ml[k] : b->two[k]).members.push_back(i);
+    }
+    // the largest partial buffer any level of a two-level member can need
+    // with at most three frequencies per block, allocated before any table
+    for (int i = 0; i < n && rc == MG3D_OK; ++i) {
+        mg3d_handle *h = b->m[i];
+        if (h->kind != 0) continue;
+        size_t need = 0;
+        for (int k = 1; k <= b->L; ++k)
+            need = std::max(need, (size_t)kRays * (size_t)h->atom.n_freq * (size_t)h->lev[k].nvox);
+        rc = ensure_partials(h, need);
+    }
+    for (int k = 1; k <= b->L && rc == MG3D_OK; ++k) rc = batch_build_level(b, k);
+    if (rc != MG3D_OK) {
+        std::string msg = g_last_error;
+        mg3d_batch_destroy(b);
+        g_last_error = msg;
+        return rc;
+    }
+    *out = b;
+    return MG3D_OK;
+}
+
+int mg3d_batch_destroy(mg3d_batch *b) {
+    if (!b) return MG3D_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_drop_graphs(b);
+    for (int k = 0; k <= MG3D_MAX_GRIDS; ++k)
+        for (auto *t : {&b->two[k], &b->ml[k]}) {
+            if (t->d_items) cudaFree(t->d_items);
+            if (t->d_args) cudaFree(t->d_args);
+        }
+    for (mg3d_handle *h : b->m) mg3d_set_stream(h, nullptr);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return MG3D_OK;
+}
+
+int mg3d_batch_fas_vcycle(mg3d_batch *b, int is_first, double *max_rel_change) {
+    if (!b) return fail(MG3D_E_ARG, "null batch");
+    if (b->L < 2) return fail(MG3D_E_STATE, "a V-cycle needs n_grids >= 2");
+    std::vector<long long> neg(b->n);
+    MG_TRY(batch_cycle(b, is_first != 0, max_rel_change, neg.data()));
+    for (int i = 0; i < b->n; ++i) b->m[i]->negatives += neg[i];
+    return MG3D_OK;
+}
+
+int mg3d_batch_fas_solve(mg3d_batch *b, double tol, int max_cycles, mg3d_stats *stats) {
+    if (!b) return fail(MG3D_E_ARG, "null batch");
+    if (b->L < 2) return fail(MG3D_E_STATE, "a V-cycle needs n_grids >= 2");
+    if (!(tol > 0.0) || max_cycles < 1) return fail(MG3D_E_ARG, "bad tol or max_cycles");
+    auto t0 = std::chrono::steady_clock::now();
+    for (mg3d_handle *h : b->m) {
+        begin_stats(h);
+        MG_TRY(zero_radiation(h, h->L));
+    }
+    std::vector<double> C(b->n, 1.0);
+    std::vector<int> done_at(b->n, 0);
+    int cyc = 0;
+    while (cyc < max_cycles) {
+        std::vector<long long> neg(b->n);
+        MG_TRY(batch_cycle(b, cyc == 0, C.data(), neg.data()));
+        ++cyc;
+        bool all = true;
+        for (int i = 0; i < b->n; ++i) {
+            b->m[i]->negatives += neg[i];
+            if (!done_at[i] && C[i] < tol) done_at[i] = cyc;
+            all = all && done_at[i];
+        }
+        if (all) break;
+    }
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    bool all = true;
+    for (int i = 0; i < b->n; ++i) {
+        if (stats) end_stats(b->m[i], &stats[i], done_at[i] ? done_at[i] : cyc, C[i], secs);
+        all = all && done_at[i];
+    }
+    if (!all) return fail(MG3D_E_MAXITER, "not every member reached tol");
+    return MG3D_OK;
+}
+
+int mg3d_batch_fmg_solve(mg3d_batch *b, double tol, int max_cycles, mg3d_stats *stats) {
+    if (!b) return fail(MG3D_E_ARG, "null batch");
+    if (b->L < 2) return fail(MG3D_E_STATE, "FMG needs n_grids >= 2");
+    if (!(tol > 0.0) || max_cycles < 1) return fail(MG3D_E_ARG, "bad tol or max_cycles");
+    auto t0 = std::chrono::steady_clock::now();
+    for (mg3d_handle *h : b->m) {
+        begin_stats(h);
+        MG_TRY(zero_radiation(h, 1));
+    }
+    for (int i = 0; i < b->params.nu_fmg; ++i) MG_TRY(batch_sweep(b, 1));
+    for (int k = 2; k <= b->L; ++k) {
+        for (mg3d_handle *h : b->m) {
+            Level &Fk = h->lev[k];
+            Level &Ck = h->lev[k - 1];
+            MG_TRY(batch_launched(b, launch_prolong(h->N, Ck.nx, Ck.ny, Ck.nz, Fk.tz, Ck.n, Fk.n,
+                                                    b->stream),
+                                  "prolong full approximation"));
+            Fk.f_default = true;
+        }
+        if (k < b->L) MG_TRY(batch_vcycle(b, k, false));
+    }
+    std::vector<double> C(b->n, 1.0);
+    std::vector<int> done_at(b->n, 0);
+    int cyc = 0;
+    while (cyc < max_cycles) {
+        std::vector<long long> neg(b->n);
+        MG_TRY(batch_cycle(b, cyc == 0, C.data(), neg.data()));
+        ++cyc;
+        bool all = true;
+        for (int i = 0; i < b->n; ++i) {
+            b->m[i]->negatives += neg[i];
+            if (!done_at[i] && C[i] < tol) done_at[i] = cyc;
+            all = all && done_at[i];
+        }
+        if (all) break;
+    }
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    bool all = true;
+    for (int i = 0; i < b->n; ++i) {
+        if (stats) end_stats(b->m[i], &stats[i], done_at[i] ? done_at[i] : cyc, C[i], secs);
+        all = all && done_at[i];
+    }
+    if (!all) return fail(MG3D_E_MAXITER, "not every member reached tol");
+    return MG3D_OK;
+}
+
+int mg3d_batch_counters(const mg3d_batch *b, long long *kernel_launches, double *fs_units) {
+    if (!b) return fail(MG3D_E_ARG, "null batch");
+    if (kernel_launches) *kernel_launches = b->launches;
+    if (fs_units) *fs_units = b->fs_units;
     return MG3D_OK;
 }
 

@@ -56,6 +56,14 @@ cudaError_t launch_exp_check(int n, const double *x, double *out, const double *
 
 size_t sweep_smem_bytes(int prec, const SweepShape &s, int nx);
 
+// One cluster of a batched sweep: problem index, ray (two-level) or
+// hemisphere (multi-level), frequency group (two-level) or frequency.
+struct BatchItem {
+    int member, ray, group;
+};
+cudaError_t launch_sweep_batch(int prec, const void *args, const BatchItem *items, int n_items,
+                               int bands, int threads, size_t smem, cudaStream_t st);
+
 // Kernel launchers; each returns the launch error.
 cudaError_t launch_opacity(int prec, long nvox, double g_ratio, double kappa,
                            const double *n, void *chi0, void *S, cudaStream_t st);
@@ -169,5 +177,8 @@ cudaError_t launch_ml_sweep_f64(const MlSweepArgs<double> &a, int bands, int thr
 cudaError_t launch_ml_sweep_f32(const MlSweepArgs<float> &a, int bands, int threads,
                                 cudaStream_t st);
 cudaError_t launch_ml_rates(const MlRateArgs &a, cudaStream_t st);
+cudaError_t launch_ml_sweep_batch(int prec, const void *args, const BatchItem *items,
+                                  int n_items, int bands, int threads, size_t smem,
+                                  cudaStream_t st);
 
 }  // namespace mg3d

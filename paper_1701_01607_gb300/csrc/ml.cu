@@ -107,12 +107,11 @@ __global__ void ml_bottom_kernel(long nplane, int nfreq, const FreqInfo *__restr
 
 // -------------------------------------------------------------------- sweep
 
-template <typename T, int MAXT>
-__global__ void __launch_bounds__(MAXT) ml_sweep_kernel(const MlSweepArgs<T> a) {
+template <typename T>
+__device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, int hemi) {
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
-    const int f = blockIdx.y;
-    const int hemi = blockIdx.z;     // 0: rays 0-11 (up), 1: rays 12-23 (down)
+    // hemi 0: rays 0-11 (up), 1: rays 12-23 (down)
     const bool up = hemi == 0;
     const int nx = a.nx, ny = a.ny, nz = a.nz, rows = a.rows;
     const int y0 = rank * rows;
@@ -201,6 +200,20 @@ __global__ void __launch_bounds__(MAXT) ml_sweep_kernel(const MlSweepArgs<T> a) 
     }
 }
 
+template <typename T, int MAXT>
+__global__ void __launch_bounds__(MAXT) ml_sweep_kernel(const MlSweepArgs<T> a) {
+    ml_sweep_body<T>(a, blockIdx.y, blockIdx.z);
+}
+
+// Batched: item y = (problem, hemisphere as ray, frequency as group).
+template <typename T, int MAXT>
+__global__ void __launch_bounds__(MAXT) ml_sweep_batch_kernel(
+    const MlSweepArgs<T> *__restrict__ args, const BatchItem *__restrict__ items) {
+    const BatchItem it = items[blockIdx.y];
+    const MlSweepArgs<T> a = args[it.member];
+    ml_sweep_body<T>(a, it.group, it.ray);
+}
+
 size_t ml_sweep_smem_bytes(int prec, int rows, int nx) {
     const size_t elem = prec == MG3D_PREC_F64 ? sizeof(double) : sizeof(float);
     return 2ull * 12 * rows * nx * elem;
@@ -227,6 +240,44 @@ static cudaError_t launch_ml_sweep_t(const MlSweepArgs<T> &a, int bands, int thr
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, ml_sweep_kernel<T, MAXT>, a);
+}
+
+template <typename T, int MAXT>
+static cudaError_t launch_ml_sweep_batch_t(const MlSweepArgs<T> *args, const BatchItem *items,
+                                           int n_items, int bands, int threads, size_t smem,
+                                           cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(ml_sweep_batch_kernel<T, MAXT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(bands, n_items, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = bands;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, ml_sweep_batch_kernel<T, MAXT>, args, items);
+}
+
+cudaError_t launch_ml_sweep_batch(int prec, const void *args, const BatchItem *items,
+                                  int n_items, int bands, int threads, size_t smem,
+                                  cudaStream_t st) {
+    if (prec == MG3D_PREC_F64)
+        return threads <= 256
+                   ? launch_ml_sweep_batch_t<double, 256>((const MlSweepArgs<double> *)args,
+                                                          items, n_items, bands, threads, smem, st)
+                   : launch_ml_sweep_batch_t<double, 512>((const MlSweepArgs<double> *)args,
+                                                          items, n_items, bands, threads, smem, st);
+    return threads <= 256
+               ? launch_ml_sweep_batch_t<float, 256>((const MlSweepArgs<float> *)args, items,
+                                                     n_items, bands, threads, smem, st)
+               : launch_ml_sweep_batch_t<float, 512>((const MlSweepArgs<float> *)args, items,
+                                                     n_items, bands, threads, smem, st);
 }
 
 cudaError_t launch_ml_sweep_f64(const MlSweepArgs<double> &a, int bands, int threads,

@@ -109,6 +109,13 @@ _SIGNATURES = {
     "mg3d_n_levels": (_I, [_H, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "mg3d_formal_solve_ml": (_I, [_H, _I, _D, _D]),
     "mg3d_destroy": (_I, [_H]),
+    "mg3d_batch_create": (_I, [_I, ctypes.POINTER(_H), ctypes.POINTER(_H)]),
+    "mg3d_batch_destroy": (_I, [_H]),
+    "mg3d_batch_fas_vcycle": (_I, [_H, _I, _D]),
+    "mg3d_batch_fas_solve": (_I, [_H, ctypes.c_double, _I, ctypes.POINTER(mg3d_stats)]),
+    "mg3d_batch_fmg_solve": (_I, [_H, ctypes.c_double, _I, ctypes.POINTER(mg3d_stats)]),
+    "mg3d_batch_counters": (_I, [_H, ctypes.POINTER(ctypes.c_longlong),
+                                 ctypes.POINTER(ctypes.c_double)]),
     "mg3d_set_stream": (_I, [_H, ctypes.c_void_p]),
     "mg3d_level_shape": (_I, [_H, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
                               ctypes.POINTER(_I)]),
@@ -423,3 +430,42 @@ def mg3d_formal_solve_noalloc(nx: int, ny: int, nz: int, dx: float, dy: float, z
     return load().mg3d_formal_solve_noalloc(nx, ny, nz, dx, dy, z_dev, ctypes.byref(at),
                                             quad_a, chi0_dev, S_dev, bbot_dev, jeff_dev,
                                             u_dev, stream_ptr)
+
+
+# ------------------------------------------------------------------ batches
+
+def mg3d_batch_create(handles):
+    arr = (_H * len(handles))(*[h.value if isinstance(h, _H) else h for h in handles])
+    b = _H()
+    _check(load().mg3d_batch_create(len(handles), arr, ctypes.byref(b)))
+    return b
+
+
+def mg3d_batch_destroy(b):
+    return _check(load().mg3d_batch_destroy(b))
+
+
+def mg3d_batch_fas_vcycle(b, n: int, is_first: bool = False):
+    c = np.empty(n)
+    _check(load().mg3d_batch_fas_vcycle(b, int(bool(is_first)), _dptr(c)))
+    return c
+
+
+def _batch_solve(fn, b, n, tol, cap, n_grids):
+    st = (mg3d_stats * n)()
+    _check(fn(b, tol, cap, st))
+    return [_stats_dict(st[i], n_grids) for i in range(n)]
+
+
+def mg3d_batch_fas_solve(b, n: int, tol: float, max_cycles: int = 1000, n_grids: int = 1):
+    return _batch_solve(load().mg3d_batch_fas_solve, b, n, tol, max_cycles, n_grids)
+
+
+def mg3d_batch_fmg_solve(b, n: int, tol: float, max_cycles: int = 1000, n_grids: int = 1):
+    return _batch_solve(load().mg3d_batch_fmg_solve, b, n, tol, max_cycles, n_grids)
+
+
+def mg3d_batch_counters(b):
+    l, u = ctypes.c_longlong(), ctypes.c_double()
+    _check(load().mg3d_batch_counters(b, ctypes.byref(l), ctypes.byref(u)))
+    return {"kernel_launches": l.value, "fs_units": u.value}
