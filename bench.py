@@ -56,6 +56,26 @@ def env_rank():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def replica_seed(rank: int) -> int:
+    """Seed of the atmosphere a rank solves: independent replicas, one per rank."""
+    return 1 + rank
+
+
+def aggregate_over_ranks(total_ms: float, units: float, dist=None, device=None):
+    """Whole-job figures of a replicated run: the slowest rank's time and the
+    units all ranks processed.  ``dist`` is torch.distributed (or None for a
+    single process); tensors live on ``device`` (cuda under NCCL, cpu under
+    gloo)."""
+    if dist is None:
+        return total_ms, units
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def build_problem(seed):
     from paper_1701_01607_gb300 import synth
     return synth.stratified_two_level(GRID[0], GRID[1], GRID[2], eps=1e-4, sigma=0.3,
@@ -127,7 +147,7 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     m.load(build_if_missing=True)
-    atm, atom = build_problem(seed=1 + rank)
+    atm, atom = build_problem(seed=replica_seed(rank))
     stream = torch.cuda.Stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
 
@@ -171,15 +191,7 @@ def run_gpu(args):
     ms, cnt = timed_cycles(h, args.steps, args.warmup, timing=True)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    total_ms = sum(ms)
-    units = cnt["fs_units"]
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        u = torch.tensor([units], device="cuda", dtype=torch.float64)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        units = float(u.item())
+    total_ms, units = aggregate_over_ranks(sum(ms), cnt["fs_units"], dist, "cuda")
     value = units / (total_ms * 1e-3) / 1e9
     fine = N_GRIDS
     fine_ms = cnt["level_fs_kernel_ms"][fine] / max(1, cnt["level_fs_timed_launches"][fine])
@@ -340,7 +352,7 @@ def run_reference(args):
 def run_profile_case(prec_name, launches, shape):
     """A few finest-grid formal solutions of the bench workload, for ncu.
 
-    ``shape`` "ng,bands,threads" fixes the sweep's launch shape (e.g. the one
+    ``shape`` "ng,bands,threads[,lean]" fixes the sweep's launch shape (e.g. the one
     the autotuner chose in a bench run); empty keeps the library default.
     No autotuning runs here, so every sweep launch is a profiled one."""
     from paper_1701_01607_gb300 import mg3d as m
@@ -350,8 +362,8 @@ def run_profile_case(prec_name, launches, shape):
     h = m.mg3d_create(atm, atom, n_grids=N_GRIDS, fs_prec=prec, **NU)
     try:
         if shape:
-            ng, bands, th = (int(v) for v in shape.split(","))
-            m.mg3d_set_fs_config(h, N_GRIDS, ng, bands, th)
+            vals = [int(v) for v in shape.split(",")]
+            m.mg3d_set_fs_config(h, N_GRIDS, *vals)
         for _ in range(launches):
             m.mg3d_formal_solve(h, N_GRIDS, want=False)
         print("profile case:", prec_name, m.mg3d_get_fs_config(h, N_GRIDS), flush=True)
@@ -372,7 +384,8 @@ def main():
     ap.add_argument("--profile-sweep", choices=["f64", "f32"],
                     help="only run a few finest-grid formal solutions (for ncu)")
     ap.add_argument("--profile-launches", type=int, default=3)
-    ap.add_argument("--profile-shape", default="", help="ng,bands,threads of the profiled sweep")
+    ap.add_argument("--profile-shape", default="",
+                    help="ng,bands,threads[,lean] of the profiled sweep")
     args = ap.parse_args()
     if args.profile_sweep:
         run_profile_case(args.profile_sweep, args.profile_launches, args.profile_shape)

@@ -98,7 +98,14 @@ typedef struct {
     int nu2;       /* post-smoothing iterations */
     int nu3;       /* iterations on the coarsest grid */
     int fs_prec;   /* MG3D_PREC_F64 or MG3D_PREC_F32 */
+    int restriction; /* of populations and residuals (Sec. 4.4):
+                        MG3D_RESTRICT_FULL (the paper's choice), _HALF, _INJECT;
+                        the atmosphere is always full-weighted (Sec. 4.7) */
 } mg3d_params;
+
+#define MG3D_RESTRICT_FULL 0    /* 27-node full weighting */
+#define MG3D_RESTRICT_HALF 1    /* centre 1/2, six axis neighbours 1/12 */
+#define MG3D_RESTRICT_INJECT 2  /* coarse node takes the fine node's value */
 
 /* Outcome of a solve. */
 typedef struct {
@@ -306,7 +313,7 @@ int mg3d_batch_fmg_solve(mg3d_batch *b, double tol, int max_cycles, mg3d_stats *
 int mg3d_batch_counters(const mg3d_batch *b, long long *kernel_launches, double *fs_units);
 
 /* Grid-transfer operators on host arrays of ncomp fields, for checking.
- * mg3d_restrict: full weighting (Sec. 4.4) from level_fine to level_fine-1,
+ * mg3d_restrict: the handle's restriction (Sec. 4.4) from level_fine to level_fine-1,
  * fine_host [ncomp][fine nodes] -> coarse_host [ncomp][coarse nodes].
  * mg3d_prolong: trilinear interpolation (Sec. 4.5) from level_fine-1 to
  * level_fine.  1 <= ncomp <= 4. */
@@ -315,20 +322,23 @@ int mg3d_restrict(mg3d_handle *h, int level_fine, int ncomp, const double *fine_
 int mg3d_prolong(mg3d_handle *h, int level_fine, int ncomp, const double *coarse_host,
                  double *fine_host);
 
-/* Sweep launch shape of a level: freq_per_block frequencies per thread block,
- * bands = thread blocks (one cluster) sharing each horizontal plane, threads
- * per block.  The library picks one at creation; this overrides it.
- * Returns MG3D_E_ARG if the shape does not fit in shared memory. */
+/* Sweep launch shape of a level (two-level handles): freq_per_block
+ * frequencies per thread block, bands = thread blocks (one cluster) sharing
+ * each horizontal plane, threads per block (32..512, a multiple of 32), and
+ * lean = 1 for the kernel variant compiled for 1024 resident threads per SM
+ * (64 registers per thread), 0 for the one with the full register budget.
+ * The library picks a shape at creation; this overrides it.  Returns
+ * MG3D_E_ARG if the shape does not fit in shared memory. */
 int mg3d_set_fs_config(mg3d_handle *h, int level, int freq_per_block, int bands,
-                       int threads);
+                       int threads, int lean);
 int mg3d_get_fs_config(const mg3d_handle *h, int level, int *freq_per_block, int *bands,
-                       int *threads);
+                       int *threads, int *lean);
 
 /* Autotuner: times candidate sweep shapes on this GPU with the level's current
  * populations and keeps the fastest per level (level = 0: every level).
- * Candidates: every number of frequency groups up to 64, 1-8 bands and
- * 128/256/512 threads that fit; one launch each, then the best eight three
- * more times.  Overwrites the partial sums (not the populations).
+ * Candidates: every number of frequency groups up to 64, 1-8 bands,
+ * 128/256/512 threads and both register budgets that fit; one launch each,
+ * then the best eight three more times.  Overwrites the partial sums (not the populations).
  * *evaluated and *seconds (nullable) report the candidates and wall time. */
 int mg3d_autotune(mg3d_handle *h, int level, int *evaluated, double *seconds);
 

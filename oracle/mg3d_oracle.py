@@ -208,9 +208,11 @@ class TwoLevelProblem:
     Populations are arrays [2, nz, ny, nx]: index 0 lower, 1 upper level.
     """
 
-    def __init__(self, atm, atom, n_grids: int = 1, quad_a: float | None = None):
+    def __init__(self, atm, atom, n_grids: int = 1, quad_a: float | None = None,
+                 restriction: int = 0):
         self.atom = atom
         self.n_grids = n_grids
+        self.restriction = restriction
         self.mu, self.wray = a4_quadrature(quad_a)
         self.x, self.phi, self.wphi = frequency_grid(atom.n_freq, atom.x_max)
         fine = Level(atm.nx, atm.ny, atm.nz, atm.dx, atm.dy, np.asarray(atm.z, float),
@@ -335,6 +337,13 @@ class TwoLevelProblem:
 
     # ---- multigrid (Secs. 2.2-2.3) ----
     def restrict(self, k_fine: int, a):
+        """Restriction of populations and residuals: full weighting (the
+        paper's choice) unless half weighting or injection was selected; the
+        atmosphere is always full-weighted (Sec. 4.7)."""
+        if getattr(self, "restriction", 0) == 1:
+            return restrict_hw(a)
+        if getattr(self, "restriction", 0) == 2:
+            return restrict_inj(a)
         return restrict_fw(a)
 
     def prolong(self, k_fine: int, a_coarse):
@@ -388,6 +397,44 @@ def max_rel_error(n, n_ref):
 # --------------------------------------------------------------------------
 # Grid transfer (Sec. 4.1, 4.4-4.7)
 # --------------------------------------------------------------------------
+
+def restrict_hw(a):
+    """Half weighting of [..., nz, ny, nx] onto every second node (Sec. 4.4).
+
+    Coarse node (K, J, I) on fine node (2K, 2J, 2I) takes 1/2 of the centre
+    and 1/12 of each of its six axis neighbours (x, y periodic).  On the two
+    fixed boundary planes only the plane itself is used: 1/2 of the centre
+    and 1/8 of each of its four in-plane neighbours.
+    """
+    a = np.asarray(a, dtype=np.float64)
+    nz, ny, nx = a.shape[-3:]
+    if nz % 2 != 1 or ny % 2 or nx % 2:
+        raise ValueError("grid does not coarsen")
+    nzc = (nz + 1) // 2
+    zi = 2 * np.arange(nzc)
+    c = a[..., zi, ::2, ::2]
+    xm = np.roll(a, 1, axis=-1)[..., zi, ::2, ::2]
+    xp = np.roll(a, -1, axis=-1)[..., zi, ::2, ::2]
+    ym = np.roll(a, 1, axis=-2)[..., zi, ::2, ::2]
+    yp = np.roll(a, -1, axis=-2)[..., zi, ::2, ::2]
+    out = 0.5 * c + (xm + xp + ym + yp) / 12.0
+    zm = a[..., np.clip(zi - 1, 0, nz - 1), ::2, ::2]
+    zp = a[..., np.clip(zi + 1, 0, nz - 1), ::2, ::2]
+    out += (zm + zp) / 12.0
+    for K in (0, nzc - 1):
+        out[..., K, :, :] = 0.5 * c[..., K, :, :] + (xm[..., K, :, :] + xp[..., K, :, :] +
+                                                      ym[..., K, :, :] + yp[..., K, :, :]) / 8.0
+    return out
+
+
+def restrict_inj(a):
+    """Injection (Sec. 4.4): the coarse node takes the fine node's value."""
+    a = np.asarray(a, dtype=np.float64)
+    return a[..., ::2, ::2, ::2].copy()
+
+
+RESTRICTIONS = {0: None, 1: restrict_hw, 2: restrict_inj}
+
 
 def restrict_fw(a):
     """Full weighting of [..., nz, ny, nx] onto every second node.
@@ -622,8 +669,10 @@ class MultiLevelProblem(TwoLevelProblem):
     qe = qa G E (rho y)^3.
     """
 
-    def __init__(self, atm, atom, n_grids: int = 1, quad_a: float | None = None):
+    def __init__(self, atm, atom, n_grids: int = 1, quad_a: float | None = None,
+                 restriction: int = 0):
         self.atom = atom
+        self.restriction = restriction
         self.N = atom.n_levels
         self.n_grids = n_grids
         self.mu, self.wray = a4_quadrature(quad_a)

@@ -24,6 +24,7 @@
 // and stores it into a partial slot (ray, group); the rate kernel adds the
 // slots in a fixed order, so results are deterministic.
 #include <cooperative_groups.h>
+#include <cuda_pipeline.h>
 
 #include <cmath>
 
@@ -55,6 +56,42 @@ __global__ void planck_bottom_kernel(long nplane, double theta, const double *__
         bbot[p] = (T)(1.0 / expm1(theta / Tgas[p]));
 }
 
+// Shared-memory layout of one block (elements of T):
+//   I planes      [2][ng][rows][nx]           plane k-1 read, plane k written
+//   staging       [2][2][2 rows + 1][nx]      per step: chi0 and S of the
+//                 upwind window (rows + 1 rows of plane k-1, shifted by the
+//                 step's row offset) then of the block's own rows of plane k
+//   tables        [3][ng]                     phi, 1/phi, w phi of the group
+// Staging for step t+1 is copied asynchronously while step t computes.
+__host__ __device__ inline long sweep_stage_elems(int rows, int nx) {
+    return 2L * (2 * rows + 1) * nx;
+}
+
+template <typename T>
+__device__ __forceinline__ void stage_rows(const SweepArgs<T> &a, T *dst, long arr_stride,
+                                           int plane, int row0, int nrows, bool wrap,
+                                           bool vec16) {
+    // rows row0 .. row0+nrows-1 of `plane` (mod ny when wrap) of chi0 into
+    // dst and of S into dst + arr_stride
+    const int nx = a.nx, ny = a.ny;
+    const long nplane = (long)nx * ny;
+    const int per_row = vec16 ? (int)(nx * sizeof(T) / 16) : nx;
+    const int total = 2 * nrows * per_row;
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        const int arr = i / (nrows * per_row);
+        const int rem = i - arr * nrows * per_row;
+        const int j = rem / per_row, c = rem - j * per_row;
+        int row = row0 + j;
+        if (wrap && row >= ny) row -= ny;
+        const T *src = (arr == 0 ? a.chi0 : a.S) + (long)plane * nplane + (long)row * nx;
+        T *d = dst + arr * arr_stride + (long)j * nx;
+        if (vec16)
+            __pipeline_memcpy_async(d + c * (16 / sizeof(T)), src + c * (16 / sizeof(T)), 16);
+        else
+            __pipeline_memcpy_async(d + c, src + c, sizeof(T));
+    }
+}
+
 // Body of the sweep for ray r and frequency group g of one problem.
 template <typename T>
 __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) {
@@ -76,12 +113,36 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf = reinterpret_cast<T *>(smem_raw);
     const long bufstride = (long)a.ng * rows * nx;
-    __shared__ double exp_tab[64];
-    if (sizeof(T) == 8) {
-        for (int i = threadIdx.x; i < 64; i += blockDim.x) exp_tab[i] = a.exp_tab[i];
-        __syncthreads();
+    T *stage = buf + 2 * bufstride;
+    const long stagestride = sweep_stage_elems(rows, nx);
+    T *tabs = stage + 2 * stagestride;
+    T *phi = tabs, *inv_phi = tabs + a.ng, *wphi = tabs + 2 * a.ng;
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+        phi[i] = a.phi[f0 + i];
+        inv_phi[i] = a.inv_phi[f0 + i];
+        wphi[i] = a.wphi[f0 + i];
     }
+    __shared__ double exp_tab[64];
+    if (sizeof(T) == 8)
+        for (int i = threadIdx.x; i < 64; i += blockDim.x) exp_tab[i] = a.exp_tab[i];
+    __syncthreads();
     const ExpNegTable et{exp_tab, a.exp_l1, a.exp_l2};
+    const bool vec16 = (nx * sizeof(T)) % 16 == 0;
+
+    // stage the window and band of step t into staging buffer t & 1
+    auto stage_step = [&](int t) {
+        const int k = up ? t : nz - 1 - t;
+        const int kp = up ? k - 1 : k + 1;
+        const StepGeom o = a.geom[(long)r * nz + t];
+        T *dst = stage + (t & 1) * stagestride;
+        int w0 = y0 + o.iy0;
+        if (w0 >= ny) w0 -= ny;
+        stage_rows<T>(a, dst, (long)(rows + 1) * nx, kp, w0, myrows + 1, true, vec16);
+        stage_rows<T>(a, dst + 2L * (rows + 1) * nx, (long)rows * nx, k, y0, myrows, false,
+                      vec16);
+        __pipeline_commit();
+    };
+    if (nz > 1) stage_step(1);
 
     for (int t = 0; t < nz; ++t) {
         const int k = up ? t : nz - 1 - t;
@@ -96,7 +157,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
                 T cj = 0, cu = 0;
                 for (int f = 0; f < nf; ++f) {
                     cur[((long)f * rows + yl) * nx + x] = Ib;
-                    const T w = a.wphi[f0 + f];
+                    const T w = wphi[f];
                     cj += w * Ib;
                     cu += w;
                 }
@@ -105,15 +166,18 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
                 pu[v] = cu;
             }
         } else {
+            __pipeline_wait_prior(0);
+            __syncthreads();
+            if (t + 1 < nz) stage_step(t + 1);
+            const T *st = stage + (t & 1) * stagestride;
+            const T *chiW = st, *SW = st + (long)(rows + 1) * nx;
+            const T *chiB = st + 2L * (rows + 1) * nx, *SB = chiB + (long)rows * nx;
             const T *prev = buf + ((t - 1) & 1) * bufstride;
             const StepGeom o = a.geom[(long)r * nz + t];
-            const int kp = up ? k - 1 : k + 1;
             const T tx = (T)o.tx, ty = (T)o.ty;
             const T half_s = (T)(0.5 * o.s);
             const T w00 = (T(1) - tx) * (T(1) - ty), w10 = tx * (T(1) - ty);
             const T w01 = (T(1) - tx) * ty, w11 = tx * ty;
-            const T *__restrict__ chip = a.chi0 + (long)kp * nplane;
-            const T *__restrict__ Sp = a.S + (long)kp * nplane;
             for (int q = threadIdx.x; q < band; q += blockDim.x) {
                 const int yl = q / nx, x = q - yl * nx;
                 const int y = y0 + yl;
@@ -123,14 +187,13 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
                 int ya = y + o.iy0;
                 if (ya >= ny) ya -= ny;
                 const int yb = (ya + 1 == ny) ? 0 : ya + 1;
-                const long ra = (long)ya * nx, rb = (long)yb * nx;
-                const T chi_up = w00 * chip[ra + xa] + w10 * chip[ra + xb] +
-                                 w01 * chip[rb + xa] + w11 * chip[rb + xb];
-                const T S_up = w00 * Sp[ra + xa] + w10 * Sp[ra + xb] + w01 * Sp[rb + xa] +
-                               w11 * Sp[rb + xb];
-                const long v = (long)k * nplane + (long)y * nx + x;
-                const T chi_loc = a.chi0[v];
-                const T S_loc = a.S[v];
+                // window row yl holds row ya, row yl + 1 holds yb
+                const T *ca = chiW + (long)yl * nx, *cb = ca + nx;
+                const T *sa = SW + (long)yl * nx, *sb = sa + nx;
+                const T chi_up = w00 * ca[xa] + w10 * ca[xb] + w01 * cb[xa] + w11 * cb[xb];
+                const T S_up = w00 * sa[xa] + w10 * sa[xb] + w01 * sb[xa] + w11 * sb[xb];
+                const T chi_loc = chiB[(long)yl * nx + x];
+                const T S_loc = SB[(long)yl * nx + x];
                 const T dtau0 = (chi_up + chi_loc) * half_s;
                 // 1/dtau0 is only used where dtau0 phi >= the series threshold,
                 // so dtau0 > 0 there
@@ -147,14 +210,15 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
                     const T I_up = w00 * Pa[off + xa] + w10 * Pa[off + xb] +
                                    w01 * Pb[off + xa] + w11 * Pb[off + xb];
                     T ex, w0, wup, u;
-                    ScWeights<T>::eval(dtau0 * a.phi[f0 + f], inv_dtau0 * a.inv_phi[f0 + f],
-                                       et, ex, w0, wup, u);
+                    ScWeights<T>::eval(dtau0 * phi[f], inv_dtau0 * inv_phi[f], et, ex, w0, wup,
+                                       u);
                     const T part = I_up * ex + wup * S_up;
                     cur[((long)f * rows + yl) * nx + x] = part + w0 * S_loc;
-                    const T w = a.wphi[f0 + f];
+                    const T w = wphi[f];
                     cj += w * part;
                     cu += w * u;
                 }
+                const long v = (long)k * nplane + (long)y * nx + x;
                 pj[v] = cj;
                 pu[v] = cu;
             }
@@ -165,10 +229,11 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
     }
 }
 
-// MAXT: the block size bound the kernel is compiled for (256 or 512); the
-// register budget per thread follows from it.
-template <typename T, int MAXT>
-__global__ void __launch_bounds__(MAXT) sweep_kernel(const SweepArgs<T> a) {
+// MAXT: the block size bound the kernel is compiled for (256 or 512); MINB:
+// blocks per SM it must fit, which sets the register budget (MINB = 1: up to
+// 255 registers; MINB = 1024/MAXT: 64 registers, 32 resident warps per SM).
+template <typename T, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) sweep_kernel(const SweepArgs<T> a) {
     sweep_body<T>(a, blockIdx.y, blockIdx.z);
 }
 
@@ -176,8 +241,8 @@ __global__ void __launch_bounds__(MAXT) sweep_kernel(const SweepArgs<T> a) {
 // ray, group) of problems args[]; every problem uses the launch's number of
 // bands.
 template <typename T, int MAXT>
-__global__ void __launch_bounds__(MAXT) sweep_batch_kernel(const SweepArgs<T> *__restrict__ args,
-                                                           const BatchItem *__restrict__ items) {
+__global__ void __launch_bounds__(MAXT, 1024 / MAXT) sweep_batch_kernel(
+    const SweepArgs<T> *__restrict__ args, const BatchItem *__restrict__ items) {
     const BatchItem it = items[blockIdx.y];
     const SweepArgs<T> a = args[it.member];
     sweep_body<T>(a, it.group, it.ray);
@@ -212,14 +277,14 @@ void exp_neg_constants(double *tab64, double *l1, double *l2) {
 
 size_t sweep_smem_bytes(int prec, const SweepShape &s, int nx) {
     size_t elem = prec == 0 ? sizeof(double) : sizeof(float);
-    return 2ull * s.ng * s.rows * nx * elem;
+    return (2ull * s.ng * s.rows * nx + 2ull * sweep_stage_elems(s.rows, nx) + 3ull * s.ng) * elem;
 }
 
-template <typename T, int MAXT>
+template <typename T, int MAXT, int MINB>
 static cudaError_t launch_sweep_t(const SweepArgs<T> &a, const SweepShape &s,
                                   cudaStream_t st) {
     size_t smem = sweep_smem_bytes(sizeof(T) == 8 ? 0 : 1, s, a.nx);
-    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, MAXT>,
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, MAXT, MINB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -235,14 +300,15 @@ static cudaError_t launch_sweep_t(const SweepArgs<T> &a, const SweepShape &s,
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, sweep_kernel<T, MAXT>, a);
+    return cudaLaunchKernelEx(&cfg, sweep_kernel<T, MAXT, MINB>, a);
 }
 
 template <typename T>
 static cudaError_t launch_sweep_any(const SweepArgs<T> &a, const SweepShape &s,
                                     cudaStream_t st) {
-    if (s.threads <= 256) return launch_sweep_t<T, 256>(a, s, st);
-    return launch_sweep_t<T, 512>(a, s, st);
+    if (s.threads <= 256)
+        return s.lean ? launch_sweep_t<T, 256, 4>(a, s, st) : launch_sweep_t<T, 256, 1>(a, s, st);
+    return s.lean ? launch_sweep_t<T, 512, 2>(a, s, st) : launch_sweep_t<T, 512, 1>(a, s, st);
 }
 
 template <typename T, int MAXT>

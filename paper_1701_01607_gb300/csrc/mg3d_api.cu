@@ -532,11 +532,13 @@ int vcycle(mg3d_handle *h, int k, bool first) {
     // residual with an extra formal solution (Eq. 5)
     MG_TRY(apply_W(h, k, kRateResidual, F.r));
     // coarse-grid equation (Eq. 9)
-    MG_TRY(launched(h, launch_restrict(h->N, F.nx, F.ny, F.nz, F.n, C.n, h->stream),
+    MG_TRY(launched(h, launch_restrict(h->N, F.nx, F.ny, F.nz, F.n, C.n, h->stream,
+                                       h->params.restriction),
                     "restrict n"));
     MG_CUDA(cudaMemcpyAsync(C.n_before, C.n, (size_t)h->N * C.nvox * sizeof(double),
                             cudaMemcpyDeviceToDevice, h->stream));
-    MG_TRY(launched(h, launch_restrict(h->N, F.nx, F.ny, F.nz, F.r, C.f, h->stream),
+    MG_TRY(launched(h, launch_restrict(h->N, F.nx, F.ny, F.nz, F.r, C.f, h->stream,
+                                       h->params.restriction),
                     "restrict r"));
     C.f_default = false;
     MG_TRY(apply_W(h, k - 1, kRateAddW, C.f));
@@ -810,15 +812,18 @@ int autotune_level(mg3d_handle *h, int k, int *evaluated) {
     std::vector<SweepShape> cands;
     for (int ng : ngs)
         for (int bands = 1; bands <= kMaxBands && bands <= L.ny; ++bands)
-            for (int th : {128, 256, 512}) {
-                SweepShape s;
-                if (make_shape(h, k, ng, bands, th, &s) != MG3D_OK) continue;
-                const int band = s.rows * L.nx;
-                if (th > 128 && th / 2 >= band) continue;  // a smaller block covers the band
-                cands.push_back(s);
-            }
+            for (int th : {128, 256, 512})
+                for (int lean = 0; lean < 2; ++lean) {
+                    SweepShape s;
+                    if (make_shape(h, k, ng, bands, th, &s) != MG3D_OK) continue;
+                    const int band = s.rows * L.nx;
+                    if (th > 128 && th / 2 >= band) continue;  // a smaller block covers the band
+                    s.lean = lean;
+                    cands.push_back(s);
+                }
     g_last_error.clear();
     if (cands.empty()) return fail(MG3D_E_ARG, "no sweep shape fits");
+    (void)0;
     size_t need = 0;
     for (auto &s : cands) need = std::max(need, (size_t)kRays * s.ngroups * (size_t)L.nvox);
     MG_TRY(ensure_partials(h, need));
@@ -1271,11 +1276,13 @@ int batch_vcycle(mg3d_batch *b, int k, bool first) {
     for (mg3d_handle *h : b->m) {
         Level &F = h->lev[k];
         Level &C = h->lev[k - 1];
-        MG_TRY(batch_launched(b, launch_restrict(h->N, F.nx, F.ny, F.nz, F.n, C.n, b->stream),
+        MG_TRY(batch_launched(b, launch_restrict(h->N, F.nx, F.ny, F.nz, F.n, C.n, b->stream,
+                                                 h->params.restriction),
                               "restrict n"));
         MG_CUDA(cudaMemcpyAsync(C.n_before, C.n, (size_t)h->N * C.nvox * sizeof(double),
                                 cudaMemcpyDeviceToDevice, b->stream));
-        MG_TRY(batch_launched(b, launch_restrict(h->N, F.nx, F.ny, F.nz, F.r, C.f, b->stream),
+        MG_TRY(batch_launched(b, launch_restrict(h->N, F.nx, F.ny, F.nz, F.r, C.f, b->stream,
+                                                 h->params.restriction),
                               "restrict r"));
         C.f_default = false;
     }
@@ -1558,6 +1565,8 @@ int mg3d_create(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_qu
     if (params->nu_fmg < 0 || params->nu0 < 0 || params->nu1 < 0 || params->nu2 < 0 ||
         params->nu3 < 0)
         return fail(MG3D_E_ARG, "negative iteration count");
+    if (params->restriction < 0 || params->restriction > 2)
+        return fail(MG3D_E_ARG, "restriction must be 0, 1 or 2");
     if (atom->n_freq < 1 || atom->n_freq > 4096 || !(atom->x_max >= 0.0) ||
         !(atom->a_ul > 0.0) || !(atom->g_ratio > 0.0) || !(atom->theta > 0.0) ||
         !(atom->kappa > 0.0))
@@ -1623,6 +1632,8 @@ int mg3d_create_ml(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
     if (params->nu_fmg < 0 || params->nu0 < 0 || params->nu1 < 0 || params->nu2 < 0 ||
         params->nu3 < 0)
         return fail(MG3D_E_ARG, "negative iteration count");
+    if (params->restriction < 0 || params->restriction > 2)
+        return fail(MG3D_E_ARG, "restriction must be 0, 1 or 2");
     if (atm->nx < 1 || atm->ny < 1 || atm->nz < 2) return fail(MG3D_E_ARG, "grid too small");
     if (!(atm->dx > 0.0) || !(atm->dy > 0.0)) return fail(MG3D_E_ARG, "dx, dy must be > 0");
     for (int k = 1; k < atm->nz; ++k)
@@ -1694,7 +1705,8 @@ int mg3d_batch_create(int n, mg3d_handle *const *members, mg3d_batch **out) {
         const mg3d_handle *h = members[i];
         const mg3d_params &p = h->params, &q = h0->params;
         if (h->L != h0->L || h->prec != h0->prec || p.nu0 != q.nu0 || p.nu1 != q.nu1 ||
-            p.nu2 != q.nu2 || p.nu3 != q.nu3 || p.nu_fmg != q.nu_fmg)
+            p.nu2 != q.nu2 || p.nu3 != q.nu3 || p.nu_fmg != q.nu_fmg ||
+            p.restriction != q.restriction)
             return fail(MG3D_E_ARG, "batch members need equal n_grids, precision and schedule");
     }
     mg3d_batch *b = new (std::nothrow) mg3d_batch();
@@ -2041,7 +2053,8 @@ int mg3d_restrict(mg3d_handle *h, int level_fine, int ncomp, const double *fine_
     int rc = dalloc(&dcoarse, (size_t)ncomp * C.nvox);
     if (rc == MG3D_OK) rc = host_to_level(h, dfine, fine_host, (size_t)ncomp * F.nvox);
     if (rc == MG3D_OK)
-        rc = launched(h, launch_restrict(ncomp, F.nx, F.ny, F.nz, dfine, dcoarse, h->stream),
+        rc = launched(h, launch_restrict(ncomp, F.nx, F.ny, F.nz, dfine, dcoarse, h->stream,
+                                         h->params.restriction),
                       "restrict");
     if (rc == MG3D_OK) rc = level_to_host(h, coarse_host, dcoarse, (size_t)ncomp * C.nvox);
     cudaFree(dfine);
@@ -2069,11 +2082,13 @@ int mg3d_prolong(mg3d_handle *h, int level_fine, int ncomp, const double *coarse
     return rc;
 }
 
-int mg3d_set_fs_config(mg3d_handle *h, int level, int freq_per_block, int bands, int threads) {
+int mg3d_set_fs_config(mg3d_handle *h, int level, int freq_per_block, int bands, int threads,
+                       int lean) {
     MG_TRY(check_level(h, level));
     if (h->kind != 0) return fail(MG3D_E_STATE, "sweep shapes apply to two-level handles");
     SweepShape s;
     MG_TRY(make_shape(h, level, freq_per_block, bands, threads, &s));
+    s.lean = lean != 0;
     MG_CUDA(cudaStreamSynchronize(h->stream));
     MG_TRY(ensure_partials(h, (size_t)kRays * s.ngroups * (size_t)h->lev[level].nvox));
     h->lev[level].shape = s;
@@ -2101,12 +2116,13 @@ int mg3d_autotune(mg3d_handle *h, int level, int *evaluated, double *seconds) {
 }
 
 int mg3d_get_fs_config(const mg3d_handle *h, int level, int *freq_per_block, int *bands,
-                       int *threads) {
+                       int *threads, int *lean) {
     MG_TRY(check_level(h, level));
     const Level &L = h->lev[level];
     if (freq_per_block) *freq_per_block = L.shape.ng;
     if (bands) *bands = L.shape.bands;
     if (threads) *threads = L.shape.threads;
+    if (lean) *lean = L.shape.lean;
     return MG3D_OK;
 }
 

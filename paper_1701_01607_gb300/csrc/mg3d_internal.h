@@ -29,6 +29,7 @@ struct SweepShape {
     int bands;    // thread blocks per cluster; each holds `rows` rows
     int rows;     // ceil(ny / bands)
     int threads;  // threads per block
+    int lean = 0; // 1: kernel compiled for 1024 resident threads per SM (64 registers)
 };
 
 // Arguments of the sweep kernel.  T is the formal-solution precision.
@@ -99,8 +100,9 @@ cudaError_t launch_rates(const RateArgs &a, cudaStream_t st);
 
 cudaError_t launch_collisions_up(long nvox, double g_ratio, double theta, const double *T,
                                  const double *c_ul, double *c_lu, cudaStream_t st);
+// mode: 0 full weighting, 1 half weighting, 2 injection
 cudaError_t launch_restrict(int ncomp, int nxf, int nyf, int nzf, const double *fine,
-                            double *coarse, cudaStream_t st);
+                            double *coarse, cudaStream_t st, int mode = 0);
 cudaError_t launch_prolong(int ncomp, int nxc, int nyc, int nzc, const double *tz,
                            const double *coarse, double *fine, cudaStream_t st);
 cudaError_t launch_prolong_correct(int ncomp, int nxc, int nyc, int nzc, const double *tz,

@@ -156,7 +156,10 @@ cudaError_t launch_collisions_up(long nvox, double g_ratio, double theta, const 
 
 // ---------------------------------------------------------------- restriction
 
-__global__ void restrict_kernel(int ncomp, int nxf, int nyf, int nzf,
+// mode 0: full weighting (27 nodes), 1: half weighting (centre 1/2, six axis
+// neighbours 1/12 each; on the boundary planes centre 1/2 and four in-plane
+// neighbours 1/8 each), 2: injection.
+__global__ void restrict_kernel(int ncomp, int nxf, int nyf, int nzf, int mode,
                                 const double *__restrict__ fine, double *__restrict__ coarse) {
     const int nxc = nxf / 2, nyc = nyf / 2, nzc = (nzf + 1) / 2;
     const long nvc = (long)nxc * nyc * nzc, nvf = (long)nxf * nyf * nzf;
@@ -173,25 +176,42 @@ __global__ void restrict_kernel(int ncomp, int nxf, int nyf, int nzf,
             xs[d] = xi < 0 ? xi + nxf : (xi >= nxf ? xi - nxf : xi);
             ys[d] = yi < 0 ? yi + nyf : (yi >= nyf ? yi - nyf : yi);
         }
+        const long plane = (long)nxf * nyf;
         for (int comp = 0; comp < ncomp; ++comp) {
             const double *F = fine + comp * nvf;
             double acc = 0.0;
-            for (int dz = 0; dz < 3; ++dz) {
-                double wz;
-                int kf;
+            if (mode == 2) {
+                acc = F[(long)(2 * K) * plane + (long)ys[1] * nxf + xs[1]];
+            } else if (mode == 1) {
+                const double *P = F + (long)(2 * K) * plane;
+                const double ctr = P[(long)ys[1] * nxf + xs[1]];
+                const double inplane = P[(long)ys[1] * nxf + xs[0]] + P[(long)ys[1] * nxf + xs[2]] +
+                                       P[(long)ys[0] * nxf + xs[1]] + P[(long)ys[2] * nxf + xs[1]];
                 if (boundary) {
-                    if (dz != 1) continue;
-                    wz = 1.0;
-                    kf = 2 * K;
+                    acc = 0.5 * ctr + inplane / 8.0;
                 } else {
-                    wz = wh[dz];
-                    kf = 2 * K + dz - 1;
+                    const double zpair = F[(long)(2 * K - 1) * plane + (long)ys[1] * nxf + xs[1]] +
+                                         F[(long)(2 * K + 1) * plane + (long)ys[1] * nxf + xs[1]];
+                    acc = 0.5 * ctr + (inplane + zpair) / 12.0;
                 }
-                const double *P = F + (long)kf * nxf * nyf;
-                for (int dy = 0; dy < 3; ++dy) {
-                    const double *R = P + (long)ys[dy] * nxf;
-                    const double wy = wz * wh[dy];
-                    acc += wy * (0.25 * R[xs[0]] + 0.5 * R[xs[1]] + 0.25 * R[xs[2]]);
+            } else {
+                for (int dz = 0; dz < 3; ++dz) {
+                    double wz;
+                    int kf;
+                    if (boundary) {
+                        if (dz != 1) continue;
+                        wz = 1.0;
+                        kf = 2 * K;
+                    } else {
+                        wz = wh[dz];
+                        kf = 2 * K + dz - 1;
+                    }
+                    const double *P = F + (long)kf * plane;
+                    for (int dy = 0; dy < 3; ++dy) {
+                        const double *R = P + (long)ys[dy] * nxf;
+                        const double wy = wz * wh[dy];
+                        acc += wy * (0.25 * R[xs[0]] + 0.5 * R[xs[1]] + 0.25 * R[xs[2]]);
+                    }
                 }
             }
             coarse[comp * nvc + c] = acc;
@@ -200,9 +220,10 @@ __global__ void restrict_kernel(int ncomp, int nxf, int nyf, int nzf,
 }
 
 cudaError_t launch_restrict(int ncomp, int nxf, int nyf, int nzf, const double *fine,
-                            double *coarse, cudaStream_t st) {
+                            double *coarse, cudaStream_t st, int mode) {
     const long nvc = (long)(nxf / 2) * (nyf / 2) * ((nzf + 1) / 2);
-    restrict_kernel<<<grid_for(nvc, 256), 256, 0, st>>>(ncomp, nxf, nyf, nzf, fine, coarse);
+    restrict_kernel<<<grid_for(nvc, 256), 256, 0, st>>>(ncomp, nxf, nyf, nzf, mode, fine,
+                                                          coarse);
     return cudaGetLastError();
 }
 

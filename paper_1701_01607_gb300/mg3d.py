@@ -25,6 +25,9 @@ MG3D_E_STATE = -8
 MG3D_MAX_GRIDS = 8
 MG3D_PREC_F64 = 0
 MG3D_PREC_F32 = 1
+MG3D_RESTRICT_FULL = 0
+MG3D_RESTRICT_HALF = 1
+MG3D_RESTRICT_INJECT = 2
 MG3D_NOALLOC_MAX_NODES = 65536
 MG3D_NOALLOC_MAX_NZ = 1024
 MG3D_NOALLOC_MAX_FREQ = 64
@@ -51,7 +54,7 @@ class mg3d_quadrature(ctypes.Structure):
 class mg3d_params(ctypes.Structure):
     _fields_ = [("n_grids", ctypes.c_int), ("nu_fmg", ctypes.c_int), ("nu0", ctypes.c_int),
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("nu3", ctypes.c_int),
-                ("fs_prec", ctypes.c_int)]
+                ("fs_prec", ctypes.c_int), ("restriction", ctypes.c_int)]
 
 
 class mg3d_line(ctypes.Structure):
@@ -131,9 +134,9 @@ _SIGNATURES = {
     "mg3d_fmg_solve": (_I, [_H, ctypes.c_double, _I, ctypes.POINTER(mg3d_stats)]),
     "mg3d_restrict": (_I, [_H, _I, _I, _D, _D]),
     "mg3d_prolong": (_I, [_H, _I, _I, _D, _D]),
-    "mg3d_set_fs_config": (_I, [_H, _I, _I, _I, _I]),
+    "mg3d_set_fs_config": (_I, [_H, _I, _I, _I, _I, _I]),
     "mg3d_get_fs_config": (_I, [_H, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
-                                ctypes.POINTER(_I)]),
+                                ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "mg3d_autotune": (_I, [_H, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),
     "mg3d_check_exp": (_I, [_I, _D, _D]),
     "mg3d_set_graphs": (_I, [_H, _I]),
@@ -201,7 +204,7 @@ def mg3d_last_error() -> str:
 
 def mg3d_create(atm, atom, quad_a: float = 0.0, n_grids: int = 1, nu_fmg: int = 16,
                 nu0: int = 0, nu1: int = 2, nu2: int = 2, nu3: int = 32,
-                fs_prec: int = MG3D_PREC_F64):
+                fs_prec: int = MG3D_PREC_F64, restriction: int = MG3D_RESTRICT_FULL):
     """mg3d_create from a synth.Atmosphere and TwoLevelAtom; returns the handle."""
     lib = load()
     z = np.ascontiguousarray(atm.z, dtype=np.float64)
@@ -212,7 +215,7 @@ def mg3d_create(atm, atom, quad_a: float = 0.0, n_grids: int = 1, nu_fmg: int = 
                         _dptr(n_tot), _dptr(c_ul))
     at = mg3d_atom(atom.a_ul, atom.g_ratio, atom.theta, atom.kappa, atom.n_freq, atom.x_max)
     q = mg3d_quadrature(quad_a)
-    p = mg3d_params(n_grids, nu_fmg, nu0, nu1, nu2, nu3, fs_prec)
+    p = mg3d_params(n_grids, nu_fmg, nu0, nu1, nu2, nu3, fs_prec, restriction)
     h = _H()
     _check(lib.mg3d_create(ctypes.byref(a), ctypes.byref(at), ctypes.byref(q),
                            ctypes.byref(p), ctypes.byref(h)))
@@ -221,7 +224,7 @@ def mg3d_create(atm, atom, quad_a: float = 0.0, n_grids: int = 1, nu_fmg: int = 
 
 def mg3d_create_ml(atm, atom, quad_a: float = 0.0, n_grids: int = 1, nu_fmg: int = 16,
                    nu0: int = 0, nu1: int = 2, nu2: int = 2, nu3: int = 32,
-                   fs_prec: int = MG3D_PREC_F64):
+                   fs_prec: int = MG3D_PREC_F64, restriction: int = MG3D_RESTRICT_FULL):
     """mg3d_create_ml from a synth.MultiLevelAtmosphere and MultiLevelAtom."""
     lib = load()
     keep = {}
@@ -242,7 +245,7 @@ def mg3d_create_ml(atm, atom, quad_a: float = 0.0, n_grids: int = 1, nu_fmg: int
     at = mg3d_ml_atom(atom.n_levels, arr("g", atom.g), arr("th", atom.theta), atom.theta_ref,
                       atom.t_ref, len(atom.lines), lines, len(atom.continua), conts)
     q = mg3d_quadrature(quad_a)
-    p = mg3d_params(n_grids, nu_fmg, nu0, nu1, nu2, nu3, fs_prec)
+    p = mg3d_params(n_grids, nu_fmg, nu0, nu1, nu2, nu3, fs_prec, restriction)
     h = _H()
     _check(lib.mg3d_create_ml(ctypes.byref(a), ctypes.byref(at), ctypes.byref(q),
                               ctypes.byref(p), ctypes.byref(h)))
@@ -367,15 +370,16 @@ def mg3d_prolong(h, level_fine: int, coarse):
     return out if coarse.ndim == 4 else out[0]
 
 
-def mg3d_set_fs_config(h, level: int, freq_per_block: int, bands: int, threads: int = 256):
-    return _check(load().mg3d_set_fs_config(h, level, freq_per_block, bands, threads))
+def mg3d_set_fs_config(h, level: int, freq_per_block: int, bands: int, threads: int = 256,
+                       lean: int = 0):
+    return _check(load().mg3d_set_fs_config(h, level, freq_per_block, bands, threads, lean))
 
 
 def mg3d_get_fs_config(h, level: int):
-    a, b, c = _I(), _I(), _I()
+    a, b, c, d = _I(), _I(), _I(), _I()
     _check(load().mg3d_get_fs_config(h, level, ctypes.byref(a), ctypes.byref(b),
-                                     ctypes.byref(c)))
-    return a.value, b.value, c.value
+                                     ctypes.byref(c), ctypes.byref(d)))
+    return a.value, b.value, c.value, d.value
 
 
 def mg3d_autotune(h, level: int = 0):

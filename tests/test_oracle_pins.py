@@ -373,3 +373,39 @@ def test_mali_fas_fmg_same_solution():
     rho_mali = h_mali[-1] / h_mali[-2]
     rho_fas = h_fas[-1] / h_fas[-2]
     assert rho_fas < 0.5 and rho_fas < rho_mali, (rho_fas, rho_mali)
+
+
+def test_half_weighting_and_injection():
+    from scipy import ndimage
+    rng = np.random.default_rng(4)
+    f = rng.uniform(1, 2, size=(2, 9, 8, 6))
+    inj = O.restrict_inj(f)
+    assert np.array_equal(inj, f[:, ::2, ::2, ::2])
+    hw = O.restrict_hw(f)
+    assert np.allclose(O.restrict_hw(np.full((9, 8, 6), 2.5)), 2.5, rtol=1e-15)
+    k3 = np.zeros((3, 3, 3))
+    k3[1, 1, 1] = 0.5
+    for (a, b, c) in ((0, 1, 1), (2, 1, 1), (1, 0, 1), (1, 2, 1), (1, 1, 0), (1, 1, 2)):
+        k3[a, b, c] = 1.0 / 12.0
+    for comp in range(2):
+        conv = ndimage.convolve(f[comp], k3, mode="wrap")
+        assert np.allclose(hw[comp, 1:-1], conv[2:-2:2, ::2, ::2], rtol=1e-14)
+        k2 = np.zeros((3, 3))
+        k2[1, 1] = 0.5
+        k2[0, 1] = k2[2, 1] = k2[1, 0] = k2[1, 2] = 0.125
+        for K, kf in ((0, 0), (4, 8)):
+            plane = ndimage.convolve(f[comp, kf], k2, mode="wrap")[::2, ::2]
+            assert np.allclose(hw[comp, K], plane, rtol=1e-14)
+
+
+def test_fas_converges_with_each_restriction():
+    """All three restrictions give a convergent FAS on a smooth problem with
+    the same fixed point (the restriction changes only the path)."""
+    atm, atom = synth.stratified_two_level(8, 8, 17, eps=1e-2, sigma=0.3, seed=9)
+    sols = []
+    for mode in (0, 1, 2):
+        prob = O.TwoLevelProblem(atm, atom, n_grids=3, restriction=mode)
+        n, cyc = O.fas_solve(prob, 1e-10, dict(nu_fmg=8, nu0=0, nu1=2, nu2=2, nu3=32))
+        sols.append(n)
+    for n in sols[1:]:
+        assert O.max_rel_error(n, sols[0]) < 1e-7

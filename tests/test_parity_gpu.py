@@ -54,15 +54,16 @@ def test_formal_solution_fp64(shape):
     assert rel(u, uo) < TOL_FS64
 
 
-@pytest.mark.parametrize("ng,bands", [(1, 1), (9, 1), (4, 3), (2, 6), (3, 8), (9, 2), (5, 6)])
-def test_formal_solution_every_launch_shape(ng, bands):
+@pytest.mark.parametrize("ng,bands,lean", [(1, 1, 0), (9, 1, 1), (4, 3, 0), (2, 6, 1), (3, 8, 0),
+                                           (9, 2, 1), (5, 6, 0)])
+def test_formal_solution_every_launch_shape(ng, bands, lean):
     """Ragged frequency groups (9 = 4+4+1) and ragged bands (16 rows as 6+6+4
     or 3x5+1) exercise the distributed-shared-memory reads across blocks."""
     atm, atom = synth.stratified_two_level(16, 16, 17, eps=1e-3, sigma=0.3, seed=2)
     h = make(atm, atom)
     try:
-        m.mg3d_set_fs_config(h, 1, ng, bands, 128)
-        assert m.mg3d_get_fs_config(h, 1) == (ng, bands, 128)
+        m.mg3d_set_fs_config(h, 1, ng, bands, 128, lean)
+        assert m.mg3d_get_fs_config(h, 1) == (ng, bands, 128, lean)
         jeff, u = m.mg3d_formal_solve(h, 1)
     finally:
         m.mg3d_destroy(h)
@@ -318,3 +319,93 @@ def test_graph_replayed_vcycles_equal_direct_launches():
     finally:
         m.mg3d_destroy(hg)
         m.mg3d_destroy(hd)
+
+
+# ------------------------------------------------ checkpoint and failures
+
+def test_resume_from_checkpoint_is_bitwise_identical():
+    """MALI for 6 sweeps equals 3 sweeps, a host checkpoint of the
+    populations, a fresh handle and 3 more sweeps, bit for bit; the same for
+    FAS V-cycles."""
+    atm, atom = synth.stratified_two_level(16, 16, 33, eps=1e-3, sigma=0.3, seed=14)
+    for n_grids, step in ((1, lambda h: m.mg3d_mali_sweep(h, 1, 1)),
+                          (3, lambda h: m.mg3d_fas_vcycle(h, False))):
+        full = make(atm, atom, n_grids=n_grids)
+        a = make(atm, atom, n_grids=n_grids)
+        try:
+            for _ in range(6):
+                step(full)
+            for _ in range(3):
+                step(a)
+            ckpt = m.mg3d_get_populations(a, n_grids)
+        finally:
+            m.mg3d_destroy(a)
+        b = make(atm, atom, n_grids=n_grids)
+        try:
+            m.mg3d_set_populations(b, n_grids, ckpt)
+            for _ in range(3):
+                step(b)
+            assert np.array_equal(m.mg3d_get_populations(b, n_grids),
+                                  m.mg3d_get_populations(full, n_grids))
+        finally:
+            m.mg3d_destroy(b)
+            m.mg3d_destroy(full)
+
+
+def test_non_finite_populations_are_reported_not_faulted():
+    """A NaN planted in the populations makes the next sweep and V-cycle
+    return MG3D_E_DIVERGED; the GPU context stays usable afterwards."""
+    atm, atom = synth.stratified_two_level(8, 8, 17, eps=1e-3, seed=15)
+    h = make(atm, atom, n_grids=2)
+    try:
+        n = m.mg3d_get_populations(h, 2)
+        n[1, 5, 3, 4] = np.nan
+        m.mg3d_set_populations(h, 2, n)
+        with pytest.raises(m.MG3DError) as ei:
+            m.mg3d_mali_sweep(h, 2, 1)
+        assert ei.value.code == m.MG3D_E_DIVERGED
+        m.mg3d_set_populations(h, 2, n)
+        with pytest.raises(m.MG3DError) as ei:
+            m.mg3d_fas_vcycle(h, False)
+        assert ei.value.code == m.MG3D_E_DIVERGED
+        m.mg3d_init_zero_radiation(h, 2)
+        assert np.isfinite(m.mg3d_mali_sweep(h, 2, 1))
+    finally:
+        m.mg3d_destroy(h)
+    h2 = make(atm, atom)
+    try:
+        m.mg3d_mali_sweep(h2, 1, 1)
+    finally:
+        m.mg3d_destroy(h2)
+
+
+def test_iteration_cap_returns_maxiter():
+    atm, atom = synth.stratified_two_level(8, 8, 17, eps=1e-3, seed=16)
+    h = make(atm, atom, n_grids=2)
+    try:
+        with pytest.raises(m.MG3DError) as ei:
+            m.mg3d_mali_solve(h, 1e-12, 3)
+        assert ei.value.code == m.MG3D_E_MAXITER
+        with pytest.raises(m.MG3DError) as ei:
+            m.mg3d_fas_solve(h, 1e-14, 2, n_grids=2)
+        assert ei.value.code == m.MG3D_E_MAXITER
+    finally:
+        m.mg3d_destroy(h)
+
+
+@pytest.mark.parametrize("mode", [m.MG3D_RESTRICT_HALF, m.MG3D_RESTRICT_INJECT])
+def test_restriction_variants_match_oracle(mode):
+    atm, atom = synth.stratified_two_level(16, 16, 33, eps=1e-3, sigma=0.3, seed=17)
+    h = m.mg3d_create(atm, atom, n_grids=3, restriction=mode, **PARAMS)
+    prob = O.TwoLevelProblem(atm, atom, n_grids=3, restriction=mode)
+    n = prob.zero_radiation(3)
+    try:
+        f = np.random.default_rng(3).uniform(0.5, 1.5, size=(2, 33, 16, 16))
+        ref = O.restrict_hw(f) if mode == m.MG3D_RESTRICT_HALF else O.restrict_inj(f)
+        assert rel(m.mg3d_restrict(h, 3, f), ref) < 1e-14
+        for cyc in range(2):
+            m.mg3d_fas_vcycle(h, cyc == 0)
+            n, _ = prob.fas_cycle(n, cyc == 0, PARAMS)
+        assert rel(m.mg3d_get_populations(h, 3), n) < TOL_POP64
+    finally:
+        m.mg3d_destroy(h)
