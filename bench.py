@@ -41,12 +41,15 @@ N_GRIDS = 3
 METRIC = "FS Gvoxel*ray*freq/s (3-grid FAS V-cycle step)"
 UNIT = "Gunit/s"
 FS_UNITS_PER_FINE = GRID[0] * GRID[1] * GRID[2] * 24 * 9
-# FP64 floating-point operations per (node, ray, frequency) of the sweep as
-# the method states it (bilinear I_up 7, optical path 1, exp 1, u 2, w0 1,
-# w_up 1, new I 5, two accumulations 4, plus 16 per node and ray shared by
-# the 9 frequencies for the chi/S interpolation and dtau), exp and the
-# division counted as one operation each.
-ALG_FLOPS_PER_UNIT = 7 + 1 + 1 + 2 + 1 + 1 + 5 + 4 + 16.0 / 9.0
+# FP64 floating-point operations per (node, ray, frequency) of the sweep
+# (bilinear I_up 7, new I 5, two accumulations 4, plus 16 per node and ray
+# shared by the 9 frequencies for the chi/S interpolation and dtau), and the
+# short-characteristics weights (optical path 1, exp 1, u 2, w0 1, w_up 1)
+# once per distinct profile value: phi(x) = phi(-x) gives mirror frequencies
+# the same optical depth, so 5 of the 9 need their own.  exp and the
+# division count as one operation each.
+N_DISTINCT_PHI = (9 + 1) // 2
+ALG_FLOPS_PER_UNIT = 7 + 5 + 4 + (1 + 1 + 2 + 1 + 1) * N_DISTINCT_PHI / 9.0 + 16.0 / 9.0
 FP64_NOMINAL_TFLOPS = 1.25      # GB300, at the 2070 MHz maximum SM clock
 SM_MAX_MHZ = 2070.0
 

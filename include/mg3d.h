@@ -324,11 +324,15 @@ int mg3d_prolong(mg3d_handle *h, int level_fine, int ncomp, const double *coarse
 
 /* Sweep launch shape of a level (two-level handles): freq_per_block
  * frequencies per thread block, bands = thread blocks (one cluster) sharing
- * each horizontal plane, threads per block (32..512, a multiple of 32), and
- * lean = 1 for the kernel variant compiled for 1024 resident threads per SM
- * (64 registers per thread), 0 for the one with the full register budget.
- * The library picks a shape at creation; this overrides it.  Returns
- * MG3D_E_ARG if the shape does not fit in shared memory. */
+ * each horizontal plane (1..16; above 8 a non-portable cluster size that not
+ * every shape can be scheduled with), threads per block (32..512, a multiple
+ * of 32), and
+ * the register budget of the kernel variant: lean = 0 full, 1 compiled for
+ * 1024 resident threads per SM (64 registers per thread), 2 for three blocks
+ * of at most 256 threads per SM (85 registers).
+ * The library picks a shape at creation (at most 8 bands); this overrides
+ * it.  Returns MG3D_E_ARG if the shape does not fit in shared memory or the
+ * GPU cannot hold one of its clusters. */
 int mg3d_set_fs_config(mg3d_handle *h, int level, int freq_per_block, int bands,
                        int threads, int lean);
 int mg3d_get_fs_config(const mg3d_handle *h, int level, int *freq_per_block, int *bands,
@@ -336,8 +340,9 @@ int mg3d_get_fs_config(const mg3d_handle *h, int level, int *freq_per_block, int
 
 /* Autotuner: times candidate sweep shapes on this GPU with the level's current
  * populations and keeps the fastest per level (level = 0: every level).
- * Candidates: every number of frequency groups up to 64, 1-8 bands,
- * 128/256/512 threads and both register budgets that fit; one launch each,
+ * Candidates: every number of frequency groups up to 64, 1-16 bands,
+ * 128/256/512 threads and the register budgets that fit and can be
+ * scheduled; one launch each,
  * then the best eight three more times.  Overwrites the partial sums (not the populations).
  * *evaluated and *seconds (nullable) report the candidates and wall time. */
 int mg3d_autotune(mg3d_handle *h, int level, int *evaluated, double *seconds);

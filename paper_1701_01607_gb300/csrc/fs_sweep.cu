@@ -128,6 +128,12 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
     __syncthreads();
     const ExpNegTable et{exp_tab, a.exp_l1, a.exp_l2};
     const bool vec16 = (nx * sizeof(T)) % 16 == 0;
+    // bit f set: frequency f needs its own weights; clear: its phi equals
+    // that of frequency f-1 (mirror halves of the profile stored next to
+    // each other), so the weights of f-1, still in registers, are its own
+    unsigned long long fresh = ~0ull;
+    for (int f = 1; f < nf && f < 64; ++f)
+        if (phi[f] == phi[f - 1]) fresh &= ~(1ull << f);
 
     // stage the window and band of step t into staging buffer t & 1
     auto stage_step = [&](int t) {
@@ -205,13 +211,14 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
                 Pa += (long)(ya - ba * rows) * nx;
                 Pb += (long)(yb - bb * rows) * nx;
                 T cj = 0, cu = 0;
+                T ex = 0, w0 = 0, wup = 0, u = 0;
                 for (int f = 0; f < nf; ++f) {
                     const long off = (long)f * rows * nx;
                     const T I_up = w00 * Pa[off + xa] + w10 * Pa[off + xb] +
                                    w01 * Pb[off + xa] + w11 * Pb[off + xb];
-                    T ex, w0, wup, u;
-                    ScWeights<T>::eval(dtau0 * phi[f], inv_dtau0 * inv_phi[f], et, ex, w0, wup,
-                                       u);
+                    if (f >= 64 || ((fresh >> f) & 1ull))
+                        ScWeights<T>::eval(dtau0 * phi[f], inv_dtau0 * inv_phi[f], et, ex, w0,
+                                           wup, u);
                     const T part = I_up * ex + wup * S_up;
                     cur[((long)f * rows + yl) * nx + x] = part + w0 * S_loc;
                     const T w = wphi[f];
@@ -231,7 +238,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
 
 // MAXT: the block size bound the kernel is compiled for (256 or 512); MINB:
 // blocks per SM it must fit, which sets the register budget (MINB = 1: up to
-// 255 registers; MINB = 1024/MAXT: 64 registers, 32 resident warps per SM).
+// 255 registers; 1024/MAXT: 64 registers, 32 resident warps per SM; 3 blocks
+// of 256: 85 registers).
 template <typename T, int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB) sweep_kernel(const SweepArgs<T> a) {
     sweep_body<T>(a, blockIdx.y, blockIdx.z);
@@ -280,35 +288,77 @@ size_t sweep_smem_bytes(int prec, const SweepShape &s, int nx) {
     return (2ull * s.ng * s.rows * nx + 2ull * sweep_stage_elems(s.rows, nx) + 3ull * s.ng) * elem;
 }
 
+// Kernel attributes for shape s (dynamic shared memory; clusters of more
+// than 8 blocks are a non-portable size the kernel must opt into) and the
+// launch configuration; a is null for an occupancy query.
 template <typename T, int MAXT, int MINB>
-static cudaError_t launch_sweep_t(const SweepArgs<T> &a, const SweepShape &s,
-                                  cudaStream_t st) {
-    size_t smem = sweep_smem_bytes(sizeof(T) == 8 ? 0 : 1, s, a.nx);
+static cudaError_t sweep_config(const SweepShape &s, int nx, cudaStream_t st,
+                                cudaLaunchConfig_t *cfg, cudaLaunchAttribute *attr) {
+    const size_t smem = sweep_smem_bytes(sizeof(T) == 8 ? 0 : 1, s, nx);
     cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, MAXT, MINB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
+    if (e == cudaSuccess && s.bands > kPortableBands)
+        e = cudaFuncSetAttribute(sweep_kernel<T, MAXT, MINB>,
+                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(s.bands, s.ngroups, kRays);
-    cfg.blockDim = dim3(s.threads, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
+    *cfg = cudaLaunchConfig_t{};
+    cfg->gridDim = dim3(s.bands, s.ngroups, kRays);
+    cfg->blockDim = dim3(s.threads, 1, 1);
+    cfg->dynamicSmemBytes = smem;
+    cfg->stream = st;
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = s.bands;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg->attrs = attr;
+    cfg->numAttrs = 1;
+    return cudaSuccess;
+}
+
+template <typename T, int MAXT, int MINB>
+static cudaError_t launch_sweep_t(const SweepArgs<T> &a, const SweepShape &s,
+                                  cudaStream_t st) {
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    cudaError_t e = sweep_config<T, MAXT, MINB>(s, a.nx, st, &cfg, attr);
+    if (e != cudaSuccess) return e;
     return cudaLaunchKernelEx(&cfg, sweep_kernel<T, MAXT, MINB>, a);
+}
+
+template <typename T, int MAXT, int MINB>
+static cudaError_t clusters_t(const SweepShape &s, int nx, int *n) {
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    cudaError_t e = sweep_config<T, MAXT, MINB>(s, nx, 0, &cfg, attr);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveClusters(n, sweep_kernel<T, MAXT, MINB>, &cfg);
 }
 
 template <typename T>
 static cudaError_t launch_sweep_any(const SweepArgs<T> &a, const SweepShape &s,
                                     cudaStream_t st) {
-    if (s.threads <= 256)
-        return s.lean ? launch_sweep_t<T, 256, 4>(a, s, st) : launch_sweep_t<T, 256, 1>(a, s, st);
-    return s.lean ? launch_sweep_t<T, 512, 2>(a, s, st) : launch_sweep_t<T, 512, 1>(a, s, st);
+    if (s.threads <= 256) {
+        if (s.lean == 1) return launch_sweep_t<T, 256, 4>(a, s, st);
+        if (s.lean == 2) return launch_sweep_t<T, 256, 3>(a, s, st);
+        return launch_sweep_t<T, 256, 1>(a, s, st);
+    }
+    return s.lean == 1 ? launch_sweep_t<T, 512, 2>(a, s, st) : launch_sweep_t<T, 512, 1>(a, s, st);
+}
+
+template <typename T>
+static cudaError_t clusters_any(const SweepShape &s, int nx, int *n) {
+    if (s.threads <= 256) {
+        if (s.lean == 1) return clusters_t<T, 256, 4>(s, nx, n);
+        if (s.lean == 2) return clusters_t<T, 256, 3>(s, nx, n);
+        return clusters_t<T, 256, 1>(s, nx, n);
+    }
+    return s.lean == 1 ? clusters_t<T, 512, 2>(s, nx, n) : clusters_t<T, 512, 1>(s, nx, n);
+}
+
+cudaError_t sweep_active_clusters(int prec, const SweepShape &s, int nx, int *n) {
+    *n = 0;
+    return prec == 0 ? clusters_any<double>(s, nx, n) : clusters_any<float>(s, nx, n);
 }
 
 template <typename T, int MAXT>

@@ -177,7 +177,8 @@ void build_frequencies(mg3d_handle *h) {
     h->wphi.assign(nf, 0.0);
     double sum = 0.0;
     for (int i = 0; i < nf; ++i) {
-        double x = nf == 1 ? 0.0 : -h->atom.x_max + 2.0 * h->atom.x_max * i / (nf - 1);
+        // x_i = -x_{nf-1-i} exactly, so mirror frequencies get equal phi
+        double x = nf == 1 ? 0.0 : h->atom.x_max * (2 * i - (nf - 1)) / (nf - 1);
         double w = nf == 1 ? 1.0 : 2.0 * h->atom.x_max / (nf - 1);
         if (nf > 1 && (i == 0 || i == nf - 1)) w *= 0.5;
         h->phi[i] = std::exp(-x * x) / std::sqrt(M_PI);
@@ -232,7 +233,7 @@ SweepShape choose_shape(int prec, int nx, int ny, int nfreq) {
     const int ngroups = (nfreq + ng - 1) / ng;
     SweepShape best{};
     long best_gap = 1L << 40;
-    for (int bands = 1; bands <= kMaxBands && bands <= ny; ++bands) {
+    for (int bands = 1; bands <= kPortableBands && bands <= ny; ++bands) {
         const int rows = (ny + bands - 1) / bands;
         if ((long)(bands - 1) * rows >= ny) continue;
         SweepShape s{ng, ngroups, bands, rows, 256};
@@ -246,7 +247,7 @@ SweepShape choose_shape(int prec, int nx, int ny, int nfreq) {
     }
     if (best.ng == 0) {
         // planes too large for three frequencies: one frequency, most bands
-        for (int bands = kMaxBands; bands >= 1; --bands) {
+        for (int bands = kPortableBands; bands >= 1; --bands) {
             if (bands > ny) continue;
             const int rows = (ny + bands - 1) / bands;
             if ((long)(bands - 1) * rows >= ny) continue;
@@ -728,6 +729,20 @@ int make_shape(const mg3d_handle *h, int k, int ng, int bands, int threads, Swee
     return MG3D_OK;
 }
 
+// MG3D_E_ARG unless the GPU can hold at least one cluster of shape s on level
+// k (clusters of more than 8 blocks are not guaranteed to fit).
+int check_schedulable(const mg3d_handle *h, int k, const SweepShape &s) {
+    int n = 0;
+    const cudaError_t e = sweep_active_clusters(h->prec, s, h->lev[k].nx, &n);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MG3D_E_ARG,
+                    std::string("sweep shape cannot be scheduled: ") + cudaGetErrorString(e));
+    }
+    if (n < 1) return fail(MG3D_E_ARG, "sweep shape cannot be scheduled: cluster does not fit");
+    return MG3D_OK;
+}
+
 void drop_graphs(mg3d_handle *h);
 
 // Partial-sum buffers of at least `need` elements (contents not kept).
@@ -813,12 +828,14 @@ int autotune_level(mg3d_handle *h, int k, int *evaluated) {
     for (int ng : ngs)
         for (int bands = 1; bands <= kMaxBands && bands <= L.ny; ++bands)
             for (int th : {128, 256, 512})
-                for (int lean = 0; lean < 2; ++lean) {
+                for (int lean = 0; lean < 3; ++lean) {
+                    if (lean == 2 && th > 256) continue;  // same as lean 0 at 512 threads
                     SweepShape s;
                     if (make_shape(h, k, ng, bands, th, &s) != MG3D_OK) continue;
                     const int band = s.rows * L.nx;
                     if (th > 128 && th / 2 >= band) continue;  // a smaller block covers the band
                     s.lean = lean;
+                    if (check_schedulable(h, k, s) != MG3D_OK) continue;
                     cands.push_back(s);
                 }
     g_last_error.clear();
@@ -946,24 +963,30 @@ int create_impl(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_qu
                                                 h->stream),
                         "planck"));
     }
-    // frequency tables in the formal-solution precision
+    // frequency tables in the formal-solution precision, in mirror-pair
+    // order (x_0, x_{nf-1}, x_1, x_{nf-2}, ..., then the centre): the sweep
+    // sums over frequencies, so their order is internal to it, and a
+    // frequency whose phi equals its predecessor's reuses that one's
+    // short-characteristics weights
     const int nf = atom->n_freq;
     MG_TRY(dev_alloc(&h->d_phi, nf * es));
     MG_TRY(dev_alloc(&h->d_wphi, nf * es));
     MG_TRY(dev_alloc(&h->d_inv_phi, nf * es));
-    std::vector<double> wphi_ray(nf), inv_phi(nf);
-    for (int i = 0; i < nf; ++i) {
-        wphi_ray[i] = h->wphi[i] / kRays;
-        inv_phi[i] = 1.0 / h->phi[i];
+    std::vector<double> phi_t(nf), wphi_ray(nf), inv_phi(nf);
+    for (int j = 0; j < nf; ++j) {
+        const int i = j % 2 == 0 ? j / 2 : nf - 1 - j / 2;
+        phi_t[j] = h->phi[i];
+        wphi_ray[j] = h->wphi[i] / kRays;
+        inv_phi[j] = 1.0 / h->phi[i];
     }
     if (h->prec == MG3D_PREC_F64) {
-        MG_CUDA(cudaMemcpy(h->d_phi, h->phi.data(), nf * es, cudaMemcpyHostToDevice));
+        MG_CUDA(cudaMemcpy(h->d_phi, phi_t.data(), nf * es, cudaMemcpyHostToDevice));
         MG_CUDA(cudaMemcpy(h->d_wphi, wphi_ray.data(), nf * es, cudaMemcpyHostToDevice));
         MG_CUDA(cudaMemcpy(h->d_inv_phi, inv_phi.data(), nf * es, cudaMemcpyHostToDevice));
     } else {
         std::vector<float> a(nf), b(nf), c(nf);
         for (int i = 0; i < nf; ++i) {
-            a[i] = (float)h->phi[i];
+            a[i] = (float)phi_t[i];
             b[i] = (float)wphi_ray[i];
             c[i] = (float)inv_phi[i];
         }
@@ -1086,7 +1109,7 @@ int create_ml_impl(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
         // bands: the fewest that fit in shared memory and give >= 300 blocks,
         // else the most that fit
         int pick = 0;
-        for (int b = 1; b <= kMaxBands && b <= L.ny; ++b) {
+        for (int b = 1; b <= kPortableBands && b <= L.ny; ++b) {
             const int rows = (L.ny + b - 1) / b;
             if ((long)(b - 1) * rows >= L.ny) continue;
             if (ml_sweep_smem_bytes(h->prec, rows, L.nx) > kMaxSweepSmem) continue;
@@ -1397,11 +1420,11 @@ int batch_build_level(mg3d_batch *b, int k) {
     // two-level members
     {
         mg3d_batch::KindLevel &t = b->two[k];
-        int bands = kMaxBands;
+        int bands = kPortableBands;
         for (int i : t.members) {
             const Level &L = b->m[i]->lev[k];
             int bmax = 0;
-            for (int bb = 1; bb <= kMaxBands && bb <= L.ny; ++bb) {
+            for (int bb = 1; bb <= kPortableBands && bb <= L.ny; ++bb) {
                 const int rows = (L.ny + bb - 1) / bb;
                 if ((long)(bb - 1) * rows < L.ny) bmax = bb;
             }
@@ -1474,7 +1497,7 @@ int batch_build_level(mg3d_batch *b, int k) {
     {
         mg3d_batch::KindLevel &q = b->ml[k];
         int bands = 0;
-        for (int bb = kMaxBands; bb >= 1 && !bands && !q.members.empty(); --bb) {
+        for (int bb = kPortableBands; bb >= 1 && !bands && !q.members.empty(); --bb) {
             bool ok = true;
             for (int i : q.members) {
                 const Level &L = b->m[i]->lev[k];
@@ -2088,7 +2111,10 @@ int mg3d_set_fs_config(mg3d_handle *h, int level, int freq_per_block, int bands,
     if (h->kind != 0) return fail(MG3D_E_STATE, "sweep shapes apply to two-level handles");
     SweepShape s;
     MG_TRY(make_shape(h, level, freq_per_block, bands, threads, &s));
-    s.lean = lean != 0;
+    if (lean < 0 || lean > 2 || (lean == 2 && threads > 256))
+        return fail(MG3D_E_ARG, "lean must be 0, 1 or (up to 256 threads) 2");
+    s.lean = lean;
+    MG_TRY(check_schedulable(h, level, s));
     MG_CUDA(cudaStreamSynchronize(h->stream));
     MG_TRY(ensure_partials(h, (size_t)kRays * s.ngroups * (size_t)h->lev[level].nvox));
     h->lev[level].shape = s;

@@ -8,7 +8,9 @@
 namespace mg3d {
 
 constexpr int kRays = 24;          // A4 quadrature, 12 up and 12 down
-constexpr int kMaxBands = 8;       // thread blocks per cluster sharing a plane
+constexpr int kMaxBands = 16;      // thread blocks per cluster sharing a plane (beyond
+                                   // 8: non-portable cluster size, checked per shape)
+constexpr int kPortableBands = 8;  // cap for shapes chosen without a measurement
 constexpr int kMaxSweepThreads = 512;
 constexpr size_t kMaxSweepSmem = 200 * 1024;
 
@@ -29,7 +31,8 @@ struct SweepShape {
     int bands;    // thread blocks per cluster; each holds `rows` rows
     int rows;     // ceil(ny / bands)
     int threads;  // threads per block
-    int lean = 0; // 1: kernel compiled for 1024 resident threads per SM (64 registers)
+    int lean = 0; // register budget: 0 full, 1: 1024 resident threads per SM (64
+                  // registers), 2: three 256-thread blocks per SM (85 registers)
 };
 
 // Arguments of the sweep kernel.  T is the formal-solution precision.
@@ -70,6 +73,8 @@ cudaError_t launch_opacity(int prec, long nvox, double g_ratio, double kappa,
                            const double *n, void *chi0, void *S, cudaStream_t st);
 cudaError_t launch_planck_bottom(int prec, long nplane, double theta, const double *T,
                                  void *bbot, cudaStream_t st);
+// How many clusters of shape s the GPU can hold at once (0: it cannot run).
+cudaError_t sweep_active_clusters(int prec, const SweepShape &s, int nx, int *n);
 cudaError_t launch_sweep_f64(const SweepArgs<double> &a, const SweepShape &s, cudaStream_t st);
 cudaError_t launch_sweep_f32(const SweepArgs<float> &a, const SweepShape &s, cudaStream_t st);
 

@@ -120,7 +120,7 @@ __global__ void noalloc_tables_kernel(int nx, int ny, int nz, double dx, double 
         double *wphi = scratch + kOffWphi;
         double sum = 0.0;
         for (int f = 0; f < nfreq; ++f) {
-            const double x = nfreq == 1 ? 0.0 : -x_max + 2.0 * x_max * f / (nfreq - 1);
+            const double x = nfreq == 1 ? 0.0 : x_max * (2 * f - (nfreq - 1)) / (nfreq - 1);
             double w = nfreq == 1 ? 1.0 : 2.0 * x_max / (nfreq - 1);
             if (nfreq > 1 && (f == 0 || f == nfreq - 1)) w *= 0.5;
             phi[f] = exp(-x * x) / sqrt(M_PI);
@@ -183,7 +183,7 @@ extern "C" int mg3d_formal_solve_noalloc(int nx, int ny, int nz, double dx, doub
     }
     // one frequency group (24 partial slots); the fewest bands that fit
     SweepShape shape{nf, 1, 0, 0, 0};
-    for (int bands = 1; bands <= kMaxBands && bands <= ny; ++bands) {
+    for (int bands = 1; bands <= kPortableBands && bands <= ny; ++bands) {
         const int rows = (ny + bands - 1) / bands;
         if ((long)(bands - 1) * rows >= ny) continue;
         SweepShape s{nf, 1, bands, rows, 0};

@@ -44,12 +44,18 @@ def test_batched_vcycles_equal_single_solves(prec):
     singles = [create(k, p, prec) for k, p in probs]
     b = m.mg3d_batch_create(members)
     try:
+        # The batched sweep is a separate kernel: the compiler may fuse its
+        # multiply-adds differently, so the two sides agree to rounding, not
+        # bitwise.  C is a relative difference of populations, so it carries
+        # their rounding in absolute terms: ~1e-15 in FP64, ~1e-7 with the
+        # FP32 formal solution.
+        c_abs = 0.0 if prec == m.MG3D_PREC_F64 else 1e-7
         for cyc in range(3):
             cb = m.mg3d_batch_fas_vcycle(b, len(members), cyc == 0)
             cs = [m.mg3d_fas_vcycle(h, cyc == 0) for h in singles]
             for i in range(len(members)):
                 if cs[i] > 1e-8:
-                    assert abs(cb[i] - cs[i]) <= 1e-6 * cs[i], (cyc, i)
+                    assert abs(cb[i] - cs[i]) <= 1e-6 * cs[i] + c_abs, (cyc, i)
         tol = 1e-10 if prec == m.MG3D_PREC_F64 else 1e-5
         for i in range(len(members)):
             assert rel(m.mg3d_get_populations(members[i], 3),

@@ -73,6 +73,24 @@ def test_formal_solution_every_launch_shape(ng, bands, lean):
     assert rel(u, uo) < TOL_FS64
 
 
+@pytest.mark.parametrize("ng,lean", [(3, 0), (9, 1), (2, 2)])
+def test_formal_solution_sixteen_block_cluster(ng, lean):
+    """Clusters of 16 blocks (a non-portable size): 31 rows as 15 bands of 2
+    and a last band of 1, so most upwind rows come from peer blocks."""
+    atm, atom = synth.stratified_two_level(8, 31, 9, eps=1e-3, sigma=0.3, seed=5)
+    h = make(atm, atom)
+    try:
+        m.mg3d_set_fs_config(h, 1, ng, 16, 32, lean)
+        assert m.mg3d_get_fs_config(h, 1) == (ng, 16, 32, lean)
+        jeff, u = m.mg3d_formal_solve(h, 1)
+    finally:
+        m.mg3d_destroy(h)
+    prob = O.TwoLevelProblem(atm, atom)
+    _, jo, uo = prob.formal_solution(1, prob.zero_radiation(1))
+    assert rel(jeff, jo) < TOL_FS64
+    assert rel(u, uo) < TOL_FS64
+
+
 def test_formal_solution_single_frequency_and_custom_quadrature():
     atom = synth.TwoLevelAtom(n_freq=1)
     atm, _ = synth.stratified_two_level(8, 8, 17, eps=1e-2, atom=atom, sigma=0.2, seed=4)
