@@ -51,6 +51,10 @@ FS_UNITS_PER_FINE = GRID[0] * GRID[1] * GRID[2] * 24 * 9
 N_DISTINCT_PHI = (9 + 1) // 2
 ALG_FLOPS_PER_UNIT = 7 + 5 + 4 + (1 + 1 + 2 + 1 + 1) * N_DISTINCT_PHI / 9.0 + 16.0 / 9.0
 FP64_NOMINAL_TFLOPS = 1.25      # GB300, at the 2070 MHz maximum SM clock
+# DRAM bytes (read + write) of one finest-grid FP64 sweep launch, from one ncu
+# capture of the current kernel at this launch shape (ng, bands, threads,
+# lean); reported only when the autotuner picks the same shape
+FINE_SWEEP_TRAFFIC = {"shape": [9, 5, 512, 0], "bytes": 13826560 + 141738240}
 SM_MAX_MHZ = 2070.0
 
 
@@ -156,10 +160,18 @@ def run_gpu(args):
 
     tuning = {}
 
+    fixed = json.loads(args.shapes) if args.shapes else None
+
     def make(prec):
         h = m.mg3d_create(atm, atom, n_grids=N_GRIDS, fs_prec=prec, **NU)
         m.mg3d_set_stream(h, stream.cuda_stream)
-        if not args.no_autotune:
+        key = "f64" if prec == m.MG3D_PREC_F64 else "f32"
+        if fixed is not None:
+            for k, shape in fixed[key].items():
+                m.mg3d_set_fs_config(h, int(k), *shape)
+            tuning[key] = {"fixed": True,
+                           "shapes": {k: m.mg3d_get_fs_config(h, k) for k in range(1, N_GRIDS + 1)}}
+        elif not args.no_autotune:
             info = m.mg3d_autotune(h)
             tuning["f64" if prec == m.MG3D_PREC_F64 else "f32"] = {
                 "seconds": round(info["seconds"], 3), "candidates": info["evaluated"],
@@ -232,6 +244,9 @@ def run_gpu(args):
         sm_mhz = clk.get("sm_mhz") or SM_MAX_MHZ
         peak = FP64_NOMINAL_TFLOPS * sm_mhz / SM_MAX_MHZ
         achieved = ALG_FLOPS_PER_UNIT * fine_units / (fine_ms * 1e-3) / 1e12
+        fine_shape = list(tuning.get("f64", {}).get("shapes", {}).get(fine, ()))
+        traffic = (FINE_SWEEP_TRAFFIC["bytes"]
+                   if fine_shape == FINE_SWEEP_TRAFFIC["shape"] else None)
         result = {
             "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
@@ -246,7 +261,7 @@ def run_gpu(args):
             "roofline": {"kernel": "sweep_kernel<double> (finest grid)", "bound": "alu",
                          "achieved": round(achieved, 4), "peak": round(peak, 4),
                          "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                         "traffic": None,
+                         "traffic": traffic,
                          "peak_source": "nominal FP64 1.25 TFLOP/s x median SM clock / 2070 MHz",
                          "alg_flops_per_unit": round(ALG_FLOPS_PER_UNIT, 3),
                          "units_per_launch": fine_units,
@@ -384,6 +399,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default sweep shapes")
+    ap.add_argument("--shapes", default="",
+                    help='sweep shapes instead of autotuning, as a bench line reports them: '
+                         '{"f64": {"1": [ng, bands, threads, lean], ...}, "f32": {...}}')
     ap.add_argument("--profile-sweep", choices=["f64", "f32"],
                     help="only run a few finest-grid formal solutions (for ncu)")
     ap.add_argument("--profile-launches", type=int, default=3)

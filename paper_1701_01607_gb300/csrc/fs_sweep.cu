@@ -61,7 +61,9 @@ __global__ void planck_bottom_kernel(long nplane, double theta, const double *__
 //   staging       [2][2][2 rows + 1][nx]      per step: chi0 and S of the
 //                 upwind window (rows + 1 rows of plane k-1, shifted by the
 //                 step's row offset) then of the block's own rows of plane k
-//   tables        [3][ng]                     phi, 1/phi, w phi of the group
+//   tables        [4][ng]                     phi, 1/phi, w phi of the group, and
+//                                             the w phi summed over frequencies
+//                                             sharing weights (for U)
 // Staging for step t+1 is copied asynchronously while step t computes.
 __host__ __device__ inline long sweep_stage_elems(int rows, int nx) {
     return 2L * (2 * rows + 1) * nx;
@@ -116,15 +118,15 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
     T *stage = buf + 2 * bufstride;
     const long stagestride = sweep_stage_elems(rows, nx);
     T *tabs = stage + 2 * stagestride;
-    T *phi = tabs, *inv_phi = tabs + a.ng, *wphi = tabs + 2 * a.ng;
+    T *phi = tabs, *inv_phi = tabs + a.ng, *wphi = tabs + 2 * a.ng, *wu = tabs + 3 * a.ng;
     for (int i = threadIdx.x; i < nf; i += blockDim.x) {
         phi[i] = a.phi[f0 + i];
         inv_phi[i] = a.inv_phi[f0 + i];
         wphi[i] = a.wphi[f0 + i];
     }
-    __shared__ double exp_tab[64];
+    __shared__ double exp_tab[kExpTab];
     if (sizeof(T) == 8)
-        for (int i = threadIdx.x; i < 64; i += blockDim.x) exp_tab[i] = a.exp_tab[i];
+        for (int i = threadIdx.x; i < kExpTab; i += blockDim.x) exp_tab[i] = a.exp_tab[i];
     __syncthreads();
     const ExpNegTable et{exp_tab, a.exp_l1, a.exp_l2};
     const bool vec16 = (nx * sizeof(T)) % 16 == 0;
@@ -134,6 +136,17 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
     unsigned long long fresh = ~0ull;
     for (int f = 1; f < nf && f < 64; ++f)
         if (phi[f] == phi[f - 1]) fresh &= ~(1ull << f);
+    auto is_fresh = [&](int f) { return f >= 64 || ((fresh >> f) & 1ull); };
+    // frequencies that share weights share u: U gets their summed w phi once
+    for (int f = threadIdx.x; f < nf; f += blockDim.x) {
+        T w = 0;
+        if (is_fresh(f)) {
+            w = wphi[f];
+            for (int h = f + 1; h < nf && !is_fresh(h); ++h) w += wphi[h];
+        }
+        wu[f] = w;
+    }
+    __syncthreads();
 
     // stage the window and band of step t into staging buffer t & 1
     auto stage_step = [&](int t) {
@@ -216,14 +229,14 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
                     const long off = (long)f * rows * nx;
                     const T I_up = w00 * Pa[off + xa] + w10 * Pa[off + xb] +
                                    w01 * Pb[off + xa] + w11 * Pb[off + xb];
-                    if (f >= 64 || ((fresh >> f) & 1ull))
+                    if (is_fresh(f)) {
                         ScWeights<T>::eval(dtau0 * phi[f], inv_dtau0 * inv_phi[f], et, ex, w0,
                                            wup, u);
+                        cu += wu[f] * u;
+                    }
                     const T part = I_up * ex + wup * S_up;
                     cur[((long)f * rows + yl) * nx + x] = part + w0 * S_loc;
-                    const T w = wphi[f];
-                    cj += w * part;
-                    cu += w * u;
+                    cj += wphi[f] * part;
                 }
                 const long v = (long)k * nplane + (long)y * nx + x;
                 pj[v] = cj;
@@ -271,21 +284,23 @@ cudaError_t launch_exp_check(int n, const double *x, double *out, const double *
     return cudaGetLastError();
 }
 
-void exp_neg_constants(double *tab64, double *l1, double *l2) {
-    // 2^{j/64} correctly rounded through the wider long double
-    for (int j = 0; j < 64; ++j) tab64[j] = (double)exp2l((long double)j / 64.0L);
+void exp_neg_constants(double *tab, double *l1, double *l2) {
+    // 2^{j/256} correctly rounded through the wider long double
+    for (int j = 0; j < kExpTab; ++j)
+        tab[j] = (double)exp2l((long double)j / (long double)kExpTab);
     // ln2 = LN2_HI + LN2_LO to about 1e-33
     const double ln2_hi = 0.6931471805599453094172321;
     const double ln2_lo = 2.3190468138462996e-17;
-    const double c = ln2_hi / 64.0;                   // exact: division by a power of two
-    const double hi = std::ldexp(std::floor(std::ldexp(c, 36 + 7)), -(36 + 7));
+    const double c = ln2_hi / kExpTab;                // exact: division by a power of two
+    // high part: c truncated to 34 significant bits (c is in [2^-9, 2^-8))
+    const double hi = std::ldexp(std::floor(std::ldexp(c, 34 + 8)), -(34 + 8));
     *l1 = hi;
-    *l2 = (c - hi) + ln2_lo / 64.0;
+    *l2 = (c - hi) + ln2_lo / kExpTab;
 }
 
 size_t sweep_smem_bytes(int prec, const SweepShape &s, int nx) {
     size_t elem = prec == 0 ? sizeof(double) : sizeof(float);
-    return (2ull * s.ng * s.rows * nx + 2ull * sweep_stage_elems(s.rows, nx) + 3ull * s.ng) * elem;
+    return (2ull * s.ng * s.rows * nx + 2ull * sweep_stage_elems(s.rows, nx) + 4ull * s.ng) * elem;
 }
 
 // Kernel attributes for shape s (dynamic shared memory; clusters of more
@@ -295,9 +310,12 @@ template <typename T, int MAXT, int MINB>
 static cudaError_t sweep_config(const SweepShape &s, int nx, cudaStream_t st,
                                 cudaLaunchConfig_t *cfg, cudaLaunchAttribute *attr) {
     const size_t smem = sweep_smem_bytes(sizeof(T) == 8 ? 0 : 1, s, nx);
+    // the limit is the same for every launch: a CUDA graph that captured a
+    // launch needing more than a later launch of the same kernel must still
+    // find the attribute large enough when it replays
     cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, MAXT, MINB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+                                         (int)kMaxSweepSmem);
     if (e == cudaSuccess && s.bands > kPortableBands)
         e = cudaFuncSetAttribute(sweep_kernel<T, MAXT, MINB>,
                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -312,7 +330,8 @@ static cudaError_t sweep_config(const SweepShape &s, int nx, cudaStream_t st,
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg->attrs = attr;
-    cfg->numAttrs = 1;
+    // one band: a plain launch (its implicit one-block cluster)
+    cfg->numAttrs = s.bands > 1 ? 1 : 0;
     return cudaSuccess;
 }
 
@@ -332,6 +351,9 @@ static cudaError_t clusters_t(const SweepShape &s, int nx, int *n) {
     cudaLaunchAttribute attr[1];
     cudaError_t e = sweep_config<T, MAXT, MINB>(s, nx, 0, &cfg, attr);
     if (e != cudaSuccess) return e;
+    if (s.bands == 1)  // plain launch: resident blocks per SM
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, sweep_kernel<T, MAXT, MINB>,
+                                                             s.threads, cfg.dynamicSmemBytes);
     return cudaOccupancyMaxActiveClusters(n, sweep_kernel<T, MAXT, MINB>, &cfg);
 }
 
@@ -366,7 +388,8 @@ static cudaError_t launch_sweep_batch_t(const SweepArgs<T> *args, const BatchIte
                                         int n_items, int bands, int threads, size_t smem,
                                         cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(sweep_batch_kernel<T, MAXT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kMaxSweepSmem);  // fixed, as for sweep_kernel
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(bands, n_items, 1);
@@ -379,7 +402,7 @@ static cudaError_t launch_sweep_batch_t(const SweepArgs<T> *args, const BatchIte
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = bands > 1 ? 1 : 0;  // one band: a plain launch
     return cudaLaunchKernelEx(&cfg, sweep_batch_kernel<T, MAXT>, args, items);
 }
 

@@ -826,18 +826,28 @@ int autotune_level(mg3d_handle *h, int k, int *evaluated) {
     }
     std::vector<SweepShape> cands;
     for (int ng : ngs)
-        for (int bands = 1; bands <= kMaxBands && bands <= L.ny; ++bands)
-            for (int th : {128, 256, 512})
+        for (int bands = 1; bands <= kMaxBands && bands <= L.ny; ++bands) {
+            // 128, 256, 512 threads and the block sizes that cover a band in
+            // 1-4 equal passes
+            const int band = ((L.ny + bands - 1) / bands) * L.nx;
+            std::vector<int> ths = {128, 256, 512};
+            for (int passes = 1; passes <= 4; ++passes) {
+                const int th = ((band + passes - 1) / passes + 31) / 32 * 32;
+                if (th >= 64 && th <= kMaxSweepThreads &&
+                    std::find(ths.begin(), ths.end(), th) == ths.end())
+                    ths.push_back(th);
+            }
+            for (int th : ths)
                 for (int lean = 0; lean < 3; ++lean) {
-                    if (lean == 2 && th > 256) continue;  // same as lean 0 at 512 threads
+                    if (lean == 2 && th > 256) continue;  // same as lean 0 above 256 threads
                     SweepShape s;
                     if (make_shape(h, k, ng, bands, th, &s) != MG3D_OK) continue;
-                    const int band = s.rows * L.nx;
                     if (th > 128 && th / 2 >= band) continue;  // a smaller block covers the band
                     s.lean = lean;
                     if (check_schedulable(h, k, s) != MG3D_OK) continue;
                     cands.push_back(s);
                 }
+        }
     g_last_error.clear();
     if (cands.empty()) return fail(MG3D_E_ARG, "no sweep shape fits");
     (void)0;
@@ -995,9 +1005,9 @@ int create_impl(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_qu
         MG_CUDA(cudaMemcpy(h->d_inv_phi, c.data(), nf * es, cudaMemcpyHostToDevice));
     }
     {
-        double tab[64];
+        double tab[kExpTab];
         exp_neg_constants(tab, &h->exp_l1, &h->exp_l2);
-        MG_TRY(dalloc(&h->d_exp_tab, 64));
+        MG_TRY(dalloc(&h->d_exp_tab, kExpTab));
         MG_CUDA(cudaMemcpy(h->d_exp_tab, tab, sizeof(tab), cudaMemcpyHostToDevice));
     }
     MG_TRY(dev_alloc(&h->pj, h->partial_elems * es));
@@ -1187,9 +1197,9 @@ int create_ml_impl(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
                         "bottom intensity"));
     }
     {
-        double tab[64];
+        double tab[kExpTab];
         exp_neg_constants(tab, &h->exp_l1, &h->exp_l2);
-        MG_TRY(dalloc(&h->d_exp_tab, 64));
+        MG_TRY(dalloc(&h->d_exp_tab, kExpTab));
         MG_CUDA(cudaMemcpy(h->d_exp_tab, tab, sizeof(tab), cudaMemcpyHostToDevice));
     }
     MG_TRY(dev_alloc(&h->ml_jx, 2 * (size_t)nf * F.nvox * es));
@@ -2154,15 +2164,16 @@ int mg3d_get_fs_config(const mg3d_handle *h, int level, int *freq_per_block, int
 
 int mg3d_check_exp(int n, const double *x_host, double *out_host) {
     if (n < 1 || !x_host || !out_host) return fail(MG3D_E_ARG, "bad arguments");
-    double tab[64], l1, l2;
+    double tab[kExpTab], l1, l2;
     exp_neg_constants(tab, &l1, &l2);
     double *d = nullptr;
-    MG_TRY(dalloc(&d, 64 + 3 * (size_t)n));
+    MG_TRY(dalloc(&d, kExpTab + 3 * (size_t)n));
     int rc = MG3D_OK;
+    double *dx = d + kExpTab, *dout = dx + n;
     cudaError_t e = cudaMemcpy(d, tab, sizeof(tab), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(d + 64, x_host, n * sizeof(double), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = launch_exp_check(n, d + 64, d + 64 + n, d, l1, l2, nullptr);
-    if (e == cudaSuccess) e = cudaMemcpy(out_host, d + 64 + n, 2 * n * sizeof(double),
+    if (e == cudaSuccess) e = cudaMemcpy(dx, x_host, n * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_exp_check(n, dx, dout, d, l1, l2, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(out_host, dout, 2 * n * sizeof(double),
                                          cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) rc = fail(MG3D_E_CUDA, std::string("exp check: ") + cudaGetErrorString(e));
     cudaFree(d);

@@ -13,6 +13,7 @@ constexpr int kMaxBands = 16;      // thread blocks per cluster sharing a plane 
 constexpr int kPortableBands = 8;  // cap for shapes chosen without a measurement
 constexpr int kMaxSweepThreads = 512;
 constexpr size_t kMaxSweepSmem = 200 * 1024;
+constexpr int kExpTab = 256;       // entries 2^{j/256} of the FP64 exp table
 
 // Upwind geometry of one sweep step of one ray.  The short characteristic of
 // every node on the plane crosses the upwind plane at the same horizontal
@@ -54,7 +55,7 @@ struct SweepArgs {
 };
 
 // Table and reduction constants of the FP64 e^{-x} of the sweep.
-void exp_neg_constants(double *tab64, double *l1, double *l2);
+void exp_neg_constants(double *tab, double *l1, double *l2);  // tab: kExpTab entries
 cudaError_t launch_exp_check(int n, const double *x, double *out, const double *tab, double l1,
                              double l2, cudaStream_t st);
 

@@ -130,9 +130,9 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
     T *buf = reinterpret_cast<T *>(smem_raw);
     const long raystride = (long)rows * nx;
     const long bufstride = 12 * raystride;
-    __shared__ double exp_tab[64];
+    __shared__ double exp_tab[kExpTab];
     if (sizeof(T) == 8) {
-        for (int i = threadIdx.x; i < 64; i += blockDim.x) exp_tab[i] = a.exp_tab[i];
+        for (int i = threadIdx.x; i < kExpTab; i += blockDim.x) exp_tab[i] = a.exp_tab[i];
         __syncthreads();
     }
     const ExpNegTable et{exp_tab, a.exp_l1, a.exp_l2};
@@ -224,8 +224,10 @@ static cudaError_t launch_ml_sweep_t(const MlSweepArgs<T> &a, int bands, int thr
                                      cudaStream_t st) {
     const size_t smem = ml_sweep_smem_bytes(sizeof(T) == 8 ? MG3D_PREC_F64 : MG3D_PREC_F32,
                                             a.rows, a.nx);
+    // one fixed limit for every launch, so graph replays never meet a lower one
     cudaError_t e = cudaFuncSetAttribute(ml_sweep_kernel<T, MAXT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kMaxSweepSmem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(bands, a.nfreq, 2);
@@ -238,7 +240,7 @@ static cudaError_t launch_ml_sweep_t(const MlSweepArgs<T> &a, int bands, int thr
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = bands > 1 ? 1 : 0;  // one band: a plain launch
     return cudaLaunchKernelEx(&cfg, ml_sweep_kernel<T, MAXT>, a);
 }
 
@@ -246,8 +248,10 @@ template <typename T, int MAXT>
 static cudaError_t launch_ml_sweep_batch_t(const MlSweepArgs<T> *args, const BatchItem *items,
                                            int n_items, int bands, int threads, size_t smem,
                                            cudaStream_t st) {
+    // one fixed limit for every launch, so graph replays never meet a lower one
     cudaError_t e = cudaFuncSetAttribute(ml_sweep_batch_kernel<T, MAXT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kMaxSweepSmem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(bands, n_items, 1);
@@ -260,7 +264,7 @@ static cudaError_t launch_ml_sweep_batch_t(const MlSweepArgs<T> *args, const Bat
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = bands > 1 ? 1 : 0;  // one band: a plain launch
     return cudaLaunchKernelEx(&cfg, ml_sweep_batch_kernel<T, MAXT>, args, items);
 }
 

@@ -44,7 +44,7 @@ constexpr long kOffPhi = kOffGeom + kGeomDoubles;
 constexpr long kOffInvPhi = kOffPhi + kMaxFreq;
 constexpr long kOffWphi = kOffInvPhi + kMaxFreq;
 constexpr long kOffExpTab = kOffWphi + kMaxFreq;
-constexpr long kScratchDoubles = kOffExpTab + 64;
+constexpr long kScratchDoubles = kOffExpTab + kExpTab;
 static_assert(sizeof(StepGeom) % sizeof(double) == 0, "geometry entries pack into doubles");
 
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
@@ -130,8 +130,9 @@ __global__ void noalloc_tables_kernel(int nx, int ny, int nz, double dx, double 
         }
         for (int f = 0; f < nfreq; ++f) wphi[f] /= sum * kRays;
     }
-    if (blockIdx.x == 0 && threadIdx.x < 64)
-        scratch[kOffExpTab + threadIdx.x] = exp2((double)threadIdx.x / 64.0);
+    if (blockIdx.x == 0)
+        for (int j = threadIdx.x; j < kExpTab; j += blockDim.x)
+            scratch[kOffExpTab + j] = exp2((double)j / kExpTab);
 }
 
 // Jeff and U: the 24 ray partials of every node added in ray order.
@@ -210,7 +211,7 @@ extern "C" int mg3d_formal_solve_noalloc(int nx, int ny, int nz, double dx, doub
         nx, ny, nz, dx, dy, z_dev, quad_a, nf, atom->x_max, scratch);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) {
-        double tab_unused[64], l1 = 0.0, l2 = 0.0;
+        double tab_unused[kExpTab], l1 = 0.0, l2 = 0.0;
         exp_neg_constants(tab_unused, &l1, &l2);
         unsigned up_mask = 0;
         for (int r = 0; r < kRays; ++r)

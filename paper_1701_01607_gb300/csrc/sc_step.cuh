@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include "mg3d_internal.h"
+
 namespace mg3d {
 
 // Linear short-characteristics weights for optical path x:
@@ -15,33 +17,32 @@ template <typename T>
 struct ScWeights;
 
 // e^{-x} for x >= 0 by the table-driven method of Tang (ACM TOMS 15, 1989):
-// -x = (64 m + j) ln2/64 + r with integer m, j in [0, 64) and |r| <= ln2/128,
-// so e^{-x} = 2^m 2^{j/64} e^r.  The reduction uses a two-part ln2/64 whose
-// high part times any |n| < 2^17 is exact; e^r - 1 is its Taylor polynomial of
-// degree 5 (truncation < 4e-17 relative); 2^{j/64} comes from a 64-entry
-// table and 2^m is applied by adding m to the exponent field.  Results below
-// e^{-708} are flushed to zero.
+// -x = (256 m + j) ln2/256 + r with integer m, j in [0, 256) and
+// |r| <= ln2/512, so e^{-x} = 2^m 2^{j/256} e^r.  The reduction uses a
+// two-part ln2/256 whose high part (34 significant bits) times any |n| < 2^19
+// is exact; e^r - 1 is its Taylor polynomial of degree 4 (truncation < 4e-17
+// relative); 2^{j/256} comes from a 256-entry table and 2^m is applied by
+// adding m to the exponent field.  Results below e^{-708} are flushed to zero.
 struct ExpNegTable {
-    const double *tab;   // [64] 2^{j/64}
-    double l1, l2;       // ln2/64 = l1 + l2, l1 with 36 significant bits
+    const double *tab;   // [kExpTab] 2^{j/256}
+    double l1, l2;       // ln2/256 = l1 + l2
 };
 
 __device__ __forceinline__ double exp_neg(double x, const ExpNegTable e) {
     if (x > 708.0) return 0.0;
     const double magic = 6755399441055744.0;  // 1.5 * 2^52
-    const double t = fma(x, -92.33248261689366, magic);  // -x * 64/ln2, rounded to an integer
+    const double t = fma(x, -369.3299304675746, magic);  // -x * 256/ln2, rounded to an integer
     const int n = __double2loint(t);
     const double nd = t - magic;
     double r = fma(-nd, e.l1, -x);
     r = fma(-nd, e.l2, r);
-    double p = fma(r, 1.0 / 120.0, 1.0 / 24.0);
-    p = fma(p, r, 1.0 / 6.0);
+    double p = fma(r, 1.0 / 24.0, 1.0 / 6.0);
     p = fma(p, r, 0.5);
     p = fma(p, r, 1.0);
     const double q = p * r;                      // e^r - 1
-    const double tj = e.tab[n & 63];
-    const double v = fma(tj, q, tj);             // 2^{j/64} e^r, in [0.99, 2.01)
-    const long long bits = __double_as_longlong(v) + ((long long)(n >> 6) << 52);
+    const double tj = e.tab[n & (kExpTab - 1)];
+    const double v = fma(tj, q, tj);             // 2^{j/256} e^r, in [0.99, 2.01)
+    const long long bits = __double_as_longlong(v) + ((long long)(n >> 8) << 52);
     return __longlong_as_double(bits);
 }
 
