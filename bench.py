@@ -53,8 +53,8 @@ ALG_FLOPS_PER_UNIT = 7 + 5 + 4 + (1 + 1 + 2 + 1 + 1) * N_DISTINCT_PHI / 9.0 + 16
 FP64_NOMINAL_TFLOPS = 1.25      # GB300, at the 2070 MHz maximum SM clock
 # DRAM bytes (read + write) of one finest-grid FP64 sweep launch, from one ncu
 # capture of the current kernel at this launch shape (ng, bands, threads,
-# lean); reported only when the autotuner picks the same shape
-FINE_SWEEP_TRAFFIC = {"shape": [9, 5, 512, 0], "bytes": 13826560 + 141738240}
+# lean, stage); reported only when the autotuner picks the same shape
+FINE_SWEEP_TRAFFIC = {"shape": [9, 5, 512, 0, 1], "bytes": 13826560 + 141738240}
 SM_MAX_MHZ = 2070.0
 
 
@@ -370,7 +370,7 @@ def run_reference(args):
 def run_profile_case(prec_name, launches, shape):
     """A few finest-grid formal solutions of the bench workload, for ncu.
 
-    ``shape`` "ng,bands,threads[,lean]" fixes the sweep's launch shape (e.g. the one
+    ``shape`` "ng,bands,threads[,lean[,stage]]" fixes the sweep's launch shape (e.g. the one
     the autotuner chose in a bench run); empty keeps the library default.
     No autotuning runs here, so every sweep launch is a profiled one."""
     from paper_1701_01607_gb300 import mg3d as m
@@ -401,12 +401,12 @@ def main():
                     help="keep the library's default sweep shapes")
     ap.add_argument("--shapes", default="",
                     help='sweep shapes instead of autotuning, as a bench line reports them: '
-                         '{"f64": {"1": [ng, bands, threads, lean], ...}, "f32": {...}}')
+                         '{"f64": {"1": [ng, bands, threads, lean, stage], ...}, "f32": {...}}')
     ap.add_argument("--profile-sweep", choices=["f64", "f32"],
                     help="only run a few finest-grid formal solutions (for ncu)")
     ap.add_argument("--profile-launches", type=int, default=3)
     ap.add_argument("--profile-shape", default="",
-                    help="ng,bands,threads[,lean] of the profiled sweep")
+                    help="ng,bands,threads[,lean[,stage]] of the profiled sweep")
     args = ap.parse_args()
     if args.profile_sweep:
         run_profile_case(args.profile_sweep, args.profile_launches, args.profile_shape)

@@ -326,23 +326,36 @@ int mg3d_prolong(mg3d_handle *h, int level_fine, int ncomp, const double *coarse
  * frequencies per thread block, bands = thread blocks (one cluster) sharing
  * each horizontal plane (1..16; above 8 a non-portable cluster size that not
  * every shape can be scheduled with), threads per block (32..512, a multiple
- * of 32), and
- * the register budget of the kernel variant: lean = 0 full, 1 compiled for
- * 1024 resident threads per SM (64 registers per thread), 2 for three blocks
- * of at most 256 threads per SM (85 registers).
- * The library picks a shape at creation (at most 8 bands); this overrides
- * it.  Returns MG3D_E_ARG if the shape does not fit in shared memory or the
- * GPU cannot hold one of its clusters. */
+ * of 32), the register budget of the kernel variant (lean = 0 full, 1
+ * compiled for 1024 resident threads per SM, i.e. 64 registers per thread, 2
+ * for three blocks of at most 256 threads per SM, 85 registers), and stage =
+ * 1 to copy each step's rows of chi0 and S into shared memory one step ahead
+ * (0: read them from global memory where used, which frees that shared
+ * memory for more resident blocks).
+ * The library picks a shape at creation (at most 8 bands, staged); this
+ * overrides it.  Returns MG3D_E_ARG if the shape does not fit in shared
+ * memory or the GPU cannot hold one of its clusters. */
 int mg3d_set_fs_config(mg3d_handle *h, int level, int freq_per_block, int bands,
-                       int threads, int lean);
+                       int threads, int lean, int stage);
 int mg3d_get_fs_config(const mg3d_handle *h, int level, int *freq_per_block, int *bands,
-                       int *threads, int *lean);
+                       int *threads, int *lean, int *stage);
+
+/* Occupancy of a candidate shape (same arguments as mg3d_set_fs_config) on
+ * this GPU without applying it: *max_clusters = clusters of the shape the GPU
+ * can hold at once (0: it cannot run; a sweep launches 24 x ceil(n_freq /
+ * freq_per_block) clusters, so fewer than that means several waves), and
+ * *smem_bytes = its dynamic shared memory per block.  Either output may be
+ * NULL.  MG3D_E_ARG for shapes mg3d_set_fs_config would reject as invalid. */
+int mg3d_get_fs_occupancy(mg3d_handle *h, int level, int freq_per_block, int bands,
+                          int threads, int lean, int stage, int *max_clusters,
+                          long long *smem_bytes);
 
 /* Autotuner: times candidate sweep shapes on this GPU with the level's current
  * populations and keeps the fastest per level (level = 0: every level).
  * Candidates: every number of frequency groups up to 64, 1-16 bands,
- * 128/256/512 threads and the register budgets that fit and can be
- * scheduled; one launch each,
+ * 128/256/512 threads and the block sizes that cover a band in 1-4 equal
+ * passes, the three register budgets, staged or not, where the shape fits and
+ * can be scheduled; one launch each,
  * then the best eight three more times.  Overwrites the partial sums (not the populations).
  * *evaluated and *seconds (nullable) report the candidates and wall time. */
 int mg3d_autotune(mg3d_handle *h, int level, int *evaluated, double *seconds);

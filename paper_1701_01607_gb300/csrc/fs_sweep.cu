@@ -94,8 +94,10 @@ __device__ __forceinline__ void stage_rows(const SweepArgs<T> &a, T *dst, long a
     }
 }
 
-// Body of the sweep for ray r and frequency group g of one problem.
-template <typename T>
+// Body of the sweep for ray r and frequency group g of one problem.  STAGE:
+// chi0 and S rows of each step are copied to shared memory one step ahead;
+// without it they are read from global memory (L1/L2) where used.
+template <typename T, bool STAGE>
 __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) {
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
@@ -116,7 +118,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
     T *buf = reinterpret_cast<T *>(smem_raw);
     const long bufstride = (long)a.ng * rows * nx;
     T *stage = buf + 2 * bufstride;
-    const long stagestride = sweep_stage_elems(rows, nx);
+    const long stagestride = STAGE ? sweep_stage_elems(rows, nx) : 0;
     T *tabs = stage + 2 * stagestride;
     T *phi = tabs, *inv_phi = tabs + a.ng, *wphi = tabs + 2 * a.ng, *wu = tabs + 3 * a.ng;
     for (int i = threadIdx.x; i < nf; i += blockDim.x) {
@@ -161,7 +163,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
                       vec16);
         __pipeline_commit();
     };
-    if (nz > 1) stage_step(1);
+    if (STAGE && nz > 1) stage_step(1);
 
     for (int t = 0; t < nz; ++t) {
         const int k = up ? t : nz - 1 - t;
@@ -185,12 +187,15 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
                 pu[v] = cu;
             }
         } else {
-            __pipeline_wait_prior(0);
-            __syncthreads();
-            if (t + 1 < nz) stage_step(t + 1);
+            if constexpr (STAGE) {
+                __pipeline_wait_prior(0);
+                __syncthreads();
+                if (t + 1 < nz) stage_step(t + 1);
+            }
             const T *st = stage + (t & 1) * stagestride;
             const T *chiW = st, *SW = st + (long)(rows + 1) * nx;
             const T *chiB = st + 2L * (rows + 1) * nx, *SB = chiB + (long)rows * nx;
+            const int kp = up ? k - 1 : k + 1;
             const T *prev = buf + ((t - 1) & 1) * bufstride;
             const StepGeom o = a.geom[(long)r * nz + t];
             const T tx = (T)o.tx, ty = (T)o.ty;
@@ -206,13 +211,30 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
                 int ya = y + o.iy0;
                 if (ya >= ny) ya -= ny;
                 const int yb = (ya + 1 == ny) ? 0 : ya + 1;
-                // window row yl holds row ya, row yl + 1 holds yb
-                const T *ca = chiW + (long)yl * nx, *cb = ca + nx;
-                const T *sa = SW + (long)yl * nx, *sb = sa + nx;
+                // rows ya, yb of chi0 and S on plane kp, row y on plane k:
+                // staged (window row yl holds ya, row yl + 1 holds yb) or in
+                // global memory
+                const T *ca, *cb, *sa, *sb, *cl, *sl;
+                if constexpr (STAGE) {
+                    ca = chiW + (long)yl * nx;
+                    cb = ca + nx;
+                    sa = SW + (long)yl * nx;
+                    sb = sa + nx;
+                    cl = chiB + (long)yl * nx;
+                    sl = SB + (long)yl * nx;
+                } else {
+                    const long pp = (long)kp * nplane, pk = (long)k * nplane + (long)y * nx;
+                    ca = a.chi0 + pp + (long)ya * nx;
+                    cb = a.chi0 + pp + (long)yb * nx;
+                    sa = a.S + pp + (long)ya * nx;
+                    sb = a.S + pp + (long)yb * nx;
+                    cl = a.chi0 + pk;
+                    sl = a.S + pk;
+                }
                 const T chi_up = w00 * ca[xa] + w10 * ca[xb] + w01 * cb[xa] + w11 * cb[xb];
                 const T S_up = w00 * sa[xa] + w10 * sa[xb] + w01 * sb[xa] + w11 * sb[xb];
-                const T chi_loc = chiB[(long)yl * nx + x];
-                const T S_loc = SB[(long)yl * nx + x];
+                const T chi_loc = cl[x];
+                const T S_loc = sl[x];
                 const T dtau0 = (chi_up + chi_loc) * half_s;
                 // 1/dtau0 is only used where dtau0 phi >= the series threshold,
                 // so dtau0 > 0 there
@@ -224,19 +246,49 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
                 Pa += (long)(ya - ba * rows) * nx;
                 Pb += (long)(yb - bb * rows) * nx;
                 T cj = 0, cu = 0;
-                T ex = 0, w0 = 0, wup = 0, u = 0;
-                for (int f = 0; f < nf; ++f) {
+                // new intensity of frequency f from its step weights
+                auto step = [&](int f, T ex, T w0, T wup) {
                     const long off = (long)f * rows * nx;
                     const T I_up = w00 * Pa[off + xa] + w10 * Pa[off + xb] +
                                    w01 * Pb[off + xa] + w11 * Pb[off + xb];
-                    if (is_fresh(f)) {
-                        ScWeights<T>::eval(dtau0 * phi[f], inv_dtau0 * inv_phi[f], et, ex, w0,
-                                           wup, u);
-                        cu += wu[f] * u;
-                    }
                     const T part = I_up * ex + wup * S_up;
                     cur[((long)f * rows + yl) * nx + x] = part + w0 * S_loc;
                     cj += wphi[f] * part;
+                };
+                // weight slots: a frequency and, when its mirror follows, the
+                // mirror.  FP32 takes two slots per pass, so that their
+                // independent weight evaluations overlap (its pipes wait on
+                // latency); FP64 is bound by the FP64 pipe's throughput, where
+                // the extra registers of two slots cost more than they hide.
+                constexpr bool kTwoSlots = sizeof(T) == 4;
+                for (int f = 0; f < nf;) {
+                    const bool a2 = f + 1 < nf && !is_fresh(f + 1);
+                    const int fb = f + (a2 ? 2 : 1);
+                    if (kTwoSlots && fb < nf) {
+                        const bool b2 = fb + 1 < nf && !is_fresh(fb + 1);
+                        const T xa_ = dtau0 * phi[f], xb_ = dtau0 * phi[fb];
+                        T exa, w0a, wupa, ua, exb, w0b, wupb, ub;
+                        ScWeights<T>::closed(xa_, inv_dtau0 * inv_phi[f], et, exa, w0a, wupa, ua);
+                        ScWeights<T>::closed(xb_, inv_dtau0 * inv_phi[fb], et, exb, w0b, wupb,
+                                             ub);
+                        if (ScWeights<T>::small(xa_)) ScWeights<T>::series(xa_, w0a, wupa, ua);
+                        if (ScWeights<T>::small(xb_)) ScWeights<T>::series(xb_, w0b, wupb, ub);
+                        cu += wu[f] * ua;
+                        cu += wu[fb] * ub;
+                        step(f, exa, w0a, wupa);
+                        if (a2) step(f + 1, exa, w0a, wupa);
+                        step(fb, exb, w0b, wupb);
+                        if (b2) step(fb + 1, exb, w0b, wupb);
+                        f = fb + (b2 ? 2 : 1);
+                    } else {
+                        T ex, w0, wup, u;
+                        ScWeights<T>::eval(dtau0 * phi[f], inv_dtau0 * inv_phi[f], et, ex, w0,
+                                           wup, u);
+                        cu += wu[f] * u;
+                        step(f, ex, w0, wup);
+                        if (a2) step(f + 1, ex, w0, wup);
+                        f = fb;
+                    }
                 }
                 const long v = (long)k * nplane + (long)y * nx + x;
                 pj[v] = cj;
@@ -253,9 +305,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
 // blocks per SM it must fit, which sets the register budget (MINB = 1: up to
 // 255 registers; 1024/MAXT: 64 registers, 32 resident warps per SM; 3 blocks
 // of 256: 85 registers).
-template <typename T, int MAXT, int MINB>
+template <typename T, int MAXT, int MINB, bool STAGE>
 __global__ void __launch_bounds__(MAXT, MINB) sweep_kernel(const SweepArgs<T> a) {
-    sweep_body<T>(a, blockIdx.y, blockIdx.z);
+    sweep_body<T, STAGE>(a, blockIdx.y, blockIdx.z);
 }
 
 // Batched sweep: cluster y of the grid runs work item items[y] = (problem,
@@ -266,7 +318,7 @@ __global__ void __launch_bounds__(MAXT, 1024 / MAXT) sweep_batch_kernel(
     const SweepArgs<T> *__restrict__ args, const BatchItem *__restrict__ items) {
     const BatchItem it = items[blockIdx.y];
     const SweepArgs<T> a = args[it.member];
-    sweep_body<T>(a, it.group, it.ray);
+    sweep_body<T, true>(a, it.group, it.ray);
 }
 
 __global__ void exp_check_kernel(int n, const double *__restrict__ x, double *__restrict__ out,
@@ -300,24 +352,26 @@ void exp_neg_constants(double *tab, double *l1, double *l2) {
 
 size_t sweep_smem_bytes(int prec, const SweepShape &s, int nx) {
     size_t elem = prec == 0 ? sizeof(double) : sizeof(float);
-    return (2ull * s.ng * s.rows * nx + 2ull * sweep_stage_elems(s.rows, nx) + 4ull * s.ng) * elem;
+    return (2ull * s.ng * s.rows * nx + (s.stage ? 2ull * sweep_stage_elems(s.rows, nx) : 0ull) +
+            4ull * s.ng) *
+           elem;
 }
 
 // Kernel attributes for shape s (dynamic shared memory; clusters of more
 // than 8 blocks are a non-portable size the kernel must opt into) and the
 // launch configuration; a is null for an occupancy query.
-template <typename T, int MAXT, int MINB>
+template <typename T, int MAXT, int MINB, bool STAGE>
 static cudaError_t sweep_config(const SweepShape &s, int nx, cudaStream_t st,
                                 cudaLaunchConfig_t *cfg, cudaLaunchAttribute *attr) {
     const size_t smem = sweep_smem_bytes(sizeof(T) == 8 ? 0 : 1, s, nx);
     // the limit is the same for every launch: a CUDA graph that captured a
     // launch needing more than a later launch of the same kernel must still
     // find the attribute large enough when it replays
-    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, MAXT, MINB>,
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, MAXT, MINB, STAGE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kMaxSweepSmem);
     if (e == cudaSuccess && s.bands > kPortableBands)
-        e = cudaFuncSetAttribute(sweep_kernel<T, MAXT, MINB>,
+        e = cudaFuncSetAttribute(sweep_kernel<T, MAXT, MINB, STAGE>,
                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     *cfg = cudaLaunchConfig_t{};
@@ -335,47 +389,59 @@ static cudaError_t sweep_config(const SweepShape &s, int nx, cudaStream_t st,
     return cudaSuccess;
 }
 
-template <typename T, int MAXT, int MINB>
+template <typename T, int MAXT, int MINB, bool STAGE>
 static cudaError_t launch_sweep_t(const SweepArgs<T> &a, const SweepShape &s,
                                   cudaStream_t st) {
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
-    cudaError_t e = sweep_config<T, MAXT, MINB>(s, a.nx, st, &cfg, attr);
+    cudaError_t e = sweep_config<T, MAXT, MINB, STAGE>(s, a.nx, st, &cfg, attr);
     if (e != cudaSuccess) return e;
-    return cudaLaunchKernelEx(&cfg, sweep_kernel<T, MAXT, MINB>, a);
+    return cudaLaunchKernelEx(&cfg, sweep_kernel<T, MAXT, MINB, STAGE>, a);
 }
 
-template <typename T, int MAXT, int MINB>
+template <typename T, int MAXT, int MINB, bool STAGE>
 static cudaError_t clusters_t(const SweepShape &s, int nx, int *n) {
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
-    cudaError_t e = sweep_config<T, MAXT, MINB>(s, nx, 0, &cfg, attr);
+    cudaError_t e = sweep_config<T, MAXT, MINB, STAGE>(s, nx, 0, &cfg, attr);
     if (e != cudaSuccess) return e;
     if (s.bands == 1)  // plain launch: resident blocks per SM
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, sweep_kernel<T, MAXT, MINB>,
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, sweep_kernel<T, MAXT, MINB, STAGE>,
                                                              s.threads, cfg.dynamicSmemBytes);
-    return cudaOccupancyMaxActiveClusters(n, sweep_kernel<T, MAXT, MINB>, &cfg);
+    return cudaOccupancyMaxActiveClusters(n, sweep_kernel<T, MAXT, MINB, STAGE>, &cfg);
+}
+
+template <typename T, bool STAGE>
+static cudaError_t launch_sweep_st(const SweepArgs<T> &a, const SweepShape &s, cudaStream_t st) {
+    if (s.threads <= 256) {
+        if (s.lean == 1) return launch_sweep_t<T, 256, 4, STAGE>(a, s, st);
+        if (s.lean == 2) return launch_sweep_t<T, 256, 3, STAGE>(a, s, st);
+        return launch_sweep_t<T, 256, 1, STAGE>(a, s, st);
+    }
+    return s.lean == 1 ? launch_sweep_t<T, 512, 2, STAGE>(a, s, st)
+                       : launch_sweep_t<T, 512, 1, STAGE>(a, s, st);
 }
 
 template <typename T>
 static cudaError_t launch_sweep_any(const SweepArgs<T> &a, const SweepShape &s,
                                     cudaStream_t st) {
+    return s.stage ? launch_sweep_st<T, true>(a, s, st) : launch_sweep_st<T, false>(a, s, st);
+}
+
+template <typename T, bool STAGE>
+static cudaError_t clusters_st(const SweepShape &s, int nx, int *n) {
     if (s.threads <= 256) {
-        if (s.lean == 1) return launch_sweep_t<T, 256, 4>(a, s, st);
-        if (s.lean == 2) return launch_sweep_t<T, 256, 3>(a, s, st);
-        return launch_sweep_t<T, 256, 1>(a, s, st);
+        if (s.lean == 1) return clusters_t<T, 256, 4, STAGE>(s, nx, n);
+        if (s.lean == 2) return clusters_t<T, 256, 3, STAGE>(s, nx, n);
+        return clusters_t<T, 256, 1, STAGE>(s, nx, n);
     }
-    return s.lean == 1 ? launch_sweep_t<T, 512, 2>(a, s, st) : launch_sweep_t<T, 512, 1>(a, s, st);
+    return s.lean == 1 ? clusters_t<T, 512, 2, STAGE>(s, nx, n)
+                       : clusters_t<T, 512, 1, STAGE>(s, nx, n);
 }
 
 template <typename T>
 static cudaError_t clusters_any(const SweepShape &s, int nx, int *n) {
-    if (s.threads <= 256) {
-        if (s.lean == 1) return clusters_t<T, 256, 4>(s, nx, n);
-        if (s.lean == 2) return clusters_t<T, 256, 3>(s, nx, n);
-        return clusters_t<T, 256, 1>(s, nx, n);
-    }
-    return s.lean == 1 ? clusters_t<T, 512, 2>(s, nx, n) : clusters_t<T, 512, 1>(s, nx, n);
+    return s.stage ? clusters_st<T, true>(s, nx, n) : clusters_st<T, false>(s, nx, n);
 }
 
 cudaError_t sweep_active_clusters(int prec, const SweepShape &s, int nx, int *n) {

@@ -107,7 +107,9 @@ struct mg3d_handle {
     unsigned up_mask = 0;
     Level lev[MG3D_MAX_GRIDS + 1];
     std::vector<double> phi, wphi;
-    void *d_phi = nullptr, *d_wphi = nullptr, *d_inv_phi = nullptr;
+    // frequency tables of the sweep, [order][phi, 1/phi, w phi / 24][n_freq]
+    // in the formal-solution precision (see freq_tables)
+    void *d_ftab = nullptr;
     double *d_exp_tab = nullptr;         // [64] table of the FP64 exp in the sweep
     double exp_l1 = 0, exp_l2 = 0;
     void *pj = nullptr, *pu = nullptr;
@@ -186,6 +188,44 @@ void build_frequencies(mg3d_handle *h) {
         sum += h->wphi[i];
     }
     for (int i = 0; i < nf; ++i) h->wphi[i] /= sum;
+}
+
+// Frequency index i at table position j.  Order 0 pairs the mirror
+// frequencies with the centre last (x_0, x_{nf-1}, x_1, x_{nf-2}, ..., centre),
+// order 1 puts the centre (odd nf) first and then the pairs.
+int mirror_order(int nf, int order, int j) {
+    if (order == 1 && nf % 2 == 1) {
+        if (j == 0) return nf / 2;
+        --j;
+    }
+    return j % 2 == 0 ? j / 2 : nf - 1 - j / 2;
+}
+
+// Frequency tables for a sweep whose blocks take ng frequencies each.  Blocks
+// of an even number of frequencies take order 0 (each group whole pairs, the
+// centre alone at the end); blocks of an odd number take order 1 (the first
+// group is the centre and pairs, and for two groups the second is pairs
+// only), so that mirror pairs share a block, and so their weights, wherever
+// the group size allows.
+template <typename T>
+void freq_tables(const mg3d_handle *h, int ng, const T **phi, const T **inv_phi,
+                 const T **wphi) {
+    const int nf = h->atom.n_freq;
+    const T *base = static_cast<const T *>(h->d_ftab) + (ng % 2 == 1 ? 3 * (size_t)nf : 0);
+    *phi = base;
+    *inv_phi = base + nf;
+    *wphi = base + 2 * (size_t)nf;
+}
+
+// Launch arguments of the sweep of level L with shape s.
+template <typename T>
+SweepArgs<T> sweep_args(const mg3d_handle *h, const Level &L, const SweepShape &s) {
+    const T *phi, *inv_phi, *wphi;
+    freq_tables<T>(h, s.ng, &phi, &inv_phi, &wphi);
+    return SweepArgs<T>{L.nx, L.ny, L.nz, h->atom.n_freq, s.ng, s.ngroups, s.rows,
+                        h->up_mask, (const T *)L.chi0, (const T *)L.S, (const T *)L.bbot,
+                        L.geom, phi, inv_phi, wphi, (T *)h->pj, (T *)h->pu, h->d_exp_tab,
+                        h->exp_l1, h->exp_l2};
 }
 
 // Upwind crossing of every (ray, sweep step): for step t the plane is
@@ -410,21 +450,9 @@ int formal_solution(mg3d_handle *h, int k) {
     }
     cudaError_t e;
     if (h->prec == MG3D_PREC_F64) {
-        SweepArgs<double> a{L.nx, L.ny, L.nz, h->atom.n_freq, L.shape.ng, L.shape.ngroups,
-                            L.shape.rows, h->up_mask, (const double *)L.chi0,
-                            (const double *)L.S, (const double *)L.bbot, L.geom,
-                            (const double *)h->d_phi, (const double *)h->d_inv_phi,
-                            (const double *)h->d_wphi, (double *)h->pj, (double *)h->pu,
-                            h->d_exp_tab, h->exp_l1, h->exp_l2};
-        e = launch_sweep_f64(a, L.shape, h->stream);
+        e = launch_sweep_f64(sweep_args<double>(h, L, L.shape), L.shape, h->stream);
     } else {
-        SweepArgs<float> a{L.nx, L.ny, L.nz, h->atom.n_freq, L.shape.ng, L.shape.ngroups,
-                           L.shape.rows, h->up_mask, (const float *)L.chi0,
-                           (const float *)L.S, (const float *)L.bbot, L.geom,
-                           (const float *)h->d_phi, (const float *)h->d_inv_phi,
-                           (const float *)h->d_wphi, (float *)h->pj, (float *)h->pu,
-                           h->d_exp_tab, h->exp_l1, h->exp_l2};
-        e = launch_sweep_f32(a, L.shape, h->stream);
+        e = launch_sweep_f32(sweep_args<float>(h, L, L.shape), L.shape, h->stream);
     }
     MG_TRY(launched(h, e, "sweep"));
     if (h->timing) {
@@ -723,7 +751,24 @@ int make_shape(const mg3d_handle *h, int k, int ng, int bands, int threads, Swee
         return fail(MG3D_E_ARG, "bad sweep shape");
     SweepShape s{ng, (nf + ng - 1) / ng, bands, (L.ny + bands - 1) / bands, threads};
     if ((long)(bands - 1) * s.rows >= L.ny) return fail(MG3D_E_ARG, "empty band");
-    if (sweep_smem_bytes(h->prec, s, L.nx) > kMaxSweepSmem)
+    *out = s;
+    return MG3D_OK;
+}
+
+// Shape of the given launch parameters on a level, validated except for
+// whether the GPU can schedule it.
+static int shape_from_args(const mg3d_handle *h, int level, int freq_per_block, int bands,
+                           int threads, int lean, int stage, SweepShape *out) {
+    MG_TRY(check_level(h, level));
+    if (h->kind != 0) return fail(MG3D_E_STATE, "sweep shapes apply to two-level handles");
+    if (lean < 0 || lean > 2 || (lean == 2 && threads > 256))
+        return fail(MG3D_E_ARG, "lean must be 0, 1 or (up to 256 threads) 2");
+    if (stage != 0 && stage != 1) return fail(MG3D_E_ARG, "stage must be 0 or 1");
+    SweepShape s;
+    MG_TRY(make_shape(h, level, freq_per_block, bands, threads, &s));
+    s.lean = lean;
+    s.stage = stage;
+    if (sweep_smem_bytes(h->prec, s, h->lev[level].nx) > kMaxSweepSmem)
         return fail(MG3D_E_ARG, "sweep shape exceeds shared memory");
     *out = s;
     return MG3D_OK;
@@ -781,21 +826,9 @@ int time_shape(mg3d_handle *h, int k, const SweepShape &s, int reps, float *ms) 
     cudaError_t e = cudaEventRecord(a, h->stream);
     for (int i = 0; i < reps && e == cudaSuccess; ++i) {
         if (h->prec == MG3D_PREC_F64) {
-            SweepArgs<double> sa{L.nx, L.ny, L.nz, h->atom.n_freq, s.ng, s.ngroups, s.rows,
-                                 h->up_mask, (const double *)L.chi0, (const double *)L.S,
-                                 (const double *)L.bbot, L.geom, (const double *)h->d_phi,
-                                 (const double *)h->d_inv_phi, (const double *)h->d_wphi,
-                                 (double *)h->pj, (double *)h->pu, h->d_exp_tab, h->exp_l1,
-                                 h->exp_l2};
-            e = launch_sweep_f64(sa, s, h->stream);
+            e = launch_sweep_f64(sweep_args<double>(h, L, s), s, h->stream);
         } else {
-            SweepArgs<float> sa{L.nx, L.ny, L.nz, h->atom.n_freq, s.ng, s.ngroups, s.rows,
-                                h->up_mask, (const float *)L.chi0, (const float *)L.S,
-                                (const float *)L.bbot, L.geom, (const float *)h->d_phi,
-                                (const float *)h->d_inv_phi, (const float *)h->d_wphi,
-                                (float *)h->pj, (float *)h->pu, h->d_exp_tab, h->exp_l1,
-                                h->exp_l2};
-            e = launch_sweep_f32(sa, s, h->stream);
+            e = launch_sweep_f32(sweep_args<float>(h, L, s), s, h->stream);
         }
         ++h->launches;
     }
@@ -838,15 +871,16 @@ int autotune_level(mg3d_handle *h, int k, int *evaluated) {
                     ths.push_back(th);
             }
             for (int th : ths)
-                for (int lean = 0; lean < 3; ++lean) {
-                    if (lean == 2 && th > 256) continue;  // same as lean 0 above 256 threads
-                    SweepShape s;
-                    if (make_shape(h, k, ng, bands, th, &s) != MG3D_OK) continue;
-                    if (th > 128 && th / 2 >= band) continue;  // a smaller block covers the band
-                    s.lean = lean;
-                    if (check_schedulable(h, k, s) != MG3D_OK) continue;
-                    cands.push_back(s);
-                }
+                for (int lean = 0; lean < 3; ++lean)
+                    for (int stage = 1; stage >= 0; --stage) {
+                        if (lean == 2 && th > 256) continue;  // same as lean 0 above 256
+                        if (th > 128 && th / 2 >= band) continue;  // a smaller block covers it
+                        SweepShape s;
+                        if (shape_from_args(h, k, ng, bands, th, lean, stage, &s) != MG3D_OK)
+                            continue;
+                        if (check_schedulable(h, k, s) != MG3D_OK) continue;
+                        cands.push_back(s);
+                    }
         }
     g_last_error.clear();
     if (cands.empty()) return fail(MG3D_E_ARG, "no sweep shape fits");
@@ -973,36 +1007,26 @@ int create_impl(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_qu
                                                 h->stream),
                         "planck"));
     }
-    // frequency tables in the formal-solution precision, in mirror-pair
-    // order (x_0, x_{nf-1}, x_1, x_{nf-2}, ..., then the centre): the sweep
-    // sums over frequencies, so their order is internal to it, and a
-    // frequency whose phi equals its predecessor's reuses that one's
-    // short-characteristics weights
+    // frequency tables in the formal-solution precision, in two orders: the
+    // sweep sums over frequencies, so their order is internal to it, and a
+    // frequency whose phi equals its predecessor's in the table reuses that
+    // one's short-characteristics weights (see freq_tables)
     const int nf = atom->n_freq;
-    MG_TRY(dev_alloc(&h->d_phi, nf * es));
-    MG_TRY(dev_alloc(&h->d_wphi, nf * es));
-    MG_TRY(dev_alloc(&h->d_inv_phi, nf * es));
-    std::vector<double> phi_t(nf), wphi_ray(nf), inv_phi(nf);
-    for (int j = 0; j < nf; ++j) {
-        const int i = j % 2 == 0 ? j / 2 : nf - 1 - j / 2;
-        phi_t[j] = h->phi[i];
-        wphi_ray[j] = h->wphi[i] / kRays;
-        inv_phi[j] = 1.0 / h->phi[i];
-    }
-    if (h->prec == MG3D_PREC_F64) {
-        MG_CUDA(cudaMemcpy(h->d_phi, phi_t.data(), nf * es, cudaMemcpyHostToDevice));
-        MG_CUDA(cudaMemcpy(h->d_wphi, wphi_ray.data(), nf * es, cudaMemcpyHostToDevice));
-        MG_CUDA(cudaMemcpy(h->d_inv_phi, inv_phi.data(), nf * es, cudaMemcpyHostToDevice));
-    } else {
-        std::vector<float> a(nf), b(nf), c(nf);
-        for (int i = 0; i < nf; ++i) {
-            a[i] = (float)phi_t[i];
-            b[i] = (float)wphi_ray[i];
-            c[i] = (float)inv_phi[i];
+    MG_TRY(dev_alloc(&h->d_ftab, 6 * (size_t)nf * es));
+    std::vector<double> tabs(6 * (size_t)nf);
+    for (int order = 0; order < 2; ++order)
+        for (int j = 0; j < nf; ++j) {
+            const int i = mirror_order(nf, order, j);
+            double *t = tabs.data() + (size_t)order * 3 * nf;
+            t[j] = h->phi[i];
+            t[nf + j] = 1.0 / h->phi[i];
+            t[2 * nf + j] = h->wphi[i] / kRays;
         }
-        MG_CUDA(cudaMemcpy(h->d_phi, a.data(), nf * es, cudaMemcpyHostToDevice));
-        MG_CUDA(cudaMemcpy(h->d_wphi, b.data(), nf * es, cudaMemcpyHostToDevice));
-        MG_CUDA(cudaMemcpy(h->d_inv_phi, c.data(), nf * es, cudaMemcpyHostToDevice));
+    if (h->prec == MG3D_PREC_F64) {
+        MG_CUDA(cudaMemcpy(h->d_ftab, tabs.data(), tabs.size() * es, cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> t32(tabs.begin(), tabs.end());
+        MG_CUDA(cudaMemcpy(h->d_ftab, t32.data(), t32.size() * es, cudaMemcpyHostToDevice));
     }
     {
         double tab[kExpTab];
@@ -1473,20 +1497,10 @@ int batch_build_level(mg3d_batch *b, int k) {
             args.resize(args.size() + asz);
             unsigned char *dst = args.data() + args.size() - asz;
             if (b->prec == MG3D_PREC_F64) {
-                SweepArgs<double> a{L.nx, L.ny, L.nz, nf, s.ng, s.ngroups, s.rows, h->up_mask,
-                                    (const double *)L.chi0, (const double *)L.S,
-                                    (const double *)L.bbot, L.geom, (const double *)h->d_phi,
-                                    (const double *)h->d_inv_phi, (const double *)h->d_wphi,
-                                    (double *)h->pj, (double *)h->pu, h->d_exp_tab, h->exp_l1,
-                                    h->exp_l2};
+                const SweepArgs<double> a = sweep_args<double>(h, L, s);
                 std::memcpy(dst, &a, asz);
             } else {
-                SweepArgs<float> a{L.nx, L.ny, L.nz, nf, s.ng, s.ngroups, s.rows, h->up_mask,
-                                   (const float *)L.chi0, (const float *)L.S,
-                                   (const float *)L.bbot, L.geom, (const float *)h->d_phi,
-                                   (const float *)h->d_inv_phi, (const float *)h->d_wphi,
-                                   (float *)h->pj, (float *)h->pu, h->d_exp_tab, h->exp_l1,
-                                   h->exp_l2};
+                const SweepArgs<float> a = sweep_args<float>(h, L, s);
                 std::memcpy(dst, &a, asz);
             }
         }
@@ -1894,7 +1908,7 @@ int mg3d_destroy(mg3d_handle *h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     drop_graphs(h);
     for (int k = 0; k <= MG3D_MAX_GRIDS; ++k) free_level(h->lev[k]);
-    void *ptrs[] = {h->d_phi, h->d_wphi, h->d_inv_phi, h->d_exp_tab, h->pj, h->pu, h->scal,
+    void *ptrs[] = {h->d_ftab, h->d_exp_tab, h->pj, h->pu, h->scal,
                     h->scratch, h->d_fi, h->d_ti, h->ml_jx, h->ml_ux};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -2116,19 +2130,30 @@ int mg3d_prolong(mg3d_handle *h, int level_fine, int ncomp, const double *coarse
 }
 
 int mg3d_set_fs_config(mg3d_handle *h, int level, int freq_per_block, int bands, int threads,
-                       int lean) {
-    MG_TRY(check_level(h, level));
-    if (h->kind != 0) return fail(MG3D_E_STATE, "sweep shapes apply to two-level handles");
+                       int lean, int stage) {
     SweepShape s;
-    MG_TRY(make_shape(h, level, freq_per_block, bands, threads, &s));
-    if (lean < 0 || lean > 2 || (lean == 2 && threads > 256))
-        return fail(MG3D_E_ARG, "lean must be 0, 1 or (up to 256 threads) 2");
-    s.lean = lean;
+    MG_TRY(shape_from_args(h, level, freq_per_block, bands, threads, lean, stage, &s));
     MG_TRY(check_schedulable(h, level, s));
     MG_CUDA(cudaStreamSynchronize(h->stream));
     MG_TRY(ensure_partials(h, (size_t)kRays * s.ngroups * (size_t)h->lev[level].nvox));
     h->lev[level].shape = s;
     drop_graphs(h);
+    return MG3D_OK;
+}
+
+int mg3d_get_fs_occupancy(mg3d_handle *h, int level, int freq_per_block, int bands,
+                          int threads, int lean, int stage, int *max_clusters,
+                          long long *smem_bytes) {
+    SweepShape s;
+    MG_TRY(shape_from_args(h, level, freq_per_block, bands, threads, lean, stage, &s));
+    int n = 0;
+    const cudaError_t e = sweep_active_clusters(h->prec, s, h->lev[level].nx, &n);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MG3D_E_CUDA, std::string("occupancy query: ") + cudaGetErrorString(e));
+    }
+    if (max_clusters) *max_clusters = n;
+    if (smem_bytes) *smem_bytes = (long long)sweep_smem_bytes(h->prec, s, h->lev[level].nx);
     return MG3D_OK;
 }
 
@@ -2152,13 +2177,14 @@ int mg3d_autotune(mg3d_handle *h, int level, int *evaluated, double *seconds) {
 }
 
 int mg3d_get_fs_config(const mg3d_handle *h, int level, int *freq_per_block, int *bands,
-                       int *threads, int *lean) {
+                       int *threads, int *lean, int *stage) {
     MG_TRY(check_level(h, level));
     const Level &L = h->lev[level];
     if (freq_per_block) *freq_per_block = L.shape.ng;
     if (bands) *bands = L.shape.bands;
     if (threads) *threads = L.shape.threads;
     if (lean) *lean = L.shape.lean;
+    if (stage) *stage = L.shape.stage;
     return MG3D_OK;
 }
 

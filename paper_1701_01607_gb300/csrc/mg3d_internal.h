@@ -34,6 +34,7 @@ struct SweepShape {
     int threads;  // threads per block
     int lean = 0; // register budget: 0 full, 1: 1024 resident threads per SM (64
                   // registers), 2: three 256-thread blocks per SM (85 registers)
+    int stage = 1; // 1: chi0/S rows staged in shared memory one step ahead
 };
 
 // Arguments of the sweep kernel.  T is the formal-solution precision.

@@ -29,7 +29,8 @@ struct ExpNegTable {
 };
 
 __device__ __forceinline__ double exp_neg(double x, const ExpNegTable e) {
-    if (x > 708.0) return 0.0;
+    const bool flush = x > 708.0;
+    x = flush ? 0.0 : x;
     const double magic = 6755399441055744.0;  // 1.5 * 2^52
     const double t = fma(x, -369.3299304675746, magic);  // -x * 256/ln2, rounded to an integer
     const int n = __double2loint(t);
@@ -43,22 +44,39 @@ __device__ __forceinline__ double exp_neg(double x, const ExpNegTable e) {
     const double tj = e.tab[n & (kExpTab - 1)];
     const double v = fma(tj, q, tj);             // 2^{j/256} e^r, in [0.99, 2.01)
     const long long bits = __double_as_longlong(v) + ((long long)(n >> 8) << 52);
-    return __longlong_as_double(bits);
+    return flush ? 0.0 : __longlong_as_double(bits);
 }
 
+// closed() has no branch, so a caller can evaluate several independent steps
+// back to back and patch the small-x ones with series() afterwards; eval()
+// takes one form or the other per lane.
 template <>
 struct ScWeights<double> {
     // inv_x = 1/x, formed by the caller as (1/dtau0)(1/phi): one division per
     // node and ray instead of one per frequency.
+    static __device__ __forceinline__ void closed(double x, double inv_x, const ExpNegTable et,
+                                                  double &ex, double &w0, double &wup,
+                                                  double &u) {
+        ex = exp_neg(x, et);
+        u = fma(-ex, inv_x, inv_x);   // (1 - e^-x)/x
+        w0 = 1.0 - u;
+        wup = u - ex;
+    }
+    static __device__ __forceinline__ bool small(double x) { return x < 1e-3; }
+    static __device__ __forceinline__ void series(double x, double &w0, double &wup, double &u) {
+        w0 = x * (0.5 - x * (1.0 / 6.0 - x * (1.0 / 24.0 - x * (1.0 / 120.0 - x / 720.0))));
+        wup = x * (0.5 - x * (1.0 / 3.0 - x * (1.0 / 8.0 - x * (1.0 / 30.0 - x / 144.0))));
+        u = 1.0 - w0;
+    }
+    // one of the two forms per lane (the closed form's three operations are
+    // skipped where the series applies)
     static __device__ __forceinline__ void eval(double x, double inv_x, const ExpNegTable et,
                                                 double &ex, double &w0, double &wup, double &u) {
         ex = exp_neg(x, et);
-        if (x < 1e-3) {
-            w0 = x * (0.5 - x * (1.0 / 6.0 - x * (1.0 / 24.0 - x * (1.0 / 120.0 - x / 720.0))));
-            wup = x * (0.5 - x * (1.0 / 3.0 - x * (1.0 / 8.0 - x * (1.0 / 30.0 - x / 144.0))));
-            u = 1.0 - w0;
+        if (small(x)) {
+            series(x, w0, wup, u);
         } else {
-            u = fma(-ex, inv_x, inv_x);   // (1 - e^-x)/x
+            u = fma(-ex, inv_x, inv_x);
             w0 = 1.0 - u;
             wup = u - ex;
         }
@@ -67,18 +85,23 @@ struct ScWeights<double> {
 
 template <>
 struct ScWeights<float> {
-    static __device__ __forceinline__ void eval(float x, float inv_x, const ExpNegTable,
-                                                float &ex, float &w0, float &wup, float &u) {
+    static __device__ __forceinline__ void closed(float x, float inv_x, const ExpNegTable,
+                                                  float &ex, float &w0, float &wup, float &u) {
         ex = __expf(-x);
-        if (x < 0.1f) {
-            w0 = x * (0.5f - x * (1.0f / 6.0f - x * (1.0f / 24.0f - x * (1.0f / 120.0f - x / 720.0f))));
-            wup = x * (0.5f - x * (1.0f / 3.0f - x * (1.0f / 8.0f - x * (1.0f / 30.0f - x / 144.0f))));
-            u = 1.0f - w0;
-        } else {
-            u = fmaf(-ex, inv_x, inv_x);   // (1 - e^-x)/x
-            w0 = 1.0f - u;
-            wup = u - ex;
-        }
+        u = fmaf(-ex, inv_x, inv_x);   // (1 - e^-x)/x
+        w0 = 1.0f - u;
+        wup = u - ex;
+    }
+    static __device__ __forceinline__ bool small(float x) { return x < 0.1f; }
+    static __device__ __forceinline__ void series(float x, float &w0, float &wup, float &u) {
+        w0 = x * (0.5f - x * (1.0f / 6.0f - x * (1.0f / 24.0f - x * (1.0f / 120.0f - x / 720.0f))));
+        wup = x * (0.5f - x * (1.0f / 3.0f - x * (1.0f / 8.0f - x * (1.0f / 30.0f - x / 144.0f))));
+        u = 1.0f - w0;
+    }
+    static __device__ __forceinline__ void eval(float x, float inv_x, const ExpNegTable et,
+                                                float &ex, float &w0, float &wup, float &u) {
+        closed(x, inv_x, et, ex, w0, wup, u);
+        if (small(x)) series(x, w0, wup, u);
     }
 };
 

@@ -134,9 +134,11 @@ _SIGNATURES = {
     "mg3d_fmg_solve": (_I, [_H, ctypes.c_double, _I, ctypes.POINTER(mg3d_stats)]),
     "mg3d_restrict": (_I, [_H, _I, _I, _D, _D]),
     "mg3d_prolong": (_I, [_H, _I, _I, _D, _D]),
-    "mg3d_set_fs_config": (_I, [_H, _I, _I, _I, _I, _I]),
+    "mg3d_set_fs_config": (_I, [_H, _I, _I, _I, _I, _I, _I]),
     "mg3d_get_fs_config": (_I, [_H, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
-                                ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+                                ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "mg3d_get_fs_occupancy": (_I, [_H, _I, _I, _I, _I, _I, _I, ctypes.POINTER(_I),
+                                   ctypes.POINTER(ctypes.c_longlong)]),
     "mg3d_autotune": (_I, [_H, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),
     "mg3d_check_exp": (_I, [_I, _D, _D]),
     "mg3d_set_graphs": (_I, [_H, _I]),
@@ -371,15 +373,25 @@ def mg3d_prolong(h, level_fine: int, coarse):
 
 
 def mg3d_set_fs_config(h, level: int, freq_per_block: int, bands: int, threads: int = 256,
-                       lean: int = 0):
-    return _check(load().mg3d_set_fs_config(h, level, freq_per_block, bands, threads, lean))
+                       lean: int = 0, stage: int = 1):
+    return _check(load().mg3d_set_fs_config(h, level, freq_per_block, bands, threads, lean,
+                                            stage))
 
 
 def mg3d_get_fs_config(h, level: int):
-    a, b, c, d = _I(), _I(), _I(), _I()
-    _check(load().mg3d_get_fs_config(h, level, ctypes.byref(a), ctypes.byref(b),
-                                     ctypes.byref(c), ctypes.byref(d)))
-    return a.value, b.value, c.value, d.value
+    """(freq_per_block, bands, threads, lean, stage) of a level's sweep."""
+    v = [_I() for _ in range(5)]
+    _check(load().mg3d_get_fs_config(h, level, *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+def mg3d_get_fs_occupancy(h, level: int, freq_per_block: int, bands: int, threads: int = 256,
+                          lean: int = 0, stage: int = 1):
+    """(clusters the GPU holds at once, dynamic shared memory bytes per block)."""
+    n, smem = _I(), ctypes.c_longlong()
+    _check(load().mg3d_get_fs_occupancy(h, level, freq_per_block, bands, threads, lean, stage,
+                                        ctypes.byref(n), ctypes.byref(smem)))
+    return n.value, smem.value
 
 
 def mg3d_autotune(h, level: int = 0):

@@ -63,7 +63,7 @@ def test_formal_solution_every_launch_shape(ng, bands, lean):
     h = make(atm, atom)
     try:
         m.mg3d_set_fs_config(h, 1, ng, bands, 128, lean)
-        assert m.mg3d_get_fs_config(h, 1) == (ng, bands, 128, lean)
+        assert m.mg3d_get_fs_config(h, 1) == (ng, bands, 128, lean, 1)
         jeff, u = m.mg3d_formal_solve(h, 1)
     finally:
         m.mg3d_destroy(h)
@@ -81,7 +81,7 @@ def test_formal_solution_sixteen_block_cluster(ng, lean):
     h = make(atm, atom)
     try:
         m.mg3d_set_fs_config(h, 1, ng, 16, 32, lean)
-        assert m.mg3d_get_fs_config(h, 1) == (ng, 16, 32, lean)
+        assert m.mg3d_get_fs_config(h, 1) == (ng, 16, 32, lean, 1)
         jeff, u = m.mg3d_formal_solve(h, 1)
     finally:
         m.mg3d_destroy(h)
