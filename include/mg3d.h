@@ -286,6 +286,29 @@ int mg3d_n_levels(const mg3d_handle *h, int *n_levels, int *n_freq);
  * [n_freq][nz][ny][nx] (nullable).  MG3D_E_STATE on a two-level handle. */
 int mg3d_formal_solve_ml(mg3d_handle *h, int level, double *jx_host, double *ux_host);
 
+/* Frequencies per chunk of the multi-level formal solution.  The opacity,
+ * the sweep and the reduction of the angle sums to the per-transition sums
+ * the rate equations use run chunk by chunk, so device memory for the
+ * per-frequency arrays scales with the chunk, not with n_freq (the rates and
+ * the populations are the same for every chunk size, up to rounding).  At
+ * creation the library takes all frequencies when their arrays fit in 60 % of
+ * the free device memory, else the largest chunk that does.  freq_per_chunk =
+ * 0 means all frequencies.  Reallocates the chunk buffers (MG3D_E_OOM if they
+ * do not fit); MG3D_E_STATE on a two-level handle.  Batch members need all
+ * frequencies in one chunk. */
+int mg3d_set_ml_chunk(mg3d_handle *h, int freq_per_chunk);
+int mg3d_get_ml_chunk(const mg3d_handle *h, int *freq_per_chunk);
+
+/* Launch shape of a level's multi-level sweep: bands = thread blocks (one
+ * cluster, 1..8) sharing each plane, rays_per_block = rays of a hemisphere
+ * each block carries (a divisor of 12; fewer rays need less shared memory,
+ * 2 x rays x rows x nx values, and give more blocks), threads per block (a
+ * multiple of 32 up to 512).  The library picks one at creation (all 12 rays
+ * where some band count fits); MG3D_E_ARG for shapes that do not fit. */
+int mg3d_set_ml_shape(mg3d_handle *h, int level, int bands, int rays_per_block, int threads);
+int mg3d_get_ml_shape(const mg3d_handle *h, int level, int *bands, int *rays_per_block,
+                      int *threads);
+
 /* ------------------------------------------------------------------------
  * Batches: many independent atmospheres of uneven size (two-level and
  * multi-level atoms mixed) iterated in lockstep.  Every formal solution of

@@ -78,6 +78,7 @@ struct Level {
     void *mchi = nullptr, *mS = nullptr, *msl = nullptr, *mfl = nullptr;  // [nf][nvox]
     void *mib = nullptr;         // [nf][nplane] bottom intensity
     int ml_bands = 0, ml_rows = 0, ml_threads = 0;
+    int ml_rpb = 12;             // rays of a hemisphere per block of the multi-level sweep
 };
 
 struct TimedLaunch {
@@ -99,7 +100,13 @@ struct mg3d_handle {
     std::vector<TransInfo> ti;
     FreqInfo *d_fi = nullptr;
     TransInfo *d_ti = nullptr;
-    void *ml_jx = nullptr, *ml_ux = nullptr;  // [2][nf][finest nvox]
+    // multi-level formal solution, in chunks of ml_chunk frequencies:
+    // angle sums of the chunk [2 hemispheres][ml_chunk][nvox] and the
+    // radiative sums per transition [ntrans][kAccTerms][finest nvox] (FP64)
+    int ml_chunk = 0;
+    int ml_slots = 2;            // most ray-group slots of any level (2 x 12 / ml_rpb)
+    void *ml_jx = nullptr, *ml_ux = nullptr;
+    double *ml_acc = nullptr;
     mg3d_atom atom{};
     mg3d_params params{};
     double mu[kRays][3];
@@ -367,10 +374,12 @@ cudaEvent_t pool_event(mg3d_handle *h) {
 
 // Multi-level formal solution on level k: per-frequency angle sums per
 // hemisphere into ml_jx/ml_ux.
-int ml_formal_solution(mg3d_handle *h, int k) {
+// Opacity and sweep of the chunk of frequencies f0 .. f0+nc-1 on level k:
+// per-frequency angle sums of both hemispheres into ml_jx/ml_ux.
+int ml_chunk_fs(mg3d_handle *h, int k, int f0, int nc) {
     Level &L = h->lev[k];
-    MlOpacityArgs oa{L.nvox, h->nfreq_ml, h->N, h->prec, h->d_fi, h->theta_ref, h->t_ref,
-                     L.n, L.T, L.chi_c, L.saha, L.mchi, L.mS, L.msl, L.mfl};
+    MlOpacityArgs oa{L.nvox, nc, h->N, h->prec, h->d_fi, h->theta_ref, h->t_ref,
+                     L.n, L.T, L.chi_c, L.saha, L.mchi, L.mS, L.msl, L.mfl, f0};
     MG_TRY(launched(h, launch_ml_opacity(oa, h->stream), "multi-level opacity"));
     TimedLaunch tl{nullptr, nullptr, k};
     if (h->timing) {
@@ -378,26 +387,58 @@ int ml_formal_solution(mg3d_handle *h, int k) {
         tl.b = pool_event(h);
         MG_CUDA(record_event(tl.a, h->stream));
     }
+    const size_t es = elem_size(h->prec);
+    const void *ib = static_cast<const unsigned char *>(L.mib) + (size_t)f0 * L.nplane * es;
     cudaError_t e;
     if (h->prec == MG3D_PREC_F64) {
-        MlSweepArgs<double> a{L.nx, L.ny, L.nz, h->nfreq_ml, L.ml_rows,
+        MlSweepArgs<double> a{L.nx, L.ny, L.nz, nc, L.ml_rows,
                               (const double *)L.mchi, (const double *)L.mS,
                               (const double *)L.msl, (const double *)L.mfl,
-                              (const double *)L.mib, L.geom, h->d_exp_tab, h->exp_l1, h->exp_l2,
-                              (double *)h->ml_jx, (double *)h->ml_ux};
+                              (const double *)ib, L.geom, h->d_exp_tab, h->exp_l1, h->exp_l2,
+                              (double *)h->ml_jx, (double *)h->ml_ux, L.ml_rpb};
         e = launch_ml_sweep_f64(a, L.ml_bands, L.ml_threads, h->stream);
     } else {
-        MlSweepArgs<float> a{L.nx, L.ny, L.nz, h->nfreq_ml, L.ml_rows,
+        MlSweepArgs<float> a{L.nx, L.ny, L.nz, nc, L.ml_rows,
                              (const float *)L.mchi, (const float *)L.mS,
                              (const float *)L.msl, (const float *)L.mfl,
-                             (const float *)L.mib, L.geom, h->d_exp_tab, h->exp_l1, h->exp_l2,
-                             (float *)h->ml_jx, (float *)h->ml_ux};
+                             (const float *)ib, L.geom, h->d_exp_tab, h->exp_l1, h->exp_l2,
+                             (float *)h->ml_jx, (float *)h->ml_ux, L.ml_rpb};
         e = launch_ml_sweep_f32(a, L.ml_bands, L.ml_threads, h->stream);
     }
     MG_TRY(launched(h, e, "multi-level sweep"));
     if (h->timing) {
         MG_CUDA(record_event(tl.b, h->stream));
         h->timed.push_back(tl);
+    }
+    return MG3D_OK;
+}
+
+// Radiative sums of level k from the chunk's angle sums (zero_rad: J = 0,
+// U = 1 for all frequencies, no formal solution).
+int ml_accumulate(mg3d_handle *h, int k, int f0, int nc, bool zero_rad) {
+    Level &L = h->lev[k];
+    MlAccumArgs a{L.nvox, f0, nc, h->ntrans, h->prec, h->d_fi, h->d_ti, h->theta_ref,
+                  h->t_ref, L.T, h->ml_jx, h->ml_ux, 2 * (12 / L.ml_rpb), zero_rad ? 1 : 0,
+                  h->ml_acc};
+    return launched(h, launch_ml_accum(a, h->stream), "radiative sums");
+}
+
+int ml_clear_acc(mg3d_handle *h, int k) {
+    MG_CUDA(cudaMemsetAsync(h->ml_acc, 0,
+                            (size_t)h->ntrans * kAccTerms * h->lev[k].nvox * sizeof(double),
+                            h->stream));
+    return MG3D_OK;
+}
+
+// Formal solution of level k, chunk by chunk, reduced to the radiative sums
+// the rate equations use.
+int ml_formal_solution(mg3d_handle *h, int k) {
+    Level &L = h->lev[k];
+    MG_TRY(ml_clear_acc(h, k));
+    for (int f0 = 0; f0 < h->nfreq_ml; f0 += h->ml_chunk) {
+        const int nc = std::min(h->ml_chunk, h->nfreq_ml - f0);
+        MG_TRY(ml_chunk_fs(h, k, f0, nc));
+        MG_TRY(ml_accumulate(h, k, f0, nc, false));
     }
     const double units = (double)L.nvox * kRays * h->nfreq_ml;
     ++h->fs_launches;
@@ -412,17 +453,10 @@ MlRateArgs ml_rate_args(mg3d_handle *h, int k, int mode) {
     Level &L = h->lev[k];
     MlRateArgs a{};
     a.nvox = L.nvox;
-    a.nfreq = h->nfreq_ml;
     a.n_levels = h->N;
     a.n_trans = h->ntrans;
-    a.prec = h->prec;
-    a.fi = h->d_fi;
     a.ti = h->d_ti;
-    a.jx = h->ml_jx;
-    a.ux = h->ml_ux;
-    a.zero_radiation = 0;
-    a.theta_ref = h->theta_ref;
-    a.t_ref = h->t_ref;
+    a.acc = h->ml_acc;
     a.T = L.T;
     a.c = L.cmat;
     a.saha = L.saha;
@@ -523,8 +557,9 @@ int zero_radiation(mg3d_handle *h, int k) {
     Level &L = h->lev[k];
     L.f_default = true;
     if (h->kind == 1) {
+        MG_TRY(ml_clear_acc(h, k));
+        MG_TRY(ml_accumulate(h, k, 0, h->nfreq_ml, true));
         MlRateArgs a = ml_rate_args(h, k, kRateSolve);
-        a.zero_radiation = 1;
         a.scal = nullptr;
         MG_TRY(launched(h, launch_ml_rates(a, h->stream), "zero radiation"));
         return MG3D_OK;
@@ -1056,6 +1091,56 @@ void trapezoid_grid(double a, double b, int n, std::vector<double> &x, std::vect
     }
 }
 
+// Bytes the multi-level formal solution needs per frequency of a chunk:
+// opacity, source function and their two transition shares on every level,
+// and the angle sums of every ray-group slot on the finest.
+size_t ml_bytes_per_freq(const mg3d_handle *h) {
+    const size_t es = elem_size(h->prec);
+    size_t b = 2 * (size_t)h->ml_slots * h->lev[h->L].nvox * es;
+    for (int k = 1; k <= h->L; ++k) b += 4 * (size_t)h->lev[k].nvox * es;
+    return b;
+}
+
+// All frequencies in one chunk when their buffers take at most 60 % of the
+// free device memory, else the largest chunk that does.
+int default_ml_chunk(const mg3d_handle *h) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return h->nfreq_ml;
+    }
+    const size_t fit = (size_t)(0.6 * (double)free_b) / ml_bytes_per_freq(h);
+    return (int)std::max<size_t>(1, std::min<size_t>(fit, (size_t)h->nfreq_ml));
+}
+
+// (Re)allocates the per-chunk buffers of a multi-level handle for `chunk`
+// frequencies per chunk.
+int alloc_ml_chunks(mg3d_handle *h, int chunk) {
+    const size_t es = elem_size(h->prec);
+    for (int k = 1; k <= h->L; ++k) {
+        Level &L = h->lev[k];
+        void **bufs[4] = {&L.mchi, &L.mS, &L.msl, &L.mfl};
+        for (void **p : bufs) {
+            if (*p) cudaFree(*p);
+            *p = nullptr;
+        }
+    }
+    if (h->ml_jx) cudaFree(h->ml_jx);
+    if (h->ml_ux) cudaFree(h->ml_ux);
+    h->ml_jx = h->ml_ux = nullptr;
+    h->ml_chunk = 0;
+    for (int k = 1; k <= h->L; ++k) {
+        Level &L = h->lev[k];
+        void **bufs[4] = {&L.mchi, &L.mS, &L.msl, &L.mfl};
+        for (void **p : bufs) MG_TRY(dev_alloc(p, (size_t)chunk * L.nvox * es));
+    }
+    const size_t nv = h->lev[h->L].nvox;
+    MG_TRY(dev_alloc(&h->ml_jx, (size_t)h->ml_slots * chunk * nv * es));
+    MG_TRY(dev_alloc(&h->ml_ux, (size_t)h->ml_slots * chunk * nv * es));
+    h->ml_chunk = chunk;
+    return MG3D_OK;
+}
+
 int create_ml_impl(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
                    const mg3d_quadrature *quad, const mg3d_params *params, mg3d_handle *h) {
     h->kind = 1;
@@ -1128,10 +1213,6 @@ int create_ml_impl(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
         MG_TRY(dalloc(&L.f, (size_t)N * L.nvox));
         MG_TRY(dalloc(&L.n_before, (size_t)N * L.nvox));
         MG_TRY(dalloc(&L.r, (size_t)N * L.nvox));
-        MG_TRY(dev_alloc(&L.mchi, (size_t)nf * L.nvox * es));
-        MG_TRY(dev_alloc(&L.mS, (size_t)nf * L.nvox * es));
-        MG_TRY(dev_alloc(&L.msl, (size_t)nf * L.nvox * es));
-        MG_TRY(dev_alloc(&L.mfl, (size_t)nf * L.nvox * es));
         MG_TRY(dev_alloc(&L.mib, (size_t)nf * L.nplane * es));
         MG_TRY(dalloc(&L.geom, (size_t)kRays * L.nz));
         std::vector<double> tz(L.nz, 0.0);
@@ -1140,15 +1221,23 @@ int create_ml_impl(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
         std::vector<StepGeom> g;
         build_geometry(h, L, g);
         MG_CUDA(cudaMemcpy(L.geom, g.data(), g.size() * sizeof(StepGeom), cudaMemcpyHostToDevice));
-        // bands: the fewest that fit in shared memory and give >= 300 blocks,
-        // else the most that fit
+        // rays per block: all 12 of a hemisphere if some band count fits in
+        // shared memory, else the largest divisor of 12 that does; bands: the
+        // fewest that fit and give >= 300 blocks, else the most that fit
         int pick = 0;
-        for (int b = 1; b <= kPortableBands && b <= L.ny; ++b) {
-            const int rows = (L.ny + b - 1) / b;
-            if ((long)(b - 1) * rows >= L.ny) continue;
-            if (ml_sweep_smem_bytes(h->prec, rows, L.nx) > kMaxSweepSmem) continue;
-            pick = b;
-            if (2L * nf * b >= 300) break;
+        for (int rpb : {12, 6, 4, 3, 2, 1}) {
+            for (int b = 1; b <= kPortableBands && b <= L.ny; ++b) {
+                const int rows = (L.ny + b - 1) / b;
+                if ((long)(b - 1) * rows >= L.ny) continue;
+                if (ml_sweep_smem_bytes(h->prec, rows, L.nx, rpb) > kMaxSweepSmem) continue;
+                pick = b;
+                if (2L * (12 / rpb) * nf * b >= 300) break;
+            }
+            if (pick) {
+                L.ml_rpb = rpb;
+                h->ml_slots = std::max(h->ml_slots, 2 * (12 / rpb));
+                break;
+            }
         }
         if (pick == 0) return fail(MG3D_E_ARG, "plane too large for the multi-level sweep");
         L.ml_bands = pick;
@@ -1226,8 +1315,8 @@ int create_ml_impl(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
         MG_TRY(dalloc(&h->d_exp_tab, kExpTab));
         MG_CUDA(cudaMemcpy(h->d_exp_tab, tab, sizeof(tab), cudaMemcpyHostToDevice));
     }
-    MG_TRY(dev_alloc(&h->ml_jx, 2 * (size_t)nf * F.nvox * es));
-    MG_TRY(dev_alloc(&h->ml_ux, 2 * (size_t)nf * F.nvox * es));
+    MG_TRY(dalloc(&h->ml_acc, (size_t)h->ntrans * kAccTerms * F.nvox));
+    MG_TRY(alloc_ml_chunks(h, default_ml_chunk(h)));
     MG_TRY(dalloc(&h->scal, 8));
     for (int k = 1; k <= h->L; ++k) MG_TRY(zero_radiation(h, k));
     MG_CUDA(cudaStreamSynchronize(h->stream));
@@ -1268,6 +1357,18 @@ int batch_launched(mg3d_batch *b, cudaError_t e, const char *what) {
     return MG3D_OK;
 }
 
+// Radiative sums of a multi-level member on level k from its angle sums (all
+// frequencies in one chunk), or for zero radiation.
+int batch_ml_sums(mg3d_batch *b, mg3d_handle *h, int k, bool zero_rad) {
+    const Level &L = h->lev[k];
+    MG_CUDA(cudaMemsetAsync(h->ml_acc, 0, (size_t)h->ntrans * kAccTerms * L.nvox * sizeof(double),
+                            b->stream));
+    MlAccumArgs a{L.nvox, 0, h->nfreq_ml, h->ntrans, h->prec, h->d_fi, h->d_ti, h->theta_ref,
+                  h->t_ref, L.T, h->ml_jx, h->ml_ux, 2 * (12 / L.ml_rpb), zero_rad ? 1 : 0,
+                  h->ml_acc};
+    return batch_launched(b, launch_ml_accum(a, b->stream), "batch radiative sums");
+}
+
 // Formal solution of level k for every member: per-member opacity, then one
 // batched sweep launch per atom kind.
 int batch_fs(mg3d_batch *b, int k) {
@@ -1292,19 +1393,22 @@ int batch_fs(mg3d_batch *b, int k) {
                                                     t.bands, t.threads, t.smem, b->stream),
                               "batched sweep"));
     mg3d_batch::KindLevel &q = b->ml[k];
-    if (q.n_items)
+    if (q.n_items) {
         MG_TRY(batch_launched(b, launch_ml_sweep_batch(b->prec, q.d_args, q.d_items, q.n_items,
                                                        q.bands, q.threads, q.smem, b->stream),
                               "batched multi-level sweep"));
+        for (mg3d_handle *h : b->m)
+            if (h->kind == 1) MG_TRY(batch_ml_sums(b, h, k, false));
+    }
     return MG3D_OK;
 }
 
 int member_rates(mg3d_batch *b, mg3d_handle *h, int k, int mode, double *out, bool zero_rad,
                  unsigned long long *scal) {
     if (h->kind == 1) {
+        if (zero_rad) MG_TRY(batch_ml_sums(b, h, k, true));
         MlRateArgs a = ml_rate_args(h, k, mode);
         a.out = out;
-        a.zero_radiation = zero_rad;
         a.scal = scal;
         return batch_launched(b, launch_ml_rates(a, b->stream), "batch rates");
     }
@@ -1527,7 +1631,7 @@ int batch_build_level(mg3d_batch *b, int k) {
                 const Level &L = b->m[i]->lev[k];
                 const int rows = (L.ny + bb - 1) / bb;
                 if (bb > L.ny || (long)(bb - 1) * rows >= L.ny ||
-                    ml_sweep_smem_bytes(b->prec, rows, L.nx) > kMaxSweepSmem)
+                    ml_sweep_smem_bytes(b->prec, rows, L.nx, L.ml_rpb) > kMaxSweepSmem)
                     ok = false;
             }
             if (ok) bands = bb;
@@ -1548,10 +1652,10 @@ int batch_build_level(mg3d_batch *b, int k) {
             L.ml_rows = rows;
             L.ml_threads = std::min(256, threads_for_band(rows * L.nx));
             threads = std::max(threads, L.ml_threads);
-            smem = std::max(smem, ml_sweep_smem_bytes(h->prec, rows, L.nx));
+            smem = std::max(smem, ml_sweep_smem_bytes(h->prec, rows, L.nx, L.ml_rpb));
             drop_graphs(h);
-            for (int hemi = 0; hemi < 2; ++hemi)
-                for (int f = 0; f < h->nfreq_ml; ++f) items.push_back(BatchItem{(int)j, hemi, f});
+            for (int slot = 0; slot < 2 * (12 / L.ml_rpb); ++slot)
+                for (int f = 0; f < h->nfreq_ml; ++f) items.push_back(BatchItem{(int)j, slot, f});
             args.resize(args.size() + asz);
             unsigned char *dst = args.data() + args.size() - asz;
             if (b->prec == MG3D_PREC_F64) {
@@ -1559,14 +1663,16 @@ int batch_build_level(mg3d_batch *b, int k) {
                                       (const double *)L.mchi, (const double *)L.mS,
                                       (const double *)L.msl, (const double *)L.mfl,
                                       (const double *)L.mib, L.geom, h->d_exp_tab, h->exp_l1,
-                                      h->exp_l2, (double *)h->ml_jx, (double *)h->ml_ux};
+                                      h->exp_l2, (double *)h->ml_jx, (double *)h->ml_ux,
+                                      L.ml_rpb};
                 std::memcpy(dst, &a, asz);
             } else {
                 MlSweepArgs<float> a{L.nx, L.ny, L.nz, h->nfreq_ml, rows,
                                      (const float *)L.mchi, (const float *)L.mS,
                                      (const float *)L.msl, (const float *)L.mfl,
                                      (const float *)L.mib, L.geom, h->d_exp_tab, h->exp_l1,
-                                     h->exp_l2, (float *)h->ml_jx, (float *)h->ml_ux};
+                                     h->exp_l2, (float *)h->ml_jx, (float *)h->ml_ux,
+                                     L.ml_rpb};
                 std::memcpy(dst, &a, asz);
             }
         }
@@ -1714,27 +1820,97 @@ int mg3d_formal_solve_ml(mg3d_handle *h, int level, double *jx_host, double *ux_
     MG_TRY(check_level(h, level));
     if (h->kind != 1) return fail(MG3D_E_STATE, "not a multi-level handle");
     Level &L = h->lev[level];
-    MG_TRY(formal_solution(h, level));
-    MG_CUDA(cudaStreamSynchronize(h->stream));
-    const size_t cnt = (size_t)h->nfreq_ml * L.nvox;
     const size_t es = elem_size(h->prec);
-    // both hemispheres of the per-frequency sums, added on the host
-    std::vector<unsigned char> hj(2 * cnt * es), hu(2 * cnt * es);
-    MG_CUDA(cudaMemcpy(hj.data(), h->ml_jx, 2 * cnt * es, cudaMemcpyDeviceToHost));
-    MG_CUDA(cudaMemcpy(hu.data(), h->ml_ux, 2 * cnt * es, cudaMemcpyDeviceToHost));
-    const size_t hs = (size_t)h->nfreq_ml * L.nvox;   // hemisphere stride of this level
-    for (size_t i = 0; i < cnt; ++i) {
-        double j0, j1, u0, u1;
-        if (h->prec == MG3D_PREC_F64) {
-            const double *J = (const double *)hj.data(), *U = (const double *)hu.data();
-            j0 = J[i]; j1 = J[hs + i]; u0 = U[i]; u1 = U[hs + i];
-        } else {
-            const float *J = (const float *)hj.data(), *U = (const float *)hu.data();
-            j0 = J[i]; j1 = J[hs + i]; u0 = U[i]; u1 = U[hs + i];
+    const size_t nv = (size_t)L.nvox;
+    std::vector<unsigned char> hj, hu;
+    for (int f0 = 0; f0 < h->nfreq_ml; f0 += h->ml_chunk) {
+        const int nc = std::min(h->ml_chunk, h->nfreq_ml - f0);
+        MG_TRY(ml_chunk_fs(h, level, f0, nc));
+        MG_CUDA(cudaStreamSynchronize(h->stream));
+        // the chunk's per-frequency sums of every ray-group slot, added on the
+        // host in slot order
+        const size_t cnt = (size_t)nc * nv;
+        const int slots = 2 * (12 / L.ml_rpb);
+        hj.resize(slots * cnt * es);
+        hu.resize(slots * cnt * es);
+        MG_CUDA(cudaMemcpy(hj.data(), h->ml_jx, slots * cnt * es, cudaMemcpyDeviceToHost));
+        MG_CUDA(cudaMemcpy(hu.data(), h->ml_ux, slots * cnt * es, cudaMemcpyDeviceToHost));
+        auto at = [&](const std::vector<unsigned char> &v, size_t i) {
+            return h->prec == MG3D_PREC_F64 ? ((const double *)v.data())[i]
+                                            : (double)((const float *)v.data())[i];
+        };
+        for (size_t i = 0; i < cnt; ++i) {
+            double J = at(hj, i), U = at(hu, i);
+            for (int sl = 1; sl < slots; ++sl) {
+                J += at(hj, sl * cnt + i);
+                U += at(hu, sl * cnt + i);
+            }
+            const size_t o = (size_t)f0 * nv + i;
+            if (jx_host) jx_host[o] = J;
+            if (ux_host) ux_host[o] = U;
         }
-        if (jx_host) jx_host[i] = j0 + j1;
-        if (ux_host) ux_host[i] = u0 + u1;
     }
+    const double units = (double)L.nvox * kRays * h->nfreq_ml;
+    ++h->fs_launches;
+    h->fs_units += units;
+    ++h->level_launches[level];
+    h->level_units[level] += units;
+    return MG3D_OK;
+}
+
+int mg3d_set_ml_chunk(mg3d_handle *h, int freq_per_chunk) {
+    if (!h) return fail(MG3D_E_ARG, "null handle");
+    if (h->kind != 1) return fail(MG3D_E_STATE, "not a multi-level handle");
+    if (freq_per_chunk < 0) return fail(MG3D_E_ARG, "negative chunk size");
+    const int c = freq_per_chunk == 0 ? h->nfreq_ml : std::min(freq_per_chunk, h->nfreq_ml);
+    MG_CUDA(cudaStreamSynchronize(h->stream));
+    drop_graphs(h);
+    return alloc_ml_chunks(h, c);
+}
+
+int mg3d_set_ml_shape(mg3d_handle *h, int level, int bands, int rays_per_block, int threads) {
+    MG_TRY(check_level(h, level));
+    if (h->kind != 1) return fail(MG3D_E_STATE, "not a multi-level handle");
+    Level &L = h->lev[level];
+    if (bands < 1 || bands > kPortableBands || bands > L.ny)
+        return fail(MG3D_E_ARG, "bands must be 1..8 and at most ny");
+    const int rows = (L.ny + bands - 1) / bands;
+    if ((long)(bands - 1) * rows >= L.ny) return fail(MG3D_E_ARG, "empty band");
+    if (rays_per_block < 1 || 12 % rays_per_block)
+        return fail(MG3D_E_ARG, "rays_per_block must divide 12");
+    if (threads < 32 || threads > kMaxSweepThreads || threads % 32)
+        return fail(MG3D_E_ARG, "threads must be a multiple of 32 up to 512");
+    if (ml_sweep_smem_bytes(h->prec, rows, L.nx, rays_per_block) > kMaxSweepSmem)
+        return fail(MG3D_E_ARG, "multi-level sweep shape exceeds shared memory");
+    MG_CUDA(cudaStreamSynchronize(h->stream));
+    L.ml_bands = bands;
+    L.ml_rows = rows;
+    L.ml_rpb = rays_per_block;
+    L.ml_threads = threads;
+    drop_graphs(h);
+    const int slots = 2 * (12 / rays_per_block);
+    if (slots > h->ml_slots) {
+        h->ml_slots = slots;
+        MG_TRY(alloc_ml_chunks(h, h->ml_chunk));
+    }
+    return MG3D_OK;
+}
+
+int mg3d_get_ml_shape(const mg3d_handle *h, int level, int *bands, int *rays_per_block,
+                      int *threads) {
+    MG_TRY(check_level(h, level));
+    if (h->kind != 1) return fail(MG3D_E_STATE, "not a multi-level handle");
+    const Level &L = h->lev[level];
+    if (bands) *bands = L.ml_bands;
+    if (rays_per_block) *rays_per_block = L.ml_rpb;
+    if (threads) *threads = L.ml_threads;
+    return MG3D_OK;
+}
+
+int mg3d_get_ml_chunk(const mg3d_handle *h, int *freq_per_chunk) {
+    if (!h || !freq_per_chunk) return fail(MG3D_E_ARG, "null argument");
+    if (h->kind != 1) return fail(MG3D_E_STATE, "not a multi-level handle");
+    *freq_per_chunk = h->ml_chunk;
     return MG3D_OK;
 }
 
@@ -1756,6 +1932,10 @@ int mg3d_batch_create(int n, mg3d_handle *const *members, mg3d_batch **out) {
             p.restriction != q.restriction)
             return fail(MG3D_E_ARG, "batch members need equal n_grids, precision and schedule");
     }
+    for (int i = 0; i < n; ++i)
+        if (members[i]->kind == 1 && members[i]->ml_chunk != members[i]->nfreq_ml)
+            return fail(MG3D_E_ARG,
+                        "multi-level batch members need all frequencies in one chunk");
     mg3d_batch *b = new (std::nothrow) mg3d_batch();
     if (!b) return fail(MG3D_E_OOM, "host allocation failed");
     b->n = n;
@@ -1909,7 +2089,7 @@ int mg3d_destroy(mg3d_handle *h) {
     drop_graphs(h);
     for (int k = 0; k <= MG3D_MAX_GRIDS; ++k) free_level(h->lev[k]);
     void *ptrs[] = {h->d_ftab, h->d_exp_tab, h->pj, h->pu, h->scal,
-                    h->scratch, h->d_fi, h->d_ti, h->ml_jx, h->ml_ux};
+                    h->scratch, h->d_fi, h->d_ti, h->ml_jx, h->ml_ux, h->ml_acc};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &t : h->timed) {

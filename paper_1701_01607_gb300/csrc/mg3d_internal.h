@@ -150,9 +150,12 @@ struct MlSweepArgs {
     const StepGeom *geom;         // [kRays][nz]
     const double *exp_tab;
     double exp_l1, exp_l2;
-    T *jx, *ux;                   // [2 hemispheres][nfreq][nvox]
+    T *jx, *ux;                   // [2 * 12 / rpb slots][nfreq][nvox]
+    int rpb;                      // rays per block: 12, 6, 4, 3, 2 or 1 of a hemisphere
 };
 
+// Opacity of the chunk of frequencies f0 .. f0+nfreq-1, written at the
+// chunk-local index [f - f0][nvox].
 struct MlOpacityArgs {
     long nvox;
     int nfreq, n_levels, prec;
@@ -160,16 +163,33 @@ struct MlOpacityArgs {
     double theta_ref, t_ref;
     const double *n, *T, *chi_c, *saha;
     void *chi, *S, *sl, *fl;
+    int f0;
+};
+
+// Radiative sums per transition and node, [n_trans][3][nvox] in FP64:
+//   line:       sum w phi, sum w phi J, sum w phi U   (phi at the node's T)
+//   continuum:  sum qa J, sum qa E J, sum qa E (rho y)^3 U
+// accumulated chunk by chunk from the per-frequency angle sums Jx, Ux.
+constexpr int kAccTerms = 3;
+
+struct MlAccumArgs {
+    long nvox;
+    int f0, nfreq, n_trans, prec;  // chunk f0 .. f0+nfreq-1
+    const FreqInfo *fi;
+    const TransInfo *ti;
+    double theta_ref, t_ref;
+    const double *T;
+    const void *jx, *ux;           // [nslots][nfreq][nvox] of the chunk
+    int nslots;                    // ray groups of both hemispheres
+    int zero_radiation;            // 1: J = 0, U = 1 (jx, ux unused)
+    double *acc;
 };
 
 struct MlRateArgs {
     long nvox;
-    int nfreq, n_levels, n_trans, prec;
-    const FreqInfo *fi;
+    int n_levels, n_trans;
     const TransInfo *ti;
-    const void *jx, *ux;          // [2][nfreq][nvox]
-    int zero_radiation;
-    double theta_ref, t_ref;
+    const double *acc;            // [n_trans][kAccTerms][nvox]
     const double *T, *c, *saha, *n_tot;   // c [N][N][nvox], saha [N][nvox]
     const double *f;              // [N][nvox] or nullptr for (n_tot, 0, ...)
     double *n, *out;              // [N][nvox]
@@ -177,7 +197,7 @@ struct MlRateArgs {
     unsigned long long *scal;
 };
 
-size_t ml_sweep_smem_bytes(int prec, int rows, int nx);
+size_t ml_sweep_smem_bytes(int prec, int rows, int nx, int rpb);
 cudaError_t launch_ml_opacity(const MlOpacityArgs &a, cudaStream_t st);
 cudaError_t launch_ml_bottom(int prec, long nplane, int nfreq, const FreqInfo *fi,
                              double theta_ref, const double *T, void *ib, cudaStream_t st);
@@ -185,6 +205,7 @@ cudaError_t launch_ml_sweep_f64(const MlSweepArgs<double> &a, int bands, int thr
                                 cudaStream_t st);
 cudaError_t launch_ml_sweep_f32(const MlSweepArgs<float> &a, int bands, int threads,
                                 cudaStream_t st);
+cudaError_t launch_ml_accum(const MlAccumArgs &a, cudaStream_t st);
 cudaError_t launch_ml_rates(const MlRateArgs &a, cudaStream_t st);
 cudaError_t launch_ml_sweep_batch(int prec, const void *args, const BatchItem *items,
                                   int n_items, int bands, int threads, size_t smem,

@@ -11,12 +11,14 @@
 // Bound-free:  chi_t = kappa y^-3 (n_l - n_u G E),  eta_t = kappa y^-3 n_u G E (rho y)^3,
 //              G = n_l*/n_u*, E = exp(-theta_ref rho y/T).
 //
-// Sweep.  One thread-block cluster per (frequency, hemisphere); its blocks
-// split the plane in row bands and each holds the 12 intensity planes of the
-// hemisphere's rays, double buffered.  A thread owns a node and walks the 12
-// rays, so the angle sums
+// Sweep.  One thread-block cluster per (frequency, group of rays of one
+// hemisphere: 12, 6, 4, 3, 2 or 1 rays); its blocks split the plane in row
+// bands and each holds the intensity planes of the group's rays, double
+// buffered.  A thread owns a node and walks the group's rays, so the angle
+// sums
 //   Jx = sum_r w_r (I - w0 sl),   Ux = sum_r w_r (1 - w0 fl)
-// of its node are complete in registers and written once per hemisphere.
+// over the group are complete in registers and written once per group; the
+// radiative sums below add the groups in order.
 //
 // Rates (Rybicki & Hummer 1992, diagonal operator).  Per node, for a line:
 //   Jbar = sum wphi Jx, Ubar = sum wphi Ux (wphi: trapezoid x profile,
@@ -58,7 +60,7 @@ __global__ void ml_opacity_kernel(const MlOpacityArgs a) {
          i += (long)gridDim.x * blockDim.x) {
         const int f = (int)(i / a.nvox);
         const long v = i - (long)f * a.nvox;
-        const FreqInfo q = a.fi[f];
+        const FreqInfo q = a.fi[a.f0 + f];
         const double Tg = a.T[v];
         const double nl = a.n[(long)q.lo * a.nvox + v];
         const double nu = a.n[(long)q.up * a.nvox + v];
@@ -108,10 +110,13 @@ __global__ void ml_bottom_kernel(long nplane, int nfreq, const FreqInfo *__restr
 // -------------------------------------------------------------------- sweep
 
 template <typename T>
-__device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, int hemi) {
+__device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, int slot) {
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
-    // hemi 0: rays 0-11 (up), 1: rays 12-23 (down)
+    // slot = (hemisphere, ray group); hemisphere 0: rays 0-11 (up), 1: 12-23
+    const int rpb = a.rpb, groups = 12 / rpb;
+    const int hemi = slot / groups;
+    const int r0 = hemi * 12 + (slot - hemi * groups) * rpb;
     const bool up = hemi == 0;
     const int nx = a.nx, ny = a.ny, nz = a.nz, rows = a.rows;
     const int y0 = rank * rows;
@@ -123,13 +128,13 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
     const T *__restrict__ Sf = a.S + (long)f * nvox;
     const T *__restrict__ slf = a.sl + (long)f * nvox;
     const T *__restrict__ flf = a.fl + (long)f * nvox;
-    T *__restrict__ jxo = a.jx + ((long)hemi * a.nfreq + f) * nvox;
-    T *__restrict__ uxo = a.ux + ((long)hemi * a.nfreq + f) * nvox;
+    T *__restrict__ jxo = a.jx + ((long)slot * a.nfreq + f) * nvox;
+    T *__restrict__ uxo = a.ux + ((long)slot * a.nfreq + f) * nvox;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf = reinterpret_cast<T *>(smem_raw);
     const long raystride = (long)rows * nx;
-    const long bufstride = 12 * raystride;
+    const long bufstride = rpb * raystride;
     __shared__ double exp_tab[kExpTab];
     if (sizeof(T) == 8) {
         for (int i = threadIdx.x; i < kExpTab; i += blockDim.x) exp_tab[i] = a.exp_tab[i];
@@ -146,10 +151,10 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
                 const int yl = q / nx, x = q - yl * nx;
                 const int y = y0 + yl;
                 const T Ib = up ? a.ib[(long)f * nplane + (long)y * nx + x] : T(0);
-                for (int j = 0; j < 12; ++j) cur[j * raystride + (long)yl * nx + x] = Ib;
+                for (int j = 0; j < rpb; ++j) cur[j * raystride + (long)yl * nx + x] = Ib;
                 const long v = (long)k * nplane + (long)y * nx + x;
-                jxo[v] = T(12) * wray * Ib;
-                uxo[v] = T(12) * wray;
+                jxo[v] = T(rpb) * wray * Ib;
+                uxo[v] = T(rpb) * wray;
             }
         } else {
             const T *prev = buf + ((t - 1) & 1) * bufstride;
@@ -162,8 +167,8 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
                 const long v = (long)k * nplane + (long)y * nx + x;
                 const T chi_loc = chif[v], S_loc = Sf[v], sl = slf[v], fl = flf[v];
                 T jx = 0, ux = 0;
-                for (int j = 0; j < 12; ++j) {
-                    const StepGeom o = a.geom[(long)(hemi * 12 + j) * nz + t];
+                for (int j = 0; j < rpb; ++j) {
+                    const StepGeom o = a.geom[(long)(r0 + j) * nz + t];
                     const T tx = (T)o.tx, ty = (T)o.ty;
                     const T w00 = (T(1) - tx) * (T(1) - ty), w10 = tx * (T(1) - ty);
                     const T w01 = (T(1) - tx) * ty, w11 = tx * ty;
@@ -205,7 +210,7 @@ __global__ void __launch_bounds__(MAXT) ml_sweep_kernel(const MlSweepArgs<T> a) 
     ml_sweep_body<T>(a, blockIdx.y, blockIdx.z);
 }
 
-// Batched: item y = (problem, hemisphere as ray, frequency as group).
+// Batched: item y = (problem, ray-group slot as ray, frequency as group).
 template <typename T, int MAXT>
 __global__ void __launch_bounds__(MAXT) ml_sweep_batch_kernel(
     const MlSweepArgs<T> *__restrict__ args, const BatchItem *__restrict__ items) {
@@ -214,23 +219,23 @@ __global__ void __launch_bounds__(MAXT) ml_sweep_batch_kernel(
     ml_sweep_body<T>(a, it.group, it.ray);
 }
 
-size_t ml_sweep_smem_bytes(int prec, int rows, int nx) {
+size_t ml_sweep_smem_bytes(int prec, int rows, int nx, int rpb) {
     const size_t elem = prec == MG3D_PREC_F64 ? sizeof(double) : sizeof(float);
-    return 2ull * 12 * rows * nx * elem;
+    return 2ull * rpb * rows * nx * elem;
 }
 
 template <typename T, int MAXT>
 static cudaError_t launch_ml_sweep_t(const MlSweepArgs<T> &a, int bands, int threads,
                                      cudaStream_t st) {
     const size_t smem = ml_sweep_smem_bytes(sizeof(T) == 8 ? MG3D_PREC_F64 : MG3D_PREC_F32,
-                                            a.rows, a.nx);
+                                            a.rows, a.nx, a.rpb);
     // one fixed limit for every launch, so graph replays never meet a lower one
     cudaError_t e = cudaFuncSetAttribute(ml_sweep_kernel<T, MAXT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kMaxSweepSmem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(bands, a.nfreq, 2);
+    cfg.gridDim = dim3(bands, a.nfreq, 2 * (12 / a.rpb));
     cfg.blockDim = dim3(threads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
@@ -302,14 +307,71 @@ __device__ __forceinline__ unsigned long long dbits_ml(double x) {
     return (unsigned long long)__double_as_longlong(x);
 }
 
+// Radiative sums of the transitions over the chunk's frequencies, added to
+// acc (frequencies in increasing order within a chunk, chunks in order).
 template <typename TP>
-__global__ void __launch_bounds__(128) ml_rates_kernel(const MlRateArgs a) {
+__global__ void ml_accum_kernel(const MlAccumArgs a) {
     const TP *__restrict__ jx = (const TP *)a.jx;
     const TP *__restrict__ ux = (const TP *)a.ux;
     const long nvox = a.nvox;
-    const int N = a.n_levels;
     const long hstride = (long)a.nfreq * nvox;
+    const int f1 = a.f0 + a.nfreq;
+    // J, U of frequency f at node v: the ray-group slots added in order
+    auto sums = [&](int f, long v, double &J, double &U) {
+        const long i = (long)(f - a.f0) * nvox + v;
+        J = (double)jx[i];
+        U = (double)ux[i];
+        for (int s = 1; s < a.nslots; ++s) {
+            J += (double)jx[(long)s * hstride + i];
+            U += (double)ux[(long)s * hstride + i];
+        }
+    };
     const double rsqpi = 0.5641895835477563;
+    for (long v = blockIdx.x * (long)blockDim.x + threadIdx.x; v < nvox;
+         v += (long)gridDim.x * blockDim.x) {
+        const double Tg = a.T[v];
+        for (int t = 0; t < a.n_trans; ++t) {
+            const TransInfo tr = a.ti[t];
+            const int fb = max(tr.f_begin, a.f0), fe = min(tr.f_end, f1);
+            if (fb >= fe) continue;
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+            if (tr.kind == 0) {
+                const double d = sqrt(Tg / a.t_ref);
+                for (int f = fb; f < fe; ++f) {
+                    const FreqInfo q = a.fi[f];
+                    const double xd = q.xy / d;
+                    const double wphi = q.w * exp(-xd * xd) * rsqpi / d;
+                    double J = 0.0, U = 1.0;
+                    if (!a.zero_radiation) sums(f, v, J, U);
+                    s0 += wphi;
+                    s1 += wphi * J;
+                    s2 += wphi * U;
+                }
+            } else {
+                for (int f = fb; f < fe; ++f) {
+                    const FreqInfo q = a.fi[f];
+                    const double y = q.xy;
+                    const double qa = tr.coef * q.w / (y * y * y * y);
+                    const double E = exp(-a.theta_ref * tr.rho * y / Tg);
+                    const double ry = tr.rho * y;
+                    double J = 0.0, U = 1.0;
+                    if (!a.zero_radiation) sums(f, v, J, U);
+                    s0 += qa * J;
+                    s1 += qa * E * J;
+                    s2 += qa * E * ry * ry * ry * U;
+                }
+            }
+            double *acc = a.acc + (long)t * kAccTerms * nvox + v;
+            acc[0] += s0;
+            acc[nvox] += s1;
+            acc[2 * nvox] += s2;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128) ml_rates_kernel(const MlRateArgs a) {
+    const long nvox = a.nvox;
+    const int N = a.n_levels;
     double cmax = 0.0;
     unsigned neg = 0, bad = 0;
     const long stride = (long)gridDim.x * blockDim.x;
@@ -319,49 +381,19 @@ __global__ void __launch_bounds__(128) ml_rates_kernel(const MlRateArgs a) {
         double P[kMaxLevels][kMaxLevels];
         for (int i = 0; i < N; ++i)
             for (int j = 0; j < N; ++j) P[i][j] = i == j ? 0.0 : a.c[((long)i * N + j) * nvox + v];
-        const double Tg = a.T[v];
         for (int t = 0; t < a.n_trans; ++t) {
             const TransInfo tr = a.ti[t];
+            const double *acc = a.acc + (long)t * kAccTerms * nvox + v;
             if (tr.kind == 0) {
-                const double d = sqrt(Tg / a.t_ref);
-                double norm = 0.0, sj = 0.0, su = 0.0;
-                for (int f = tr.f_begin; f < tr.f_end; ++f) {
-                    const FreqInfo q = a.fi[f];
-                    const double xd = q.xy / d;
-                    const double wphi = q.w * exp(-xd * xd) * rsqpi / d;
-                    double J = 0.0, U = 1.0;
-                    if (!a.zero_radiation) {
-                        J = (double)jx[(long)f * nvox + v] + (double)jx[hstride + (long)f * nvox + v];
-                        U = (double)ux[(long)f * nvox + v] + (double)ux[hstride + (long)f * nvox + v];
-                    }
-                    norm += wphi;
-                    sj += wphi * J;
-                    su += wphi * U;
-                }
-                const double Jb = sj / norm, Ub = su / norm;
+                const double norm = acc[0];
+                const double Jb = acc[nvox] / norm, Ub = acc[2 * nvox] / norm;
                 const double b_ul = tr.coef / (tr.rho * tr.rho * tr.rho);
                 P[tr.lo][tr.up] += tr.gr * b_ul * Jb;
                 P[tr.up][tr.lo] += tr.coef * Ub + b_ul * Jb;
             } else {
                 const double G = a.saha[(long)tr.lo * nvox + v];
-                double s1 = 0.0, s2 = 0.0, s3 = 0.0;
-                for (int f = tr.f_begin; f < tr.f_end; ++f) {
-                    const FreqInfo q = a.fi[f];
-                    const double y = q.xy;
-                    const double qa = tr.coef * q.w / (y * y * y * y);
-                    const double E = exp(-a.theta_ref * tr.rho * y / Tg);
-                    const double ry = tr.rho * y;
-                    double J = 0.0, U = 1.0;
-                    if (!a.zero_radiation) {
-                        J = (double)jx[(long)f * nvox + v] + (double)jx[hstride + (long)f * nvox + v];
-                        U = (double)ux[(long)f * nvox + v] + (double)ux[hstride + (long)f * nvox + v];
-                    }
-                    s1 += qa * J;
-                    s2 += qa * E * J;
-                    s3 += qa * E * ry * ry * ry * U;
-                }
-                P[tr.lo][tr.up] += s1;
-                P[tr.up][tr.lo] += G * (s3 + s2);
+                P[tr.lo][tr.up] += acc[0];
+                P[tr.up][tr.lo] += G * (acc[2 * nvox] + acc[nvox]);
             }
         }
         // W(n) = M n: row 0 conservation, row i: n_i sum_j P_ij - sum_j n_j P_ji
@@ -478,11 +510,16 @@ cudaError_t launch_ml_bottom(int prec, long nplane, int nfreq, const FreqInfo *f
     return cudaGetLastError();
 }
 
-cudaError_t launch_ml_rates(const MlRateArgs &a, cudaStream_t st) {
+cudaError_t launch_ml_accum(const MlAccumArgs &a, cudaStream_t st) {
     if (a.prec == MG3D_PREC_F64)
-        ml_rates_kernel<double><<<grid_for(a.nvox, 128), 128, 0, st>>>(a);
+        ml_accum_kernel<double><<<grid_for(a.nvox, 128), 128, 0, st>>>(a);
     else
-        ml_rates_kernel<float><<<grid_for(a.nvox, 128), 128, 0, st>>>(a);
+        ml_accum_kernel<float><<<grid_for(a.nvox, 128), 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ml_rates(const MlRateArgs &a, cudaStream_t st) {
+    ml_rates_kernel<<<grid_for(a.nvox, 128), 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -137,6 +137,11 @@ _SIGNATURES = {
     "mg3d_set_fs_config": (_I, [_H, _I, _I, _I, _I, _I, _I]),
     "mg3d_get_fs_config": (_I, [_H, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
                                 ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "mg3d_set_ml_chunk": (_I, [_H, _I]),
+    "mg3d_get_ml_chunk": (_I, [_H, ctypes.POINTER(_I)]),
+    "mg3d_set_ml_shape": (_I, [_H, _I, _I, _I, _I]),
+    "mg3d_get_ml_shape": (_I, [_H, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                               ctypes.POINTER(_I)]),
     "mg3d_get_fs_occupancy": (_I, [_H, _I, _I, _I, _I, _I, _I, ctypes.POINTER(_I),
                                    ctypes.POINTER(ctypes.c_longlong)]),
     "mg3d_autotune": (_I, [_H, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),
@@ -382,6 +387,28 @@ def mg3d_get_fs_config(h, level: int):
     """(freq_per_block, bands, threads, lean, stage) of a level's sweep."""
     v = [_I() for _ in range(5)]
     _check(load().mg3d_get_fs_config(h, level, *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+def mg3d_set_ml_chunk(h, freq_per_chunk: int):
+    """Frequencies per chunk of a multi-level formal solution (0: all)."""
+    return _check(load().mg3d_set_ml_chunk(h, freq_per_chunk))
+
+
+def mg3d_get_ml_chunk(h) -> int:
+    c = _I()
+    _check(load().mg3d_get_ml_chunk(h, ctypes.byref(c)))
+    return c.value
+
+
+def mg3d_set_ml_shape(h, level: int, bands: int, rays_per_block: int, threads: int = 256):
+    return _check(load().mg3d_set_ml_shape(h, level, bands, rays_per_block, threads))
+
+
+def mg3d_get_ml_shape(h, level: int):
+    """(bands, rays_per_block, threads) of a level's multi-level sweep."""
+    v = [_I() for _ in range(3)]
+    _check(load().mg3d_get_ml_shape(h, level, *[ctypes.byref(x) for x in v]))
     return tuple(x.value for x in v)
 
 

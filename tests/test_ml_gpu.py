@@ -190,3 +190,104 @@ def test_ml_six_level_atom_600_frequencies():
             err, where = per_frequency_error(got, ref, p)
             assert err < tol_fs, (prec, err, where)
         assert rel(n_gpu, n1) < tol_n, prec
+
+
+# ------------------------------------------------------- frequency chunks
+
+def test_ml_chunked_angle_sums_equal_one_chunk():
+    """Every frequency's sweep is independent of the chunking: the angle sums
+    are bitwise the same for any chunk size, including chunks that split a
+    transition's frequencies."""
+    atm, atom = small()
+    h = m.mg3d_create_ml(atm, atom, n_grids=1)
+    try:
+        _, nf = m.mg3d_n_levels(h)
+        assert m.mg3d_get_ml_chunk(h) == nf
+        jx1, ux1 = m.mg3d_formal_solve_ml(h, 1)
+        for chunk in (8, 1, nf - 1):
+            m.mg3d_set_ml_chunk(h, chunk)
+            assert m.mg3d_get_ml_chunk(h) == chunk
+            jx, ux = m.mg3d_formal_solve_ml(h, 1)
+            assert np.array_equal(jx, jx1) and np.array_equal(ux, ux1), chunk
+        m.mg3d_set_ml_chunk(h, 0)
+        assert m.mg3d_get_ml_chunk(h) == nf
+    finally:
+        m.mg3d_destroy(h)
+
+
+@pytest.mark.parametrize("chunk", [7, 13])
+def test_ml_chunked_mali_matches_oracle(chunk):
+    """Transitions split across chunks: the radiative sums are added chunk by
+    chunk, and the populations still follow the oracle to 1e-10."""
+    atm, atom = small()
+    h = m.mg3d_create_ml(atm, atom, n_grids=1)
+    p = O.MultiLevelProblem(atm, atom)
+    n = p.zero_radiation(1)
+    try:
+        m.mg3d_set_ml_chunk(h, chunk)
+        for _ in range(4):
+            c_gpu = m.mg3d_mali_sweep(h, 1, 1)
+            n, c_orc = p.mali_sweep(1, n)
+            assert abs(c_gpu - c_orc) <= 1e-8 * c_orc
+        assert rel(m.mg3d_get_populations(h, 1), n) < 1e-10
+    finally:
+        m.mg3d_destroy(h)
+
+
+def test_ml_chunked_fas_equals_one_chunk():
+    atm, atom = small(16, 16, 33)
+    ha = m.mg3d_create_ml(atm, atom, n_grids=2, **ML_PARAMS)
+    hb = m.mg3d_create_ml(atm, atom, n_grids=2, **ML_PARAMS)
+    try:
+        m.mg3d_set_ml_chunk(hb, 9)
+        for cyc in range(2):
+            ca = m.mg3d_fas_vcycle(ha, cyc == 0)
+            cb = m.mg3d_fas_vcycle(hb, cyc == 0)
+            if ca > 1e-8:
+                assert abs(ca - cb) <= 1e-9 * ca
+            else:   # both at the rounding floor of the change over a cycle
+                assert cb < 1e-8
+        # a transition split across chunks sums its frequencies in two parts,
+        # a change of rounding order the cycles carry up to the FP64
+        # population tolerance
+        assert rel(m.mg3d_get_populations(hb, 2), m.mg3d_get_populations(ha, 2)) < 1e-10
+    finally:
+        m.mg3d_destroy(ha)
+        m.mg3d_destroy(hb)
+
+
+def test_ml_batch_rejects_chunked_members():
+    atm, atom = small()
+    h = m.mg3d_create_ml(atm, atom, n_grids=1)
+    try:
+        m.mg3d_set_ml_chunk(h, 5)
+        with pytest.raises(m.MG3DError, match="one chunk"):
+            m.mg3d_batch_create([h])
+    finally:
+        m.mg3d_destroy(h)
+
+
+@pytest.mark.parametrize("rpb,bands", [(6, 2), (4, 3), (3, 1), (1, 4)])
+def test_ml_ray_groups_match_oracle(rpb, bands):
+    """Blocks carrying fewer than the 12 rays of a hemisphere: the ray-group
+    slots are added after the sweep, and the sums and populations still
+    follow the oracle."""
+    atm, atom = small()
+    h = m.mg3d_create_ml(atm, atom, n_grids=1)
+    p = O.MultiLevelProblem(atm, atom)
+    n0 = p.zero_radiation(1)
+    Jo, Uo, _ = p.formal_solution(1, n0)
+    n1, _ = p.mali_sweep(1, n0)
+    n2, _ = p.mali_sweep(1, n1)
+    try:
+        m.mg3d_set_ml_shape(h, 1, bands, rpb, 64)
+        assert m.mg3d_get_ml_shape(h, 1) == (bands, rpb, 64)
+        jx, ux = m.mg3d_formal_solve_ml(h, 1)
+        for got, ref in ((jx, Jo), (ux, Uo)):
+            err, where = per_frequency_error(got, ref, p)
+            assert err < TOL_FS_ML, (err, where)
+        m.mg3d_set_ml_chunk(h, 11)
+        m.mg3d_mali_sweep(h, 1, 2)
+        assert rel(m.mg3d_get_populations(h, 1), n2) < 1e-10
+    finally:
+        m.mg3d_destroy(h)
