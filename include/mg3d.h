@@ -143,7 +143,7 @@ const char *mg3d_last_error(void);
  * coarser grids by
  * dropping every second node and full-weighting T, n_tot and c_ul (Sec. 4.1,
  * 4.7), and precomputes the per-plane upwind geometry of every ray.
- * Populations start at zero-radiation equilibrium (Sec. 4.9) on every grid.
+ * Populations start at zero-radiation equilibrium (Sec. 4.11) on every grid.
  * On success *out holds the handle; on failure *out is NULL. */
 int mg3d_create(const mg3d_atmosphere *atm, const mg3d_atom *atom,
                 const mg3d_quadrature *quad, const mg3d_params *params,
@@ -166,7 +166,7 @@ int mg3d_get_populations(mg3d_handle *h, int level, double *n_host);
 int mg3d_set_populations(mg3d_handle *h, int level, const double *n_host);
 
 /* Reset a level's populations to the zero-radiation solution of statistical
- * equilibrium (all radiative rates from J = 0; Sec. 4.9) and its right-hand
+ * equilibrium (all radiative rates from J = 0; Sec. 4.11) and its right-hand
  * side to f = (n_tot, 0). */
 int mg3d_init_zero_radiation(mg3d_handle *h, int level);
 
@@ -188,7 +188,7 @@ int mg3d_mali_sweep(mg3d_handle *h, int level, int n_sweeps, double *max_rel_cha
 int mg3d_residual(mg3d_handle *h, int level, double *r_host);
 
 /* One FAS V-cycle from the finest grid (Sec. 2.2).  is_first selects nu0
- * instead of nu1 for the finest-grid pre-smoothing (Sec. 4.10).
+ * instead of nu1 for the finest-grid pre-smoothing (Sec. 4.12).
  * *max_rel_change (nullable) receives C over the whole cycle. */
 int mg3d_fas_vcycle(mg3d_handle *h, int is_first, double *max_rel_change);
 

@@ -29,10 +29,10 @@ What each function follows in the paper (Bjorgen & Leenaarts 2017):
 * ``prolong_trilinear`` -- trilinear interpolation (Sec. 4.5).
 * ``vcycle``            -- FAS V-cycle, Eqs. 5-11 and the recursion of Sec. 2.2
   with nu_1 pre-, nu_2 post-smoothing, nu_3 coarse iterations, nu_0 in the
-  first cycle (Sec. 4.10) and the 10 % fix for negative populations (Sec. 4.8).
+  first cycle (Sec. 4.12) and the 10 % fix for negative populations (Sec. 4.10).
 * ``fmg_solve``         -- full multigrid (Sec. 2.3, Fig. 1).
 
-Readings where the paper is silent (each also listed in the design doc):
+Readings where the paper is silent (the same readings hold on the GPU path):
 full weighting at the fixed z boundaries injects in z; n_before of Eq. 10 is
 R(n^k) as it enters level k-1; the negative fix applies per (level, node)
 whenever n_old (1 + I(e)) <= 0; W(n) on the right of Eq. 9 is evaluated in
@@ -320,7 +320,7 @@ class TwoLevelProblem:
         return self.apply(self.rate_matrix(k, Jeff, U), n)
 
     def zero_radiation(self, k: int):
-        """Populations from statistical equilibrium with J = 0 (Sec. 4.9)."""
+        """Populations from statistical equilibrium with J = 0 (Sec. 4.11)."""
         lev = self.levels[k]
         zeros = np.zeros(lev.shape)
         ones = np.ones(lev.shape)
@@ -404,7 +404,9 @@ def restrict_hw(a):
     Coarse node (K, J, I) on fine node (2K, 2J, 2I) takes 1/2 of the centre
     and 1/12 of each of its six axis neighbours (x, y periodic).  On the two
     fixed boundary planes only the plane itself is used: 1/2 of the centre
-    and 1/8 of each of its four in-plane neighbours.
+    and 1/8 of each of its four in-plane neighbours.  (Reading: the paper
+    calls half weighting an average of the node and its six neighbours
+    without giving weights; these are the standard half-weighting ones.)
     """
     a = np.asarray(a, dtype=np.float64)
     nz, ny, nx = a.shape[-3:]
@@ -807,7 +809,7 @@ class MultiLevelProblem(TwoLevelProblem):
         return self.apply(self.rate_matrix_from(k, Jx, Ux, terms), n)
 
     def zero_radiation(self, k: int):
-        """Statistical equilibrium with J = 0 (Sec. 4.9): Jx = 0, Ux = 1."""
+        """Statistical equilibrium with J = 0 (Sec. 4.11): Jx = 0, Ux = 1."""
         lev = self.levels[k]
         nvox = lev.nx * lev.ny * lev.nz
         nf = len(self.freqs)

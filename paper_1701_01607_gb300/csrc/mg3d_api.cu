@@ -7,7 +7,7 @@
 //                f^{k-1} = R r^k + W^{k-1}_*(R n^k)         (Eq. 9, extra FS)
 //                k-1 == 1 ? nu3 MALI sweeps : V-cycle(k-1)
 //                e = (n_after - n_before)/n_before           (Eq. 10)
-//                n^k <- n^k (1 + I e), <= 0 -> 0.1 n^k       (Eq. 11, Sec. 4.8)
+//                n^k <- n^k (1 + I e), <= 0 -> 0.1 n^k       (Eq. 11, Sec. 4.10)
 //                nu2 MALI sweeps
 //   FMG:         nu_fmg sweeps on grid 1, then for k = 2..l: n^k = I n^{k-1}
 //                and one V-cycle on grid k (k < l); V-cycles on grid l until
@@ -611,7 +611,7 @@ int vcycle(mg3d_handle *h, int k, bool first) {
     } else {
         MG_TRY(vcycle(h, k - 1, false));
     }
-    // relative correction, interpolated (Eqs. 10-11), 10 % rule (Sec. 4.8)
+    // relative correction, interpolated (Eqs. 10-11), 10 % rule (Sec. 4.10)
     MG_TRY(launched(h, launch_prolong_correct(h->N, C.nx, C.ny, C.nz, F.tz, C.n, C.n_before, F.n,
                                               h->scal, h->stream),
                     "prolong correction"));

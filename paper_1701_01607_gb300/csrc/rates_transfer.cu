@@ -15,7 +15,7 @@
 // (periodic in x and y; on the two boundary planes the z stencil is the
 // plane itself, so the boundary heights stay fixed), trilinear interpolation
 // (linear in physical height for z), and the relative correction of
-// Eqs. 10-11 with the 10 % rule for negative populations (Sec. 4.8).
+// Eqs. 10-11 with the 10 % rule for negative populations (Sec. 4.10).
 #include "mg3d_internal.h"
 
 namespace mg3d {
@@ -280,7 +280,7 @@ __global__ void prolong_kernel(int ncomp, int nxc, int nyc, int nzc,
 }
 
 // n_fine <- n_fine (1 + I(e)), e = (n_after - n_before)/n_before on the
-// coarse grid (Eqs. 10-11); a result <= 0 becomes 0.1 n_fine (Sec. 4.8).
+// coarse grid (Eqs. 10-11); a result <= 0 becomes 0.1 n_fine (Sec. 4.10).
 __global__ void __launch_bounds__(256) prolong_correct_kernel(
     int ncomp, int nxc, int nyc, int nzc, const double *__restrict__ tz,
     const double *__restrict__ n_after, const double *__restrict__ n_before,
