@@ -54,7 +54,7 @@ FP64_NOMINAL_TFLOPS = 1.25      # GB300, at the 2070 MHz maximum SM clock
 # DRAM bytes (read + write) of one finest-grid FP64 sweep launch, from one ncu
 # capture of the current kernel at this launch shape (ng, bands, threads,
 # lean, stage); reported only when the autotuner picks the same shape
-FINE_SWEEP_TRAFFIC = {"shape": [9, 5, 512, 0, 1], "bytes": 13826560 + 141738240}
+FINE_SWEEP_TRAFFIC = {"shape": [9, 5, 512, 0, 0], "bytes": 13247744 + 142105600}
 SM_MAX_MHZ = 2070.0
 
 
@@ -389,6 +389,26 @@ def run_profile_case(prec_name, launches, shape):
         m.mg3d_destroy(h)
 
 
+def run_profile_ml(prec_name, launches):
+    """A few multi-level formal solutions for ncu: the 6-level atom with 120
+    frequencies (lines 5 x 20, continua 5 x 4) on a 64x64x129 chromosphere,
+    about 2 GB on the device in FP32."""
+    from paper_1701_01607_gb300 import mg3d as m
+    from paper_1701_01607_gb300 import synth
+    m.load(build_if_missing=True)
+    atom = synth.hydrogen_like_atom(line_freq=20, cont_freq=4, seed=2)
+    atm = synth.chromosphere(64, 64, 129, atom, seed=2)
+    prec = m.MG3D_PREC_F64 if prec_name == "f64" else m.MG3D_PREC_F32
+    h = m.mg3d_create_ml(atm, atom, n_grids=1, fs_prec=prec)
+    try:
+        for _ in range(launches):
+            m.mg3d_mali_sweep(h, 1, 1)
+        print("profile case: multi-level", prec_name, m.mg3d_get_ml_shape(h, 1),
+              "chunk", m.mg3d_get_ml_chunk(h), flush=True)
+    finally:
+        m.mg3d_destroy(h)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -404,12 +424,17 @@ def main():
                          '{"f64": {"1": [ng, bands, threads, lean, stage], ...}, "f32": {...}}')
     ap.add_argument("--profile-sweep", choices=["f64", "f32"],
                     help="only run a few finest-grid formal solutions (for ncu)")
+    ap.add_argument("--profile-ml", choices=["f64", "f32"],
+                    help="only run a few multi-level MALI sweeps (for ncu)")
     ap.add_argument("--profile-launches", type=int, default=3)
     ap.add_argument("--profile-shape", default="",
                     help="ng,bands,threads[,lean[,stage]] of the profiled sweep")
     args = ap.parse_args()
     if args.profile_sweep:
         run_profile_case(args.profile_sweep, args.profile_launches, args.profile_shape)
+        return
+    if args.profile_ml:
+        run_profile_ml(args.profile_ml, args.profile_launches)
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
