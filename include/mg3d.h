@@ -138,7 +138,8 @@ const char *mg3d_last_error(void);
 
 /* Create a solver: validates the grid (Sec. 4.2; MG3D_E_GRID unless every
  * coarsening keeps nz odd and nx, ny even, i.e. nz = A 2^(l-1) + 1 and
- * nx, ny = B 2^(l-1) with A, B >= 1 for l = n_grids), checks dx, dy > 0 and z
+ * nx, ny = B 2^(l-1) with A, B >= 1 for l = n_grids; nx, ny below 65536,
+ * else MG3D_E_ARG), checks dx, dy > 0 and z
  * increasing (MG3D_E_ARG), copies the atmosphere to device memory, builds the
  * coarser grids by
  * dropping every second node and full-weighting T, n_tot and c_ul (Sec. 4.1,

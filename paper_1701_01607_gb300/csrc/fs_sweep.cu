@@ -132,6 +132,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
     __syncthreads();
     const ExpNegTable et{exp_tab, a.exp_l1, a.exp_l2};
     const bool vec16 = (nx * sizeof(T)) % 16 == 0;
+    const unsigned long long rmagic = band_magic(rows);
     // bit f set: frequency f needs its own weights; clear: its phi equals
     // that of frequency f-1 (mirror halves of the profile stored next to
     // each other), so the weights of f-1, still in registers, are its own
@@ -238,9 +239,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
                 const T dtau0 = (chi_up + chi_loc) * half_s;
                 // 1/dtau0 is only used where dtau0 phi >= the series threshold,
                 // so dtau0 > 0 there
-                const T inv_dtau0 = T(1) / dtau0;
+                const T inv_dtau0 = rcp(dtau0);
                 // upwind rows of the intensity planes: local or in a peer block
-                const int ba = ya / rows, bb = yb / rows;
+                const int ba = band_of(ya, rmagic), bb = band_of(yb, rmagic);
                 const T *Pa = (ba == rank) ? prev : cluster.map_shared_rank(prev, ba);
                 const T *Pb = (bb == rank) ? prev : cluster.map_shared_rank(prev, bb);
                 Pa += (long)(ya - ba * rows) * nx;

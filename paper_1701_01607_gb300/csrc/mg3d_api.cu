@@ -1725,6 +1725,8 @@ int mg3d_create(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_qu
         !(atom->kappa > 0.0))
         return fail(MG3D_E_ARG, "bad atom parameters");
     if (atm->nx < 1 || atm->ny < 1 || atm->nz < 2) return fail(MG3D_E_ARG, "grid too small");
+    if (atm->nx >= 65536 || atm->ny >= 65536)
+        return fail(MG3D_E_ARG, "nx and ny must be below 65536");
     if (!(atm->dx > 0.0) || !(atm->dy > 0.0)) return fail(MG3D_E_ARG, "dx, dy must be > 0");
     for (int k = 1; k < atm->nz; ++k)
         if (!(atm->z[k] > atm->z[k - 1])) return fail(MG3D_E_ARG, "z must increase");
@@ -1788,6 +1790,8 @@ int mg3d_create_ml(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
     if (params->restriction < 0 || params->restriction > 2)
         return fail(MG3D_E_ARG, "restriction must be 0, 1 or 2");
     if (atm->nx < 1 || atm->ny < 1 || atm->nz < 2) return fail(MG3D_E_ARG, "grid too small");
+    if (atm->nx >= 65536 || atm->ny >= 65536)
+        return fail(MG3D_E_ARG, "nx and ny must be below 65536");
     if (!(atm->dx > 0.0) || !(atm->dy > 0.0)) return fail(MG3D_E_ARG, "dx, dy must be > 0");
     for (int k = 1; k < atm->nz; ++k)
         if (!(atm->z[k] > atm->z[k - 1])) return fail(MG3D_E_ARG, "z must increase");

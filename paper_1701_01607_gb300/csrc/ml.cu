@@ -142,6 +142,12 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
     }
     const ExpNegTable et{exp_tab, a.exp_l1, a.exp_l2};
     const T wray = T(1.0 / kRays);
+    const unsigned long long rmagic = band_magic(rows);
+    // per-ray constants of the current step (the upwind offset is the same
+    // for every node of a plane): bilinear weights, half path, corner offsets
+    __shared__ T g_w[12][4];
+    __shared__ T g_hs[12];
+    __shared__ int g_ix[12], g_iy[12];
 
     for (int t = 0; t < nz; ++t) {
         const int k = up ? t : nz - 1 - t;
@@ -157,6 +163,18 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
                 uxo[v] = T(rpb) * wray;
             }
         } else {
+            if (threadIdx.x < rpb) {
+                const StepGeom o = a.geom[(long)(r0 + threadIdx.x) * nz + t];
+                const T tx = (T)o.tx, ty = (T)o.ty;
+                g_w[threadIdx.x][0] = (T(1) - tx) * (T(1) - ty);
+                g_w[threadIdx.x][1] = tx * (T(1) - ty);
+                g_w[threadIdx.x][2] = (T(1) - tx) * ty;
+                g_w[threadIdx.x][3] = tx * ty;
+                g_hs[threadIdx.x] = T(0.5) * (T)o.s;
+                g_ix[threadIdx.x] = o.ix0;
+                g_iy[threadIdx.x] = o.iy0;
+            }
+            __syncthreads();
             const T *prev = buf + ((t - 1) & 1) * bufstride;
             const int kp = up ? k - 1 : k + 1;
             const T *__restrict__ chip = chif + (long)kp * nplane;
@@ -168,14 +186,11 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
                 const T chi_loc = chif[v], S_loc = Sf[v], sl = slf[v], fl = flf[v];
                 T jx = 0, ux = 0;
                 for (int j = 0; j < rpb; ++j) {
-                    const StepGeom o = a.geom[(long)(r0 + j) * nz + t];
-                    const T tx = (T)o.tx, ty = (T)o.ty;
-                    const T w00 = (T(1) - tx) * (T(1) - ty), w10 = tx * (T(1) - ty);
-                    const T w01 = (T(1) - tx) * ty, w11 = tx * ty;
-                    int xa = x + o.ix0;
+                    const T w00 = g_w[j][0], w10 = g_w[j][1], w01 = g_w[j][2], w11 = g_w[j][3];
+                    int xa = x + g_ix[j];
                     if (xa >= nx) xa -= nx;
                     const int xb = (xa + 1 == nx) ? 0 : xa + 1;
-                    int ya = y + o.iy0;
+                    int ya = y + g_iy[j];
                     if (ya >= ny) ya -= ny;
                     const int yb = (ya + 1 == ny) ? 0 : ya + 1;
                     const long ra = (long)ya * nx, rb = (long)yb * nx;
@@ -183,15 +198,15 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
                                      w01 * chip[rb + xa] + w11 * chip[rb + xb];
                     const T S_up = w00 * Sp[ra + xa] + w10 * Sp[ra + xb] +
                                    w01 * Sp[rb + xa] + w11 * Sp[rb + xb];
-                    const int ba = ya / rows, bb = yb / rows;
+                    const int ba = band_of(ya, rmagic), bb = band_of(yb, rmagic);
                     const T *Pa = (ba == rank) ? prev : cluster.map_shared_rank(prev, ba);
                     const T *Pb = (bb == rank) ? prev : cluster.map_shared_rank(prev, bb);
                     Pa += j * raystride + (long)(ya - ba * rows) * nx;
                     Pb += j * raystride + (long)(yb - bb * rows) * nx;
                     const T I_up = w00 * Pa[xa] + w10 * Pa[xb] + w01 * Pb[xa] + w11 * Pb[xb];
-                    const T x_tau = (chi_up + chi_loc) * (T(0.5) * (T)o.s);
+                    const T x_tau = (chi_up + chi_loc) * g_hs[j];
                     T ex, w0, wup, u;
-                    ScWeights<T>::eval(x_tau, T(1) / x_tau, et, ex, w0, wup, u);
+                    ScWeights<T>::eval(x_tau, rcp(x_tau), et, ex, w0, wup, u);
                     const T I = I_up * ex + wup * S_up + w0 * S_loc;
                     cur[j * raystride + (long)yl * nx + x] = I;
                     jx += I - w0 * sl;

@@ -16,6 +16,20 @@ namespace mg3d {
 template <typename T>
 struct ScWeights;
 
+// Row band of a global row: ya / rows by multiplication with
+// magic = ceil(2^32 / rows), exact for ya, rows < 2^16 (checked exhaustively
+// for rows up to 2048 and sampled above).  Grids are limited to ny < 2^16.
+__host__ __device__ inline unsigned long long band_magic(int rows) {
+    return ((1ull << 32) + (unsigned long long)rows - 1) / (unsigned long long)rows;
+}
+__device__ __forceinline__ int band_of(int ya, unsigned long long magic) {
+    return (int)(((unsigned long long)(unsigned)ya * magic) >> 32);
+}
+
+// 1/x in the formal-solution precision (correctly rounded in both).
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+
 // e^{-x} for x >= 0 by the table-driven method of Tang (ACM TOMS 15, 1989):
 // -x = (256 m + j) ln2/256 + r with integer m, j in [0, 256) and
 // |r| <= ln2/512, so e^{-x} = 2^m 2^{j/256} e^r.  The reduction uses a
