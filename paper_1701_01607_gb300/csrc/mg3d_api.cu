@@ -379,7 +379,8 @@ cudaEvent_t pool_event(mg3d_handle *h) {
 int ml_chunk_fs(mg3d_handle *h, int k, int f0, int nc) {
     Level &L = h->lev[k];
     MlOpacityArgs oa{L.nvox, nc, h->N, h->prec, h->d_fi, h->theta_ref, h->t_ref,
-                     L.n, L.T, L.chi_c, L.saha, L.mchi, L.mS, L.msl, L.mfl, f0};
+                     L.n, L.T, L.chi_c, L.saha, L.mchi, L.mS, L.msl, L.mfl, f0,
+                     h->d_exp_tab, h->exp_l1, h->exp_l2};
     MG_TRY(launched(h, launch_ml_opacity(oa, h->stream), "multi-level opacity"));
     TimedLaunch tl{nullptr, nullptr, k};
     if (h->timing) {
@@ -419,7 +420,7 @@ int ml_accumulate(mg3d_handle *h, int k, int f0, int nc, bool zero_rad) {
     Level &L = h->lev[k];
     MlAccumArgs a{L.nvox, f0, nc, h->ntrans, h->prec, h->d_fi, h->d_ti, h->theta_ref,
                   h->t_ref, L.T, h->ml_jx, h->ml_ux, 2 * (12 / L.ml_rpb), zero_rad ? 1 : 0,
-                  h->ml_acc};
+                  h->ml_acc, h->d_exp_tab, h->exp_l1, h->exp_l2};
     return launched(h, launch_ml_accum(a, h->stream), "radiative sums");
 }
 
@@ -1365,7 +1366,7 @@ int batch_ml_sums(mg3d_batch *b, mg3d_handle *h, int k, bool zero_rad) {
                             b->stream));
     MlAccumArgs a{L.nvox, 0, h->nfreq_ml, h->ntrans, h->prec, h->d_fi, h->d_ti, h->theta_ref,
                   h->t_ref, L.T, h->ml_jx, h->ml_ux, 2 * (12 / L.ml_rpb), zero_rad ? 1 : 0,
-                  h->ml_acc};
+                  h->ml_acc, h->d_exp_tab, h->exp_l1, h->exp_l2};
     return batch_launched(b, launch_ml_accum(a, b->stream), "batch radiative sums");
 }
 
@@ -1376,7 +1377,8 @@ int batch_fs(mg3d_batch *b, int k) {
         Level &L = h->lev[k];
         if (h->kind == 1) {
             MlOpacityArgs oa{L.nvox, h->nfreq_ml, h->N, h->prec, h->d_fi, h->theta_ref, h->t_ref,
-                             L.n, L.T, L.chi_c, L.saha, L.mchi, L.mS, L.msl, L.mfl};
+                             L.n, L.T, L.chi_c, L.saha, L.mchi, L.mS, L.msl, L.mfl, 0,
+                             h->d_exp_tab, h->exp_l1, h->exp_l2};
             MG_TRY(batch_launched(b, launch_ml_opacity(oa, b->stream), "batch opacity"));
             b->fs_units += (double)L.nvox * kRays * h->nfreq_ml;
         } else {

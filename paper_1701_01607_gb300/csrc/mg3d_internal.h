@@ -164,6 +164,8 @@ struct MlOpacityArgs {
     const double *n, *T, *chi_c, *saha;
     void *chi, *S, *sl, *fl;
     int f0;
+    const double *exp_tab;         // FP64 exp table of the sweep
+    double exp_l1, exp_l2;
 };
 
 // Radiative sums per transition and node, [n_trans][3][nvox] in FP64:
@@ -183,6 +185,8 @@ struct MlAccumArgs {
     int nslots;                    // ray groups of both hemispheres
     int zero_radiation;            // 1: J = 0, U = 1 (jx, ux unused)
     double *acc;
+    const double *exp_tab;         // FP64 exp table of the sweep
+    double exp_l1, exp_l2;
 };
 
 struct MlRateArgs {

@@ -52,43 +52,73 @@ __device__ __forceinline__ double planck_rho(double rho, double theta_ref, doubl
 
 // ------------------------------------------------------------------ opacity
 
+// exp(-x), x >= 0, in the opacity's precision: the sweep's table-driven FP64
+// exp, or the FP32 library exp for the FP32 formal solution.
+__device__ __forceinline__ double opac_exp(double x, const ExpNegTable &et) {
+    return exp_neg(x, et);
+}
+__device__ __forceinline__ float opac_exp(float x, const ExpNegTable &) { return expf(-x); }
+
+// One thread per node walks the chunk's frequencies, so per-node quantities
+// (temperature, Doppler width, background) and per-transition ones
+// (populations, the line-centre Planck function) are formed once.  The
+// profile and the source terms are evaluated in the formal-solution
+// precision T; population differences in FP64.
 template <typename T>
 __global__ void ml_opacity_kernel(const MlOpacityArgs a) {
-    const long total = (long)a.nfreq * a.nvox;
+    __shared__ double tab[kExpTab];
+    for (int i = threadIdx.x; i < kExpTab; i += blockDim.x) tab[i] = a.exp_tab[i];
+    __syncthreads();
+    const ExpNegTable et{tab, a.exp_l1, a.exp_l2};
     const double rsqpi = 0.5641895835477563;  // 1/sqrt(pi)
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total;
-         i += (long)gridDim.x * blockDim.x) {
-        const int f = (int)(i / a.nvox);
-        const long v = i - (long)f * a.nvox;
-        const FreqInfo q = a.fi[a.f0 + f];
+    const long nvox = a.nvox;
+    for (long v = blockIdx.x * (long)blockDim.x + threadIdx.x; v < nvox;
+         v += (long)gridDim.x * blockDim.x) {
         const double Tg = a.T[v];
-        const double nl = a.n[(long)q.lo * a.nvox + v];
-        const double nu = a.n[(long)q.up * a.nvox + v];
-        double chi_t, eta_t, B;
-        if (q.kind == 0) {
-            const double d = sqrt(Tg / a.t_ref);
-            const double xd = q.xy / d;
-            const double phi = exp(-xd * xd) * rsqpi / d;
-            chi_t = q.kappa * phi * (q.gr * nl - nu);
-            eta_t = q.kappa * q.rho * q.rho * q.rho * nu * phi;
-            B = planck_rho(q.rho, a.theta_ref, Tg);
-        } else {
-            const double y = q.xy;
-            const double G = a.saha[(long)q.lo * a.nvox + v];
-            const double E = exp(-a.theta_ref * q.rho * y / Tg);
-            const double alpha = 1.0 / (y * y * y);
-            const double ry = q.rho * y;
-            chi_t = q.kappa * alpha * (nl - nu * G * E);
-            eta_t = q.kappa * alpha * nu * G * E * ry * ry * ry;
-            B = planck_rho(ry, a.theta_ref, Tg);
-        }
         const double cc = a.chi_c[v];
-        const double chi = chi_t + cc;
-        const double inv = 1.0 / chi;
-        ((T *)a.chi)[i] = (T)chi;
-        ((T *)a.S)[i] = (T)((eta_t + cc * B) * inv);
-        ((T *)a.sl)[i] = (T)(eta_t * inv);
-        ((T *)a.fl)[i] = (T)(chi_t * inv);
+        const double inv_d = sqrt(a.t_ref / Tg);   // 1/d, d = sqrt(T/t_ref)
+        const T pnorm = (T)(rsqpi * inv_d);
+        int lo = -1, up = -1;
+        double nl = 0.0, nu = 0.0, G = 0.0, rho_b = -1.0;
+        T B = 0;
+        for (int fl = 0; fl < a.nfreq; ++fl) {
+            const FreqInfo q = a.fi[a.f0 + fl];
+            if (q.lo != lo || q.up != up) {
+                lo = q.lo;
+                up = q.up;
+                nl = a.n[(long)lo * nvox + v];
+                nu = a.n[(long)up * nvox + v];
+                G = a.saha[(long)lo * nvox + v];
+                rho_b = -1.0;
+            }
+            T chi_t, eta_t;
+            if (q.kind == 0) {
+                if (q.rho != rho_b) {
+                    rho_b = q.rho;
+                    B = (T)planck_rho(q.rho, a.theta_ref, Tg);
+                }
+                const double xd = q.xy * inv_d;
+                const T phi = opac_exp((T)(xd * xd), et) * pnorm;
+                chi_t = (T)q.kappa * phi * (T)(q.gr * nl - nu);
+                eta_t = (T)(q.kappa * q.rho * q.rho * q.rho) * (T)nu * phi;
+            } else {
+                const double y = q.xy;
+                const T E = opac_exp((T)(a.theta_ref * q.rho * y / Tg), et);
+                const double ry = q.rho * y;
+                const T alpha = (T)(q.kappa / (y * y * y));
+                chi_t = alpha * ((T)nl - (T)(nu * G) * E);
+                eta_t = alpha * (T)(nu * G * ry * ry * ry) * E;
+                B = (T)planck_rho(ry, a.theta_ref, Tg);
+                rho_b = -1.0;
+            }
+            const T chi = chi_t + (T)cc;
+            const T inv = T(1) / chi;
+            const long i = (long)fl * nvox + v;
+            ((T *)a.chi)[i] = chi;
+            ((T *)a.S)[i] = (eta_t + (T)cc * B) * inv;
+            ((T *)a.sl)[i] = eta_t * inv;
+            ((T *)a.fl)[i] = chi_t * inv;
+        }
     }
 }
 
@@ -326,6 +356,10 @@ __device__ __forceinline__ unsigned long long dbits_ml(double x) {
 // acc (frequencies in increasing order within a chunk, chunks in order).
 template <typename TP>
 __global__ void ml_accum_kernel(const MlAccumArgs a) {
+    __shared__ double tab[kExpTab];
+    for (int i = threadIdx.x; i < kExpTab; i += blockDim.x) tab[i] = a.exp_tab[i];
+    __syncthreads();
+    const ExpNegTable et{tab, a.exp_l1, a.exp_l2};
     const TP *__restrict__ jx = (const TP *)a.jx;
     const TP *__restrict__ ux = (const TP *)a.ux;
     const long nvox = a.nvox;
@@ -351,11 +385,12 @@ __global__ void ml_accum_kernel(const MlAccumArgs a) {
             if (fb >= fe) continue;
             double s0 = 0.0, s1 = 0.0, s2 = 0.0;
             if (tr.kind == 0) {
-                const double d = sqrt(Tg / a.t_ref);
+                const double inv_d = sqrt(a.t_ref / Tg);
                 for (int f = fb; f < fe; ++f) {
                     const FreqInfo q = a.fi[f];
-                    const double xd = q.xy / d;
-                    const double wphi = q.w * exp(-xd * xd) * rsqpi / d;
+                    const double xd = q.xy * inv_d;
+                    // profile in the formal-solution precision, sums in FP64
+                    const double wphi = q.w * (double)opac_exp((TP)(xd * xd), et) * rsqpi * inv_d;
                     double J = 0.0, U = 1.0;
                     if (!a.zero_radiation) sums(f, v, J, U);
                     s0 += wphi;
@@ -367,7 +402,7 @@ __global__ void ml_accum_kernel(const MlAccumArgs a) {
                     const FreqInfo q = a.fi[f];
                     const double y = q.xy;
                     const double qa = tr.coef * q.w / (y * y * y * y);
-                    const double E = exp(-a.theta_ref * tr.rho * y / Tg);
+                    const double E = (double)opac_exp((TP)(a.theta_ref * tr.rho * y / Tg), et);
                     const double ry = tr.rho * y;
                     double J = 0.0, U = 1.0;
                     if (!a.zero_radiation) sums(f, v, J, U);
@@ -505,11 +540,10 @@ __global__ void __launch_bounds__(128) ml_rates_kernel(const MlRateArgs a) {
 }
 
 cudaError_t launch_ml_opacity(const MlOpacityArgs &a, cudaStream_t st) {
-    const long total = (long)a.nfreq * a.nvox;
     if (a.prec == MG3D_PREC_F64)
-        ml_opacity_kernel<double><<<grid_for(total, 256), 256, 0, st>>>(a);
+        ml_opacity_kernel<double><<<grid_for(a.nvox, 256), 256, 0, st>>>(a);
     else
-        ml_opacity_kernel<float><<<grid_for(total, 256), 256, 0, st>>>(a);
+        ml_opacity_kernel<float><<<grid_for(a.nvox, 256), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
