@@ -389,6 +389,82 @@ def run_profile_case(prec_name, launches, shape):
         m.mg3d_destroy(h)
 
 
+BATCH_SIZES = [(32, 32, 33), (48, 48, 97), (64, 64, 129), (96, 96, 193)]
+
+
+def batch_members(n=32, seed0=100, ml_chunk=100):
+    """The 32-atmosphere batch: seeds seed0 .. seed0+n-1, sizes drawn from
+    BATCH_SIZES by each seed, two-level atoms (9 frequencies) for even seeds
+    and the 6-level atom (600 frequencies) for odd seeds; FP32 formal
+    solution, FP64 rates, 3 grids.  Returns (kind, atmosphere, atom) tuples."""
+    from paper_1701_01607_gb300 import synth
+    ml_atom = synth.hydrogen_like_atom(line_freq=100, cont_freq=20, seed=2)
+    out = []
+    for i in range(n):
+        seed = seed0 + i
+        nx, ny, nz = BATCH_SIZES[int(np.random.default_rng(seed).integers(len(BATCH_SIZES)))]
+        if seed % 2 == 0:
+            atm, atom = synth.stratified_two_level(nx, ny, nz, eps=1e-3, sigma=0.3, seed=seed)
+            out.append(("two", atm, atom))
+        else:
+            out.append(("ml", synth.chromosphere(nx, ny, nz, ml_atom, seed=seed), ml_atom))
+    return out
+
+
+def run_batch(args):
+    """Batched V-cycles of the 32-atmosphere batch (opt-in, --batch): one
+    batched sweep launch per atom kind (per frequency chunk for the 6-level
+    members), V-cycles replayed from CUDA graphs.  Prints one JSON line."""
+    import torch
+
+    from paper_1701_01607_gb300 import mg3d as m
+    m.load(build_if_missing=True)
+    t0 = time.perf_counter()
+    spec = batch_members()
+    params = dict(n_grids=3, fs_prec=m.MG3D_PREC_F32, nu_fmg=16, nu0=10, nu1=2, nu2=4,
+                  nu3=32)
+    hs = []
+    for kind, atm, atom in spec:
+        if kind == "two":
+            hs.append(m.mg3d_create(atm, atom, **params))
+        else:
+            hs.append(m.mg3d_create_ml(atm, atom, ml_chunk=100, **params))
+    b = m.mg3d_batch_create(hs)
+    setup_s = time.perf_counter() - t0
+    free, total = torch.cuda.mem_get_info()
+    try:
+        for i in range(args.warmup):
+            m.mg3d_batch_fas_vcycle(b, len(hs), i == 0)
+        c0 = m.mg3d_batch_counters(b)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _ in range(args.steps):
+            C = m.mg3d_batch_fas_vcycle(b, len(hs), False)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t1
+        c1 = m.mg3d_batch_counters(b)
+    finally:
+        m.mg3d_batch_destroy(b)
+        for h in hs:
+            m.mg3d_destroy(h)
+    units = c1["fs_units"] - c0["fs_units"]
+    kinds = [k for k, _, _ in spec]
+    return {"metric": "batched FS Gvoxel*ray*freq/s (32 uneven atmospheres, 3-grid FAS V-cycle)",
+            "value": round(units / wall / 1e9, 4), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(wall / args.steps * 1e3, 2), "higher_is_better": True,
+            "dtype": "f32 formal solution, f64 rates", "data": "synthetic",
+            "config": {"workload": "32 atmospheres, seeds 100-131, sizes from "
+                                   + ", ".join("x".join(map(str, s)) for s in BATCH_SIZES),
+                       "two_level_members": kinds.count("two"),
+                       "six_level_members": kinds.count("ml"),
+                       "freq_per_chunk_six_level": 100, **params},
+            "gpu_launches_per_step": round((c1["kernel_launches"] - c0["kernel_launches"])
+                                           / args.steps, 1),
+            "device_gb_in_use": round((total - free) / 1e9, 1), "setup_s": round(setup_s, 1),
+            "max_rel_change_last_step": float(np.max(C))}
+
+
 def run_profile_ml(prec_name, launches):
     """A few multi-level formal solutions for ncu: the 6-level atom with 120
     frequencies (lines 5 x 20, continua 5 x 4) on a 64x64x129 chromosphere,
@@ -424,6 +500,8 @@ def main():
                          '{"f64": {"1": [ng, bands, threads, lean, stage], ...}, "f32": {...}}')
     ap.add_argument("--profile-sweep", choices=["f64", "f32"],
                     help="only run a few finest-grid formal solutions (for ncu)")
+    ap.add_argument("--batch", action="store_true",
+                    help="time batched V-cycles of the 32-atmosphere batch instead")
     ap.add_argument("--profile-ml", choices=["f64", "f32"],
                     help="only run a few multi-level MALI sweeps (for ncu)")
     ap.add_argument("--profile-launches", type=int, default=3)
@@ -435,6 +513,9 @@ def main():
         return
     if args.profile_ml:
         run_profile_ml(args.profile_ml, args.profile_launches)
+        return
+    if args.batch:
+        print(json.dumps(run_batch(args)), flush=True)
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

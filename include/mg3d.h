@@ -89,7 +89,7 @@ typedef struct {
     double a;
 } mg3d_quadrature;
 
-/* Multigrid schedule (Sec. 2.2-2.3, 4.10, Table 1). */
+/* Multigrid schedule (Sec. 2.2-2.3, 4.12, Table 1). */
 typedef struct {
     int n_grids;   /* number of grids l, 1..MG3D_MAX_GRIDS */
     int nu_fmg;    /* MALI iterations on the coarsest grid in FMG */
@@ -101,6 +101,9 @@ typedef struct {
     int restriction; /* of populations and residuals (Sec. 4.4):
                         MG3D_RESTRICT_FULL (the paper's choice), _HALF, _INJECT;
                         the atmosphere is always full-weighted (Sec. 4.7) */
+    int ml_chunk;  /* multi-level handles: frequencies per chunk of the formal
+                      solution, 0 for the automatic choice (mg3d_set_ml_chunk);
+                      ignored by two-level handles */
 } mg3d_params;
 
 #define MG3D_RESTRICT_FULL 0    /* 27-node full weighting */

@@ -1317,7 +1317,10 @@ int create_ml_impl(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
         MG_CUDA(cudaMemcpy(h->d_exp_tab, tab, sizeof(tab), cudaMemcpyHostToDevice));
     }
     MG_TRY(dalloc(&h->ml_acc, (size_t)h->ntrans * kAccTerms * F.nvox));
-    MG_TRY(alloc_ml_chunks(h, default_ml_chunk(h)));
+    if (params && params->ml_chunk < 0) return fail(MG3D_E_ARG, "negative ml_chunk");
+    MG_TRY(alloc_ml_chunks(h, params && params->ml_chunk > 0
+                                  ? std::min(params->ml_chunk, h->nfreq_ml)
+                                  : default_ml_chunk(h)));
     MG_TRY(dalloc(&h->scal, 8));
     for (int k = 1; k <= h->L; ++k) MG_TRY(zero_radiation(h, k));
     MG_CUDA(cudaStreamSynchronize(h->stream));
@@ -1340,6 +1343,9 @@ struct mg3d_batch {
         BatchItem *d_items = nullptr;
         void *d_args = nullptr;
     } two[MG3D_MAX_GRIDS + 1], ml[MG3D_MAX_GRIDS + 1];
+    // multi-level members: one sweep table per chunk index c, covering the
+    // members that have a chunk c (each member's own chunk size)
+    std::vector<KindLevel> mlc[MG3D_MAX_GRIDS + 1];
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     long long launches = 0, delta_launches[2] = {0, 0};
     double fs_units = 0, delta_units[2] = {0, 0};
@@ -1358,28 +1364,31 @@ int batch_launched(mg3d_batch *b, cudaError_t e, const char *what) {
     return MG3D_OK;
 }
 
-// Radiative sums of a multi-level member on level k from its angle sums (all
-// frequencies in one chunk), or for zero radiation.
-int batch_ml_sums(mg3d_batch *b, mg3d_handle *h, int k, bool zero_rad) {
+// Radiative sums of a multi-level member on level k: the chunk f0 .. f0+nc-1
+// of its angle sums added (clear: start from zero), or, for zero radiation,
+// all frequencies with J = 0 and U = 1.
+int batch_ml_sums(mg3d_batch *b, mg3d_handle *h, int k, int f0, int nc, bool zero_rad,
+                  bool clear) {
     const Level &L = h->lev[k];
-    MG_CUDA(cudaMemsetAsync(h->ml_acc, 0, (size_t)h->ntrans * kAccTerms * L.nvox * sizeof(double),
-                            b->stream));
-    MlAccumArgs a{L.nvox, 0, h->nfreq_ml, h->ntrans, h->prec, h->d_fi, h->d_ti, h->theta_ref,
+    if (clear)
+        MG_CUDA(cudaMemsetAsync(h->ml_acc, 0,
+                                (size_t)h->ntrans * kAccTerms * L.nvox * sizeof(double),
+                                b->stream));
+    MlAccumArgs a{L.nvox, f0, nc, h->ntrans, h->prec, h->d_fi, h->d_ti, h->theta_ref,
                   h->t_ref, L.T, h->ml_jx, h->ml_ux, 2 * (12 / L.ml_rpb), zero_rad ? 1 : 0,
                   h->ml_acc, h->d_exp_tab, h->exp_l1, h->exp_l2};
     return batch_launched(b, launch_ml_accum(a, b->stream), "batch radiative sums");
 }
 
+int ml_chunks(const mg3d_handle *h) { return (h->nfreq_ml + h->ml_chunk - 1) / h->ml_chunk; }
+
 // Formal solution of level k for every member: per-member opacity, then one
-// batched sweep launch per atom kind.
+// batched sweep launch per atom kind (per frequency chunk for multi-level
+// members, each chunk followed by the members' radiative sums).
 int batch_fs(mg3d_batch *b, int k) {
     for (mg3d_handle *h : b->m) {
         Level &L = h->lev[k];
         if (h->kind == 1) {
-            MlOpacityArgs oa{L.nvox, h->nfreq_ml, h->N, h->prec, h->d_fi, h->theta_ref, h->t_ref,
-                             L.n, L.T, L.chi_c, L.saha, L.mchi, L.mS, L.msl, L.mfl, 0,
-                             h->d_exp_tab, h->exp_l1, h->exp_l2};
-            MG_TRY(batch_launched(b, launch_ml_opacity(oa, b->stream), "batch opacity"));
             b->fs_units += (double)L.nvox * kRays * h->nfreq_ml;
         } else {
             MG_TRY(batch_launched(b, launch_opacity(h->prec, L.nvox, h->atom.g_ratio,
@@ -1394,13 +1403,29 @@ int batch_fs(mg3d_batch *b, int k) {
         MG_TRY(batch_launched(b, launch_sweep_batch(b->prec, t.d_args, t.d_items, t.n_items,
                                                     t.bands, t.threads, t.smem, b->stream),
                               "batched sweep"));
-    mg3d_batch::KindLevel &q = b->ml[k];
-    if (q.n_items) {
-        MG_TRY(batch_launched(b, launch_ml_sweep_batch(b->prec, q.d_args, q.d_items, q.n_items,
-                                                       q.bands, q.threads, q.smem, b->stream),
-                              "batched multi-level sweep"));
-        for (mg3d_handle *h : b->m)
-            if (h->kind == 1) MG_TRY(batch_ml_sums(b, h, k, false));
+    for (size_t c = 0; c < b->mlc[k].size(); ++c) {
+        for (int i : b->ml[k].members) {
+            mg3d_handle *h = b->m[i];
+            if ((int)c >= ml_chunks(h)) continue;
+            Level &L = h->lev[k];
+            const int f0 = (int)c * h->ml_chunk, nc = std::min(h->ml_chunk, h->nfreq_ml - f0);
+            MlOpacityArgs oa{L.nvox, nc, h->N, h->prec, h->d_fi, h->theta_ref, h->t_ref,
+                             L.n, L.T, L.chi_c, L.saha, L.mchi, L.mS, L.msl, L.mfl, f0,
+                             h->d_exp_tab, h->exp_l1, h->exp_l2};
+            MG_TRY(batch_launched(b, launch_ml_opacity(oa, b->stream), "batch opacity"));
+        }
+        mg3d_batch::KindLevel &q = b->mlc[k][c];
+        if (q.n_items)
+            MG_TRY(batch_launched(b, launch_ml_sweep_batch(b->prec, q.d_args, q.d_items,
+                                                           q.n_items, q.bands, q.threads, q.smem,
+                                                           b->stream),
+                                  "batched multi-level sweep"));
+        for (int i : b->ml[k].members) {
+            mg3d_handle *h = b->m[i];
+            if ((int)c >= ml_chunks(h)) continue;
+            const int f0 = (int)c * h->ml_chunk, nc = std::min(h->ml_chunk, h->nfreq_ml - f0);
+            MG_TRY(batch_ml_sums(b, h, k, f0, nc, false, c == 0));
+        }
     }
     return MG3D_OK;
 }
@@ -1408,7 +1433,7 @@ int batch_fs(mg3d_batch *b, int k) {
 int member_rates(mg3d_batch *b, mg3d_handle *h, int k, int mode, double *out, bool zero_rad,
                  unsigned long long *scal) {
     if (h->kind == 1) {
-        if (zero_rad) MG_TRY(batch_ml_sums(b, h, k, true));
+        if (zero_rad) MG_TRY(batch_ml_sums(b, h, k, 0, h->nfreq_ml, true, true));
         MlRateArgs a = ml_rate_args(h, k, mode);
         a.out = out;
         a.scal = scal;
@@ -1640,14 +1665,12 @@ int batch_build_level(mg3d_batch *b, int k) {
         }
         if (!q.members.empty() && !bands)
             return fail(MG3D_E_ARG, "multi-level batch members need a common band count");
-        std::vector<BatchItem> items;
-        std::vector<unsigned char> args;
         const size_t asz = b->prec == MG3D_PREC_F64 ? sizeof(MlSweepArgs<double>)
                                                     : sizeof(MlSweepArgs<float>);
-        int threads = 32;
+        int threads = 32, chunks = 0;
         size_t smem = 0;
-        for (size_t j = 0; j < q.members.size(); ++j) {
-            mg3d_handle *h = b->m[q.members[j]];
+        for (int i : q.members) {
+            mg3d_handle *h = b->m[i];
             Level &L = h->lev[k];
             const int rows = (L.ny + bands - 1) / bands;
             L.ml_bands = bands;
@@ -1655,40 +1678,59 @@ int batch_build_level(mg3d_batch *b, int k) {
             L.ml_threads = std::min(256, threads_for_band(rows * L.nx));
             threads = std::max(threads, L.ml_threads);
             smem = std::max(smem, ml_sweep_smem_bytes(h->prec, rows, L.nx, L.ml_rpb));
+            chunks = std::max(chunks, ml_chunks(h));
             drop_graphs(h);
-            for (int slot = 0; slot < 2 * (12 / L.ml_rpb); ++slot)
-                for (int f = 0; f < h->nfreq_ml; ++f) items.push_back(BatchItem{(int)j, slot, f});
-            args.resize(args.size() + asz);
-            unsigned char *dst = args.data() + args.size() - asz;
-            if (b->prec == MG3D_PREC_F64) {
-                MlSweepArgs<double> a{L.nx, L.ny, L.nz, h->nfreq_ml, rows,
-                                      (const double *)L.mchi, (const double *)L.mS,
-                                      (const double *)L.msl, (const double *)L.mfl,
-                                      (const double *)L.mib, L.geom, h->d_exp_tab, h->exp_l1,
-                                      h->exp_l2, (double *)h->ml_jx, (double *)h->ml_ux,
-                                      L.ml_rpb};
-                std::memcpy(dst, &a, asz);
-            } else {
-                MlSweepArgs<float> a{L.nx, L.ny, L.nz, h->nfreq_ml, rows,
-                                     (const float *)L.mchi, (const float *)L.mS,
-                                     (const float *)L.msl, (const float *)L.mfl,
-                                     (const float *)L.mib, L.geom, h->d_exp_tab, h->exp_l1,
-                                     h->exp_l2, (float *)h->ml_jx, (float *)h->ml_ux,
-                                     L.ml_rpb};
-                std::memcpy(dst, &a, asz);
-            }
         }
-        if (items.size() > 65535) return fail(MG3D_E_ARG, "batch too large for one launch");
-        q.n_items = (int)items.size();
-        q.bands = bands;
-        q.threads = threads;
-        q.smem = smem;
-        if (q.n_items) {
-            MG_TRY(dev_alloc((void **)&q.d_items, items.size() * sizeof(BatchItem)));
-            MG_TRY(dev_alloc(&q.d_args, args.size()));
-            MG_CUDA(cudaMemcpy(q.d_items, items.data(), items.size() * sizeof(BatchItem),
-                               cudaMemcpyHostToDevice));
-            MG_CUDA(cudaMemcpy(q.d_args, args.data(), args.size(), cudaMemcpyHostToDevice));
+        b->mlc[k].assign(chunks, mg3d_batch::KindLevel{});
+        for (int c = 0; c < chunks; ++c) {
+            std::vector<BatchItem> items;
+            std::vector<unsigned char> args;
+            int j = 0;
+            for (int i : q.members) {
+                mg3d_handle *h = b->m[i];
+                if (c >= ml_chunks(h)) continue;
+                Level &L = h->lev[k];
+                const int f0 = c * h->ml_chunk, nc = std::min(h->ml_chunk, h->nfreq_ml - f0);
+                for (int slot = 0; slot < 2 * (12 / L.ml_rpb); ++slot)
+                    for (int f = 0; f < nc; ++f) items.push_back(BatchItem{j, slot, f});
+                ++j;
+                args.resize(args.size() + asz);
+                unsigned char *dst = args.data() + args.size() - asz;
+                const size_t es = elem_size(h->prec);
+                const void *ib =
+                    static_cast<const unsigned char *>(L.mib) + (size_t)f0 * L.nplane * es;
+                if (b->prec == MG3D_PREC_F64) {
+                    MlSweepArgs<double> a{L.nx, L.ny, L.nz, nc, L.ml_rows,
+                                          (const double *)L.mchi, (const double *)L.mS,
+                                          (const double *)L.msl, (const double *)L.mfl,
+                                          (const double *)ib, L.geom, h->d_exp_tab, h->exp_l1,
+                                          h->exp_l2, (double *)h->ml_jx, (double *)h->ml_ux,
+                                          L.ml_rpb};
+                    std::memcpy(dst, &a, asz);
+                } else {
+                    MlSweepArgs<float> a{L.nx, L.ny, L.nz, nc, L.ml_rows,
+                                         (const float *)L.mchi, (const float *)L.mS,
+                                         (const float *)L.msl, (const float *)L.mfl,
+                                         (const float *)ib, L.geom, h->d_exp_tab, h->exp_l1,
+                                         h->exp_l2, (float *)h->ml_jx, (float *)h->ml_ux,
+                                         L.ml_rpb};
+                    std::memcpy(dst, &a, asz);
+                }
+            }
+            if (items.size() > 65535)
+                return fail(MG3D_E_ARG, "batch chunk too large for one launch (use smaller chunks)");
+            mg3d_batch::KindLevel &t = b->mlc[k][c];
+            t.n_items = (int)items.size();
+            t.bands = bands;
+            t.threads = threads;
+            t.smem = smem;
+            if (t.n_items) {
+                MG_TRY(dev_alloc((void **)&t.d_items, items.size() * sizeof(BatchItem)));
+                MG_TRY(dev_alloc(&t.d_args, args.size()));
+                MG_CUDA(cudaMemcpy(t.d_items, items.data(), items.size() * sizeof(BatchItem),
+                                   cudaMemcpyHostToDevice));
+                MG_CUDA(cudaMemcpy(t.d_args, args.data(), args.size(), cudaMemcpyHostToDevice));
+            }
         }
     }
     return MG3D_OK;
@@ -1938,10 +1980,7 @@ int mg3d_batch_create(int n, mg3d_handle *const *members, mg3d_batch **out) {
             p.restriction != q.restriction)
             return fail(MG3D_E_ARG, "batch members need equal n_grids, precision and schedule");
     }
-    for (int i = 0; i < n; ++i)
-        if (members[i]->kind == 1 && members[i]->ml_chunk != members[i]->nfreq_ml)
-            return fail(MG3D_E_ARG,
-                        "multi-level batch members need all frequencies in one chunk");
+
     mg3d_batch *b = new (std::nothrow) mg3d_batch();
     if (!b) return fail(MG3D_E_OOM, "host allocation failed");
     b->n = n;
@@ -1983,10 +2022,16 @@ int mg3d_batch_destroy(mg3d_batch *b) {
     if (b->stream) cudaStreamSynchronize(b->stream);
     batch_drop_graphs(b);
     for (int k = 0; k <= MG3D_MAX_GRIDS; ++k)
+    {
         for (auto *t : {&b->two[k], &b->ml[k]}) {
             if (t->d_items) cudaFree(t->d_items);
             if (t->d_args) cudaFree(t->d_args);
         }
+        for (auto &t : b->mlc[k]) {
+            if (t.d_items) cudaFree(t.d_items);
+            if (t.d_args) cudaFree(t.d_args);
+        }
+    }
     for (mg3d_handle *h : b->m) mg3d_set_stream(h, nullptr);
     if (b->stream) cudaStreamDestroy(b->stream);
     delete b;

@@ -54,7 +54,8 @@ class mg3d_quadrature(ctypes.Structure):
 class mg3d_params(ctypes.Structure):
     _fields_ = [("n_grids", ctypes.c_int), ("nu_fmg", ctypes.c_int), ("nu0", ctypes.c_int),
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("nu3", ctypes.c_int),
-                ("fs_prec", ctypes.c_int), ("restriction", ctypes.c_int)]
+                ("fs_prec", ctypes.c_int), ("restriction", ctypes.c_int),
+                ("ml_chunk", ctypes.c_int)]
 
 
 class mg3d_line(ctypes.Structure):
@@ -231,7 +232,8 @@ def mg3d_create(atm, atom, quad_a: float = 0.0, n_grids: int = 1, nu_fmg: int = 
 
 def mg3d_create_ml(atm, atom, quad_a: float = 0.0, n_grids: int = 1, nu_fmg: int = 16,
                    nu0: int = 0, nu1: int = 2, nu2: int = 2, nu3: int = 32,
-                   fs_prec: int = MG3D_PREC_F64, restriction: int = MG3D_RESTRICT_FULL):
+                   fs_prec: int = MG3D_PREC_F64, restriction: int = MG3D_RESTRICT_FULL,
+                   ml_chunk: int = 0):
     """mg3d_create_ml from a synth.MultiLevelAtmosphere and MultiLevelAtom."""
     lib = load()
     keep = {}
@@ -252,7 +254,7 @@ def mg3d_create_ml(atm, atom, quad_a: float = 0.0, n_grids: int = 1, nu_fmg: int
     at = mg3d_ml_atom(atom.n_levels, arr("g", atom.g), arr("th", atom.theta), atom.theta_ref,
                       atom.t_ref, len(atom.lines), lines, len(atom.continua), conts)
     q = mg3d_quadrature(quad_a)
-    p = mg3d_params(n_grids, nu_fmg, nu0, nu1, nu2, nu3, fs_prec, restriction)
+    p = mg3d_params(n_grids, nu_fmg, nu0, nu1, nu2, nu3, fs_prec, restriction, ml_chunk)
     h = _H()
     _check(lib.mg3d_create_ml(ctypes.byref(a), ctypes.byref(at), ctypes.byref(q),
                               ctypes.byref(p), ctypes.byref(h)))

@@ -100,3 +100,33 @@ def test_batched_fas_and_fmg_solves():
             assert rel(n_fmg[i], m.mg3d_get_populations(h, 3)) < 1e-9
         finally:
             m.mg3d_destroy(h)
+
+
+def test_batched_multi_level_members_in_chunks():
+    """Multi-level members whose formal solutions run in chunks of different
+    sizes (so in different numbers of batched launches) next to a two-level
+    member: batched V-cycles equal the members' unchunked single solves."""
+    m.load(build_if_missing=True)
+    atom = synth.hydrogen_like_atom(line_freq=7, cont_freq=4, seed=2)
+    probs = [("ml", (synth.chromosphere(8, 8, 17, atom, seed=2), atom)),
+             ("ml", (synth.chromosphere(16, 8, 17, atom, seed=5), atom)),
+             ("two", synth.stratified_two_level(16, 16, 33, eps=1e-3, sigma=0.3, seed=31))]
+    members = [create(k, p, m.MG3D_PREC_F64) for k, p in probs]
+    singles = [create(k, p, m.MG3D_PREC_F64) for k, p in probs]
+    m.mg3d_set_ml_chunk(members[0], 9)
+    m.mg3d_set_ml_chunk(members[1], 20)
+    b = m.mg3d_batch_create(members)
+    try:
+        for cyc in range(3):
+            cb = m.mg3d_batch_fas_vcycle(b, len(members), cyc == 0)
+            cs = [m.mg3d_fas_vcycle(h, cyc == 0) for h in singles]
+            for i in range(len(members)):
+                if cs[i] > 1e-8:
+                    assert abs(cb[i] - cs[i]) <= 1e-6 * cs[i], (cyc, i)
+        for i in range(len(members)):
+            assert rel(m.mg3d_get_populations(members[i], 3),
+                       m.mg3d_get_populations(singles[i], 3)) < 1e-10, i
+    finally:
+        m.mg3d_batch_destroy(b)
+        for h in members + singles:
+            m.mg3d_destroy(h)

@@ -256,17 +256,6 @@ def test_ml_chunked_fas_equals_one_chunk():
         m.mg3d_destroy(hb)
 
 
-def test_ml_batch_rejects_chunked_members():
-    atm, atom = small()
-    h = m.mg3d_create_ml(atm, atom, n_grids=1)
-    try:
-        m.mg3d_set_ml_chunk(h, 5)
-        with pytest.raises(m.MG3DError, match="one chunk"):
-            m.mg3d_batch_create([h])
-    finally:
-        m.mg3d_destroy(h)
-
-
 @pytest.mark.parametrize("rpb,bands", [(6, 2), (4, 3), (3, 1), (1, 4)])
 def test_ml_ray_groups_match_oracle(rpb, bands):
     """Blocks carrying fewer than the 12 rays of a hemisphere: the ray-group
