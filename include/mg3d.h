@@ -379,7 +379,10 @@ int mg3d_get_fs_occupancy(mg3d_handle *h, int level, int freq_per_block, int ban
 
 /* Autotuner: times candidate sweep shapes on this GPU with the level's current
  * populations and keeps the fastest per level (level = 0: every level).
- * Candidates: every number of frequency groups up to 64, 1-16 bands,
+ * Multi-level handles: every band count (1-8), 12/6/4/3/2 rays per block and
+ * 128/256/512 threads that fit, timed on the first 32 frequencies; the chunk
+ * buffers are then resized for the chosen shapes (keeping a requested chunk
+ * size).  Two-level handles: every number of frequency groups up to 64, 1-16 bands,
  * 128/256/512 threads and the block sizes that cover a band in 1-4 equal
  * passes, the three register budgets, staged or not, where the shape fits and
  * can be scheduled; one launch each,

@@ -104,6 +104,7 @@ struct mg3d_handle {
     // angle sums of the chunk [2 hemispheres][ml_chunk][nvox] and the
     // radiative sums per transition [ntrans][kAccTerms][finest nvox] (FP64)
     int ml_chunk = 0;
+    int ml_chunk_req = 0;        // chunk asked for (0: automatic), kept across retuning
     int ml_slots = 2;            // most ray-group slots of any level (2 x 12 / ml_rpb)
     void *ml_jx = nullptr, *ml_ux = nullptr;
     double *ml_acc = nullptr;
@@ -1142,6 +1143,135 @@ int alloc_ml_chunks(mg3d_handle *h, int chunk) {
     return MG3D_OK;
 }
 
+// Device time (ms per launch) of `reps` multi-level sweeps of level k's first
+// nc frequencies with shape (bands, rpb, threads); the opacity of those
+// frequencies must be in place and the angle-sum buffers hold 2 x 12 / rpb
+// slots.
+int time_ml_shape(mg3d_handle *h, int k, int bands, int rpb, int threads, int nc, int reps,
+                  float *ms) {
+    Level &L = h->lev[k];
+    const int sb = L.ml_bands, sr = L.ml_rows, sp = L.ml_rpb, sth = L.ml_threads;
+    L.ml_bands = bands;
+    L.ml_rows = (L.ny + bands - 1) / bands;
+    L.ml_rpb = rpb;
+    L.ml_threads = threads;
+    cudaEvent_t a = pool_event(h), b = pool_event(h);
+    int rc = MG3D_OK;
+    cudaError_t e = cudaEventRecord(a, h->stream);
+    for (int i = 0; i < reps && e == cudaSuccess; ++i) {
+        if (h->prec == MG3D_PREC_F64) {
+            MlSweepArgs<double> sa{L.nx, L.ny, L.nz, nc, L.ml_rows,
+                                   (const double *)L.mchi, (const double *)L.mS,
+                                   (const double *)L.msl, (const double *)L.mfl,
+                                   (const double *)L.mib, L.geom, h->d_exp_tab, h->exp_l1,
+                                   h->exp_l2, (double *)h->ml_jx, (double *)h->ml_ux, rpb};
+            e = launch_ml_sweep_f64(sa, bands, threads, h->stream);
+        } else {
+            MlSweepArgs<float> sa{L.nx, L.ny, L.nz, nc, L.ml_rows,
+                                  (const float *)L.mchi, (const float *)L.mS,
+                                  (const float *)L.msl, (const float *)L.mfl,
+                                  (const float *)L.mib, L.geom, h->d_exp_tab, h->exp_l1,
+                                  h->exp_l2, (float *)h->ml_jx, (float *)h->ml_ux, rpb};
+            e = launch_ml_sweep_f32(sa, bands, threads, h->stream);
+        }
+        ++h->launches;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
+    if (e != cudaSuccess)
+        rc = fail(MG3D_E_CUDA, std::string("multi-level autotune: ") + cudaGetErrorString(e));
+    else
+        *ms /= (float)reps;
+    h->event_pool.push_back(a);
+    h->event_pool.push_back(b);
+    L.ml_bands = sb;
+    L.ml_rows = sr;
+    L.ml_rpb = sp;
+    L.ml_threads = sth;
+    return rc;
+}
+
+// Times the multi-level sweep shapes of level k on its first nc frequencies
+// (every band count, rays per block 12, 6, 4, 3 or 2 and 128/256/512 threads
+// that fit; once each, the best six three more times) and keeps the fastest.
+int autotune_ml_level(mg3d_handle *h, int k, int nc, int *evaluated) {
+    Level &L = h->lev[k];
+    MlOpacityArgs oa{L.nvox, nc, h->N, h->prec, h->d_fi, h->theta_ref, h->t_ref,
+                     L.n, L.T, L.chi_c, L.saha, L.mchi, L.mS, L.msl, L.mfl, 0,
+                     h->d_exp_tab, h->exp_l1, h->exp_l2};
+    MG_TRY(launched(h, launch_ml_opacity(oa, h->stream), "multi-level opacity"));
+    struct Cand {
+        int bands, rpb, threads;
+    };
+    std::vector<Cand> cands;
+    for (int rpb : {12, 6, 4, 3, 2})
+        for (int bands = 1; bands <= kPortableBands && bands <= L.ny; ++bands) {
+            const int rows = (L.ny + bands - 1) / bands;
+            if ((long)(bands - 1) * rows >= L.ny) continue;
+            if (ml_sweep_smem_bytes(h->prec, rows, L.nx, rpb) > kMaxSweepSmem) continue;
+            for (int th : {128, 256, 512}) {
+                if (th > 128 && th / 2 >= rows * L.nx) continue;  // a smaller block covers it
+                cands.push_back(Cand{bands, rpb, th});
+            }
+        }
+    if (cands.empty()) return fail(MG3D_E_ARG, "no multi-level sweep shape fits");
+    float warm = 0.f;
+    MG_TRY(time_ml_shape(h, k, L.ml_bands, L.ml_rpb, L.ml_threads, nc, 1, &warm));
+    std::vector<std::pair<float, size_t>> t1;
+    for (size_t i = 0; i < cands.size(); ++i) {
+        float ms = 0.f;
+        MG_TRY(time_ml_shape(h, k, cands[i].bands, cands[i].rpb, cands[i].threads, nc, 1, &ms));
+        t1.push_back({ms, i});
+    }
+    std::sort(t1.begin(), t1.end());
+    float best_ms = 1e30f;
+    size_t best = t1[0].second;
+    for (size_t j = 0; j < std::min<size_t>(6, t1.size()); ++j) {
+        const Cand &c = cands[t1[j].second];
+        float ms = 0.f;
+        MG_TRY(time_ml_shape(h, k, c.bands, c.rpb, c.threads, nc, 3, &ms));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = t1[j].second;
+        }
+    }
+    L.ml_bands = cands[best].bands;
+    L.ml_rows = (L.ny + L.ml_bands - 1) / L.ml_bands;
+    L.ml_rpb = cands[best].rpb;
+    L.ml_threads = cands[best].threads;
+    if (evaluated) *evaluated = (int)cands.size();
+    return MG3D_OK;
+}
+
+// Autotunes every level (or `level`) of a multi-level handle, then sizes the
+// chunk buffers for the chosen shapes (the requested chunk, else the
+// automatic one).
+int autotune_ml(mg3d_handle *h, int level, int *evaluated) {
+    MG_CUDA(cudaStreamSynchronize(h->stream));
+    drop_graphs(h);
+    // tuning buffers: up to 12 slots, at most 32 frequencies that fit
+    h->ml_slots = 12;
+    MG_TRY(alloc_ml_chunks(h, 1));
+    const int nc = std::min(32, default_ml_chunk(h));
+    MG_TRY(alloc_ml_chunks(h, nc));
+    int count = 0;
+    for (int k = 1; k <= h->L; ++k) {
+        if (level != 0 && k != level) continue;
+        int c = 0;
+        MG_TRY(autotune_ml_level(h, k, nc, &c));
+        count += c;
+    }
+    h->ml_slots = 2;
+    for (int k = 1; k <= h->L; ++k) h->ml_slots = std::max(h->ml_slots, 2 * (12 / h->lev[k].ml_rpb));
+    MG_TRY(alloc_ml_chunks(h, 1));
+    const int chunk = h->ml_chunk_req > 0 ? std::min(h->ml_chunk_req, h->nfreq_ml)
+                                          : default_ml_chunk(h);
+    MG_TRY(alloc_ml_chunks(h, chunk));
+    if (evaluated) *evaluated = count;
+    return MG3D_OK;
+}
+
 int create_ml_impl(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
                    const mg3d_quadrature *quad, const mg3d_params *params, mg3d_handle *h) {
     h->kind = 1;
@@ -1318,6 +1448,7 @@ int create_ml_impl(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
     }
     MG_TRY(dalloc(&h->ml_acc, (size_t)h->ntrans * kAccTerms * F.nvox));
     if (params && params->ml_chunk < 0) return fail(MG3D_E_ARG, "negative ml_chunk");
+    h->ml_chunk_req = params ? params->ml_chunk : 0;
     MG_TRY(alloc_ml_chunks(h, params && params->ml_chunk > 0
                                   ? std::min(params->ml_chunk, h->nfreq_ml)
                                   : default_ml_chunk(h)));
@@ -1911,6 +2042,7 @@ int mg3d_set_ml_chunk(mg3d_handle *h, int freq_per_chunk) {
     if (h->kind != 1) return fail(MG3D_E_STATE, "not a multi-level handle");
     if (freq_per_chunk < 0) return fail(MG3D_E_ARG, "negative chunk size");
     const int c = freq_per_chunk == 0 ? h->nfreq_ml : std::min(freq_per_chunk, h->nfreq_ml);
+    h->ml_chunk_req = c;
     MG_CUDA(cudaStreamSynchronize(h->stream));
     drop_graphs(h);
     return alloc_ml_chunks(h, c);
@@ -2393,7 +2525,14 @@ int mg3d_autotune(mg3d_handle *h, int level, int *evaluated, double *seconds) {
     if (level != 0) MG_TRY(check_level(h, level));
     auto t0 = std::chrono::steady_clock::now();
     int count = 0;
-    for (int k = 1; k <= h->L && h->kind == 0; ++k) {
+    if (h->kind == 1) {
+        MG_TRY(autotune_ml(h, level, &count));
+        if (evaluated) *evaluated = count;
+        if (seconds)
+            *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        return MG3D_OK;
+    }
+    for (int k = 1; k <= h->L; ++k) {
         if (level != 0 && k != level) continue;
         int c = 0;
         MG_TRY(autotune_level(h, k, &c));

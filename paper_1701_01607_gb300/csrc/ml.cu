@@ -17,8 +17,9 @@
 // buffered.  A thread owns a node and walks the group's rays, so the angle
 // sums
 //   Jx = sum_r w_r (I - w0 sl),   Ux = sum_r w_r (1 - w0 fl)
-// over the group are complete in registers and written once per group; the
-// radiative sums below add the groups in order.
+// over the group are complete in registers (as sum I - sl sum w0 and
+// rays - fl sum w0, sl and fl being the node's) and written once per group;
+// the radiative sums below add the groups in order.
 //
 // Rates (Rybicki & Hummer 1992, diagonal operator).  Per node, for a line:
 //   Jbar = sum wphi Jx, Ubar = sum wphi Ux (wphi: trapezoid x profile,
@@ -214,7 +215,9 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
                 const int y = y0 + yl;
                 const long v = (long)k * nplane + (long)y * nx + x;
                 const T chi_loc = chif[v], S_loc = Sf[v], sl = slf[v], fl = flf[v];
-                T jx = 0, ux = 0;
+                // sl and fl are the node's: sum I and w0 over the rays and
+                // form Jx = sum I - sl sum w0, Ux = rays - fl sum w0 once
+                T sum_i = 0, sum_w0 = 0;
                 for (int j = 0; j < rpb; ++j) {
                     const T w00 = g_w[j][0], w10 = g_w[j][1], w01 = g_w[j][2], w11 = g_w[j][3];
                     int xa = x + g_ix[j];
@@ -239,11 +242,11 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
                     ScWeights<T>::eval(x_tau, rcp(x_tau), et, ex, w0, wup, u);
                     const T I = I_up * ex + wup * S_up + w0 * S_loc;
                     cur[j * raystride + (long)yl * nx + x] = I;
-                    jx += I - w0 * sl;
-                    ux += T(1) - w0 * fl;
+                    sum_i += I;
+                    sum_w0 += w0;
                 }
-                jxo[v] = wray * jx;
-                uxo[v] = wray * ux;
+                jxo[v] = wray * (sum_i - sl * sum_w0);
+                uxo[v] = wray * (T(rpb) - fl * sum_w0);
             }
         }
         cluster.sync();

@@ -280,3 +280,26 @@ def test_ml_ray_groups_match_oracle(rpb, bands):
         assert rel(m.mg3d_get_populations(h, 1), n2) < 1e-10
     finally:
         m.mg3d_destroy(h)
+
+
+def test_ml_autotuned_shapes_keep_parity():
+    """The multi-level autotuner changes bands, rays per block and threads
+    (and resizes the chunk buffers); populations still follow the oracle."""
+    atm, atom = small(16, 16, 33)
+    h = m.mg3d_create_ml(atm, atom, n_grids=2)
+    p = O.MultiLevelProblem(atm, atom, n_grids=2)
+    n = p.zero_radiation(2)
+    try:
+        info = m.mg3d_autotune(h)
+        assert info["evaluated"] > 10
+        for k in (1, 2):
+            bands, rpb, threads = m.mg3d_get_ml_shape(h, k)
+            assert 12 % rpb == 0 and 1 <= bands <= 8
+        _, nf = m.mg3d_n_levels(h)
+        assert m.mg3d_get_ml_chunk(h) == nf
+        for _ in range(3):
+            m.mg3d_mali_sweep(h, 2, 1)
+            n, _ = p.mali_sweep(2, n)
+        assert rel(m.mg3d_get_populations(h, 2), n) < 1e-10
+    finally:
+        m.mg3d_destroy(h)
