@@ -465,10 +465,12 @@ def run_batch(args):
             "max_rel_change_last_step": float(np.max(C))}
 
 
-def run_profile_ml(prec_name, launches):
+def run_profile_ml(prec_name, launches, shape=""):
     """A few multi-level formal solutions for ncu: the 6-level atom with 120
     frequencies (lines 5 x 20, continua 5 x 4) on a 64x64x129 chromosphere,
-    about 2 GB on the device in FP32."""
+    about 2 GB on the device in FP32.  ``shape`` "bands,rays_per_block,threads"
+    fixes the multi-level sweep's shape (e.g. an autotuned one); no tuning
+    runs here, so every sweep launch is a profiled one."""
     from paper_1701_01607_gb300 import mg3d as m
     from paper_1701_01607_gb300 import synth
     m.load(build_if_missing=True)
@@ -477,6 +479,8 @@ def run_profile_ml(prec_name, launches):
     prec = m.MG3D_PREC_F64 if prec_name == "f64" else m.MG3D_PREC_F32
     h = m.mg3d_create_ml(atm, atom, n_grids=1, fs_prec=prec)
     try:
+        if shape:
+            m.mg3d_set_ml_shape(h, 1, *[int(v) for v in shape.split(",")])
         for _ in range(launches):
             m.mg3d_mali_sweep(h, 1, 1)
         print("profile case: multi-level", prec_name, m.mg3d_get_ml_shape(h, 1),
@@ -506,13 +510,14 @@ def main():
                     help="only run a few multi-level MALI sweeps (for ncu)")
     ap.add_argument("--profile-launches", type=int, default=3)
     ap.add_argument("--profile-shape", default="",
-                    help="ng,bands,threads[,lean[,stage]] of the profiled sweep")
+                    help="ng,bands,threads[,lean[,stage]] of the profiled sweep, or "
+                         "bands,rays_per_block,threads with --profile-ml")
     args = ap.parse_args()
     if args.profile_sweep:
         run_profile_case(args.profile_sweep, args.profile_launches, args.profile_shape)
         return
     if args.profile_ml:
-        run_profile_ml(args.profile_ml, args.profile_launches)
+        run_profile_ml(args.profile_ml, args.profile_launches, args.profile_shape)
         return
     if args.batch:
         print(json.dumps(run_batch(args)), flush=True)
