@@ -166,6 +166,13 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
     T *buf = reinterpret_cast<T *>(smem_raw);
     const long raystride = (long)rows * nx;
     const long bufstride = rpb * raystride;
+    // per step and (ray, local row): the upwind rows of the intensity planes
+    // (here or in a peer block) and of chi, S on the upwind plane
+    struct RowRef {
+        const T *pa, *pb;
+        int ra, rb;
+    };
+    RowRef *rowref = reinterpret_cast<RowRef *>(buf + 2 * bufstride);
     __shared__ double exp_tab[kExpTab];
     if (sizeof(T) == 8) {
         for (int i = threadIdx.x; i < kExpTab; i += blockDim.x) exp_tab[i] = a.exp_tab[i];
@@ -178,7 +185,7 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
     // for every node of a plane): bilinear weights, half path, corner offsets
     __shared__ T g_w[12][4];
     __shared__ T g_hs[12];
-    __shared__ int g_ix[12], g_iy[12];
+    __shared__ int g_ix[12];
 
     for (int t = 0; t < nz; ++t) {
         const int k = up ? t : nz - 1 - t;
@@ -194,6 +201,7 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
                 uxo[v] = T(rpb) * wray;
             }
         } else {
+            const T *prev = buf + ((t - 1) & 1) * bufstride;
             if (threadIdx.x < rpb) {
                 const StepGeom o = a.geom[(long)(r0 + threadIdx.x) * nz + t];
                 const T tx = (T)o.tx, ty = (T)o.ty;
@@ -203,10 +211,23 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
                 g_w[threadIdx.x][3] = tx * ty;
                 g_hs[threadIdx.x] = T(0.5) * (T)o.s;
                 g_ix[threadIdx.x] = o.ix0;
-                g_iy[threadIdx.x] = o.iy0;
+            }
+            for (int i = threadIdx.x; i < rpb * myrows; i += blockDim.x) {
+                const int j = i / myrows, yl = i - j * myrows;
+                int ya = y0 + yl + a.geom[(long)(r0 + j) * nz + t].iy0;
+                if (ya >= ny) ya -= ny;
+                const int yb = (ya + 1 == ny) ? 0 : ya + 1;
+                const int ba = band_of(ya, rmagic), bb = band_of(yb, rmagic);
+                const T *Pa = (ba == rank) ? prev : cluster.map_shared_rank(prev, ba);
+                const T *Pb = (bb == rank) ? prev : cluster.map_shared_rank(prev, bb);
+                RowRef r;
+                r.pa = Pa + j * raystride + (long)(ya - ba * rows) * nx;
+                r.pb = Pb + j * raystride + (long)(yb - bb * rows) * nx;
+                r.ra = ya * nx;
+                r.rb = yb * nx;
+                rowref[j * rows + yl] = r;
             }
             __syncthreads();
-            const T *prev = buf + ((t - 1) & 1) * bufstride;
             const int kp = up ? k - 1 : k + 1;
             const T *__restrict__ chip = chif + (long)kp * nplane;
             const T *__restrict__ Sp = Sf + (long)kp * nplane;
@@ -223,19 +244,12 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
                     int xa = x + g_ix[j];
                     if (xa >= nx) xa -= nx;
                     const int xb = (xa + 1 == nx) ? 0 : xa + 1;
-                    int ya = y + g_iy[j];
-                    if (ya >= ny) ya -= ny;
-                    const int yb = (ya + 1 == ny) ? 0 : ya + 1;
-                    const long ra = (long)ya * nx, rb = (long)yb * nx;
-                    const T chi_up = w00 * chip[ra + xa] + w10 * chip[ra + xb] +
-                                     w01 * chip[rb + xa] + w11 * chip[rb + xb];
-                    const T S_up = w00 * Sp[ra + xa] + w10 * Sp[ra + xb] +
-                                   w01 * Sp[rb + xa] + w11 * Sp[rb + xb];
-                    const int ba = band_of(ya, rmagic), bb = band_of(yb, rmagic);
-                    const T *Pa = (ba == rank) ? prev : cluster.map_shared_rank(prev, ba);
-                    const T *Pb = (bb == rank) ? prev : cluster.map_shared_rank(prev, bb);
-                    Pa += j * raystride + (long)(ya - ba * rows) * nx;
-                    Pb += j * raystride + (long)(yb - bb * rows) * nx;
+                    const RowRef r = rowref[j * rows + yl];
+                    const T *ca = chip + r.ra, *cb = chip + r.rb;
+                    const T *sa = Sp + r.ra, *sb = Sp + r.rb;
+                    const T chi_up = w00 * ca[xa] + w10 * ca[xb] + w01 * cb[xa] + w11 * cb[xb];
+                    const T S_up = w00 * sa[xa] + w10 * sa[xb] + w01 * sb[xa] + w11 * sb[xb];
+                    const T *Pa = r.pa, *Pb = r.pb;
                     const T I_up = w00 * Pa[xa] + w10 * Pa[xb] + w01 * Pb[xa] + w11 * Pb[xb];
                     const T x_tau = (chi_up + chi_loc) * g_hs[j];
                     T ex, w0, wup, u;
@@ -269,7 +283,9 @@ __global__ void __launch_bounds__(MAXT) ml_sweep_batch_kernel(
 
 size_t ml_sweep_smem_bytes(int prec, int rows, int nx, int rpb) {
     const size_t elem = prec == MG3D_PREC_F64 ? sizeof(double) : sizeof(float);
-    return 2ull * rpb * rows * nx * elem;
+    // intensity planes, then the per-(ray, row) upwind row table (two
+    // pointers and two offsets, 24 bytes; the planes end on an 8-byte boundary)
+    return 2ull * rpb * rows * nx * elem + 24ull * rpb * rows;
 }
 
 template <typename T, int MAXT>

@@ -26,9 +26,10 @@ __device__ __forceinline__ int band_of(int ya, unsigned long long magic) {
     return (int)(((unsigned long long)(unsigned)ya * magic) >> 32);
 }
 
-// 1/x in the formal-solution precision (correctly rounded in both).
+// 1/x in the formal-solution precision: FP64 correctly rounded; FP32 the
+// hardware approximation (within 2 ulp), ample for the FP32 formal solution.
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
-__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
 
 // e^{-x} for x >= 0 by the table-driven method of Tang (ACM TOMS 15, 1989):
 // -x = (256 m + j) ln2/256 + r with integer m, j in [0, 256) and
