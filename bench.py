@@ -318,6 +318,51 @@ def time_to_solution(m, atm, atom, stream, tol=1e-3):
     out["tol"] = tol
     out["speedup_fas"] = round(out["mali"]["seconds"] / out["fas"]["seconds"], 3)
     out["speedup_fmg"] = round(out["mali"]["seconds"] / out["fmg"]["seconds"], 3)
+    out["equal_accuracy"] = equal_accuracy(m, atm, atom, stream, n_ref)
+    return out
+
+
+def equal_accuracy(m, atm, atom, stream, n_ref, target=1e-3):
+    """MALI, FAS and FMG, each run until its true error E_inf against the
+    converged reference is at most `target` (the same accuracy for all three):
+    timed iterations only, the E_inf checks between them are not timed.
+    MALI is checked every 5 sweeps, FAS and FMG after every V-cycle (FMG's
+    first call is its full-multigrid pass with one V-cycle)."""
+    def e_inf(h, grids):
+        n = m.mg3d_get_populations(h, grids)
+        return float(np.max(np.abs(n - n_ref) / np.abs(n_ref)))
+
+    out = {"target_e_inf": target}
+    for method in ("mali", "fas", "fmg"):
+        grids = 1 if method == "mali" else N_GRIDS
+        h = m.mg3d_create(atm, atom, n_grids=grids, fs_prec=m.MG3D_PREC_F64, **NU)
+        m.mg3d_set_stream(h, stream.cuda_stream)
+        m.mg3d_reset_counters(h)
+        secs, its, err = 0.0, 0, 1.0
+        try:
+            while err > target and its < 20000:
+                t0 = time.perf_counter()
+                if method == "mali":
+                    m.mg3d_mali_sweep(h, 1, 5)
+                    its += 5
+                elif method == "fas":
+                    m.mg3d_fas_vcycle(h, its == 0)
+                    its += 1
+                elif its == 0:
+                    m.mg3d_fmg_solve(h, 1e300, 1, n_grids=grids)
+                    its += 1
+                else:
+                    m.mg3d_fas_vcycle(h, False)
+                    its += 1
+                secs += time.perf_counter() - t0
+                err = e_inf(h, grids)
+            units = m.mg3d_get_counters(h)["fs_units"]
+        finally:
+            m.mg3d_destroy(h)
+        out[method] = {"seconds": round(secs, 4), "iterations": its, "e_inf": err,
+                       "fine_fs_equivalents": round(units / FS_UNITS_PER_FINE, 3)}
+    out["speedup_fas"] = round(out["mali"]["seconds"] / out["fas"]["seconds"], 3)
+    out["speedup_fmg"] = round(out["mali"]["seconds"] / out["fmg"]["seconds"], 3)
     return out
 
 
