@@ -510,6 +510,46 @@ def run_batch(args):
             "max_rel_change_last_step": float(np.max(C))}
 
 
+def run_chromosphere(args):
+    """MALI, FAS and FMG from the zero-radiation start to C < 1e-3 on the
+    128x128x257 chromosphere with the 6-level atom at 600 frequencies (FP32
+    formal solution, FP64 rates, 3 grids, (nu_0, nu_1, nu_2, nu_3) =
+    (20, 4, 8, 32), sweep shapes autotuned first; opt-in, --chromosphere).
+    Prints one JSON line."""
+    from paper_1701_01607_gb300 import mg3d as m
+    from paper_1701_01607_gb300 import synth
+    m.load(build_if_missing=True)
+    atom = synth.hydrogen_like_atom(line_freq=100, cont_freq=20, seed=2)
+    atm = synth.chromosphere(128, 128, 257, atom, seed=2)
+    params = dict(fs_prec=m.MG3D_PREC_F32, nu_fmg=16, nu0=20, nu1=4, nu2=8, nu3=32)
+    units_fine = 128 * 128 * 257 * 24 * 600
+    out = {"metric": "time to C < 1e-3, 6-level atom (600 frequencies), 128x128x257",
+           "unit": "s", "higher_is_better": False, "n_gpus": 1,
+           "dtype": "f32 formal solution, f64 rates", "data": "synthetic",
+           "config": {"workload": "chromosphere 128x128x257, 6-level atom, seed 2", **params}}
+    for method, grids, fn, cap in (("fas", 3, m.mg3d_fas_solve, 40),
+                                   ("fmg", 3, m.mg3d_fmg_solve, 40),
+                                   ("mali", 1, m.mg3d_mali_solve, 400)):
+        h = m.mg3d_create_ml(atm, atom, n_grids=grids, **params)
+        try:
+            m.mg3d_autotune(h)
+            m.mg3d_set_timing(h, True)
+            m.mg3d_reset_counters(h)
+            st = fn(h, 1e-3, cap, n_grids=grids)
+            c = m.mg3d_get_counters(h)
+            n = m.mg3d_get_populations(h, grids)
+        finally:
+            m.mg3d_destroy(h)
+        out[method] = {"seconds": round(st["seconds"], 2), "iterations": st["iterations"],
+                       "fine_fs_equivalents": round(st["fine_fs_equivalents"], 1),
+                       "fs_gunits_s": round(c["fs_units"] / (c["fs_kernel_ms"] * 1e-3) / 1e9, 2),
+                       "negatives": st["negatives"],
+                       "conservation": float(np.max(np.abs(n.sum(axis=0) / atm.n_tot - 1)))}
+    out["value"] = out["fas"]["seconds"]
+    out["fine_fs_units"] = units_fine
+    return out
+
+
 def run_profile_ml(prec_name, launches, shape=""):
     """A few multi-level formal solutions for ncu: the 6-level atom with 120
     frequencies (lines 5 x 20, continua 5 x 4) on a 64x64x129 chromosphere,
@@ -549,6 +589,8 @@ def main():
                          '{"f64": {"1": [ng, bands, threads, lean, stage], ...}, "f32": {...}}')
     ap.add_argument("--profile-sweep", choices=["f64", "f32"],
                     help="only run a few finest-grid formal solutions (for ncu)")
+    ap.add_argument("--chromosphere", action="store_true",
+                    help="time MALI, FAS and FMG on the 128x128x257 6-level chromosphere instead")
     ap.add_argument("--batch", action="store_true",
                     help="time batched V-cycles of the 32-atmosphere batch instead")
     ap.add_argument("--profile-ml", choices=["f64", "f32"],
@@ -566,6 +608,9 @@ def main():
         return
     if args.batch:
         print(json.dumps(run_batch(args)), flush=True)
+        return
+    if args.chromosphere:
+        print(json.dumps(run_chromosphere(args)), flush=True)
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
