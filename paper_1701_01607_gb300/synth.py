@@ -297,7 +297,7 @@ def chromosphere(nx: int, ny: int, nz: int, atom: MultiLevelAtom, seed: int = 2,
                  t_min: float = 4000.0, t_max: float = 10000.0, scale_heights: float = 8.0,
                  n_bottom: float = 1e4, sigma_t: float = 0.1, ionisation: float = 1e-3,
                  saha_scale: float = 10.0, c_strength: float = 1e-2, chi_c0: float = 1e-2,
-                 dx: float = 1.0, z=None) -> MultiLevelAtmosphere:
+                 dx: float = 1.0, z=None, ground_collisions: float = 1.0) -> MultiLevelAtmosphere:
     """Chromosphere-like box: T rises from t_min to t_max with height (with
     seeded 3D perturbations of relative size sigma_t), the density falls by
     e^scale_heights from bottom to top; electron density = ionisation x
@@ -305,7 +305,10 @@ def chromosphere(nx: int, ny: int, nz: int, atom: MultiLevelAtom, seed: int = 2,
     seeded strengths and detailed balance; Saha-like LTE ratios
     saha_i = saha_scale n_e T^-3/2 (g_i/g_c) exp(theta_ion_i / T).  With the
     default strengths no line or continuum is inverted at the zero-radiation
-    start (ten times weaker collisions make the upper lines mase)."""
+    start (ten times weaker collisions make the upper lines mase).
+    ground_collisions scales the collisions out of the ground level only, so
+    that the resonance lines can be made scattering-dominated while the upper
+    lines keep the collisions that prevent inversions."""
     rng = np.random.default_rng(seed)
     if z is None:
         z = np.arange(nz, dtype=np.float64) * dx
@@ -328,6 +331,8 @@ def chromosphere(nx: int, ny: int, nz: int, atom: MultiLevelAtom, seed: int = 2,
     for i in range(N):
         for j in range(i + 1, N):
             s = c_strength * (1.0 + 0.2 * (2.0 * rng.random() - 1.0)) / (1.0 + (j - i))
+            if i == 0:
+                s *= ground_collisions
             down = s * n_e * (T / 5000.0) ** -0.5          # j -> i
             if j == cont:
                 # detailed balance with the LTE ratio n_i*/n_c* = saha_i
