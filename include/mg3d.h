@@ -383,8 +383,8 @@ int mg3d_get_fs_occupancy(mg3d_handle *h, int level, int freq_per_block, int ban
  * 128/256/512 threads that fit, timed on the first 32 frequencies; the chunk
  * buffers are then resized for the chosen shapes (keeping a requested chunk
  * size).  Two-level handles: every number of frequency groups up to 64, 1-16 bands,
- * 128/256/512 threads and the block sizes that cover a band in 1-4 equal
- * passes, the three register budgets, staged or not, where the shape fits and
+ * 32-512 threads in powers of two and the block sizes that cover a band in
+ * 1-4 equal passes, the three register budgets, staged or not, where the shape fits and
  * can be scheduled; one launch each,
  * then the best eight three more times.  Overwrites the partial sums (not the populations).
  * *evaluated and *seconds (nullable) report the candidates and wall time. */

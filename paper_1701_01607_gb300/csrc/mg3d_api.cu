@@ -897,21 +897,20 @@ int autotune_level(mg3d_handle *h, int k, int *evaluated) {
     std::vector<SweepShape> cands;
     for (int ng : ngs)
         for (int bands = 1; bands <= kMaxBands && bands <= L.ny; ++bands) {
-            // 128, 256, 512 threads and the block sizes that cover a band in
-            // 1-4 equal passes
+            // 32 to 512 threads in powers of two and the block sizes that
+            // cover a band in 1-4 equal passes
             const int band = ((L.ny + bands - 1) / bands) * L.nx;
-            std::vector<int> ths = {128, 256, 512};
+            std::vector<int> ths = {32, 64, 128, 256, 512};
             for (int passes = 1; passes <= 4; ++passes) {
                 const int th = ((band + passes - 1) / passes + 31) / 32 * 32;
-                if (th >= 64 && th <= kMaxSweepThreads &&
-                    std::find(ths.begin(), ths.end(), th) == ths.end())
+                if (th <= kMaxSweepThreads && std::find(ths.begin(), ths.end(), th) == ths.end())
                     ths.push_back(th);
             }
             for (int th : ths)
                 for (int lean = 0; lean < 3; ++lean)
                     for (int stage = 1; stage >= 0; --stage) {
                         if (lean == 2 && th > 256) continue;  // same as lean 0 above 256
-                        if (th > 128 && th / 2 >= band) continue;  // a smaller block covers it
+                        if (th > 32 && th / 2 >= band) continue;  // a smaller block covers it
                         SweepShape s;
                         if (shape_from_args(h, k, ng, bands, th, lean, stage, &s) != MG3D_OK)
                             continue;
