@@ -510,6 +510,61 @@ def run_batch(args):
             "max_rel_change_last_step": float(np.max(C))}
 
 
+def run_experiments(args):
+    """Synthetic analogues of the paper's restriction and grid-count tests
+    (Sec. 4.3, Sec. 4.4): FAS from the zero-radiation start until the true
+    error E_inf against a converged reference is <= 1e-3 (cap 60 cycles), for
+    full weighting, half weighting and injection on 2, 3 and 4 grids, on the
+    rough 64x64x129 box (log-normal sigma = 0.3) and on a smooth one
+    (sigma = 0, horizontally homogeneous); FP64.  Opt-in, --experiments."""
+    import torch
+
+    from paper_1701_01607_gb300 import mg3d as m
+    from paper_1701_01607_gb300 import synth
+    m.load(build_if_missing=True)
+    stream = torch.cuda.Stream()
+    restrictions = (("full", m.MG3D_RESTRICT_FULL), ("half", m.MG3D_RESTRICT_HALF),
+                    ("injection", m.MG3D_RESTRICT_INJECT))
+    out = {"metric": "V-cycles and seconds to E_inf <= 1e-3 (FAS, two-level atom, 64x64x129)",
+           "unit": "s", "higher_is_better": False, "n_gpus": 1, "dtype": "f64",
+           "data": "synthetic", "config": {"nu": NU, "target_e_inf": 1e-3, "cap_cycles": 60}}
+    for name, sigma in (("rough", 0.3), ("smooth", 0.0)):
+        atm, atom = synth.stratified_two_level(GRID[0], GRID[1], GRID[2], eps=1e-4,
+                                               sigma=sigma, seed=1)
+        ref = m.mg3d_create(atm, atom, n_grids=3, fs_prec=m.MG3D_PREC_F64, **NU)
+        m.mg3d_set_stream(ref, stream.cuda_stream)
+        m.mg3d_fas_solve(ref, 1e-9, 400, n_grids=3)
+        n_ref = m.mg3d_get_populations(ref, 3)
+        m.mg3d_destroy(ref)
+        rows = {}
+        for rname, rmode in restrictions:
+            for grids in (2, 3, 4):
+                h = m.mg3d_create(atm, atom, n_grids=grids, fs_prec=m.MG3D_PREC_F64,
+                                  restriction=rmode, **NU)
+                m.mg3d_set_stream(h, stream.cuda_stream)
+                secs, errs = 0.0, []
+                try:
+                    for cyc in range(60):
+                        t0 = time.perf_counter()
+                        m.mg3d_fas_vcycle(h, cyc == 0)
+                        secs += time.perf_counter() - t0
+                        n = m.mg3d_get_populations(h, grids)
+                        errs.append(float(np.max(np.abs(n - n_ref) / np.abs(n_ref))))
+                        if errs[-1] <= 1e-3:
+                            break
+                    status = "ok" if errs[-1] <= 1e-3 else "no"
+                except m.MG3DError as e:
+                    status = f"error: {e}"
+                finally:
+                    m.mg3d_destroy(h)
+                rows[f"{rname}_{grids}grids"] = {
+                    "reached": status, "cycles": len(errs), "seconds": round(secs, 3),
+                    "e_inf": [float(f"{x:.3g}") for x in errs[:8]] + (
+                        [float(f"{errs[-1]:.3g}")] if len(errs) > 8 else [])}
+        out[name] = rows
+    return out
+
+
 def run_chromosphere(args):
     """MALI, FAS and FMG from the zero-radiation start to C < 1e-3 on the
     128x128x257 chromosphere with the 6-level atom at 600 frequencies (FP32
@@ -589,6 +644,8 @@ def main():
                          '{"f64": {"1": [ng, bands, threads, lean, stage], ...}, "f32": {...}}')
     ap.add_argument("--profile-sweep", choices=["f64", "f32"],
                     help="only run a few finest-grid formal solutions (for ncu)")
+    ap.add_argument("--experiments", action="store_true",
+                    help="run the restriction / grid-count experiments instead")
     ap.add_argument("--chromosphere", action="store_true",
                     help="time MALI, FAS and FMG on the 128x128x257 6-level chromosphere instead")
     ap.add_argument("--batch", action="store_true",
@@ -611,6 +668,9 @@ def main():
         return
     if args.chromosphere:
         print(json.dumps(run_chromosphere(args)), flush=True)
+        return
+    if args.experiments:
+        print(json.dumps(run_experiments(args)), flush=True)
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
