@@ -179,8 +179,9 @@ int orc_formal_solution(long nx, long ny, long nz, double dx, double dy,
  *     sl = eta_t / chi   (the part of S the transition's new populations set)
  *     fl = chi_t / chi   (the transition's share of the opacity)
  * Returned per frequency and node (zeroed here):
- *     Jx = sum_r w_r (I - w_0 sl),     Ux = sum_r w_r (1 - w_0 fl).
- * Shapes: chi, S, sl, fl, Jx, Ux [nfreq][nz][ny][nx]; I_bottom, I_top
+ *     Jx = sum_r w_r (I - w_0 sl),     Ux = sum_r w_r (1 - w_0 fl),
+ * and, when Jm is not NULL, the mean intensity Jm = sum_r w_r I.
+ * Shapes: chi, S, sl, fl, Jx, Ux, Jm [nfreq][nz][ny][nx]; I_bottom, I_top
  * [nfreq][ny][nx].  Returns 0, or -1 on a bad argument.
  */
 int orc_formal_solution_nu(long nx, long ny, long nz, double dx, double dy,
@@ -188,13 +189,14 @@ int orc_formal_solution_nu(long nx, long ny, long nz, double dx, double dy,
                            const double *wray, long nfreq, const double *chi,
                            const double *S, const double *sl, const double *fl,
                            const double *I_bottom, const double *I_top,
-                           double *Jx, double *Ux)
+                           double *Jx, double *Ux, double *Jm)
 {
     if (nx < 1 || ny < 1 || nz < 2 || nrays < 1 || nfreq < 1 || dx <= 0 || dy <= 0)
         return -1;
     long nplane = nx * ny, nvox = nplane * nz;
     memset(Jx, 0, sizeof(double) * nvox * nfreq);
     memset(Ux, 0, sizeof(double) * nvox * nfreq);
+    if (Jm) memset(Jm, 0, sizeof(double) * nvox * nfreq);
     double *Iprev = malloc(sizeof(double) * nplane);
     double *Icur = malloc(sizeof(double) * nplane);
     double *W0 = malloc(sizeof(double) * nplane);
@@ -243,6 +245,7 @@ int orc_formal_solution_nu(long nx, long ny, long nz, double dx, double dy,
                     long v = k * nplane + q;
                     Jf[v] += wray[r] * (Icur[q] - W0[q] * slf[v]);
                     Uf[v] += wray[r] * (1.0 - W0[q] * flf[v]);
+                    if (Jm) Jm[f * nvox + v] += wray[r] * Icur[q];
                 }
                 double *t = Iprev;
                 Iprev = Icur;

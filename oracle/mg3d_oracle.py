@@ -88,7 +88,7 @@ def _load():
         lib.orc_formal_solution_nu.restype = ctypes.c_int
         lib.orc_formal_solution_nu.argtypes = [
             ctypes.c_long, ctypes.c_long, ctypes.c_long, ctypes.c_double, ctypes.c_double,
-            d, ctypes.c_long, d, d, ctypes.c_long, d, d, d, d, d, d, d, d]
+            d, ctypes.c_long, d, d, ctypes.c_long, d, d, d, d, d, d, d, d, d]
         _lib = lib
     return _lib
 
@@ -358,6 +358,7 @@ class TwoLevelProblem:
         r = f[k] - self.W(k, n[k])
         # coarse-grid equation (Eq. 9)
         n[k - 1] = self.restrict(k, n[k])
+        self.coarse_entry(k)
         n_before = n[k - 1].copy()
         f[k - 1] = self.restrict(k, r) + self.W(k - 1, n[k - 1])
         if k - 1 == 1:
@@ -375,6 +376,12 @@ class TwoLevelProblem:
         n[k] = n_new
         for _ in range(params["nu2"]):
             n[k], _ = self.mali_sweep(k, n[k], f[k])
+
+    def coarse_entry(self, k: int):
+        """Hook: a V-cycle enters grid k-1 from k (no state to move here)."""
+
+    def fmg_prolong(self, k: int):
+        """Hook: FMG moves the full approximation from grid k-1 to k."""
 
     def fas_cycle(self, n_fine, first: bool, params):
         L = self.n_grids
@@ -567,6 +574,7 @@ def fmg_solve(prob: TwoLevelProblem, tol: float, params, max_cycles: int = 1000,
     n_k = n1
     for k in range(2, L + 1):
         n_k = prob.prolong(k, n_k)
+        prob.fmg_prolong(k)
         if k < L:
             n = {k: n_k}
             f = {k: prob.default_rhs(k)}
@@ -601,6 +609,7 @@ class MLLevel:
     chi_c: np.ndarray
     c: np.ndarray       # [N, N, nz, ny, nx]
     saha: np.ndarray    # [N, nz, ny, nx]
+    sigma_c: np.ndarray  # background coherent scattering coefficient
 
     @property
     def shape(self):
@@ -609,15 +618,18 @@ class MLLevel:
 
 def coarsen_ml_level(lev: MLLevel) -> MLLevel:
     """Coarser grid (Sec. 4.1, 4.7): every second node, full weighting of every
-    atmospheric field (T, n_tot, background opacity, collisional rates, LTE
-    ratios)."""
+    atmospheric field (T, n_tot, background absorption and scattering,
+    collisional rates, LTE ratios)."""
     return MLLevel(lev.nx // 2, lev.ny // 2, (lev.nz + 1) // 2, 2 * lev.dx, 2 * lev.dy,
                    lev.z[::2].copy(), restrict_fw(lev.T), restrict_fw(lev.n_tot),
-                   restrict_fw(lev.chi_c), restrict_fw(lev.c), restrict_fw(lev.saha))
+                   restrict_fw(lev.chi_c), restrict_fw(lev.c), restrict_fw(lev.saha),
+                   restrict_fw(lev.sigma_c))
 
 
-def formal_solution_nu_raw(z, dx, dy, mu, wray, chi, S, sl, fl, I_bottom, I_top):
-    """Per-frequency angle sums Jx, Ux [nfreq, nz, ny, nx] (see fs_oracle.c)."""
+def formal_solution_nu_raw(z, dx, dy, mu, wray, chi, S, sl, fl, I_bottom, I_top,
+                           want_j: bool = False):
+    """Per-frequency angle sums Jx, Ux [nfreq, nz, ny, nx] (see fs_oracle.c),
+    and with want_j also the mean intensity J = sum_r w_r I."""
     chi = np.ascontiguousarray(chi, dtype=np.float64)
     nf, nz, ny, nx = chi.shape
     arrs = [np.ascontiguousarray(np.broadcast_to(a, chi.shape), dtype=np.float64)
@@ -626,15 +638,16 @@ def formal_solution_nu_raw(z, dx, dy, mu, wray, chi, S, sl, fl, I_bottom, I_top)
     It = np.ascontiguousarray(np.broadcast_to(I_top, (nf, ny, nx)), dtype=np.float64)
     Jx = np.empty(chi.shape)
     Ux = np.empty(chi.shape)
+    Jm = np.empty(chi.shape) if want_j else None
     rc = _load().orc_formal_solution_nu(nx, ny, nz, float(dx), float(dy),
                                         _ptr(np.ascontiguousarray(z, dtype=np.float64)),
                                         len(wray), _ptr(np.ascontiguousarray(mu)),
                                         _ptr(np.ascontiguousarray(wray)), nf, _ptr(chi),
                                         _ptr(arrs[0]), _ptr(arrs[1]), _ptr(arrs[2]), _ptr(Ib),
-                                        _ptr(It), _ptr(Jx), _ptr(Ux))
+                                        _ptr(It), _ptr(Jx), _ptr(Ux), _ptr(Jm))
     if rc != 0:
         raise RuntimeError("oracle formal solution failed")
-    return Jx, Ux
+    return (Jx, Ux, Jm) if want_j else (Jx, Ux)
 
 
 def trapezoid_weights(x):
@@ -662,6 +675,20 @@ class MultiLevelProblem(TwoLevelProblem):
     e = kappa y^-3 G E (rho y)^3 with y = nu/nu_threshold, G = n_l*/n_u* and
     E = exp(-theta_ref rho y / T).  B_nu = (rho y)^3 / (exp(theta_ref rho y/T) - 1)
     (rho y -> rho for lines: one Planck value per line).
+    With background coherent scattering (grey, isotropic, frequency-preserving
+    coefficient sigma_c beside the absorption chi_c; Sec. 4.8):
+        chi = chi_t + chi_c + sigma_c,
+        S = (eta_t + chi_c B_nu + sigma_c J_nu) / chi,
+    where J_nu is the mean intensity of the previous formal solution on the
+    same grid (Lambda-iteration for the background; the preconditioning below
+    treats only the transition's own emission as new).  Every formal solution
+    stores its J_nu as the grid's background field; the zero-radiation start
+    clears it and adds one Lambda-iteration; a V-cycle entering a coarser grid
+    restricts it by full weighting, and FMG prolongs it with the populations
+    (readings of Sec. 4.8, which restricts the field and runs one or two
+    Lambda-iterations per coarse grid: here the coarse grid's own formal
+    solutions, the first of them for the tau-correction, are those
+    iterations).
     Preconditioned radiative rates (Rybicki & Hummer 1992, diagonal operator),
     with Jx = sum_r w_r (I - w0 sl), Ux = sum_r w_r (1 - w0 fl) per frequency:
         R_lu = sum_nu qa Jx,   R_ul = sum_nu (qe Ux + qb Jx),
@@ -678,10 +705,13 @@ class MultiLevelProblem(TwoLevelProblem):
         self.N = atom.n_levels
         self.n_grids = n_grids
         self.mu, self.wray = a4_quadrature(quad_a)
+        sigma = getattr(atm, "sigma_c", None)
+        sigma = (np.zeros(np.shape(atm.T)) if sigma is None else np.asarray(sigma, float))
         fine = MLLevel(atm.nx, atm.ny, atm.nz, atm.dx, atm.dy, np.asarray(atm.z, float),
                        np.asarray(atm.T, float), np.asarray(atm.n_tot, float),
                        np.asarray(atm.chi_c, float), np.asarray(atm.c, float),
-                       np.asarray(atm.saha, float))
+                       np.asarray(atm.saha, float), sigma)
+        self.scatter = bool(np.any(sigma > 0))
         self.levels = {n_grids: fine}
         for k in range(n_grids - 1, 0, -1):
             self.levels[k] = coarsen_ml_level(self.levels[k + 1])
@@ -698,6 +728,9 @@ class MultiLevelProblem(TwoLevelProblem):
         self.fs_count = {k: 0 for k in self.levels}
         self.sweep_count = {k: 0 for k in self.levels}
         self.negatives = 0
+        nf = len(self.freqs)
+        # background radiation field per grid, [nfreq, nvox]
+        self.jbg = {k: np.zeros((nf, lev.nx * lev.ny * lev.nz)) for k, lev in self.levels.items()}
 
     def planck_rho(self, rho, T):
         return rho ** 3 / np.expm1(self.atom.theta_ref * rho / T)
@@ -713,6 +746,7 @@ class MultiLevelProblem(TwoLevelProblem):
         out = {key: np.empty((nf, nvox)) for key in ("chi", "S", "sl", "fl", "qa", "qb", "qe")}
         Ib = np.empty((nf, lev.nx * lev.ny))
         chi_c = lev.chi_c.reshape(-1)
+        sigma = lev.sigma_c.reshape(-1)
         nn = n.reshape(self.N, -1)
         # line profile normalisation per node and line
         d = np.sqrt(T / at.t_ref)
@@ -754,25 +788,52 @@ class MultiLevelProblem(TwoLevelProblem):
                 Ib[f] = self.planck_rho(ct.rho * xv, lev.T[0].reshape(-1))
             chi_t = nn[lo] * a - nn[up] * b
             eta_t = nn[up] * e
-            chi = chi_t + chi_c
+            chi = chi_t + chi_c + sigma
             out["chi"][f] = chi
-            out["S"][f] = (eta_t + chi_c * B) / chi
+            out["S"][f] = (eta_t + chi_c * B + sigma * self.jbg[k][f]) / chi
             out["sl"][f] = eta_t / chi
             out["fl"][f] = chi_t / chi
         return out, Ib
 
     def formal_solution(self, k: int, n):
-        """Per-frequency (Jx, Ux) [nfreq, nz, ny, nx] and the rate weights."""
+        """Per-frequency (Jx, Ux) [nfreq, nz, ny, nx] and the rate weights; with
+        background scattering the grid's background field becomes this
+        solution's mean intensity."""
         lev = self.levels[k]
         terms, Ib = self.transition_terms(k, n)
         nf = len(self.freqs)
         shp = (nf,) + lev.shape
-        Jx, Ux = formal_solution_nu_raw(lev.z, lev.dx, lev.dy, self.mu, self.wray,
-                                        terms["chi"].reshape(shp), terms["S"].reshape(shp),
-                                        terms["sl"].reshape(shp), terms["fl"].reshape(shp),
-                                        Ib.reshape((nf, lev.ny, lev.nx)), 0.0)
+        res = formal_solution_nu_raw(lev.z, lev.dx, lev.dy, self.mu, self.wray,
+                                     terms["chi"].reshape(shp), terms["S"].reshape(shp),
+                                     terms["sl"].reshape(shp), terms["fl"].reshape(shp),
+                                     Ib.reshape((nf, lev.ny, lev.nx)), 0.0,
+                                     want_j=self.scatter)
+        Jx, Ux = res[0], res[1]
+        if self.scatter:
+            self.jbg[k] = res[2].reshape(nf, -1)
         self.fs_count[k] += 1
         return Jx.reshape(nf, -1), Ux.reshape(nf, -1), terms
+
+    def lambda_iteration(self, k: int, n):
+        """One Lambda-iteration of the background field (Sec. 4.8): a formal
+        solution with the populations held."""
+        self.formal_solution(k, n)
+
+    def coarse_entry(self, k: int):
+        """Entering grid k-1 from k in a V-cycle: the background field of k,
+        full-weighted (Sec. 4.8)."""
+        if self.scatter:
+            fine = self.levels[k]
+            jf = self.jbg[k].reshape((-1,) + fine.shape)
+            self.jbg[k - 1] = restrict_fw(jf).reshape(jf.shape[0], -1)
+
+    def fmg_prolong(self, k: int):
+        """FMG moving the full approximation from grid k-1 to k: the
+        background field moves with it (trilinear)."""
+        if self.scatter:
+            coarse = self.levels[k - 1]
+            jc = self.jbg[k - 1].reshape((-1,) + coarse.shape)
+            self.jbg[k] = self.prolong(k, jc).reshape(jc.shape[0], -1)
 
     def rate_matrix_from(self, k: int, Jx, Ux, terms):
         """M [nvox, N, N] with W(n) = M n: row 0 particle conservation (Eq. 3),
@@ -816,7 +877,12 @@ class MultiLevelProblem(TwoLevelProblem):
         n_any = np.ones((self.N,) + lev.shape)   # weights do not depend on n
         terms, _ = self.transition_terms(k, n_any)
         M = self.rate_matrix_from(k, np.zeros((nf, nvox)), np.ones((nf, nvox)), terms)
-        return self.solve(M, self.default_rhs(k))
+        n = self.solve(M, self.default_rhs(k))
+        if self.scatter:
+            # background field from nothing: cleared, then one Lambda-iteration
+            self.jbg[k] = np.zeros((nf, nvox))
+            self.lambda_iteration(k, n)
+        return n
 
     def mali_sweep(self, k: int, n, f=None):
         if f is None:

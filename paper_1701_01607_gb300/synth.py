@@ -29,6 +29,8 @@ from __future__ import annotations
 import dataclasses
 import math
 
+from typing import Optional
+
 import numpy as np
 
 H_PLANCK = 6.62607015e-34
@@ -224,7 +226,8 @@ class MultiLevelAtmosphere:
     c[i, j] is the collisional rate from level i to level j (i != j);
     saha[i] is the LTE ratio n_i*/n_c* of bound level i to the continuum
     level (used by bound-free transitions); chi_c is the grey background
-    opacity, whose source function is the Planck function.
+    absorption, whose source function is the Planck function; sigma_c (None
+    for none) is a grey background coherent-scattering coefficient.
     """
     nx: int
     ny: int
@@ -237,6 +240,7 @@ class MultiLevelAtmosphere:
     chi_c: np.ndarray
     c: np.ndarray        # [N, N, nz, ny, nx]
     saha: np.ndarray     # [N, nz, ny, nx] (0 for levels without a continuum)
+    sigma_c: Optional[np.ndarray] = None
 
     @property
     def shape(self):
@@ -297,7 +301,8 @@ def chromosphere(nx: int, ny: int, nz: int, atom: MultiLevelAtom, seed: int = 2,
                  t_min: float = 4000.0, t_max: float = 10000.0, scale_heights: float = 8.0,
                  n_bottom: float = 1e4, sigma_t: float = 0.1, ionisation: float = 1e-3,
                  saha_scale: float = 10.0, c_strength: float = 1e-2, chi_c0: float = 1e-2,
-                 dx: float = 1.0, z=None, ground_collisions: float = 1.0) -> MultiLevelAtmosphere:
+                 dx: float = 1.0, z=None, ground_collisions: float = 1.0,
+                 scattering: float = 0.0) -> MultiLevelAtmosphere:
     """Chromosphere-like box: T rises from t_min to t_max with height (with
     seeded 3D perturbations of relative size sigma_t), the density falls by
     e^scale_heights from bottom to top; electron density = ionisation x
@@ -308,7 +313,8 @@ def chromosphere(nx: int, ny: int, nz: int, atom: MultiLevelAtom, seed: int = 2,
     start (ten times weaker collisions make the upper lines mase).
     ground_collisions scales the collisions out of the ground level only, so
     that the resonance lines can be made scattering-dominated while the upper
-    lines keep the collisions that prevent inversions."""
+    lines keep the collisions that prevent inversions.  scattering > 0 adds
+    grey background coherent scattering sigma_c = scattering x chi_c."""
     rng = np.random.default_rng(seed)
     if z is None:
         z = np.arange(nz, dtype=np.float64) * dx
@@ -341,5 +347,6 @@ def chromosphere(nx: int, ny: int, nz: int, atom: MultiLevelAtom, seed: int = 2,
                 up = down * (atom.g[j] / atom.g[i]) * np.exp(-(atom.theta[j] - atom.theta[i]) / T)
             c[j, i] = down
             c[i, j] = up
+    sigma_c = scattering * chi_c if scattering > 0 else None
     return MultiLevelAtmosphere(nx=nx, ny=ny, nz=nz, dx=dx, dy=dx, z=z, T=T, n_tot=n_tot,
-                                chi_c=chi_c, c=c, saha=saha)
+                                chi_c=chi_c, c=c, saha=saha, sigma_c=sigma_c)
