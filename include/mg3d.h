@@ -270,9 +270,19 @@ typedef struct {
     const double *z;        /* [nz] */
     const double *T;        /* [nz][ny][nx] */
     const double *n_tot;    /* [nz][ny][nx] */
-    const double *chi_c;    /* [nz][ny][nx] grey background opacity */
+    const double *chi_c;    /* [nz][ny][nx] grey background absorption (source B_nu) */
     const double *c;        /* [N][N][nz][ny][nx] collisional rate from i to j (i != j) */
     const double *saha;     /* [N][nz][ny][nx] LTE ratio (n_i/n_c) to the last level */
+    const double *sigma_c;  /* [nz][ny][nx] grey background coherent scattering, or NULL
+                               (Sec. 4.8): chi = chi_t + chi_c + sigma_c and
+                               S = (eta_t + chi_c B_nu + sigma_c J_nu)/chi, with J_nu the
+                               mean intensity of the previous formal solution on the same
+                               grid (a Lambda-iteration of the background; the MALI
+                               preconditioning treats only the transition's own emission
+                               as new).  The zero-radiation start clears the field and
+                               runs one Lambda-iteration; a V-cycle entering a coarser
+                               grid full-weights it; FMG prolongs it with the
+                               populations.  Not supported in batches. */
 } mg3d_ml_atmosphere;
 
 /* Create a solver for a multi-level atom; everything else as mg3d_create.

@@ -77,6 +77,8 @@ struct Level {
     double *saha = nullptr;      // [N][nvox] LTE ratios to the continuum
     void *mchi = nullptr, *mS = nullptr, *msl = nullptr, *mfl = nullptr;  // [nf][nvox]
     void *mib = nullptr;         // [nf][nplane] bottom intensity
+    double *sigma_c = nullptr;   // background coherent scattering [nvox] (FP64)
+    void *jbg = nullptr;         // background radiation field [nf][nvox] (FS precision)
     int ml_bands = 0, ml_rows = 0, ml_threads = 0;
     int ml_rpb = 12;             // rays of a hemisphere per block of the multi-level sweep
 };
@@ -105,6 +107,8 @@ struct mg3d_handle {
     // radiative sums per transition [ntrans][kAccTerms][finest nvox] (FP64)
     int ml_chunk = 0;
     int ml_chunk_req = 0;        // chunk asked for (0: automatic), kept across retuning
+    bool scatter = false;        // background coherent scattering present
+    void *ml_jm = nullptr;       // mean intensity per slot [slots][chunk][nvox] (scatter)
     int ml_slots = 2;            // most ray-group slots of any level (2 x 12 / ml_rpb)
     void *ml_jx = nullptr, *ml_ux = nullptr;
     double *ml_acc = nullptr;
@@ -328,7 +332,7 @@ int dalloc(P **p, size_t count) {
 void free_level(Level &L) {
     void *ptrs[] = {L.T,     L.n_tot, L.c_ul, L.c_lu, L.tz,   L.n,    L.f,   L.n_before,
                     L.r,     L.chi0,  L.S,    L.bbot, L.geom, L.chi_c, L.cmat, L.saha,
-                    L.mchi,  L.mS,    L.msl,  L.mfl,  L.mib};
+                    L.mchi,  L.mS,    L.msl,  L.mfl,  L.mib,  L.sigma_c, L.jbg};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     L = Level{};
@@ -381,7 +385,8 @@ int ml_chunk_fs(mg3d_handle *h, int k, int f0, int nc) {
     Level &L = h->lev[k];
     MlOpacityArgs oa{L.nvox, nc, h->N, h->prec, h->d_fi, h->theta_ref, h->t_ref,
                      L.n, L.T, L.chi_c, L.saha, L.mchi, L.mS, L.msl, L.mfl, f0,
-                     h->d_exp_tab, h->exp_l1, h->exp_l2};
+                     h->d_exp_tab, h->exp_l1, h->exp_l2,
+                     h->scatter ? L.sigma_c : nullptr, h->scatter ? L.jbg : nullptr};
     MG_TRY(launched(h, launch_ml_opacity(oa, h->stream), "multi-level opacity"));
     TimedLaunch tl{nullptr, nullptr, k};
     if (h->timing) {
@@ -397,14 +402,16 @@ int ml_chunk_fs(mg3d_handle *h, int k, int f0, int nc) {
                               (const double *)L.mchi, (const double *)L.mS,
                               (const double *)L.msl, (const double *)L.mfl,
                               (const double *)ib, L.geom, h->d_exp_tab, h->exp_l1, h->exp_l2,
-                              (double *)h->ml_jx, (double *)h->ml_ux, L.ml_rpb};
+                              (double *)h->ml_jx, (double *)h->ml_ux, L.ml_rpb,
+                              (double *)h->ml_jm};
         e = launch_ml_sweep_f64(a, L.ml_bands, L.ml_threads, h->stream);
     } else {
         MlSweepArgs<float> a{L.nx, L.ny, L.nz, nc, L.ml_rows,
                              (const float *)L.mchi, (const float *)L.mS,
                              (const float *)L.msl, (const float *)L.mfl,
                              (const float *)ib, L.geom, h->d_exp_tab, h->exp_l1, h->exp_l2,
-                             (float *)h->ml_jx, (float *)h->ml_ux, L.ml_rpb};
+                             (float *)h->ml_jx, (float *)h->ml_ux, L.ml_rpb,
+                             (float *)h->ml_jm};
         e = launch_ml_sweep_f32(a, L.ml_bands, L.ml_threads, h->stream);
     }
     MG_TRY(launched(h, e, "multi-level sweep"));
@@ -419,9 +426,11 @@ int ml_chunk_fs(mg3d_handle *h, int k, int f0, int nc) {
 // U = 1 for all frequencies, no formal solution).
 int ml_accumulate(mg3d_handle *h, int k, int f0, int nc, bool zero_rad) {
     Level &L = h->lev[k];
+    const bool bg = h->scatter && !zero_rad;   // the new mean intensity becomes the field
     MlAccumArgs a{L.nvox, f0, nc, h->ntrans, h->prec, h->d_fi, h->d_ti, h->theta_ref,
                   h->t_ref, L.T, h->ml_jx, h->ml_ux, 2 * (12 / L.ml_rpb), zero_rad ? 1 : 0,
-                  h->ml_acc, h->d_exp_tab, h->exp_l1, h->exp_l2};
+                  h->ml_acc, h->d_exp_tab, h->exp_l1, h->exp_l2, bg ? h->ml_jm : nullptr,
+                  bg ? L.jbg : nullptr};
     return launched(h, launch_ml_accum(a, h->stream), "radiative sums");
 }
 
@@ -564,6 +573,15 @@ int zero_radiation(mg3d_handle *h, int k) {
         MlRateArgs a = ml_rate_args(h, k, kRateSolve);
         a.scal = nullptr;
         MG_TRY(launched(h, launch_ml_rates(a, h->stream), "zero radiation"));
+        if (h->scatter) {
+            // background field from nothing: cleared, then one Lambda-iteration
+            // (a formal solution with the populations held, Sec. 4.8)
+            Level &L = h->lev[k];
+            MG_CUDA(cudaMemsetAsync(L.jbg, 0,
+                                    (size_t)h->nfreq_ml * L.nvox * elem_size(h->prec),
+                                    h->stream));
+            MG_TRY(ml_formal_solution(h, k));
+        }
         return MG3D_OK;
     }
     RateArgs a = rate_args(h, k, kRateSolve);
@@ -603,6 +621,10 @@ int vcycle(mg3d_handle *h, int k, bool first) {
                     "restrict n"));
     MG_CUDA(cudaMemcpyAsync(C.n_before, C.n, (size_t)h->N * C.nvox * sizeof(double),
                             cudaMemcpyDeviceToDevice, h->stream));
+    if (h->kind == 1 && h->scatter)   // background field, full-weighted (Sec. 4.8)
+        MG_TRY(launched(h, launch_restrict_prec(h->prec, h->nfreq_ml, F.nx, F.ny, F.nz, F.jbg,
+                                                C.jbg, h->stream),
+                        "restrict background field"));
     MG_TRY(launched(h, launch_restrict(h->N, F.nx, F.ny, F.nz, F.r, C.f, h->stream,
                                        h->params.restriction),
                     "restrict r"));
@@ -1097,7 +1119,7 @@ void trapezoid_grid(double a, double b, int n, std::vector<double> &x, std::vect
 // and the angle sums of every ray-group slot on the finest.
 size_t ml_bytes_per_freq(const mg3d_handle *h) {
     const size_t es = elem_size(h->prec);
-    size_t b = 2 * (size_t)h->ml_slots * h->lev[h->L].nvox * es;
+    size_t b = (h->scatter ? 3 : 2) * (size_t)h->ml_slots * h->lev[h->L].nvox * es;
     for (int k = 1; k <= h->L; ++k) b += 4 * (size_t)h->lev[k].nvox * es;
     return b;
 }
@@ -1128,7 +1150,8 @@ int alloc_ml_chunks(mg3d_handle *h, int chunk) {
     }
     if (h->ml_jx) cudaFree(h->ml_jx);
     if (h->ml_ux) cudaFree(h->ml_ux);
-    h->ml_jx = h->ml_ux = nullptr;
+    if (h->ml_jm) cudaFree(h->ml_jm);
+    h->ml_jx = h->ml_ux = h->ml_jm = nullptr;
     h->ml_chunk = 0;
     for (int k = 1; k <= h->L; ++k) {
         Level &L = h->lev[k];
@@ -1138,6 +1161,7 @@ int alloc_ml_chunks(mg3d_handle *h, int chunk) {
     const size_t nv = h->lev[h->L].nvox;
     MG_TRY(dev_alloc(&h->ml_jx, (size_t)h->ml_slots * chunk * nv * es));
     MG_TRY(dev_alloc(&h->ml_ux, (size_t)h->ml_slots * chunk * nv * es));
+    if (h->scatter) MG_TRY(dev_alloc(&h->ml_jm, (size_t)h->ml_slots * chunk * nv * es));
     h->ml_chunk = chunk;
     return MG3D_OK;
 }
@@ -1444,6 +1468,25 @@ int create_ml_impl(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
         exp_neg_constants(tab, &h->exp_l1, &h->exp_l2);
         MG_TRY(dalloc(&h->d_exp_tab, kExpTab));
         MG_CUDA(cudaMemcpy(h->d_exp_tab, tab, sizeof(tab), cudaMemcpyHostToDevice));
+    }
+    if (atm->sigma_c) {
+        for (long i = 0; i < F.nvox && !h->scatter; ++i) h->scatter = atm->sigma_c[i] > 0.0;
+        for (long i = 0; i < F.nvox; ++i)
+            if (!(atm->sigma_c[i] >= 0.0)) return fail(MG3D_E_ARG, "negative sigma_c");
+    }
+    if (h->scatter) {
+        for (int k = 1; k <= h->L; ++k) {
+            Level &L = h->lev[k];
+            MG_TRY(dalloc(&L.sigma_c, L.nvox));
+            MG_TRY(dev_alloc(&L.jbg, (size_t)nf * L.nvox * elem_size(h->prec)));
+            MG_CUDA(cudaMemset(L.jbg, 0, (size_t)nf * L.nvox * elem_size(h->prec)));
+        }
+        MG_CUDA(cudaMemcpy(F.sigma_c, atm->sigma_c, F.nvox * 8, cudaMemcpyHostToDevice));
+        for (int k = h->L; k >= 2; --k)   // full weighting, like the atmosphere (Sec. 4.7)
+            MG_TRY(launched(h, launch_restrict(1, h->lev[k].nx, h->lev[k].ny, h->lev[k].nz,
+                                               h->lev[k].sigma_c, h->lev[k - 1].sigma_c,
+                                               h->stream),
+                            "restrict scattering"));
     }
     MG_TRY(dalloc(&h->ml_acc, (size_t)h->ntrans * kAccTerms * F.nvox));
     if (params && params->ml_chunk < 0) return fail(MG3D_E_ARG, "negative ml_chunk");
@@ -2004,6 +2047,7 @@ int mg3d_formal_solve_ml(mg3d_handle *h, int level, double *jx_host, double *ux_
     for (int f0 = 0; f0 < h->nfreq_ml; f0 += h->ml_chunk) {
         const int nc = std::min(h->ml_chunk, h->nfreq_ml - f0);
         MG_TRY(ml_chunk_fs(h, level, f0, nc));
+        if (h->scatter) MG_TRY(ml_accumulate(h, level, f0, nc, false));   // background field
         MG_CUDA(cudaStreamSynchronize(h->stream));
         // the chunk's per-frequency sums of every ray-group slot, added on the
         // host in slot order
@@ -2099,6 +2143,8 @@ int mg3d_batch_create(int n, mg3d_handle *const *members, mg3d_batch **out) {
     if (n < 1 || !members) return fail(MG3D_E_ARG, "empty batch");
     for (int i = 0; i < n; ++i) {
         if (!members[i]) return fail(MG3D_E_ARG, "null member");
+        if (members[i]->scatter)
+            return fail(MG3D_E_ARG, "batches do not take background scattering");
         for (int j = 0; j < i; ++j)
             if (members[j] == members[i]) return fail(MG3D_E_ARG, "member listed twice");
     }
@@ -2271,7 +2317,8 @@ int mg3d_destroy(mg3d_handle *h) {
     drop_graphs(h);
     for (int k = 0; k <= MG3D_MAX_GRIDS; ++k) free_level(h->lev[k]);
     void *ptrs[] = {h->d_ftab, h->d_exp_tab, h->pj, h->pu, h->scal,
-                    h->scratch, h->d_fi, h->d_ti, h->ml_jx, h->ml_ux, h->ml_acc};
+                    h->scratch, h->d_fi, h->d_ti, h->ml_jx, h->ml_ux, h->ml_acc,
+                    h->ml_jm};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &t : h->timed) {
@@ -2426,6 +2473,10 @@ int mg3d_fmg_solve(mg3d_handle *h, double tol, int max_cycles, mg3d_stats *stats
         Level &Ck = h->lev[k - 1];
         MG_TRY(launched(h, launch_prolong(h->N, Ck.nx, Ck.ny, Ck.nz, Fk.tz, Ck.n, Fk.n, h->stream),
                         "prolong full approximation"));
+        if (h->kind == 1 && h->scatter)
+            MG_TRY(launched(h, launch_prolong_prec(h->prec, h->nfreq_ml, Ck.nx, Ck.ny, Ck.nz,
+                                                   Fk.tz, Ck.jbg, Fk.jbg, h->stream),
+                            "prolong background field"));
         Fk.f_default = true;
         if (k < h->L) {
             MG_TRY(reset_scalars(h));

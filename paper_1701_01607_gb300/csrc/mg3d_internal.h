@@ -110,6 +110,13 @@ cudaError_t launch_collisions_up(long nvox, double g_ratio, double theta, const 
 // mode: 0 full weighting, 1 half weighting, 2 injection
 cudaError_t launch_restrict(int ncomp, int nxf, int nyf, int nzf, const double *fine,
                             double *coarse, cudaStream_t st, int mode = 0);
+// The same operators (full weighting, trilinear) on arrays of the
+// formal-solution precision (prec 0 FP64, 1 FP32), accumulated in FP64.
+cudaError_t launch_restrict_prec(int prec, int ncomp, int nxf, int nyf, int nzf,
+                                 const void *fine, void *coarse, cudaStream_t st);
+cudaError_t launch_prolong_prec(int prec, int ncomp, int nxc, int nyc, int nzc,
+                                const double *tz, const void *coarse, void *fine,
+                                cudaStream_t st);
 cudaError_t launch_prolong(int ncomp, int nxc, int nyc, int nzc, const double *tz,
                            const double *coarse, double *fine, cudaStream_t st);
 cudaError_t launch_prolong_correct(int ncomp, int nxc, int nyc, int nzc, const double *tz,
@@ -152,6 +159,7 @@ struct MlSweepArgs {
     double exp_l1, exp_l2;
     T *jx, *ux;                   // [2 * 12 / rpb slots][nfreq][nvox]
     int rpb;                      // rays per block: 12, 6, 4, 3, 2 or 1 of a hemisphere
+    T *jm;                        // mean intensity sum_r w_r I per slot, or null
 };
 
 // Opacity of the chunk of frequencies f0 .. f0+nfreq-1, written at the
@@ -166,6 +174,8 @@ struct MlOpacityArgs {
     int f0;
     const double *exp_tab;         // FP64 exp table of the sweep
     double exp_l1, exp_l2;
+    const double *sigma_c;         // background scattering [nvox], or null
+    const void *jbg;               // background field [n_freq][nvox] (FS precision)
 };
 
 // Radiative sums per transition and node, [n_trans][3][nvox] in FP64:
@@ -187,6 +197,8 @@ struct MlAccumArgs {
     double *acc;
     const double *exp_tab;         // FP64 exp table of the sweep
     double exp_l1, exp_l2;
+    const void *jm;                // mean intensity per slot [nslots][nfreq][nvox], or null
+    void *jbg;                     // background field [n_freq][nvox] written from jm
 };
 
 struct MlRateArgs {

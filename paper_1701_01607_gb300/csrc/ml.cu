@@ -112,11 +112,21 @@ __global__ void ml_opacity_kernel(const MlOpacityArgs a) {
                 B = (T)planck_rho(ry, a.theta_ref, Tg);
                 rho_b = -1.0;
             }
-            const T chi = chi_t + (T)cc;
-            const T inv = T(1) / chi;
             const long i = (long)fl * nvox + v;
+            T chi, src;
+            if (a.sigma_c) {
+                // background coherent scattering with the previous mean intensity
+                const T sg = (T)a.sigma_c[v];
+                const T jb = ((const T *)a.jbg)[(long)(a.f0 + fl) * nvox + v];
+                chi = chi_t + (T)cc + sg;
+                src = eta_t + (T)cc * B + sg * jb;
+            } else {
+                chi = chi_t + (T)cc;
+                src = eta_t + (T)cc * B;
+            }
+            const T inv = T(1) / chi;
             ((T *)a.chi)[i] = chi;
-            ((T *)a.S)[i] = (eta_t + (T)cc * B) * inv;
+            ((T *)a.S)[i] = src * inv;
             ((T *)a.sl)[i] = eta_t * inv;
             ((T *)a.fl)[i] = chi_t * inv;
         }
@@ -161,6 +171,7 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
     const T *__restrict__ flf = a.fl + (long)f * nvox;
     T *__restrict__ jxo = a.jx + ((long)slot * a.nfreq + f) * nvox;
     T *__restrict__ uxo = a.ux + ((long)slot * a.nfreq + f) * nvox;
+    T *__restrict__ jmo = a.jm ? a.jm + ((long)slot * a.nfreq + f) * nvox : nullptr;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf = reinterpret_cast<T *>(smem_raw);
@@ -199,6 +210,7 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
                 const long v = (long)k * nplane + (long)y * nx + x;
                 jxo[v] = T(rpb) * wray * Ib;
                 uxo[v] = T(rpb) * wray;
+                if (jmo) jmo[v] = T(rpb) * wray * Ib;
             }
         } else {
             const T *prev = buf + ((t - 1) & 1) * bufstride;
@@ -261,6 +273,7 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
                 }
                 jxo[v] = wray * (sum_i - sl * sum_w0);
                 uxo[v] = wray * (T(rpb) - fl * sum_w0);
+                if (jmo) jmo[v] = wray * sum_i;
             }
         }
         cluster.sync();
@@ -434,6 +447,16 @@ __global__ void ml_accum_kernel(const MlAccumArgs a) {
             acc[0] += s0;
             acc[nvox] += s1;
             acc[2 * nvox] += s2;
+        }
+        // background field of the chunk's frequencies: the new mean intensity
+        if (a.jbg && !a.zero_radiation) {
+            const TP *__restrict__ jm = (const TP *)a.jm;
+            for (int fl = 0; fl < a.nfreq; ++fl) {
+                const long i = (long)fl * nvox + v;
+                double J = (double)jm[i];
+                for (int s = 1; s < a.nslots; ++s) J += (double)jm[(long)s * hstride + i];
+                ((TP *)a.jbg)[(long)(a.f0 + fl) * nvox + v] = (TP)J;
+            }
         }
     }
 }

@@ -159,8 +159,9 @@ cudaError_t launch_collisions_up(long nvox, double g_ratio, double theta, const 
 // mode 0: full weighting (27 nodes), 1: half weighting (centre 1/2, six axis
 // neighbours 1/12 each; on the boundary planes centre 1/2 and four in-plane
 // neighbours 1/8 each), 2: injection.
+template <typename V>
 __global__ void restrict_kernel(int ncomp, int nxf, int nyf, int nzf, int mode,
-                                const double *__restrict__ fine, double *__restrict__ coarse) {
+                                const V *__restrict__ fine, V *__restrict__ coarse) {
     const int nxc = nxf / 2, nyc = nyf / 2, nzc = (nzf + 1) / 2;
     const long nvc = (long)nxc * nyc * nzc, nvf = (long)nxf * nyf * nzf;
     for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < nvc;
@@ -178,20 +179,23 @@ __global__ void restrict_kernel(int ncomp, int nxf, int nyf, int nzf, int mode,
         }
         const long plane = (long)nxf * nyf;
         for (int comp = 0; comp < ncomp; ++comp) {
-            const double *F = fine + comp * nvf;
+            const V *F = fine + comp * nvf;
             double acc = 0.0;
             if (mode == 2) {
                 acc = F[(long)(2 * K) * plane + (long)ys[1] * nxf + xs[1]];
             } else if (mode == 1) {
-                const double *P = F + (long)(2 * K) * plane;
+                const V *P = F + (long)(2 * K) * plane;
                 const double ctr = P[(long)ys[1] * nxf + xs[1]];
-                const double inplane = P[(long)ys[1] * nxf + xs[0]] + P[(long)ys[1] * nxf + xs[2]] +
-                                       P[(long)ys[0] * nxf + xs[1]] + P[(long)ys[2] * nxf + xs[1]];
+                const double inplane = (double)P[(long)ys[1] * nxf + xs[0]] +
+                                       (double)P[(long)ys[1] * nxf + xs[2]] +
+                                       (double)P[(long)ys[0] * nxf + xs[1]] +
+                                       (double)P[(long)ys[2] * nxf + xs[1]];
                 if (boundary) {
                     acc = 0.5 * ctr + inplane / 8.0;
                 } else {
-                    const double zpair = F[(long)(2 * K - 1) * plane + (long)ys[1] * nxf + xs[1]] +
-                                         F[(long)(2 * K + 1) * plane + (long)ys[1] * nxf + xs[1]];
+                    const double zpair =
+                        (double)F[(long)(2 * K - 1) * plane + (long)ys[1] * nxf + xs[1]] +
+                        (double)F[(long)(2 * K + 1) * plane + (long)ys[1] * nxf + xs[1]];
                     acc = 0.5 * ctr + (inplane + zpair) / 12.0;
                 }
             } else {
@@ -206,15 +210,16 @@ __global__ void restrict_kernel(int ncomp, int nxf, int nyf, int nzf, int mode,
                         wz = wh[dz];
                         kf = 2 * K + dz - 1;
                     }
-                    const double *P = F + (long)kf * plane;
+                    const V *P = F + (long)kf * plane;
                     for (int dy = 0; dy < 3; ++dy) {
-                        const double *R = P + (long)ys[dy] * nxf;
+                        const V *R = P + (long)ys[dy] * nxf;
                         const double wy = wz * wh[dy];
-                        acc += wy * (0.25 * R[xs[0]] + 0.5 * R[xs[1]] + 0.25 * R[xs[2]]);
+                        acc += wy * (0.25 * (double)R[xs[0]] + 0.5 * (double)R[xs[1]] +
+                                     0.25 * (double)R[xs[2]]);
                     }
                 }
             }
-            coarse[comp * nvc + c] = acc;
+            coarse[comp * nvc + c] = (V)acc;
         }
     }
 }
@@ -222,8 +227,20 @@ __global__ void restrict_kernel(int ncomp, int nxf, int nyf, int nzf, int mode,
 cudaError_t launch_restrict(int ncomp, int nxf, int nyf, int nzf, const double *fine,
                             double *coarse, cudaStream_t st, int mode) {
     const long nvc = (long)(nxf / 2) * (nyf / 2) * ((nzf + 1) / 2);
-    restrict_kernel<<<grid_for(nvc, 256), 256, 0, st>>>(ncomp, nxf, nyf, nzf, mode, fine,
-                                                          coarse);
+    restrict_kernel<double><<<grid_for(nvc, 256), 256, 0, st>>>(ncomp, nxf, nyf, nzf, mode,
+                                                                  fine, coarse);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_restrict_prec(int prec, int ncomp, int nxf, int nyf, int nzf,
+                                 const void *fine, void *coarse, cudaStream_t st) {
+    const long nvc = (long)(nxf / 2) * (nyf / 2) * ((nzf + 1) / 2);
+    if (prec == 0)
+        restrict_kernel<double><<<grid_for(nvc, 256), 256, 0, st>>>(
+            ncomp, nxf, nyf, nzf, 0, (const double *)fine, (double *)coarse);
+    else
+        restrict_kernel<float><<<grid_for(nvc, 256), 256, 0, st>>>(
+            ncomp, nxf, nyf, nzf, 0, (const float *)fine, (float *)coarse);
     return cudaGetLastError();
 }
 
@@ -261,9 +278,10 @@ __device__ __forceinline__ void corners(long f, int nxc, int nyc, int nzc,
             }
 }
 
+template <typename V>
 __global__ void prolong_kernel(int ncomp, int nxc, int nyc, int nzc,
-                               const double *__restrict__ tz, const double *__restrict__ coarse,
-                               double *__restrict__ fine) {
+                               const double *__restrict__ tz, const V *__restrict__ coarse,
+                               V *__restrict__ fine) {
     const long nvf = (long)(2 * nxc) * (2 * nyc) * (2 * nzc - 1);
     const long nvc = (long)nxc * nyc * nzc;
     for (long f = blockIdx.x * (long)blockDim.x + threadIdx.x; f < nvf;
@@ -271,10 +289,10 @@ __global__ void prolong_kernel(int ncomp, int nxc, int nyc, int nzc,
         Corners cr;
         corners(f, nxc, nyc, nzc, tz, cr);
         for (int comp = 0; comp < ncomp; ++comp) {
-            const double *C = coarse + comp * nvc;
+            const V *C = coarse + comp * nvc;
             double acc = 0.0;
-            for (int c = 0; c < 8; ++c) acc += cr.w[c] * C[cr.idx[c]];
-            fine[comp * nvf + f] = acc;
+            for (int c = 0; c < 8; ++c) acc += cr.w[c] * (double)C[cr.idx[c]];
+            fine[comp * nvf + f] = (V)acc;
         }
     }
 }
@@ -318,7 +336,21 @@ __global__ void __launch_bounds__(256) prolong_correct_kernel(
 cudaError_t launch_prolong(int ncomp, int nxc, int nyc, int nzc, const double *tz,
                            const double *coarse, double *fine, cudaStream_t st) {
     const long nvf = (long)(2 * nxc) * (2 * nyc) * (2 * nzc - 1);
-    prolong_kernel<<<grid_for(nvf, 256), 256, 0, st>>>(ncomp, nxc, nyc, nzc, tz, coarse, fine);
+    prolong_kernel<double><<<grid_for(nvf, 256), 256, 0, st>>>(ncomp, nxc, nyc, nzc, tz, coarse,
+                                                                 fine);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_prec(int prec, int ncomp, int nxc, int nyc, int nzc,
+                                const double *tz, const void *coarse, void *fine,
+                                cudaStream_t st) {
+    const long nvf = (long)(2 * nxc) * (2 * nyc) * (2 * nzc - 1);
+    if (prec == 0)
+        prolong_kernel<double><<<grid_for(nvf, 256), 256, 0, st>>>(
+            ncomp, nxc, nyc, nzc, tz, (const double *)coarse, (double *)fine);
+    else
+        prolong_kernel<float><<<grid_for(nvf, 256), 256, 0, st>>>(
+            ncomp, nxc, nyc, nzc, tz, (const float *)coarse, (float *)fine);
     return cudaGetLastError();
 }
 

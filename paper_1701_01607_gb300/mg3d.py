@@ -79,7 +79,7 @@ class mg3d_ml_atom(ctypes.Structure):
 class mg3d_ml_atmosphere(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("z", _D), ("T", _D),
-                ("n_tot", _D), ("chi_c", _D), ("c", _D), ("saha", _D)]
+                ("n_tot", _D), ("chi_c", _D), ("c", _D), ("saha", _D), ("sigma_c", _D)]
 
 
 class mg3d_stats(ctypes.Structure):
@@ -242,9 +242,11 @@ def mg3d_create_ml(atm, atom, quad_a: float = 0.0, n_grids: int = 1, nu_fmg: int
         keep[name] = np.ascontiguousarray(a, dtype=np.float64)
         return _dptr(keep[name])
 
+    sigma = getattr(atm, "sigma_c", None)
     a = mg3d_ml_atmosphere(atm.nx, atm.ny, atm.nz, atm.dx, atm.dy, arr("z", atm.z),
                            arr("T", atm.T), arr("n", atm.n_tot), arr("cc", atm.chi_c),
-                           arr("c", atm.c), arr("s", atm.saha))
+                           arr("c", atm.c), arr("s", atm.saha),
+                           arr("sg", sigma) if sigma is not None else None)
     lines = (mg3d_line * max(1, len(atom.lines)))(
         *[mg3d_line(l.lower, l.upper, l.rho, l.a_ul, l.kappa, l.n_freq, l.x_max)
           for l in atom.lines])

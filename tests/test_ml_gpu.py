@@ -303,3 +303,105 @@ def test_ml_autotuned_shapes_keep_parity():
         assert rel(m.mg3d_get_populations(h, 2), n) < 1e-10
     finally:
         m.mg3d_destroy(h)
+
+
+# -------------------------------------------- background coherent scattering
+
+def scat_box(nx=8, ny=8, nz=17, seed=2):
+    atom = synth.hydrogen_like_atom(line_freq=7, cont_freq=4, seed=seed)
+    atm = synth.chromosphere(nx, ny, nz, atom, seed=seed, scattering=2.0)
+    return atm, atom
+
+
+def test_ml_scattering_formal_solution_fp64():
+    """After the zero-radiation start (with its Lambda-iteration) the
+    per-frequency angle sums with a scattering background follow the oracle."""
+    atm, atom = scat_box()
+    h = m.mg3d_create_ml(atm, atom, n_grids=1)
+    try:
+        jx, ux = m.mg3d_formal_solve_ml(h, 1)
+    finally:
+        m.mg3d_destroy(h)
+    p = O.MultiLevelProblem(atm, atom)
+    n0 = p.zero_radiation(1)
+    Jo, Uo, _ = p.formal_solution(1, n0)
+    for got, ref in ((jx, Jo), (ux, Uo)):
+        err, where = per_frequency_error(got, ref, p)
+        assert err < TOL_FS_ML, (err, where)
+
+
+@pytest.mark.parametrize("chunk,rpb", [(0, 12), (7, 12), (0, 3)])
+def test_ml_scattering_mali_fp64(chunk, rpb):
+    """MALI sweeps with the background field lagged one formal solution, in
+    one chunk, in chunks that split transitions, and with three-ray blocks."""
+    atm, atom = scat_box()
+    h = m.mg3d_create_ml(atm, atom, n_grids=1, ml_chunk=chunk)
+    if rpb != 12:
+        m.mg3d_set_ml_shape(h, 1, 2, rpb, 64)
+    p = O.MultiLevelProblem(atm, atom)
+    n = p.zero_radiation(1)
+    try:
+        for _ in range(4):
+            c_gpu = m.mg3d_mali_sweep(h, 1, 1)
+            n, c_orc = p.mali_sweep(1, n)
+            assert abs(c_gpu - c_orc) <= 1e-8 * c_orc
+        assert rel(m.mg3d_get_populations(h, 1), n) < 1e-10
+    finally:
+        m.mg3d_destroy(h)
+
+
+@pytest.mark.parametrize("n_grids", [2, 3])
+def test_ml_scattering_fas_vcycles_fp64(n_grids):
+    """V-cycles restrict the background field on each coarse-grid entry."""
+    atm, atom = scat_box(16, 16, 33)
+    h = m.mg3d_create_ml(atm, atom, n_grids=n_grids, **ML_PARAMS)
+    p = O.MultiLevelProblem(atm, atom, n_grids=n_grids)
+    n = p.zero_radiation(n_grids)
+    try:
+        for cyc in range(2):
+            c_gpu = m.mg3d_fas_vcycle(h, cyc == 0)
+            n, c_orc = p.fas_cycle(n, cyc == 0, ML_PARAMS)
+            if c_orc > 1e-8:
+                assert abs(c_gpu - c_orc) <= 1e-6 * c_orc
+            assert rel(m.mg3d_get_populations(h, n_grids), n) < 1e-10
+    finally:
+        m.mg3d_destroy(h)
+
+
+def test_ml_scattering_fmg_fp64():
+    """FMG prolongs the background field with the populations."""
+    atm, atom = scat_box(16, 16, 33)
+    h = m.mg3d_create_ml(atm, atom, n_grids=2, **ML_PARAMS)
+    try:
+        st = m.mg3d_fmg_solve(h, 1e-6, n_grids=2)
+        n_gpu = m.mg3d_get_populations(h, 2)
+    finally:
+        m.mg3d_destroy(h)
+    p = O.MultiLevelProblem(atm, atom, n_grids=2)
+    n_o, cyc = O.fmg_solve(p, 1e-6, ML_PARAMS)
+    assert st["iterations"] == cyc
+    assert rel(n_gpu, n_o) < 1e-10
+
+
+def test_ml_scattering_fp32():
+    atm, atom = scat_box()
+    h = m.mg3d_create_ml(atm, atom, n_grids=1, fs_prec=m.MG3D_PREC_F32)
+    p = O.MultiLevelProblem(atm, atom)
+    n = p.zero_radiation(1)
+    try:
+        m.mg3d_mali_sweep(h, 1, 6)
+        for _ in range(6):
+            n, _ = p.mali_sweep(1, n)
+        assert rel(m.mg3d_get_populations(h, 1), n) < 1e-4
+    finally:
+        m.mg3d_destroy(h)
+
+
+def test_ml_scattering_not_in_batches():
+    atm, atom = scat_box()
+    h = m.mg3d_create_ml(atm, atom, n_grids=1)
+    try:
+        with pytest.raises(m.MG3DError, match="scattering"):
+            m.mg3d_batch_create([h])
+    finally:
+        m.mg3d_destroy(h)
