@@ -7,12 +7,20 @@
  *
  * What it computes (Sec. 3, "Computational setup"; Eq. 1): the transfer
  * equation dI/dtau = S - I is integrated cell by cell with the short
- * characteristics method of Kunasz & Auer (1988) with linear interpolation.
+ * characteristics method of Kunasz & Auer (1988).
  * For a node on plane k and a ray with direction (mux, muy, muz) the short
  * characteristic runs back to the neighbouring plane upwind (k-1 for muz > 0,
- * k+1 for muz < 0).  Where it crosses that plane, I, chi and S are taken by
- * bilinear interpolation between the four surrounding nodes, periodic in x and
- * y (Sec. 4.2).  Along the characteristic of length s = |dz|/|muz| the optical
+ * k+1 for muz < 0).  Where it crosses that plane, I, chi and S are
+ * interpolated, periodic in x and y (Sec. 4.2), with one of the two schemes
+ * Sec. 3 names:
+ *   interp = 0: linear -- bilinear between the four surrounding nodes;
+ *   interp = 1: Hermite spline -- monotone cubic Hermite interpolation
+ *     (Auer 2003) along x on the four rows around the crossing point, then
+ *     along y through the four results (a 4 x 4 stencil).  The slope at a
+ *     node is the harmonic mean of the two neighbouring secants when they
+ *     have the same sign and zero otherwise (Fritsch & Butland 1984), so the
+ *     interpolant stays between the two nodes of each interval.
+ * Along the characteristic of length s = |dz|/|muz| the optical
  * depth is the trapezoid dtau = (chi_up + chi_0) s / 2 and S is linear in tau,
  * which gives
  *     I_0 = I_up exp(-dtau) + w_up S_up + w_0 S_0,
@@ -76,13 +84,62 @@ static double bilinear(const double *plane, long nx, long ny, double xu, double 
          + (1.0 - tx) * ty * f01 + tx * ty * f11;
 }
 
+/* Monotone slope at a node of a uniform periodic row from its two secants
+ * (in units of one cell): the harmonic mean 2 a b / (a + b) when a and b have
+ * the same strict sign, else zero. */
+static double harmonic_slope(double a, double b)
+{
+    if ((a > 0.0 && b > 0.0) || (a < 0.0 && b < 0.0))
+        return 2.0 * a * b / (a + b);
+    return 0.0;
+}
+
+/* Cubic Hermite on [0, 1] from end values p0, p1 and end slopes d0, d1 (per
+ * unit of t), at t. */
+static double hermite01(double p0, double p1, double d0, double d1, double t)
+{
+    double t2 = t * t, t3 = t2 * t;
+    return (2.0 * t3 - 3.0 * t2 + 1.0) * p0 + (t3 - 2.0 * t2 + t) * d0
+         + (-2.0 * t3 + 3.0 * t2) * p1 + (t3 - t2) * d1;
+}
+
+/* Monotone cubic Hermite through q[0..3] (uniform spacing) on the interval
+ * between q[1] and q[2], at fraction t. */
+static double hermite4(const double *q, double t)
+{
+    double d1 = harmonic_slope(q[1] - q[0], q[2] - q[1]);
+    double d2 = harmonic_slope(q[2] - q[1], q[3] - q[2]);
+    return hermite01(q[1], q[2], d1, d2, t);
+}
+
+static double bicubic_hermite(const double *plane, long nx, long ny, double xu, double yu)
+{
+    double fx0 = floor(xu), fy0 = floor(yu);
+    double tx = xu - fx0, ty = yu - fy0;
+    double col[4], row[4];
+    for (int j = 0; j < 4; ++j) {
+        long y = periodic((long)fy0 - 1 + j, ny);
+        for (int i = 0; i < 4; ++i)
+            row[i] = plane[y * nx + periodic((long)fx0 - 1 + i, nx)];
+        col[j] = hermite4(row, tx);
+    }
+    return hermite4(col, ty);
+}
+
+static double upwind_value(const double *plane, long nx, long ny, double xu, double yu,
+                           int interp)
+{
+    return interp ? bicubic_hermite(plane, nx, ny, xu, yu) : bilinear(plane, nx, ny, xu, yu);
+}
+
 /*
  * Formal solution for all rays and frequencies.
  *   chi, S, wphi : [nfreq][nz][ny][nx]
  *   I_bottom, I_top : [nfreq][ny][nx]
  *   mu : [nrays][3] direction cosines, wray : [nrays]
  * Outputs (zeroed here) Jbar, Jeff, U : [nz][ny][nx]; I_out, if not NULL,
- * receives every intensity as [nrays][nfreq][nz][ny][nx].
+ * receives every intensity as [nrays][nfreq][nz][ny][nx].  interp selects the
+ * upwind interpolation (0 linear, 1 monotone cubic Hermite).
  * Returns 0, or -1 on a bad argument.
  */
 int orc_formal_solution(long nx, long ny, long nz, double dx, double dy,
@@ -90,9 +147,10 @@ int orc_formal_solution(long nx, long ny, long nz, double dx, double dy,
                         const double *wray, long nfreq, const double *chi,
                         const double *S, const double *wphi,
                         const double *I_bottom, const double *I_top,
-                        double *Jbar, double *Jeff, double *U, double *I_out)
+                        double *Jbar, double *Jeff, double *U, double *I_out, int interp)
 {
-    if (nx < 1 || ny < 1 || nz < 2 || nrays < 1 || nfreq < 1 || dx <= 0 || dy <= 0)
+    if (nx < 1 || ny < 1 || nz < 2 || nrays < 1 || nfreq < 1 || dx <= 0 || dy <= 0 ||
+        interp < 0 || interp > 1)
         return -1;
     long nplane = nx * ny, nvox = nplane * nz;
     memset(Jbar, 0, sizeof(double) * nvox);
@@ -132,9 +190,9 @@ int orc_formal_solution(long nx, long ny, long nz, double dx, double dy,
                             /* upwind crossing point, in units of cells */
                             double xu = (double)x - s * mx / dx;
                             double yu = (double)y - s * my / dy;
-                            double I_up = bilinear(Iprev, nx, ny, xu, yu);
-                            double chi_up = bilinear(chip, nx, ny, xu, yu);
-                            double S_up = bilinear(Sp, nx, ny, xu, yu);
+                            double I_up = upwind_value(Iprev, nx, ny, xu, yu, interp);
+                            double chi_up = upwind_value(chip, nx, ny, xu, yu, interp);
+                            double S_up = upwind_value(Sp, nx, ny, xu, yu, interp);
                             long v = node_index(x, y, k, nx, ny);
                             double dtau = 0.5 * (chi_up + chif[v]) * s;
                             double ex, w0, wup;
@@ -182,16 +240,18 @@ int orc_formal_solution(long nx, long ny, long nz, double dx, double dy,
  *     Jx = sum_r w_r (I - w_0 sl),     Ux = sum_r w_r (1 - w_0 fl),
  * and, when Jm is not NULL, the mean intensity Jm = sum_r w_r I.
  * Shapes: chi, S, sl, fl, Jx, Ux, Jm [nfreq][nz][ny][nx]; I_bottom, I_top
- * [nfreq][ny][nx].  Returns 0, or -1 on a bad argument.
+ * [nfreq][ny][nx].  interp as for orc_formal_solution.  Returns 0, or -1 on
+ * a bad argument.
  */
 int orc_formal_solution_nu(long nx, long ny, long nz, double dx, double dy,
                            const double *z, long nrays, const double *mu,
                            const double *wray, long nfreq, const double *chi,
                            const double *S, const double *sl, const double *fl,
                            const double *I_bottom, const double *I_top,
-                           double *Jx, double *Ux, double *Jm)
+                           double *Jx, double *Ux, double *Jm, int interp)
 {
-    if (nx < 1 || ny < 1 || nz < 2 || nrays < 1 || nfreq < 1 || dx <= 0 || dy <= 0)
+    if (nx < 1 || ny < 1 || nz < 2 || nrays < 1 || nfreq < 1 || dx <= 0 || dy <= 0 ||
+        interp < 0 || interp > 1)
         return -1;
     long nplane = nx * ny, nvox = nplane * nz;
     memset(Jx, 0, sizeof(double) * nvox * nfreq);
@@ -229,9 +289,9 @@ int orc_formal_solution_nu(long nx, long ny, long nz, double dx, double dy,
                         for (long x = 0; x < nx; ++x) {
                             double xu = (double)x - s * mx / dx;
                             double yu = (double)y - s * my / dy;
-                            double I_up = bilinear(Iprev, nx, ny, xu, yu);
-                            double chi_up = bilinear(chip, nx, ny, xu, yu);
-                            double S_up = bilinear(Sp, nx, ny, xu, yu);
+                            double I_up = upwind_value(Iprev, nx, ny, xu, yu, interp);
+                            double chi_up = upwind_value(chip, nx, ny, xu, yu, interp);
+                            double S_up = upwind_value(Sp, nx, ny, xu, yu, interp);
                             long v = node_index(x, y, k, nx, ny);
                             double dtau = 0.5 * (chi_up + chif[v]) * s;
                             double ex, w0, wup;

@@ -16,8 +16,9 @@ What each function follows in the paper (Bjorgen & Leenaarts 2017):
 * ``frequency_grid``    -- CRD Doppler profile sampled at equidistant offsets
   with trapezoid weights, renormalised so that sum(w phi) = 1 (reading; the
   paper only states CRD).
-* ``formal_solution``   -- short characteristics with linear interpolation
-  (Sec. 3) accumulating Jbar, Jeff = Jbar - Lambda* S and U = 1 - Lambda*.
+* ``formal_solution``   -- short characteristics with linear or Hermite-spline
+  upwind interpolation (Sec. 3) accumulating Jbar, Jeff = Jbar - Lambda* S and
+  U = 1 - Lambda*.
 * ``rate_matrix`` / ``W`` -- statistical equilibrium (Eq. 2) with the first
   rate equation replaced by particle conservation (Eq. 3), so that
   W(n) = f with f = (n_tot, 0, ..., 0) (Eq. 4 and the f vector after it).
@@ -27,6 +28,8 @@ What each function follows in the paper (Bjorgen & Leenaarts 2017):
   C_i of Sec. 3.3.
 * ``restrict_fw``       -- full-weighting restriction (Sec. 4.4), 27 points.
 * ``prolong_trilinear`` -- trilinear interpolation (Sec. 4.5).
+* ``prolong_hermite``   -- monotone cubic Hermite interpolation, the paper's
+  other interpolation operator (Sec. 4.5), as successive 1D passes x, y, z.
 * ``vcycle``            -- FAS V-cycle, Eqs. 5-11 and the recursion of Sec. 2.2
   with nu_1 pre-, nu_2 post-smoothing, nu_3 coarse iterations, nu_0 in the
   first cycle (Sec. 4.12) and the 10 % fix for negative populations (Sec. 4.10).
@@ -84,11 +87,11 @@ def _load():
         lib.orc_formal_solution.restype = ctypes.c_int
         lib.orc_formal_solution.argtypes = [
             ctypes.c_long, ctypes.c_long, ctypes.c_long, ctypes.c_double, ctypes.c_double,
-            d, ctypes.c_long, d, d, ctypes.c_long, d, d, d, d, d, d, d, d, d]
+            d, ctypes.c_long, d, d, ctypes.c_long, d, d, d, d, d, d, d, d, d, ctypes.c_int]
         lib.orc_formal_solution_nu.restype = ctypes.c_int
         lib.orc_formal_solution_nu.argtypes = [
             ctypes.c_long, ctypes.c_long, ctypes.c_long, ctypes.c_double, ctypes.c_double,
-            d, ctypes.c_long, d, d, ctypes.c_long, d, d, d, d, d, d, d, d, d]
+            d, ctypes.c_long, d, d, ctypes.c_long, d, d, d, d, d, d, d, d, d, ctypes.c_int]
         _lib = lib
     return _lib
 
@@ -149,11 +152,12 @@ def frequency_grid(n_freq: int, x_max: float):
 
 
 def formal_solution_raw(z, dx, dy, mu, wray, chi, S, wphi, I_bottom, I_top,
-                        want_intensity=False):
+                        want_intensity=False, interp=0):
     """Formal solution for given chi, S [nfreq, nz, ny, nx] (Sec. 3).
 
     ``wphi`` [nfreq, nz, ny, nx] weights the frequency sum; ``I_bottom`` and
-    ``I_top`` [nfreq, ny, nx] are the entering intensities.  Returns
+    ``I_top`` [nfreq, ny, nx] are the entering intensities; ``interp`` picks
+    the upwind interpolation (0 bilinear, 1 monotone cubic Hermite).  Returns
     (Jbar, Jeff, U) [nz, ny, nx] and, if asked, I [nrays, nfreq, nz, ny, nx].
     """
     chi = np.ascontiguousarray(chi, dtype=np.float64)
@@ -172,7 +176,7 @@ def formal_solution_raw(z, dx, dy, mu, wray, chi, S, wphi, I_bottom, I_top,
     rc = _load().orc_formal_solution(nx, ny, nz, float(dx), float(dy), _ptr(z), len(wray),
                                      _ptr(mu), _ptr(wray), nf, _ptr(chi), _ptr(S),
                                      _ptr(wphi), _ptr(Ib), _ptr(It), _ptr(Jbar), _ptr(Jeff),
-                                     _ptr(U), _ptr(I))
+                                     _ptr(U), _ptr(I), int(interp))
     if rc != 0:
         raise RuntimeError("oracle formal solution failed")
     if want_intensity:
@@ -209,10 +213,12 @@ class TwoLevelProblem:
     """
 
     def __init__(self, atm, atom, n_grids: int = 1, quad_a: float | None = None,
-                 restriction: int = 0):
+                 restriction: int = 0, interpolation: int = 0, sc_interp: int = 0):
         self.atom = atom
         self.n_grids = n_grids
         self.restriction = restriction
+        self.interpolation = interpolation
+        self.sc_interp = sc_interp
         self.mu, self.wray = a4_quadrature(quad_a)
         self.x, self.phi, self.wphi = frequency_grid(atom.n_freq, atom.x_max)
         fine = Level(atm.nx, atm.ny, atm.nz, atm.dx, atm.dy, np.asarray(atm.z, float),
@@ -264,7 +270,8 @@ class TwoLevelProblem:
         rc = _load().orc_formal_solution(
             lev.nx, lev.ny, lev.nz, lev.dx, lev.dy, _ptr(np.ascontiguousarray(lev.z)),
             len(self.wray), _ptr(mu), _ptr(self.wray), nf, _ptr(chi), _ptr(Sf),
-            _ptr(wphi), _ptr(Ib), _ptr(It), _ptr(Jbar), _ptr(Jeff), _ptr(U), None)
+            _ptr(wphi), _ptr(Ib), _ptr(It), _ptr(Jbar), _ptr(Jeff), _ptr(U), None,
+            int(self.sc_interp))
         if rc != 0:
             raise RuntimeError("oracle formal solution failed")
         self.fs_count[k] += 1
@@ -347,6 +354,10 @@ class TwoLevelProblem:
         return restrict_fw(a)
 
     def prolong(self, k_fine: int, a_coarse):
+        """Interpolation operator (Sec. 4.5): trilinear, or monotone cubic
+        Hermite when ``interpolation`` is 1."""
+        if self.interpolation == 1:
+            return prolong_hermite(a_coarse, self.levels[k_fine].z)
         return prolong_trilinear(a_coarse, self.levels[k_fine].z)
 
     def vcycle(self, k: int, n: dict, f: dict, first: bool, params):
@@ -514,6 +525,102 @@ def prolong_trilinear(ac, z_fine):
     return out
 
 
+def pchip_slopes(y, h, periodic: bool):
+    """Node slopes of the monotone cubic Hermite interpolant along the last
+    axis of ``y`` (Auer 2003; Fritsch & Butland 1984): with secants
+    delta_i = (y_{i+1} - y_i)/h_i, an interior slope is the weighted harmonic
+    mean (w1 + w2)/(w1/delta_{i-1} + w2/delta_i), w1 = 2h_i + h_{i-1},
+    w2 = h_i + 2h_{i-1}, where both secants have the same strict sign, and 0
+    otherwise.  ``periodic``: node n-1 is followed by node 0 at spacing h[-1]
+    (every node is interior).  Otherwise the end slopes are the shape-
+    preserving three-point ones: s = ((2h_0 + h_1) delta_0 - h_0 delta_1)/
+    (h_0 + h_1), set to 0 if its sign differs from delta_0's and to 3 delta_0
+    if delta_0 and delta_1 differ in sign and |s| > 3|delta_0| (the same at
+    the far end); with two nodes the slope is the one secant.  ``h``: the
+    n - 1 spacings (n when periodic)."""
+    y = np.asarray(y, dtype=np.float64)
+    h = np.asarray(h, dtype=np.float64)
+    n = y.shape[-1]
+    if periodic:
+        delta = (np.roll(y, -1, axis=-1) - y) / h
+        dm, dp = np.roll(delta, 1, axis=-1), delta
+        hm, hp = np.roll(h, 1), h
+    else:
+        delta = np.diff(y, axis=-1) / h
+        if n == 2:
+            return np.concatenate([delta, delta], axis=-1)
+        dm, dp = delta[..., :-1], delta[..., 1:]
+        hm, hp = h[:-1], h[1:]
+    w1, w2 = 2.0 * hp + hm, hp + 2.0 * hm
+    same = ((dm > 0) & (dp > 0)) | ((dm < 0) & (dp < 0))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        d = np.where(same, (w1 + w2) / (w1 / dm + w2 / dp), 0.0)
+    if periodic:
+        return d
+
+    def end(d0, d1, h0, h1):
+        s = ((2.0 * h0 + h1) * d0 - h0 * d1) / (h0 + h1)
+        s = np.where(np.sign(s) != np.sign(d0), 0.0, s)
+        return np.where((np.sign(d0) != np.sign(d1)) & (np.abs(s) > 3.0 * np.abs(d0)),
+                        3.0 * d0, s)
+
+    first = end(delta[..., 0], delta[..., 1], h[0], h[1])
+    last = end(delta[..., -1], delta[..., -2], h[-1], h[-2])
+    return np.concatenate([first[..., None], d, last[..., None]], axis=-1)
+
+
+def hermite_eval(y0, y1, d0, d1, h, t):
+    """Cubic Hermite on an interval of length h from end values y0, y1 and end
+    slopes d0, d1, at fraction t."""
+    t2, t3 = t * t, t * t * t
+    return ((2 * t3 - 3 * t2 + 1) * y0 + (t3 - 2 * t2 + t) * h * d0
+            + (-2 * t3 + 3 * t2) * y1 + (t3 - t2) * h * d1)
+
+
+def _hermite_refine_axis(a, axis, periodic, xc, xf):
+    """Monotone cubic Hermite of ``a`` along ``axis`` from nodes xc onto the
+    finer nodes xf (xf[2i] = xc[i]; odd xf between two coarse nodes)."""
+    a = np.moveaxis(np.asarray(a, dtype=np.float64), axis, -1)
+    nc = a.shape[-1]
+    if periodic:
+        h = np.full(nc, xc[1] - xc[0] if nc > 1 else 1.0)
+    else:
+        h = np.diff(xc)
+    d = pchip_slopes(a, h, periodic) if nc > 1 else np.zeros_like(a)
+    nf = len(xf)
+    out = np.empty(a.shape[:-1] + (nf,))
+    out[..., 0::2] = a[..., : (nf + 1) // 2]
+    i = np.arange(1, nf, 2)
+    i0 = i // 2
+    i1 = (i0 + 1) % nc
+    hh = h[i0]
+    t = (xf[i] - xc[i0]) / hh
+    out[..., 1::2] = hermite_eval(a[..., i0], a[..., i1], d[..., i0], d[..., i1], hh, t)
+    return np.moveaxis(out, -1, axis)
+
+
+def prolong_hermite(ac, z_fine):
+    """Monotone cubic Hermite interpolation of [..., nzc, nyc, nxc] onto the
+    finer grid (Sec. 4.5, the alternative to trilinear interpolation).
+
+    Reading: one-dimensional monotone Hermite passes (``pchip_slopes``),
+    first along x (periodic, uniform), then along y (periodic, uniform), then
+    along z at the physical heights (fixed ends); a fine node thus depends on
+    the 4 x 4 x 4 coarse nodes around it.  Fine nodes on even indices keep
+    the coarse value along that axis.  Each pass keeps a value between the
+    two coarse values of its interval, so every fine value lies within the
+    range of the 2 x 2 x 2 coarse nodes around it.
+    """
+    ac = np.asarray(ac, dtype=np.float64)
+    nzc, nyc, nxc = ac.shape[-3:]
+    nz, ny, nx = 2 * nzc - 1, 2 * nyc, 2 * nxc
+    zf = np.asarray(z_fine, dtype=np.float64)
+    a = _hermite_refine_axis(ac, -1, True, np.arange(nxc, dtype=float),
+                             np.arange(nx) / 2.0)
+    a = _hermite_refine_axis(a, -2, True, np.arange(nyc, dtype=float), np.arange(ny) / 2.0)
+    return _hermite_refine_axis(a, -3, False, zf[::2], zf)
+
+
 def coarsen_level(lev: Level) -> Level:
     """Atmosphere on the next coarser grid (Sec. 4.1, 4.7).
 
@@ -627,7 +734,7 @@ def coarsen_ml_level(lev: MLLevel) -> MLLevel:
 
 
 def formal_solution_nu_raw(z, dx, dy, mu, wray, chi, S, sl, fl, I_bottom, I_top,
-                           want_j: bool = False):
+                           want_j: bool = False, interp: int = 0):
     """Per-frequency angle sums Jx, Ux [nfreq, nz, ny, nx] (see fs_oracle.c),
     and with want_j also the mean intensity J = sum_r w_r I."""
     chi = np.ascontiguousarray(chi, dtype=np.float64)
@@ -644,7 +751,7 @@ def formal_solution_nu_raw(z, dx, dy, mu, wray, chi, S, sl, fl, I_bottom, I_top,
                                         len(wray), _ptr(np.ascontiguousarray(mu)),
                                         _ptr(np.ascontiguousarray(wray)), nf, _ptr(chi),
                                         _ptr(arrs[0]), _ptr(arrs[1]), _ptr(arrs[2]), _ptr(Ib),
-                                        _ptr(It), _ptr(Jx), _ptr(Ux), _ptr(Jm))
+                                        _ptr(It), _ptr(Jx), _ptr(Ux), _ptr(Jm), int(interp))
     if rc != 0:
         raise RuntimeError("oracle formal solution failed")
     return (Jx, Ux, Jm) if want_j else (Jx, Ux)
@@ -699,9 +806,11 @@ class MultiLevelProblem(TwoLevelProblem):
     """
 
     def __init__(self, atm, atom, n_grids: int = 1, quad_a: float | None = None,
-                 restriction: int = 0):
+                 restriction: int = 0, interpolation: int = 0, sc_interp: int = 0):
         self.atom = atom
         self.restriction = restriction
+        self.interpolation = interpolation
+        self.sc_interp = sc_interp
         self.N = atom.n_levels
         self.n_grids = n_grids
         self.mu, self.wray = a4_quadrature(quad_a)
@@ -807,7 +916,7 @@ class MultiLevelProblem(TwoLevelProblem):
                                      terms["chi"].reshape(shp), terms["S"].reshape(shp),
                                      terms["sl"].reshape(shp), terms["fl"].reshape(shp),
                                      Ib.reshape((nf, lev.ny, lev.nx)), 0.0,
-                                     want_j=self.scatter)
+                                     want_j=self.scatter, interp=self.sc_interp)
         Jx, Ux = res[0], res[1]
         if self.scatter:
             self.jbg[k] = res[2].reshape(nf, -1)
