@@ -104,7 +104,23 @@ typedef struct {
     int ml_chunk;  /* multi-level handles: frequencies per chunk of the formal
                       solution, 0 for the automatic choice (mg3d_set_ml_chunk);
                       ignored by two-level handles */
+    int interpolation; /* interpolation operator (Sec. 4.5) of the V-cycle
+                          correction, the FMG transfer and mg3d_prolong:
+                          MG3D_INTERP_LINEAR (trilinear, the paper's choice)
+                          or MG3D_INTERP_HERMITE (monotone cubic Hermite) */
+    int sc_interp; /* upwind interpolation of the formal solution (Sec. 3):
+                      MG3D_INTERP_LINEAR (bilinear) or MG3D_INTERP_HERMITE */
 } mg3d_params;
+
+/* Monotone cubic Hermite (Auer 2003) means successive 1D passes along x and
+ * y (periodic) and, for the prolongation, z (physical heights): on each
+ * interval the cubic through its two nodes with slopes from their
+ * neighbours, the harmonic mean of the adjacent secants where they have the
+ * same sign and 0 otherwise (Fritsch & Butland 1984; shape-preserving
+ * three-point slopes at the z ends).  Values stay between the two nodes of
+ * every interval, so positive data give positive results. */
+#define MG3D_INTERP_LINEAR 0
+#define MG3D_INTERP_HERMITE 1
 
 #define MG3D_RESTRICT_FULL 0    /* 27-node full weighting */
 #define MG3D_RESTRICT_HALF 1    /* centre 1/2, six axis neighbours 1/12 */

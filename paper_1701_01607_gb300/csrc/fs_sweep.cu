@@ -19,6 +19,13 @@
 // shared by all frequencies of the group, because for the two-level atom the
 // opacity factorises as chi0(node) phi(nu) and S does not depend on nu.
 //
+// With the Hermite-spline option (Sec. 3) the upwind values come from a 4 x 4
+// stencil instead: monotone cubic Hermite along x on the four rows around the
+// crossing, then along y.  Each finished intensity plane gets its per-node
+// x-slopes next to it in shared memory (one pass over the band after a block
+// barrier), so that an upwind row costs four values and four products; chi0
+// and S take their x-slopes from global memory, computed after the opacity.
+//
 // Each block accumulates, per node, the frequency sum of its group for
 //   Jeff = sum w phi (I - w0 S)    and    U = sum w phi (1 - w0)
 // and stores it into a partial slot (ray, group); the rate kernel adds the
@@ -58,6 +65,8 @@ __global__ void planck_bottom_kernel(long nplane, double theta, const double *__
 
 // Shared-memory layout of one block (elements of T):
 //   I planes      [2][ng][rows][nx]           plane k-1 read, plane k written
+//   slope planes  [2][ng][rows][nx]           Hermite sweeps only: x-slopes of
+//                                             the I planes
 //   staging       [2][2][2 rows + 1][nx]      per step: chi0 and S of the
 //                 upwind window (rows + 1 rows of plane k-1, shifted by the
 //                 step's row offset) then of the block's own rows of plane k
@@ -94,11 +103,98 @@ __device__ __forceinline__ void stage_rows(const SweepArgs<T> &a, T *dst, long a
     }
 }
 
+// One sweep step (plane k from upwind plane kp) of a block's band with
+// monotone cubic Hermite upwind interpolation: for each node the rows
+// ya-1, ya, ya+1, ya+2 (periodic) of plane kp are interpolated along x at
+// tx (values and slopes at xa and xa+1), then the four results along y at
+// ty.  chi0 and S come from global memory with their x-slopes; I and its
+// slopes from the block's or a peer block's shared memory.  Weights,
+// accumulation and the mirror-frequency sharing are those of the linear
+// step.
+template <typename T, typename Fresh>
+__device__ __forceinline__ void hermite_step(
+    const SweepArgs<T> &a, int rank, unsigned long long rmagic, cg::cluster_group &cluster,
+    const T *prev, const T *dprev, T *cur, T *__restrict__ pj, T *__restrict__ pu, int k, int kp,
+    const StepGeom &o, T half_s, int nf, const T *phi, const T *inv_phi, const T *wphi,
+    const T *wu, const ExpNegTable &et, const Fresh &is_fresh) {
+    const int nx = a.nx, ny = a.ny, rows = a.rows;
+    const int y0 = rank * rows;
+    const int myrows = max(0, min(rows, ny - y0));
+    const int band = myrows * nx;
+    const long nplane = (long)nx * ny;
+    const HermiteBasis<T> bx((T)o.tx), by((T)o.ty);
+    for (int q = threadIdx.x; q < band; q += blockDim.x) {
+        const int yl = q / nx, x = q - yl * nx;
+        const int y = y0 + yl;
+        int xa = x + o.ix0;
+        if (xa >= nx) xa -= nx;
+        const int xb = (xa + 1 == nx) ? 0 : xa + 1;
+        int ya = y + o.iy0;
+        if (ya >= ny) ya -= ny;
+        int yr[4];
+        yr[1] = ya;
+        yr[0] = ya == 0 ? ny - 1 : ya - 1;
+        yr[2] = ya + 1 == ny ? 0 : ya + 1;
+        yr[3] = yr[2] + 1 == ny ? 0 : yr[2] + 1;
+        const long pp = (long)kp * nplane, pk = (long)k * nplane + (long)y * nx;
+        auto up2d = [&](const T *v, const T *d) {
+            T gq[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const long ro = (long)yr[m] * nx;
+                gq[m] = bx.at(v[ro + xa], d[ro + xa], v[ro + xb], d[ro + xb]);
+            }
+            return by.through4(gq[0], gq[1], gq[2], gq[3]);
+        };
+        const T chi_up = up2d(a.chi0 + pp, a.dchi0 + pp);
+        const T S_up = up2d(a.S + pp, a.dS + pp);
+        const T chi_loc = a.chi0[pk + x];
+        const T S_loc = a.S[pk + x];
+        const T dtau0 = (chi_up + chi_loc) * half_s;
+        const T inv_dtau0 = rcp(dtau0);
+        // the four upwind rows of the intensity and slope planes
+        const T *P[4], *D[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int b = band_of(yr[m], rmagic);
+            const long ro = (long)(yr[m] - b * rows) * nx;
+            P[m] = (b == rank ? prev : cluster.map_shared_rank(prev, b)) + ro;
+            D[m] = (b == rank ? dprev : cluster.map_shared_rank(dprev, b)) + ro;
+        }
+        T cj = 0, cu = 0;
+        auto step = [&](int f, T ex, T w0, T wup) {
+            const long off = (long)f * rows * nx;
+            T gq[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+                gq[m] = bx.at(P[m][off + xa], D[m][off + xa], P[m][off + xb], D[m][off + xb]);
+            const T I_up = by.through4(gq[0], gq[1], gq[2], gq[3]);
+            const T part = I_up * ex + wup * S_up;
+            cur[((long)f * rows + yl) * nx + x] = part + w0 * S_loc;
+            cj += wphi[f] * part;
+        };
+        for (int f = 0; f < nf;) {
+            const bool a2 = f + 1 < nf && !is_fresh(f + 1);
+            T ex, w0, wup, u;
+            ScWeights<T>::eval(dtau0 * phi[f], inv_dtau0 * inv_phi[f], et, ex, w0, wup, u);
+            cu += wu[f] * u;
+            step(f, ex, w0, wup);
+            if (a2) step(f + 1, ex, w0, wup);
+            f += a2 ? 2 : 1;
+        }
+        const long v = (long)k * nplane + (long)y * nx + x;
+        pj[v] = cj;
+        pu[v] = cu;
+    }
+}
+
 // Body of the sweep for ray r and frequency group g of one problem.  STAGE:
 // chi0 and S rows of each step are copied to shared memory one step ahead;
-// without it they are read from global memory (L1/L2) where used.
-template <typename T, bool STAGE>
+// without it they are read from global memory (L1/L2) where used.  HERM:
+// monotone cubic Hermite upwind interpolation (unstaged).
+template <typename T, bool STAGE, bool HERM>
 __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) {
+    static_assert(!(STAGE && HERM), "Hermite sweeps run unstaged");
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int nx = a.nx, ny = a.ny, nz = a.nz, rows = a.rows;
@@ -117,7 +213,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf = reinterpret_cast<T *>(smem_raw);
     const long bufstride = (long)a.ng * rows * nx;
-    T *stage = buf + 2 * bufstride;
+    T *dbuf = buf + 2 * bufstride;  // slope planes (HERM)
+    T *stage = buf + (HERM ? 4 : 2) * bufstride;
     const long stagestride = STAGE ? sweep_stage_elems(rows, nx) : 0;
     T *tabs = stage + 2 * stagestride;
     T *phi = tabs, *inv_phi = tabs + a.ng, *wphi = tabs + 2 * a.ng, *wu = tabs + 3 * a.ng;
@@ -203,6 +300,11 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
             const T half_s = (T)(0.5 * o.s);
             const T w00 = (T(1) - tx) * (T(1) - ty), w10 = tx * (T(1) - ty);
             const T w01 = (T(1) - tx) * ty, w11 = tx * ty;
+            if constexpr (HERM) {
+                hermite_step(a, rank, rmagic, cluster, prev, dbuf + ((t - 1) & 1) * bufstride,
+                             cur, pj, pu, k, kp, o, half_s, nf, phi, inv_phi, wphi, wu, et,
+                             is_fresh);
+            } else
             for (int q = threadIdx.x; q < band; q += blockDim.x) {
                 const int yl = q / nx, x = q - yl * nx;
                 const int y = y0 + yl;
@@ -296,6 +398,20 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
                 pu[v] = cu;
             }
         }
+        if constexpr (HERM) {
+            // x-slopes of the new plane; a band holds whole rows
+            __syncthreads();
+            T *dcur = dbuf + (t & 1) * bufstride;
+            for (int q = threadIdx.x; q < band; q += blockDim.x) {
+                const int yl = q / nx, x = q - yl * nx;
+                const int xm = x == 0 ? nx - 1 : x - 1, xp = x + 1 == nx ? 0 : x + 1;
+                for (int f = 0; f < nf; ++f) {
+                    const long row = ((long)f * rows + yl) * nx;
+                    dcur[row + x] =
+                        mono_slope(cur[row + x] - cur[row + xm], cur[row + xp] - cur[row + x]);
+                }
+            }
+        }
         // plane t complete in every block before any block reads it, and no
         // block overwrites plane t-1 (written again at t+1) while it is read
         cluster.sync();
@@ -306,9 +422,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
 // blocks per SM it must fit, which sets the register budget (MINB = 1: up to
 // 255 registers; 1024/MAXT: 64 registers, 32 resident warps per SM; 3 blocks
 // of 256: 85 registers).
-template <typename T, int MAXT, int MINB, bool STAGE>
+template <typename T, int MAXT, int MINB, bool STAGE, bool HERM>
 __global__ void __launch_bounds__(MAXT, MINB) sweep_kernel(const SweepArgs<T> a) {
-    sweep_body<T, STAGE>(a, blockIdx.y, blockIdx.z);
+    sweep_body<T, STAGE, HERM>(a, blockIdx.y, blockIdx.z);
 }
 
 // Batched sweep: cluster y of the grid runs work item items[y] = (problem,
@@ -319,7 +435,7 @@ __global__ void __launch_bounds__(MAXT, 1024 / MAXT) sweep_batch_kernel(
     const SweepArgs<T> *__restrict__ args, const BatchItem *__restrict__ items) {
     const BatchItem it = items[blockIdx.y];
     const SweepArgs<T> a = args[it.member];
-    sweep_body<T, true>(a, it.group, it.ray);
+    sweep_body<T, true, false>(a, it.group, it.ray);
 }
 
 __global__ void exp_check_kernel(int n, const double *__restrict__ x, double *__restrict__ out,
@@ -353,26 +469,26 @@ void exp_neg_constants(double *tab, double *l1, double *l2) {
 
 size_t sweep_smem_bytes(int prec, const SweepShape &s, int nx) {
     size_t elem = prec == 0 ? sizeof(double) : sizeof(float);
-    return (2ull * s.ng * s.rows * nx + (s.stage ? 2ull * sweep_stage_elems(s.rows, nx) : 0ull) +
-            4ull * s.ng) *
+    return ((s.herm ? 4ull : 2ull) * s.ng * s.rows * nx +
+            (s.stage ? 2ull * sweep_stage_elems(s.rows, nx) : 0ull) + 4ull * s.ng) *
            elem;
 }
 
 // Kernel attributes for shape s (dynamic shared memory; clusters of more
 // than 8 blocks are a non-portable size the kernel must opt into) and the
 // launch configuration; a is null for an occupancy query.
-template <typename T, int MAXT, int MINB, bool STAGE>
+template <typename T, int MAXT, int MINB, bool STAGE, bool HERM>
 static cudaError_t sweep_config(const SweepShape &s, int nx, cudaStream_t st,
                                 cudaLaunchConfig_t *cfg, cudaLaunchAttribute *attr) {
     const size_t smem = sweep_smem_bytes(sizeof(T) == 8 ? 0 : 1, s, nx);
     // the limit is the same for every launch: a CUDA graph that captured a
     // launch needing more than a later launch of the same kernel must still
     // find the attribute large enough when it replays
-    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, MAXT, MINB, STAGE>,
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, MAXT, MINB, STAGE, HERM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kMaxSweepSmem);
     if (e == cudaSuccess && s.bands > kPortableBands)
-        e = cudaFuncSetAttribute(sweep_kernel<T, MAXT, MINB, STAGE>,
+        e = cudaFuncSetAttribute(sweep_kernel<T, MAXT, MINB, STAGE, HERM>,
                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     *cfg = cudaLaunchConfig_t{};
@@ -390,59 +506,65 @@ static cudaError_t sweep_config(const SweepShape &s, int nx, cudaStream_t st,
     return cudaSuccess;
 }
 
-template <typename T, int MAXT, int MINB, bool STAGE>
+template <typename T, int MAXT, int MINB, bool STAGE, bool HERM>
 static cudaError_t launch_sweep_t(const SweepArgs<T> &a, const SweepShape &s,
                                   cudaStream_t st) {
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
-    cudaError_t e = sweep_config<T, MAXT, MINB, STAGE>(s, a.nx, st, &cfg, attr);
+    cudaError_t e = sweep_config<T, MAXT, MINB, STAGE, HERM>(s, a.nx, st, &cfg, attr);
     if (e != cudaSuccess) return e;
-    return cudaLaunchKernelEx(&cfg, sweep_kernel<T, MAXT, MINB, STAGE>, a);
+    return cudaLaunchKernelEx(&cfg, sweep_kernel<T, MAXT, MINB, STAGE, HERM>, a);
 }
 
-template <typename T, int MAXT, int MINB, bool STAGE>
+template <typename T, int MAXT, int MINB, bool STAGE, bool HERM>
 static cudaError_t clusters_t(const SweepShape &s, int nx, int *n) {
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
-    cudaError_t e = sweep_config<T, MAXT, MINB, STAGE>(s, nx, 0, &cfg, attr);
+    cudaError_t e = sweep_config<T, MAXT, MINB, STAGE, HERM>(s, nx, 0, &cfg, attr);
     if (e != cudaSuccess) return e;
     if (s.bands == 1)  // plain launch: resident blocks per SM
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, sweep_kernel<T, MAXT, MINB, STAGE>,
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, sweep_kernel<T, MAXT, MINB, STAGE, HERM>,
                                                              s.threads, cfg.dynamicSmemBytes);
-    return cudaOccupancyMaxActiveClusters(n, sweep_kernel<T, MAXT, MINB, STAGE>, &cfg);
+    return cudaOccupancyMaxActiveClusters(n, sweep_kernel<T, MAXT, MINB, STAGE, HERM>, &cfg);
 }
 
-template <typename T, bool STAGE>
+template <typename T, bool STAGE, bool HERM>
 static cudaError_t launch_sweep_st(const SweepArgs<T> &a, const SweepShape &s, cudaStream_t st) {
     if (s.threads <= 256) {
-        if (s.lean == 1) return launch_sweep_t<T, 256, 4, STAGE>(a, s, st);
-        if (s.lean == 2) return launch_sweep_t<T, 256, 3, STAGE>(a, s, st);
-        return launch_sweep_t<T, 256, 1, STAGE>(a, s, st);
+        if (s.lean == 1) return launch_sweep_t<T, 256, 4, STAGE, HERM>(a, s, st);
+        if (s.lean == 2) return launch_sweep_t<T, 256, 3, STAGE, HERM>(a, s, st);
+        return launch_sweep_t<T, 256, 1, STAGE, HERM>(a, s, st);
     }
-    return s.lean == 1 ? launch_sweep_t<T, 512, 2, STAGE>(a, s, st)
-                       : launch_sweep_t<T, 512, 1, STAGE>(a, s, st);
+    return s.lean == 1 ? launch_sweep_t<T, 512, 2, STAGE, HERM>(a, s, st)
+                       : launch_sweep_t<T, 512, 1, STAGE, HERM>(a, s, st);
 }
 
 template <typename T>
 static cudaError_t launch_sweep_any(const SweepArgs<T> &a, const SweepShape &s,
                                     cudaStream_t st) {
-    return s.stage ? launch_sweep_st<T, true>(a, s, st) : launch_sweep_st<T, false>(a, s, st);
+    if (s.herm) {
+        if (s.stage || !a.dchi0 || !a.dS) return cudaErrorInvalidValue;
+        return launch_sweep_st<T, false, true>(a, s, st);
+    }
+    return s.stage ? launch_sweep_st<T, true, false>(a, s, st)
+                   : launch_sweep_st<T, false, false>(a, s, st);
 }
 
-template <typename T, bool STAGE>
+template <typename T, bool STAGE, bool HERM>
 static cudaError_t clusters_st(const SweepShape &s, int nx, int *n) {
     if (s.threads <= 256) {
-        if (s.lean == 1) return clusters_t<T, 256, 4, STAGE>(s, nx, n);
-        if (s.lean == 2) return clusters_t<T, 256, 3, STAGE>(s, nx, n);
-        return clusters_t<T, 256, 1, STAGE>(s, nx, n);
+        if (s.lean == 1) return clusters_t<T, 256, 4, STAGE, HERM>(s, nx, n);
+        if (s.lean == 2) return clusters_t<T, 256, 3, STAGE, HERM>(s, nx, n);
+        return clusters_t<T, 256, 1, STAGE, HERM>(s, nx, n);
     }
-    return s.lean == 1 ? clusters_t<T, 512, 2, STAGE>(s, nx, n)
-                       : clusters_t<T, 512, 1, STAGE>(s, nx, n);
+    return s.lean == 1 ? clusters_t<T, 512, 2, STAGE, HERM>(s, nx, n)
+                       : clusters_t<T, 512, 1, STAGE, HERM>(s, nx, n);
 }
 
 template <typename T>
 static cudaError_t clusters_any(const SweepShape &s, int nx, int *n) {
-    return s.stage ? clusters_st<T, true>(s, nx, n) : clusters_st<T, false>(s, nx, n);
+    if (s.herm) return s.stage ? cudaErrorInvalidValue : clusters_st<T, false, true>(s, nx, n);
+    return s.stage ? clusters_st<T, true, false>(s, nx, n) : clusters_st<T, false, false>(s, nx, n);
 }
 
 cudaError_t sweep_active_clusters(int prec, const SweepShape &s, int nx, int *n) {
@@ -512,6 +634,31 @@ cudaError_t launch_opacity(int prec, long nvox, double g_ratio, double kappa,
     else
         opacity_kernel<float><<<grid_for(nvox, th), th, 0, st>>>(
             nvox, g_ratio, kappa, n, (float *)chi0, (float *)S);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void xslope_kernel(int nx, long nvox, const T *__restrict__ a, const T *__restrict__ b,
+                              T *__restrict__ da, T *__restrict__ db) {
+    for (long v = blockIdx.x * (long)blockDim.x + threadIdx.x; v < nvox;
+         v += (long)gridDim.x * blockDim.x) {
+        const int x = (int)(v % nx);
+        const long vm = v + ((x == 0 ? nx - 1 : x - 1) - x);
+        const long vp = v + ((x + 1 == nx ? 0 : x + 1) - x);
+        da[v] = mono_slope(a[v] - a[vm], a[vp] - a[v]);
+        db[v] = mono_slope(b[v] - b[vm], b[vp] - b[v]);
+    }
+}
+
+cudaError_t launch_xslopes(int prec, int nx, long nvox, const void *a, const void *b, void *da,
+                           void *db, cudaStream_t st) {
+    const int th = 256;
+    if (prec == 0)
+        xslope_kernel<double><<<grid_for(nvox, th), th, 0, st>>>(
+            nx, nvox, (const double *)a, (const double *)b, (double *)da, (double *)db);
+    else
+        xslope_kernel<float><<<grid_for(nvox, th), th, 0, st>>>(
+            nx, nvox, (const float *)a, (const float *)b, (float *)da, (float *)db);
     return cudaGetLastError();
 }
 

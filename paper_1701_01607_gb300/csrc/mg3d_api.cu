@@ -63,12 +63,14 @@ struct Level {
     std::vector<double> z;
     double *T = nullptr, *n_tot = nullptr, *c_ul = nullptr, *c_lu = nullptr;
     double *tz = nullptr;        // [nz] prolongation weight of the upper coarse plane
+    double *zf = nullptr;        // [nz] heights (Hermite prolongation onto this grid)
     double *n = nullptr;         // [2][nvox]
     double *f = nullptr;         // [2][nvox]
     bool f_default = true;       // f = (n_tot, 0)
     double *n_before = nullptr;  // [2][nvox]
     double *r = nullptr;         // [2][nvox] residual / scratch
     void *chi0 = nullptr, *S = nullptr, *bbot = nullptr;
+    void *dchi0 = nullptr, *dS = nullptr;  // x-slopes of chi0, S (Hermite upwind interpolation)
     StepGeom *geom = nullptr;    // [kRays][nz]
     SweepShape shape{};
     // multi-level atom only
@@ -76,6 +78,7 @@ struct Level {
     double *cmat = nullptr;      // [N][N][nvox] collisional rates
     double *saha = nullptr;      // [N][nvox] LTE ratios to the continuum
     void *mchi = nullptr, *mS = nullptr, *msl = nullptr, *mfl = nullptr;  // [nf][nvox]
+    void *mdchi = nullptr, *mdS = nullptr;  // [nf][nvox] x-slopes of mchi, mS (Hermite)
     void *mib = nullptr;         // [nf][nplane] bottom intensity
     double *sigma_c = nullptr;   // background coherent scattering [nvox] (FP64)
     void *jbg = nullptr;         // background radiation field [nf][nvox] (FS precision)
@@ -237,7 +240,7 @@ SweepArgs<T> sweep_args(const mg3d_handle *h, const Level &L, const SweepShape &
     return SweepArgs<T>{L.nx, L.ny, L.nz, h->atom.n_freq, s.ng, s.ngroups, s.rows,
                         h->up_mask, (const T *)L.chi0, (const T *)L.S, (const T *)L.bbot,
                         L.geom, phi, inv_phi, wphi, (T *)h->pj, (T *)h->pu, h->d_exp_tab,
-                        h->exp_l1, h->exp_l2};
+                        h->exp_l1, h->exp_l2, (const T *)L.dchi0, (const T *)L.dS};
 }
 
 // Upwind crossing of every (ray, sweep step): for step t the plane is
@@ -280,15 +283,20 @@ int threads_for_band(int band) {
 // the number of bands that brings the grid closest to two blocks per SM (the
 // shapes measured fastest on the 64x64 planes of the bench workload, in both
 // precisions, were of this kind); mg3d_autotune replaces it by measurement.
-SweepShape choose_shape(int prec, int nx, int ny, int nfreq) {
+SweepShape choose_shape(int prec, int nx, int ny, int nfreq, int herm) {
     const int ng = nfreq < 3 ? nfreq : 3;
     const int ngroups = (nfreq + ng - 1) / ng;
     SweepShape best{};
+    auto with_mode = [&](SweepShape s) {
+        s.herm = herm;
+        s.stage = herm ? 0 : 1;
+        return s;
+    };
     long best_gap = 1L << 40;
     for (int bands = 1; bands <= kPortableBands && bands <= ny; ++bands) {
         const int rows = (ny + bands - 1) / bands;
         if ((long)(bands - 1) * rows >= ny) continue;
-        SweepShape s{ng, ngroups, bands, rows, 256};
+        const SweepShape s = with_mode(SweepShape{ng, ngroups, bands, rows, 256});
         if (sweep_smem_bytes(prec, s, nx) > kMaxSweepSmem) continue;
         const long blocks = (long)kRays * ngroups * bands;
         const long gap = blocks > 304 ? blocks - 304 : 304 - blocks;
@@ -303,7 +311,7 @@ SweepShape choose_shape(int prec, int nx, int ny, int nfreq) {
             if (bands > ny) continue;
             const int rows = (ny + bands - 1) / bands;
             if ((long)(bands - 1) * rows >= ny) continue;
-            SweepShape s{1, nfreq, bands, rows, 256};
+            const SweepShape s = with_mode(SweepShape{1, nfreq, bands, rows, 256});
             if (sweep_smem_bytes(prec, s, nx) <= kMaxSweepSmem) {
                 best = s;
                 break;
@@ -330,9 +338,10 @@ int dalloc(P **p, size_t count) {
 }
 
 void free_level(Level &L) {
-    void *ptrs[] = {L.T,     L.n_tot, L.c_ul, L.c_lu, L.tz,   L.n,    L.f,   L.n_before,
+    void *ptrs[] = {L.T,     L.n_tot, L.c_ul, L.c_lu, L.tz,   L.zf,   L.n,    L.f,   L.n_before,
                     L.r,     L.chi0,  L.S,    L.bbot, L.geom, L.chi_c, L.cmat, L.saha,
-                    L.mchi,  L.mS,    L.msl,  L.mfl,  L.mib,  L.sigma_c, L.jbg};
+                    L.mchi,  L.mS,    L.msl,  L.mfl,  L.mib,  L.sigma_c, L.jbg,
+                    L.dchi0, L.dS,   L.mdchi, L.mdS};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     L = Level{};
@@ -388,6 +397,10 @@ int ml_chunk_fs(mg3d_handle *h, int k, int f0, int nc) {
                      h->d_exp_tab, h->exp_l1, h->exp_l2,
                      h->scatter ? L.sigma_c : nullptr, h->scatter ? L.jbg : nullptr};
     MG_TRY(launched(h, launch_ml_opacity(oa, h->stream), "multi-level opacity"));
+    if (h->params.sc_interp)
+        MG_TRY(launched(h, launch_xslopes(h->prec, L.nx, (long)nc * L.nvox, L.mchi, L.mS, L.mdchi,
+                                          L.mdS, h->stream),
+                        "x-slopes"));
     TimedLaunch tl{nullptr, nullptr, k};
     if (h->timing) {
         tl.a = pool_event(h);
@@ -403,7 +416,8 @@ int ml_chunk_fs(mg3d_handle *h, int k, int f0, int nc) {
                               (const double *)L.msl, (const double *)L.mfl,
                               (const double *)ib, L.geom, h->d_exp_tab, h->exp_l1, h->exp_l2,
                               (double *)h->ml_jx, (double *)h->ml_ux, L.ml_rpb,
-                              (double *)h->ml_jm};
+                              (double *)h->ml_jm, (const double *)L.mdchi, (const double *)L.mdS,
+                              h->params.sc_interp};
         e = launch_ml_sweep_f64(a, L.ml_bands, L.ml_threads, h->stream);
     } else {
         MlSweepArgs<float> a{L.nx, L.ny, L.nz, nc, L.ml_rows,
@@ -411,7 +425,8 @@ int ml_chunk_fs(mg3d_handle *h, int k, int f0, int nc) {
                              (const float *)L.msl, (const float *)L.mfl,
                              (const float *)ib, L.geom, h->d_exp_tab, h->exp_l1, h->exp_l2,
                              (float *)h->ml_jx, (float *)h->ml_ux, L.ml_rpb,
-                             (float *)h->ml_jm};
+                             (float *)h->ml_jm, (const float *)L.mdchi, (const float *)L.mdS,
+                             h->params.sc_interp};
         e = launch_ml_sweep_f32(a, L.ml_bands, L.ml_threads, h->stream);
     }
     MG_TRY(launched(h, e, "multi-level sweep"));
@@ -487,6 +502,10 @@ int formal_solution(mg3d_handle *h, int k) {
     MG_TRY(launched(h, launch_opacity(h->prec, L.nvox, h->atom.g_ratio, h->atom.kappa, L.n,
                                       L.chi0, L.S, h->stream),
                     "opacity"));
+    if (h->params.sc_interp)
+        MG_TRY(launched(h, launch_xslopes(h->prec, L.nx, L.nvox, L.chi0, L.S, L.dchi0, L.dS,
+                                          h->stream),
+                        "x-slopes"));
     TimedLaunch tl{nullptr, nullptr, k};
     if (h->timing) {
         tl.a = pool_event(h);
@@ -636,9 +655,11 @@ int vcycle(mg3d_handle *h, int k, bool first) {
         MG_TRY(vcycle(h, k - 1, false));
     }
     // relative correction, interpolated (Eqs. 10-11), 10 % rule (Sec. 4.10)
-    MG_TRY(launched(h, launch_prolong_correct(h->N, C.nx, C.ny, C.nz, F.tz, C.n, C.n_before, F.n,
-                                              h->scal, h->stream),
+    MG_TRY(launched(h, launch_prolong_correct(h->params.interpolation, h->N, C.nx, C.ny, C.nz,
+                                              F.tz, F.zf, C.n, C.n_before, F.n, h->scal,
+                                              h->stream),
                     "prolong correction"));
+    if (h->params.interpolation) ++h->launches;  // the Hermite correction is two kernels
     for (int i = 0; i < h->params.nu2; ++i) MG_TRY(sweep(h, k));
     return MG3D_OK;
 }
@@ -810,6 +831,8 @@ int make_shape(const mg3d_handle *h, int k, int ng, int bands, int threads, Swee
         return fail(MG3D_E_ARG, "bad sweep shape");
     SweepShape s{ng, (nf + ng - 1) / ng, bands, (L.ny + bands - 1) / bands, threads};
     if ((long)(bands - 1) * s.rows >= L.ny) return fail(MG3D_E_ARG, "empty band");
+    s.herm = h->params.sc_interp;
+    s.stage = s.herm ? 0 : 1;
     *out = s;
     return MG3D_OK;
 }
@@ -823,6 +846,8 @@ static int shape_from_args(const mg3d_handle *h, int level, int freq_per_block, 
     if (lean < 0 || lean > 2 || (lean == 2 && threads > 256))
         return fail(MG3D_E_ARG, "lean must be 0, 1 or (up to 256 threads) 2");
     if (stage != 0 && stage != 1) return fail(MG3D_E_ARG, "stage must be 0 or 1");
+    if (stage && h->params.sc_interp)
+        return fail(MG3D_E_ARG, "Hermite upwind interpolation runs unstaged (stage 0)");
     SweepShape s;
     MG_TRY(make_shape(h, level, freq_per_block, bands, threads, &s));
     s.lean = lean;
@@ -949,6 +974,10 @@ int autotune_level(mg3d_handle *h, int k, int *evaluated) {
     MG_TRY(launched(h, launch_opacity(h->prec, L.nvox, h->atom.g_ratio, h->atom.kappa, L.n,
                                       L.chi0, L.S, h->stream),
                     "opacity"));
+    if (h->params.sc_interp)
+        MG_TRY(launched(h, launch_xslopes(h->prec, L.nx, L.nvox, L.chi0, L.S, L.dchi0, L.dS,
+                                          h->stream),
+                        "x-slopes"));
     float warm = 0.f;
     MG_TRY(time_shape(h, k, L.shape, 1, &warm));
     std::vector<std::pair<float, size_t>> t1;
@@ -1024,10 +1053,16 @@ int create_impl(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_qu
         std::vector<double> tz(L.nz, 0.0);
         for (int i = 1; i + 1 < L.nz; i += 2) tz[i] = (L.z[i] - L.z[i - 1]) / (L.z[i + 1] - L.z[i - 1]);
         MG_CUDA(cudaMemcpy(L.tz, tz.data(), L.nz * sizeof(double), cudaMemcpyHostToDevice));
+        MG_TRY(dalloc(&L.zf, L.nz));
+        MG_CUDA(cudaMemcpy(L.zf, L.z.data(), L.nz * sizeof(double), cudaMemcpyHostToDevice));
         std::vector<StepGeom> g;
         build_geometry(h, L, g);
         MG_CUDA(cudaMemcpy(L.geom, g.data(), g.size() * sizeof(StepGeom), cudaMemcpyHostToDevice));
-        L.shape = choose_shape(h->prec, L.nx, L.ny, atom->n_freq);
+        L.shape = choose_shape(h->prec, L.nx, L.ny, atom->n_freq, params->sc_interp);
+        if (params->sc_interp) {
+            MG_TRY(dev_alloc(&L.dchi0, L.nvox * es));
+            MG_TRY(dev_alloc(&L.dS, L.nvox * es));
+        }
         if (L.shape.ng == 0) return fail(MG3D_E_ARG, "no sweep shape fits in shared memory");
         h->partial_elems = std::max(h->partial_elems,
                                     (size_t)kRays * L.shape.ngroups * (size_t)L.nvox);
@@ -1120,7 +1155,8 @@ void trapezoid_grid(double a, double b, int n, std::vector<double> &x, std::vect
 size_t ml_bytes_per_freq(const mg3d_handle *h) {
     const size_t es = elem_size(h->prec);
     size_t b = (h->scatter ? 3 : 2) * (size_t)h->ml_slots * h->lev[h->L].nvox * es;
-    for (int k = 1; k <= h->L; ++k) b += 4 * (size_t)h->lev[k].nvox * es;
+    const size_t per_level = h->params.sc_interp ? 6 : 4;  // Hermite: slopes of chi, S
+    for (int k = 1; k <= h->L; ++k) b += per_level * (size_t)h->lev[k].nvox * es;
     return b;
 }
 
@@ -1142,7 +1178,7 @@ int alloc_ml_chunks(mg3d_handle *h, int chunk) {
     const size_t es = elem_size(h->prec);
     for (int k = 1; k <= h->L; ++k) {
         Level &L = h->lev[k];
-        void **bufs[4] = {&L.mchi, &L.mS, &L.msl, &L.mfl};
+        void **bufs[6] = {&L.mchi, &L.mS, &L.msl, &L.mfl, &L.mdchi, &L.mdS};
         for (void **p : bufs) {
             if (*p) cudaFree(*p);
             *p = nullptr;
@@ -1155,8 +1191,9 @@ int alloc_ml_chunks(mg3d_handle *h, int chunk) {
     h->ml_chunk = 0;
     for (int k = 1; k <= h->L; ++k) {
         Level &L = h->lev[k];
-        void **bufs[4] = {&L.mchi, &L.mS, &L.msl, &L.mfl};
-        for (void **p : bufs) MG_TRY(dev_alloc(p, (size_t)chunk * L.nvox * es));
+        void **bufs[6] = {&L.mchi, &L.mS, &L.msl, &L.mfl, &L.mdchi, &L.mdS};
+        const int nbufs = h->params.sc_interp ? 6 : 4;
+        for (int i = 0; i < nbufs; ++i) MG_TRY(dev_alloc(bufs[i], (size_t)chunk * L.nvox * es));
     }
     const size_t nv = h->lev[h->L].nvox;
     MG_TRY(dev_alloc(&h->ml_jx, (size_t)h->ml_slots * chunk * nv * es));
@@ -1187,14 +1224,18 @@ int time_ml_shape(mg3d_handle *h, int k, int bands, int rpb, int threads, int nc
                                    (const double *)L.mchi, (const double *)L.mS,
                                    (const double *)L.msl, (const double *)L.mfl,
                                    (const double *)L.mib, L.geom, h->d_exp_tab, h->exp_l1,
-                                   h->exp_l2, (double *)h->ml_jx, (double *)h->ml_ux, rpb};
+                                   h->exp_l2, (double *)h->ml_jx, (double *)h->ml_ux, rpb,
+                                   nullptr, (const double *)L.mdchi, (const double *)L.mdS,
+                                   h->params.sc_interp};
             e = launch_ml_sweep_f64(sa, bands, threads, h->stream);
         } else {
             MlSweepArgs<float> sa{L.nx, L.ny, L.nz, nc, L.ml_rows,
                                   (const float *)L.mchi, (const float *)L.mS,
                                   (const float *)L.msl, (const float *)L.mfl,
                                   (const float *)L.mib, L.geom, h->d_exp_tab, h->exp_l1,
-                                  h->exp_l2, (float *)h->ml_jx, (float *)h->ml_ux, rpb};
+                                  h->exp_l2, (float *)h->ml_jx, (float *)h->ml_ux, rpb,
+                                  nullptr, (const float *)L.mdchi, (const float *)L.mdS,
+                                  h->params.sc_interp};
             e = launch_ml_sweep_f32(sa, bands, threads, h->stream);
         }
         ++h->launches;
@@ -1224,6 +1265,10 @@ int autotune_ml_level(mg3d_handle *h, int k, int nc, int *evaluated) {
                      L.n, L.T, L.chi_c, L.saha, L.mchi, L.mS, L.msl, L.mfl, 0,
                      h->d_exp_tab, h->exp_l1, h->exp_l2};
     MG_TRY(launched(h, launch_ml_opacity(oa, h->stream), "multi-level opacity"));
+    if (h->params.sc_interp)
+        MG_TRY(launched(h, launch_xslopes(h->prec, L.nx, (long)nc * L.nvox, L.mchi, L.mS, L.mdchi,
+                                          L.mdS, h->stream),
+                        "x-slopes"));
     struct Cand {
         int bands, rpb, threads;
     };
@@ -1232,7 +1277,9 @@ int autotune_ml_level(mg3d_handle *h, int k, int nc, int *evaluated) {
         for (int bands = 1; bands <= kPortableBands && bands <= L.ny; ++bands) {
             const int rows = (L.ny + bands - 1) / bands;
             if ((long)(bands - 1) * rows >= L.ny) continue;
-            if (ml_sweep_smem_bytes(h->prec, rows, L.nx, rpb) > kMaxSweepSmem) continue;
+            if (ml_sweep_smem_bytes(h->prec, rows, L.nx, rpb, h->params.sc_interp) >
+                kMaxSweepSmem)
+                continue;
             for (int th : {128, 256, 512}) {
                 if (th > 128 && th / 2 >= rows * L.nx) continue;  // a smaller block covers it
                 cands.push_back(Cand{bands, rpb, th});
@@ -1372,6 +1419,8 @@ int create_ml_impl(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
         std::vector<double> tz(L.nz, 0.0);
         for (int i = 1; i + 1 < L.nz; i += 2) tz[i] = (L.z[i] - L.z[i - 1]) / (L.z[i + 1] - L.z[i - 1]);
         MG_CUDA(cudaMemcpy(L.tz, tz.data(), L.nz * sizeof(double), cudaMemcpyHostToDevice));
+        MG_TRY(dalloc(&L.zf, L.nz));
+        MG_CUDA(cudaMemcpy(L.zf, L.z.data(), L.nz * sizeof(double), cudaMemcpyHostToDevice));
         std::vector<StepGeom> g;
         build_geometry(h, L, g);
         MG_CUDA(cudaMemcpy(L.geom, g.data(), g.size() * sizeof(StepGeom), cudaMemcpyHostToDevice));
@@ -1383,7 +1432,9 @@ int create_ml_impl(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
             for (int b = 1; b <= kPortableBands && b <= L.ny; ++b) {
                 const int rows = (L.ny + b - 1) / b;
                 if ((long)(b - 1) * rows >= L.ny) continue;
-                if (ml_sweep_smem_bytes(h->prec, rows, L.nx, rpb) > kMaxSweepSmem) continue;
+                if (ml_sweep_smem_bytes(h->prec, rows, L.nx, rpb, params->sc_interp) >
+                    kMaxSweepSmem)
+                    continue;
                 pick = b;
                 if (2L * (12 / rpb) * nf * b >= 300) break;
             }
@@ -1658,9 +1709,11 @@ int batch_vcycle(mg3d_batch *b, int k, bool first) {
     for (mg3d_handle *h : b->m) {
         Level &F = h->lev[k];
         Level &C = h->lev[k - 1];
-        MG_TRY(batch_launched(b, launch_prolong_correct(h->N, C.nx, C.ny, C.nz, F.tz, C.n,
-                                                        C.n_before, F.n, h->scal, b->stream),
+        MG_TRY(batch_launched(b, launch_prolong_correct(h->params.interpolation, h->N, C.nx, C.ny,
+                                                        C.nz, F.tz, F.zf, C.n, C.n_before, F.n,
+                                                        h->scal, b->stream),
                               "prolong correction"));
+        if (h->params.interpolation) ++b->launches;
     }
     for (int i = 0; i < b->params.nu2; ++i) MG_TRY(batch_sweep(b, k));
     return MG3D_OK;
@@ -1937,6 +1990,10 @@ int mg3d_create(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_qu
         return fail(MG3D_E_ARG, "negative iteration count");
     if (params->restriction < 0 || params->restriction > 2)
         return fail(MG3D_E_ARG, "restriction must be 0, 1 or 2");
+    if (params->interpolation < 0 || params->interpolation > 1)
+        return fail(MG3D_E_ARG, "interpolation must be 0 or 1");
+    if (params->sc_interp < 0 || params->sc_interp > 1)
+        return fail(MG3D_E_ARG, "sc_interp must be 0 or 1");
     if (atom->n_freq < 1 || atom->n_freq > 4096 || !(atom->x_max >= 0.0) ||
         !(atom->a_ul > 0.0) || !(atom->g_ratio > 0.0) || !(atom->theta > 0.0) ||
         !(atom->kappa > 0.0))
@@ -2006,6 +2063,10 @@ int mg3d_create_ml(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
         return fail(MG3D_E_ARG, "negative iteration count");
     if (params->restriction < 0 || params->restriction > 2)
         return fail(MG3D_E_ARG, "restriction must be 0, 1 or 2");
+    if (params->interpolation < 0 || params->interpolation > 1)
+        return fail(MG3D_E_ARG, "interpolation must be 0 or 1");
+    if (params->sc_interp < 0 || params->sc_interp > 1)
+        return fail(MG3D_E_ARG, "sc_interp must be 0 or 1");
     if (atm->nx < 1 || atm->ny < 1 || atm->nz < 2) return fail(MG3D_E_ARG, "grid too small");
     if (atm->nx >= 65536 || atm->ny >= 65536)
         return fail(MG3D_E_ARG, "nx and ny must be below 65536");
@@ -2103,7 +2164,8 @@ int mg3d_set_ml_shape(mg3d_handle *h, int level, int bands, int rays_per_block, 
         return fail(MG3D_E_ARG, "rays_per_block must divide 12");
     if (threads < 32 || threads > kMaxSweepThreads || threads % 32)
         return fail(MG3D_E_ARG, "threads must be a multiple of 32 up to 512");
-    if (ml_sweep_smem_bytes(h->prec, rows, L.nx, rays_per_block) > kMaxSweepSmem)
+    if (ml_sweep_smem_bytes(h->prec, rows, L.nx, rays_per_block, h->params.sc_interp) >
+        kMaxSweepSmem)
         return fail(MG3D_E_ARG, "multi-level sweep shape exceeds shared memory");
     MG_CUDA(cudaStreamSynchronize(h->stream));
     L.ml_bands = bands;
@@ -2145,6 +2207,8 @@ int mg3d_batch_create(int n, mg3d_handle *const *members, mg3d_batch **out) {
         if (!members[i]) return fail(MG3D_E_ARG, "null member");
         if (members[i]->scatter)
             return fail(MG3D_E_ARG, "batches do not take background scattering");
+        if (members[i]->params.sc_interp)
+            return fail(MG3D_E_ARG, "batches do not take Hermite upwind interpolation");
         for (int j = 0; j < i; ++j)
             if (members[j] == members[i]) return fail(MG3D_E_ARG, "member listed twice");
     }
@@ -2154,7 +2218,8 @@ int mg3d_batch_create(int n, mg3d_handle *const *members, mg3d_batch **out) {
         const mg3d_params &p = h->params, &q = h0->params;
         if (h->L != h0->L || h->prec != h0->prec || p.nu0 != q.nu0 || p.nu1 != q.nu1 ||
             p.nu2 != q.nu2 || p.nu3 != q.nu3 || p.nu_fmg != q.nu_fmg ||
-            p.restriction != q.restriction)
+            p.restriction != q.restriction || p.interpolation != q.interpolation ||
+            p.sc_interp != q.sc_interp)
             return fail(MG3D_E_ARG, "batch members need equal n_grids, precision and schedule");
     }
 
@@ -2272,8 +2337,8 @@ int mg3d_batch_fmg_solve(mg3d_batch *b, double tol, int max_cycles, mg3d_stats *
         for (mg3d_handle *h : b->m) {
             Level &Fk = h->lev[k];
             Level &Ck = h->lev[k - 1];
-            MG_TRY(batch_launched(b, launch_prolong(h->N, Ck.nx, Ck.ny, Ck.nz, Fk.tz, Ck.n, Fk.n,
-                                                    b->stream),
+            MG_TRY(batch_launched(b, launch_prolong(h->params.interpolation, h->N, Ck.nx, Ck.ny,
+                                                    Ck.nz, Fk.tz, Fk.zf, Ck.n, Fk.n, b->stream),
                                   "prolong full approximation"));
             Fk.f_default = true;
         }
@@ -2471,11 +2536,13 @@ int mg3d_fmg_solve(mg3d_handle *h, double tol, int max_cycles, mg3d_stats *stats
     for (int k = 2; k <= h->L; ++k) {
         Level &Fk = h->lev[k];
         Level &Ck = h->lev[k - 1];
-        MG_TRY(launched(h, launch_prolong(h->N, Ck.nx, Ck.ny, Ck.nz, Fk.tz, Ck.n, Fk.n, h->stream),
+        MG_TRY(launched(h, launch_prolong(h->params.interpolation, h->N, Ck.nx, Ck.ny, Ck.nz,
+                                          Fk.tz, Fk.zf, Ck.n, Fk.n, h->stream),
                         "prolong full approximation"));
         if (h->kind == 1 && h->scatter)
-            MG_TRY(launched(h, launch_prolong_prec(h->prec, h->nfreq_ml, Ck.nx, Ck.ny, Ck.nz,
-                                                   Fk.tz, Ck.jbg, Fk.jbg, h->stream),
+            MG_TRY(launched(h, launch_prolong_prec(h->params.interpolation, h->prec, h->nfreq_ml,
+                                                   Ck.nx, Ck.ny, Ck.nz, Fk.tz, Fk.zf, Ck.jbg,
+                                                   Fk.jbg, h->stream),
                             "prolong background field"));
         Fk.f_default = true;
         if (k < h->L) {
@@ -2534,7 +2601,8 @@ int mg3d_prolong(mg3d_handle *h, int level_fine, int ncomp, const double *coarse
     int rc = dalloc(&dfine, (size_t)ncomp * F.nvox);
     if (rc == MG3D_OK) rc = host_to_level(h, dcoarse, coarse_host, (size_t)ncomp * C.nvox);
     if (rc == MG3D_OK)
-        rc = launched(h, launch_prolong(ncomp, C.nx, C.ny, C.nz, F.tz, dcoarse, dfine, h->stream),
+        rc = launched(h, launch_prolong(h->params.interpolation, ncomp, C.nx, C.ny, C.nz, F.tz,
+                                        F.zf, dcoarse, dfine, h->stream),
                       "prolong");
     if (rc == MG3D_OK) rc = level_to_host(h, fine_host, dfine, (size_t)ncomp * F.nvox);
     cudaFree(dcoarse);

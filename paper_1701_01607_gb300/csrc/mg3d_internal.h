@@ -35,6 +35,7 @@ struct SweepShape {
     int lean = 0; // register budget: 0 full, 1: 1024 resident threads per SM (64
                   // registers), 2: three 256-thread blocks per SM (85 registers)
     int stage = 1; // 1: chi0/S rows staged in shared memory one step ahead
+    int herm = 0;  // 1: monotone cubic Hermite upwind interpolation (unstaged)
 };
 
 // Arguments of the sweep kernel.  T is the formal-solution precision.
@@ -51,8 +52,9 @@ struct SweepArgs {
     const T *inv_phi;        // [nfreq] 1/profile
     const T *wphi;           // [nfreq] ray weight x frequency weight x profile
     T *pj, *pu;              // [kRays*ngroups][nvox] partial Jeff and U
-    const double *exp_tab;   // [64] 2^{j/64} for the FP64 exp (FP64 sweeps only)
-    double exp_l1, exp_l2;   // two-part ln2/64
+    const double *exp_tab;   // [kExpTab] 2^{j/kExpTab} for the FP64 exp (FP64 sweeps only)
+    double exp_l1, exp_l2;   // two-part ln2/kExpTab
+    const T *dchi0, *dS;     // [nvox] x-slopes of chi0 and S (Hermite sweeps only)
 };
 
 // Table and reduction constants of the FP64 e^{-x} of the sweep.
@@ -61,6 +63,9 @@ cudaError_t launch_exp_check(int n, const double *x, double *out, const double *
                              double l2, cudaStream_t st);
 
 size_t sweep_smem_bytes(int prec, const SweepShape &s, int nx);
+// Monotone x-slopes (one cell units, periodic rows of nx) of a and b.
+cudaError_t launch_xslopes(int prec, int nx, long nvox, const void *a, const void *b, void *da,
+                           void *db, cudaStream_t st);
 
 // One cluster of a batched sweep: problem index, ray (two-level) or
 // hemisphere (multi-level), frequency group (two-level) or frequency.
@@ -110,18 +115,24 @@ cudaError_t launch_collisions_up(long nvox, double g_ratio, double theta, const 
 // mode: 0 full weighting, 1 half weighting, 2 injection
 cudaError_t launch_restrict(int ncomp, int nxf, int nyf, int nzf, const double *fine,
                             double *coarse, cudaStream_t st, int mode = 0);
-// The same operators (full weighting, trilinear) on arrays of the
-// formal-solution precision (prec 0 FP64, 1 FP32), accumulated in FP64.
+// The same operators (full weighting; trilinear or Hermite) on arrays of
+// the formal-solution precision (prec 0 FP64, 1 FP32), accumulated in FP64.
 cudaError_t launch_restrict_prec(int prec, int ncomp, int nxf, int nyf, int nzf,
                                  const void *fine, void *coarse, cudaStream_t st);
-cudaError_t launch_prolong_prec(int prec, int ncomp, int nxc, int nyc, int nzc,
-                                const double *tz, const void *coarse, void *fine,
-                                cudaStream_t st);
-cudaError_t launch_prolong(int ncomp, int nxc, int nyc, int nzc, const double *tz,
-                           const double *coarse, double *fine, cudaStream_t st);
-cudaError_t launch_prolong_correct(int ncomp, int nxc, int nyc, int nzc, const double *tz,
-                                   const double *n_after, const double *n_before,
-                                   double *n_fine, unsigned long long *scal,
+// Interpolation onto the fine grid (Sec. 4.5): interp 0 trilinear (tz: the
+// fine grid's upper-plane weights), 1 monotone cubic Hermite (zf: the fine
+// grid's heights).
+cudaError_t launch_prolong_prec(int interp, int prec, int ncomp, int nxc, int nyc, int nzc,
+                                const double *tz, const double *zf, const void *coarse,
+                                void *fine, cudaStream_t st);
+cudaError_t launch_prolong(int interp, int ncomp, int nxc, int nyc, int nzc, const double *tz,
+                           const double *zf, const double *coarse, double *fine,
+                           cudaStream_t st);
+// Eqs. 10-11 with the 10 % rule; the Hermite variant first overwrites
+// n_before with the relative correction.
+cudaError_t launch_prolong_correct(int interp, int ncomp, int nxc, int nyc, int nzc,
+                                   const double *tz, const double *zf, const double *n_after,
+                                   double *n_before, double *n_fine, unsigned long long *scal,
                                    cudaStream_t st);
 cudaError_t launch_max_rel_change(long len, const double *n_new, const double *n_old,
                                   unsigned long long *scal, cudaStream_t st);
@@ -160,6 +171,8 @@ struct MlSweepArgs {
     T *jx, *ux;                   // [2 * 12 / rpb slots][nfreq][nvox]
     int rpb;                      // rays per block: 12, 6, 4, 3, 2 or 1 of a hemisphere
     T *jm;                        // mean intensity sum_r w_r I per slot, or null
+    const T *dchi, *dS;           // [nfreq][nvox] x-slopes of chi and S (herm only)
+    int herm;                     // 1: monotone cubic Hermite upwind interpolation
 };
 
 // Opacity of the chunk of frequencies f0 .. f0+nfreq-1, written at the
@@ -213,7 +226,7 @@ struct MlRateArgs {
     unsigned long long *scal;
 };
 
-size_t ml_sweep_smem_bytes(int prec, int rows, int nx, int rpb);
+size_t ml_sweep_smem_bytes(int prec, int rows, int nx, int rpb, int herm = 0);
 cudaError_t launch_ml_opacity(const MlOpacityArgs &a, cudaStream_t st);
 cudaError_t launch_ml_bottom(int prec, long nplane, int nfreq, const FreqInfo *fi,
                              double theta_ref, const double *T, void *ib, cudaStream_t st);

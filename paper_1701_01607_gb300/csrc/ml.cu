@@ -150,7 +150,12 @@ __global__ void ml_bottom_kernel(long nplane, int nfreq, const FreqInfo *__restr
 
 // -------------------------------------------------------------------- sweep
 
-template <typename T>
+// HERM: monotone cubic Hermite upwind interpolation (the Hermite-spline
+// option of Sec. 3): per ray and local row the table holds the four upwind
+// rows ya-1 .. ya+2 of the intensity and slope planes and of chi, S; each
+// finished plane gets its x-slopes after a block barrier; chi and S take
+// theirs from dchi, dS.
+template <typename T, bool HERM>
 __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, int slot) {
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
@@ -183,7 +188,13 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
         const T *pa, *pb;
         int ra, rb;
     };
-    RowRef *rowref = reinterpret_cast<RowRef *>(buf + 2 * bufstride);
+    struct RowRef4 {
+        const T *p[4], *d[4];
+        int r[4];
+    };
+    T *dbuf = buf + 2 * bufstride;  // slope planes (HERM)
+    RowRef *rowref = reinterpret_cast<RowRef *>(buf + (HERM ? 4 : 2) * bufstride);
+    RowRef4 *rowref4 = reinterpret_cast<RowRef4 *>(rowref);
     __shared__ double exp_tab[kExpTab];
     if (sizeof(T) == 8) {
         for (int i = threadIdx.x; i < kExpTab; i += blockDim.x) exp_tab[i] = a.exp_tab[i];
@@ -194,9 +205,12 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
     const unsigned long long rmagic = band_magic(rows);
     // per-ray constants of the current step (the upwind offset is the same
     // for every node of a plane): bilinear weights, half path, corner offsets
-    __shared__ T g_w[12][4];
+    __shared__ T g_w[12][4];        // bilinear weights, or the x and y Hermite
+    __shared__ T g_wy[12][4];       // bases (HERM)
     __shared__ T g_hs[12];
     __shared__ int g_ix[12];
+    const T *__restrict__ dchif = HERM ? a.dchi + (long)f * nvox : nullptr;
+    const T *__restrict__ dSf = HERM ? a.dS + (long)f * nvox : nullptr;
 
     for (int t = 0; t < nz; ++t) {
         const int k = up ? t : nz - 1 - t;
@@ -217,10 +231,22 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
             if (threadIdx.x < rpb) {
                 const StepGeom o = a.geom[(long)(r0 + threadIdx.x) * nz + t];
                 const T tx = (T)o.tx, ty = (T)o.ty;
-                g_w[threadIdx.x][0] = (T(1) - tx) * (T(1) - ty);
-                g_w[threadIdx.x][1] = tx * (T(1) - ty);
-                g_w[threadIdx.x][2] = (T(1) - tx) * ty;
-                g_w[threadIdx.x][3] = tx * ty;
+                if constexpr (HERM) {
+                    const HermiteBasis<T> bx(tx), by(ty);
+                    g_w[threadIdx.x][0] = bx.c0;
+                    g_w[threadIdx.x][1] = bx.c1;
+                    g_w[threadIdx.x][2] = bx.c2;
+                    g_w[threadIdx.x][3] = bx.c3;
+                    g_wy[threadIdx.x][0] = by.c0;
+                    g_wy[threadIdx.x][1] = by.c1;
+                    g_wy[threadIdx.x][2] = by.c2;
+                    g_wy[threadIdx.x][3] = by.c3;
+                } else {
+                    g_w[threadIdx.x][0] = (T(1) - tx) * (T(1) - ty);
+                    g_w[threadIdx.x][1] = tx * (T(1) - ty);
+                    g_w[threadIdx.x][2] = (T(1) - tx) * ty;
+                    g_w[threadIdx.x][3] = tx * ty;
+                }
                 g_hs[threadIdx.x] = T(0.5) * (T)o.s;
                 g_ix[threadIdx.x] = o.ix0;
             }
@@ -229,6 +255,20 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
                 int ya = y0 + yl + a.geom[(long)(r0 + j) * nz + t].iy0;
                 if (ya >= ny) ya -= ny;
                 const int yb = (ya + 1 == ny) ? 0 : ya + 1;
+                if constexpr (HERM) {
+                    const T *dprev = dbuf + ((t - 1) & 1) * bufstride;
+                    int yr[4] = {ya == 0 ? ny - 1 : ya - 1, ya, yb, yb + 1 == ny ? 0 : yb + 1};
+                    RowRef4 r4;
+                    for (int m = 0; m < 4; ++m) {
+                        const int b = band_of(yr[m], rmagic);
+                        const long ro = j * raystride + (long)(yr[m] - b * rows) * nx;
+                        r4.p[m] = (b == rank ? prev : cluster.map_shared_rank(prev, b)) + ro;
+                        r4.d[m] = (b == rank ? dprev : cluster.map_shared_rank(dprev, b)) + ro;
+                        r4.r[m] = yr[m] * nx;
+                    }
+                    rowref4[j * rows + yl] = r4;
+                    continue;
+                }
                 const int ba = band_of(ya, rmagic), bb = band_of(yb, rmagic);
                 const T *Pa = (ba == rank) ? prev : cluster.map_shared_rank(prev, ba);
                 const T *Pb = (bb == rank) ? prev : cluster.map_shared_rank(prev, bb);
@@ -251,6 +291,40 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
                 // sl and fl are the node's: sum I and w0 over the rays and
                 // form Jx = sum I - sl sum w0, Ux = rays - fl sum w0 once
                 T sum_i = 0, sum_w0 = 0;
+                if constexpr (HERM) {
+                    for (int j = 0; j < rpb; ++j) {
+                        int xa = x + g_ix[j];
+                        if (xa >= nx) xa -= nx;
+                        const int xb = (xa + 1 == nx) ? 0 : xa + 1;
+                        const RowRef4 &r4 = rowref4[j * rows + yl];
+                        const T c0 = g_w[j][0], c1 = g_w[j][1], c2 = g_w[j][2], c3 = g_w[j][3];
+                        const T e0 = g_wy[j][0], e1 = g_wy[j][1], e2 = g_wy[j][2], e3 = g_wy[j][3];
+                        // x pass on four rows, then y pass through their values
+                        auto up2d = [&](auto value_row, auto slope_row) {
+                            T gq[4];
+#pragma unroll
+                            for (int m = 0; m < 4; ++m) {
+                                const T *v = value_row(m), *d = slope_row(m);
+                                gq[m] = c0 * v[xa] + c1 * d[xa] + c2 * v[xb] + c3 * d[xb];
+                            }
+                            return e0 * gq[1] + e1 * mono_slope(gq[1] - gq[0], gq[2] - gq[1]) +
+                                   e2 * gq[2] + e3 * mono_slope(gq[2] - gq[1], gq[3] - gq[2]);
+                        };
+                        const T chi_up = up2d([&](int m) { return chip + r4.r[m]; },
+                                              [&](int m) { return dchif + (long)kp * nplane + r4.r[m]; });
+                        const T S_up = up2d([&](int m) { return Sp + r4.r[m]; },
+                                            [&](int m) { return dSf + (long)kp * nplane + r4.r[m]; });
+                        const T I_up = up2d([&](int m) { return r4.p[m]; },
+                                            [&](int m) { return r4.d[m]; });
+                        const T x_tau = (chi_up + chi_loc) * g_hs[j];
+                        T ex, w0, wup, u;
+                        ScWeights<T>::eval(x_tau, rcp(x_tau), et, ex, w0, wup, u);
+                        const T I = I_up * ex + wup * S_up + w0 * S_loc;
+                        cur[j * raystride + (long)yl * nx + x] = I;
+                        sum_i += I;
+                        sum_w0 += w0;
+                    }
+                } else
                 for (int j = 0; j < rpb; ++j) {
                     const T w00 = g_w[j][0], w10 = g_w[j][1], w01 = g_w[j][2], w11 = g_w[j][3];
                     int xa = x + g_ix[j];
@@ -276,13 +350,26 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
                 if (jmo) jmo[v] = wray * sum_i;
             }
         }
+        if constexpr (HERM) {
+            // x-slopes of the new planes; a band holds whole rows
+            __syncthreads();
+            T *dcur = dbuf + (t & 1) * bufstride;
+            for (int i = threadIdx.x; i < rpb * band; i += blockDim.x) {
+                const int j = i / band, q = i - j * band;
+                const int yl = q / nx, x = q - yl * nx;
+                const int xm = x == 0 ? nx - 1 : x - 1, xp = x + 1 == nx ? 0 : x + 1;
+                const T *row = cur + j * raystride + (long)yl * nx;
+                dcur[j * raystride + (long)yl * nx + x] =
+                    mono_slope(row[x] - row[xm], row[xp] - row[x]);
+            }
+        }
         cluster.sync();
     }
 }
 
-template <typename T, int MAXT>
+template <typename T, int MAXT, bool HERM>
 __global__ void __launch_bounds__(MAXT) ml_sweep_kernel(const MlSweepArgs<T> a) {
-    ml_sweep_body<T>(a, blockIdx.y, blockIdx.z);
+    ml_sweep_body<T, HERM>(a, blockIdx.y, blockIdx.z);
 }
 
 // Batched: item y = (problem, ray-group slot as ray, frequency as group).
@@ -291,23 +378,27 @@ __global__ void __launch_bounds__(MAXT) ml_sweep_batch_kernel(
     const MlSweepArgs<T> *__restrict__ args, const BatchItem *__restrict__ items) {
     const BatchItem it = items[blockIdx.y];
     const MlSweepArgs<T> a = args[it.member];
-    ml_sweep_body<T>(a, it.group, it.ray);
+    ml_sweep_body<T, false>(a, it.group, it.ray);
 }
 
-size_t ml_sweep_smem_bytes(int prec, int rows, int nx, int rpb) {
+size_t ml_sweep_smem_bytes(int prec, int rows, int nx, int rpb, int herm) {
     const size_t elem = prec == MG3D_PREC_F64 ? sizeof(double) : sizeof(float);
-    // intensity planes, then the per-(ray, row) upwind row table (two
-    // pointers and two offsets, 24 bytes; the planes end on an 8-byte boundary)
+    // intensity planes (and their slope planes), then the per-(ray, row)
+    // upwind row table: two pointers and two offsets (24 bytes), or eight
+    // pointers and four offsets (80 bytes); the planes end on an 8-byte
+    // boundary
+    if (herm) return 4ull * rpb * rows * nx * elem + 80ull * rpb * rows;
     return 2ull * rpb * rows * nx * elem + 24ull * rpb * rows;
 }
 
-template <typename T, int MAXT>
+template <typename T, int MAXT, bool HERM>
 static cudaError_t launch_ml_sweep_t(const MlSweepArgs<T> &a, int bands, int threads,
                                      cudaStream_t st) {
     const size_t smem = ml_sweep_smem_bytes(sizeof(T) == 8 ? MG3D_PREC_F64 : MG3D_PREC_F32,
-                                            a.rows, a.nx, a.rpb);
+                                            a.rows, a.nx, a.rpb, HERM ? 1 : 0);
+    if (HERM && (!a.dchi || !a.dS)) return cudaErrorInvalidValue;
     // one fixed limit for every launch, so graph replays never meet a lower one
-    cudaError_t e = cudaFuncSetAttribute(ml_sweep_kernel<T, MAXT>,
+    cudaError_t e = cudaFuncSetAttribute(ml_sweep_kernel<T, MAXT, HERM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kMaxSweepSmem);
     if (e != cudaSuccess) return e;
@@ -323,7 +414,7 @@ static cudaError_t launch_ml_sweep_t(const MlSweepArgs<T> &a, int bands, int thr
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = bands > 1 ? 1 : 0;  // one band: a plain launch
-    return cudaLaunchKernelEx(&cfg, ml_sweep_kernel<T, MAXT>, a);
+    return cudaLaunchKernelEx(&cfg, ml_sweep_kernel<T, MAXT, HERM>, a);
 }
 
 template <typename T, int MAXT>
@@ -366,16 +457,24 @@ cudaError_t launch_ml_sweep_batch(int prec, const void *args, const BatchItem *i
                                                      n_items, bands, threads, smem, st);
 }
 
+template <typename T>
+static cudaError_t launch_ml_sweep_any(const MlSweepArgs<T> &a, int bands, int threads,
+                                       cudaStream_t st) {
+    if (a.herm)
+        return threads <= 256 ? launch_ml_sweep_t<T, 256, true>(a, bands, threads, st)
+                              : launch_ml_sweep_t<T, 512, true>(a, bands, threads, st);
+    return threads <= 256 ? launch_ml_sweep_t<T, 256, false>(a, bands, threads, st)
+                          : launch_ml_sweep_t<T, 512, false>(a, bands, threads, st);
+}
+
 cudaError_t launch_ml_sweep_f64(const MlSweepArgs<double> &a, int bands, int threads,
                                 cudaStream_t st) {
-    return threads <= 256 ? launch_ml_sweep_t<double, 256>(a, bands, threads, st)
-                          : launch_ml_sweep_t<double, 512>(a, bands, threads, st);
+    return launch_ml_sweep_any<double>(a, bands, threads, st);
 }
 
 cudaError_t launch_ml_sweep_f32(const MlSweepArgs<float> &a, int bands, int threads,
                                 cudaStream_t st) {
-    return threads <= 256 ? launch_ml_sweep_t<float, 256>(a, bands, threads, st)
-                          : launch_ml_sweep_t<float, 512>(a, bands, threads, st);
+    return launch_ml_sweep_any<float>(a, bands, threads, st);
 }
 
 // -------------------------------------------------------------------- rates

@@ -333,19 +333,184 @@ __global__ void __launch_bounds__(256) prolong_correct_kernel(
     if (threadIdx.x == 0 && tn && scal) atomicAdd(scal + 3, (unsigned long long)tn);
 }
 
-cudaError_t launch_prolong(int ncomp, int nxc, int nyc, int nzc, const double *tz,
-                           const double *coarse, double *fine, cudaStream_t st) {
+// ------------------------------------ monotone cubic Hermite prolongation
+// The other interpolation operator of Sec. 4.5: monotone cubic Hermite
+// (Auer 2003) in successive 1D passes along x and y (periodic, uniform) and
+// then z (at the physical heights).  On an odd index of an axis the fine
+// node lies between two coarse nodes and takes the cubic through them, with
+// slopes from their neighbours: the harmonic mean of the two adjacent
+// secants where they have the same strict sign, else 0 (Fritsch & Butland
+// 1984), weighted by the spacings in z, where the end nodes take the
+// shape-preserving three-point slope.  On an even index the fine node keeps
+// the coarse value along that axis.  A fine node reads the 4 x 4 x 4 coarse
+// nodes around it, and each pass stays between the two coarse values of its
+// interval.
+
+__device__ __forceinline__ double mono_slope_unit(double a, double b) {
+    return ((a > 0.0 && b > 0.0) || (a < 0.0 && b < 0.0)) ? 2.0 * a * b / (a + b) : 0.0;
+}
+
+// cubic through q1, q2 at the midpoint, unit spacing
+__device__ __forceinline__ double hermite_half(double q0, double q1, double q2, double q3) {
+    const double d1 = mono_slope_unit(q1 - q0, q2 - q1);
+    const double d2 = mono_slope_unit(q2 - q1, q3 - q2);
+    return 0.5 * (q1 + q2) + 0.125 * (d1 - d2);
+}
+
+__device__ __forceinline__ int sign_of(double v) { return (v > 0.0) - (v < 0.0); }
+
+__device__ __forceinline__ double slope_inner(double dm, double dp, double hm, double hp) {
+    if (!((dm > 0.0 && dp > 0.0) || (dm < 0.0 && dp < 0.0))) return 0.0;
+    const double w1 = 2.0 * hp + hm, w2 = hp + 2.0 * hm;
+    return (w1 + w2) / (w1 / dm + w2 / dp);
+}
+
+// slope at an end node from the secant d0 of its interval (length h0) and
+// the next one, d1 (length h1)
+__device__ __forceinline__ double slope_end(double d0, double d1, double h0, double h1) {
+    const double s = ((2.0 * h0 + h1) * d0 - h0 * d1) / (h0 + h1);
+    if (sign_of(s) != sign_of(d0)) return 0.0;
+    if (sign_of(d0) != sign_of(d1) && fabs(s) > 3.0 * fabs(d0)) return 3.0 * d0;
+    return s;
+}
+
+// x then y pass on coarse plane kk for fine column (i, j); get(kk, y, x)
+// returns a coarse value
+template <typename Get>
+__device__ __forceinline__ double hermite_xy(const Get &get, int kk, int i, int j, int nxc,
+                                             int nyc) {
+    auto xrow = [&](int yy) -> double {
+        const int i0 = i >> 1;
+        if (!(i & 1)) return get(kk, yy, i0);
+        const int im = i0 == 0 ? nxc - 1 : i0 - 1;
+        const int i1 = i0 + 1 == nxc ? 0 : i0 + 1;
+        const int i2 = i1 + 1 == nxc ? 0 : i1 + 1;
+        return hermite_half(get(kk, yy, im), get(kk, yy, i0), get(kk, yy, i1), get(kk, yy, i2));
+    };
+    const int j0 = j >> 1;
+    if (!(j & 1)) return xrow(j0);
+    const int jm = j0 == 0 ? nyc - 1 : j0 - 1;
+    const int j1 = j0 + 1 == nyc ? 0 : j0 + 1;
+    const int j2 = j1 + 1 == nyc ? 0 : j1 + 1;
+    return hermite_half(xrow(jm), xrow(j0), xrow(j1), xrow(j2));
+}
+
+// the fine value at fine node f; zf: the fine grid's heights (coarse plane
+// m at zf[2m])
+template <typename Get>
+__device__ double hermite_fine(const Get &get, long f, int nxc, int nyc, int nzc,
+                               const double *__restrict__ zf) {
+    const int nxf = 2 * nxc, nyf = 2 * nyc;
+    const int i = (int)(f % nxf);
+    const int j = (int)((f / nxf) % nyf);
+    const int k = (int)(f / ((long)nxf * nyf));
+    const int K = k >> 1;
+    if (!(k & 1)) return hermite_xy(get, K, i, j, nxc, nyc);
+    const double zK = zf[2 * K], zK1 = zf[2 * K + 2];
+    const double h = zK1 - zK;
+    const double qK = hermite_xy(get, K, i, j, nxc, nyc);
+    const double qK1 = hermite_xy(get, K + 1, i, j, nxc, nyc);
+    const double dK = (qK1 - qK) / h;
+    double sK = dK, sK1 = dK;
+    if (nzc > 2) {
+        double dm = 0.0, hm = 0.0;
+        if (K > 0) {
+            hm = zK - zf[2 * K - 2];
+            dm = (qK - hermite_xy(get, K - 1, i, j, nxc, nyc)) / hm;
+        }
+        double dp = 0.0, hp = 0.0;
+        if (K + 2 < nzc) {
+            hp = zf[2 * K + 4] - zK1;
+            dp = (hermite_xy(get, K + 2, i, j, nxc, nyc) - qK1) / hp;
+        }
+        sK = K > 0 ? slope_inner(dm, dK, hm, h) : slope_end(dK, dp, h, hp);
+        sK1 = K + 2 < nzc ? slope_inner(dK, dp, h, hp) : slope_end(dK, dm, h, hm);
+    }
+    const double t = (zf[k] - zK) / h, t2 = t * t, t3 = t2 * t;
+    return (2.0 * t3 - 3.0 * t2 + 1.0) * qK + (t3 - 2.0 * t2 + t) * h * sK +
+           (-2.0 * t3 + 3.0 * t2) * qK1 + (t3 - t2) * h * sK1;
+}
+
+template <typename V>
+__global__ void __launch_bounds__(256) prolong_hermite_kernel(
+    int ncomp, int nxc, int nyc, int nzc, const double *__restrict__ zf,
+    const V *__restrict__ coarse, V *__restrict__ fine) {
     const long nvf = (long)(2 * nxc) * (2 * nyc) * (2 * nzc - 1);
-    prolong_kernel<double><<<grid_for(nvf, 256), 256, 0, st>>>(ncomp, nxc, nyc, nzc, tz, coarse,
-                                                                 fine);
+    const long nvc = (long)nxc * nyc * nzc;
+    for (long f = blockIdx.x * (long)blockDim.x + threadIdx.x; f < nvf;
+         f += (long)gridDim.x * blockDim.x) {
+        for (int comp = 0; comp < ncomp; ++comp) {
+            const V *C = coarse + comp * nvc;
+            auto get = [&](int kk, int yy, int xx) -> double {
+                return (double)C[((long)kk * nyc + yy) * nxc + xx];
+            };
+            fine[comp * nvf + f] = (V)hermite_fine(get, f, nxc, nyc, nzc, zf);
+        }
+    }
+}
+
+// e = (n_after - n_before)/n_before written over n_before (Eq. 10)
+__global__ void rel_correction_kernel(long len, const double *__restrict__ n_after,
+                                      double *__restrict__ n_before) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < len;
+         i += (long)gridDim.x * blockDim.x)
+        n_before[i] = (n_after[i] - n_before[i]) / n_before[i];
+}
+
+// n_fine <- n_fine (1 + I(e)) with the Hermite I, and the 10 % rule
+__global__ void __launch_bounds__(256) prolong_correct_hermite_kernel(
+    int ncomp, int nxc, int nyc, int nzc, const double *__restrict__ zf,
+    const double *__restrict__ e, double *__restrict__ n_fine, unsigned long long *scal) {
+    const long nvf = (long)(2 * nxc) * (2 * nyc) * (2 * nzc - 1);
+    const long nvc = (long)nxc * nyc * nzc;
+    unsigned neg = 0;
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long base = (long)blockIdx.x * blockDim.x; base < nvf; base += stride) {
+        const long f = base + threadIdx.x;
+        if (f >= nvf) continue;
+        for (int comp = 0; comp < ncomp; ++comp) {
+            const double *E = e + comp * nvc;
+            auto get = [&](int kk, int yy, int xx) -> double {
+                return E[((long)kk * nyc + yy) * nxc + xx];
+            };
+            const double ie = hermite_fine(get, f, nxc, nyc, nzc, zf);
+            const double old = n_fine[comp * nvf + f];
+            double nw = old * (1.0 + ie);
+            if (nw <= 0.0) {
+                nw = 0.1 * old;
+                ++neg;
+            }
+            n_fine[comp * nvf + f] = nw;
+        }
+    }
+    unsigned tn = block_count(neg);
+    if (threadIdx.x == 0 && tn && scal) atomicAdd(scal + 3, (unsigned long long)tn);
+}
+
+cudaError_t launch_prolong(int interp, int ncomp, int nxc, int nyc, int nzc, const double *tz,
+                           const double *zf, const double *coarse, double *fine,
+                           cudaStream_t st) {
+    const long nvf = (long)(2 * nxc) * (2 * nyc) * (2 * nzc - 1);
+    if (interp)
+        prolong_hermite_kernel<double><<<grid_for(nvf, 256), 256, 0, st>>>(ncomp, nxc, nyc, nzc,
+                                                                         zf, coarse, fine);
+    else
+        prolong_kernel<double><<<grid_for(nvf, 256), 256, 0, st>>>(ncomp, nxc, nyc, nzc, tz,
+                                                                     coarse, fine);
     return cudaGetLastError();
 }
 
-cudaError_t launch_prolong_prec(int prec, int ncomp, int nxc, int nyc, int nzc,
-                                const double *tz, const void *coarse, void *fine,
-                                cudaStream_t st) {
+cudaError_t launch_prolong_prec(int interp, int prec, int ncomp, int nxc, int nyc, int nzc,
+                                const double *tz, const double *zf, const void *coarse,
+                                void *fine, cudaStream_t st) {
     const long nvf = (long)(2 * nxc) * (2 * nyc) * (2 * nzc - 1);
-    if (prec == 0)
+    if (interp && prec == 0)
+        prolong_hermite_kernel<double><<<grid_for(nvf, 256), 256, 0, st>>>(
+            ncomp, nxc, nyc, nzc, zf, (const double *)coarse, (double *)fine);
+    else if (interp)
+        prolong_hermite_kernel<float><<<grid_for(nvf, 256), 256, 0, st>>>(
+            ncomp, nxc, nyc, nzc, zf, (const float *)coarse, (float *)fine);
+    else if (prec == 0)
         prolong_kernel<double><<<grid_for(nvf, 256), 256, 0, st>>>(
             ncomp, nxc, nyc, nzc, tz, (const double *)coarse, (double *)fine);
     else
@@ -354,11 +519,18 @@ cudaError_t launch_prolong_prec(int prec, int ncomp, int nxc, int nyc, int nzc,
     return cudaGetLastError();
 }
 
-cudaError_t launch_prolong_correct(int ncomp, int nxc, int nyc, int nzc, const double *tz,
-                                   const double *n_after, const double *n_before,
-                                   double *n_fine, unsigned long long *scal,
+cudaError_t launch_prolong_correct(int interp, int ncomp, int nxc, int nyc, int nzc,
+                                   const double *tz, const double *zf, const double *n_after,
+                                   double *n_before, double *n_fine, unsigned long long *scal,
                                    cudaStream_t st) {
     const long nvf = (long)(2 * nxc) * (2 * nyc) * (2 * nzc - 1);
+    if (interp) {
+        const long len = (long)ncomp * nxc * nyc * nzc;
+        rel_correction_kernel<<<grid_for(len, 256), 256, 0, st>>>(len, n_after, n_before);
+        prolong_correct_hermite_kernel<<<grid_for(nvf, 256), 256, 0, st>>>(
+            ncomp, nxc, nyc, nzc, zf, n_before, n_fine, scal);
+        return cudaGetLastError();
+    }
     prolong_correct_kernel<<<grid_for(nvf, 256), 256, 0, st>>>(ncomp, nxc, nyc, nzc, tz,
                                                                  n_after, n_before, n_fine,
                                                                  scal);

@@ -120,4 +120,36 @@ struct ScWeights<float> {
     }
 };
 
+// Monotone cubic Hermite upwind interpolation (the Hermite-spline option of
+// Sec. 3; Auer 2003).  The slope at a node of a uniform periodic row, in
+// units of one cell, is the harmonic mean 2ab/(a+b) of its two adjacent
+// secants a and b when they have the same strict sign, else 0 (Fritsch &
+// Butland 1984); the cubic on [0, 1] through p0, p1 with slopes d0, d1 at t
+// is c0 p0 + c1 d0 + c2 p1 + c3 d1 with the Hermite basis c of t.  Rows are
+// interpolated along x, then the four row values along y.
+template <typename T>
+__device__ __forceinline__ T mono_slope(T a, T b) {
+    return ((a > T(0) && b > T(0)) || (a < T(0) && b < T(0))) ? T(2) * a * b * rcp(a + b) : T(0);
+}
+
+template <typename T>
+struct HermiteBasis {
+    T c0, c1, c2, c3;
+    __device__ __forceinline__ explicit HermiteBasis(T t) {
+        const T t2 = t * t, t3 = t2 * t;
+        c0 = T(2) * t3 - T(3) * t2 + T(1);
+        c1 = t3 - T(2) * t2 + t;
+        c2 = T(3) * t2 - T(2) * t3;
+        c3 = t3 - t2;
+    }
+    // the cubic from values and slopes
+    __device__ __forceinline__ T at(T p0, T d0, T p1, T d1) const {
+        return c0 * p0 + c1 * d0 + c2 * p1 + c3 * d1;
+    }
+    // the cubic between q1 and q2 of four consecutive values
+    __device__ __forceinline__ T through4(T q0, T q1, T q2, T q3) const {
+        return at(q1, mono_slope(q1 - q0, q2 - q1), q2, mono_slope(q2 - q1, q3 - q2));
+    }
+};
+
 }  // namespace mg3d

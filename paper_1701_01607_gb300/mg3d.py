@@ -28,6 +28,8 @@ MG3D_PREC_F32 = 1
 MG3D_RESTRICT_FULL = 0
 MG3D_RESTRICT_HALF = 1
 MG3D_RESTRICT_INJECT = 2
+MG3D_INTERP_LINEAR = 0
+MG3D_INTERP_HERMITE = 1
 MG3D_NOALLOC_MAX_NODES = 65536
 MG3D_NOALLOC_MAX_NZ = 1024
 MG3D_NOALLOC_MAX_FREQ = 64
@@ -55,7 +57,8 @@ class mg3d_params(ctypes.Structure):
     _fields_ = [("n_grids", ctypes.c_int), ("nu_fmg", ctypes.c_int), ("nu0", ctypes.c_int),
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("nu3", ctypes.c_int),
                 ("fs_prec", ctypes.c_int), ("restriction", ctypes.c_int),
-                ("ml_chunk", ctypes.c_int)]
+                ("ml_chunk", ctypes.c_int), ("interpolation", ctypes.c_int),
+                ("sc_interp", ctypes.c_int)]
 
 
 class mg3d_line(ctypes.Structure):
@@ -212,7 +215,8 @@ def mg3d_last_error() -> str:
 
 def mg3d_create(atm, atom, quad_a: float = 0.0, n_grids: int = 1, nu_fmg: int = 16,
                 nu0: int = 0, nu1: int = 2, nu2: int = 2, nu3: int = 32,
-                fs_prec: int = MG3D_PREC_F64, restriction: int = MG3D_RESTRICT_FULL):
+                fs_prec: int = MG3D_PREC_F64, restriction: int = MG3D_RESTRICT_FULL,
+                interpolation: int = MG3D_INTERP_LINEAR, sc_interp: int = MG3D_INTERP_LINEAR):
     """mg3d_create from a synth.Atmosphere and TwoLevelAtom; returns the handle."""
     lib = load()
     z = np.ascontiguousarray(atm.z, dtype=np.float64)
@@ -223,7 +227,8 @@ def mg3d_create(atm, atom, quad_a: float = 0.0, n_grids: int = 1, nu_fmg: int = 
                         _dptr(n_tot), _dptr(c_ul))
     at = mg3d_atom(atom.a_ul, atom.g_ratio, atom.theta, atom.kappa, atom.n_freq, atom.x_max)
     q = mg3d_quadrature(quad_a)
-    p = mg3d_params(n_grids, nu_fmg, nu0, nu1, nu2, nu3, fs_prec, restriction)
+    p = mg3d_params(n_grids, nu_fmg, nu0, nu1, nu2, nu3, fs_prec, restriction, 0, interpolation,
+                    sc_interp)
     h = _H()
     _check(lib.mg3d_create(ctypes.byref(a), ctypes.byref(at), ctypes.byref(q),
                            ctypes.byref(p), ctypes.byref(h)))
@@ -233,7 +238,8 @@ def mg3d_create(atm, atom, quad_a: float = 0.0, n_grids: int = 1, nu_fmg: int = 
 def mg3d_create_ml(atm, atom, quad_a: float = 0.0, n_grids: int = 1, nu_fmg: int = 16,
                    nu0: int = 0, nu1: int = 2, nu2: int = 2, nu3: int = 32,
                    fs_prec: int = MG3D_PREC_F64, restriction: int = MG3D_RESTRICT_FULL,
-                   ml_chunk: int = 0):
+                   ml_chunk: int = 0, interpolation: int = MG3D_INTERP_LINEAR,
+                   sc_interp: int = MG3D_INTERP_LINEAR):
     """mg3d_create_ml from a synth.MultiLevelAtmosphere and MultiLevelAtom."""
     lib = load()
     keep = {}
@@ -256,7 +262,8 @@ def mg3d_create_ml(atm, atom, quad_a: float = 0.0, n_grids: int = 1, nu_fmg: int
     at = mg3d_ml_atom(atom.n_levels, arr("g", atom.g), arr("th", atom.theta), atom.theta_ref,
                       atom.t_ref, len(atom.lines), lines, len(atom.continua), conts)
     q = mg3d_quadrature(quad_a)
-    p = mg3d_params(n_grids, nu_fmg, nu0, nu1, nu2, nu3, fs_prec, restriction, ml_chunk)
+    p = mg3d_params(n_grids, nu_fmg, nu0, nu1, nu2, nu3, fs_prec, restriction, ml_chunk,
+                    interpolation, sc_interp)
     h = _H()
     _check(lib.mg3d_create_ml(ctypes.byref(a), ctypes.byref(at), ctypes.byref(q),
                               ctypes.byref(p), ctypes.byref(h)))
