@@ -566,6 +566,97 @@ def run_scattering(args):
     return out
 
 
+def run_interpolation(args):
+    """The Hermite options of Sec. 3 and Sec. 4.5 on the 64x64x129 two-level
+    box (eps = 1e-4; rough sigma = 0.3 and smooth sigma = 0), FP64:
+    iterations and seconds to E_inf <= 1e-3 for MALI and 3-grid FAS with
+    trilinear or Hermite prolongation, each upwind scheme against its own
+    FAS reference converged to C < 1e-9; then the autotuned sweep time of
+    each upwind scheme (two-level box, FP64 and FP32; 6-level atom with 120
+    frequencies on a 64x64x129 chromosphere).  Opt-in, --interp-experiment;
+    prints one JSON line."""
+    from paper_1701_01607_gb300 import mg3d as m
+    from paper_1701_01607_gb300 import synth
+    m.load(build_if_missing=True)
+    out = {"metric": "iterations and seconds to E_inf <= 1e-3; sweep ms per launch",
+           "unit": "s", "higher_is_better": False, "n_gpus": 1, "dtype": "f64",
+           "data": "synthetic", "config": {"nu": NU, "target_e_inf": 1e-3}}
+
+    def to_target(make, grids, n_ref, step, cap):
+        h = make()
+        secs, errs = 0.0, []
+        try:
+            for it in range(cap):
+                t0 = time.perf_counter()
+                step(h, it)
+                secs += time.perf_counter() - t0
+                n = m.mg3d_get_populations(h, grids)
+                errs.append(float(np.max(np.abs(n - n_ref) / np.abs(n_ref))))
+                if errs[-1] <= 1e-3:
+                    break
+        finally:
+            m.mg3d_destroy(h)
+        return {"reached": errs[-1] <= 1e-3, "iterations": len(errs), "seconds": round(secs, 3),
+                "e_inf_last": float(f"{errs[-1]:.3g}")}
+
+    for name, sigma in (("rough", 0.3), ("smooth", 0.0)):
+        atm, atom = synth.stratified_two_level(GRID[0], GRID[1], GRID[2], eps=1e-4,
+                                               sigma=sigma, seed=1)
+        for sc in (0, 1):
+            ref = m.mg3d_create(atm, atom, n_grids=3, sc_interp=sc, **NU)
+            m.mg3d_fas_solve(ref, 1e-9, 400, n_grids=3)
+            n_ref = m.mg3d_get_populations(ref, 3)
+            m.mg3d_destroy(ref)
+            row = {}
+            for interp in (0, 1):
+                row[f"fas_{'hermite' if interp else 'trilinear'}"] = to_target(
+                    lambda: m.mg3d_create(atm, atom, n_grids=3, sc_interp=sc,
+                                          interpolation=interp, **NU),
+                    3, n_ref, lambda h, it: m.mg3d_fas_vcycle(h, it == 0), 60)
+            row["mali"] = to_target(lambda: m.mg3d_create(atm, atom, n_grids=1, sc_interp=sc, **NU),
+                                    1, n_ref, lambda h, it: m.mg3d_mali_sweep(h, 1, 1), 2000)
+            out[f"{name}_upwind_{'hermite' if sc else 'linear'}"] = row
+
+    sweeps = {}
+    atm, atom = synth.stratified_two_level(GRID[0], GRID[1], GRID[2], eps=1e-4, sigma=0.3,
+                                           seed=1)
+    for prec, pname in ((m.MG3D_PREC_F64, "f64"), (m.MG3D_PREC_F32, "f32")):
+        for sc in (0, 1):
+            h = m.mg3d_create(atm, atom, n_grids=1, fs_prec=prec, sc_interp=sc, **NU)
+            try:
+                m.mg3d_autotune(h)
+                m.mg3d_set_timing(h, True)
+                m.mg3d_reset_counters(h)
+                for _ in range(5):
+                    m.mg3d_formal_solve(h, 1, want=False)
+                c = m.mg3d_get_counters(h)
+                sweeps[f"two_level_{pname}_{'hermite' if sc else 'linear'}"] = {
+                    "ms": round(c["fs_kernel_ms"] / c["fs_timed_launches"], 3),
+                    "shape": list(m.mg3d_get_fs_config(h, 1))}
+            finally:
+                m.mg3d_destroy(h)
+    ml_atom = synth.hydrogen_like_atom(line_freq=20, cont_freq=4, seed=2)
+    ml_atm = synth.chromosphere(64, 64, 129, ml_atom, seed=2)
+    for prec, pname in ((m.MG3D_PREC_F32, "f32"), (m.MG3D_PREC_F64, "f64")):
+        for sc in (0, 1):
+            h = m.mg3d_create_ml(ml_atm, ml_atom, n_grids=1, fs_prec=prec, sc_interp=sc)
+            try:
+                m.mg3d_autotune(h)
+                m.mg3d_set_timing(h, True)
+                m.mg3d_reset_counters(h)
+                for _ in range(3):
+                    m.mg3d_formal_solve_ml(h, 1)
+                c = m.mg3d_get_counters(h)
+                sweeps[f"six_level_{pname}_{'hermite' if sc else 'linear'}"] = {
+                    "ms": round(c["fs_kernel_ms"] / c["fs_timed_launches"], 3),
+                    "gunits_s": round(c["fs_units"] / (c["fs_kernel_ms"] * 1e-3) / 1e9, 2),
+                    "shape": list(m.mg3d_get_ml_shape(h, 1))}
+            finally:
+                m.mg3d_destroy(h)
+    out["sweeps"] = sweeps
+    return out
+
+
 def run_experiments(args):
     """Synthetic analogues of the paper's restriction and grid-count tests
     (Sec. 4.3, Sec. 4.4): FAS from the zero-radiation start until the true
@@ -716,6 +807,8 @@ def main():
                     help="run the restriction / grid-count experiments instead")
     ap.add_argument("--chromosphere", action="store_true",
                     help="time MALI, FAS and FMG on the 128x128x257 6-level chromosphere instead")
+    ap.add_argument("--interp-experiment", action="store_true",
+                    help="the Hermite interpolation options against the linear ones")
     ap.add_argument("--scattering-experiment", action="store_true",
                     help="MALI and FAS to E_inf <= 1e-3 against background scattering strength")
     ap.add_argument("--chromo-size", default="128,128,257", help="nx,ny,nz of --chromosphere")
@@ -740,6 +833,9 @@ def main():
         return
     if args.batch:
         print(json.dumps(run_batch(args)), flush=True)
+        return
+    if args.interp_experiment:
+        print(json.dumps(run_interpolation(args)), flush=True)
         return
     if args.scattering_experiment:
         print(json.dumps(run_scattering(args)), flush=True)

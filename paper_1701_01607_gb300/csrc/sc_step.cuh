@@ -127,9 +127,13 @@ struct ScWeights<float> {
 // Butland 1984); the cubic on [0, 1] through p0, p1 with slopes d0, d1 at t
 // is c0 p0 + c1 d0 + c2 p1 + c3 d1 with the Hermite basis c of t.  Rows are
 // interpolated along x, then the four row values along y.
+// Branch-free: the division always runs (on 1 where the slope is 0), so a
+// warp whose lanes disagree on the sign test does not split.
 template <typename T>
 __device__ __forceinline__ T mono_slope(T a, T b) {
-    return ((a > T(0) && b > T(0)) || (a < T(0) && b < T(0))) ? T(2) * a * b * rcp(a + b) : T(0);
+    const bool same = (a > T(0) && b > T(0)) || (a < T(0) && b < T(0));
+    const T q = T(2) * a * b * rcp(same ? a + b : T(1));
+    return same ? q : T(0);
 }
 
 template <typename T>
