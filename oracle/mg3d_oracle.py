@@ -199,6 +199,7 @@ class Level:
     T: np.ndarray
     n_tot: np.ndarray
     c_ul: np.ndarray
+    vel: np.ndarray | None = None   # [3, nz, ny, nx] in Doppler widths
 
     @property
     def shape(self):
@@ -221,9 +222,11 @@ class TwoLevelProblem:
         self.sc_interp = sc_interp
         self.mu, self.wray = a4_quadrature(quad_a)
         self.x, self.phi, self.wphi = frequency_grid(atom.n_freq, atom.x_max)
+        vel = getattr(atm, "vel", None)
         fine = Level(atm.nx, atm.ny, atm.nz, atm.dx, atm.dy, np.asarray(atm.z, float),
                      np.asarray(atm.T, float), np.asarray(atm.n_tot, float),
-                     np.asarray(atm.c_ul, float))
+                     np.asarray(atm.c_ul, float),
+                     None if vel is None else np.asarray(vel, float))
         self.levels = {n_grids: fine}
         for k in range(n_grids - 1, 0, -1):
             self.levels[k] = coarsen_level(self.levels[k + 1])
@@ -254,6 +257,8 @@ class TwoLevelProblem:
     def formal_solution(self, k: int, n):
         """One formal solution on level k with populations n: (Jbar, Jeff, U)."""
         lev = self.levels[k]
+        if lev.vel is not None:
+            return self.formal_solution_moving(k, n)
         nvox = lev.nx * lev.ny * lev.nz
         nf = len(self.phi)
         chi, S = self.opacity_source(lev, n)
@@ -274,6 +279,54 @@ class TwoLevelProblem:
             int(self.sc_interp))
         if rc != 0:
             raise RuntimeError("oracle formal solution failed")
+        self.fs_count[k] += 1
+        return (Jbar.reshape(lev.shape), Jeff.reshape(lev.shape), U.reshape(lev.shape))
+
+    def formal_solution_moving(self, k: int, n):
+        """Formal solution in a moving atmosphere (CRD; the paper's Bifrost
+        atmospheres move).  Reading: along ray r the line profile at a node
+        is Doppler-shifted by the projected velocity, phi(x_nu - mu_r . u)
+        with u in Doppler widths, and the frequency weights w_nu phi are
+        renormalised per node and ray to sum to 1, so that Jbar stays a
+        profile average.  Opacity and weights then depend on the ray: each
+        ray is solved on its own by the C loop nest and the sums are added.
+        """
+        lev = self.levels[k]
+        nvox = lev.nx * lev.ny * lev.nz
+        nf = len(self.phi)
+        g = self.atom.g_ratio
+        nl = n[0].reshape(-1)
+        nu = n[1].reshape(-1)
+        diff = nl * g - nu
+        chi0 = self.atom.kappa * diff
+        S = np.ascontiguousarray(np.broadcast_to((nu / diff)[None, :], (nf, nvox)))
+        wq = self.wphi / self.phi          # the frequency quadrature weights
+        u = lev.vel.reshape(3, -1)
+        Ib = np.ascontiguousarray(np.broadcast_to(
+            self.planck(lev.T[0]).reshape(1, -1), (nf, lev.nx * lev.ny)))
+        It = np.zeros((nf, lev.nx * lev.ny))
+        Jbar = np.zeros(nvox)
+        Jeff = np.zeros(nvox)
+        U = np.zeros(nvox)
+        z = np.ascontiguousarray(lev.z)
+        for r in range(len(self.wray)):
+            ur = self.mu[r] @ u                                   # [nvox]
+            prof = np.exp(-(self.x[:, None] - ur[None, :]) ** 2) / math.sqrt(math.pi)
+            wphi = wq[:, None] * prof
+            wphi = np.ascontiguousarray(wphi / wphi.sum(axis=0))
+            chi = np.ascontiguousarray(chi0[None, :] * prof)
+            jb, je, uu = (np.empty(nvox) for _ in range(3))
+            mu1 = np.ascontiguousarray(self.mu[r:r + 1])
+            w1 = np.ascontiguousarray(self.wray[r:r + 1])
+            rc = _load().orc_formal_solution(
+                lev.nx, lev.ny, lev.nz, lev.dx, lev.dy, _ptr(z), 1, _ptr(mu1), _ptr(w1), nf,
+                _ptr(chi), _ptr(S), _ptr(wphi), _ptr(Ib), _ptr(It), _ptr(jb), _ptr(je),
+                _ptr(uu), None, int(self.sc_interp))
+            if rc != 0:
+                raise RuntimeError("oracle formal solution failed")
+            Jbar += jb
+            Jeff += je
+            U += uu
         self.fs_count[k] += 1
         return (Jbar.reshape(lev.shape), Jeff.reshape(lev.shape), U.reshape(lev.shape))
 
@@ -626,11 +679,11 @@ def coarsen_level(lev: Level) -> Level:
 
     The grid keeps every second node (z coordinates by dropping nodes, so the
     boundary heights stay fixed); T, n_tot and the collisional rate are
-    carried over by full weighting.
+    carried over by full weighting, and so is the velocity field.
     """
     return Level(lev.nx // 2, lev.ny // 2, (lev.nz + 1) // 2, 2 * lev.dx, 2 * lev.dy,
                  lev.z[::2].copy(), restrict_fw(lev.T), restrict_fw(lev.n_tot),
-                 restrict_fw(lev.c_ul))
+                 restrict_fw(lev.c_ul), None if lev.vel is None else restrict_fw(lev.vel))
 
 
 # --------------------------------------------------------------------------

@@ -73,6 +73,8 @@ class Atmosphere:
     T: np.ndarray        # [nz, ny, nx] kelvin
     n_tot: np.ndarray    # [nz, ny, nx] total number density of the atom
     c_ul: np.ndarray     # [nz, ny, nx] collisional de-excitation rate
+    vel: Optional[np.ndarray] = None  # [3, nz, ny, nx] (x, y, z) velocity in
+                                      # Doppler widths, or None (static)
 
     @property
     def shape(self):
@@ -124,7 +126,8 @@ def stratified_two_level(nx: int, ny: int, nz: int, eps: float,
                          tau_top: float = 1e-4, tau_bottom: float = 1e4,
                          T: float = 5000.0, sigma: float = 0.0, seed: int = 0,
                          atom: TwoLevelAtom | None = None,
-                         dx: float = 1.0) -> tuple[Atmosphere, TwoLevelAtom]:
+                         dx: float = 1.0, velocity: float = 0.0
+                         ) -> tuple[Atmosphere, TwoLevelAtom]:
     """Isothermal, exponentially stratified box for the two-level atom.
 
     ``nz`` is the number of nodes (odd, so the grid coarsens with fixed
@@ -134,7 +137,9 @@ def stratified_two_level(nx: int, ny: int, nz: int, eps: float,
     exponential atmosphere equals ``tau_top`` at the top node and
     ``tau_bottom`` at the bottom node.  ``sigma`` > 0 multiplies n_tot by the
     log-normal factor exp(sigma G - sigma^2/2) of a seeded Gaussian random
-    field G.
+    field G.  ``velocity`` > 0 adds a velocity field whose three components
+    are independent seeded Gaussian random fields (seeds seed+101..103) with
+    that rms, in Doppler widths.
     """
     atom = atom or TwoLevelAtom()
     z = np.arange(nz, dtype=np.float64) * dx
@@ -153,8 +158,12 @@ def stratified_two_level(nx: int, ny: int, nz: int, eps: float,
         n_tot *= np.exp(sigma * g - 0.5 * sigma * sigma)
     Tarr = np.full((nz, ny, nx), float(T))
     c_ul = collisional_rate_for_eps(np.full((nz, ny, nx), eps), atom, Tarr)
+    vel = None
+    if velocity > 0:
+        vel = np.stack([velocity * gaussian_random_field((nz, ny, nx), seed + 101 + c)
+                        for c in range(3)])
     atm = Atmosphere(nx=nx, ny=ny, nz=nz, dx=dx, dy=dx, z=z, T=Tarr,
-                     n_tot=n_tot, c_ul=np.ascontiguousarray(c_ul))
+                     n_tot=n_tot, c_ul=np.ascontiguousarray(c_ul), vel=vel)
     return atm, atom
 
 
