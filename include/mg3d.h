@@ -64,6 +64,14 @@ typedef struct {
     const double *T;       /* [nz][ny][nx] gas temperature, K */
     const double *n_tot;   /* [nz][ny][nx] total number density of the atom */
     const double *c_ul;    /* [nz][ny][nx] collisional de-excitation rate */
+    const double *vel;     /* nullable: [3][nz][ny][nx] velocity (x, y, z components)
+                              in Doppler widths.  A moving atmosphere (the paper's
+                              Bifrost snapshots move): along ray r the CRD profile
+                              at a node is phi(x - mu_r . vel), and the frequency
+                              weights w phi are renormalised per node and ray to sum
+                              to 1; coarse grids full-weight the field.  Takes the
+                              linear upwind interpolation, no batches; the mirror
+                              frequency sharing of the static sweep does not apply. */
 } mg3d_atmosphere;
 
 /* Two-level model atom (Sec. 3.2).  Intensities are in units of

@@ -188,13 +188,94 @@ __device__ __forceinline__ void hermite_step(
     }
 }
 
+// Doppler profile exp(-d2)/sqrt(pi) in the formal-solution precision.
+__device__ __forceinline__ double doppler_profile(double d2, const ExpNegTable &et) {
+    return 0.56418958354775628 * exp_neg(d2, et);
+}
+__device__ __forceinline__ float doppler_profile(float d2, const ExpNegTable &) {
+    return 0.564189584f * __expf(-d2);
+}
+
+// One sweep step of a band in a moving atmosphere (CRD).  Along ray r the
+// profile of frequency x_f at a node is phi(x_f - u) with u the velocity
+// projected on the ray (in Doppler widths), so the line opacity chi0 phi
+// depends on node, ray and frequency: it is formed at the node, used for
+// the node's half of the optical depth and kept in the opacity plane next to
+// the intensity plane, where the next step interpolates its upwind value
+// like the intensity's.  The frequency weights are w_f phi(x_f - u) times
+// the node's and ray's normalisation, so that they sum to 1 over all
+// frequencies.  Mirror frequencies no longer share weights.
+template <typename T>
+__device__ __forceinline__ void moving_step(
+    const SweepArgs<T> &a, int r, int rank, unsigned long long rmagic, cg::cluster_group &cluster,
+    const T *prev, const T *cprev, T *cur, T *ccur, T *__restrict__ pj, T *__restrict__ pu, int k,
+    int kp, const StepGeom &o, T half_s, int f0, int nf, const ExpNegTable &et) {
+    const int nx = a.nx, ny = a.ny, rows = a.rows;
+    const int y0 = rank * rows;
+    const int myrows = max(0, min(rows, ny - y0));
+    const int band = myrows * nx;
+    const long nplane = (long)nx * ny;
+    const long nvox = nplane * a.nz;
+    const T tx = (T)o.tx, ty = (T)o.ty;
+    const T w00 = (T(1) - tx) * (T(1) - ty), w10 = tx * (T(1) - ty);
+    const T w01 = (T(1) - tx) * ty, w11 = tx * ty;
+    const long pp = (long)kp * nplane;
+    for (int q = threadIdx.x; q < band; q += blockDim.x) {
+        const int yl = q / nx, x = q - yl * nx;
+        const int y = y0 + yl;
+        int xa = x + o.ix0;
+        if (xa >= nx) xa -= nx;
+        const int xb = (xa + 1 == nx) ? 0 : xa + 1;
+        int ya = y + o.iy0;
+        if (ya >= ny) ya -= ny;
+        const int yb = (ya + 1 == ny) ? 0 : ya + 1;
+        const T *sa = a.S + pp + (long)ya * nx, *sb = a.S + pp + (long)yb * nx;
+        const T S_up = w00 * sa[xa] + w10 * sa[xb] + w01 * sb[xa] + w11 * sb[xb];
+        const long v = (long)k * nplane + (long)y * nx + x;
+        const T S_loc = a.S[v], c0 = a.chi0[v];
+        const T u = a.uproj[(long)r * nvox + v], nrm = a.vnorm[(long)r * nvox + v];
+        const int ba = band_of(ya, rmagic), bb = band_of(yb, rmagic);
+        const long ra = (long)(ya - ba * rows) * nx, rb = (long)(yb - bb * rows) * nx;
+        const T *Pa = (ba == rank ? prev : cluster.map_shared_rank(prev, ba)) + ra;
+        const T *Pb = (bb == rank ? prev : cluster.map_shared_rank(prev, bb)) + rb;
+        const T *Ca = (ba == rank ? cprev : cluster.map_shared_rank(cprev, ba)) + ra;
+        const T *Cb = (bb == rank ? cprev : cluster.map_shared_rank(cprev, bb)) + rb;
+        T cj = 0, cu = 0;
+        for (int f = 0; f < nf; ++f) {
+            const long off = (long)f * rows * nx;
+            const T d = a.xf[f0 + f] - u;
+            const T prof = doppler_profile(d * d, et);
+            const T chi_loc = c0 * prof;
+            const T chi_up = w00 * Ca[off + xa] + w10 * Ca[off + xb] + w01 * Cb[off + xa] +
+                             w11 * Cb[off + xb];
+            const T I_up = w00 * Pa[off + xa] + w10 * Pa[off + xb] + w01 * Pb[off + xa] +
+                           w11 * Pb[off + xb];
+            const T dtau = (chi_up + chi_loc) * half_s;
+            T ex, w0, wup, uu;
+            ScWeights<T>::eval(dtau, rcp(dtau), et, ex, w0, wup, uu);
+            const T part = I_up * ex + wup * S_up;
+            const long i = off + (long)yl * nx + x;
+            cur[i] = part + w0 * S_loc;
+            ccur[i] = chi_loc;
+            const T w = a.wq[f0 + f] * prof * nrm;
+            cj += w * part;
+            cu += w * uu;
+        }
+        pj[v] = cj;
+        pu[v] = cu;
+    }
+}
+
 // Body of the sweep for ray r and frequency group g of one problem.  STAGE:
 // chi0 and S rows of each step are copied to shared memory one step ahead;
 // without it they are read from global memory (L1/L2) where used.  HERM:
-// monotone cubic Hermite upwind interpolation (unstaged).
-template <typename T, bool STAGE, bool HERM>
+// monotone cubic Hermite upwind interpolation (unstaged).  MODE: kSweepLinear,
+// kSweepHermite (Hermite upwind interpolation) or kSweepMoving (a velocity
+// field; unstaged).
+template <typename T, bool STAGE, int MODE>
 __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) {
-    static_assert(!(STAGE && HERM), "Hermite sweeps run unstaged");
+    constexpr bool HERM = MODE == kSweepHermite, VEL = MODE == kSweepMoving;
+    static_assert(!(STAGE && MODE != kSweepLinear), "Hermite and moving sweeps run unstaged");
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int nx = a.nx, ny = a.ny, nz = a.nz, rows = a.rows;
@@ -213,8 +294,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf = reinterpret_cast<T *>(smem_raw);
     const long bufstride = (long)a.ng * rows * nx;
-    T *dbuf = buf + 2 * bufstride;  // slope planes (HERM)
-    T *stage = buf + (HERM ? 4 : 2) * bufstride;
+    T *dbuf = buf + 2 * bufstride;  // slope planes (HERM) or opacity planes (VEL)
+    T *stage = buf + (MODE != kSweepLinear ? 4 : 2) * bufstride;
     const long stagestride = STAGE ? sweep_stage_elems(rows, nx) : 0;
     T *tabs = stage + 2 * stagestride;
     T *phi = tabs, *inv_phi = tabs + a.ng, *wphi = tabs + 2 * a.ng, *wu = tabs + 3 * a.ng;
@@ -266,7 +347,32 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
     for (int t = 0; t < nz; ++t) {
         const int k = up ? t : nz - 1 - t;
         T *cur = buf + (t & 1) * bufstride;
-        if (t == 0) {
+        if (t == 0 && VEL) {
+            // entering boundary of a moving atmosphere: I prescribed, w0 = 0;
+            // the opacity plane gets the shifted profile for the next step
+            T *ccur = dbuf + (t & 1) * bufstride;
+            for (int q = threadIdx.x; q < band; q += blockDim.x) {
+                const int yl = q / nx, x = q - yl * nx;
+                const int y = y0 + yl;
+                const long v = (long)k * nplane + (long)y * nx + x;
+                const T Ib = up ? a.bbot[(long)y * nx + x] : T(0);
+                const T u = a.uproj[(long)r * nvox + v], nrm = a.vnorm[(long)r * nvox + v];
+                const T c0 = a.chi0[v];
+                T cj = 0, cu = 0;
+                for (int f = 0; f < nf; ++f) {
+                    const T d = a.xf[f0 + f] - u;
+                    const T prof = doppler_profile(d * d, et);
+                    const long i = ((long)f * rows + yl) * nx + x;
+                    cur[i] = Ib;
+                    ccur[i] = c0 * prof;
+                    const T w = a.wq[f0 + f] * prof * nrm;
+                    cj += w * Ib;
+                    cu += w;
+                }
+                pj[v] = cj;
+                pu[v] = cu;
+            }
+        } else if (t == 0) {
             // entering boundary: I prescribed (bottom: Planck at the local
             // temperature; top: zero), so w0 = 0 and 1 - w0 = 1
             for (int q = threadIdx.x; q < band; q += blockDim.x) {
@@ -304,6 +410,10 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
                 hermite_step(a, rank, rmagic, cluster, prev, dbuf + ((t - 1) & 1) * bufstride,
                              cur, pj, pu, k, kp, o, half_s, nf, phi, inv_phi, wphi, wu, et,
                              is_fresh);
+            } else if constexpr (VEL) {
+                moving_step(a, r, rank, rmagic, cluster, prev, dbuf + ((t - 1) & 1) * bufstride,
+                            cur, dbuf + (t & 1) * bufstride, pj, pu, k, kp, o, half_s, f0, nf,
+                            et);
             } else
             for (int q = threadIdx.x; q < band; q += blockDim.x) {
                 const int yl = q / nx, x = q - yl * nx;
@@ -422,9 +532,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
 // blocks per SM it must fit, which sets the register budget (MINB = 1: up to
 // 255 registers; 1024/MAXT: 64 registers, 32 resident warps per SM; 3 blocks
 // of 256: 85 registers).
-template <typename T, int MAXT, int MINB, bool STAGE, bool HERM>
+template <typename T, int MAXT, int MINB, bool STAGE, int MODE>
 __global__ void __launch_bounds__(MAXT, MINB) sweep_kernel(const SweepArgs<T> a) {
-    sweep_body<T, STAGE, HERM>(a, blockIdx.y, blockIdx.z);
+    sweep_body<T, STAGE, MODE>(a, blockIdx.y, blockIdx.z);
 }
 
 // Batched sweep: cluster y of the grid runs work item items[y] = (problem,
@@ -435,7 +545,7 @@ __global__ void __launch_bounds__(MAXT, 1024 / MAXT) sweep_batch_kernel(
     const SweepArgs<T> *__restrict__ args, const BatchItem *__restrict__ items) {
     const BatchItem it = items[blockIdx.y];
     const SweepArgs<T> a = args[it.member];
-    sweep_body<T, true, false>(a, it.group, it.ray);
+    sweep_body<T, true, kSweepLinear>(a, it.group, it.ray);
 }
 
 __global__ void exp_check_kernel(int n, const double *__restrict__ x, double *__restrict__ out,
@@ -469,7 +579,7 @@ void exp_neg_constants(double *tab, double *l1, double *l2) {
 
 size_t sweep_smem_bytes(int prec, const SweepShape &s, int nx) {
     size_t elem = prec == 0 ? sizeof(double) : sizeof(float);
-    return ((s.herm ? 4ull : 2ull) * s.ng * s.rows * nx +
+    return ((s.herm || s.vel ? 4ull : 2ull) * s.ng * s.rows * nx +
             (s.stage ? 2ull * sweep_stage_elems(s.rows, nx) : 0ull) + 4ull * s.ng) *
            elem;
 }
@@ -477,18 +587,18 @@ size_t sweep_smem_bytes(int prec, const SweepShape &s, int nx) {
 // Kernel attributes for shape s (dynamic shared memory; clusters of more
 // than 8 blocks are a non-portable size the kernel must opt into) and the
 // launch configuration; a is null for an occupancy query.
-template <typename T, int MAXT, int MINB, bool STAGE, bool HERM>
+template <typename T, int MAXT, int MINB, bool STAGE, int MODE>
 static cudaError_t sweep_config(const SweepShape &s, int nx, cudaStream_t st,
                                 cudaLaunchConfig_t *cfg, cudaLaunchAttribute *attr) {
     const size_t smem = sweep_smem_bytes(sizeof(T) == 8 ? 0 : 1, s, nx);
     // the limit is the same for every launch: a CUDA graph that captured a
     // launch needing more than a later launch of the same kernel must still
     // find the attribute large enough when it replays
-    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, MAXT, MINB, STAGE, HERM>,
+    cudaError_t e = cudaFuncSetAttribute(sweep_kernel<T, MAXT, MINB, STAGE, MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kMaxSweepSmem);
     if (e == cudaSuccess && s.bands > kPortableBands)
-        e = cudaFuncSetAttribute(sweep_kernel<T, MAXT, MINB, STAGE, HERM>,
+        e = cudaFuncSetAttribute(sweep_kernel<T, MAXT, MINB, STAGE, MODE>,
                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     *cfg = cudaLaunchConfig_t{};
@@ -506,65 +616,73 @@ static cudaError_t sweep_config(const SweepShape &s, int nx, cudaStream_t st,
     return cudaSuccess;
 }
 
-template <typename T, int MAXT, int MINB, bool STAGE, bool HERM>
+template <typename T, int MAXT, int MINB, bool STAGE, int MODE>
 static cudaError_t launch_sweep_t(const SweepArgs<T> &a, const SweepShape &s,
                                   cudaStream_t st) {
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
-    cudaError_t e = sweep_config<T, MAXT, MINB, STAGE, HERM>(s, a.nx, st, &cfg, attr);
+    cudaError_t e = sweep_config<T, MAXT, MINB, STAGE, MODE>(s, a.nx, st, &cfg, attr);
     if (e != cudaSuccess) return e;
-    return cudaLaunchKernelEx(&cfg, sweep_kernel<T, MAXT, MINB, STAGE, HERM>, a);
+    return cudaLaunchKernelEx(&cfg, sweep_kernel<T, MAXT, MINB, STAGE, MODE>, a);
 }
 
-template <typename T, int MAXT, int MINB, bool STAGE, bool HERM>
+template <typename T, int MAXT, int MINB, bool STAGE, int MODE>
 static cudaError_t clusters_t(const SweepShape &s, int nx, int *n) {
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
-    cudaError_t e = sweep_config<T, MAXT, MINB, STAGE, HERM>(s, nx, 0, &cfg, attr);
+    cudaError_t e = sweep_config<T, MAXT, MINB, STAGE, MODE>(s, nx, 0, &cfg, attr);
     if (e != cudaSuccess) return e;
     if (s.bands == 1)  // plain launch: resident blocks per SM
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, sweep_kernel<T, MAXT, MINB, STAGE, HERM>,
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, sweep_kernel<T, MAXT, MINB, STAGE, MODE>,
                                                              s.threads, cfg.dynamicSmemBytes);
-    return cudaOccupancyMaxActiveClusters(n, sweep_kernel<T, MAXT, MINB, STAGE, HERM>, &cfg);
+    return cudaOccupancyMaxActiveClusters(n, sweep_kernel<T, MAXT, MINB, STAGE, MODE>, &cfg);
 }
 
-template <typename T, bool STAGE, bool HERM>
+template <typename T, bool STAGE, int MODE>
 static cudaError_t launch_sweep_st(const SweepArgs<T> &a, const SweepShape &s, cudaStream_t st) {
     if (s.threads <= 256) {
-        if (s.lean == 1) return launch_sweep_t<T, 256, 4, STAGE, HERM>(a, s, st);
-        if (s.lean == 2) return launch_sweep_t<T, 256, 3, STAGE, HERM>(a, s, st);
-        return launch_sweep_t<T, 256, 1, STAGE, HERM>(a, s, st);
+        if (s.lean == 1) return launch_sweep_t<T, 256, 4, STAGE, MODE>(a, s, st);
+        if (s.lean == 2) return launch_sweep_t<T, 256, 3, STAGE, MODE>(a, s, st);
+        return launch_sweep_t<T, 256, 1, STAGE, MODE>(a, s, st);
     }
-    return s.lean == 1 ? launch_sweep_t<T, 512, 2, STAGE, HERM>(a, s, st)
-                       : launch_sweep_t<T, 512, 1, STAGE, HERM>(a, s, st);
+    return s.lean == 1 ? launch_sweep_t<T, 512, 2, STAGE, MODE>(a, s, st)
+                       : launch_sweep_t<T, 512, 1, STAGE, MODE>(a, s, st);
 }
 
 template <typename T>
 static cudaError_t launch_sweep_any(const SweepArgs<T> &a, const SweepShape &s,
                                     cudaStream_t st) {
+    if (s.herm && s.vel) return cudaErrorInvalidValue;
     if (s.herm) {
         if (s.stage || !a.dchi0 || !a.dS) return cudaErrorInvalidValue;
-        return launch_sweep_st<T, false, true>(a, s, st);
+        return launch_sweep_st<T, false, kSweepHermite>(a, s, st);
     }
-    return s.stage ? launch_sweep_st<T, true, false>(a, s, st)
-                   : launch_sweep_st<T, false, false>(a, s, st);
+    if (s.vel) {
+        if (s.stage || !a.uproj || !a.vnorm || !a.xf || !a.wq) return cudaErrorInvalidValue;
+        return launch_sweep_st<T, false, kSweepMoving>(a, s, st);
+    }
+    return s.stage ? launch_sweep_st<T, true, kSweepLinear>(a, s, st)
+                   : launch_sweep_st<T, false, kSweepLinear>(a, s, st);
 }
 
-template <typename T, bool STAGE, bool HERM>
+template <typename T, bool STAGE, int MODE>
 static cudaError_t clusters_st(const SweepShape &s, int nx, int *n) {
     if (s.threads <= 256) {
-        if (s.lean == 1) return clusters_t<T, 256, 4, STAGE, HERM>(s, nx, n);
-        if (s.lean == 2) return clusters_t<T, 256, 3, STAGE, HERM>(s, nx, n);
-        return clusters_t<T, 256, 1, STAGE, HERM>(s, nx, n);
+        if (s.lean == 1) return clusters_t<T, 256, 4, STAGE, MODE>(s, nx, n);
+        if (s.lean == 2) return clusters_t<T, 256, 3, STAGE, MODE>(s, nx, n);
+        return clusters_t<T, 256, 1, STAGE, MODE>(s, nx, n);
     }
-    return s.lean == 1 ? clusters_t<T, 512, 2, STAGE, HERM>(s, nx, n)
-                       : clusters_t<T, 512, 1, STAGE, HERM>(s, nx, n);
+    return s.lean == 1 ? clusters_t<T, 512, 2, STAGE, MODE>(s, nx, n)
+                       : clusters_t<T, 512, 1, STAGE, MODE>(s, nx, n);
 }
 
 template <typename T>
 static cudaError_t clusters_any(const SweepShape &s, int nx, int *n) {
-    if (s.herm) return s.stage ? cudaErrorInvalidValue : clusters_st<T, false, true>(s, nx, n);
-    return s.stage ? clusters_st<T, true, false>(s, nx, n) : clusters_st<T, false, false>(s, nx, n);
+    if ((s.herm || s.vel) && s.stage) return cudaErrorInvalidValue;
+    if (s.herm) return clusters_st<T, false, kSweepHermite>(s, nx, n);
+    if (s.vel) return clusters_st<T, false, kSweepMoving>(s, nx, n);
+    return s.stage ? clusters_st<T, true, kSweepLinear>(s, nx, n)
+                   : clusters_st<T, false, kSweepLinear>(s, nx, n);
 }
 
 cudaError_t sweep_active_clusters(int prec, const SweepShape &s, int nx, int *n) {
@@ -659,6 +777,46 @@ cudaError_t launch_xslopes(int prec, int nx, long nvox, const void *a, const voi
     else
         xslope_kernel<float><<<grid_for(nvox, th), th, 0, st>>>(
             nx, nvox, (const float *)a, (const float *)b, (float *)da, (float *)db);
+    return cudaGetLastError();
+}
+
+// Projected velocity u_r = mu_r . v and the inverse of kRays sum_f w_f
+// phi(x_f - u_r) at every node, per ray (the velocity field of a level does
+// not change), so that the weights w_f phi vnorm of a node and ray sum to the
+// ray weight 1/kRays.
+template <typename T>
+__global__ void vel_prep_kernel(long nvox, int nfreq, const double *__restrict__ mu,
+                                const double *__restrict__ vel, const double *__restrict__ xf,
+                                const double *__restrict__ wq, T *__restrict__ uproj,
+                                T *__restrict__ vnorm) {
+    const long total = (long)kRays * nvox;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total;
+         i += (long)gridDim.x * blockDim.x) {
+        const int r = (int)(i / nvox);
+        const long v = i - (long)r * nvox;
+        const double u = mu[3 * r] * vel[v] + mu[3 * r + 1] * vel[nvox + v] +
+                         mu[3 * r + 2] * vel[2 * nvox + v];
+        double sum = 0.0;
+        for (int f = 0; f < nfreq; ++f) {
+            const double d = xf[f] - u;
+            sum += wq[f] * 0.56418958354775628 * exp(-d * d);
+        }
+        uproj[i] = (T)u;
+        vnorm[i] = (T)(1.0 / (kRays * sum));  // with the ray weight 1/kRays
+    }
+}
+
+cudaError_t launch_vel_prep(int prec, long nvox, int nfreq, const double *mu, const double *vel,
+                            const double *xf, const double *wq, void *uproj, void *vnorm,
+                            cudaStream_t st) {
+    const int th = 256;
+    const long total = (long)kRays * nvox;
+    if (prec == 0)
+        vel_prep_kernel<double><<<grid_for(total, th), th, 0, st>>>(
+            nvox, nfreq, mu, vel, xf, wq, (double *)uproj, (double *)vnorm);
+    else
+        vel_prep_kernel<float><<<grid_for(total, th), th, 0, st>>>(
+            nvox, nfreq, mu, vel, xf, wq, (float *)uproj, (float *)vnorm);
     return cudaGetLastError();
 }
 

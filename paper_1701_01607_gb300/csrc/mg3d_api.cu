@@ -71,6 +71,8 @@ struct Level {
     double *r = nullptr;         // [2][nvox] residual / scratch
     void *chi0 = nullptr, *S = nullptr, *bbot = nullptr;
     void *dchi0 = nullptr, *dS = nullptr;  // x-slopes of chi0, S (Hermite upwind interpolation)
+    double *vel = nullptr;       // [3][nvox] velocity in Doppler widths (moving atmosphere)
+    void *uproj = nullptr, *vnorm = nullptr;  // [kRays][nvox] projected velocity, 1/sum w phi
     StepGeom *geom = nullptr;    // [kRays][nz]
     SweepShape shape{};
     // multi-level atom only
@@ -125,6 +127,8 @@ struct mg3d_handle {
     // frequency tables of the sweep, [order][phi, 1/phi, w phi / 24][n_freq]
     // in the formal-solution precision (see freq_tables)
     void *d_ftab = nullptr;
+    void *d_vtab = nullptr;      // moving atmospheres: [nf] offsets x, [nf] weights w
+    bool moving = false;         // the atmosphere has a velocity field
     double *d_exp_tab = nullptr;         // [64] table of the FP64 exp in the sweep
     double exp_l1 = 0, exp_l2 = 0;
     void *pj = nullptr, *pu = nullptr;
@@ -240,7 +244,10 @@ SweepArgs<T> sweep_args(const mg3d_handle *h, const Level &L, const SweepShape &
     return SweepArgs<T>{L.nx, L.ny, L.nz, h->atom.n_freq, s.ng, s.ngroups, s.rows,
                         h->up_mask, (const T *)L.chi0, (const T *)L.S, (const T *)L.bbot,
                         L.geom, phi, inv_phi, wphi, (T *)h->pj, (T *)h->pu, h->d_exp_tab,
-                        h->exp_l1, h->exp_l2, (const T *)L.dchi0, (const T *)L.dS};
+                        h->exp_l1, h->exp_l2, (const T *)L.dchi0, (const T *)L.dS,
+                        (const T *)L.uproj, (const T *)L.vnorm,
+                        h->moving ? (const T *)h->d_vtab : nullptr,
+                        h->moving ? (const T *)h->d_vtab + h->atom.n_freq : nullptr};
 }
 
 // Upwind crossing of every (ray, sweep step): for step t the plane is
@@ -283,13 +290,14 @@ int threads_for_band(int band) {
 // the number of bands that brings the grid closest to two blocks per SM (the
 // shapes measured fastest on the 64x64 planes of the bench workload, in both
 // precisions, were of this kind); mg3d_autotune replaces it by measurement.
-SweepShape choose_shape(int prec, int nx, int ny, int nfreq, int herm) {
+SweepShape choose_shape(int prec, int nx, int ny, int nfreq, int herm, int vel) {
     const int ng = nfreq < 3 ? nfreq : 3;
     const int ngroups = (nfreq + ng - 1) / ng;
     SweepShape best{};
     auto with_mode = [&](SweepShape s) {
         s.herm = herm;
-        s.stage = herm ? 0 : 1;
+        s.vel = vel;
+        s.stage = herm || vel ? 0 : 1;
         return s;
     };
     long best_gap = 1L << 40;
@@ -341,7 +349,7 @@ void free_level(Level &L) {
     void *ptrs[] = {L.T,     L.n_tot, L.c_ul, L.c_lu, L.tz,   L.zf,   L.n,    L.f,   L.n_before,
                     L.r,     L.chi0,  L.S,    L.bbot, L.geom, L.chi_c, L.cmat, L.saha,
                     L.mchi,  L.mS,    L.msl,  L.mfl,  L.mib,  L.sigma_c, L.jbg,
-                    L.dchi0, L.dS,   L.mdchi, L.mdS};
+                    L.dchi0, L.dS,   L.mdchi, L.mdS,  L.vel,  L.uproj, L.vnorm};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     L = Level{};
@@ -832,7 +840,8 @@ int make_shape(const mg3d_handle *h, int k, int ng, int bands, int threads, Swee
     SweepShape s{ng, (nf + ng - 1) / ng, bands, (L.ny + bands - 1) / bands, threads};
     if ((long)(bands - 1) * s.rows >= L.ny) return fail(MG3D_E_ARG, "empty band");
     s.herm = h->params.sc_interp;
-    s.stage = s.herm ? 0 : 1;
+    s.vel = h->moving ? 1 : 0;
+    s.stage = s.herm || s.vel ? 0 : 1;
     *out = s;
     return MG3D_OK;
 }
@@ -848,6 +857,7 @@ static int shape_from_args(const mg3d_handle *h, int level, int freq_per_block, 
     if (stage != 0 && stage != 1) return fail(MG3D_E_ARG, "stage must be 0 or 1");
     if (stage && h->params.sc_interp)
         return fail(MG3D_E_ARG, "Hermite upwind interpolation runs unstaged (stage 0)");
+    if (stage && h->moving) return fail(MG3D_E_ARG, "moving atmospheres run unstaged (stage 0)");
     SweepShape s;
     MG_TRY(make_shape(h, level, freq_per_block, bands, threads, &s));
     s.lean = lean;
@@ -1003,12 +1013,68 @@ int autotune_level(mg3d_handle *h, int k, int *evaluated) {
     return MG3D_OK;
 }
 
+// Velocity field of a moving atmosphere: the fine field, full-weighted onto
+// every coarser grid like the other atmosphere fields; per level and ray the
+// projected velocity and the profile normalisation; the frequency offsets
+// and quadrature weights in natural order.
+int setup_velocity(mg3d_handle *h, const double *vel_host) {
+    const int nf = h->atom.n_freq;
+    const size_t es = elem_size(h->prec);
+    std::vector<double> xw(2 * (size_t)nf);
+    for (int i = 0; i < nf; ++i) {
+        xw[i] = nf == 1 ? 0.0 : h->atom.x_max * (2 * i - (nf - 1)) / (nf - 1);
+        double w = nf == 1 ? 1.0 : 2.0 * h->atom.x_max / (nf - 1);
+        if (nf > 1 && (i == 0 || i == nf - 1)) w *= 0.5;
+        xw[nf + i] = w;
+    }
+    MG_TRY(dev_alloc(&h->d_vtab, 2 * (size_t)nf * es));
+    if (h->prec == MG3D_PREC_F64) {
+        MG_CUDA(cudaMemcpy(h->d_vtab, xw.data(), xw.size() * es, cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> f32(xw.begin(), xw.end());
+        MG_CUDA(cudaMemcpy(h->d_vtab, f32.data(), f32.size() * es, cudaMemcpyHostToDevice));
+    }
+    for (int k = 1; k <= h->L; ++k) MG_TRY(dalloc(&h->lev[k].vel, 3 * (size_t)h->lev[k].nvox));
+    Level &F = h->lev[h->L];
+    MG_CUDA(cudaMemcpy(F.vel, vel_host, 3 * (size_t)F.nvox * sizeof(double),
+                       cudaMemcpyHostToDevice));
+    for (int k = h->L; k >= 2; --k) {
+        Level &Fk = h->lev[k];
+        MG_TRY(launched(h, launch_restrict(3, Fk.nx, Fk.ny, Fk.nz, Fk.vel, h->lev[k - 1].vel,
+                                           h->stream),
+                        "restrict velocity"));
+    }
+    double *dmu = nullptr, *dxw = nullptr;
+    MG_TRY(dalloc(&dmu, 3 * (size_t)kRays));
+    int rc = dalloc(&dxw, xw.size());
+    if (rc == MG3D_OK && (cudaMemcpy(dmu, h->mu, 3 * kRays * sizeof(double),
+                                     cudaMemcpyHostToDevice) != cudaSuccess ||
+                          cudaMemcpy(dxw, xw.data(), xw.size() * sizeof(double),
+                                     cudaMemcpyHostToDevice) != cudaSuccess))
+        rc = fail(MG3D_E_CUDA, "velocity tables");
+    for (int k = 1; k <= h->L && rc == MG3D_OK; ++k) {
+        Level &L = h->lev[k];
+        rc = dev_alloc(&L.uproj, (size_t)kRays * L.nvox * es);
+        if (rc == MG3D_OK) rc = dev_alloc(&L.vnorm, (size_t)kRays * L.nvox * es);
+        if (rc == MG3D_OK)
+            rc = launched(h, launch_vel_prep(h->prec, L.nvox, nf, dmu, L.vel, dxw, dxw + nf,
+                                             L.uproj, L.vnorm, h->stream),
+                          "velocity projection");
+    }
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess && rc == MG3D_OK)
+        rc = fail(MG3D_E_CUDA, "velocity set-up");
+    cudaFree(dmu);
+    if (dxw) cudaFree(dxw);
+    return rc;
+}
+
 int create_impl(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_quadrature *quad,
                 const mg3d_params *params, mg3d_handle *h) {
     h->L = params->n_grids;
     h->prec = params->fs_prec;
     h->atom = *atom;
     h->params = *params;
+    h->moving = atm->vel != nullptr;
     build_quadrature(h, quad ? quad->a : 0.0);
     build_frequencies(h);
     MG_CUDA(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
@@ -1058,7 +1124,8 @@ int create_impl(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_qu
         std::vector<StepGeom> g;
         build_geometry(h, L, g);
         MG_CUDA(cudaMemcpy(L.geom, g.data(), g.size() * sizeof(StepGeom), cudaMemcpyHostToDevice));
-        L.shape = choose_shape(h->prec, L.nx, L.ny, atom->n_freq, params->sc_interp);
+        L.shape = choose_shape(h->prec, L.nx, L.ny, atom->n_freq, params->sc_interp,
+                               atm->vel ? 1 : 0);
         if (params->sc_interp) {
             MG_TRY(dev_alloc(&L.dchi0, L.nvox * es));
             MG_TRY(dev_alloc(&L.dS, L.nvox * es));
@@ -1091,6 +1158,7 @@ int create_impl(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_qu
         MG_CUDA(cudaMemcpyAsync(Ck.c_ul, coarse + 2 * Ck.nvox, Ck.nvox * 8,
                                 cudaMemcpyDeviceToDevice, h->stream));
     }
+    if (h->moving) MG_TRY(setup_velocity(h, atm->vel));
     for (int k = 1; k <= h->L; ++k) {
         Level &L = h->lev[k];
         MG_TRY(launched(h, launch_collisions_up(L.nvox, atom->g_ratio, atom->theta, L.T, L.c_ul,
@@ -1994,6 +2062,8 @@ int mg3d_create(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_qu
         return fail(MG3D_E_ARG, "interpolation must be 0 or 1");
     if (params->sc_interp < 0 || params->sc_interp > 1)
         return fail(MG3D_E_ARG, "sc_interp must be 0 or 1");
+    if (atm->vel && params->sc_interp)
+        return fail(MG3D_E_ARG, "moving atmospheres take the linear upwind interpolation");
     if (atom->n_freq < 1 || atom->n_freq > 4096 || !(atom->x_max >= 0.0) ||
         !(atom->a_ul > 0.0) || !(atom->g_ratio > 0.0) || !(atom->theta > 0.0) ||
         !(atom->kappa > 0.0))
@@ -2209,6 +2279,8 @@ int mg3d_batch_create(int n, mg3d_handle *const *members, mg3d_batch **out) {
             return fail(MG3D_E_ARG, "batches do not take background scattering");
         if (members[i]->params.sc_interp)
             return fail(MG3D_E_ARG, "batches do not take Hermite upwind interpolation");
+        if (members[i]->moving)
+            return fail(MG3D_E_ARG, "batches do not take moving atmospheres");
         for (int j = 0; j < i; ++j)
             if (members[j] == members[i]) return fail(MG3D_E_ARG, "member listed twice");
     }
@@ -2381,7 +2453,7 @@ int mg3d_destroy(mg3d_handle *h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     drop_graphs(h);
     for (int k = 0; k <= MG3D_MAX_GRIDS; ++k) free_level(h->lev[k]);
-    void *ptrs[] = {h->d_ftab, h->d_exp_tab, h->pj, h->pu, h->scal,
+    void *ptrs[] = {h->d_ftab, h->d_vtab, h->d_exp_tab, h->pj, h->pu, h->scal,
                     h->scratch, h->d_fi, h->d_ti, h->ml_jx, h->ml_ux, h->ml_acc,
                     h->ml_jm};
     for (void *p : ptrs)

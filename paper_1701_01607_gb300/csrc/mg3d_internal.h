@@ -36,7 +36,11 @@ struct SweepShape {
                   // registers), 2: three 256-thread blocks per SM (85 registers)
     int stage = 1; // 1: chi0/S rows staged in shared memory one step ahead
     int herm = 0;  // 1: monotone cubic Hermite upwind interpolation (unstaged)
+    int vel = 0;   // 1: moving atmosphere, ray-dependent profiles (unstaged)
 };
+
+// Sweep variants: linear upwind interpolation, Hermite, moving atmosphere.
+constexpr int kSweepLinear = 0, kSweepHermite = 1, kSweepMoving = 2;
 
 // Arguments of the sweep kernel.  T is the formal-solution precision.
 template <typename T>
@@ -55,6 +59,10 @@ struct SweepArgs {
     const double *exp_tab;   // [kExpTab] 2^{j/kExpTab} for the FP64 exp (FP64 sweeps only)
     double exp_l1, exp_l2;   // two-part ln2/kExpTab
     const T *dchi0, *dS;     // [nvox] x-slopes of chi0 and S (Hermite sweeps only)
+    // moving atmospheres only: per ray and node the projected velocity and
+    // the profile normalisation [kRays][nvox]; per frequency (natural order)
+    // the offset x_f and the quadrature weight w_f [nfreq]
+    const T *uproj, *vnorm, *xf, *wq;
 };
 
 // Table and reduction constants of the FP64 e^{-x} of the sweep.
@@ -63,6 +71,12 @@ cudaError_t launch_exp_check(int n, const double *x, double *out, const double *
                              double l2, cudaStream_t st);
 
 size_t sweep_smem_bytes(int prec, const SweepShape &s, int nx);
+// Projected velocities and profile normalisations of a level ([kRays][nvox]
+// each) from mu [kRays][3], the velocity [3][nvox] and the frequency offsets
+// and weights [nfreq].
+cudaError_t launch_vel_prep(int prec, long nvox, int nfreq, const double *mu, const double *vel,
+                            const double *xf, const double *wq, void *uproj, void *vnorm,
+                            cudaStream_t st);
 // Monotone x-slopes (one cell units, periodic rows of nx) of a and b.
 cudaError_t launch_xslopes(int prec, int nx, long nvox, const void *a, const void *b, void *da,
                            void *db, cudaStream_t st);

@@ -40,7 +40,7 @@ _D = ctypes.POINTER(ctypes.c_double)
 class mg3d_atmosphere(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double),
-                ("z", _D), ("T", _D), ("n_tot", _D), ("c_ul", _D)]
+                ("z", _D), ("T", _D), ("n_tot", _D), ("c_ul", _D), ("vel", _D)]
 
 
 class mg3d_atom(ctypes.Structure):
@@ -223,8 +223,10 @@ def mg3d_create(atm, atom, quad_a: float = 0.0, n_grids: int = 1, nu_fmg: int = 
     T = np.ascontiguousarray(atm.T, dtype=np.float64)
     n_tot = np.ascontiguousarray(atm.n_tot, dtype=np.float64)
     c_ul = np.ascontiguousarray(atm.c_ul, dtype=np.float64)
+    vel = getattr(atm, "vel", None)
+    vel = None if vel is None else np.ascontiguousarray(vel, dtype=np.float64)
     a = mg3d_atmosphere(atm.nx, atm.ny, atm.nz, atm.dx, atm.dy, _dptr(z), _dptr(T),
-                        _dptr(n_tot), _dptr(c_ul))
+                        _dptr(n_tot), _dptr(c_ul), _dptr(vel))
     at = mg3d_atom(atom.a_ul, atom.g_ratio, atom.theta, atom.kappa, atom.n_freq, atom.x_max)
     q = mg3d_quadrature(quad_a)
     p = mg3d_params(n_grids, nu_fmg, nu0, nu1, nu2, nu3, fs_prec, restriction, 0, interpolation,
