@@ -566,6 +566,73 @@ def run_scattering(args):
     return out
 
 
+def _to_target(m, make, grids, n_ref, step, cap, target=1e-3):
+    """Iterations (step(h, it)) of a fresh handle until the true error
+    E_inf against n_ref is <= target; wall time of the steps only."""
+    h = make()
+    secs, errs = 0.0, []
+    try:
+        for it in range(cap):
+            t0 = time.perf_counter()
+            step(h, it)
+            secs += time.perf_counter() - t0
+            n = m.mg3d_get_populations(h, grids)
+            errs.append(float(np.max(np.abs(n - n_ref) / np.abs(n_ref))))
+            if errs[-1] <= target:
+                break
+    finally:
+        m.mg3d_destroy(h)
+    return {"reached": errs[-1] <= target, "iterations": len(errs), "seconds": round(secs, 3),
+            "e_inf_last": float(f"{errs[-1]:.3g}")}
+
+
+def run_velocity(args):
+    """Moving atmospheres (CRD with Doppler-shifted profiles): the 64x64x129
+    box (eps = 1e-4, sigma = 0.3) with a 17-point frequency grid on
+    [-5, 5] Doppler widths, static and with a seeded velocity field of rms 1
+    Doppler width; FP64 MALI and 3-grid FAS to E_inf <= 1e-3 against each
+    case's FAS reference converged to C < 1e-9, and the autotuned sweep time
+    of each case in FP64 and FP32.  Opt-in, --velocity-experiment; prints one
+    JSON line."""
+    from paper_1701_01607_gb300 import mg3d as m
+    from paper_1701_01607_gb300 import synth
+    m.load(build_if_missing=True)
+    atom = synth.TwoLevelAtom(n_freq=17, x_max=5.0)
+    out = {"metric": "iterations and seconds to E_inf <= 1e-3; sweep ms per launch",
+           "unit": "s", "higher_is_better": False, "n_gpus": 1, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": "64x64x129 two-level box, eps 1e-4, sigma 0.3, seed 1, "
+                                  "17 frequencies on [-5, 5]", "nu": NU, "target_e_inf": 1e-3}}
+    for vel in (0.0, 1.0):
+        atm, _ = synth.stratified_two_level(GRID[0], GRID[1], GRID[2], eps=1e-4, sigma=0.3,
+                                            seed=1, atom=atom, velocity=vel)
+        ref = m.mg3d_create(atm, atom, n_grids=3, **NU)
+        m.mg3d_fas_solve(ref, 1e-9, 400, n_grids=3)
+        n_ref = m.mg3d_get_populations(ref, 3)
+        m.mg3d_destroy(ref)
+        row = {"fas": _to_target(m, lambda: m.mg3d_create(atm, atom, n_grids=3, **NU), 3, n_ref,
+                                 lambda h, it: m.mg3d_fas_vcycle(h, it == 0), 60),
+               "mali": _to_target(m, lambda: m.mg3d_create(atm, atom, n_grids=1, **NU), 1, n_ref,
+                                  lambda h, it: m.mg3d_mali_sweep(h, 1, 1), 3000)}
+        for prec, pname in ((m.MG3D_PREC_F64, "f64"), (m.MG3D_PREC_F32, "f32")):
+            h = m.mg3d_create(atm, atom, n_grids=1, fs_prec=prec, **NU)
+            try:
+                m.mg3d_autotune(h)
+                m.mg3d_set_timing(h, True)
+                m.mg3d_reset_counters(h)
+                for _ in range(5):
+                    m.mg3d_formal_solve(h, 1, want=False)
+                c = m.mg3d_get_counters(h)
+                row[f"sweep_{pname}"] = {
+                    "ms": round(c["fs_kernel_ms"] / c["fs_timed_launches"], 3),
+                    "gunits_s": round(c["fs_units"] / (c["fs_kernel_ms"] * 1e-3) / 1e9, 2),
+                    "shape": list(m.mg3d_get_fs_config(h, 1))}
+            finally:
+                m.mg3d_destroy(h)
+        out["moving" if vel else "static"] = row
+    return out
+
+
 def run_interpolation(args):
     """The Hermite options of Sec. 3 and Sec. 4.5 on the 64x64x129 two-level
     box (eps = 1e-4; rough sigma = 0.3 and smooth sigma = 0), FP64:
@@ -582,23 +649,6 @@ def run_interpolation(args):
            "unit": "s", "higher_is_better": False, "n_gpus": 1, "dtype": "f64",
            "data": "synthetic", "config": {"nu": NU, "target_e_inf": 1e-3}}
 
-    def to_target(make, grids, n_ref, step, cap):
-        h = make()
-        secs, errs = 0.0, []
-        try:
-            for it in range(cap):
-                t0 = time.perf_counter()
-                step(h, it)
-                secs += time.perf_counter() - t0
-                n = m.mg3d_get_populations(h, grids)
-                errs.append(float(np.max(np.abs(n - n_ref) / np.abs(n_ref))))
-                if errs[-1] <= 1e-3:
-                    break
-        finally:
-            m.mg3d_destroy(h)
-        return {"reached": errs[-1] <= 1e-3, "iterations": len(errs), "seconds": round(secs, 3),
-                "e_inf_last": float(f"{errs[-1]:.3g}")}
-
     for name, sigma in (("rough", 0.3), ("smooth", 0.0)):
         atm, atom = synth.stratified_two_level(GRID[0], GRID[1], GRID[2], eps=1e-4,
                                                sigma=sigma, seed=1)
@@ -609,12 +659,13 @@ def run_interpolation(args):
             m.mg3d_destroy(ref)
             row = {}
             for interp in (0, 1):
-                row[f"fas_{'hermite' if interp else 'trilinear'}"] = to_target(
-                    lambda: m.mg3d_create(atm, atom, n_grids=3, sc_interp=sc,
-                                          interpolation=interp, **NU),
+                row[f"fas_{'hermite' if interp else 'trilinear'}"] = _to_target(
+                    m, lambda: m.mg3d_create(atm, atom, n_grids=3, sc_interp=sc,
+                                             interpolation=interp, **NU),
                     3, n_ref, lambda h, it: m.mg3d_fas_vcycle(h, it == 0), 60)
-            row["mali"] = to_target(lambda: m.mg3d_create(atm, atom, n_grids=1, sc_interp=sc, **NU),
-                                    1, n_ref, lambda h, it: m.mg3d_mali_sweep(h, 1, 1), 2000)
+            row["mali"] = _to_target(
+                m, lambda: m.mg3d_create(atm, atom, n_grids=1, sc_interp=sc, **NU),
+                1, n_ref, lambda h, it: m.mg3d_mali_sweep(h, 1, 1), 2000)
             out[f"{name}_upwind_{'hermite' if sc else 'linear'}"] = row
 
     sweeps = {}
@@ -807,6 +858,8 @@ def main():
                     help="run the restriction / grid-count experiments instead")
     ap.add_argument("--chromosphere", action="store_true",
                     help="time MALI, FAS and FMG on the 128x128x257 6-level chromosphere instead")
+    ap.add_argument("--velocity-experiment", action="store_true",
+                    help="a moving atmosphere against a static one")
     ap.add_argument("--interp-experiment", action="store_true",
                     help="the Hermite interpolation options against the linear ones")
     ap.add_argument("--scattering-experiment", action="store_true",
@@ -833,6 +886,9 @@ def main():
         return
     if args.batch:
         print(json.dumps(run_batch(args)), flush=True)
+        return
+    if args.velocity_experiment:
+        print(json.dumps(run_velocity(args)), flush=True)
         return
     if args.interp_experiment:
         print(json.dumps(run_interpolation(args)), flush=True)
