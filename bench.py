@@ -54,7 +54,7 @@ FP64_NOMINAL_TFLOPS = 1.25      # GB300, at the 2070 MHz maximum SM clock
 # DRAM bytes (read + write) of one finest-grid FP64 sweep launch, from one ncu
 # capture of the current kernel at this launch shape (ng, bands, threads,
 # lean, stage); reported only when the autotuner picks the same shape
-FINE_SWEEP_TRAFFIC = {"shape": [9, 5, 512, 0, 0], "bytes": 13247744 + 142105600}
+FINE_SWEEP_TRAFFIC = {"shape": [9, 5, 512, 0, 0], "bytes": 13261312 + 141663488}
 SM_MAX_MHZ = 2070.0
 
 
