@@ -422,7 +422,7 @@ class TwoLevelProblem:
         r = f[k] - self.W(k, n[k])
         # coarse-grid equation (Eq. 9)
         n[k - 1] = self.restrict(k, n[k])
-        self.coarse_entry(k)
+        self.coarse_entry(k, n[k - 1])
         n_before = n[k - 1].copy()
         f[k - 1] = self.restrict(k, r) + self.W(k - 1, n[k - 1])
         if k - 1 == 1:
@@ -441,7 +441,7 @@ class TwoLevelProblem:
         for _ in range(params["nu2"]):
             n[k], _ = self.mali_sweep(k, n[k], f[k])
 
-    def coarse_entry(self, k: int):
+    def coarse_entry(self, k: int, n_coarse):
         """Hook: a V-cycle enters grid k-1 from k (no state to move here)."""
 
     def fmg_prolong(self, k: int):
@@ -449,6 +449,7 @@ class TwoLevelProblem:
 
     def fas_cycle(self, n_fine, first: bool, params):
         L = self.n_grids
+        self.top = L
         n = {L: n_fine.copy()}
         f = {L: self.default_rhs(L)}
         self.vcycle(L, n, f, first, params)
@@ -728,11 +729,13 @@ def fmg_solve(prob: TwoLevelProblem, tol: float, params, max_cycles: int = 1000,
     approximation upward with one V-cycle per intermediate level, then
     regular V-cycles on the finest grid until C < tol."""
     L = prob.n_grids
+    prob.top = 1          # the grid the current stage solves on
     n1 = prob.zero_radiation(1)
     for _ in range(params["nu_fmg"]):
         n1, _ = prob.mali_sweep(1, n1)
     n_k = n1
     for k in range(2, L + 1):
+        prob.top = k
         n_k = prob.prolong(k, n_k)
         prob.fmg_prolong(k)
         if k < L:
@@ -770,6 +773,7 @@ class MLLevel:
     c: np.ndarray       # [N, N, nz, ny, nx]
     saha: np.ndarray    # [N, nz, ny, nx]
     sigma_c: np.ndarray  # background coherent scattering coefficient
+    vel: np.ndarray | None = None   # [3, nz, ny, nx] in Doppler widths at t_ref
 
     @property
     def shape(self):
@@ -783,7 +787,7 @@ def coarsen_ml_level(lev: MLLevel) -> MLLevel:
     return MLLevel(lev.nx // 2, lev.ny // 2, (lev.nz + 1) // 2, 2 * lev.dx, 2 * lev.dy,
                    lev.z[::2].copy(), restrict_fw(lev.T), restrict_fw(lev.n_tot),
                    restrict_fw(lev.chi_c), restrict_fw(lev.c), restrict_fw(lev.saha),
-                   restrict_fw(lev.sigma_c))
+                   restrict_fw(lev.sigma_c), None if lev.vel is None else restrict_fw(lev.vel))
 
 
 def formal_solution_nu_raw(z, dx, dy, mu, wray, chi, S, sl, fl, I_bottom, I_top,
@@ -869,10 +873,12 @@ class MultiLevelProblem(TwoLevelProblem):
         self.mu, self.wray = a4_quadrature(quad_a)
         sigma = getattr(atm, "sigma_c", None)
         sigma = (np.zeros(np.shape(atm.T)) if sigma is None else np.asarray(sigma, float))
+        vel = getattr(atm, "vel", None)
         fine = MLLevel(atm.nx, atm.ny, atm.nz, atm.dx, atm.dy, np.asarray(atm.z, float),
                        np.asarray(atm.T, float), np.asarray(atm.n_tot, float),
                        np.asarray(atm.chi_c, float), np.asarray(atm.c, float),
-                       np.asarray(atm.saha, float), sigma)
+                       np.asarray(atm.saha, float), sigma,
+                       None if vel is None else np.asarray(vel, float))
         self.scatter = bool(np.any(sigma > 0))
         self.levels = {n_grids: fine}
         for k in range(n_grids - 1, 0, -1):
@@ -893,6 +899,10 @@ class MultiLevelProblem(TwoLevelProblem):
         nf = len(self.freqs)
         # background radiation field per grid, [nfreq, nvox]
         self.jbg = {k: np.zeros((nf, lev.nx * lev.ny * lev.nz)) for k, lev in self.levels.items()}
+        # the grid a solve or V-cycle currently treats as its finest: only its
+        # formal solutions update its background field (see coarse_entry)
+        self.top = n_grids
+        self._force_bg = False
 
     def planck_rho(self, rho, T):
         return rho ** 3 / np.expm1(self.atom.theta_ref * rho / T)
@@ -962,6 +972,8 @@ class MultiLevelProblem(TwoLevelProblem):
         background scattering the grid's background field becomes this
         solution's mean intensity."""
         lev = self.levels[k]
+        if lev.vel is not None:
+            return self.formal_solution_moving(k, n)
         terms, Ib = self.transition_terms(k, n)
         nf = len(self.freqs)
         shp = (nf,) + lev.shape
@@ -971,23 +983,40 @@ class MultiLevelProblem(TwoLevelProblem):
                                      Ib.reshape((nf, lev.ny, lev.nx)), 0.0,
                                      want_j=self.scatter, interp=self.sc_interp)
         Jx, Ux = res[0], res[1]
-        if self.scatter:
+        if self.updates_background(k):
             self.jbg[k] = res[2].reshape(nf, -1)
         self.fs_count[k] += 1
         return Jx.reshape(nf, -1), Ux.reshape(nf, -1), terms
 
+    def updates_background(self, k: int) -> bool:
+        """Whether a formal solution on grid k replaces the grid's background
+        field by its own mean intensity: on the grid being solved (the finest
+        of the V-cycle, or of the FMG stage) always; on a coarser grid only in
+        the Lambda-iteration that starts it, so that W on that grid is one
+        operator from the tau-correction of Eq. 9 to the correction of Eq. 10
+        (a converged fine solution then gets a zero correction)."""
+        return self.scatter and (k == self.top or self._force_bg)
+
     def lambda_iteration(self, k: int, n):
         """One Lambda-iteration of the background field (Sec. 4.8): a formal
-        solution with the populations held."""
-        self.formal_solution(k, n)
+        solution with the populations held, whose mean intensity becomes the
+        field."""
+        self._force_bg = True
+        try:
+            self.formal_solution(k, n)
+        finally:
+            self._force_bg = False
 
-    def coarse_entry(self, k: int):
-        """Entering grid k-1 from k in a V-cycle: the background field of k,
-        full-weighted (Sec. 4.8)."""
+    def coarse_entry(self, k: int, n_coarse):
+        """Entering grid k-1 from k in a V-cycle (Sec. 4.8): the background
+        field of k, full-weighted, then one Lambda-iteration with the
+        restricted populations; the field then stays fixed on grid k-1
+        until the cycle leaves it."""
         if self.scatter:
             fine = self.levels[k]
             jf = self.jbg[k].reshape((-1,) + fine.shape)
             self.jbg[k - 1] = restrict_fw(jf).reshape(jf.shape[0], -1)
+            self.lambda_iteration(k - 1, n_coarse)
 
     def fmg_prolong(self, k: int):
         """FMG moving the full approximation from grid k-1 to k: the
@@ -996,6 +1025,80 @@ class MultiLevelProblem(TwoLevelProblem):
             coarse = self.levels[k - 1]
             jc = self.jbg[k - 1].reshape((-1,) + coarse.shape)
             self.jbg[k] = self.prolong(k, jc).reshape(jc.shape[0], -1)
+
+    def formal_solution_moving(self, k: int, n):
+        """Formal solution in a moving atmosphere (the same reading as for the
+        two-level atom): along ray r a line's profile at a node is
+        phi((x - mu_r . u)/d)/(d sqrt(pi)), d the node's Doppler width in
+        units of the one at t_ref, renormalised over the line's frequencies
+        per node and ray; continua and the background do not shift.  Line
+        opacity, emissivity and so chi, S and the transition shares depend
+        on the ray, and so does the profile weight of the rates: each ray is
+        solved on its own, and its angle sums enter the line sums weighted by
+        its own profile weight.  Returned: those weighted sums with rate
+        weights without the profile factor for lines (qa = g_u/g_l B_ul,
+        qb = B_ul, qe = A_ul), and the plain sums with the usual weights for
+        continua, so that the rates sum q J as in the static case."""
+        lev = self.levels[k]
+        at = self.atom
+        terms, Ib = self.transition_terms(k, n)
+        T = lev.T.reshape(-1)
+        nvox = T.size
+        nf = len(self.freqs)
+        d = np.sqrt(T / at.t_ref)
+        nn = n.reshape(self.N, -1)
+        chi_c = lev.chi_c.reshape(-1)
+        sigma = lev.sigma_c.reshape(-1)
+        u = lev.vel.reshape(3, -1)
+        Jw = np.zeros((nf, nvox))
+        Uw = np.zeros((nf, nvox))
+        Jm = np.zeros((nf, nvox))
+        line_freqs = {}
+        for f, (kind, ti, xv, wv) in enumerate(self.freqs):
+            if kind == "line":
+                line_freqs.setdefault(ti, []).append(f)
+        shp = (nf,) + lev.shape
+        for r in range(len(self.wray)):
+            ur = self.mu[r] @ u
+            chi, S = terms["chi"].copy(), terms["S"].copy()
+            sl, fl = terms["sl"].copy(), terms["fl"].copy()
+            w = np.ones((nf, nvox))
+            for ti, fs in line_freqs.items():
+                ln = at.lines[ti]
+                lo, up = ln.lower, ln.upper
+                gr = at.g[up] / at.g[lo]
+                B = self.planck_rho(ln.rho, T)
+                phis = [np.exp(-((self.freqs[f][2] - ur) / d) ** 2) / (math.sqrt(math.pi) * d)
+                        for f in fs]
+                norm = sum(self.freqs[f][3] * ph for f, ph in zip(fs, phis))
+                for f, ph in zip(fs, phis):
+                    chi_t = ln.kappa * ph * (nn[lo] * gr - nn[up])
+                    eta_t = ln.kappa * ln.rho ** 3 * ph * nn[up]
+                    chi[f] = chi_t + chi_c + sigma
+                    S[f] = (eta_t + chi_c * B + sigma * self.jbg[k][f]) / chi[f]
+                    sl[f] = eta_t / chi[f]
+                    fl[f] = chi_t / chi[f]
+                    w[f] = self.freqs[f][3] * ph / norm
+            res = formal_solution_nu_raw(lev.z, lev.dx, lev.dy, self.mu[r:r + 1],
+                                         self.wray[r:r + 1], chi.reshape(shp), S.reshape(shp),
+                                         sl.reshape(shp), fl.reshape(shp),
+                                         Ib.reshape((nf, lev.ny, lev.nx)), 0.0, want_j=True,
+                                         interp=self.sc_interp)
+            Jw += w * res[0].reshape(nf, -1)
+            Uw += w * res[1].reshape(nf, -1)
+            Jm += res[2].reshape(nf, -1)
+        for ti, fs in line_freqs.items():
+            ln = at.lines[ti]
+            gr = at.g[ln.upper] / at.g[ln.lower]
+            b_ul = ln.a_ul / ln.rho ** 3
+            for f in fs:
+                terms["qa"][f] = gr * b_ul
+                terms["qb"][f] = b_ul
+                terms["qe"][f] = ln.a_ul
+        if self.updates_background(k):
+            self.jbg[k] = Jm
+        self.fs_count[k] += 1
+        return Jw, Uw, terms
 
     def rate_matrix_from(self, k: int, Jx, Ux, terms):
         """M [nvox, N, N] with W(n) = M n: row 0 particle conservation (Eq. 3),

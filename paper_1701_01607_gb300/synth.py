@@ -250,6 +250,8 @@ class MultiLevelAtmosphere:
     c: np.ndarray        # [N, N, nz, ny, nx]
     saha: np.ndarray     # [N, nz, ny, nx] (0 for levels without a continuum)
     sigma_c: Optional[np.ndarray] = None
+    vel: Optional[np.ndarray] = None   # [3, nz, ny, nx] (x, y, z) velocity in units of
+                                       # the Doppler width at t_ref, or None (static)
 
     @property
     def shape(self):
@@ -311,7 +313,7 @@ def chromosphere(nx: int, ny: int, nz: int, atom: MultiLevelAtom, seed: int = 2,
                  n_bottom: float = 1e4, sigma_t: float = 0.1, ionisation: float = 1e-3,
                  saha_scale: float = 10.0, c_strength: float = 1e-2, chi_c0: float = 1e-2,
                  dx: float = 1.0, z=None, ground_collisions: float = 1.0,
-                 scattering: float = 0.0) -> MultiLevelAtmosphere:
+                 scattering: float = 0.0, velocity: float = 0.0) -> MultiLevelAtmosphere:
     """Chromosphere-like box: T rises from t_min to t_max with height (with
     seeded 3D perturbations of relative size sigma_t), the density falls by
     e^scale_heights from bottom to top; electron density = ionisation x
@@ -323,7 +325,10 @@ def chromosphere(nx: int, ny: int, nz: int, atom: MultiLevelAtom, seed: int = 2,
     ground_collisions scales the collisions out of the ground level only, so
     that the resonance lines can be made scattering-dominated while the upper
     lines keep the collisions that prevent inversions.  scattering > 0 adds
-    grey background coherent scattering sigma_c = scattering x chi_c."""
+    grey background coherent scattering sigma_c = scattering x chi_c.
+    velocity > 0 adds a flow whose three components are independent seeded
+    Gaussian random fields (seeds seed+101..103) with that rms, in Doppler
+    widths at t_ref."""
     rng = np.random.default_rng(seed)
     if z is None:
         z = np.arange(nz, dtype=np.float64) * dx
@@ -357,5 +362,9 @@ def chromosphere(nx: int, ny: int, nz: int, atom: MultiLevelAtom, seed: int = 2,
             c[j, i] = down
             c[i, j] = up
     sigma_c = scattering * chi_c if scattering > 0 else None
+    vel = None
+    if velocity > 0:
+        vel = np.stack([velocity * gaussian_random_field((nz, ny, nx), seed + 101 + k)
+                        for k in range(3)])
     return MultiLevelAtmosphere(nx=nx, ny=ny, nz=nz, dx=dx, dy=dx, z=z, T=T, n_tot=n_tot,
-                                chi_c=chi_c, c=c, saha=saha, sigma_c=sigma_c)
+                                chi_c=chi_c, c=c, saha=saha, sigma_c=sigma_c, vel=vel)

@@ -170,9 +170,11 @@ def test_background_scattering_converges_to_direct_solve():
 
 
 def test_background_scattering_conservation_and_fas():
-    """Scattering background: particle conservation in every sweep, and FAS
-    from the zero-radiation start converges (C < 1e-8) with the background
-    field restricted on each coarse-grid entry."""
+    """Scattering background: particle conservation in every sweep; FAS from
+    the zero-radiation start converges (C < 1e-8) with the background field
+    restricted on each coarse-grid entry, and FAS and FMG reach MALI's
+    solution (the coarse field is frozen after its Lambda-iteration, so a
+    converged fine solution gets no correction)."""
     atom = synth.hydrogen_like_atom(line_freq=5, cont_freq=3, seed=2)
     atm = synth.chromosphere(8, 8, 17, atom, seed=2, scattering=2.0)
     p = O.MultiLevelProblem(atm, atom, n_grids=2)
@@ -183,3 +185,10 @@ def test_background_scattering_conservation_and_fas():
     params = dict(nu_fmg=8, nu0=10, nu1=2, nu2=4, nu3=16)
     n, cyc = O.fas_solve(p, 1e-8, params, max_cycles=60)
     assert np.all(n > 0) and cyc < 60
+    n, _ = O.fas_solve(O.MultiLevelProblem(atm, atom, n_grids=2), 1e-11, params)
+    n_fmg, _ = O.fmg_solve(O.MultiLevelProblem(atm, atom, n_grids=2), 1e-11, params)
+    p1 = O.MultiLevelProblem(atm, atom)
+    n1 = p1.zero_radiation(1)
+    for _ in range(40):
+        n1, _ = p1.mali_sweep(1, n1)
+    assert O.max_rel_error(n, n1) < 1e-9 and O.max_rel_error(n_fmg, n1) < 1e-9

@@ -160,3 +160,70 @@ def test_moving_conservation_and_multigrid_agreement():
     assert O.max_rel_error(n_fmg, n_mali) < 1e-8
     # the coarse grids carry the full-weighted flow
     assert np.allclose(p.levels[2].vel, O.restrict_fw(atm.vel))
+
+
+# ------------------------------------------------------- multi-level atom
+
+def _ml(velocity=1.0, nx=4, nz=9, scattering=0.0):
+    atom = synth.hydrogen_like_atom(line_freq=5, cont_freq=3, seed=2)
+    atm = synth.chromosphere(nx, nx, nz, atom, seed=2, velocity=velocity, scattering=scattering)
+    return atm, atom
+
+
+def test_multilevel_zero_flow_equals_static_path():
+    """With u = 0 the weighted angle sums times the profile-free line weights
+    equal the static sums times the static weights, frequency by frequency,
+    so the rates and the MALI update agree."""
+    atm, atom = _ml(velocity=0.0)
+    p0 = O.MultiLevelProblem(atm, atom)
+    n = p0.zero_radiation(1)
+    J0, U0, t0 = p0.formal_solution(1, n)
+    atm.vel = np.zeros((3,) + atm.shape)
+    p1 = O.MultiLevelProblem(atm, atom)
+    J1, U1, t1 = p1.formal_solution(1, n)
+    for a, b in ((t1["qa"] * J1, t0["qa"] * J0), (t1["qb"] * J1, t0["qb"] * J0),
+                 (t1["qe"] * U1, t0["qe"] * U0)):
+        # on each frequency's scale: the sums differ in rounding order only
+        err = np.max(np.abs(a - b), axis=1) / np.max(np.abs(b), axis=1)
+        assert np.max(err) < 1e-12
+    na, _ = p0.mali_sweep(1, n)
+    nb, _ = p1.mali_sweep(1, n)
+    # the rate solve amplifies the rounding-order differences of the sums
+    assert O.max_rel_error(nb, na) < 1e-10
+
+
+def test_multilevel_reversed_flow_gives_the_same_populations():
+    """Line frequency grids are symmetric about line centre and continua do
+    not shift, so reversing the flow permutes each line's profile values
+    over its grid: the rates, and so the MALI iterates, do not change."""
+    atm, atom = _ml()
+    p = O.MultiLevelProblem(atm, atom)
+    n = p.zero_radiation(1)
+    na, _ = p.mali_sweep(1, n)
+    na, _ = p.mali_sweep(1, na)
+    atm.vel = -atm.vel
+    q = O.MultiLevelProblem(atm, atom)
+    nb, _ = q.mali_sweep(1, n)
+    nb, _ = q.mali_sweep(1, nb)
+    assert O.max_rel_error(nb, na) < 1e-10
+    atm.vel = np.zeros_like(atm.vel)
+    s = O.MultiLevelProblem(atm, atom)
+    ns, _ = s.mali_sweep(1, n)
+    ns, _ = s.mali_sweep(1, ns)
+    assert O.max_rel_error(ns, na) > 1e-4
+
+
+def test_multilevel_moving_conservation_and_fas():
+    atm, atom = _ml(nx=8, nz=17, scattering=1.0)
+    p = O.MultiLevelProblem(atm, atom, n_grids=2)
+    n = p.zero_radiation(2)
+    for _ in range(3):
+        n, _ = p.mali_sweep(2, n)
+        assert np.max(np.abs(n.sum(axis=0) / atm.n_tot - 1.0)) < 1e-13
+    n_fas, _ = O.fas_solve(p, 1e-10, PARAMS, max_cycles=60)
+    p1 = O.MultiLevelProblem(atm, atom, n_grids=1)
+    n_mali = p1.zero_radiation(1)
+    for _ in range(40):
+        n_mali, _ = p1.mali_sweep(1, n_mali)
+    assert O.max_rel_error(n_fas, n_mali) < 1e-9
+    assert np.allclose(p.levels[1].vel, O.restrict_fw(atm.vel))
