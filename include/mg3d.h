@@ -307,6 +307,16 @@ typedef struct {
                                runs one Lambda-iteration; a V-cycle entering a coarser
                                grid full-weights it; FMG prolongs it with the
                                populations.  Not supported in batches. */
+    const double *vel;      /* [3][nz][ny][nx] velocity in Doppler widths at t_ref, or
+                               NULL: a moving atmosphere.  Along ray r a line's profile
+                               at a node is phi((x - mu_r . vel)/d)/(d sqrt(pi)), d the
+                               node's Doppler width in units of the one at t_ref,
+                               renormalised over the line's frequencies per node and
+                               ray; continua and the background do not shift.  The
+                               per-frequency angle sums of mg3d_formal_solve_ml then
+                               carry each ray's normalised profile weight of a line
+                               inside the ray sum.  Linear upwind interpolation only;
+                               not supported in batches. */
 } mg3d_ml_atmosphere;
 
 /* Create a solver for a multi-level atom; everything else as mg3d_create.

@@ -73,6 +73,8 @@ struct Level {
     void *dchi0 = nullptr, *dS = nullptr;  // x-slopes of chi0, S (Hermite upwind interpolation)
     double *vel = nullptr;       // [3][nvox] velocity in Doppler widths (moving atmosphere)
     void *uproj = nullptr, *vnorm = nullptr;  // [kRays][nvox] projected velocity, 1/sum w phi
+                                              // (multi-level: vnorm [nlines][kRays][nvox])
+    void *dinv = nullptr;        // multi-level, moving: 1/d per node [nvox]
     StepGeom *geom = nullptr;    // [kRays][nz]
     SweepShape shape{};
     // multi-level atom only
@@ -113,6 +115,9 @@ struct mg3d_handle {
     int ml_chunk = 0;
     int ml_chunk_req = 0;        // chunk asked for (0: automatic), kept across retuning
     bool scatter = false;        // background coherent scattering present
+    int top = 0;                 // grid being solved (0: the finest); only its formal
+                                 // solutions update its background field
+    bool force_bg = false;       // the current formal solution is a Lambda-iteration
     void *ml_jm = nullptr;       // mean intensity per slot [slots][chunk][nvox] (scatter)
     int ml_slots = 2;            // most ray-group slots of any level (2 x 12 / ml_rpb)
     void *ml_jx = nullptr, *ml_ux = nullptr;
@@ -128,6 +133,7 @@ struct mg3d_handle {
     // in the formal-solution precision (see freq_tables)
     void *d_ftab = nullptr;
     void *d_vtab = nullptr;      // moving atmospheres: [nf] offsets x, [nf] weights w
+    int *d_vline = nullptr;      // multi-level, moving: line index of each frequency or -1
     bool moving = false;         // the atmosphere has a velocity field
     double *d_exp_tab = nullptr;         // [64] table of the FP64 exp in the sweep
     double exp_l1 = 0, exp_l2 = 0;
@@ -349,7 +355,7 @@ void free_level(Level &L) {
     void *ptrs[] = {L.T,     L.n_tot, L.c_ul, L.c_lu, L.tz,   L.zf,   L.n,    L.f,   L.n_before,
                     L.r,     L.chi0,  L.S,    L.bbot, L.geom, L.chi_c, L.cmat, L.saha,
                     L.mchi,  L.mS,    L.msl,  L.mfl,  L.mib,  L.sigma_c, L.jbg,
-                    L.dchi0, L.dS,   L.mdchi, L.mdS,  L.vel,  L.uproj, L.vnorm};
+                    L.dchi0, L.dS,   L.mdchi, L.mdS,  L.vel,  L.uproj, L.vnorm, L.dinv};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     L = Level{};
@@ -403,7 +409,8 @@ int ml_chunk_fs(mg3d_handle *h, int k, int f0, int nc) {
     MlOpacityArgs oa{L.nvox, nc, h->N, h->prec, h->d_fi, h->theta_ref, h->t_ref,
                      L.n, L.T, L.chi_c, L.saha, L.mchi, L.mS, L.msl, L.mfl, f0,
                      h->d_exp_tab, h->exp_l1, h->exp_l2,
-                     h->scatter ? L.sigma_c : nullptr, h->scatter ? L.jbg : nullptr};
+                     h->scatter ? L.sigma_c : nullptr, h->scatter ? L.jbg : nullptr,
+                     h->moving ? 1 : 0};
     MG_TRY(launched(h, launch_ml_opacity(oa, h->stream), "multi-level opacity"));
     if (h->params.sc_interp)
         MG_TRY(launched(h, launch_xslopes(h->prec, L.nx, (long)nc * L.nvox, L.mchi, L.mS, L.mdchi,
@@ -425,7 +432,10 @@ int ml_chunk_fs(mg3d_handle *h, int k, int f0, int nc) {
                               (const double *)ib, L.geom, h->d_exp_tab, h->exp_l1, h->exp_l2,
                               (double *)h->ml_jx, (double *)h->ml_ux, L.ml_rpb,
                               (double *)h->ml_jm, (const double *)L.mdchi, (const double *)L.mdS,
-                              h->params.sc_interp};
+                              h->params.sc_interp, h->moving ? 1 : 0, f0,
+                              (const double *)h->d_vtab, (const double *)h->d_vtab + h->nfreq_ml,
+                              h->d_vline, (const double *)L.vnorm, (const double *)L.uproj,
+                              (const double *)L.dinv};
         e = launch_ml_sweep_f64(a, L.ml_bands, L.ml_threads, h->stream);
     } else {
         MlSweepArgs<float> a{L.nx, L.ny, L.nz, nc, L.ml_rows,
@@ -434,7 +444,10 @@ int ml_chunk_fs(mg3d_handle *h, int k, int f0, int nc) {
                              (const float *)ib, L.geom, h->d_exp_tab, h->exp_l1, h->exp_l2,
                              (float *)h->ml_jx, (float *)h->ml_ux, L.ml_rpb,
                              (float *)h->ml_jm, (const float *)L.mdchi, (const float *)L.mdS,
-                             h->params.sc_interp};
+                             h->params.sc_interp, h->moving ? 1 : 0, f0,
+                             (const float *)h->d_vtab, (const float *)h->d_vtab + h->nfreq_ml,
+                             h->d_vline, (const float *)L.vnorm, (const float *)L.uproj,
+                             (const float *)L.dinv};
         e = launch_ml_sweep_f32(a, L.ml_bands, L.ml_threads, h->stream);
     }
     MG_TRY(launched(h, e, "multi-level sweep"));
@@ -445,15 +458,36 @@ int ml_chunk_fs(mg3d_handle *h, int k, int f0, int nc) {
     return MG3D_OK;
 }
 
+// Whether a formal solution of grid k replaces the grid's background field
+// by its mean intensity (Sec. 4.8): always on the grid being solved (the
+// finest of a V-cycle, the current grid of an FMG stage or of MALI); on a
+// coarser grid only in the Lambda-iteration that starts it, so that the
+// coarse operator stays the same from the tau-correction of Eq. 9 to the
+// correction of Eq. 10.
+bool updates_background(const mg3d_handle *h, int k) {
+    return h->scatter && (h->force_bg || k == (h->top ? h->top : h->L));
+}
+
+int ml_formal_solution(mg3d_handle *h, int k);
+
+// One Lambda-iteration of the background field of grid k: a formal solution
+// with the populations held whose mean intensity becomes the field.
+int lambda_iteration(mg3d_handle *h, int k) {
+    h->force_bg = true;
+    const int rc = ml_formal_solution(h, k);
+    h->force_bg = false;
+    return rc;
+}
+
 // Radiative sums of level k from the chunk's angle sums (zero_rad: J = 0,
 // U = 1 for all frequencies, no formal solution).
 int ml_accumulate(mg3d_handle *h, int k, int f0, int nc, bool zero_rad) {
     Level &L = h->lev[k];
-    const bool bg = h->scatter && !zero_rad;   // the new mean intensity becomes the field
+    const bool bg = !zero_rad && updates_background(h, k);   // the mean intensity becomes the field
     MlAccumArgs a{L.nvox, f0, nc, h->ntrans, h->prec, h->d_fi, h->d_ti, h->theta_ref,
                   h->t_ref, L.T, h->ml_jx, h->ml_ux, 2 * (12 / L.ml_rpb), zero_rad ? 1 : 0,
                   h->ml_acc, h->d_exp_tab, h->exp_l1, h->exp_l2, bg ? h->ml_jm : nullptr,
-                  bg ? L.jbg : nullptr};
+                  bg ? L.jbg : nullptr, h->moving ? 1 : 0};
     return launched(h, launch_ml_accum(a, h->stream), "radiative sums");
 }
 
@@ -607,7 +641,7 @@ int zero_radiation(mg3d_handle *h, int k) {
             MG_CUDA(cudaMemsetAsync(L.jbg, 0,
                                     (size_t)h->nfreq_ml * L.nvox * elem_size(h->prec),
                                     h->stream));
-            MG_TRY(ml_formal_solution(h, k));
+            MG_TRY(lambda_iteration(h, k));
         }
         return MG3D_OK;
     }
@@ -648,10 +682,15 @@ int vcycle(mg3d_handle *h, int k, bool first) {
                     "restrict n"));
     MG_CUDA(cudaMemcpyAsync(C.n_before, C.n, (size_t)h->N * C.nvox * sizeof(double),
                             cudaMemcpyDeviceToDevice, h->stream));
-    if (h->kind == 1 && h->scatter)   // background field, full-weighted (Sec. 4.8)
+    if (h->kind == 1 && h->scatter) {
+        // background field: full-weighted, then one Lambda-iteration with the
+        // restricted populations; fixed on this grid until the cycle leaves
+        // it (Sec. 4.8)
         MG_TRY(launched(h, launch_restrict_prec(h->prec, h->nfreq_ml, F.nx, F.ny, F.nz, F.jbg,
                                                 C.jbg, h->stream),
                         "restrict background field"));
+        MG_TRY(lambda_iteration(h, k - 1));
+    }
     MG_TRY(launched(h, launch_restrict(h->N, F.nx, F.ny, F.nz, F.r, C.f, h->stream,
                                        h->params.restriction),
                     "restrict r"));
@@ -774,6 +813,7 @@ int graph_cycle(mg3d_handle *h, bool first) {
 // a CUDA graph unless graphs are off or per-launch timing is on.
 int fas_cycle(mg3d_handle *h, bool first, double *C, long long *neg) {
     if (h->L < 2) return fail(MG3D_E_STATE, "a V-cycle needs n_grids >= 2");
+    h->top = h->L;
     const bool graphs = h->use_graphs;
     if (graphs) {
         MG_TRY(graph_cycle(h, first));
@@ -1294,7 +1334,11 @@ int time_ml_shape(mg3d_handle *h, int k, int bands, int rpb, int threads, int nc
                                    (const double *)L.mib, L.geom, h->d_exp_tab, h->exp_l1,
                                    h->exp_l2, (double *)h->ml_jx, (double *)h->ml_ux, rpb,
                                    nullptr, (const double *)L.mdchi, (const double *)L.mdS,
-                                   h->params.sc_interp};
+                                   h->params.sc_interp, h->moving ? 1 : 0, 0,
+                                   (const double *)h->d_vtab,
+                                   (const double *)h->d_vtab + h->nfreq_ml, h->d_vline,
+                                   (const double *)L.vnorm, (const double *)L.uproj,
+                                   (const double *)L.dinv};
             e = launch_ml_sweep_f64(sa, bands, threads, h->stream);
         } else {
             MlSweepArgs<float> sa{L.nx, L.ny, L.nz, nc, L.ml_rows,
@@ -1303,7 +1347,11 @@ int time_ml_shape(mg3d_handle *h, int k, int bands, int rpb, int threads, int nc
                                   (const float *)L.mib, L.geom, h->d_exp_tab, h->exp_l1,
                                   h->exp_l2, (float *)h->ml_jx, (float *)h->ml_ux, rpb,
                                   nullptr, (const float *)L.mdchi, (const float *)L.mdS,
-                                  h->params.sc_interp};
+                                  h->params.sc_interp, h->moving ? 1 : 0, 0,
+                                  (const float *)h->d_vtab,
+                                  (const float *)h->d_vtab + h->nfreq_ml, h->d_vline,
+                                  (const float *)L.vnorm, (const float *)L.uproj,
+                                  (const float *)L.dinv};
             e = launch_ml_sweep_f32(sa, bands, threads, h->stream);
         }
         ++h->launches;
@@ -1331,7 +1379,7 @@ int autotune_ml_level(mg3d_handle *h, int k, int nc, int *evaluated) {
     Level &L = h->lev[k];
     MlOpacityArgs oa{L.nvox, nc, h->N, h->prec, h->d_fi, h->theta_ref, h->t_ref,
                      L.n, L.T, L.chi_c, L.saha, L.mchi, L.mS, L.msl, L.mfl, 0,
-                     h->d_exp_tab, h->exp_l1, h->exp_l2};
+                     h->d_exp_tab, h->exp_l1, h->exp_l2, nullptr, nullptr, h->moving ? 1 : 0};
     MG_TRY(launched(h, launch_ml_opacity(oa, h->stream), "multi-level opacity"));
     if (h->params.sc_interp)
         MG_TRY(launched(h, launch_xslopes(h->prec, L.nx, (long)nc * L.nvox, L.mchi, L.mS, L.mdchi,
@@ -1345,8 +1393,8 @@ int autotune_ml_level(mg3d_handle *h, int k, int nc, int *evaluated) {
         for (int bands = 1; bands <= kPortableBands && bands <= L.ny; ++bands) {
             const int rows = (L.ny + bands - 1) / bands;
             if ((long)(bands - 1) * rows >= L.ny) continue;
-            if (ml_sweep_smem_bytes(h->prec, rows, L.nx, rpb, h->params.sc_interp) >
-                kMaxSweepSmem)
+            if (ml_sweep_smem_bytes(h->prec, rows, L.nx, rpb, h->params.sc_interp,
+                                    h->moving ? 1 : 0) > kMaxSweepSmem)
                 continue;
             for (int th : {128, 256, 512}) {
                 if (th > 128 && th / 2 >= rows * L.nx) continue;  // a smaller block covers it
@@ -1410,6 +1458,67 @@ int autotune_ml(mg3d_handle *h, int level, int *evaluated) {
     return MG3D_OK;
 }
 
+// Velocity field of a moving multi-level atmosphere: per frequency the line
+// offset, weight and line index (lines numbered in transition order); the
+// field on every grid (full weighting downward); per grid the projected
+// velocities, 1/d and the inverse profile sums of every line and ray.
+int setup_velocity_ml(mg3d_handle *h, const double *vel_host) {
+    const int nf = h->nfreq_ml;
+    const size_t es = elem_size(h->prec);
+    std::vector<double> xw(2 * (size_t)nf, 0.0);
+    std::vector<int> line(nf, -1);
+    int nlines = 0;
+    for (const TransInfo &t : h->ti) {
+        if (t.kind != 0) continue;
+        for (int f = t.f_begin; f < t.f_end; ++f) {
+            xw[f] = h->fi[f].xy;
+            xw[nf + f] = h->fi[f].w;
+            line[f] = nlines;
+        }
+        ++nlines;
+    }
+    MG_TRY(dev_alloc(&h->d_vtab, 2 * (size_t)nf * es));
+    if (h->prec == MG3D_PREC_F64) {
+        MG_CUDA(cudaMemcpy(h->d_vtab, xw.data(), xw.size() * es, cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> f32(xw.begin(), xw.end());
+        MG_CUDA(cudaMemcpy(h->d_vtab, f32.data(), f32.size() * es, cudaMemcpyHostToDevice));
+    }
+    MG_TRY(dev_alloc((void **)&h->d_vline, (size_t)nf * sizeof(int)));
+    MG_CUDA(cudaMemcpy(h->d_vline, line.data(), (size_t)nf * sizeof(int), cudaMemcpyHostToDevice));
+    for (int k = 1; k <= h->L; ++k) MG_TRY(dalloc(&h->lev[k].vel, 3 * (size_t)h->lev[k].nvox));
+    Level &F = h->lev[h->L];
+    MG_CUDA(cudaMemcpy(F.vel, vel_host, 3 * (size_t)F.nvox * sizeof(double),
+                       cudaMemcpyHostToDevice));
+    for (int k = h->L; k >= 2; --k) {
+        Level &Fk = h->lev[k];
+        MG_TRY(launched(h, launch_restrict(3, Fk.nx, Fk.ny, Fk.nz, Fk.vel, h->lev[k - 1].vel,
+                                           h->stream),
+                        "restrict velocity"));
+    }
+    double *dmu = nullptr;
+    MG_TRY(dalloc(&dmu, 3 * (size_t)kRays));
+    int rc = MG3D_OK;
+    if (cudaMemcpy(dmu, h->mu, 3 * kRays * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = fail(MG3D_E_CUDA, "velocity tables");
+    for (int k = 1; k <= h->L && rc == MG3D_OK; ++k) {
+        Level &L = h->lev[k];
+        rc = dev_alloc(&L.uproj, (size_t)kRays * L.nvox * es);
+        if (rc == MG3D_OK) rc = dev_alloc(&L.dinv, (size_t)L.nvox * es);
+        if (rc == MG3D_OK)
+            rc = dev_alloc(&L.vnorm, (size_t)std::max(1, nlines) * kRays * L.nvox * es);
+        if (rc == MG3D_OK)
+            rc = launched(h, launch_ml_vel_prep(h->prec, L.nvox, h->ntrans, h->d_ti, h->d_fi, dmu,
+                                                L.vel, L.T, h->t_ref, L.uproj, L.dinv, L.vnorm,
+                                                h->stream),
+                          "velocity projection");
+    }
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess && rc == MG3D_OK)
+        rc = fail(MG3D_E_CUDA, "velocity set-up");
+    cudaFree(dmu);
+    return rc;
+}
+
 int create_ml_impl(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
                    const mg3d_quadrature *quad, const mg3d_params *params, mg3d_handle *h) {
     h->kind = 1;
@@ -1417,6 +1526,7 @@ int create_ml_impl(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
     h->L = params->n_grids;
     h->prec = params->fs_prec;
     h->params = *params;
+    h->moving = atm->vel != nullptr;
     h->theta_ref = atom->theta_ref;
     h->t_ref = atom->t_ref;
     build_quadrature(h, quad ? quad->a : 0.0);
@@ -1500,8 +1610,8 @@ int create_ml_impl(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
             for (int b = 1; b <= kPortableBands && b <= L.ny; ++b) {
                 const int rows = (L.ny + b - 1) / b;
                 if ((long)(b - 1) * rows >= L.ny) continue;
-                if (ml_sweep_smem_bytes(h->prec, rows, L.nx, rpb, params->sc_interp) >
-                    kMaxSweepSmem)
+                if (ml_sweep_smem_bytes(h->prec, rows, L.nx, rpb, params->sc_interp,
+                                        atm->vel ? 1 : 0) > kMaxSweepSmem)
                     continue;
                 pick = b;
                 if (2L * (12 / rpb) * nf * b >= 300) break;
@@ -1607,6 +1717,7 @@ int create_ml_impl(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
                                                h->stream),
                             "restrict scattering"));
     }
+    if (h->moving) MG_TRY(setup_velocity_ml(h, atm->vel));
     MG_TRY(dalloc(&h->ml_acc, (size_t)h->ntrans * kAccTerms * F.nvox));
     if (params && params->ml_chunk < 0) return fail(MG3D_E_ARG, "negative ml_chunk");
     h->ml_chunk_req = params ? params->ml_chunk : 0;
@@ -2137,6 +2248,8 @@ int mg3d_create_ml(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
         return fail(MG3D_E_ARG, "interpolation must be 0 or 1");
     if (params->sc_interp < 0 || params->sc_interp > 1)
         return fail(MG3D_E_ARG, "sc_interp must be 0 or 1");
+    if (atm->vel && params->sc_interp)
+        return fail(MG3D_E_ARG, "moving atmospheres take the linear upwind interpolation");
     if (atm->nx < 1 || atm->ny < 1 || atm->nz < 2) return fail(MG3D_E_ARG, "grid too small");
     if (atm->nx >= 65536 || atm->ny >= 65536)
         return fail(MG3D_E_ARG, "nx and ny must be below 65536");
@@ -2178,7 +2291,12 @@ int mg3d_formal_solve_ml(mg3d_handle *h, int level, double *jx_host, double *ux_
     for (int f0 = 0; f0 < h->nfreq_ml; f0 += h->ml_chunk) {
         const int nc = std::min(h->ml_chunk, h->nfreq_ml - f0);
         MG_TRY(ml_chunk_fs(h, level, f0, nc));
-        if (h->scatter) MG_TRY(ml_accumulate(h, level, f0, nc, false));   // background field
+        if (h->scatter) {   // the background field takes the new mean intensity
+            h->force_bg = true;
+            const int rc = ml_accumulate(h, level, f0, nc, false);
+            h->force_bg = false;
+            MG_TRY(rc);
+        }
         MG_CUDA(cudaStreamSynchronize(h->stream));
         // the chunk's per-frequency sums of every ray-group slot, added on the
         // host in slot order
@@ -2234,8 +2352,8 @@ int mg3d_set_ml_shape(mg3d_handle *h, int level, int bands, int rays_per_block, 
         return fail(MG3D_E_ARG, "rays_per_block must divide 12");
     if (threads < 32 || threads > kMaxSweepThreads || threads % 32)
         return fail(MG3D_E_ARG, "threads must be a multiple of 32 up to 512");
-    if (ml_sweep_smem_bytes(h->prec, rows, L.nx, rays_per_block, h->params.sc_interp) >
-        kMaxSweepSmem)
+    if (ml_sweep_smem_bytes(h->prec, rows, L.nx, rays_per_block, h->params.sc_interp,
+                            h->moving ? 1 : 0) > kMaxSweepSmem)
         return fail(MG3D_E_ARG, "multi-level sweep shape exceeds shared memory");
     MG_CUDA(cudaStreamSynchronize(h->stream));
     L.ml_bands = bands;
@@ -2453,7 +2571,7 @@ int mg3d_destroy(mg3d_handle *h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     drop_graphs(h);
     for (int k = 0; k <= MG3D_MAX_GRIDS; ++k) free_level(h->lev[k]);
-    void *ptrs[] = {h->d_ftab, h->d_vtab, h->d_exp_tab, h->pj, h->pu, h->scal,
+    void *ptrs[] = {h->d_ftab, h->d_vtab, h->d_vline, h->d_exp_tab, h->pj, h->pu, h->scal,
                     h->scratch, h->d_fi, h->d_ti, h->ml_jx, h->ml_ux, h->ml_acc,
                     h->ml_jm};
     for (void *p : ptrs)
@@ -2525,6 +2643,7 @@ int mg3d_formal_solve(mg3d_handle *h, int level, double *jeff_host, double *u_ho
 int mg3d_mali_sweep(mg3d_handle *h, int level, int n_sweeps, double *max_rel_change) {
     MG_TRY(check_level(h, level));
     if (n_sweeps < 0) return fail(MG3D_E_ARG, "negative sweep count");
+    h->top = level;
     double C = 0.0;
     long long bad = 0;
     for (int i = 0; i < n_sweeps; ++i) {
@@ -2558,6 +2677,7 @@ int mg3d_mali_solve(mg3d_handle *h, double tol, int max_sweeps, mg3d_stats *stat
     if (!(tol > 0.0) || max_sweeps < 1) return fail(MG3D_E_ARG, "bad tol or max_sweeps");
     auto t0 = std::chrono::steady_clock::now();
     begin_stats(h);
+    h->top = h->L;
     MG_TRY(zero_radiation(h, h->L));
     double C = 1.0;
     int it = 0;
@@ -2603,11 +2723,13 @@ int mg3d_fmg_solve(mg3d_handle *h, double tol, int max_cycles, mg3d_stats *stats
     if (h->L < 2) return fail(MG3D_E_STATE, "FMG needs n_grids >= 2");
     auto t0 = std::chrono::steady_clock::now();
     begin_stats(h);
+    h->top = 1;  // each stage solves on its own grid
     MG_TRY(zero_radiation(h, 1));
     for (int i = 0; i < h->params.nu_fmg; ++i) MG_TRY(sweep(h, 1));
     for (int k = 2; k <= h->L; ++k) {
         Level &Fk = h->lev[k];
         Level &Ck = h->lev[k - 1];
+        h->top = k;
         MG_TRY(launched(h, launch_prolong(h->params.interpolation, h->N, Ck.nx, Ck.ny, Ck.nz,
                                           Fk.tz, Fk.zf, Ck.n, Fk.n, h->stream),
                         "prolong full approximation"));

@@ -187,6 +187,15 @@ struct MlSweepArgs {
     T *jm;                        // mean intensity sum_r w_r I per slot, or null
     const T *dchi, *dS;           // [nfreq][nvox] x-slopes of chi and S (herm only)
     int herm;                     // 1: monotone cubic Hermite upwind interpolation
+    // moving atmospheres (moving = 1): chi, S, sl, fl hold the parts the
+    // opacity kernel writes in moving mode; per global frequency f0 + f the
+    // line offset, quadrature weight and line index (-1: continuum); per
+    // line, ray and node the inverse profile sum [nlines][kRays][nvox]; per
+    // ray and node the projected velocity [kRays][nvox]; per node 1/d [nvox]
+    int moving, f0;
+    const T *vx, *vwq;
+    const int *vline;
+    const T *vnorm, *uproj, *dinv;
 };
 
 // Opacity of the chunk of frequencies f0 .. f0+nfreq-1, written at the
@@ -203,6 +212,11 @@ struct MlOpacityArgs {
     double exp_l1, exp_l2;
     const double *sigma_c;         // background scattering [nvox], or null
     const void *jbg;               // background field [n_freq][nvox] (FS precision)
+    int moving;                    // 1: write the ray-independent parts instead (a
+                                   // moving atmosphere): chi <- the transition's opacity
+                                   // at unit profile, S <- its emissivity at unit profile
+                                   // (continua: their own), sl <- background opacity,
+                                   // fl <- background emissivity
 };
 
 // Radiative sums per transition and node, [n_trans][3][nvox] in FP64:
@@ -226,6 +240,8 @@ struct MlAccumArgs {
     double exp_l1, exp_l2;
     const void *jm;                // mean intensity per slot [nslots][nfreq][nvox], or null
     void *jbg;                     // background field [n_freq][nvox] written from jm
+    int moving;                    // 1: line sums already carry their per-ray profile
+                                   // weights (sum 1 over a line), so they add as they are
 };
 
 struct MlRateArgs {
@@ -240,7 +256,14 @@ struct MlRateArgs {
     unsigned long long *scal;
 };
 
-size_t ml_sweep_smem_bytes(int prec, int rows, int nx, int rpb, int herm = 0);
+size_t ml_sweep_smem_bytes(int prec, int rows, int nx, int rpb, int herm = 0,
+                           int moving = 0);
+// Moving multi-level atmospheres: uproj [kRays][nvox], dinv [nvox] and vnorm
+// [nlines][kRays][nvox] of a level (see MlSweepArgs).
+cudaError_t launch_ml_vel_prep(int prec, long nvox, int ntrans, const TransInfo *ti,
+                               const FreqInfo *fi, const double *mu, const double *vel,
+                               const double *T, double t_ref, void *uproj, void *dinv,
+                               void *vnorm, cudaStream_t st);
 cudaError_t launch_ml_opacity(const MlOpacityArgs &a, cudaStream_t st);
 cudaError_t launch_ml_bottom(int prec, long nplane, int nfreq, const FreqInfo *fi,
                              double theta_ref, const double *T, void *ib, cudaStream_t st);

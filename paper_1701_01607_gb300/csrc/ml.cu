@@ -30,6 +30,7 @@
 // is solved by Gaussian elimination with partial pivoting.
 #include <cooperative_groups.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "mg3d.h"
@@ -59,6 +60,14 @@ __device__ __forceinline__ double opac_exp(double x, const ExpNegTable &et) {
     return exp_neg(x, et);
 }
 __device__ __forceinline__ float opac_exp(float x, const ExpNegTable &) { return expf(-x); }
+
+// Line profile exp(-dd2) di / sqrt(pi) in the formal-solution precision.
+__device__ __forceinline__ double ml_doppler(double dd2, double di, const ExpNegTable &et) {
+    return exp_neg(dd2, et) * di * 0.56418958354775628;
+}
+__device__ __forceinline__ float ml_doppler(float dd2, float di, const ExpNegTable &) {
+    return __expf(-dd2) * di * 0.564189584f;
+}
 
 // One thread per node walks the chunk's frequencies, so per-node quantities
 // (temperature, Doppler width, background) and per-transition ones
@@ -113,6 +122,26 @@ __global__ void ml_opacity_kernel(const MlOpacityArgs a) {
                 rho_b = -1.0;
             }
             const long i = (long)fl * nvox + v;
+            if (a.moving) {
+                // ray-independent parts; a line's profile is applied per ray
+                // in the sweep (continua do not shift)
+                T ca = chi_t, ea = eta_t;
+                if (q.kind == 0) {
+                    ca = (T)q.kappa * (T)(q.gr * nl - nu);
+                    ea = (T)(q.kappa * q.rho * q.rho * q.rho) * (T)nu;
+                }
+                T cb = (T)cc, eb = (T)cc * B;
+                if (a.sigma_c) {
+                    const T sg = (T)a.sigma_c[v];
+                    cb += sg;
+                    eb += sg * ((const T *)a.jbg)[(long)(a.f0 + fl) * nvox + v];
+                }
+                ((T *)a.chi)[i] = ca;
+                ((T *)a.S)[i] = ea;
+                ((T *)a.sl)[i] = cb;
+                ((T *)a.fl)[i] = eb;
+                continue;
+            }
             T chi, src;
             if (a.sigma_c) {
                 // background coherent scattering with the previous mean intensity
@@ -155,8 +184,17 @@ __global__ void ml_bottom_kernel(long nplane, int nfreq, const FreqInfo *__restr
 // rows ya-1 .. ya+2 of the intensity and slope planes and of chi, S; each
 // finished plane gets its x-slopes after a block barrier; chi and S take
 // theirs from dchi, dS.
-template <typename T, bool HERM>
+//
+// MODE kSweepMoving (a velocity field): along ray r a line's profile at a node
+// is phi((x - u_r) / d) / (d sqrt(pi)), so chi, S and the transition shares
+// are formed per node, ray and frequency from the ray-independent parts the
+// opacity kernel wrote, and kept in opacity and source planes next to the
+// intensity planes, from which the next step interpolates the upwind values;
+// the angle sums carry the ray's normalised profile weight inside the ray
+// sum.
+template <typename T, int MODE>
 __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, int slot) {
+    constexpr bool HERM = MODE == kSweepHermite, VEL = MODE == kSweepMoving;
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     // slot = (hemisphere, ray group); hemisphere 0: rays 0-11 (up), 1: 12-23
@@ -193,7 +231,11 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
         int r[4];
     };
     T *dbuf = buf + 2 * bufstride;  // slope planes (HERM)
-    RowRef *rowref = reinterpret_cast<RowRef *>(buf + (HERM ? 4 : 2) * bufstride);
+    // VEL: opacity planes at buf + 2 bufstride, source planes at buf + 4 bufstride,
+    // the same offsets from the intensity planes in every block of the cluster
+    const long coff = 2 * bufstride, soff = 4 * bufstride;
+    RowRef *rowref =
+        reinterpret_cast<RowRef *>(buf + (HERM ? 4 : (VEL ? 6 : 2)) * bufstride);
     RowRef4 *rowref4 = reinterpret_cast<RowRef4 *>(rowref);
     __shared__ double exp_tab[kExpTab];
     if (sizeof(T) == 8) {
@@ -211,11 +253,54 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
     __shared__ int g_ix[12];
     const T *__restrict__ dchif = HERM ? a.dchi + (long)f * nvox : nullptr;
     const T *__restrict__ dSf = HERM ? a.dS + (long)f * nvox : nullptr;
+    // VEL: this frequency's line (or -1), offset and weight
+    const int vl = VEL ? a.vline[a.f0 + f] : -1;
+    const T vxf = VEL ? a.vx[a.f0 + f] : T(0), vwf = VEL ? a.vwq[a.f0 + f] : T(0);
+    // chi, S, sl, fl and the profile weight of node v for ray r0 + j
+    auto moving_terms = [&](long v, int j, T &chi, T &S, T &sl, T &fl, T &wr) {
+        const T A = chif[v], E = Sf[v], cb = slf[v], eb = flf[v];
+        T prof = T(1);
+        wr = T(1);
+        if (vl >= 0) {
+            const long rv = (long)(r0 + j) * nvox + v;
+            const T di = a.dinv[v];
+            const T dd = (vxf - a.uproj[rv]) * di;
+            prof = ml_doppler(dd * dd, di, et);
+            wr = vwf * prof * a.vnorm[(long)vl * kRays * nvox + rv];
+        }
+        const T ct = A * prof, et_ = E * prof;
+        chi = ct + cb;
+        const T inv = T(1) / chi;
+        S = (et_ + eb) * inv;
+        sl = et_ * inv;
+        fl = ct * inv;
+    };
 
     for (int t = 0; t < nz; ++t) {
         const int k = up ? t : nz - 1 - t;
         T *cur = buf + (t & 1) * bufstride;
-        if (t == 0) {
+        if (t == 0 && VEL) {
+            for (int q = threadIdx.x; q < band; q += blockDim.x) {
+                const int yl = q / nx, x = q - yl * nx;
+                const int y = y0 + yl;
+                const T Ib = up ? a.ib[(long)f * nplane + (long)y * nx + x] : T(0);
+                const long v = (long)k * nplane + (long)y * nx + x;
+                T jacc = 0, uacc = 0;
+                for (int j = 0; j < rpb; ++j) {
+                    T chi, S, sl, fl, wr;
+                    moving_terms(v, j, chi, S, sl, fl, wr);
+                    const long i = j * raystride + (long)yl * nx + x;
+                    cur[i] = Ib;
+                    cur[coff + i] = chi;
+                    cur[soff + i] = S;
+                    jacc += wr * Ib;
+                    uacc += wr;
+                }
+                jxo[v] = wray * jacc;
+                uxo[v] = wray * uacc;
+                if (jmo) jmo[v] = T(rpb) * wray * Ib;
+            }
+        } else if (t == 0) {
             for (int q = threadIdx.x; q < band; q += blockDim.x) {
                 const int yl = q / nx, x = q - yl * nx;
                 const int y = y0 + yl;
@@ -291,6 +376,40 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
                 // sl and fl are the node's: sum I and w0 over the rays and
                 // form Jx = sum I - sl sum w0, Ux = rays - fl sum w0 once
                 T sum_i = 0, sum_w0 = 0;
+                if constexpr (VEL) {
+                    T jacc = 0, uacc = 0;
+                    for (int j = 0; j < rpb; ++j) {
+                        const T w00 = g_w[j][0], w10 = g_w[j][1], w01 = g_w[j][2],
+                                w11 = g_w[j][3];
+                        int xa = x + g_ix[j];
+                        if (xa >= nx) xa -= nx;
+                        const int xb = (xa + 1 == nx) ? 0 : xa + 1;
+                        const RowRef r = rowref[j * rows + yl];
+                        const T *Pa = r.pa, *Pb = r.pb;
+                        auto bil = [&](long o) {
+                            return w00 * Pa[o + xa] + w10 * Pa[o + xb] + w01 * Pb[o + xa] +
+                                   w11 * Pb[o + xb];
+                        };
+                        const T I_up = bil(0), chi_up = bil(coff), S_up = bil(soff);
+                        T chi, S, sl_r, fl_r, wr;
+                        moving_terms(v, j, chi, S, sl_r, fl_r, wr);
+                        const T x_tau = (chi_up + chi) * g_hs[j];
+                        T ex, w0, wup, u;
+                        ScWeights<T>::eval(x_tau, rcp(x_tau), et, ex, w0, wup, u);
+                        const T I = I_up * ex + wup * S_up + w0 * S;
+                        const long i = j * raystride + (long)yl * nx + x;
+                        cur[i] = I;
+                        cur[coff + i] = chi;
+                        cur[soff + i] = S;
+                        sum_i += I;
+                        jacc += wr * (I - w0 * sl_r);
+                        uacc += wr * (T(1) - w0 * fl_r);
+                    }
+                    jxo[v] = wray * jacc;
+                    uxo[v] = wray * uacc;
+                    if (jmo) jmo[v] = wray * sum_i;
+                    continue;
+                }
                 if constexpr (HERM) {
                     for (int j = 0; j < rpb; ++j) {
                         int xa = x + g_ix[j];
@@ -367,9 +486,9 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
     }
 }
 
-template <typename T, int MAXT, bool HERM>
+template <typename T, int MAXT, int MODE>
 __global__ void __launch_bounds__(MAXT) ml_sweep_kernel(const MlSweepArgs<T> a) {
-    ml_sweep_body<T, HERM>(a, blockIdx.y, blockIdx.z);
+    ml_sweep_body<T, MODE>(a, blockIdx.y, blockIdx.z);
 }
 
 // Batched: item y = (problem, ray-group slot as ray, frequency as group).
@@ -378,11 +497,13 @@ __global__ void __launch_bounds__(MAXT) ml_sweep_batch_kernel(
     const MlSweepArgs<T> *__restrict__ args, const BatchItem *__restrict__ items) {
     const BatchItem it = items[blockIdx.y];
     const MlSweepArgs<T> a = args[it.member];
-    ml_sweep_body<T, false>(a, it.group, it.ray);
+    ml_sweep_body<T, kSweepLinear>(a, it.group, it.ray);
 }
 
-size_t ml_sweep_smem_bytes(int prec, int rows, int nx, int rpb, int herm) {
+size_t ml_sweep_smem_bytes(int prec, int rows, int nx, int rpb, int herm, int moving) {
     const size_t elem = prec == MG3D_PREC_F64 ? sizeof(double) : sizeof(float);
+    // moving: intensity, opacity and source planes and the 24-byte table
+    if (moving) return 6ull * rpb * rows * nx * elem + 24ull * rpb * rows;
     // intensity planes (and their slope planes), then the per-(ray, row)
     // upwind row table: two pointers and two offsets (24 bytes), or eight
     // pointers and four offsets (80 bytes); the planes end on an 8-byte
@@ -391,14 +512,17 @@ size_t ml_sweep_smem_bytes(int prec, int rows, int nx, int rpb, int herm) {
     return 2ull * rpb * rows * nx * elem + 24ull * rpb * rows;
 }
 
-template <typename T, int MAXT, bool HERM>
+template <typename T, int MAXT, int MODE>
 static cudaError_t launch_ml_sweep_t(const MlSweepArgs<T> &a, int bands, int threads,
                                      cudaStream_t st) {
     const size_t smem = ml_sweep_smem_bytes(sizeof(T) == 8 ? MG3D_PREC_F64 : MG3D_PREC_F32,
-                                            a.rows, a.nx, a.rpb, HERM ? 1 : 0);
-    if (HERM && (!a.dchi || !a.dS)) return cudaErrorInvalidValue;
+                                            a.rows, a.nx, a.rpb, MODE == kSweepHermite ? 1 : 0,
+                                            MODE == kSweepMoving ? 1 : 0);
+    if (MODE == kSweepHermite && (!a.dchi || !a.dS)) return cudaErrorInvalidValue;
+    if (MODE == kSweepMoving && (!a.vx || !a.vwq || !a.vline || !a.vnorm || !a.uproj || !a.dinv))
+        return cudaErrorInvalidValue;
     // one fixed limit for every launch, so graph replays never meet a lower one
-    cudaError_t e = cudaFuncSetAttribute(ml_sweep_kernel<T, MAXT, HERM>,
+    cudaError_t e = cudaFuncSetAttribute(ml_sweep_kernel<T, MAXT, MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kMaxSweepSmem);
     if (e != cudaSuccess) return e;
@@ -414,7 +538,7 @@ static cudaError_t launch_ml_sweep_t(const MlSweepArgs<T> &a, int bands, int thr
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = bands > 1 ? 1 : 0;  // one band: a plain launch
-    return cudaLaunchKernelEx(&cfg, ml_sweep_kernel<T, MAXT, HERM>, a);
+    return cudaLaunchKernelEx(&cfg, ml_sweep_kernel<T, MAXT, MODE>, a);
 }
 
 template <typename T, int MAXT>
@@ -460,11 +584,68 @@ cudaError_t launch_ml_sweep_batch(int prec, const void *args, const BatchItem *i
 template <typename T>
 static cudaError_t launch_ml_sweep_any(const MlSweepArgs<T> &a, int bands, int threads,
                                        cudaStream_t st) {
+    if (a.herm && a.moving) return cudaErrorInvalidValue;
     if (a.herm)
-        return threads <= 256 ? launch_ml_sweep_t<T, 256, true>(a, bands, threads, st)
-                              : launch_ml_sweep_t<T, 512, true>(a, bands, threads, st);
-    return threads <= 256 ? launch_ml_sweep_t<T, 256, false>(a, bands, threads, st)
-                          : launch_ml_sweep_t<T, 512, false>(a, bands, threads, st);
+        return threads <= 256 ? launch_ml_sweep_t<T, 256, kSweepHermite>(a, bands, threads, st)
+                              : launch_ml_sweep_t<T, 512, kSweepHermite>(a, bands, threads, st);
+    if (a.moving)
+        return threads <= 256 ? launch_ml_sweep_t<T, 256, kSweepMoving>(a, bands, threads, st)
+                              : launch_ml_sweep_t<T, 512, kSweepMoving>(a, bands, threads, st);
+    return threads <= 256 ? launch_ml_sweep_t<T, 256, kSweepLinear>(a, bands, threads, st)
+                          : launch_ml_sweep_t<T, 512, kSweepLinear>(a, bands, threads, st);
+}
+
+// Moving atmospheres: per ray and node the projected velocity u = mu_r . v,
+// per node 1/d = sqrt(t_ref/T), and per line, ray and node the inverse of
+// sum_f w_f phi((x_f - u)/d)/(d sqrt(pi)) over the line's frequencies (lines
+// numbered in transition order).
+template <typename T>
+__global__ void ml_vel_prep_kernel(long nvox, int ntrans, const TransInfo *__restrict__ ti,
+                                   const FreqInfo *__restrict__ fi, const double *__restrict__ mu,
+                                   const double *__restrict__ vel, const double *__restrict__ Tg,
+                                   double t_ref, T *__restrict__ uproj, T *__restrict__ dinv,
+                                   T *__restrict__ vnorm) {
+    const long total = (long)kRays * nvox;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total;
+         i += (long)gridDim.x * blockDim.x) {
+        const int r = (int)(i / nvox);
+        const long v = i - (long)r * nvox;
+        const double u = mu[3 * r] * vel[v] + mu[3 * r + 1] * vel[nvox + v] +
+                         mu[3 * r + 2] * vel[2 * nvox + v];
+        const double di = sqrt(t_ref / Tg[v]);
+        uproj[i] = (T)u;
+        if (r == 0) dinv[v] = (T)di;
+        int l = 0;
+        for (int t = 0; t < ntrans; ++t) {
+            const TransInfo tr = ti[t];
+            if (tr.kind != 0) continue;
+            double sum = 0.0;
+            for (int f = tr.f_begin; f < tr.f_end; ++f) {
+                const double dd = (fi[f].xy - u) * di;
+                sum += fi[f].w * exp(-dd * dd) * di * 0.56418958354775628;
+            }
+            vnorm[((long)l * kRays + r) * nvox + v] = (T)(1.0 / sum);
+            ++l;
+        }
+    }
+}
+
+cudaError_t launch_ml_vel_prep(int prec, long nvox, int ntrans, const TransInfo *ti,
+                               const FreqInfo *fi, const double *mu, const double *vel,
+                               const double *T, double t_ref, void *uproj, void *dinv,
+                               void *vnorm, cudaStream_t st) {
+    const long total = (long)kRays * nvox;
+    const int th = 256;
+    const long b = std::min<long>((total + th - 1) / th, 152L * 32);
+    if (prec == MG3D_PREC_F64)
+        ml_vel_prep_kernel<double><<<(int)b, th, 0, st>>>(nvox, ntrans, ti, fi, mu, vel, T, t_ref,
+                                                          (double *)uproj, (double *)dinv,
+                                                          (double *)vnorm);
+    else
+        ml_vel_prep_kernel<float><<<(int)b, th, 0, st>>>(nvox, ntrans, ti, fi, mu, vel, T, t_ref,
+                                                         (float *)uproj, (float *)dinv,
+                                                         (float *)vnorm);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_ml_sweep_f64(const MlSweepArgs<double> &a, int bands, int threads,
@@ -518,6 +699,15 @@ __global__ void ml_accum_kernel(const MlAccumArgs a) {
             if (tr.kind == 0) {
                 const double inv_d = sqrt(a.t_ref / Tg);
                 for (int f = fb; f < fe; ++f) {
+                    if (a.moving && !a.zero_radiation) {
+                        // the per-ray profile weights are inside J and U already
+                        double J, U;
+                        sums(f, v, J, U);
+                        s0 += f == tr.f_begin ? 1.0 : 0.0;
+                        s1 += J;
+                        s2 += U;
+                        continue;
+                    }
                     const FreqInfo q = a.fi[f];
                     const double xd = q.xy * inv_d;
                     // profile in the formal-solution precision, sums in FP64

@@ -82,7 +82,8 @@ class mg3d_ml_atom(ctypes.Structure):
 class mg3d_ml_atmosphere(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("z", _D), ("T", _D),
-                ("n_tot", _D), ("chi_c", _D), ("c", _D), ("saha", _D), ("sigma_c", _D)]
+                ("n_tot", _D), ("chi_c", _D), ("c", _D), ("saha", _D), ("sigma_c", _D),
+                ("vel", _D)]
 
 
 class mg3d_stats(ctypes.Structure):
@@ -251,10 +252,12 @@ def mg3d_create_ml(atm, atom, quad_a: float = 0.0, n_grids: int = 1, nu_fmg: int
         return _dptr(keep[name])
 
     sigma = getattr(atm, "sigma_c", None)
+    vel = getattr(atm, "vel", None)
     a = mg3d_ml_atmosphere(atm.nx, atm.ny, atm.nz, atm.dx, atm.dy, arr("z", atm.z),
                            arr("T", atm.T), arr("n", atm.n_tot), arr("cc", atm.chi_c),
                            arr("c", atm.c), arr("s", atm.saha),
-                           arr("sg", sigma) if sigma is not None else None)
+                           arr("sg", sigma) if sigma is not None else None,
+                           arr("v", vel) if vel is not None else None)
     lines = (mg3d_line * max(1, len(atom.lines)))(
         *[mg3d_line(l.lower, l.upper, l.rho, l.a_ul, l.kappa, l.n_freq, l.x_max)
           for l in atom.lines])
