@@ -630,6 +630,41 @@ def run_velocity(args):
             finally:
                 m.mg3d_destroy(h)
         out["moving" if vel else "static"] = row
+    # the 6-level atom: sweep cost on the 64x64x129 chromosphere (120
+    # frequencies), convergence on a 32x32x65 one with the ground-level
+    # collisions weakened 1e3 times (resonance lines scattering)
+    ml_atom = synth.hydrogen_like_atom(line_freq=20, cont_freq=4, seed=2)
+    ml = {}
+    for vel in (0.0, 1.0):
+        key = "moving" if vel else "static"
+        atm = synth.chromosphere(64, 64, 129, ml_atom, seed=2, velocity=vel)
+        for prec, pname in ((m.MG3D_PREC_F32, "f32"), (m.MG3D_PREC_F64, "f64")):
+            h = m.mg3d_create_ml(atm, ml_atom, n_grids=1, fs_prec=prec)
+            try:
+                m.mg3d_autotune(h)
+                m.mg3d_set_timing(h, True)
+                m.mg3d_reset_counters(h)
+                for _ in range(3):
+                    m.mg3d_formal_solve_ml(h, 1)
+                c = m.mg3d_get_counters(h)
+                ml[f"{key}_sweep_{pname}"] = {
+                    "ms": round(c["fs_kernel_ms"] / c["fs_timed_launches"], 3),
+                    "gunits_s": round(c["fs_units"] / (c["fs_kernel_ms"] * 1e-3) / 1e9, 2),
+                    "shape": list(m.mg3d_get_ml_shape(h, 1))}
+            finally:
+                m.mg3d_destroy(h)
+        atm = synth.chromosphere(32, 32, 65, ml_atom, seed=2, ground_collisions=1e-3,
+                                 velocity=vel)
+        mp = dict(fs_prec=m.MG3D_PREC_F64, nu_fmg=16, nu0=20, nu1=4, nu2=8, nu3=32)
+        ref = m.mg3d_create_ml(atm, ml_atom, n_grids=3, **mp)
+        m.mg3d_fas_solve(ref, 1e-9, 400, n_grids=3)
+        n_ref = m.mg3d_get_populations(ref, 3)
+        m.mg3d_destroy(ref)
+        ml[f"{key}_fas"] = _to_target(m, lambda: m.mg3d_create_ml(atm, ml_atom, n_grids=3, **mp),
+                                      3, n_ref, lambda h, it: m.mg3d_fas_vcycle(h, it == 0), 60)
+        ml[f"{key}_mali"] = _to_target(m, lambda: m.mg3d_create_ml(atm, ml_atom, n_grids=1, **mp),
+                                       1, n_ref, lambda h, it: m.mg3d_mali_sweep(h, 1, 1), 2000)
+    out["six_level"] = ml
     return out
 
 
