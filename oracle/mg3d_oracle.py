@@ -233,6 +233,73 @@ class TwoLevelProblem:
         self.fs_count = {k: 0 for k in self.levels}
         self.sweep_count = {k: 0 for k in self.levels}
         self.negatives = 0
+        # partial redistribution: the lagged mean intensity per frequency and
+        # grid, and the discrete redistribution matrix
+        self.gamma = float(getattr(atom, "gamma_prd", 0.0))
+        self.prd = self.gamma > 0.0
+        if self.prd and fine.vel is not None:
+            raise ValueError("partial redistribution takes a static atmosphere")
+        nf = len(self.x)
+        self.jnu = {k: np.zeros((nf, lev.nx * lev.ny * lev.nz)) for k, lev in self.levels.items()}
+        self.wq = self.wphi / self.phi
+        self.R = prd_matrix(self.x, self.wq, self.phi) if self.prd else None
+        self.top = n_grids
+        self._force_bg = False
+
+    # ---- the lagged radiation field (partial redistribution) ----
+    def updates_background(self, k: int) -> bool:
+        """Whether a formal solution on grid k replaces the grid's lagged
+        field by its own mean intensity: on the grid being solved always; on
+        a coarser grid only in the Lambda-iteration that starts it (see the
+        multi-level class)."""
+        return self.prd and (k == self.top or self._force_bg)
+
+    def lambda_iteration(self, k: int, n):
+        self._force_bg = True
+        try:
+            self.formal_solution(k, n)
+        finally:
+            self._force_bg = False
+
+    def prd_profile_ratio(self, k: int):
+        """rho_f = psi_f/phi_f at every node from the lagged field J_f:
+        rho = 1 + gamma f_rad (sum_f' w_f' R(f', f) J_f' / (phi_f Jbar) - 1),
+        with Jbar = sum w phi J and f_rad = B_lu Jbar/(B_lu Jbar + C_lu), the
+        radiative share of the upward transitions (equal at statistical
+        equilibrium to n_l B_lu Jbar/(n_u P_u)); rho = 1 where Jbar = 0."""
+        lev = self.levels[k]
+        J = self.jnu[k]
+        Jbar = self.wphi @ J
+        g, A = self.atom.g_ratio, self.atom.a_ul
+        c_lu = lev.c_ul.reshape(-1) * g * np.exp(-self.atom.theta / lev.T.reshape(-1))
+        frad = g * A * Jbar / (g * A * Jbar + c_lu)
+        Af = (self.R * self.wq[:, None]).T @ J                   # [nf, nvox]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            ratio = np.where(Jbar > 0, Af / (self.phi[:, None] * Jbar[None, :]), 1.0)
+        return 1.0 + self.gamma * frad[None, :] * (ratio - 1.0)
+
+    def formal_solution_prd(self, k: int, n):
+        """Formal solution with partial redistribution: S_f = rho_f S with S
+        the CRD source function of the populations and rho_f from the lagged
+        field; the MALI sums Jeff = sum w phi (I - w0 rho S) and
+        U = sum w phi (1 - w0 rho) treat S as new and rho as fixed."""
+        lev = self.levels[k]
+        chi, S = self.opacity_source(lev, n)
+        rho = self.prd_profile_ratio(k)
+        Sf = rho * S[None, :]
+        nf = len(self.phi)
+        shp = (nf,) + lev.shape
+        Ib = self.planck(lev.T[0]).reshape(1, lev.ny, lev.nx)
+        Jx, Ux, Jm = formal_solution_nu_raw(lev.z, lev.dx, lev.dy, self.mu, self.wray,
+                                            chi.reshape(shp), Sf.reshape(shp), Sf.reshape(shp),
+                                            rho.reshape(shp), Ib, 0.0, want_j=True,
+                                            interp=self.sc_interp)
+        Jx, Ux, Jm = (a.reshape(nf, -1) for a in (Jx, Ux, Jm))
+        if self.updates_background(k):
+            self.jnu[k] = Jm
+        self.fs_count[k] += 1
+        return ((self.wphi @ Jm).reshape(lev.shape), (self.wphi @ Jx).reshape(lev.shape),
+                (self.wphi @ Ux).reshape(lev.shape))
 
     # ---- opacity and source function (Eq. 1, CRD two-level atom) ----
     def planck(self, T):
@@ -259,6 +326,8 @@ class TwoLevelProblem:
         lev = self.levels[k]
         if lev.vel is not None:
             return self.formal_solution_moving(k, n)
+        if self.prd:
+            return self.formal_solution_prd(k, n)
         nvox = lev.nx * lev.ny * lev.nz
         nf = len(self.phi)
         chi, S = self.opacity_source(lev, n)
@@ -380,10 +449,14 @@ class TwoLevelProblem:
         return self.apply(self.rate_matrix(k, Jeff, U), n)
 
     def zero_radiation(self, k: int):
-        """Populations from statistical equilibrium with J = 0 (Sec. 4.11)."""
+        """Populations from statistical equilibrium with J = 0 (Sec. 4.11);
+        with partial redistribution the lagged field starts at zero, so the
+        first formal solution sees rho = 1 (CRD)."""
         lev = self.levels[k]
         zeros = np.zeros(lev.shape)
         ones = np.ones(lev.shape)
+        if self.prd:
+            self.jnu[k] = np.zeros_like(self.jnu[k])
         return self.solve(self.rate_matrix(k, zeros, ones), self.default_rhs(k))
 
     def mali_sweep(self, k: int, n, f=None):
@@ -442,10 +515,20 @@ class TwoLevelProblem:
             n[k], _ = self.mali_sweep(k, n[k], f[k])
 
     def coarse_entry(self, k: int, n_coarse):
-        """Hook: a V-cycle enters grid k-1 from k (no state to move here)."""
+        """A V-cycle enters grid k-1 from k: with partial redistribution the
+        lagged field of k, full-weighted, then one Lambda-iteration; the
+        field stays fixed on grid k-1 until the cycle leaves it."""
+        if self.prd:
+            jf = self.jnu[k].reshape((-1,) + self.levels[k].shape)
+            self.jnu[k - 1] = restrict_fw(jf).reshape(jf.shape[0], -1)
+            self.lambda_iteration(k - 1, n_coarse)
 
     def fmg_prolong(self, k: int):
-        """Hook: FMG moves the full approximation from grid k-1 to k."""
+        """FMG moves the full approximation from grid k-1 to k, and the
+        lagged field of partial redistribution with it."""
+        if self.prd:
+            jc = self.jnu[k - 1].reshape((-1,) + self.levels[k - 1].shape)
+            self.jnu[k] = self.prolong(k, jc).reshape(jc.shape[0], -1)
 
     def fas_cycle(self, n_fine, first: bool, params):
         L = self.n_grids
@@ -673,6 +756,24 @@ def prolong_hermite(ac, z_fine):
                              np.arange(nx) / 2.0)
     a = _hermite_refine_axis(a, -2, True, np.arange(nyc, dtype=float), np.arange(ny) / 2.0)
     return _hermite_refine_axis(a, -3, False, zf[::2], zf)
+
+
+def prd_matrix(x, wq, phi, iters: int = 200):
+    """Discrete angle-averaged redistribution matrix R[f', f] on the frequency
+    grid: Hummer's R_I-A(x', x) = erfc(max(|x|, |x'|))/2 (pure Doppler
+    redistribution; R_II-A for zero damping), whose marginals are the
+    Doppler profile, scaled symmetrically, R = diag(c) R0 diag(c), so that the
+    discrete marginals sum_f' wq_f' R[f', f] equal phi_f exactly (fixed-point
+    iteration c <- sqrt(c phi / (R0^T (wq c)))).  Then a frequency-flat J
+    gives rho = 1 and the emission profile keeps sum w phi rho = 1."""
+    from scipy.special import erfc
+    x = np.asarray(x, dtype=np.float64)
+    ax = np.abs(x)
+    R0 = 0.5 * erfc(np.maximum(ax[:, None], ax[None, :]))
+    c = np.ones(len(x))
+    for _ in range(iters):
+        c = np.sqrt(c * phi / (R0.T @ (wq * c)))
+    return c[:, None] * R0 * c[None, :]
 
 
 def coarsen_level(lev: Level) -> Level:

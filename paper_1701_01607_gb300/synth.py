@@ -58,6 +58,7 @@ class TwoLevelAtom:
     kappa: float = 1.0
     n_freq: int = 9
     x_max: float = 3.0
+    gamma_prd: float = 0.0        # coherence fraction of partial redistribution (0: CRD)
 
 
 @dataclasses.dataclass
