@@ -87,6 +87,21 @@ typedef struct {
     double kappa;    /* line opacity constant */
     int n_freq;      /* frequency points across the line, >= 1 */
     double x_max;    /* half width of the grid in Doppler widths */
+    double gamma_prd; /* coherence fraction of partial redistribution in [0, 1];
+                         0: complete redistribution (the paper's runs).  Reading
+                         of the next step the paper names: angle-averaged Doppler
+                         redistribution R(x', x) = erfc(max(|x|, |x'|))/2 on the
+                         grid (scaled symmetrically so that both marginals are
+                         the profile), mixed with CRD by gamma; the line source
+                         function of frequency f is rho_f S with
+                         rho_f = 1 + gamma f_rad (sum_f' w_f' R(f', f) J_f' /
+                         (phi_f Jbar) - 1), f_rad = B_lu Jbar/(B_lu Jbar + C_lu),
+                         from the mean intensity of the previous formal solution on
+                         the grid (lagged like a background field: restricted and
+                         Lambda-iterated once on a coarse-grid entry, then fixed on
+                         that grid; prolonged in FMG); MALI preconditions with
+                         U = sum w phi (1 - w0 rho).  Static atmospheres, linear
+                         upwind interpolation, no batches. */
 } mg3d_atom;
 
 /* Angle quadrature: the 24-direction A4 set of Carlson (Sec. 3): per octant

@@ -266,6 +266,73 @@ __device__ __forceinline__ void moving_step(
     }
 }
 
+// One sweep step of a band with partial redistribution (two-level atom):
+// the opacity is the static chi0 phi_f, so mirror frequencies share their
+// step weights, but the source function rho_f S depends on the frequency.
+// Its upwind value is interpolated per frequency from global memory; U takes
+// w phi (1 - w0 rho_f); every new intensity is added, with the ray weight,
+// into the new mean intensity of its frequency (atomically: the rays of a
+// node run in different clusters).
+template <typename T>
+__device__ __forceinline__ void prd_step(
+    const SweepArgs<T> &a, int rank, unsigned long long rmagic, cg::cluster_group &cluster,
+    const T *prev, T *cur, T *__restrict__ pj, T *__restrict__ pu, int k, int kp,
+    const StepGeom &o, T half_s, int f0, int nf, const T *phi, const T *inv_phi, const T *wphi,
+    const ExpNegTable &et) {
+    const int nx = a.nx, ny = a.ny, rows = a.rows;
+    const int y0 = rank * rows;
+    const int myrows = max(0, min(rows, ny - y0));
+    const int band = myrows * nx;
+    const long nplane = (long)nx * ny;
+    const long nvox = nplane * a.nz;
+    const T tx = (T)o.tx, ty = (T)o.ty;
+    const T w00 = (T(1) - tx) * (T(1) - ty), w10 = tx * (T(1) - ty);
+    const T w01 = (T(1) - tx) * ty, w11 = tx * ty;
+    const long pp = (long)kp * nplane;
+    const T wr = T(1.0 / kRays);
+    for (int q = threadIdx.x; q < band; q += blockDim.x) {
+        const int yl = q / nx, x = q - yl * nx;
+        const int y = y0 + yl;
+        int xa = x + o.ix0;
+        if (xa >= nx) xa -= nx;
+        const int xb = (xa + 1 == nx) ? 0 : xa + 1;
+        int ya = y + o.iy0;
+        if (ya >= ny) ya -= ny;
+        const int yb = (ya + 1 == ny) ? 0 : ya + 1;
+        const T *ca = a.chi0 + pp + (long)ya * nx, *cb = a.chi0 + pp + (long)yb * nx;
+        const T chi_up = w00 * ca[xa] + w10 * ca[xb] + w01 * cb[xa] + w11 * cb[xb];
+        const long v = (long)k * nplane + (long)y * nx + x;
+        const T dtau0 = (chi_up + a.chi0[v]) * half_s;
+        const T inv_dtau0 = rcp(dtau0);
+        const int ba = band_of(ya, rmagic), bb = band_of(yb, rmagic);
+        const T *Pa = (ba == rank ? prev : cluster.map_shared_rank(prev, ba)) +
+                      (long)(ya - ba * rows) * nx;
+        const T *Pb = (bb == rank ? prev : cluster.map_shared_rank(prev, bb)) +
+                      (long)(yb - bb * rows) * nx;
+        T cj = 0, cu = 0;
+        for (int f = 0; f < nf; ++f) {
+            const long fo = (long)a.fidx[f0 + f] * nvox;
+            const T *sa = a.rhoS + fo + pp + (long)ya * nx;
+            const T *sb = a.rhoS + fo + pp + (long)yb * nx;
+            const T S_up = w00 * sa[xa] + w10 * sa[xb] + w01 * sb[xa] + w11 * sb[xb];
+            const T S_loc = a.rhoS[fo + v], rho_loc = a.rho[fo + v];
+            T ex, w0, wup, uu;
+            ScWeights<T>::eval(dtau0 * phi[f], inv_dtau0 * inv_phi[f], et, ex, w0, wup, uu);
+            const long off = (long)f * rows * nx;
+            const T I_up = w00 * Pa[off + xa] + w10 * Pa[off + xb] + w01 * Pb[off + xa] +
+                           w11 * Pb[off + xb];
+            const T part = I_up * ex + wup * S_up;
+            const T I = part + w0 * S_loc;
+            cur[off + (long)yl * nx + x] = I;
+            cj += wphi[f] * part;
+            cu += wphi[f] * (T(1) - w0 * rho_loc);
+            atomicAdd(a.jnu + fo + v, wr * I);
+        }
+        pj[v] = cj;
+        pu[v] = cu;
+    }
+}
+
 // Body of the sweep for ray r and frequency group g of one problem.  STAGE:
 // chi0 and S rows of each step are copied to shared memory one step ahead;
 // without it they are read from global memory (L1/L2) where used.  HERM:
@@ -275,6 +342,7 @@ __device__ __forceinline__ void moving_step(
 template <typename T, bool STAGE, int MODE>
 __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) {
     constexpr bool HERM = MODE == kSweepHermite, VEL = MODE == kSweepMoving;
+    constexpr bool PRD = MODE == kSweepPrd;
     static_assert(!(STAGE && MODE != kSweepLinear), "Hermite and moving sweeps run unstaged");
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
@@ -295,7 +363,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
     T *buf = reinterpret_cast<T *>(smem_raw);
     const long bufstride = (long)a.ng * rows * nx;
     T *dbuf = buf + 2 * bufstride;  // slope planes (HERM) or opacity planes (VEL)
-    T *stage = buf + (MODE != kSweepLinear ? 4 : 2) * bufstride;
+    // Hermite and moving sweeps keep a second plane pair (sweep_smem_bytes)
+    T *stage = buf + ((HERM || VEL) ? 4 : 2) * bufstride;
     const long stagestride = STAGE ? sweep_stage_elems(rows, nx) : 0;
     T *tabs = stage + 2 * stagestride;
     T *phi = tabs, *inv_phi = tabs + a.ng, *wphi = tabs + 2 * a.ng, *wu = tabs + 3 * a.ng;
@@ -372,6 +441,25 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
                 pj[v] = cj;
                 pu[v] = cu;
             }
+        } else if (t == 0 && PRD) {
+            // entering boundary with partial redistribution: as below, and
+            // the intensity enters the new mean intensity of its frequency
+            for (int q = threadIdx.x; q < band; q += blockDim.x) {
+                const int yl = q / nx, x = q - yl * nx;
+                const int y = y0 + yl;
+                const long v = (long)k * nplane + (long)y * nx + x;
+                const T Ib = up ? a.bbot[(long)y * nx + x] : T(0);
+                T cj = 0, cu = 0;
+                for (int f = 0; f < nf; ++f) {
+                    cur[((long)f * rows + yl) * nx + x] = Ib;
+                    cj += wphi[f] * Ib;
+                    cu += wphi[f];
+                    if (Ib != T(0))
+                        atomicAdd(a.jnu + (long)a.fidx[f0 + f] * nvox + v, Ib * T(1.0 / kRays));
+                }
+                pj[v] = cj;
+                pu[v] = cu;
+            }
         } else if (t == 0) {
             // entering boundary: I prescribed (bottom: Planck at the local
             // temperature; top: zero), so w0 = 0 and 1 - w0 = 1
@@ -414,6 +502,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
                 moving_step(a, r, rank, rmagic, cluster, prev, dbuf + ((t - 1) & 1) * bufstride,
                             cur, dbuf + (t & 1) * bufstride, pj, pu, k, kp, o, half_s, f0, nf,
                             et);
+            } else if constexpr (PRD) {
+                prd_step(a, rank, rmagic, cluster, prev, cur, pj, pu, k, kp, o, half_s, f0, nf,
+                         phi, inv_phi, wphi, et);
             } else
             for (int q = threadIdx.x; q < band; q += blockDim.x) {
                 const int yl = q / nx, x = q - yl * nx;
@@ -661,6 +752,10 @@ static cudaError_t launch_sweep_any(const SweepArgs<T> &a, const SweepShape &s,
         if (s.stage || !a.uproj || !a.vnorm || !a.xf || !a.wq) return cudaErrorInvalidValue;
         return launch_sweep_st<T, false, kSweepMoving>(a, s, st);
     }
+    if (s.prd) {
+        if (s.stage || !a.rhoS || !a.rho || !a.fidx || !a.jnu) return cudaErrorInvalidValue;
+        return launch_sweep_st<T, false, kSweepPrd>(a, s, st);
+    }
     return s.stage ? launch_sweep_st<T, true, kSweepLinear>(a, s, st)
                    : launch_sweep_st<T, false, kSweepLinear>(a, s, st);
 }
@@ -678,9 +773,10 @@ static cudaError_t clusters_st(const SweepShape &s, int nx, int *n) {
 
 template <typename T>
 static cudaError_t clusters_any(const SweepShape &s, int nx, int *n) {
-    if ((s.herm || s.vel) && s.stage) return cudaErrorInvalidValue;
+    if ((s.herm || s.vel || s.prd) && s.stage) return cudaErrorInvalidValue;
     if (s.herm) return clusters_st<T, false, kSweepHermite>(s, nx, n);
     if (s.vel) return clusters_st<T, false, kSweepMoving>(s, nx, n);
+    if (s.prd) return clusters_st<T, false, kSweepPrd>(s, nx, n);
     return s.stage ? clusters_st<T, true, kSweepLinear>(s, nx, n)
                    : clusters_st<T, false, kSweepLinear>(s, nx, n);
 }
@@ -817,6 +913,53 @@ cudaError_t launch_vel_prep(int prec, long nvox, int nfreq, const double *mu, co
     else
         vel_prep_kernel<float><<<grid_for(total, th), th, 0, st>>>(
             nvox, nfreq, mu, vel, xf, wq, (float *)uproj, (float *)vnorm);
+    return cudaGetLastError();
+}
+
+// Per node: Jbar = sum wphi_f J_f, f_rad = B_lu Jbar/(B_lu Jbar + C_lu),
+// rho_f = 1 + gamma f_rad (sum_f' kmat[f'][f] J_f' / Jbar - 1) (1 where
+// Jbar = 0), and rho_f S with S = n_u/(n_l g - n_u); sums in FP64.
+template <typename T>
+__global__ void prd_source_kernel(long nvox, int nfreq, double gamma, double g_ratio, double a_ul,
+                                  const double *__restrict__ kmat,
+                                  const double *__restrict__ wphi, const double *__restrict__ n,
+                                  const double *__restrict__ c_lu, const T *__restrict__ jnu,
+                                  T *__restrict__ rho, T *__restrict__ rhoS) {
+    for (long v = blockIdx.x * (long)blockDim.x + threadIdx.x; v < nvox;
+         v += (long)gridDim.x * blockDim.x) {
+        double jbar = 0.0;
+        for (int f = 0; f < nfreq; ++f) jbar += wphi[f] * (double)jnu[(long)f * nvox + v];
+        const double blu = g_ratio * a_ul;
+        const double frad = jbar > 0.0 ? blu * jbar / (blu * jbar + c_lu[v]) : 0.0;
+        const double nl = n[v], nu = n[nvox + v];
+        const double S = nu / (nl * g_ratio - nu);
+        for (int f = 0; f < nfreq; ++f) {
+            double r = 1.0;
+            if (jbar > 0.0) {
+                double acc = 0.0;
+                for (int fp = 0; fp < nfreq; ++fp)
+                    acc += kmat[(long)fp * nfreq + f] * (double)jnu[(long)fp * nvox + v];
+                r = 1.0 + gamma * frad * (acc / jbar - 1.0);
+            }
+            rho[(long)f * nvox + v] = (T)r;
+            rhoS[(long)f * nvox + v] = (T)(r * S);
+        }
+    }
+}
+
+cudaError_t launch_prd_source(int prec, long nvox, int nfreq, double gamma, double g_ratio,
+                              double a_ul, const double *kmat, const double *wphi,
+                              const double *n, const double *c_lu, const void *jnu, void *rho,
+                              void *rhoS, cudaStream_t st) {
+    const int th = 256;
+    if (prec == 0)
+        prd_source_kernel<double><<<grid_for(nvox, th), th, 0, st>>>(
+            nvox, nfreq, gamma, g_ratio, a_ul, kmat, wphi, n, c_lu, (const double *)jnu,
+            (double *)rho, (double *)rhoS);
+    else
+        prd_source_kernel<float><<<grid_for(nvox, th), th, 0, st>>>(
+            nvox, nfreq, gamma, g_ratio, a_ul, kmat, wphi, n, c_lu, (const float *)jnu,
+            (float *)rho, (float *)rhoS);
     return cudaGetLastError();
 }
 

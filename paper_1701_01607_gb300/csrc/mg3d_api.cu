@@ -75,6 +75,9 @@ struct Level {
     void *uproj = nullptr, *vnorm = nullptr;  // [kRays][nvox] projected velocity, 1/sum w phi
                                               // (multi-level: vnorm [nlines][kRays][nvox])
     void *dinv = nullptr;        // multi-level, moving: 1/d per node [nvox]
+    // partial redistribution (two-level): the lagged and the new mean
+    // intensity per frequency, rho and rho S [nf][nvox] (natural order)
+    void *jnu = nullptr, *jnu_new = nullptr, *rho = nullptr, *rhoS = nullptr;
     StepGeom *geom = nullptr;    // [kRays][nz]
     SweepShape shape{};
     // multi-level atom only
@@ -134,6 +137,10 @@ struct mg3d_handle {
     void *d_ftab = nullptr;
     void *d_vtab = nullptr;      // moving atmospheres: [nf] offsets x, [nf] weights w
     int *d_vline = nullptr;      // multi-level, moving: line index of each frequency or -1
+    bool prd = false;            // two-level partial redistribution
+    double *d_kmat = nullptr;    // [nf][nf] w_f' R(f', f) / phi_f
+    double *d_wphin = nullptr;   // [nf] normalised w phi, natural order
+    int *d_fidx = nullptr;       // [2][nf] natural frequency of each table position
     bool moving = false;         // the atmosphere has a velocity field
     double *d_exp_tab = nullptr;         // [64] table of the FP64 exp in the sweep
     double exp_l1 = 0, exp_l2 = 0;
@@ -253,7 +260,10 @@ SweepArgs<T> sweep_args(const mg3d_handle *h, const Level &L, const SweepShape &
                         h->exp_l1, h->exp_l2, (const T *)L.dchi0, (const T *)L.dS,
                         (const T *)L.uproj, (const T *)L.vnorm,
                         h->moving ? (const T *)h->d_vtab : nullptr,
-                        h->moving ? (const T *)h->d_vtab + h->atom.n_freq : nullptr};
+                        h->moving ? (const T *)h->d_vtab + h->atom.n_freq : nullptr,
+                        (const T *)L.rhoS, (const T *)L.rho,
+                        h->prd ? h->d_fidx + (s.ng % 2 == 1 ? h->atom.n_freq : 0) : nullptr,
+                        (T *)L.jnu_new};
 }
 
 // Upwind crossing of every (ray, sweep step): for step t the plane is
@@ -296,14 +306,15 @@ int threads_for_band(int band) {
 // the number of bands that brings the grid closest to two blocks per SM (the
 // shapes measured fastest on the 64x64 planes of the bench workload, in both
 // precisions, were of this kind); mg3d_autotune replaces it by measurement.
-SweepShape choose_shape(int prec, int nx, int ny, int nfreq, int herm, int vel) {
+SweepShape choose_shape(int prec, int nx, int ny, int nfreq, int herm, int vel, int prd) {
     const int ng = nfreq < 3 ? nfreq : 3;
     const int ngroups = (nfreq + ng - 1) / ng;
     SweepShape best{};
     auto with_mode = [&](SweepShape s) {
         s.herm = herm;
         s.vel = vel;
-        s.stage = herm || vel ? 0 : 1;
+        s.prd = prd;
+        s.stage = herm || vel || prd ? 0 : 1;
         return s;
     };
     long best_gap = 1L << 40;
@@ -355,7 +366,8 @@ void free_level(Level &L) {
     void *ptrs[] = {L.T,     L.n_tot, L.c_ul, L.c_lu, L.tz,   L.zf,   L.n,    L.f,   L.n_before,
                     L.r,     L.chi0,  L.S,    L.bbot, L.geom, L.chi_c, L.cmat, L.saha,
                     L.mchi,  L.mS,    L.msl,  L.mfl,  L.mib,  L.sigma_c, L.jbg,
-                    L.dchi0, L.dS,   L.mdchi, L.mdS,  L.vel,  L.uproj, L.vnorm, L.dinv};
+                    L.dchi0, L.dS,   L.mdchi, L.mdS,  L.vel,  L.uproj, L.vnorm, L.dinv,
+                    L.jnu,   L.jnu_new, L.rho, L.rhoS};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     L = Level{};
@@ -465,16 +477,17 @@ int ml_chunk_fs(mg3d_handle *h, int k, int f0, int nc) {
 // coarse operator stays the same from the tau-correction of Eq. 9 to the
 // correction of Eq. 10.
 bool updates_background(const mg3d_handle *h, int k) {
-    return h->scatter && (h->force_bg || k == (h->top ? h->top : h->L));
+    return (h->scatter || h->prd) && (h->force_bg || k == (h->top ? h->top : h->L));
 }
 
-int ml_formal_solution(mg3d_handle *h, int k);
+int formal_solution(mg3d_handle *h, int k);
 
-// One Lambda-iteration of the background field of grid k: a formal solution
-// with the populations held whose mean intensity becomes the field.
+// One Lambda-iteration of the lagged field of grid k (background field, or
+// the mean intensity of partial redistribution): a formal solution with the
+// populations held whose mean intensity becomes the field.
 int lambda_iteration(mg3d_handle *h, int k) {
     h->force_bg = true;
-    const int rc = ml_formal_solution(h, k);
+    const int rc = formal_solution(h, k);
     h->force_bg = false;
     return rc;
 }
@@ -537,6 +550,19 @@ MlRateArgs ml_rate_args(mg3d_handle *h, int k, int mode) {
     return a;
 }
 
+// Partial redistribution before a sweep of level k: rho and rho S from the
+// lagged field, and the new mean intensity cleared for the sweep to add into.
+int prd_prepare(mg3d_handle *h, int k) {
+    Level &L = h->lev[k];
+    MG_TRY(launched(h, launch_prd_source(h->prec, L.nvox, h->atom.n_freq, h->atom.gamma_prd,
+                                         h->atom.g_ratio, h->atom.a_ul, h->d_kmat, h->d_wphin,
+                                         L.n, L.c_lu, L.jnu, L.rho, L.rhoS, h->stream),
+                    "partial redistribution"));
+    MG_CUDA(cudaMemsetAsync(L.jnu_new, 0, (size_t)h->atom.n_freq * L.nvox * elem_size(h->prec),
+                            h->stream));
+    return MG3D_OK;
+}
+
 // Formal solution on level k with its populations: partial sums into pj/pu.
 int formal_solution(mg3d_handle *h, int k) {
     if (h->kind == 1) return ml_formal_solution(h, k);
@@ -548,6 +574,7 @@ int formal_solution(mg3d_handle *h, int k) {
         MG_TRY(launched(h, launch_xslopes(h->prec, L.nx, L.nvox, L.chi0, L.S, L.dchi0, L.dS,
                                           h->stream),
                         "x-slopes"));
+    if (h->prd) MG_TRY(prd_prepare(h, k));
     TimedLaunch tl{nullptr, nullptr, k};
     if (h->timing) {
         tl.a = pool_event(h);
@@ -565,6 +592,10 @@ int formal_solution(mg3d_handle *h, int k) {
         MG_CUDA(record_event(tl.b, h->stream));
         h->timed.push_back(tl);
     }
+    if (h->prd && updates_background(h, k))   // the new mean intensity becomes the field
+        MG_CUDA(cudaMemcpyAsync(L.jnu, L.jnu_new,
+                                (size_t)h->atom.n_freq * L.nvox * elem_size(h->prec),
+                                cudaMemcpyDeviceToDevice, h->stream));
     ++h->fs_launches;
     h->fs_units += (double)L.nvox * kRays * h->atom.n_freq;
     ++h->level_launches[k];
@@ -649,6 +680,10 @@ int zero_radiation(mg3d_handle *h, int k) {
     a.zero_radiation = 1;
     a.scal = nullptr;
     MG_TRY(launched(h, launch_rates(a, h->stream), "zero radiation"));
+    if (h->prd)   // the lagged field starts at zero: the first formal solution sees CRD
+        MG_CUDA(cudaMemsetAsync(h->lev[k].jnu, 0,
+                                (size_t)h->atom.n_freq * h->lev[k].nvox * elem_size(h->prec),
+                                h->stream));
     return MG3D_OK;
 }
 
@@ -689,6 +724,14 @@ int vcycle(mg3d_handle *h, int k, bool first) {
         MG_TRY(launched(h, launch_restrict_prec(h->prec, h->nfreq_ml, F.nx, F.ny, F.nz, F.jbg,
                                                 C.jbg, h->stream),
                         "restrict background field"));
+        MG_TRY(lambda_iteration(h, k - 1));
+    }
+    if (h->kind == 0 && h->prd) {
+        // the lagged mean intensity of partial redistribution, like the
+        // background field: full-weighted, one Lambda-iteration, then fixed
+        MG_TRY(launched(h, launch_restrict_prec(h->prec, h->atom.n_freq, F.nx, F.ny, F.nz, F.jnu,
+                                                C.jnu, h->stream),
+                        "restrict mean intensity"));
         MG_TRY(lambda_iteration(h, k - 1));
     }
     MG_TRY(launched(h, launch_restrict(h->N, F.nx, F.ny, F.nz, F.r, C.f, h->stream,
@@ -881,7 +924,8 @@ int make_shape(const mg3d_handle *h, int k, int ng, int bands, int threads, Swee
     if ((long)(bands - 1) * s.rows >= L.ny) return fail(MG3D_E_ARG, "empty band");
     s.herm = h->params.sc_interp;
     s.vel = h->moving ? 1 : 0;
-    s.stage = s.herm || s.vel ? 0 : 1;
+    s.prd = h->prd ? 1 : 0;
+    s.stage = s.herm || s.vel || s.prd ? 0 : 1;
     *out = s;
     return MG3D_OK;
 }
@@ -898,6 +942,8 @@ static int shape_from_args(const mg3d_handle *h, int level, int freq_per_block, 
     if (stage && h->params.sc_interp)
         return fail(MG3D_E_ARG, "Hermite upwind interpolation runs unstaged (stage 0)");
     if (stage && h->moving) return fail(MG3D_E_ARG, "moving atmospheres run unstaged (stage 0)");
+    if (stage && h->prd)
+        return fail(MG3D_E_ARG, "partial redistribution runs unstaged (stage 0)");
     SweepShape s;
     MG_TRY(make_shape(h, level, freq_per_block, bands, threads, &s));
     s.lean = lean;
@@ -1028,6 +1074,7 @@ int autotune_level(mg3d_handle *h, int k, int *evaluated) {
         MG_TRY(launched(h, launch_xslopes(h->prec, L.nx, L.nvox, L.chi0, L.S, L.dchi0, L.dS,
                                           h->stream),
                         "x-slopes"));
+    if (h->prd) MG_TRY(prd_prepare(h, k));
     float warm = 0.f;
     MG_TRY(time_shape(h, k, L.shape, 1, &warm));
     std::vector<std::pair<float, size_t>> t1;
@@ -1108,6 +1155,49 @@ int setup_velocity(mg3d_handle *h, const double *vel_host) {
     return rc;
 }
 
+// Partial redistribution tables: the discrete redistribution matrix
+// R = diag(c) R0 diag(c), R0(x', x) = erfc(max(|x|, |x'|))/2, with c from the
+// fixed-point iteration c <- sqrt(c phi / (R0^T (wq c))) so that both
+// marginals sum_f' wq_f' R(f', f) are phi_f (wq: the quadrature weights
+// normalised so that sum wq phi = 1); uploaded as kmat[f'][f] = wq_f' R(f', f)
+// / phi_f with the normalised w phi and the table-order to natural-order map.
+int setup_prd(mg3d_handle *h) {
+    const int nf = h->atom.n_freq;
+    std::vector<double> x(nf), wq(nf);
+    for (int i = 0; i < nf; ++i) {
+        x[i] = nf == 1 ? 0.0 : h->atom.x_max * (2 * i - (nf - 1)) / (nf - 1);
+        wq[i] = h->wphi[i] / h->phi[i];
+    }
+    std::vector<double> R0((size_t)nf * nf), c(nf, 1.0), t(nf);
+    for (int a = 0; a < nf; ++a)
+        for (int b = 0; b < nf; ++b)
+            R0[(size_t)a * nf + b] = 0.5 * std::erfc(std::max(std::fabs(x[a]), std::fabs(x[b])));
+    for (int it = 0; it < 200; ++it) {
+        for (int b = 0; b < nf; ++b) {
+            double s = 0.0;
+            for (int a = 0; a < nf; ++a) s += R0[(size_t)a * nf + b] * wq[a] * c[a];
+            t[b] = s;
+        }
+        for (int b = 0; b < nf; ++b) c[b] = std::sqrt(c[b] * h->phi[b] / t[b]);
+    }
+    std::vector<double> kmat((size_t)nf * nf);
+    for (int a = 0; a < nf; ++a)
+        for (int b = 0; b < nf; ++b)
+            kmat[(size_t)a * nf + b] = wq[a] * c[a] * R0[(size_t)a * nf + b] * c[b] / h->phi[b];
+    std::vector<int> fidx(2 * (size_t)nf);
+    for (int order = 0; order < 2; ++order)
+        for (int j = 0; j < nf; ++j) fidx[(size_t)order * nf + j] = mirror_order(nf, order, j);
+    MG_TRY(dalloc(&h->d_kmat, kmat.size()));
+    MG_TRY(dalloc(&h->d_wphin, (size_t)nf));
+    MG_TRY(dev_alloc((void **)&h->d_fidx, fidx.size() * sizeof(int)));
+    MG_CUDA(cudaMemcpy(h->d_kmat, kmat.data(), kmat.size() * sizeof(double),
+                       cudaMemcpyHostToDevice));
+    MG_CUDA(cudaMemcpy(h->d_wphin, h->wphi.data(), (size_t)nf * sizeof(double),
+                       cudaMemcpyHostToDevice));
+    MG_CUDA(cudaMemcpy(h->d_fidx, fidx.data(), fidx.size() * sizeof(int), cudaMemcpyHostToDevice));
+    return MG3D_OK;
+}
+
 int create_impl(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_quadrature *quad,
                 const mg3d_params *params, mg3d_handle *h) {
     h->L = params->n_grids;
@@ -1115,6 +1205,7 @@ int create_impl(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_qu
     h->atom = *atom;
     h->params = *params;
     h->moving = atm->vel != nullptr;
+    h->prd = atom->gamma_prd > 0.0;
     build_quadrature(h, quad ? quad->a : 0.0);
     build_frequencies(h);
     MG_CUDA(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
@@ -1165,7 +1256,12 @@ int create_impl(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_qu
         build_geometry(h, L, g);
         MG_CUDA(cudaMemcpy(L.geom, g.data(), g.size() * sizeof(StepGeom), cudaMemcpyHostToDevice));
         L.shape = choose_shape(h->prec, L.nx, L.ny, atom->n_freq, params->sc_interp,
-                               atm->vel ? 1 : 0);
+                               atm->vel ? 1 : 0, atom->gamma_prd > 0.0 ? 1 : 0);
+        if (atom->gamma_prd > 0.0) {
+            void **bufs[4] = {&L.jnu, &L.jnu_new, &L.rho, &L.rhoS};
+            for (void **p : bufs) MG_TRY(dev_alloc(p, (size_t)atom->n_freq * L.nvox * es));
+            MG_CUDA(cudaMemset(L.jnu, 0, (size_t)atom->n_freq * L.nvox * es));
+        }
         if (params->sc_interp) {
             MG_TRY(dev_alloc(&L.dchi0, L.nvox * es));
             MG_TRY(dev_alloc(&L.dS, L.nvox * es));
@@ -1229,6 +1325,7 @@ int create_impl(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_qu
         std::vector<float> t32(tabs.begin(), tabs.end());
         MG_CUDA(cudaMemcpy(h->d_ftab, t32.data(), t32.size() * es, cudaMemcpyHostToDevice));
     }
+    if (h->prd) MG_TRY(setup_prd(h));
     {
         double tab[kExpTab];
         exp_neg_constants(tab, &h->exp_l1, &h->exp_l2);
@@ -2175,6 +2272,11 @@ int mg3d_create(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_qu
         return fail(MG3D_E_ARG, "sc_interp must be 0 or 1");
     if (atm->vel && params->sc_interp)
         return fail(MG3D_E_ARG, "moving atmospheres take the linear upwind interpolation");
+    if (!(atom->gamma_prd >= 0.0 && atom->gamma_prd <= 1.0))
+        return fail(MG3D_E_ARG, "gamma_prd must lie in [0, 1]");
+    if (atom->gamma_prd > 0.0 && (atm->vel || params->sc_interp))
+        return fail(MG3D_E_ARG,
+                    "partial redistribution takes a static atmosphere and linear interpolation");
     if (atom->n_freq < 1 || atom->n_freq > 4096 || !(atom->x_max >= 0.0) ||
         !(atom->a_ul > 0.0) || !(atom->g_ratio > 0.0) || !(atom->theta > 0.0) ||
         !(atom->kappa > 0.0))
@@ -2399,6 +2501,8 @@ int mg3d_batch_create(int n, mg3d_handle *const *members, mg3d_batch **out) {
             return fail(MG3D_E_ARG, "batches do not take Hermite upwind interpolation");
         if (members[i]->moving)
             return fail(MG3D_E_ARG, "batches do not take moving atmospheres");
+        if (members[i]->prd)
+            return fail(MG3D_E_ARG, "batches do not take partial redistribution");
         for (int j = 0; j < i; ++j)
             if (members[j] == members[i]) return fail(MG3D_E_ARG, "member listed twice");
     }
@@ -2571,7 +2675,8 @@ int mg3d_destroy(mg3d_handle *h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     drop_graphs(h);
     for (int k = 0; k <= MG3D_MAX_GRIDS; ++k) free_level(h->lev[k]);
-    void *ptrs[] = {h->d_ftab, h->d_vtab, h->d_vline, h->d_exp_tab, h->pj, h->pu, h->scal,
+    void *ptrs[] = {h->d_ftab, h->d_vtab, h->d_vline, h->d_kmat, h->d_wphin, h->d_fidx,
+                    h->d_exp_tab, h->pj, h->pu, h->scal,
                     h->scratch, h->d_fi, h->d_ti, h->ml_jx, h->ml_ux, h->ml_acc,
                     h->ml_jm};
     for (void *p : ptrs)
@@ -2738,6 +2843,11 @@ int mg3d_fmg_solve(mg3d_handle *h, double tol, int max_cycles, mg3d_stats *stats
                                                    Ck.nx, Ck.ny, Ck.nz, Fk.tz, Fk.zf, Ck.jbg,
                                                    Fk.jbg, h->stream),
                             "prolong background field"));
+        if (h->kind == 0 && h->prd)
+            MG_TRY(launched(h, launch_prolong_prec(h->params.interpolation, h->prec,
+                                                   h->atom.n_freq, Ck.nx, Ck.ny, Ck.nz, Fk.tz,
+                                                   Fk.zf, Ck.jnu, Fk.jnu, h->stream),
+                            "prolong mean intensity"));
         Fk.f_default = true;
         if (k < h->L) {
             MG_TRY(reset_scalars(h));

@@ -37,10 +37,12 @@ struct SweepShape {
     int stage = 1; // 1: chi0/S rows staged in shared memory one step ahead
     int herm = 0;  // 1: monotone cubic Hermite upwind interpolation (unstaged)
     int vel = 0;   // 1: moving atmosphere, ray-dependent profiles (unstaged)
+    int prd = 0;   // 1: partial redistribution, frequency-dependent S (unstaged)
 };
 
-// Sweep variants: linear upwind interpolation, Hermite, moving atmosphere.
-constexpr int kSweepLinear = 0, kSweepHermite = 1, kSweepMoving = 2;
+// Sweep variants: linear upwind interpolation, Hermite, moving atmosphere,
+// partial redistribution.
+constexpr int kSweepLinear = 0, kSweepHermite = 1, kSweepMoving = 2, kSweepPrd = 3;
 
 // Arguments of the sweep kernel.  T is the formal-solution precision.
 template <typename T>
@@ -63,6 +65,13 @@ struct SweepArgs {
     // the profile normalisation [kRays][nvox]; per frequency (natural order)
     // the offset x_f and the quadrature weight w_f [nfreq]
     const T *uproj, *vnorm, *xf, *wq;
+    // partial redistribution only: rho S and rho per frequency in natural
+    // order [nfreq][nvox], the natural index of each table position
+    // [nfreq], and the new mean intensity per frequency [nfreq][nvox] the
+    // sweep adds into (zeroed before)
+    const T *rhoS, *rho;
+    const int *fidx;
+    T *jnu;
 };
 
 // Table and reduction constants of the FP64 e^{-x} of the sweep.
@@ -77,6 +86,14 @@ size_t sweep_smem_bytes(int prec, const SweepShape &s, int nx);
 cudaError_t launch_vel_prep(int prec, long nvox, int nfreq, const double *mu, const double *vel,
                             const double *xf, const double *wq, void *uproj, void *vnorm,
                             cudaStream_t st);
+// Partial redistribution (two-level atom): per node rho_f and rho_f S from
+// the lagged mean intensity jnu [nfreq][nvox] (natural frequency order), the
+// populations n [2][nvox] and the collisional rates; kmat [nfreq][nfreq] =
+// w_f' R(f', f) / phi_f and wphi [nfreq] (normalised) in natural order.
+cudaError_t launch_prd_source(int prec, long nvox, int nfreq, double gamma, double g_ratio,
+                              double a_ul, const double *kmat, const double *wphi,
+                              const double *n, const double *c_lu, const void *jnu, void *rho,
+                              void *rhoS, cudaStream_t st);
 // Monotone x-slopes (one cell units, periodic rows of nx) of a and b.
 cudaError_t launch_xslopes(int prec, int nx, long nvox, const void *a, const void *b, void *da,
                            void *db, cudaStream_t st);
