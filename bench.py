@@ -668,6 +668,51 @@ def run_velocity(args):
     return out
 
 
+def run_prd(args):
+    """Partial redistribution (two-level atom): the 64x64x129 box (eps =
+    1e-4, sigma = 0.3) with 17 frequencies on [-5, 5] Doppler widths and
+    coherence fractions 0 (CRD), 0.5 and 1; FP64 MALI and 3-grid FAS to
+    E_inf <= 1e-3 against each case's FAS reference converged to C < 1e-9,
+    and the autotuned sweep time in FP64 and FP32.  Opt-in,
+    --prd-experiment; prints one JSON line."""
+    from paper_1701_01607_gb300 import mg3d as m
+    from paper_1701_01607_gb300 import synth
+    m.load(build_if_missing=True)
+    out = {"metric": "iterations and seconds to E_inf <= 1e-3; sweep ms per launch",
+           "unit": "s", "higher_is_better": False, "n_gpus": 1, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": "64x64x129 two-level box, eps 1e-4, sigma 0.3, seed 1, "
+                                  "17 frequencies on [-5, 5]", "nu": NU, "target_e_inf": 1e-3}}
+    for gamma in (0.0, 0.5, 1.0):
+        atom = synth.TwoLevelAtom(n_freq=17, x_max=5.0, gamma_prd=gamma)
+        atm, _ = synth.stratified_two_level(GRID[0], GRID[1], GRID[2], eps=1e-4, sigma=0.3,
+                                            seed=1, atom=atom)
+        ref = m.mg3d_create(atm, atom, n_grids=3, **NU)
+        m.mg3d_fas_solve(ref, 1e-9, 400, n_grids=3)
+        n_ref = m.mg3d_get_populations(ref, 3)
+        m.mg3d_destroy(ref)
+        row = {"fas": _to_target(m, lambda: m.mg3d_create(atm, atom, n_grids=3, **NU), 3, n_ref,
+                                 lambda h, it: m.mg3d_fas_vcycle(h, it == 0), 60),
+               "mali": _to_target(m, lambda: m.mg3d_create(atm, atom, n_grids=1, **NU), 1, n_ref,
+                                  lambda h, it: m.mg3d_mali_sweep(h, 1, 1), 3000)}
+        for prec, pname in ((m.MG3D_PREC_F64, "f64"), (m.MG3D_PREC_F32, "f32")):
+            h = m.mg3d_create(atm, atom, n_grids=1, fs_prec=prec, **NU)
+            try:
+                m.mg3d_autotune(h)
+                m.mg3d_set_timing(h, True)
+                m.mg3d_reset_counters(h)
+                for _ in range(5):
+                    m.mg3d_formal_solve(h, 1, want=False)
+                c = m.mg3d_get_counters(h)
+                row[f"sweep_{pname}"] = {
+                    "ms": round(c["fs_kernel_ms"] / c["fs_timed_launches"], 3),
+                    "shape": list(m.mg3d_get_fs_config(h, 1))}
+            finally:
+                m.mg3d_destroy(h)
+        out[f"gamma_{gamma:g}"] = row
+    return out
+
+
 def run_interpolation(args):
     """The Hermite options of Sec. 3 and Sec. 4.5 on the 64x64x129 two-level
     box (eps = 1e-4; rough sigma = 0.3 and smooth sigma = 0), FP64:
@@ -893,6 +938,8 @@ def main():
                     help="run the restriction / grid-count experiments instead")
     ap.add_argument("--chromosphere", action="store_true",
                     help="time MALI, FAS and FMG on the 128x128x257 6-level chromosphere instead")
+    ap.add_argument("--prd-experiment", action="store_true",
+                    help="partial redistribution against complete redistribution")
     ap.add_argument("--velocity-experiment", action="store_true",
                     help="a moving atmosphere against a static one")
     ap.add_argument("--interp-experiment", action="store_true",
@@ -921,6 +968,9 @@ def main():
         return
     if args.batch:
         print(json.dumps(run_batch(args)), flush=True)
+        return
+    if args.prd_experiment:
+        print(json.dumps(run_prd(args)), flush=True)
         return
     if args.velocity_experiment:
         print(json.dumps(run_velocity(args)), flush=True)
