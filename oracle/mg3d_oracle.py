@@ -34,6 +34,16 @@ What each function follows in the paper (Bjorgen & Leenaarts 2017):
   with nu_1 pre-, nu_2 post-smoothing, nu_3 coarse iterations, nu_0 in the
   first cycle (Sec. 4.12) and the 10 % fix for negative populations (Sec. 4.10).
 * ``fmg_solve``         -- full multigrid (Sec. 2.3, Fig. 1).
+* ``MultiLevelProblem`` -- the multi-level atom (Eqs. 2-4 with lines, continua
+  and a grey background, Sec. 3.2), with optional background coherent
+  scattering whose field is lagged, Lambda-iterated at the zero-radiation
+  start and on each coarse-grid entry, and held on coarse grids (Sec. 4.8).
+* ``formal_solution_moving`` -- moving atmospheres (both atom kinds): the
+  profile seen along ray r shifted by mu_r . u and renormalised per node and
+  ray (the paper's Bifrost atmospheres move; Sec. 3.1, Sec. 6).
+* ``prd_matrix`` / ``formal_solution_prd`` -- partial redistribution for the
+  two-level atom (the next step of Sec. 6): angle-averaged Doppler
+  redistribution mixed with CRD, S_f = rho_f S from the lagged field.
 
 Readings where the paper is silent (the same readings hold on the GPU path):
 full weighting at the fixed z boundaries injects in z; n_before of Eq. 10 is

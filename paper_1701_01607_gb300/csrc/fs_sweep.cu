@@ -724,7 +724,8 @@ static cudaError_t clusters_t(const SweepShape &s, int nx, int *n) {
     cudaError_t e = sweep_config<T, MAXT, MINB, STAGE, MODE>(s, nx, 0, &cfg, attr);
     if (e != cudaSuccess) return e;
     if (s.bands == 1)  // plain launch: resident blocks per SM
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, sweep_kernel<T, MAXT, MINB, STAGE, MODE>,
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(n,
+                                                             sweep_kernel<T, MAXT, MINB, STAGE, MODE>,
                                                              s.threads, cfg.dynamicSmemBytes);
     return cudaOccupancyMaxActiveClusters(n, sweep_kernel<T, MAXT, MINB, STAGE, MODE>, &cfg);
 }

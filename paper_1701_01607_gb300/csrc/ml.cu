@@ -352,17 +352,17 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
                         r4.r[m] = yr[m] * nx;
                     }
                     rowref4[j * rows + yl] = r4;
-                    continue;
+                } else {
+                    const int ba = band_of(ya, rmagic), bb = band_of(yb, rmagic);
+                    const T *Pa = (ba == rank) ? prev : cluster.map_shared_rank(prev, ba);
+                    const T *Pb = (bb == rank) ? prev : cluster.map_shared_rank(prev, bb);
+                    RowRef r;
+                    r.pa = Pa + j * raystride + (long)(ya - ba * rows) * nx;
+                    r.pb = Pb + j * raystride + (long)(yb - bb * rows) * nx;
+                    r.ra = ya * nx;
+                    r.rb = yb * nx;
+                    rowref[j * rows + yl] = r;
                 }
-                const int ba = band_of(ya, rmagic), bb = band_of(yb, rmagic);
-                const T *Pa = (ba == rank) ? prev : cluster.map_shared_rank(prev, ba);
-                const T *Pb = (bb == rank) ? prev : cluster.map_shared_rank(prev, bb);
-                RowRef r;
-                r.pa = Pa + j * raystride + (long)(ya - ba * rows) * nx;
-                r.pb = Pb + j * raystride + (long)(yb - bb * rows) * nx;
-                r.ra = ya * nx;
-                r.rb = yb * nx;
-                rowref[j * rows + yl] = r;
             }
             __syncthreads();
             const int kp = up ? k - 1 : k + 1;
@@ -429,10 +429,11 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
                             return e0 * gq[1] + e1 * mono_slope(gq[1] - gq[0], gq[2] - gq[1]) +
                                    e2 * gq[2] + e3 * mono_slope(gq[2] - gq[1], gq[3] - gq[2]);
                         };
+                        const T *dchip = dchif + (long)kp * nplane, *dSp = dSf + (long)kp * nplane;
                         const T chi_up = up2d([&](int m) { return chip + r4.r[m]; },
-                                              [&](int m) { return dchif + (long)kp * nplane + r4.r[m]; });
+                                              [&](int m) { return dchip + r4.r[m]; });
                         const T S_up = up2d([&](int m) { return Sp + r4.r[m]; },
-                                            [&](int m) { return dSf + (long)kp * nplane + r4.r[m]; });
+                                            [&](int m) { return dSp + r4.r[m]; });
                         const T I_up = up2d([&](int m) { return r4.p[m]; },
                                             [&](int m) { return r4.d[m]; });
                         const T x_tau = (chi_up + chi_loc) * g_hs[j];
