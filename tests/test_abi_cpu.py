@@ -65,3 +65,33 @@ def test_null_handle_is_an_argument_error(lib):
     assert lib.mg3d_destroy(None) == m.MG3D_OK
     assert lib.mg3d_fas_vcycle(None, 0, None) == m.MG3D_E_ARG
     assert lib.mg3d_set_timing(None, 1) == m.MG3D_E_ARG
+
+
+STRUCTS = ("mg3d_atmosphere", "mg3d_atom", "mg3d_quadrature", "mg3d_params", "mg3d_stats",
+           "mg3d_counters", "mg3d_line", "mg3d_continuum", "mg3d_ml_atom", "mg3d_ml_atmosphere")
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every struct of the header has the binding's size and field offsets
+    (gcc compiles the header and prints them), so a field added on one side
+    only fails here."""
+    import ctypes
+    import subprocess
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "mg3d.h"', 'int main(void) {']
+    for name in STRUCTS:
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in getattr(m, name)._fields_:
+            lines.append(f'printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c99", "-I", os.path.dirname(HEADER), "-o", str(exe),
+                           str(src)])
+    out = subprocess.check_output([str(exe)], text=True).split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for name in STRUCTS:
+        cls = getattr(m, name)
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
