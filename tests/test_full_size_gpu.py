@@ -105,3 +105,37 @@ def test_chromosphere_64x64x129_mixed_precision_converged(atom):
     assert c32 == c64
     assert np.all(n32 > 0)
     assert float(np.max(np.abs(n32 - n64) / n64)) < 1e-4
+
+
+# ------------------------ the 64x64x129 bench box with a flow and with PRD
+
+def _two_level_sweeps(atm, atom, sweeps=2):
+    h = m.mg3d_create(atm, atom, n_grids=1, nu_fmg=16, nu0=0, nu1=2, nu2=2, nu3=32)
+    try:
+        m.mg3d_autotune(h)
+        m.mg3d_mali_sweep(h, 1, sweeps)
+        n_gpu = m.mg3d_get_populations(h, 1)
+    finally:
+        m.mg3d_destroy(h)
+    p = O.TwoLevelProblem(atm, atom)
+    n = p.zero_radiation(1)
+    for _ in range(sweeps):
+        n, _ = p.mali_sweep(1, n)
+    return float(np.max(np.abs(n_gpu - n) / np.abs(n)))
+
+
+def test_bench_box_moving_fp64():
+    """The 64x64x129 workload (eps = 1e-4, sigma = 0.3) with a flow of rms 1
+    Doppler width and autotuned shapes: two MALI sweeps against the oracle."""
+    atom = synth.TwoLevelAtom(n_freq=9)
+    atm, atom = synth.stratified_two_level(64, 64, 129, eps=1e-4, sigma=0.3, seed=1, atom=atom,
+                                           velocity=1.0)
+    assert _two_level_sweeps(atm, atom) < 1e-10
+
+
+def test_bench_box_prd_fp64():
+    """The same box with full coherence (gamma = 1): the second sweep uses the
+    mean intensity of the first."""
+    atom = synth.TwoLevelAtom(n_freq=9, gamma_prd=1.0)
+    atm, atom = synth.stratified_two_level(64, 64, 129, eps=1e-4, sigma=0.3, seed=1, atom=atom)
+    assert _two_level_sweeps(atm, atom) < 1e-10
