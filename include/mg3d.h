@@ -204,7 +204,12 @@ int mg3d_set_stream(mg3d_handle *h, void *cuda_stream);
 int mg3d_level_shape(const mg3d_handle *h, int level, int *nx, int *ny, int *nz);
 
 /* Copy a level's populations [n_levels][nz][ny][nx] out to, or in from, host
- * memory. */
+ * memory.  The populations are the whole state of a CRD handle, so a new
+ * handle given them resumes bit for bit.  The lagged fields of background
+ * scattering (sigma_c) and of partial redistribution (gamma_prd) are not
+ * part of them: a resumed handle restarts those from the state its creation
+ * left (the zero-radiation field), and its next iterates differ from the
+ * uninterrupted run until the fields have been recomputed. */
 int mg3d_get_populations(mg3d_handle *h, int level, double *n_host);
 int mg3d_set_populations(mg3d_handle *h, int level, const double *n_host);
 
