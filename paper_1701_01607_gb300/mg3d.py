@@ -219,7 +219,12 @@ def mg3d_create(atm, atom, quad_a: float = 0.0, n_grids: int = 1, nu_fmg: int = 
                 nu0: int = 0, nu1: int = 2, nu2: int = 2, nu3: int = 32,
                 fs_prec: int = MG3D_PREC_F64, restriction: int = MG3D_RESTRICT_FULL,
                 interpolation: int = MG3D_INTERP_LINEAR, sc_interp: int = MG3D_INTERP_LINEAR):
-    """mg3d_create from a synth.Atmosphere and TwoLevelAtom; returns the handle."""
+    """mg3d_create from a synth.Atmosphere and TwoLevelAtom; returns the handle.
+
+    Variants: ``restriction`` (MG3D_RESTRICT_*), ``interpolation`` and
+    ``sc_interp`` (MG3D_INTERP_LINEAR or _HERMITE), a velocity field in
+    ``atm.vel`` ([3, nz, ny, nx] in Doppler widths) and partial redistribution
+    through ``atom.gamma_prd``; the C header documents each."""
     lib = load()
     z = np.ascontiguousarray(atm.z, dtype=np.float64)
     T = np.ascontiguousarray(atm.T, dtype=np.float64)
@@ -245,7 +250,12 @@ def mg3d_create_ml(atm, atom, quad_a: float = 0.0, n_grids: int = 1, nu_fmg: int
                    fs_prec: int = MG3D_PREC_F64, restriction: int = MG3D_RESTRICT_FULL,
                    ml_chunk: int = 0, interpolation: int = MG3D_INTERP_LINEAR,
                    sc_interp: int = MG3D_INTERP_LINEAR):
-    """mg3d_create_ml from a synth.MultiLevelAtmosphere and MultiLevelAtom."""
+    """mg3d_create_ml from a synth.MultiLevelAtmosphere and MultiLevelAtom.
+
+    Variants: ``restriction``, ``interpolation``, ``sc_interp`` as for
+    mg3d_create, background scattering in ``atm.sigma_c`` and a velocity
+    field in ``atm.vel`` (Doppler widths at the atom's t_ref); ``ml_chunk``
+    sets the frequencies per chunk (0: automatic)."""
     lib = load()
     keep = {}
 
