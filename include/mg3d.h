@@ -102,6 +102,10 @@ typedef struct {
                          that grid; prolonged in FMG); MALI preconditions with
                          U = sum w phi (1 - w0 rho).  Static atmospheres, linear
                          upwind interpolation, no batches. */
+    double a_damp;    /* damping parameter of a Voigt line profile in Doppler
+                         widths; must be 0 (Doppler profile): Voigt profiles and
+                         the damped redistribution R_II-A are not built in the
+                         library, which refuses a_damp != 0 with MG3D_E_ARG */
 } mg3d_atom;
 
 /* Angle quadrature: the 24-direction A4 set of Carlson (Sec. 3): per octant

@@ -138,16 +138,28 @@ def a4_quadrature(a: float | None = None):
     return mu, w
 
 
-def frequency_grid(n_freq: int, x_max: float):
-    """Doppler-profile frequency grid: offsets x, profile phi(x), weights.
+def line_profile(x, a: float = 0.0):
+    """phi(x) per unit Doppler width: exp(-x^2)/sqrt(pi), or for damping
+    a > 0 the Voigt profile H(a, x)/sqrt(pi), H(a, x) = Re w(x + i a) with w
+    the Faddeeva function."""
+    x = np.asarray(x, dtype=np.float64)
+    if a > 0.0:
+        from scipy.special import wofz
+        return wofz(x + 1j * a).real / math.sqrt(math.pi)
+    return np.exp(-x * x) / math.sqrt(math.pi)
 
-    phi(x) = exp(-x^2)/sqrt(pi) per unit Doppler width; weights are the
-    trapezoid rule on equidistant x in [-x_max, x_max], scaled so that
-    sum_nu w phi = 1 exactly.  Returns (x, phi, wphi) with wphi = w * phi.
+
+def frequency_grid(n_freq: int, x_max: float, a_damp: float = 0.0):
+    """Frequency grid: offsets x, profile phi(x) (``line_profile``), weights.
+
+    The weights are the trapezoid rule on equidistant x in [-x_max, x_max],
+    scaled so that sum_nu w phi = 1 exactly (with damping this renormalises
+    the Lorentzian wings cut at x_max).  Returns (x, phi, wphi) with
+    wphi = w * phi.
     """
     if n_freq == 1:
         x = np.zeros(1)
-        phi = np.ones(1) / math.sqrt(math.pi)
+        phi = line_profile(x, a_damp)
         w = np.ones(1)
     else:
         x = np.linspace(-x_max, x_max, n_freq)
@@ -155,7 +167,7 @@ def frequency_grid(n_freq: int, x_max: float):
         w = np.full(n_freq, h)
         w[0] *= 0.5
         w[-1] *= 0.5
-        phi = np.exp(-x * x) / math.sqrt(math.pi)
+        phi = line_profile(x, a_damp)
     wphi = w * phi
     wphi = wphi / wphi.sum()
     return x, phi, wphi
@@ -231,7 +243,8 @@ class TwoLevelProblem:
         self.interpolation = interpolation
         self.sc_interp = sc_interp
         self.mu, self.wray = a4_quadrature(quad_a)
-        self.x, self.phi, self.wphi = frequency_grid(atom.n_freq, atom.x_max)
+        self.a_damp = float(getattr(atom, "a_damp", 0.0))
+        self.x, self.phi, self.wphi = frequency_grid(atom.n_freq, atom.x_max, self.a_damp)
         vel = getattr(atm, "vel", None)
         fine = Level(atm.nx, atm.ny, atm.nz, atm.dx, atm.dy, np.asarray(atm.z, float),
                      np.asarray(atm.T, float), np.asarray(atm.n_tot, float),
@@ -252,7 +265,7 @@ class TwoLevelProblem:
         nf = len(self.x)
         self.jnu = {k: np.zeros((nf, lev.nx * lev.ny * lev.nz)) for k, lev in self.levels.items()}
         self.wq = self.wphi / self.phi
-        self.R = prd_matrix(self.x, self.wq, self.phi) if self.prd else None
+        self.R = prd_matrix(self.x, self.wq, self.phi, self.a_damp) if self.prd else None
         self.top = n_grids
         self._force_bg = False
 
@@ -390,7 +403,7 @@ class TwoLevelProblem:
         z = np.ascontiguousarray(lev.z)
         for r in range(len(self.wray)):
             ur = self.mu[r] @ u                                   # [nvox]
-            prof = np.exp(-(self.x[:, None] - ur[None, :]) ** 2) / math.sqrt(math.pi)
+            prof = line_profile(self.x[:, None] - ur[None, :], self.a_damp)
             wphi = wq[:, None] * prof
             wphi = np.ascontiguousarray(wphi / wphi.sum(axis=0))
             chi = np.ascontiguousarray(chi0[None, :] * prof)
@@ -768,18 +781,48 @@ def prolong_hermite(ac, z_fine):
     return _hermite_refine_axis(a, -3, False, zf[::2], zf)
 
 
-def prd_matrix(x, wq, phi, iters: int = 200):
+def redistribution_r2a(x, xp, a: float):
+    """Hummer's angle-averaged R_II (upper level broadened, damping a > 0,
+    coherent in the atom's frame, isotropic scattering), written as the
+    average over the scattering angle g with weight sin(g)/2 of R_II(g):
+        R_II-A(x, x') = (1/2pi) int_0^pi exp(-[(x - x')/(2 sin(g/2))]^2)
+                        H(a / cos(g/2), (x + x')/(2 cos(g/2))) dg,
+    H(a, v) = Re w(v + i a).  Its marginal is the Voigt profile; for a -> 0 it
+    tends to erfc(max(|x|, |x'|))/2.  Unlike that limit it is not symmetric
+    under x -> -x: far-wing photons stay in their wing."""
+    from scipy.integrate import quad
+    from scipy.special import wofz
+
+    def f(g):
+        s, c = math.sin(0.5 * g), math.cos(0.5 * g)
+        if s <= 0.0 or c <= 0.0:
+            return 0.0
+        return (math.exp(-((x - xp) / (2.0 * s)) ** 2)
+                * wofz((x + xp) / (2.0 * c) + 1j * a / c).real)
+
+    return quad(f, 0.0, math.pi, epsabs=1e-15, epsrel=1e-13, limit=400)[0] / (2.0 * math.pi)
+
+
+def prd_matrix(x, wq, phi, a_damp: float = 0.0, iters: int = 200):
     """Discrete angle-averaged redistribution matrix R[f', f] on the frequency
     grid: Hummer's R_I-A(x', x) = erfc(max(|x|, |x'|))/2 (pure Doppler
-    redistribution; R_II-A for zero damping), whose marginals are the
-    Doppler profile, scaled symmetrically, R = diag(c) R0 diag(c), so that the
-    discrete marginals sum_f' wq_f' R[f', f] equal phi_f exactly (fixed-point
-    iteration c <- sqrt(c phi / (R0^T (wq c)))).  Then a frequency-flat J
-    gives rho = 1 and the emission profile keeps sum w phi rho = 1."""
+    redistribution; R_II-A for zero damping), or R_II-A with damping
+    (``redistribution_r2a``), whose marginals are the line profile, scaled
+    symmetrically, R = diag(c) R0 diag(c), so that the discrete marginals
+    sum_f' wq_f' R[f', f] equal phi_f exactly (fixed-point iteration
+    c <- sqrt(c phi / (R0^T (wq c)))).  Then a frequency-flat J gives rho = 1
+    and the emission profile keeps sum w phi rho = 1."""
     from scipy.special import erfc
     x = np.asarray(x, dtype=np.float64)
     ax = np.abs(x)
-    R0 = 0.5 * erfc(np.maximum(ax[:, None], ax[None, :]))
+    if a_damp > 0.0:
+        n = len(x)
+        R0 = np.empty((n, n))
+        for i in range(n):
+            for j in range(i, n):
+                R0[i, j] = R0[j, i] = redistribution_r2a(x[i], x[j], a_damp)
+    else:
+        R0 = 0.5 * erfc(np.maximum(ax[:, None], ax[None, :]))
     c = np.ones(len(x))
     for _ in range(iters):
         c = np.sqrt(c * phi / (R0.T @ (wq * c)))

@@ -2274,6 +2274,8 @@ int mg3d_create(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_qu
         return fail(MG3D_E_ARG, "moving atmospheres take the linear upwind interpolation");
     if (!(atom->gamma_prd >= 0.0 && atom->gamma_prd <= 1.0))
         return fail(MG3D_E_ARG, "gamma_prd must lie in [0, 1]");
+    if (atom->a_damp != 0.0)
+        return fail(MG3D_E_ARG, "damping (Voigt profiles) is not built: a_damp must be 0");
     if (atom->gamma_prd > 0.0 && (atm->vel || params->sc_interp))
         return fail(MG3D_E_ARG,
                     "partial redistribution takes a static atmosphere and linear interpolation");

@@ -47,7 +47,7 @@ class mg3d_atom(ctypes.Structure):
     _fields_ = [("a_ul", ctypes.c_double), ("g_ratio", ctypes.c_double),
                 ("theta", ctypes.c_double), ("kappa", ctypes.c_double),
                 ("n_freq", ctypes.c_int), ("x_max", ctypes.c_double),
-                ("gamma_prd", ctypes.c_double)]
+                ("gamma_prd", ctypes.c_double), ("a_damp", ctypes.c_double)]
 
 
 class mg3d_quadrature(ctypes.Structure):
@@ -235,7 +235,7 @@ def mg3d_create(atm, atom, quad_a: float = 0.0, n_grids: int = 1, nu_fmg: int = 
     a = mg3d_atmosphere(atm.nx, atm.ny, atm.nz, atm.dx, atm.dy, _dptr(z), _dptr(T),
                         _dptr(n_tot), _dptr(c_ul), _dptr(vel))
     at = mg3d_atom(atom.a_ul, atom.g_ratio, atom.theta, atom.kappa, atom.n_freq, atom.x_max,
-                   getattr(atom, "gamma_prd", 0.0))
+                   getattr(atom, "gamma_prd", 0.0), getattr(atom, "a_damp", 0.0))
     q = mg3d_quadrature(quad_a)
     p = mg3d_params(n_grids, nu_fmg, nu0, nu1, nu2, nu3, fs_prec, restriction, 0, interpolation,
                     sc_interp)
@@ -498,7 +498,7 @@ def mg3d_formal_solve_noalloc(nx: int, ny: int, nz: int, dx: float, dy: float, z
     callers can inspect limit errors.
     """
     at = mg3d_atom(atom.a_ul, atom.g_ratio, atom.theta, atom.kappa, atom.n_freq, atom.x_max,
-                   getattr(atom, "gamma_prd", 0.0))
+                   getattr(atom, "gamma_prd", 0.0), getattr(atom, "a_damp", 0.0))
     return load().mg3d_formal_solve_noalloc(nx, ny, nz, dx, dy, z_dev, ctypes.byref(at),
                                             quad_a, chi0_dev, S_dev, bbot_dev, jeff_dev,
                                             u_dev, stream_ptr)

@@ -59,6 +59,7 @@ class TwoLevelAtom:
     n_freq: int = 9
     x_max: float = 3.0
     gamma_prd: float = 0.0        # coherence fraction of partial redistribution (0: CRD)
+    a_damp: float = 0.0           # damping (Voigt) parameter in Doppler widths (0: Doppler)
 
 
 @dataclasses.dataclass

@@ -59,6 +59,11 @@ def test_create_rejects_bad_grids_before_touching_the_gpu(lib):
         m.mg3d_create(bad, atom, n_grids=1)
     assert ei.value.code == m.MG3D_E_ARG
     assert "z must increase" in m.mg3d_last_error()
+    # damping is known to the oracle only: the library refuses it
+    damped = synth.TwoLevelAtom(a_damp=0.05)
+    with pytest.raises(m.MG3DError) as ei:
+        m.mg3d_create(atm, damped, n_grids=1)
+    assert ei.value.code == m.MG3D_E_ARG and "damping" in m.mg3d_last_error()
 
 
 def test_null_handle_is_an_argument_error(lib):

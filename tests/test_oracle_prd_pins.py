@@ -94,3 +94,51 @@ def test_prd_conservation_multigrid_agreement_and_effect():
     atom.gamma_prd = 0.0
     n_crd, _ = O.mali_solve(O.TwoLevelProblem(atm, atom, n_grids=3), 1e-11)
     assert O.max_rel_error(n_crd, n_mali) > 1e-4
+
+
+# ------------------------------------------------------ damping (Voigt, R_II-A)
+
+def test_voigt_profile_matches_scipy():
+    x = np.linspace(-6, 6, 25)
+    for a in (0.01, 0.1, 1.0):
+        ref = special.voigt_profile(x, 1.0 / math.sqrt(2.0), a)
+        assert np.allclose(O.line_profile(x, a), ref, rtol=1e-12, atol=1e-15)
+    assert np.allclose(O.line_profile(x, 0.0), np.exp(-x * x) / math.sqrt(math.pi))
+
+
+def test_r2a_marginal_is_the_voigt_profile():
+    """int R_II-A(x, x') dx' = H(a, x)/sqrt(pi): the angle-averaged function
+    redistributes exactly the absorbed profile."""
+    for a, x in ((0.05, 1.0), (0.5, 2.5)):
+        m = sum(integrate.quad(lambda xp: O.redistribution_r2a(x, xp, a), lo, hi,
+                               epsabs=1e-11, limit=200)[0]
+                for lo, hi in ((-np.inf, -x), (-x, x), (x, np.inf)))
+        assert abs(m / O.line_profile(np.array([x]), a)[0] - 1.0) < 1e-9
+
+
+def test_r2a_limits_and_symmetries():
+    r = O.redistribution_r2a
+    assert abs(r(0.7, 1.3, 1e-6) - 0.5 * special.erfc(1.3)) < 1e-5
+    assert abs(r(0.7, 1.3, 0.1) - r(1.3, 0.7, 0.1)) < 1e-14
+    assert abs(r(-0.7, -1.3, 0.1) - r(0.7, 1.3, 0.1)) < 1e-14
+    # coherent in the atom's frame: far-wing photons stay in their wing
+    assert r(-3.5, 4.0, 0.05) < 1e-3 * r(3.5, 4.0, 0.05)
+
+
+def test_prd_with_damping_conserves_and_fas_matches_mali():
+    atom = synth.TwoLevelAtom(gamma_prd=1.0, a_damp=0.05, n_freq=13, x_max=5.0)
+    atm, atom = synth.stratified_two_level(4, 4, 9, eps=3e-2, sigma=0.3, seed=3, atom=atom)
+    p = O.TwoLevelProblem(atm, atom, n_grids=3)
+    assert np.allclose((p.R * p.wq[:, None]).sum(axis=0), p.phi, rtol=1e-13)
+    n = p.zero_radiation(3)
+    for _ in range(3):
+        n, _ = p.mali_sweep(3, n)
+        assert np.max(np.abs(n.sum(axis=0) / atm.n_tot - 1.0)) < 1e-13
+    p1 = O.TwoLevelProblem(atm, atom, n_grids=3)
+    n_mali = p1.zero_radiation(3)
+    for _ in range(400):
+        n_mali, C = p1.mali_sweep(3, n_mali)
+        if C < 1e-13:
+            break
+    n_fas, _ = O.fas_solve(O.TwoLevelProblem(atm, atom, n_grids=3), 1e-11, PARAMS)
+    assert O.max_rel_error(n_fas, n_mali) < 1e-8
