@@ -102,10 +102,15 @@ typedef struct {
                          that grid; prolonged in FMG); MALI preconditions with
                          U = sum w phi (1 - w0 rho).  Static atmospheres, linear
                          upwind interpolation, no batches. */
-    double a_damp;    /* damping parameter of a Voigt line profile in Doppler
-                         widths; must be 0 (Doppler profile): Voigt profiles and
-                         the damped redistribution R_II-A are not built in the
-                         library, which refuses a_damp != 0 with MG3D_E_ARG */
+    double a_damp;    /* damping parameter in Doppler widths, >= 0: the line
+                         profile is the Voigt profile H(a, x)/sqrt(pi) (0: the
+                         Doppler profile), and partial redistribution uses
+                         Hummer's angle-averaged R_II (the average over the
+                         scattering angle g, weight sin g/2, of exp(-[(x - x')/(2
+                         sin(g/2))]^2) H(a/cos(g/2), (x + x')/(2 cos(g/2)))/(pi
+                         sin g)); both are tabulated on the host by adaptive
+                         Gauss-Kronrod quadrature at creation.  Static
+                         atmospheres only (MG3D_E_ARG with a velocity field). */
 } mg3d_atom;
 
 /* Angle quadrature: the 24-direction A4 set of Carlson (Sec. 3): per octant
@@ -494,7 +499,8 @@ int mg3d_reset_counters(mg3d_handle *h);
  *   S_dev    [nz][ny][nx] line source function n_u / (n_l g_u/g_l - n_u);
  *   bbot_dev [ny][nx] intensity entering through the bottom plane;
  *   jeff_dev, u_dev [nz][ny][nx] outputs Jeff and U = 1 - Lambda*;
- *   atom gives n_freq and x_max; quad_a selects the A4 set as in
+ *   atom gives n_freq and x_max (Doppler profile, CRD: gamma_prd and a_damp
+ *   must be 0, else MG3D_E_ARG); quad_a selects the A4 set as in
  *   mg3d_quadrature; cuda_stream orders the work (NULL: the legacy default
  *   stream).  The call returns once the work is enqueued.
  * Limits: at most MG3D_NOALLOC_MAX_NODES nodes, MG3D_NOALLOC_MAX_NZ planes and

@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "mg3d.h"
+#include "profiles.h"
 #include "mg3d_internal.h"
 
 using namespace mg3d;
@@ -215,7 +216,8 @@ void build_frequencies(mg3d_handle *h) {
         double x = nf == 1 ? 0.0 : h->atom.x_max * (2 * i - (nf - 1)) / (nf - 1);
         double w = nf == 1 ? 1.0 : 2.0 * h->atom.x_max / (nf - 1);
         if (nf > 1 && (i == 0 || i == nf - 1)) w *= 0.5;
-        h->phi[i] = std::exp(-x * x) / std::sqrt(M_PI);
+        // Doppler, or Voigt with damping (even in x: mirror offsets stay equal)
+        h->phi[i] = voigt_H(h->atom.a_damp, x) / std::sqrt(M_PI);
         h->wphi[i] = w * h->phi[i];
         sum += h->wphi[i];
     }
@@ -1170,8 +1172,9 @@ int setup_prd(mg3d_handle *h) {
     }
     std::vector<double> R0((size_t)nf * nf), c(nf, 1.0), t(nf);
     for (int a = 0; a < nf; ++a)
-        for (int b = 0; b < nf; ++b)
-            R0[(size_t)a * nf + b] = 0.5 * std::erfc(std::max(std::fabs(x[a]), std::fabs(x[b])));
+        for (int b = a; b < nf; ++b)   // R_I-A, or R_II-A with damping; symmetric
+            R0[(size_t)a * nf + b] = R0[(size_t)b * nf + a] =
+                redistribution_r2a(x[a], x[b], h->atom.a_damp);
     for (int it = 0; it < 200; ++it) {
         for (int b = 0; b < nf; ++b) {
             double s = 0.0;
@@ -2274,8 +2277,10 @@ int mg3d_create(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_qu
         return fail(MG3D_E_ARG, "moving atmospheres take the linear upwind interpolation");
     if (!(atom->gamma_prd >= 0.0 && atom->gamma_prd <= 1.0))
         return fail(MG3D_E_ARG, "gamma_prd must lie in [0, 1]");
-    if (atom->a_damp != 0.0)
-        return fail(MG3D_E_ARG, "damping (Voigt profiles) is not built: a_damp must be 0");
+    if (!(atom->a_damp >= 0.0 && atom->a_damp < 1e3))
+        return fail(MG3D_E_ARG, "a_damp must lie in [0, 1000)");
+    if (atom->a_damp > 0.0 && atm->vel)
+        return fail(MG3D_E_ARG, "moving atmospheres take Doppler profiles (a_damp 0)");
     if (atom->gamma_prd > 0.0 && (atm->vel || params->sc_interp))
         return fail(MG3D_E_ARG,
                     "partial redistribution takes a static atmosphere and linear interpolation");

@@ -177,6 +177,11 @@ extern "C" int mg3d_formal_solve_noalloc(int nx, int ny, int nz, double dx, doub
                      " planes");
         return MG3D_E_ARG;
     }
+    if (atom->gamma_prd != 0.0 || atom->a_damp != 0.0) {
+        record_error("the allocation-free call takes Doppler profiles and complete "
+                     "redistribution (gamma_prd and a_damp 0)");
+        return MG3D_E_ARG;
+    }
     const int nf = atom->n_freq;
     if (nf < 1 || nf > kMaxFreq || !(atom->x_max >= 0.0)) {
         record_error("n_freq must be 1.." + std::to_string(kMaxFreq) + " on the allocation-free path");

@@ -59,11 +59,23 @@ def test_create_rejects_bad_grids_before_touching_the_gpu(lib):
         m.mg3d_create(bad, atom, n_grids=1)
     assert ei.value.code == m.MG3D_E_ARG
     assert "z must increase" in m.mg3d_last_error()
-    # damping is known to the oracle only: the library refuses it
-    damped = synth.TwoLevelAtom(a_damp=0.05)
+    # damping: non-negative, and not with a velocity field
     with pytest.raises(m.MG3DError) as ei:
-        m.mg3d_create(atm, damped, n_grids=1)
-    assert ei.value.code == m.MG3D_E_ARG and "damping" in m.mg3d_last_error()
+        m.mg3d_create(atm, synth.TwoLevelAtom(a_damp=-0.1), n_grids=1)
+    assert ei.value.code == m.MG3D_E_ARG and "a_damp" in m.mg3d_last_error()
+    vatm, _ = synth.stratified_two_level(16, 16, 33, eps=1e-3, velocity=1.0)
+    with pytest.raises(m.MG3DError) as ei:
+        m.mg3d_create(vatm, synth.TwoLevelAtom(a_damp=0.05), n_grids=1)
+    assert ei.value.code == m.MG3D_E_ARG and "Doppler" in m.mg3d_last_error()
+
+
+def test_allocation_free_call_refuses_prd_and_damping(lib):
+    """Checked before any CUDA call: the dummy addresses are never touched."""
+    for atom in (synth.TwoLevelAtom(gamma_prd=0.5), synth.TwoLevelAtom(a_damp=0.1)):
+        rc = m.mg3d_formal_solve_noalloc(4, 4, 5, 1.0, 1.0, 256, atom, 0.0, 256, 256, 256,
+                                         256, 256)
+        assert rc == m.MG3D_E_ARG
+        assert "Doppler" in m.mg3d_last_error()
 
 
 def test_null_handle_is_an_argument_error(lib):

@@ -120,3 +120,37 @@ def test_prd_refusals():
     vatm, _ = synth.stratified_two_level(8, 8, 17, eps=1e-3, atom=atom, velocity=1.0)
     with pytest.raises(m.MG3DError, match="static atmosphere"):
         m.mg3d_create(vatm, atom, n_grids=1, **PARAMS)
+
+
+# ------------------------------------------------------------ damping (Voigt)
+
+def test_damped_crd_formal_solution_and_prd_sweeps_fp64():
+    """Voigt profiles (a = 0.05) and, with full coherence, R_II-A: the formal
+    solution after the zero-radiation start (CRD) and three MALI sweeps with
+    partial redistribution against the oracle."""
+    atom = synth.TwoLevelAtom(n_freq=13, x_max=5.0, a_damp=0.05)
+    atm, atom = synth.stratified_two_level(16, 16, 33, eps=1e-3, sigma=0.3, seed=5, atom=atom)
+    h = m.mg3d_create(atm, atom, n_grids=1, **PARAMS)
+    try:
+        jeff, u = m.mg3d_formal_solve(h, 1)
+    finally:
+        m.mg3d_destroy(h)
+    p = O.TwoLevelProblem(atm, atom)
+    _, jo, uo = p.formal_solution(1, p.zero_radiation(1))
+    assert rel(jeff, jo) < 1e-12 and rel(u, uo) < 1e-12
+
+    atom.gamma_prd = 1.0
+    p = O.TwoLevelProblem(atm, atom, n_grids=2)
+    n = p.zero_radiation(2)
+    h = m.mg3d_create(atm, atom, n_grids=2, **PARAMS)
+    try:
+        for _ in range(3):
+            m.mg3d_mali_sweep(h, 2, 1)
+            n, _ = p.mali_sweep(2, n)
+        assert rel(m.mg3d_get_populations(h, 2), n) < TOL_POP64
+        c_gpu = m.mg3d_fas_vcycle(h, False)
+        n, c_orc = p.fas_cycle(n, False, PARAMS)
+        assert abs(c_gpu - c_orc) <= 1e-8 * c_orc
+        assert rel(m.mg3d_get_populations(h, 2), n) < TOL_POP64
+    finally:
+        m.mg3d_destroy(h)
