@@ -270,12 +270,13 @@ __device__ __forceinline__ void moving_step(
 // the opacity is the static chi0 phi_f, so mirror frequencies share their
 // step weights, but the source function rho_f S depends on the frequency.
 // Its upwind value is interpolated per frequency from global memory; U takes
-// w phi (1 - w0 rho_f); every new intensity is added, with the ray weight,
-// into the new mean intensity of its frequency (atomically: the rays of a
-// node run in different clusters).
+// w phi (1 - w0 rho_f); every new intensity, with the ray weight, is stored
+// in the ray's slot of the new mean intensity (each (ray, frequency, node)
+// has one writer; the slots are added in ray order afterwards, so the sum
+// does not depend on scheduling).
 template <typename T>
 __device__ __forceinline__ void prd_step(
-    const SweepArgs<T> &a, int rank, unsigned long long rmagic, cg::cluster_group &cluster,
+    const SweepArgs<T> &a, int r, int rank, unsigned long long rmagic, cg::cluster_group &cluster,
     const T *prev, T *cur, T *__restrict__ pj, T *__restrict__ pu, int k, int kp,
     const StepGeom &o, T half_s, int f0, int nf, const T *phi, const T *inv_phi, const T *wphi,
     const ExpNegTable &et) {
@@ -326,7 +327,7 @@ __device__ __forceinline__ void prd_step(
             cur[off + (long)yl * nx + x] = I;
             cj += wphi[f] * part;
             cu += wphi[f] * (T(1) - w0 * rho_loc);
-            atomicAdd(a.jnu + fo + v, wr * I);
+            a.jnu[(long)r * a.nfreq * nvox + fo + v] = wr * I;
         }
         pj[v] = cj;
         pu[v] = cu;
@@ -454,8 +455,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
                     cur[((long)f * rows + yl) * nx + x] = Ib;
                     cj += wphi[f] * Ib;
                     cu += wphi[f];
-                    if (Ib != T(0))
-                        atomicAdd(a.jnu + (long)a.fidx[f0 + f] * nvox + v, Ib * T(1.0 / kRays));
+                    a.jnu[((long)r * a.nfreq + a.fidx[f0 + f]) * nvox + v] = Ib * T(1.0 / kRays);
                 }
                 pj[v] = cj;
                 pu[v] = cu;
@@ -503,7 +503,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
                             cur, dbuf + (t & 1) * bufstride, pj, pu, k, kp, o, half_s, f0, nf,
                             et);
             } else if constexpr (PRD) {
-                prd_step(a, rank, rmagic, cluster, prev, cur, pj, pu, k, kp, o, half_s, f0, nf,
+                prd_step(a, r, rank, rmagic, cluster, prev, cur, pj, pu, k, kp, o, half_s, f0, nf,
                          phi, inv_phi, wphi, et);
             } else
             for (int q = threadIdx.x; q < band; q += blockDim.x) {
@@ -961,6 +961,29 @@ cudaError_t launch_prd_source(int prec, long nvox, int nfreq, double gamma, doub
         prd_source_kernel<float><<<grid_for(nvox, th), th, 0, st>>>(
             nvox, nfreq, gamma, g_ratio, a_ul, kmat, wphi, n, c_lu, (const float *)jnu,
             (float *)rho, (float *)rhoS);
+    return cudaGetLastError();
+}
+
+// jnu[f][v] = sum over rays r, in order, of slots[r][f][v].
+template <typename T>
+__global__ void prd_collect_kernel(long len, const T *__restrict__ slots, T *__restrict__ jnu) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < len;
+         i += (long)gridDim.x * blockDim.x) {
+        T s = slots[i];
+        for (int r = 1; r < kRays; ++r) s += slots[(long)r * len + i];
+        jnu[i] = s;
+    }
+}
+
+cudaError_t launch_prd_collect(int prec, long len, const void *slots, void *jnu,
+                               cudaStream_t st) {
+    const int th = 256;
+    if (prec == 0)
+        prd_collect_kernel<double><<<grid_for(len, th), th, 0, st>>>(len, (const double *)slots,
+                                                                     (double *)jnu);
+    else
+        prd_collect_kernel<float><<<grid_for(len, th), th, 0, st>>>(len, (const float *)slots,
+                                                                    (float *)jnu);
     return cudaGetLastError();
 }
 

@@ -76,8 +76,9 @@ struct Level {
     void *uproj = nullptr, *vnorm = nullptr;  // [kRays][nvox] projected velocity, 1/sum w phi
                                               // (multi-level: vnorm [nlines][kRays][nvox])
     void *dinv = nullptr;        // multi-level, moving: 1/d per node [nvox]
-    // partial redistribution (two-level): the lagged and the new mean
-    // intensity per frequency, rho and rho S [nf][nvox] (natural order)
+    // partial redistribution (two-level): the lagged mean intensity, rho and
+    // rho S [nf][nvox] (natural order); per-ray slots of the new mean
+    // intensity [kRays][nf][nvox]
     void *jnu = nullptr, *jnu_new = nullptr, *rho = nullptr, *rhoS = nullptr;
     StepGeom *geom = nullptr;    // [kRays][nz]
     SweepShape shape{};
@@ -553,15 +554,13 @@ MlRateArgs ml_rate_args(mg3d_handle *h, int k, int mode) {
 }
 
 // Partial redistribution before a sweep of level k: rho and rho S from the
-// lagged field, and the new mean intensity cleared for the sweep to add into.
+// lagged field (the sweep writes every slot of the new mean intensity).
 int prd_prepare(mg3d_handle *h, int k) {
     Level &L = h->lev[k];
     MG_TRY(launched(h, launch_prd_source(h->prec, L.nvox, h->atom.n_freq, h->atom.gamma_prd,
                                          h->atom.g_ratio, h->atom.a_ul, h->d_kmat, h->d_wphin,
                                          L.n, L.c_lu, L.jnu, L.rho, L.rhoS, h->stream),
                     "partial redistribution"));
-    MG_CUDA(cudaMemsetAsync(L.jnu_new, 0, (size_t)h->atom.n_freq * L.nvox * elem_size(h->prec),
-                            h->stream));
     return MG3D_OK;
 }
 
@@ -595,9 +594,9 @@ int formal_solution(mg3d_handle *h, int k) {
         h->timed.push_back(tl);
     }
     if (h->prd && updates_background(h, k))   // the new mean intensity becomes the field
-        MG_CUDA(cudaMemcpyAsync(L.jnu, L.jnu_new,
-                                (size_t)h->atom.n_freq * L.nvox * elem_size(h->prec),
-                                cudaMemcpyDeviceToDevice, h->stream));
+        MG_TRY(launched(h, launch_prd_collect(h->prec, (long)h->atom.n_freq * L.nvox, L.jnu_new,
+                                              L.jnu, h->stream),
+                        "mean intensity"));
     ++h->fs_launches;
     h->fs_units += (double)L.nvox * kRays * h->atom.n_freq;
     ++h->level_launches[k];
@@ -1261,8 +1260,9 @@ int create_impl(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_qu
         L.shape = choose_shape(h->prec, L.nx, L.ny, atom->n_freq, params->sc_interp,
                                atm->vel ? 1 : 0, atom->gamma_prd > 0.0 ? 1 : 0);
         if (atom->gamma_prd > 0.0) {
-            void **bufs[4] = {&L.jnu, &L.jnu_new, &L.rho, &L.rhoS};
+            void **bufs[3] = {&L.jnu, &L.rho, &L.rhoS};
             for (void **p : bufs) MG_TRY(dev_alloc(p, (size_t)atom->n_freq * L.nvox * es));
+            MG_TRY(dev_alloc(&L.jnu_new, (size_t)kRays * atom->n_freq * L.nvox * es));
             MG_CUDA(cudaMemset(L.jnu, 0, (size_t)atom->n_freq * L.nvox * es));
         }
         if (params->sc_interp) {

@@ -67,8 +67,8 @@ struct SweepArgs {
     const T *uproj, *vnorm, *xf, *wq;
     // partial redistribution only: rho S and rho per frequency in natural
     // order [nfreq][nvox], the natural index of each table position
-    // [nfreq], and the new mean intensity per frequency [nfreq][nvox] the
-    // sweep adds into (zeroed before)
+    // [nfreq], and the per-ray slots of the new mean intensity
+    // [kRays][nfreq][nvox] (w_r I; every element written by the sweep)
     const T *rhoS, *rho;
     const int *fidx;
     T *jnu;
@@ -94,6 +94,9 @@ cudaError_t launch_prd_source(int prec, long nvox, int nfreq, double gamma, doub
                               double a_ul, const double *kmat, const double *wphi,
                               const double *n, const double *c_lu, const void *jnu, void *rho,
                               void *rhoS, cudaStream_t st);
+// jnu [len] = the sum of slots [kRays][len] over rays, in ray order.
+cudaError_t launch_prd_collect(int prec, long len, const void *slots, void *jnu,
+                               cudaStream_t st);
 // Monotone x-slopes (one cell units, periodic rows of nx) of a and b.
 cudaError_t launch_xslopes(int prec, int nx, long nvox, const void *a, const void *b, void *da,
                            void *db, cudaStream_t st);
