@@ -154,3 +154,19 @@ def test_damped_crd_formal_solution_and_prd_sweeps_fp64():
         assert rel(m.mg3d_get_populations(h, 2), n) < TOL_POP64
     finally:
         m.mg3d_destroy(h)
+
+
+def test_prd_is_bit_reproducible():
+    """The new mean intensity is stored per ray and summed in ray order, so
+    two runs of the same problem agree bit for bit."""
+    atm, atom = prd_box(gamma=1.0)
+    out = []
+    for _ in range(2):
+        h = m.mg3d_create(atm, atom, n_grids=2, **PARAMS)
+        try:
+            m.mg3d_mali_sweep(h, 2, 3)
+            m.mg3d_fas_vcycle(h, False)
+            out.append(m.mg3d_get_populations(h, 2))
+        finally:
+            m.mg3d_destroy(h)
+    assert np.array_equal(out[0], out[1])
