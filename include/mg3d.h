@@ -469,6 +469,15 @@ int mg3d_autotune(mg3d_handle *h, int level, int *evaluated, double *seconds);
  * memory; out_host holds 2n doubles. */
 int mg3d_check_exp(int n, const double *x_host, double *out_host);
 
+/* Check of the host-built line tables of a damped two-level atom (no GPU):
+ * for each i, out_host[2i] = the Voigt function H(a, x_host[i]) (profile
+ * times sqrt(pi)) and out_host[2i+1] = the angle-averaged redistribution
+ * R_II-A(x_host[i], xp_host[i]) (R_I-A for a = 0), as the frequency table and
+ * the partial-redistribution matrix use them.  a >= 0; out_host holds 2n
+ * doubles. */
+int mg3d_check_profiles(int n, double a, const double *x_host, const double *xp_host,
+                        double *out_host);
+
 /* Replay V-cycles from CUDA graphs (default on).  The first V-cycle of each
  * kind (first cycle / later cycles) is captured on the handle's stream and
  * later ones replay the graph; graphs are rebuilt after a change of stream or

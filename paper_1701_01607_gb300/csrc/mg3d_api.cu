@@ -2987,6 +2987,17 @@ int mg3d_get_fs_config(const mg3d_handle *h, int level, int *freq_per_block, int
     return MG3D_OK;
 }
 
+int mg3d_check_profiles(int n, double a, const double *x_host, const double *xp_host,
+                        double *out_host) {
+    if (n < 1 || !x_host || !xp_host || !out_host || !(a >= 0.0 && a < 1e3))
+        return fail(MG3D_E_ARG, "bad arguments");
+    for (int i = 0; i < n; ++i) {
+        out_host[2 * i] = voigt_H(a, x_host[i]);
+        out_host[2 * i + 1] = redistribution_r2a(x_host[i], xp_host[i], a);
+    }
+    return MG3D_OK;
+}
+
 int mg3d_check_exp(int n, const double *x_host, double *out_host) {
     if (n < 1 || !x_host || !out_host) return fail(MG3D_E_ARG, "bad arguments");
     double tab[kExpTab], l1, l2;

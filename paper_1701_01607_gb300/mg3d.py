@@ -152,6 +152,7 @@ _SIGNATURES = {
                                    ctypes.POINTER(ctypes.c_longlong)]),
     "mg3d_autotune": (_I, [_H, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),
     "mg3d_check_exp": (_I, [_I, _D, _D]),
+    "mg3d_check_profiles": (_I, [_I, ctypes.c_double, _D, _D, _D]),
     "mg3d_set_graphs": (_I, [_H, _I]),
     "mg3d_set_timing": (_I, [_H, _I]),
     "mg3d_get_counters": (_I, [_H, ctypes.POINTER(mg3d_counters)]),
@@ -460,6 +461,15 @@ def mg3d_check_exp(x):
     x = np.ascontiguousarray(x, dtype=np.float64)
     out = np.empty(2 * x.size)
     _check(load().mg3d_check_exp(x.size, _dptr(x), _dptr(out)))
+    return out[0::2], out[1::2]
+
+
+def mg3d_check_profiles(a: float, x, xp):
+    """(H(a, x), R_II-A(x, xp)) as the library's host tables compute them."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    xp = np.ascontiguousarray(np.broadcast_to(xp, x.shape), dtype=np.float64)
+    out = np.empty(2 * x.size)
+    _check(load().mg3d_check_profiles(x.size, float(a), _dptr(x), _dptr(xp), _dptr(out)))
     return out[0::2], out[1::2]
 
 

@@ -78,6 +78,24 @@ def test_allocation_free_call_refuses_prd_and_damping(lib):
         assert "Doppler" in m.mg3d_last_error()
 
 
+def test_host_line_tables_match_scipy_and_the_oracle(lib):
+    """The Voigt function and R_II-A the library tabulates for damped atoms
+    (host code, no GPU) against scipy's Faddeeva function and the oracle's
+    angle-averaged redistribution."""
+    special = pytest.importorskip("scipy.special")
+    from oracle import mg3d_oracle as O
+    x = np.array([0.0, 0.3, 1.0, 2.5, 5.0, 8.0, -1.7])
+    xp = np.array([0.0, 1.3, -0.7, 4.0, -5.0, 2.0, 1.1])
+    for a in (0.01, 0.05, 0.5):
+        H, R = m.mg3d_check_profiles(a, x, xp)
+        assert np.allclose(H, special.wofz(x + 1j * a).real, rtol=1e-12, atol=0)
+        ref = np.array([O.redistribution_r2a(u, v, a) for u, v in zip(x, xp)])
+        assert np.allclose(R, ref, rtol=1e-8, atol=1e-15)
+    H0, R0 = m.mg3d_check_profiles(0.0, x, xp)
+    assert np.allclose(H0, np.exp(-x * x), rtol=1e-15)
+    assert np.allclose(R0, 0.5 * special.erfc(np.maximum(np.abs(x), np.abs(xp))), rtol=1e-15)
+
+
 def test_null_handle_is_an_argument_error(lib):
     assert lib.mg3d_destroy(None) == m.MG3D_OK
     assert lib.mg3d_fas_vcycle(None, 0, None) == m.MG3D_E_ARG
