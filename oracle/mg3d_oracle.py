@@ -1294,7 +1294,10 @@ class MultiLevelProblem(TwoLevelProblem):
         nvox = lev.nx * lev.ny * lev.nz
         nf = len(self.freqs)
         n_any = np.ones((self.N,) + lev.shape)   # weights do not depend on n
-        terms, _ = self.transition_terms(k, n_any)
+        # only the rate weights are read; chi, S, sl and fl of these stand-in
+        # populations go unused (and divide by zero where g_u = g_l)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            terms, _ = self.transition_terms(k, n_any)
         M = self.rate_matrix_from(k, np.zeros((nf, nvox)), np.ones((nf, nvox)), terms)
         n = self.solve(M, self.default_rhs(k))
         if self.scatter:

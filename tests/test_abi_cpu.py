@@ -16,7 +16,8 @@ HEADER = os.path.join(B.ROOT, "include", "mg3d.h")
 
 
 def declared_functions():
-    text = open(HEADER).read()
+    with open(HEADER) as fh:
+        text = fh.read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(mg3d_[a-z_0-9]+)\s*\(", text)))
 
