@@ -294,6 +294,9 @@ typedef struct {
     double kappa;       /* opacity coefficient at unit profile */
     int n_freq;
     double x_max;
+    double a_damp;      /* Voigt damping parameter at t_ref; must be 0 (Doppler
+                           profiles): damped lines of multi-level atoms are
+                           refused with MG3D_E_ARG */
 } mg3d_line;
 
 typedef struct {

@@ -44,6 +44,9 @@ What each function follows in the paper (Bjorgen & Leenaarts 2017):
 * ``prd_matrix`` / ``formal_solution_prd`` -- partial redistribution for the
   two-level atom (the next step of Sec. 6): angle-averaged Doppler
   redistribution mixed with CRD, S_f = rho_f S from the lagged field.
+* ``line_profile`` / ``ml_line_profile`` -- Doppler or, with damping, Voigt
+  profiles (the paper's atoms have damped lines); a multi-level line's
+  damping parameter scales as 1/d with the node's Doppler width d.
 
 Readings where the paper is silent (the same readings hold on the GPU path):
 full weighting at the fixed z boundaries injects in z; n_before of Eq. 10 is
@@ -147,6 +150,20 @@ def line_profile(x, a: float = 0.0):
         from scipy.special import wofz
         return wofz(x + 1j * a).real / math.sqrt(math.pi)
     return np.exp(-x * x) / math.sqrt(math.pi)
+
+
+def ml_line_profile(x, d, a: float = 0.0):
+    """A multi-level line's profile per unit reference Doppler width at
+    offset x (reference widths) at a node whose Doppler width is d reference
+    widths: phi(x/d; a/d)/d with phi = ``line_profile``.  The damping width
+    does not scale with temperature, so the node's damping parameter is a/d
+    (a given at t_ref)."""
+    x = np.asarray(x, dtype=np.float64)
+    d = np.asarray(d, dtype=np.float64)
+    if a > 0.0:
+        from scipy.special import wofz
+        return wofz(x / d + 1j * (a / d)).real / (math.sqrt(math.pi) * d)
+    return np.exp(-(x / d) ** 2) / (math.sqrt(math.pi) * d)
 
 
 def frequency_grid(n_freq: int, x_max: float, a_damp: float = 0.0):
@@ -988,7 +1005,9 @@ class MultiLevelProblem(TwoLevelProblem):
         chi = chi_t + chi_c,     S = (eta_t + chi_c B_nu)/chi,
         sl = eta_t / chi,        fl = chi_t / chi.
     Lines: a = kappa (g_u/g_l) phi, b = kappa phi, e = kappa rho^3 phi with the
-    Doppler profile phi(x) = exp(-(x/d)^2)/(sqrt(pi) d), d = sqrt(T/t_ref).
+    Doppler profile phi(x) = exp(-(x/d)^2)/(sqrt(pi) d), d = sqrt(T/t_ref),
+    or for a line with damping a (at t_ref) the Voigt profile
+    H(a/d, x/d)/(sqrt(pi) d) (``ml_line_profile``).
     Bound-free (l -> continuum u): a = kappa y^-3, b = kappa y^-3 G E,
     e = kappa y^-3 G E (rho y)^3 with y = nu/nu_threshold, G = n_l*/n_u* and
     E = exp(-theta_ref rho y / T).  B_nu = (rho y)^3 / (exp(theta_ref rho y/T) - 1)
@@ -1079,13 +1098,13 @@ class MultiLevelProblem(TwoLevelProblem):
         norm = {}
         for (kind, ti, xv, wv) in self.freqs:
             if kind == "line":
-                phi = np.exp(-(xv / d) ** 2) / (math.sqrt(math.pi) * d)
+                phi = ml_line_profile(xv, d, at.lines[ti].a_damp)
                 norm[ti] = norm.get(ti, 0.0) + wv * phi
         for f, (kind, ti, xv, wv) in enumerate(self.freqs):
             if kind == "line":
                 ln = at.lines[ti]
                 lo, up = ln.lower, ln.upper
-                phi = np.exp(-(xv / d) ** 2) / (math.sqrt(math.pi) * d)
+                phi = ml_line_profile(xv, d, ln.a_damp)
                 gr = at.g[up] / at.g[lo]
                 a = ln.kappa * gr * phi
                 b = ln.kappa * phi
@@ -1222,8 +1241,7 @@ class MultiLevelProblem(TwoLevelProblem):
                 lo, up = ln.lower, ln.upper
                 gr = at.g[up] / at.g[lo]
                 B = self.planck_rho(ln.rho, T)
-                phis = [np.exp(-((self.freqs[f][2] - ur) / d) ** 2) / (math.sqrt(math.pi) * d)
-                        for f in fs]
+                phis = [ml_line_profile(self.freqs[f][2] - ur, d, ln.a_damp) for f in fs]
                 norm = sum(self.freqs[f][3] * ph for f, ph in zip(fs, phis))
                 for f, ph in zip(fs, phis):
                     chi_t = ln.kappa * ph * (nn[lo] * gr - nn[up])

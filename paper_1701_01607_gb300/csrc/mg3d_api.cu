@@ -2334,6 +2334,9 @@ int mg3d_create_ml(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
         if (ln.lower < 0 || ln.upper >= N || ln.lower >= ln.upper || ln.n_freq < 1 ||
             !(ln.rho > 0) || !(ln.a_ul > 0) || !(ln.kappa >= 0) || !(ln.x_max >= 0))
             return fail(MG3D_E_ARG, "bad line " + std::to_string(t));
+        if (ln.a_damp != 0.0)
+            return fail(MG3D_E_ARG, "line " + std::to_string(t) +
+                                        ": multi-level atoms take Doppler profiles (a_damp 0)");
         nf += ln.n_freq;
     }
     for (int t = 0; t < atom->n_continua; ++t) {

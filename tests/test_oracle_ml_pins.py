@@ -6,12 +6,15 @@
 * with the radiation field set to the Planck function (and no local
   operator) the radiative rates alone must be in detailed balance with the
   Saha-Boltzmann populations, transition by transition;
-* particle conservation, the FAS fixed point, and MALI/FAS/FMG agreement.
+* particle conservation, the FAS fixed point, and MALI/FAS/FMG agreement;
+* damped (Voigt) lines: the profile's closed forms, one damped line at
+  T = t_ref equal to the damped two-level oracle, conservation and FAS.
 """
 
 import math
 
 import numpy as np
+import pytest
 
 from oracle import mg3d_oracle as O
 from paper_1701_01607_gb300 import synth
@@ -192,3 +195,85 @@ def test_background_scattering_conservation_and_fas():
     for _ in range(40):
         n1, _ = p1.mali_sweep(1, n1)
     assert O.max_rel_error(n, n1) < 1e-9 and O.max_rel_error(n_fmg, n1) < 1e-9
+
+
+# ------------------------------------------------------------ damped lines
+
+def test_ml_line_profile_closed_forms():
+    """phi(x; d, a) = H(a/d, x/d)/(sqrt(pi) d): the two-level profile at
+    d = 1, the Doppler profile at a = 0, unit area at any d, and the line
+    centre value exp(a'^2) erfc(a')/(sqrt(pi) d) with a' = a/d."""
+    integrate = pytest.importorskip("scipy.integrate")
+    x = np.linspace(-5.0, 5.0, 21)
+    assert np.array_equal(O.ml_line_profile(x, 1.0, 0.05), O.line_profile(x, 0.05))
+    for d in (0.7, 1.3):
+        assert np.allclose(O.ml_line_profile(x, d, 0.0),
+                           np.exp(-(x / d) ** 2) / (math.sqrt(math.pi) * d), rtol=1e-15)
+        for a in (0.02, 0.4):
+            ap = a / d
+            ref = math.exp(ap * ap) * math.erfc(ap) / (math.sqrt(math.pi) * d)
+            assert abs(O.ml_line_profile(0.0, d, a) / ref - 1.0) < 1e-13
+            area = 2.0 * sum(integrate.quad(lambda v: float(O.ml_line_profile(v, d, a)), lo, hi,
+                                            limit=400, epsabs=1e-13)[0]
+                             for lo, hi in ((0.0, 6.0 * d), (6.0 * d, np.inf)))
+            assert abs(area - 1.0) < 1e-9
+
+
+def test_ml_damped_reduces_to_two_level_damped():
+    """One damped line at T = t_ref (d = 1), no continuum, no background:
+    the two-level oracle with the same Voigt profile."""
+    a = 0.05
+    atom2 = synth.TwoLevelAtom(a_damp=a, n_freq=13, x_max=5.0)
+    atm2, atom2 = synth.stratified_two_level(8, 8, 17, eps=1e-2, sigma=0.3, seed=4, atom=atom2)
+    assert np.all(atm2.T == 5000.0)
+    line = synth.Line(0, 1, 1.0, atom2.a_ul, atom2.kappa, atom2.n_freq, atom2.x_max, a)
+    ml_atom = synth.MultiLevelAtom(g=np.array([1.0, 1.0]), theta=np.array([0.0, atom2.theta]),
+                                   theta_ref=atom2.theta, lines=[line], continua=[],
+                                   t_ref=5000.0)
+    c = np.zeros((2, 2) + atm2.shape)
+    c[1, 0] = atm2.c_ul
+    c[0, 1] = atm2.c_ul * np.exp(-atom2.theta / atm2.T)
+    ml_atm = synth.MultiLevelAtmosphere(atm2.nx, atm2.ny, atm2.nz, atm2.dx, atm2.dy, atm2.z,
+                                        atm2.T, atm2.n_tot, np.zeros(atm2.shape), c,
+                                        np.zeros((2,) + atm2.shape))
+    p2 = O.TwoLevelProblem(atm2, atom2)
+    pm = O.MultiLevelProblem(ml_atm, ml_atom)
+    n2 = p2.zero_radiation(1)
+    nm = pm.zero_radiation(1)
+    for _ in range(4):
+        n2, c2 = p2.mali_sweep(1, n2)
+        nm, cm = pm.mali_sweep(1, nm)
+    assert np.allclose(nm, n2, rtol=1e-12)
+    assert abs(cm - c2) < 1e-10
+    # and the damping matters
+    line.a_damp = 0.0
+    pd = O.MultiLevelProblem(ml_atm, ml_atom)
+    nd = pd.zero_radiation(1)
+    for _ in range(4):
+        nd, _ = pd.mali_sweep(1, nd)
+    assert O.max_rel_error(nd, nm) > 1e-4
+
+
+def test_ml_damped_conservation_multigrid_and_flow():
+    atom = synth.hydrogen_like_atom(line_freq=9, cont_freq=4, seed=2, a_damp=0.03)
+    atm = synth.chromosphere(8, 8, 17, atom, seed=2)
+    p = O.MultiLevelProblem(atm, atom, n_grids=2)
+    n = p.zero_radiation(2)
+    for _ in range(3):
+        n, _ = p.mali_sweep(2, n)
+        assert np.allclose(n.sum(axis=0), atm.n_tot, rtol=1e-13)
+        assert np.all(n > 0)
+    params = dict(nu_fmg=8, nu0=10, nu1=2, nu2=4, nu3=16)
+    n_mali, _ = O.mali_solve(O.MultiLevelProblem(atm, atom, n_grids=2), 1e-11)
+    n_fas, _ = O.fas_solve(O.MultiLevelProblem(atm, atom, n_grids=2), 1e-10, params)
+    assert O.max_rel_error(n_fas, n_mali) < 1e-8
+    # zero flow takes the static damped path, frequency by frequency
+    q0 = O.MultiLevelProblem(atm, atom)
+    n0 = q0.zero_radiation(1)
+    J0, U0, t0 = q0.formal_solution(1, n0)
+    atm.vel = np.zeros((3,) + atm.shape)
+    q1 = O.MultiLevelProblem(atm, atom)
+    J1, U1, t1 = q1.formal_solution(1, n0)
+    for a, b in ((t1["qa"] * J1, t0["qa"] * J0), (t1["qe"] * U1, t0["qe"] * U0)):
+        err = np.max(np.abs(a - b), axis=1) / np.max(np.abs(b), axis=1)
+        assert np.max(err) < 1e-12
