@@ -481,6 +481,15 @@ int mg3d_check_exp(int n, const double *x_host, double *out_host);
 int mg3d_check_profiles(int n, double a, const double *x_host, const double *xp_host,
                         double *out_host);
 
+/* Check of the rational Voigt function (no GPU): Weideman's 40-term
+ * expansion of the Faddeeva function, plain arithmetic that host and device
+ * code can both evaluate; R_II-A's angle integrand uses it.  For each i,
+ * out_host[i] = H(a_host[i], x_host[i]) with a_host[i] > 0; relative error
+ * below 5e-14 + 2e-14/a (rounding, in the cancellation of the expansion's
+ * two terms as a -> 0).  MG3D_E_ARG for n < 1, null pointers or a
+ * non-positive (or non-finite) a; out_host holds n doubles. */
+int mg3d_check_voigt(int n, const double *a_host, const double *x_host, double *out_host);
+
 /* Replay V-cycles from CUDA graphs (default on).  The first V-cycle of each
  * kind (first cycle / later cycles) is captured on the handle's stream and
  * later ones replay the graph; graphs are rebuilt after a change of stream or

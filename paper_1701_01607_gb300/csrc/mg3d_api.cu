@@ -3001,6 +3001,16 @@ int mg3d_check_profiles(int n, double a, const double *x_host, const double *xp_
     return MG3D_OK;
 }
 
+int mg3d_check_voigt(int n, const double *a_host, const double *x_host, double *out_host) {
+    if (n < 1 || !a_host || !x_host || !out_host) return fail(MG3D_E_ARG, "bad arguments");
+    for (int i = 0; i < n; ++i)
+        if (!(a_host[i] > 0.0 && a_host[i] < INFINITY) || !std::isfinite(x_host[i]))
+            return fail(MG3D_E_ARG, "a must be positive and finite, x finite");
+    const VoigtTable &tab = voigt_coefficients();
+    for (int i = 0; i < n; ++i) out_host[i] = voigt_H_rational(tab, a_host[i], x_host[i]);
+    return MG3D_OK;
+}
+
 int mg3d_check_exp(int n, const double *x_host, double *out_host) {
     if (n < 1 || !x_host || !out_host) return fail(MG3D_E_ARG, "bad arguments");
     double tab[kExpTab], l1, l2;

@@ -153,6 +153,7 @@ _SIGNATURES = {
     "mg3d_autotune": (_I, [_H, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),
     "mg3d_check_exp": (_I, [_I, _D, _D]),
     "mg3d_check_profiles": (_I, [_I, ctypes.c_double, _D, _D, _D]),
+    "mg3d_check_voigt": (_I, [_I, _D, _D, _D]),
     "mg3d_set_graphs": (_I, [_H, _I]),
     "mg3d_set_timing": (_I, [_H, _I]),
     "mg3d_get_counters": (_I, [_H, ctypes.POINTER(mg3d_counters)]),
@@ -471,6 +472,15 @@ def mg3d_check_profiles(a: float, x, xp):
     out = np.empty(2 * x.size)
     _check(load().mg3d_check_profiles(x.size, float(a), _dptr(x), _dptr(xp), _dptr(out)))
     return out[0::2], out[1::2]
+
+
+def mg3d_check_voigt(a, x):
+    """H(a, x) by the library's rational Voigt function (host code)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    a = np.ascontiguousarray(np.broadcast_to(a, x.shape), dtype=np.float64)
+    out = np.empty(x.size)
+    _check(load().mg3d_check_voigt(x.size, _dptr(a), _dptr(x), _dptr(out)))
+    return out.reshape(x.shape)
 
 
 def mg3d_set_graphs(h, enable: bool):

@@ -103,6 +103,23 @@ def test_host_line_tables_match_scipy_and_the_oracle(lib):
     assert np.allclose(R0, 0.5 * special.erfc(np.maximum(np.abs(x), np.abs(xp))), rtol=1e-15)
 
 
+def test_rational_voigt_function_within_its_error_bound(lib):
+    """The 40-term rational Voigt function against scipy's Faddeeva function
+    over damping 1e-4 .. 1e4 and offsets to 1e5: relative error below
+    5e-14 + 2e-14/a (its rounding bound); invalid damping is refused."""
+    special = pytest.importorskip("scipy.special")
+    x = np.r_[np.linspace(0.0, 10.0, 401), np.linspace(10.0, 100.0, 91),
+              np.geomspace(100.0, 1e5, 16)]
+    x = np.r_[-x[::-1], x]
+    for a in (1e-4, 1e-3, 0.01, 0.05, 0.5, 1.0, 3.0, 30.0, 1e4):
+        H = m.mg3d_check_voigt(a, x)
+        ref = special.wofz(x + 1j * a).real
+        assert np.all(np.abs(H / ref - 1.0) <= 5e-14 + 2e-14 / a), a
+    for bad in (0.0, -1.0, np.inf, np.nan):
+        with pytest.raises(m.MG3DError):
+            m.mg3d_check_voigt(bad, x[:3])
+
+
 def test_null_handle_is_an_argument_error(lib):
     assert lib.mg3d_destroy(None) == m.MG3D_OK
     assert lib.mg3d_fas_vcycle(None, 0, None) == m.MG3D_E_ARG
