@@ -154,3 +154,139 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         assert got[(name, "size")] == ctypes.sizeof(cls), name
         for field, _ in cls._fields_:
             assert got[(name, field)] == getattr(cls, field).offset, (name, field)
+
+
+# Every argument check of the two create calls runs before any CUDA call, so
+# each refusal is exercised here without a GPU: (mutation, words of the
+# message).  Each mutation turns one valid input into an invalid one.
+def _grid(nx, ny, nz):
+    atm, _ = synth.stratified_two_level(nx, ny, nz, eps=1e-3)
+    return atm
+
+
+TWO_LEVEL_REFUSALS = [
+    (dict(params=dict(n_grids=0)), "n_grids"),
+    (dict(params=dict(n_grids=99)), "n_grids"),
+    (dict(params=dict(nu1=-1)), "negative iteration"),
+    (dict(params=dict(nu_fmg=-2)), "negative iteration"),
+    (dict(params=dict(restriction=3)), "restriction"),
+    (dict(params=dict(interpolation=2)), "interpolation"),
+    (dict(params=dict(sc_interp=-1)), "sc_interp"),
+    (dict(atom=dict(gamma_prd=1.5)), "gamma_prd"),
+    (dict(atom=dict(gamma_prd=float("nan"))), "gamma_prd"),
+    (dict(atom=dict(a_damp=1e3)), "a_damp"),
+    (dict(atom=dict(gamma_prd=0.5), params=dict(sc_interp=1)), "partial redistribution"),
+    (dict(atom=dict(n_freq=0)), "bad atom"),
+    (dict(atom=dict(n_freq=4097)), "bad atom"),
+    (dict(atom=dict(x_max=-1.0)), "bad atom"),
+    (dict(atom=dict(a_ul=0.0)), "bad atom"),
+    (dict(atom=dict(g_ratio=-1.0)), "bad atom"),
+    (dict(atom=dict(theta=0.0)), "bad atom"),
+    (dict(atom=dict(kappa=float("nan"))), "bad atom"),
+    (dict(atm=dict(nz=1, z=np.zeros(1))), "grid too small"),
+    (dict(atm=dict(dx=0.0)), "dx, dy"),
+    (dict(atm=dict(dy=-1.0)), "dx, dy"),
+    (dict(atm="wide"), "below 65536"),
+    (dict(atm="moving", params=dict(sc_interp=1)), "linear upwind"),
+]
+
+
+@pytest.mark.parametrize("mut,words", TWO_LEVEL_REFUSALS)
+def test_create_refuses_each_bad_argument(lib, mut, words):
+    import dataclasses
+    atm, atom = synth.stratified_two_level(8, 8, 17, eps=1e-3)
+    if mut.get("atm") == "wide":
+        atm = _grid(65536, 1, 3)
+    elif mut.get("atm") == "moving":
+        atm, _ = synth.stratified_two_level(8, 8, 17, eps=1e-3, velocity=1.0)
+    elif "atm" in mut:
+        atm = dataclasses.replace(atm, **mut["atm"])
+    atom = dataclasses.replace(atom, **mut.get("atom", {}))
+    with pytest.raises(m.MG3DError) as ei:
+        m.mg3d_create(atm, atom, **mut.get("params", {}))
+    assert ei.value.code == m.MG3D_E_ARG
+    assert words in m.mg3d_last_error()
+
+
+def _ml_inputs():
+    atom = synth.hydrogen_like_atom(line_freq=5, cont_freq=3)
+    return synth.chromosphere(8, 8, 17, atom), atom
+
+
+def _bad_line(i, **kw):
+    def mutate(atom):
+        import dataclasses
+        atom.lines[i] = dataclasses.replace(atom.lines[i], **kw)
+    return mutate
+
+
+def _bad_cont(i, **kw):
+    def mutate(atom):
+        import dataclasses
+        atom.continua[i] = dataclasses.replace(atom.continua[i], **kw)
+    return mutate
+
+
+def _set(**kw):
+    def mutate(atom):
+        for k, v in kw.items():
+            setattr(atom, k, v)
+    return mutate
+
+
+ML_REFUSALS = [
+    (_bad_line(0, lower=1, upper=1), "bad line 0"),
+    (_bad_line(1, upper=9), "bad line 1"),
+    (_bad_line(2, n_freq=0), "bad line 2"),
+    (_bad_line(0, rho=0.0), "bad line 0"),
+    (_bad_line(0, a_ul=-1.0), "bad line 0"),
+    (_bad_line(0, kappa=-1.0), "bad line 0"),
+    (_bad_line(0, x_max=float("nan")), "bad line 0"),
+    (_bad_cont(0, lower=5), "bad continuum 0"),
+    (_bad_cont(1, y_max=0.5), "bad continuum 1"),
+    (_bad_cont(0, n_freq=0), "bad continuum 0"),
+    (_bad_cont(0, beta=-1.0), "bad continuum 0"),
+    (_bad_line(0, n_freq=70000), "too many frequencies"),
+    (_set(theta_ref=0.0), "theta_ref"),
+    (_set(t_ref=-1.0), "t_ref"),
+    (_set(lines=[], continua=[]), "no transitions"),
+]
+
+
+@pytest.mark.parametrize("mutate,words", ML_REFUSALS)
+def test_create_ml_refuses_each_bad_argument(lib, mutate, words):
+    atm, atom = _ml_inputs()
+    mutate(atom)
+    with pytest.raises(m.MG3DError) as ei:
+        m.mg3d_create_ml(atm, atom, n_grids=1)
+    assert ei.value.code == m.MG3D_E_ARG
+    assert words in m.mg3d_last_error()
+
+
+def test_create_ml_refuses_bad_levels_grids_and_options(lib):
+    import dataclasses
+    atm, atom = _ml_inputs()
+    for kw, words in ((dict(n_grids=0), "n_grids"), (dict(fs_prec=7), "fs_prec"),
+                      (dict(nu3=-1), "negative iteration"), (dict(restriction=5), "restriction"),
+                      (dict(interpolation=-1), "interpolation"), (dict(sc_interp=3), "sc_interp")):
+        with pytest.raises(m.MG3DError) as ei:
+            m.mg3d_create_ml(atm, atom, **kw)
+        assert ei.value.code == m.MG3D_E_ARG and words in m.mg3d_last_error(), kw
+    vatm = synth.chromosphere(8, 8, 17, atom, velocity=1.0)
+    with pytest.raises(m.MG3DError):
+        m.mg3d_create_ml(vatm, atom, n_grids=1, sc_interp=1)
+    assert "linear upwind" in m.mg3d_last_error()
+    for bad_atm, words in ((dataclasses.replace(atm, dx=0.0), "dx, dy"),
+                           (dataclasses.replace(atm, nz=1, z=atm.z[:1]), "grid too small"),
+                           (dataclasses.replace(atm, z=atm.z[::-1].copy()), "z must increase")):
+        with pytest.raises(m.MG3DError) as ei:
+            m.mg3d_create_ml(bad_atm, atom, n_grids=1)
+        assert ei.value.code == m.MG3D_E_ARG and words in m.mg3d_last_error()
+    with pytest.raises(m.MG3DError) as ei:
+        m.mg3d_create_ml(atm, atom, n_grids=5)      # 8 nodes coarsen three times at most
+    assert ei.value.code == m.MG3D_E_GRID
+    # more than eight levels
+    big = synth.hydrogen_like_atom(n_bound=8, line_freq=3, cont_freq=2)
+    with pytest.raises(m.MG3DError) as ei:
+        m.mg3d_create_ml(synth.chromosphere(8, 8, 17, big), big, n_grids=1)
+    assert ei.value.code == m.MG3D_E_ARG and "n_levels" in m.mg3d_last_error()
