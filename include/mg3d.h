@@ -297,6 +297,9 @@ typedef struct {
     double a_damp;      /* Voigt damping parameter at t_ref; must be 0 (Doppler
                            profiles): damped lines of multi-level atoms are
                            refused with MG3D_E_ARG */
+    double gamma_prd;   /* coherence fraction of partial redistribution; must
+                           be 0 (CRD): multi-level PRD is refused with
+                           MG3D_E_ARG */
 } mg3d_line;
 
 typedef struct {

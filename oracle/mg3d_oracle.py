@@ -44,6 +44,10 @@ What each function follows in the paper (Bjorgen & Leenaarts 2017):
 * ``prd_matrix`` / ``formal_solution_prd`` -- partial redistribution for the
   two-level atom (the next step of Sec. 6): angle-averaged Doppler
   redistribution mixed with CRD, S_f = rho_f S from the lagged field.
+* ``MultiLevelProblem.prd_ratios`` / ``prd_tables`` -- partial redistribution
+  of multi-level lines, the two-level reading generalised: R_I-A at each
+  node's Doppler width, f_rad from the plain lagged rates into the upper
+  level, the emissivity and the transition's share of chi scaled by rho.
 * ``line_profile`` / ``ml_line_profile`` -- Doppler or, with damping, Voigt
   profiles (the paper's atoms have damped lines); a multi-level line's
   damping parameter scales as 1/d with the node's Doppler width d.
@@ -1066,6 +1070,21 @@ class MultiLevelProblem(TwoLevelProblem):
             y = np.linspace(1.0, ct.y_max, ct.n_freq) if ct.n_freq > 1 else np.ones(1)
             for yv, wv in zip(y, trapezoid_weights(y)):
                 self.freqs.append(("cont", ti, float(yv), float(wv)))
+        self.line_freqs = {}
+        for f, (kind, ti, xv, wv) in enumerate(self.freqs):
+            if kind == "line":
+                self.line_freqs.setdefault(ti, []).append(f)
+        # partial redistribution of lines with a coherence fraction
+        self.prd_lines = [ti for ti, ln in enumerate(atom.lines)
+                          if getattr(ln, "gamma_prd", 0.0) > 0.0]
+        if self.prd_lines and fine.vel is not None:
+            raise ValueError("partial redistribution takes a static atmosphere")
+        if any(getattr(atom.lines[ti], "a_damp", 0.0) > 0.0 for ti in self.prd_lines):
+            raise ValueError("partial redistribution of damped lines is not built")
+        self._prd_tables = {}
+        # the lagged mean intensity per frequency serves background scattering
+        # and partial redistribution alike
+        self.lagged = self.scatter or bool(self.prd_lines)
         self.fs_count = {k: 0 for k in self.levels}
         self.sweep_count = {k: 0 for k in self.levels}
         self.negatives = 0
@@ -1138,7 +1157,80 @@ class MultiLevelProblem(TwoLevelProblem):
             out["S"][f] = (eta_t + chi_c * B + sigma * self.jbg[k][f]) / chi
             out["sl"][f] = eta_t / chi
             out["fl"][f] = chi_t / chi
+        if self.prd_lines:
+            # emission profile rho phi: the line emissivity, and with it the
+            # transition's share of S, scales by rho; in the local operator
+            # rho multiplies the transition's share of chi (the two-level
+            # U = sum w phi (1 - w0 rho))
+            for ti, rho in self.prd_ratios(k, n, out).items():
+                for j, f in enumerate(self.line_freqs[ti]):
+                    out["S"][f] += (rho[j] - 1.0) * out["sl"][f]
+                    out["sl"][f] *= rho[j]
+                    out["fl"][f] *= rho[j]
         return out, Ib
+
+    # ---- partial redistribution of lines ----
+    def prd_tables(self, k: int, ti: int):
+        """For PRD line ti on grid k, per node: the redistribution matrix
+        R[v, f', f] (R_I-A at the node's Doppler width d,
+        R0(x', x) = erfc(max(|x|, |x'|)/d)/(2 d^2), scaled symmetrically so
+        that its discrete marginals sum_f' wq R[f', f] are the node's profile,
+        the fixed point of ``prd_matrix`` node by node), the normalised
+        quadrature weights wq [v, f] and the profile phi [v, f]."""
+        key = (k, ti)
+        if key not in self._prd_tables:
+            from scipy.special import erfc
+            fs = self.line_freqs[ti]
+            x = np.array([self.freqs[f][2] for f in fs])
+            w = np.array([self.freqs[f][3] for f in fs])
+            d = np.sqrt(self.levels[k].T.reshape(-1) / self.atom.t_ref)
+            phi = ml_line_profile(x[None, :], d[:, None])
+            wq = w[None, :] / (w[None, :] * phi).sum(axis=1)[:, None]
+            ax = np.abs(x)
+            dd = d[:, None, None]
+            R0 = 0.5 * erfc(np.maximum(ax[:, None], ax[None, :])[None, :, :] / dd) / dd ** 2
+            c = np.ones_like(phi)
+            for _ in range(200):
+                c = np.sqrt(c * phi / np.einsum("vab,va->vb", R0, wq * c))
+            self._prd_tables[key] = (c[:, :, None] * R0 * c[:, None, :], wq, phi)
+        return self._prd_tables[key]
+
+    def prd_ratios(self, k: int, n, terms):
+        """rho_f = psi_f/phi_f for every PRD line at every node from the lagged
+        field J_f (the two-level reading generalised):
+            rho = 1 + gamma f_rad (sum_f' wq_f' R(f', f) J_f' / (phi_f Jbar) - 1),
+        Jbar = sum wq phi J over the line, f_rad = n_l B_lu Jbar / sum_j n_j P_ju
+        the radiative excitation's share of all transitions into the upper
+        level (plain rates: the lagged J, no local operator, collisions);
+        rho = 1 where Jbar = 0.  Returns {ti: rho [nf_line, nvox]}."""
+        lev = self.levels[k]
+        N = self.N
+        nvox = lev.nx * lev.ny * lev.nz
+        nn = n.reshape(N, -1)
+        J = self.jbg[k]
+        P = lev.c.reshape(N, N, nvox).copy()
+        for f, (kind, ti, xv, wv) in enumerate(self.freqs):
+            if kind == "line":
+                lo, up = self.atom.lines[ti].lower, self.atom.lines[ti].upper
+            else:
+                lo, up = self.atom.continua[ti].lower, N - 1
+            P[lo, up] += terms["qa"][f] * J[f]
+            P[up, lo] += terms["qe"][f] + terms["qb"][f] * J[f]
+        out = {}
+        for ti in self.prd_lines:
+            ln = self.atom.lines[ti]
+            fs = self.line_freqs[ti]
+            R, wq, phi = self.prd_tables(k, ti)
+            Jl = J[fs].T                                             # [nvox, nf_line]
+            Jbar = np.sum(wq * phi * Jl, axis=1)
+            excite = nn[ln.lower] * sum(terms["qa"][f] * J[f] for f in fs)
+            inflow = sum(nn[j] * P[j, ln.upper] for j in range(N) if j != ln.upper)
+            frad = excite / inflow
+            Af = np.einsum("vab,va->vb", R, wq * Jl)
+            with np.errstate(divide="ignore", invalid="ignore"):
+                ratio = np.where(Jbar[:, None] > 0, Af / (phi * Jbar[:, None]), 1.0)
+            out[ti] = (1.0 + ln.gamma_prd * frad[:, None] * (ratio - 1.0)).T
+        return out
 
     def formal_solution(self, k: int, n):
         """Per-frequency (Jx, Ux) [nfreq, nz, ny, nx] and the rate weights; with
@@ -1154,7 +1246,7 @@ class MultiLevelProblem(TwoLevelProblem):
                                      terms["chi"].reshape(shp), terms["S"].reshape(shp),
                                      terms["sl"].reshape(shp), terms["fl"].reshape(shp),
                                      Ib.reshape((nf, lev.ny, lev.nx)), 0.0,
-                                     want_j=self.scatter, interp=self.sc_interp)
+                                     want_j=self.lagged, interp=self.sc_interp)
         Jx, Ux = res[0], res[1]
         if self.updates_background(k):
             self.jbg[k] = res[2].reshape(nf, -1)
@@ -1168,7 +1260,7 @@ class MultiLevelProblem(TwoLevelProblem):
         the Lambda-iteration that starts it, so that W on that grid is one
         operator from the tau-correction of Eq. 9 to the correction of Eq. 10
         (a converged fine solution then gets a zero correction)."""
-        return self.scatter and (k == self.top or self._force_bg)
+        return self.lagged and (k == self.top or self._force_bg)
 
     def lambda_iteration(self, k: int, n):
         """One Lambda-iteration of the background field (Sec. 4.8): a formal
@@ -1185,7 +1277,7 @@ class MultiLevelProblem(TwoLevelProblem):
         field of k, full-weighted, then one Lambda-iteration with the
         restricted populations; the field then stays fixed on grid k-1
         until the cycle leaves it."""
-        if self.scatter:
+        if self.lagged:
             fine = self.levels[k]
             jf = self.jbg[k].reshape((-1,) + fine.shape)
             self.jbg[k - 1] = restrict_fw(jf).reshape(jf.shape[0], -1)
@@ -1194,7 +1286,7 @@ class MultiLevelProblem(TwoLevelProblem):
     def fmg_prolong(self, k: int):
         """FMG moving the full approximation from grid k-1 to k: the
         background field moves with it (trilinear)."""
-        if self.scatter:
+        if self.lagged:
             coarse = self.levels[k - 1]
             jc = self.jbg[k - 1].reshape((-1,) + coarse.shape)
             self.jbg[k] = self.prolong(k, jc).reshape(jc.shape[0], -1)
@@ -1318,10 +1410,12 @@ class MultiLevelProblem(TwoLevelProblem):
             terms, _ = self.transition_terms(k, n_any)
         M = self.rate_matrix_from(k, np.zeros((nf, nvox)), np.ones((nf, nvox)), terms)
         n = self.solve(M, self.default_rhs(k))
-        if self.scatter:
-            # background field from nothing: cleared, then one Lambda-iteration
+        if self.lagged:
+            # the lagged field from nothing: cleared (rho = 1 for partial
+            # redistribution); with background scattering one Lambda-iteration
             self.jbg[k] = np.zeros((nf, nvox))
-            self.lambda_iteration(k, n)
+            if self.scatter:
+                self.lambda_iteration(k, n)
         return n
 
     def mali_sweep(self, k: int, n, f=None):

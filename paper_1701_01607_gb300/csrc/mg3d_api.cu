@@ -2337,6 +2337,10 @@ int mg3d_create_ml(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
         if (ln.a_damp != 0.0)
             return fail(MG3D_E_ARG, "line " + std::to_string(t) +
                                         ": multi-level atoms take Doppler profiles (a_damp 0)");
+        if (ln.gamma_prd != 0.0)
+            return fail(MG3D_E_ARG, "line " + std::to_string(t) +
+                                        ": partial redistribution of multi-level atoms is not "
+                                        "built (gamma_prd 0)");
         nf += ln.n_freq;
     }
     for (int t = 0; t < atom->n_continua; ++t) {

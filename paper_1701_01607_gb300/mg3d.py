@@ -65,7 +65,8 @@ class mg3d_params(ctypes.Structure):
 class mg3d_line(ctypes.Structure):
     _fields_ = [("lower", ctypes.c_int), ("upper", ctypes.c_int), ("rho", ctypes.c_double),
                 ("a_ul", ctypes.c_double), ("kappa", ctypes.c_double), ("n_freq", ctypes.c_int),
-                ("x_max", ctypes.c_double), ("a_damp", ctypes.c_double)]
+                ("x_max", ctypes.c_double), ("a_damp", ctypes.c_double),
+                ("gamma_prd", ctypes.c_double)]
 
 
 class mg3d_continuum(ctypes.Structure):
@@ -274,7 +275,8 @@ def mg3d_create_ml(atm, atom, quad_a: float = 0.0, n_grids: int = 1, nu_fmg: int
                            arr("v", vel) if vel is not None else None)
     lines = (mg3d_line * max(1, len(atom.lines)))(
         *[mg3d_line(l.lower, l.upper, l.rho, l.a_ul, l.kappa, l.n_freq, l.x_max,
-                    getattr(l, "a_damp", 0.0)) for l in atom.lines])
+                    getattr(l, "a_damp", 0.0), getattr(l, "gamma_prd", 0.0))
+          for l in atom.lines])
     conts = (mg3d_continuum * max(1, len(atom.continua)))(
         *[mg3d_continuum(c.lower, c.rho, c.beta, c.kappa, c.n_freq, c.y_max)
           for c in atom.continua])

@@ -199,6 +199,7 @@ class Line:
     n_freq: int
     x_max: float        # half width in reference Doppler widths
     a_damp: float = 0.0  # damping parameter at t_ref (0: Doppler profile)
+    gamma_prd: float = 0.0  # coherence fraction of partial redistribution (0: CRD)
 
 
 @dataclasses.dataclass
@@ -265,7 +266,8 @@ def hydrogen_like_atom(n_bound: int = 5, line_freq: int = 100, cont_freq: int = 
                        seed: int = 2, theta_ref: float = 40000.0, x_max: float = 4.0,
                        y_max: float = 2.5, kappa_line: float = 10.0,
                        kappa_cont: float = 1e-3, beta_cont: float = 0.05,
-                       jitter: float = 0.2, a_damp: float = 0.0) -> MultiLevelAtom:
+                       jitter: float = 0.2, a_damp: float = 0.0,
+                       gamma_prd: float = 0.0) -> MultiLevelAtom:
     """A seeded hydrogen-like atom: n_bound bound levels plus a continuum.
 
     Level n (1-based) has g = 2 n^2 and energy theta_ref (1 - 1/n^2)/(3/4)
@@ -274,8 +276,9 @@ def hydrogen_like_atom(n_bound: int = 5, line_freq: int = 100, cont_freq: int = 
     Kramers-like oscillator strengths; one bound-free continuum per bound
     level with a nu^-3 cross-section.  Strengths carry a seeded +-jitter.
     a_damp > 0 gives every line that damping parameter at t_ref (Voigt
-    profiles); it draws no random numbers, so the seeded strengths do not
-    change with it.
+    profiles), gamma_prd > 0 the resonance lines (lower level 0) that
+    coherence fraction of partial redistribution; neither draws random
+    numbers, so the seeded strengths do not change with them.
     """
     rng = np.random.default_rng(seed)
     nl = n_bound + 1
@@ -304,7 +307,7 @@ def hydrogen_like_atom(n_bound: int = 5, line_freq: int = 100, cont_freq: int = 
         # A_ul ~ f_lu (g_l/g_u) nu^2, in units where the 1-2 line has A = 1
         a_ul = (f_lu / f12) * (g[lo] / g[up]) / (g[0] / g[1]) * rho ** 2
         lines.append(Line(lo, up, rho, a_ul * jit(), kappa_line * (f_lu / f12) * jit(),
-                          line_freq, x_max, a_damp))
+                          line_freq, x_max, a_damp, gamma_prd if lo == 0 else 0.0))
     continua = []
     for lo in range(n_bound):
         rho = (theta_ion - theta[lo]) / theta_ref

@@ -250,6 +250,7 @@ ML_REFUSALS = [
     (_set(theta_ref=0.0), "theta_ref"),
     (_set(t_ref=-1.0), "t_ref"),
     (_set(lines=[], continua=[]), "no transitions"),
+    (_bad_line(0, gamma_prd=0.5), "partial redistribution"),
 ]
 
 

@@ -277,3 +277,131 @@ def test_ml_damped_conservation_multigrid_and_flow():
     for a, b in ((t1["qa"] * J1, t0["qa"] * J0), (t1["qe"] * U1, t0["qe"] * U0)):
         err = np.max(np.abs(a - b), axis=1) / np.max(np.abs(b), axis=1)
         assert np.max(err) < 1e-12
+
+
+# ------------------------------------------------- partial redistribution
+
+def _two_level_pair(gamma, nx=8, nz=17):
+    atom2 = synth.TwoLevelAtom(gamma_prd=gamma, n_freq=9, x_max=3.0)
+    atm2, atom2 = synth.stratified_two_level(nx, nx, nz, eps=1e-2, sigma=0.3, seed=4, atom=atom2)
+    line = synth.Line(0, 1, 1.0, atom2.a_ul, atom2.kappa, atom2.n_freq, atom2.x_max, 0.0, gamma)
+    ml_atom = synth.MultiLevelAtom(g=np.array([1.0, 1.0]), theta=np.array([0.0, atom2.theta]),
+                                   theta_ref=atom2.theta, lines=[line], continua=[],
+                                   t_ref=5000.0)
+    c = np.zeros((2, 2) + atm2.shape)
+    c[1, 0] = atm2.c_ul
+    c[0, 1] = atm2.c_ul * np.exp(-atom2.theta / atm2.T)
+    ml_atm = synth.MultiLevelAtmosphere(atm2.nx, atm2.ny, atm2.nz, atm2.dx, atm2.dy, atm2.z,
+                                        atm2.T, atm2.n_tot, np.zeros(atm2.shape), c,
+                                        np.zeros((2,) + atm2.shape))
+    return (atm2, atom2), (ml_atm, ml_atom)
+
+
+def test_ml_prd_reduces_to_two_level_prd():
+    """One PRD line at T = t_ref: the two-level PRD oracle (pinned on its
+    own), through MALI sweeps and a V-cycle with its coarse-grid entry."""
+    (atm2, atom2), (ml_atm, ml_atom) = _two_level_pair(0.9)
+    p2 = O.TwoLevelProblem(atm2, atom2, n_grids=2)
+    pm = O.MultiLevelProblem(ml_atm, ml_atom, n_grids=2)
+    n2, nm = p2.zero_radiation(2), pm.zero_radiation(2)
+    for _ in range(4):
+        n2, c2 = p2.mali_sweep(2, n2)
+        nm, cm = pm.mali_sweep(2, nm)
+        assert abs(cm - c2) < 1e-12
+    assert O.max_rel_error(nm, n2) < 1e-12
+    params = dict(nu_fmg=4, nu0=4, nu1=2, nu2=2, nu3=32)
+    n2, c2 = p2.fas_cycle(n2, False, params)
+    nm, cm = pm.fas_cycle(nm, False, params)
+    assert O.max_rel_error(nm, n2) < 1e-12 and abs(cm - c2) < 1e-12
+
+
+def _ml_prd_box(gamma=1.0, nx=8, nz=17, line_freq=7):
+    atom = synth.hydrogen_like_atom(line_freq=line_freq, cont_freq=4, seed=2, gamma_prd=gamma)
+    atm = synth.chromosphere(nx, nx, nz, atom, seed=2, ground_collisions=1e-3)
+    return atm, atom
+
+
+def test_ml_prd_table_follows_the_continuous_kernel():
+    """At every node the matrix is c_a R0(x_a, x_b) c_b with R0 the kernel
+    erfc(max(|x|, |x'|)/d)/(2 d^2) at the node's Doppler width; on a fine
+    grid the symmetric factors c tend to 1 (the kernel's marginal is the
+    node's profile), so a wrong width scaling would show; the discrete
+    marginals are the profile exactly."""
+    special = pytest.importorskip("scipy.special")
+    atm, atom = _ml_prd_box(line_freq=41)
+    p = O.MultiLevelProblem(atm, atom)
+    ti = p.prd_lines[0]
+    R, wq, phi = p.prd_tables(1, ti)
+    x = np.array([p.freqs[f][2] for f in p.line_freqs[ti]])
+    d = np.sqrt(atm.T.reshape(-1) / atom.t_ref)
+    assert d.min() < 0.95 and d.max() > 1.2
+    ax = np.abs(x)
+    R0 = 0.5 * special.erfc(np.maximum(ax[:, None], ax[None, :])[None] / d[:, None, None]) \
+        / d[:, None, None] ** 2
+    cc = R / R0                                    # c_a c_b
+    c = np.sqrt(np.einsum("vaa->va", cc))
+    assert np.allclose(cc, c[:, :, None] * c[:, None, :], rtol=1e-12)
+    # inside |x| <= 3 (the grid ends at 4, where truncation of the kernel
+    # shows): 4e-3 here, against 0.15 with R0 scaled by 1/d instead of 1/d^2
+    # and 12 without the width
+    assert np.max(np.abs(c[:, ax <= 3.0] - 1.0)) < 1e-2
+    assert np.allclose(np.einsum("vab,va->vb", R, wq), phi, rtol=1e-12)
+
+
+def test_ml_prd_ratio_conserves_photons_and_reduces_to_crd():
+    atm, atom = _ml_prd_box()
+    p = O.MultiLevelProblem(atm, atom)
+    n = p.zero_radiation(1)
+    terms, _ = p.transition_terms(1, n)
+    rng = np.random.default_rng(3)
+    p.jbg[1] = np.exp(rng.normal(size=p.jbg[1].shape))
+    rho = p.prd_ratios(1, n, terms)
+    assert set(rho) == set(p.prd_lines) and len(rho) == 2    # both resonance lines
+    for ti, r in rho.items():
+        _, wq, phi = p.prd_tables(1, ti)
+        assert np.allclose(np.sum(wq * phi * r.T, axis=1), 1.0, rtol=0, atol=1e-13)
+        assert np.max(np.abs(r - 1.0)) > 1e-3
+    # a field flat across each line: rho = 1
+    for ti, fs in p.line_freqs.items():
+        p.jbg[1][fs] = p.jbg[1][fs[0]]
+    for r in p.prd_ratios(1, n, terms).values():
+        assert np.max(np.abs(r - 1.0)) < 1e-13
+    # vanishing coherence takes the CRD path
+    atm2, atom0 = _ml_prd_box(gamma=0.0)
+    atm3, atom_eps = _ml_prd_box(gamma=1e-14)
+    q0, q1 = O.MultiLevelProblem(atm2, atom0), O.MultiLevelProblem(atm3, atom_eps)
+    m0, m1 = q0.zero_radiation(1), q1.zero_radiation(1)
+    for _ in range(3):
+        m0, _ = q0.mali_sweep(1, m0)
+        m1, _ = q1.mali_sweep(1, m1)
+    assert O.max_rel_error(m1, m0) < 1e-12
+
+
+def test_ml_prd_conservation_multigrid_and_effect():
+    atm, atom = _ml_prd_box(nx=4, nz=9)
+    p = O.MultiLevelProblem(atm, atom, n_grids=2)
+    n = p.zero_radiation(2)
+    for _ in range(3):
+        n, _ = p.mali_sweep(2, n)
+        assert np.allclose(n.sum(axis=0), atm.n_tot, rtol=1e-13)
+        assert np.all(n > 0)
+    params = dict(nu_fmg=8, nu0=10, nu1=2, nu2=4, nu3=16)
+    n_mali, _ = O.mali_solve(O.MultiLevelProblem(atm, atom, n_grids=2), 1e-11)
+    n_fas, _ = O.fas_solve(O.MultiLevelProblem(atm, atom, n_grids=2), 1e-10, params)
+    n_fmg, _ = O.fmg_solve(O.MultiLevelProblem(atm, atom, n_grids=2), 1e-10, params)
+    assert O.max_rel_error(n_fas, n_mali) < 1e-8
+    assert O.max_rel_error(n_fmg, n_mali) < 1e-8
+    _, crd_atom = _ml_prd_box(gamma=0.0, nx=4, nz=9)
+    n_crd, _ = O.mali_solve(O.MultiLevelProblem(atm, crd_atom, n_grids=2), 1e-11)
+    assert O.max_rel_error(n_crd, n_mali) > 1e-4
+
+
+def test_ml_prd_refusals():
+    atm, atom = _ml_prd_box()
+    vatm = synth.chromosphere(8, 8, 17, atom, seed=2, velocity=1.0)
+    with pytest.raises(ValueError, match="static"):
+        O.MultiLevelProblem(vatm, atom)
+    damped = synth.hydrogen_like_atom(line_freq=7, cont_freq=4, seed=2, gamma_prd=1.0,
+                                      a_damp=0.01)
+    with pytest.raises(ValueError, match="damped"):
+        O.MultiLevelProblem(atm, damped)
