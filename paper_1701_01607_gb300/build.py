@@ -17,8 +17,8 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libmg3d.so")
 INCLUDE = os.path.join(ROOT, "include")
 SOURCES = ["fs_sweep.cu", "rates_transfer.cu", "mg3d_api.cu", "noalloc.cu", "ml.cu"]
-HEADERS = [os.path.join(CSRC, "mg3d_internal.h"), os.path.join(CSRC, "sc_step.cuh"),
-           os.path.join(INCLUDE, "mg3d.h")]
+HEADERS = [os.path.join(CSRC, h) for h in ("mg3d_internal.h", "sc_step.cuh", "profiles.h",
+                                            "voigt.cuh")] + [os.path.join(INCLUDE, "mg3d.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "-I", INCLUDE, "-I", CSRC]
