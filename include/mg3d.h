@@ -108,9 +108,11 @@ typedef struct {
                          Hummer's angle-averaged R_II (the average over the
                          scattering angle g, weight sin g/2, of exp(-[(x - x')/(2
                          sin(g/2))]^2) H(a/cos(g/2), (x + x')/(2 cos(g/2)))/(pi
-                         sin g)); both are tabulated on the host by adaptive
-                         Gauss-Kronrod quadrature at creation.  Static
-                         atmospheres only (MG3D_E_ARG with a velocity field). */
+                         sin g)); both are tabulated on the host at creation,
+                         H by adaptive Gauss-Kronrod quadrature, R_II-A by the
+                         same quadrature over g with H from Weideman's rational
+                         expansion (mg3d_check_voigt).  Static atmospheres only
+                         (MG3D_E_ARG with a velocity field). */
 } mg3d_atom;
 
 /* Angle quadrature: the 24-direction A4 set of Carlson (Sec. 3): per octant
