@@ -281,7 +281,6 @@ def hydrogen_like_atom(n_bound: int = 5, line_freq: int = 100, cont_freq: int = 
     numbers, so the seeded strengths do not change with them.
     """
     rng = np.random.default_rng(seed)
-    nl = n_bound + 1
     n = np.arange(1, n_bound + 1, dtype=np.float64)
     g = np.r_[2.0 * n * n, 1.0]
     theta_ion = theta_ref / 0.75
