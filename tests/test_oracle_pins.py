@@ -409,3 +409,36 @@ def test_fas_converges_with_each_restriction():
         sols.append(n)
     for n in sols[1:]:
         assert O.max_rel_error(n, sols[0]) < 1e-7
+
+
+def _mali_history(nz, eps=1e-3, nx=4):
+    atm, atom = synth.stratified_two_level(nx, nx, nz, eps=eps, sigma=0.3, seed=3)
+    n_inf, it = O.mali_solve(O.TwoLevelProblem(atm, atom), 1e-14)
+    p = O.TwoLevelProblem(atm, atom)
+    n = p.zero_radiation(1)
+    C, E = [], []
+    for _ in range(it):
+        n, c = p.mali_sweep(1, n)
+        C.append(c)
+        E.append(O.max_rel_error(n, n_inf))
+    return np.array(C), np.array(E)
+
+
+def test_mali_error_estimate_of_eq13_and_spectral_radius():
+    """In the asymptotic linear regime the true error follows
+    E_i = rho/(1 - rho) C_i with rho estimated as C_(i+1)/C_i (Eq. 13 and the
+    estimate after it), and that rho is the operational spectral radius
+    E_(i+1)/E_i (Eq. 12); one-grid MALI's spectral radius grows as the grid
+    is refined (Sec. 4.13)."""
+    radii = []
+    for nz in (17, 33):
+        C, E = _mali_history(nz)
+        sel = (C[:-1] < 1e-4) & (C[:-1] > 1e-9)
+        assert sel.sum() >= 10
+        rho_c = C[1:] / C[:-1]
+        rho_e = E[1:] / E[:-1]
+        est = rho_c / (1.0 - rho_c) * C[:-1]
+        assert np.max(np.abs(est[sel] / E[:-1][sel] - 1.0)) < 1e-3
+        assert np.max(np.abs(rho_c[sel] / rho_e[sel] - 1.0)) < 1e-3
+        radii.append(float(np.median(rho_c[sel])))
+    assert 0.5 < radii[0] < radii[1] < 1.0
