@@ -442,3 +442,31 @@ def test_mali_error_estimate_of_eq13_and_spectral_radius():
         assert np.max(np.abs(rho_c[sel] / rho_e[sel] - 1.0)) < 1e-3
         radii.append(float(np.median(rho_c[sel])))
     assert 0.5 < radii[0] < radii[1] < 1.0
+
+
+def test_multigrid_spectral_radius_nearly_independent_of_grid_spacing():
+    """Sec. 4.13: unlike one-grid MALI, whose spectral radius grows as the
+    grid is refined (so its iterations per decade of error roughly double
+    from 17 to 33 nodes per column), the V-cycle's stays nearly constant when
+    a grid is added over the same coarsest grid."""
+    params = dict(nu_fmg=4, nu0=4, nu1=2, nu2=2, nu3=32)
+    per_decade = {}
+    for nz, ng in ((17, 2), (33, 3)):
+        atm, atom = synth.stratified_two_level(4, 4, nz, eps=1e-3, sigma=0.3, seed=3)
+        n_inf, _ = O.fas_solve(O.TwoLevelProblem(atm, atom, n_grids=ng), 1e-13, params)
+        p = O.TwoLevelProblem(atm, atom, n_grids=ng)
+        n = p.zero_radiation(ng)
+        E = []
+        for cyc in range(6):
+            n, _ = p.fas_cycle(n, cyc == 0, params)
+            E.append(O.max_rel_error(n, n_inf))
+        rho = float(np.median(np.array(E[2:]) / np.array(E[1:-1])))
+        assert rho < 0.35
+        per_decade[nz] = -1.0 / math.log10(rho)
+    C17, _ = _mali_history(17)
+    C33, _ = _mali_history(33)
+    mali = {nz: -1.0 / math.log10(float(np.median((C[1:] / C[:-1])[(C[:-1] < 1e-4) &
+                                                                       (C[:-1] > 1e-9)])))
+            for nz, C in ((17, C17), (33, C33))}
+    assert mali[33] / mali[17] > 2.0
+    assert per_decade[33] / per_decade[17] < 1.5
