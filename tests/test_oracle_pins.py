@@ -470,3 +470,32 @@ def test_multigrid_spectral_radius_nearly_independent_of_grid_spacing():
             for nz, C in ((17, C17), (33, C33))}
     assert mali[33] / mali[17] > 2.0
     assert per_decade[33] / per_decade[17] < 1.5
+
+
+def test_zero_radiation_start_gives_a_smoother_error_than_lte():
+    """Sec. 4.11: after the first MALI sweeps the error left by the
+    zero-radiation start is smoother than the one left by an LTE start; the
+    smoothing number of Sec. 4.11, the largest second difference of
+    (n_i - n_inf)/n_inf (here along z, x and y), is several times smaller."""
+    atm, atom = synth.stratified_two_level(4, 4, 33, eps=1e-3, sigma=0.3, seed=3)
+    n_inf, _ = O.mali_solve(O.TwoLevelProblem(atm, atom), 1e-13)
+
+    def smoothing_number(n):
+        e = (n - n_inf) / n_inf
+        d2 = np.abs(e[:, 2:] - 2.0 * e[:, 1:-1] + e[:, :-2]).max()
+        for ax in (2, 3):
+            d2 = max(d2, np.abs(np.roll(e, 1, ax) - 2.0 * e + np.roll(e, -1, ax)).max())
+        return d2
+
+    r = atom.g_ratio * np.exp(-atom.theta / atm.T)
+    starts = {"zero": O.TwoLevelProblem(atm, atom).zero_radiation(1),
+              "lte": np.stack([atm.n_tot / (1.0 + r), atm.n_tot * r / (1.0 + r)])}
+    hist = {}
+    for name, n in starts.items():
+        p = O.TwoLevelProblem(atm, atom)
+        hist[name] = []
+        for _ in range(8):
+            n, _ = p.mali_sweep(1, n)
+            hist[name].append(smoothing_number(n))
+    ratio = np.array(hist["lte"]) / np.array(hist["zero"])
+    assert np.all(ratio[1:] > 3.0), ratio
