@@ -405,3 +405,22 @@ def test_ml_prd_refusals():
                                       a_damp=0.01)
     with pytest.raises(ValueError, match="damped"):
         O.MultiLevelProblem(atm, damped)
+
+
+def test_ml_prd_with_background_scattering_shares_the_lagged_field():
+    """PRD lines and background scattering read the same lagged field; the
+    start Lambda-iterates it (scattering), conservation holds and FAS meets
+    MALI."""
+    atom = synth.hydrogen_like_atom(line_freq=7, cont_freq=4, seed=2, gamma_prd=1.0)
+    atm = synth.chromosphere(4, 4, 9, atom, seed=2, ground_collisions=1e-3, scattering=1.0)
+    p = O.MultiLevelProblem(atm, atom, n_grids=2)
+    assert p.scatter and p.prd_lines and p.lagged
+    n = p.zero_radiation(2)
+    assert np.any(p.jbg[2] > 0)          # the start's Lambda-iteration
+    for _ in range(3):
+        n, _ = p.mali_sweep(2, n)
+        assert np.allclose(n.sum(axis=0), atm.n_tot, rtol=1e-13)
+    params = dict(nu_fmg=8, nu0=10, nu1=2, nu2=4, nu3=16)
+    n_mali, _ = O.mali_solve(O.MultiLevelProblem(atm, atom, n_grids=2), 1e-11)
+    n_fas, _ = O.fas_solve(O.MultiLevelProblem(atm, atom, n_grids=2), 1e-10, params)
+    assert O.max_rel_error(n_fas, n_mali) < 1e-8
