@@ -43,7 +43,9 @@ What each function follows in the paper (Bjorgen & Leenaarts 2017):
   ray (the paper's Bifrost atmospheres move; Sec. 3.1, Sec. 6).
 * ``prd_matrix`` / ``formal_solution_prd`` -- partial redistribution for the
   two-level atom (the next step of Sec. 6): angle-averaged Doppler
-  redistribution mixed with CRD, S_f = rho_f S from the lagged field.
+  redistribution mixed with CRD, S_f = rho_f S from the lagged field; in a
+  flow (``_formal_solution_moving_prd``) the redistribution happens in each
+  node's comoving frame and each ray reads rho at its shifted offsets.
 * ``MultiLevelProblem.prd_ratios`` / ``prd_tables`` -- partial redistribution
   of multi-level lines, the two-level reading generalised: R_I-A at each
   node's Doppler width, f_rad from the plain lagged rates into the upper
@@ -281,8 +283,6 @@ class TwoLevelProblem:
         # grid, and the discrete redistribution matrix
         self.gamma = float(getattr(atom, "gamma_prd", 0.0))
         self.prd = self.gamma > 0.0
-        if self.prd and fine.vel is not None:
-            raise ValueError("partial redistribution takes a static atmosphere")
         nf = len(self.x)
         self.jnu = {k: np.zeros((nf, lev.nx * lev.ny * lev.nz)) for k, lev in self.levels.items()}
         self.wq = self.wphi / self.phi
@@ -415,6 +415,8 @@ class TwoLevelProblem:
         S = np.ascontiguousarray(np.broadcast_to((nu / diff)[None, :], (nf, nvox)))
         wq = self.wphi / self.phi          # the frequency quadrature weights
         u = lev.vel.reshape(3, -1)
+        if self.prd:
+            return self._formal_solution_moving_prd(k, lev, chi0, nu / diff, u)
         Ib = np.ascontiguousarray(np.broadcast_to(
             self.planck(lev.T[0]).reshape(1, -1), (nf, lev.nx * lev.ny)))
         It = np.zeros((nf, lev.nx * lev.ny))
@@ -442,6 +444,68 @@ class TwoLevelProblem:
             U += uu
         self.fs_count[k] += 1
         return (Jbar.reshape(lev.shape), Jeff.reshape(lev.shape), U.reshape(lev.shape))
+
+    def _shifted(self, v, y, outside):
+        """v [nf, nvox] on the frequency grid, read at offsets y [nf, nvox] by
+        linear interpolation; beyond the grid the edge value (outside None)
+        or the constant ``outside``."""
+        nf = len(self.x)
+        if nf == 1:
+            return v.copy()
+        h = self.x[1] - self.x[0]
+        p = (y - self.x[0]) / h
+        i = np.clip(np.floor(p).astype(np.int64), 0, nf - 2)
+        t = p - i
+        out = (1.0 - t) * np.take_along_axis(v, i, axis=0) + \
+            t * np.take_along_axis(v, i + 1, axis=0)
+        lo, hi = p < 0.0, p > nf - 1
+        if outside is None:
+            return np.where(lo, v[:1], np.where(hi, v[-1:], out))
+        return np.where(lo | hi, outside, out)
+
+    def _formal_solution_moving_prd(self, k: int, lev, chi0, S, u):
+        """Partial redistribution in a flow (reading: redistribution in each
+        node's comoving frame, the hybrid treatment of Leenaarts, Pereira &
+        Uitenbroek 2012).  Along ray r the shift is s = mu_r . u.  The lagged
+        field is the comoving mean intensity J_cm(y) = sum_r w_r I_r(y + s),
+        I_r read at observer offset y + s by linear interpolation in
+        frequency (edge value beyond the grid); rho_cm follows from it as in
+        the static case, and the emission of ray r at observer offset x has
+        the ratio rho_cm(x - s) (1 beyond the grid).  Opacity and the
+        renormalised weights are those of the moving CRD solution; the MALI
+        sums treat rho as fixed, as in the static case."""
+        nvox = lev.nx * lev.ny * lev.nz
+        nf = len(self.phi)
+        wq = self.wphi / self.phi
+        rho_cm = self.prd_profile_ratio(k)
+        shp = (nf,) + lev.shape
+        Ib = self.planck(lev.T[0]).reshape(1, lev.ny, lev.nx)
+        Jbar, Jeff, U = (np.zeros(nvox) for _ in range(3))
+        Jcm = np.zeros((nf, nvox))
+        for r in range(len(self.wray)):
+            ur = self.mu[r] @ u
+            xs = self.x[:, None] - ur[None, :]                      # comoving offsets
+            prof = line_profile(xs, self.a_damp)
+            wphi = wq[:, None] * prof
+            wphi = wphi / wphi.sum(axis=0)
+            chi = chi0[None, :] * prof
+            rho = self._shifted(rho_cm, xs, 1.0)
+            Sf = rho * S[None, :]
+            Jx, Ux, Jm = formal_solution_nu_raw(lev.z, lev.dx, lev.dy, self.mu[r:r + 1],
+                                                self.wray[r:r + 1], chi.reshape(shp),
+                                                Sf.reshape(shp), Sf.reshape(shp),
+                                                rho.reshape(shp), Ib, 0.0, want_j=True,
+                                                interp=self.sc_interp)
+            Jx, Ux, Jm = (a.reshape(nf, -1) for a in (Jx, Ux, Jm))
+            Jbar += np.sum(wphi * Jm, axis=0)
+            Jeff += np.sum(wphi * Jx, axis=0)
+            U += np.sum(wphi * Ux, axis=0)
+            I_r = Jm / self.wray[r]
+            Jcm += self.wray[r] * self._shifted(I_r, self.x[:, None] + ur[None, :], None)
+        if self.updates_background(k):
+            self.jnu[k] = Jcm
+        self.fs_count[k] += 1
+        return Jbar.reshape(lev.shape), Jeff.reshape(lev.shape), U.reshape(lev.shape)
 
     # ---- statistical equilibrium (Eqs. 2-4) ----
     def rate_matrix(self, k: int, Jeff, U):

@@ -1,7 +1,7 @@
 """Pins of the oracle on variant combinations: a flow with the Hermite-spline
 upwind interpolation or with damped (Voigt) profiles, partial redistribution
-with the Hermite upwind interpolation, and the multi-level atom in a flow
-with the Hermite upwind.
+with the Hermite upwind interpolation or in a flow (redistribution in the
+comoving frame), and the multi-level atom in a flow with the Hermite upwind.
 
 Each combination reduces in a limit to a path pinned on its own (zero flow
 gives the static path, vanishing coherence gives CRD), follows the
@@ -286,3 +286,59 @@ def test_multilevel_hermite_flow_reversal_conservation_and_fas():
         if C < 1e-12:
             break
     assert O.max_rel_error(n_fas, n_mali) < 1e-9
+
+
+# ------------------------------ partial redistribution in a flow (two-level)
+
+def test_prd_in_a_flow_reduces_to_static_prd_and_moving_crd():
+    """Zero flow: the static PRD oracle (sweeps, a V-cycle, the lagged
+    field); vanishing coherence: the moving CRD oracle."""
+    atm, atom = _box(nx=4, nz=9, velocity=0.0, gamma=0.9)
+    ps = O.TwoLevelProblem(atm, atom, n_grids=2)
+    ns = ps.zero_radiation(2)
+    atm.vel = np.zeros((3,) + atm.shape)
+    pm = O.TwoLevelProblem(atm, atom, n_grids=2)
+    nm = pm.zero_radiation(2)
+    for _ in range(3):
+        ns, cs = ps.mali_sweep(2, ns)
+        nm, cm = pm.mali_sweep(2, nm)
+        assert abs(cm - cs) < 1e-12
+    ns, _ = ps.fas_cycle(ns, False, PARAMS)
+    nm, _ = pm.fas_cycle(nm, False, PARAMS)
+    assert O.max_rel_error(nm, ns) < 1e-12
+    assert np.allclose(pm.jnu[2], ps.jnu[2], rtol=1e-12)
+    atm2, atom2 = _box(nx=4, nz=9, gamma=1e-14)
+    atm3, atom3 = _box(nx=4, nz=9, gamma=0.0)
+    q = O.TwoLevelProblem(atm2, atom2)
+    q.jnu[1] = np.exp(np.random.default_rng(4).normal(size=q.jnu[1].shape))
+    n0 = q.zero_radiation(1)
+    q.jnu[1] = np.exp(np.random.default_rng(4).normal(size=q.jnu[1].shape))
+    got = q.formal_solution(1, n0)
+    ref = O.TwoLevelProblem(atm3, atom3).formal_solution(1, n0)
+    for a, b in zip(got, ref):
+        assert np.allclose(a, b, rtol=1e-12)
+
+
+def test_prd_in_a_uniform_flow_tends_to_static_prd():
+    """A uniform flow is a Galilean shift: with redistribution in the
+    comoving frame the converged populations approach the static PRD ones
+    at second order in the frequency step (linear interpolation in
+    frequency); a wrong sign in either frequency shift leaves a gap near
+    0.025 that refinement does not close."""
+    gaps = []
+    for n_freq in (41, 81):
+        atm, atom = _box(nx=4, nz=9, velocity=0.0, gamma=1.0, n_freq=n_freq, x_max=6.0)
+        n_static, _ = O.mali_solve(O.TwoLevelProblem(atm, atom), 1e-12)
+        atm.vel = np.empty((3,) + atm.shape)
+        atm.vel[0], atm.vel[1], atm.vel[2] = 0.4, -0.3, 0.6
+        n_flow, _ = O.mali_solve(O.TwoLevelProblem(atm, atom), 1e-12)
+        gaps.append(O.max_rel_error(n_flow, n_static))
+    assert gaps[1] < 3e-3 and gaps[1] < 0.3 * gaps[0], gaps
+
+
+def test_prd_in_a_flow_conserves_and_multigrid_agrees():
+    atm, atom = _box(nx=4, nz=9, eps=3e-2, gamma=0.9, n_freq=11, x_max=4.0)
+    n_prd = _agreement(atm, atom, interp=0)
+    atom.gamma_prd = 0.0
+    n_crd = _agreement(atm, atom, interp=0)
+    assert O.max_rel_error(n_prd, n_crd) > 1e-4
