@@ -290,14 +290,16 @@ def test_multilevel_hermite_flow_reversal_conservation_and_fas():
 
 # ------------------------------ partial redistribution in a flow (two-level)
 
-def test_prd_in_a_flow_reduces_to_static_prd_and_moving_crd():
+@pytest.mark.parametrize("interp", [0, 1])
+def test_prd_in_a_flow_reduces_to_static_prd_and_moving_crd(interp):
     """Zero flow: the static PRD oracle (sweeps, a V-cycle, the lagged
-    field); vanishing coherence: the moving CRD oracle."""
+    field) with either upwind interpolation; vanishing coherence: the moving
+    CRD oracle."""
     atm, atom = _box(nx=4, nz=9, velocity=0.0, gamma=0.9)
-    ps = O.TwoLevelProblem(atm, atom, n_grids=2)
+    ps = O.TwoLevelProblem(atm, atom, n_grids=2, sc_interp=interp)
     ns = ps.zero_radiation(2)
     atm.vel = np.zeros((3,) + atm.shape)
-    pm = O.TwoLevelProblem(atm, atom, n_grids=2)
+    pm = O.TwoLevelProblem(atm, atom, n_grids=2, sc_interp=interp)
     nm = pm.zero_radiation(2)
     for _ in range(3):
         ns, cs = ps.mali_sweep(2, ns)
