@@ -186,7 +186,8 @@ typedef struct {
     long long level_fs_timed_launches[MG3D_MAX_GRIDS + 1];
 } mg3d_counters;
 
-/* Message of the last failed call on this thread ("" if none). */
+/* Message of the last failed call on this thread ("" if none).
+ * No counterpart in the paper (error reporting). */
 const char *mg3d_last_error(void);
 
 /* Create a solver: validates the grid (Sec. 4.2; MG3D_E_GRID unless every
@@ -203,15 +204,18 @@ int mg3d_create(const mg3d_atmosphere *atm, const mg3d_atom *atom,
                 const mg3d_quadrature *quad, const mg3d_params *params,
                 mg3d_handle **out);
 
-/* Free every device and host resource of the handle (NULL is accepted). */
+/* Free every device and host resource of the handle (NULL is accepted).
+ * No counterpart in the paper (resource management). */
 int mg3d_destroy(mg3d_handle *h);
 
 /* Order the handle's work on an existing CUDA stream (a cudaStream_t passed
  * as void*; NULL restores the handle's own stream).  The caller keeps
- * ownership of the stream and must keep it alive while the handle uses it. */
+ * ownership of the stream and must keep it alive while the handle uses it.
+ * No counterpart in the paper (launch control). */
 int mg3d_set_stream(mg3d_handle *h, void *cuda_stream);
 
-/* Shape of a level's grid. */
+/* Shape of a level's grid.
+ * The levels are the grids of Sec. 2.2, coarsened as in Sec. 4.3. */
 int mg3d_level_shape(const mg3d_handle *h, int level, int *nx, int *ny, int *nz);
 
 /* Copy a level's populations [n_levels][nz][ny][nx] out to, or in from, host
@@ -220,7 +224,9 @@ int mg3d_level_shape(const mg3d_handle *h, int level, int *nx, int *ny, int *nz)
  * scattering (sigma_c) and of partial redistribution (gamma_prd) are not
  * part of them: a resumed handle restarts those from the state its creation
  * left (the zero-radiation field), and its next iterates differ from the
- * uninterrupted run until the fields have been recomputed. */
+ * uninterrupted run until the fields have been recomputed.
+ * n is the unknown of Eq. 4; checkpoint and resume have no counterpart in
+ * the paper. */
 int mg3d_get_populations(mg3d_handle *h, int level, double *n_host);
 int mg3d_set_populations(mg3d_handle *h, int level, const double *n_host);
 
@@ -252,10 +258,12 @@ int mg3d_residual(mg3d_handle *h, int level, double *r_host);
 int mg3d_fas_vcycle(mg3d_handle *h, int is_first, double *max_rel_change);
 
 /* Plain MALI on the finest grid from the zero-radiation start until C < tol
- * (MG3D_E_MAXITER after max_sweeps).  stats is nullable. */
+ * (MG3D_E_MAXITER after max_sweeps).  stats is nullable.
+ * Follows Sec. 2.1 and Sec. 3 (MALI), Sec. 4.11 (the start) and Sec. 3.3 (C). */
 int mg3d_mali_solve(mg3d_handle *h, double tol, int max_sweeps, mg3d_stats *stats);
 
-/* FAS V-cycles from the zero-radiation start until C(cycle) < tol. */
+/* FAS V-cycles from the zero-radiation start until C(cycle) < tol.
+ * Follows Sec. 2.2 (the V-cycle, Eqs. 5-11) and Sec. 3.3 (C). */
 int mg3d_fas_solve(mg3d_handle *h, double tol, int max_cycles, mg3d_stats *stats);
 
 /* Full multigrid (Sec. 2.3): nu_fmg MALI iterations on grid 1 from the
@@ -357,18 +365,21 @@ typedef struct {
 } mg3d_ml_atmosphere;
 
 /* Create a solver for a multi-level atom; everything else as mg3d_create.
- * Populations are [n_levels][nz][ny][nx] in every entry point. */
+ * Populations are [n_levels][nz][ny][nx] in every entry point.
+ * The atom, its opacities and rates follow Eqs. 1-4 and Sec. 3.2. */
 int mg3d_create_ml(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
                    const mg3d_quadrature *quad, const mg3d_params *params,
                    mg3d_handle **out);
 
-/* Levels of the handle's atom and its number of frequency points. */
+/* Levels of the handle's atom and its number of frequency points.
+ * No counterpart in the paper. */
 int mg3d_n_levels(const mg3d_handle *h, int *n_levels, int *n_freq);
 
 /* One multi-level formal solution: per frequency and node the angle sums
  * Jx = sum_r w_r (I - w0 S_t) and Ux = sum_r w_r (1 - w0 chi_t/chi), with S_t
  * the transition's part of the source function; host outputs
- * [n_freq][nz][ny][nx] (nullable).  MG3D_E_STATE on a two-level handle. */
+ * [n_freq][nz][ny][nx] (nullable).  MG3D_E_STATE on a two-level handle.
+ * The formal solution of Sec. 3 at every frequency of every transition. */
 int mg3d_formal_solve_ml(mg3d_handle *h, int level, double *jx_host, double *ux_host);
 
 /* Frequencies per chunk of the multi-level formal solution.  The opacity,
@@ -380,7 +391,8 @@ int mg3d_formal_solve_ml(mg3d_handle *h, int level, double *jx_host, double *ux_
  * the free device memory, else the largest chunk that does.  freq_per_chunk =
  * 0 means all frequencies.  Reallocates the chunk buffers (MG3D_E_OOM if they
  * do not fit); MG3D_E_STATE on a two-level handle.  Batch members need all
- * frequencies in one chunk. */
+ * frequencies in one chunk.
+ * No counterpart in the paper (memory layout). */
 int mg3d_set_ml_chunk(mg3d_handle *h, int freq_per_chunk);
 int mg3d_get_ml_chunk(const mg3d_handle *h, int *freq_per_chunk);
 
@@ -389,7 +401,8 @@ int mg3d_get_ml_chunk(const mg3d_handle *h, int *freq_per_chunk);
  * each block carries (a divisor of 12; fewer rays need less shared memory,
  * 2 x rays x rows x nx values, and give more blocks), threads per block (a
  * multiple of 32 up to 512).  The library picks one at creation (all 12 rays
- * where some band count fits); MG3D_E_ARG for shapes that do not fit. */
+ * where some band count fits); MG3D_E_ARG for shapes that do not fit.
+ * No counterpart in the paper (launch control). */
 int mg3d_set_ml_shape(mg3d_handle *h, int level, int bands, int rays_per_block, int threads);
 int mg3d_get_ml_shape(const mg3d_handle *h, int level, int *bands, int *rays_per_block,
                       int *threads);
@@ -409,15 +422,20 @@ typedef struct mg3d_batch mg3d_batch;
 int mg3d_batch_create(int n, mg3d_handle *const *members, mg3d_batch **out);
 int mg3d_batch_destroy(mg3d_batch *b);
 /* One lockstep V-cycle; max_rel_change (nullable) receives C of each member
- * ([n] doubles). */
+ * ([n] doubles).
+ * The V-cycle of Sec. 2.2 per member; batching has no counterpart in the
+ * paper. */
 int mg3d_batch_fas_vcycle(mg3d_batch *b, int is_first, double *max_rel_change);
 /* FAS from the zero-radiation start, or full multigrid, until every member's
  * change over a cycle is below tol; stats (nullable) is [n] (iterations: the
- * cycle at which each member first met tol). */
+ * cycle at which each member first met tol).
+ * FAS and FMG of Sec. 2.2-2.3 per member; batching has no counterpart in the
+ * paper. */
 int mg3d_batch_fas_solve(mg3d_batch *b, double tol, int max_cycles, mg3d_stats *stats);
 int mg3d_batch_fmg_solve(mg3d_batch *b, double tol, int max_cycles, mg3d_stats *stats);
 /* Kernel launches and formal-solution units (nodes x rays x frequencies)
- * of the batch so far. */
+ * of the batch so far.
+ * No counterpart in the paper (instrumentation). */
 int mg3d_batch_counters(const mg3d_batch *b, long long *kernel_launches, double *fs_units);
 
 /* Grid-transfer operators on host arrays of ncomp fields, for checking.
@@ -442,7 +460,8 @@ int mg3d_prolong(mg3d_handle *h, int level_fine, int ncomp, const double *coarse
  * memory for more resident blocks).
  * The library picks a shape at creation (at most 8 bands, staged); this
  * overrides it.  Returns MG3D_E_ARG if the shape does not fit in shared
- * memory or the GPU cannot hold one of its clusters. */
+ * memory or the GPU cannot hold one of its clusters.
+ * No counterpart in the paper (launch control). */
 int mg3d_set_fs_config(mg3d_handle *h, int level, int freq_per_block, int bands,
                        int threads, int lean, int stage);
 int mg3d_get_fs_config(const mg3d_handle *h, int level, int *freq_per_block, int *bands,
@@ -453,7 +472,8 @@ int mg3d_get_fs_config(const mg3d_handle *h, int level, int *freq_per_block, int
  * can hold at once (0: it cannot run; a sweep launches 24 x ceil(n_freq /
  * freq_per_block) clusters, so fewer than that means several waves), and
  * *smem_bytes = its dynamic shared memory per block.  Either output may be
- * NULL.  MG3D_E_ARG for shapes mg3d_set_fs_config would reject as invalid. */
+ * NULL.  MG3D_E_ARG for shapes mg3d_set_fs_config would reject as invalid.
+ * No counterpart in the paper (launch control). */
 int mg3d_get_fs_occupancy(mg3d_handle *h, int level, int freq_per_block, int bands,
                           int threads, int lean, int stage, int *max_clusters,
                           long long *smem_bytes);
@@ -468,13 +488,15 @@ int mg3d_get_fs_occupancy(mg3d_handle *h, int level, int freq_per_block, int ban
  * 1-4 equal passes, the three register budgets, staged or not, where the shape fits and
  * can be scheduled; one launch each,
  * then the best eight three more times.  Overwrites the partial sums (not the populations).
- * *evaluated and *seconds (nullable) report the candidates and wall time. */
+ * *evaluated and *seconds (nullable) report the candidates and wall time.
+ * No counterpart in the paper (launch control). */
 int mg3d_autotune(mg3d_handle *h, int level, int *evaluated, double *seconds);
 
 /* Check of the FP64 exponential the sweep uses: for each x_host[i] >= 0 the
  * GPU writes out_host[2i] = the sweep's e^{-x} and out_host[2i+1] = CUDA's
  * exp(-x), so callers can bound the difference.  Allocates temporary device
- * memory; out_host holds 2n doubles. */
+ * memory; out_host holds 2n doubles.
+ * A test of a building block; no counterpart in the paper. */
 int mg3d_check_exp(int n, const double *x_host, double *out_host);
 
 /* Check of the host-built line tables of a damped two-level atom (no GPU):
@@ -482,7 +504,8 @@ int mg3d_check_exp(int n, const double *x_host, double *out_host);
  * times sqrt(pi)) and out_host[2i+1] = the angle-averaged redistribution
  * R_II-A(x_host[i], xp_host[i]) (R_I-A for a = 0), as the frequency table and
  * the partial-redistribution matrix use them.  a >= 0; out_host holds 2n
- * doubles. */
+ * doubles.
+ * A test of a building block; no counterpart in the paper. */
 int mg3d_check_profiles(int n, double a, const double *x_host, const double *xp_host,
                         double *out_host);
 
@@ -492,18 +515,21 @@ int mg3d_check_profiles(int n, double a, const double *x_host, const double *xp_
  * out_host[i] = H(a_host[i], x_host[i]) with a_host[i] > 0; relative error
  * below 5e-14 + 2e-14/a (rounding, in the cancellation of the expansion's
  * two terms as a -> 0).  MG3D_E_ARG for n < 1, null pointers or a
- * non-positive (or non-finite) a; out_host holds n doubles. */
+ * non-positive (or non-finite) a; out_host holds n doubles.
+ * A test of a building block; no counterpart in the paper. */
 int mg3d_check_voigt(int n, const double *a_host, const double *x_host, double *out_host);
 
 /* Replay V-cycles from CUDA graphs (default on).  The first V-cycle of each
  * kind (first cycle / later cycles) is captured on the handle's stream and
  * later ones replay the graph; graphs are rebuilt after a change of stream or
  * sweep shapes or of the timing switch; with timing on, the graphs carry
- * the event records and each replay's sweep times are read back. */
+ * the event records and each replay's sweep times are read back.
+ * No counterpart in the paper (launch control). */
 int mg3d_set_graphs(mg3d_handle *h, int enable);
 
 /* Per-launch device timing of the sweep kernel (CUDA events on the handle's
- * stream) on or off, counters and their reset. */
+ * stream) on or off, counters and their reset.
+ * No counterpart in the paper (instrumentation). */
 int mg3d_set_timing(mg3d_handle *h, int enable);
 int mg3d_get_counters(mg3d_handle *h, mg3d_counters *out);
 int mg3d_reset_counters(mg3d_handle *h);

@@ -35,6 +35,24 @@ def test_header_declares_the_boundary():
         assert required in names
 
 
+def test_every_declaration_is_documented_with_its_passage():
+    """Each function of the header sits under a comment that cites the
+    passage of the paper it follows (Sec., Eq., Table or Fig.) or says that
+    it has no counterpart in the paper; grouped declarations share their
+    group's comment."""
+    with open(HEADER) as fh:
+        text = fh.read()
+    decls = list(re.finditer(r"^(?:int|const char|void)\s*\**\s*(mg3d_[a-z_0-9]+)\s*\(",
+                             text, flags=re.M))
+    assert {d.group(1) for d in decls} == set(declared_functions())
+    for d in decls:
+        before = text[:d.start()]
+        end = before.rfind("*/")
+        comment = before[before.rfind("/*", 0, end):end]
+        assert re.search(r"Sec\.|Eqs?\.|Table|Fig\.|no counterpart in the paper", comment,
+                         flags=re.I), d.group(1)
+
+
 def test_library_exports_every_declared_symbol(lib):
     for name in declared_functions():
         assert hasattr(lib, name), name
