@@ -309,3 +309,46 @@ def test_create_ml_refuses_bad_levels_grids_and_options(lib):
     with pytest.raises(m.MG3DError) as ei:
         m.mg3d_create_ml(synth.chromosphere(8, 8, 17, big), big, n_grids=1)
     assert ei.value.code == m.MG3D_E_ARG and "n_levels" in m.mg3d_last_error()
+
+
+def test_oracle_and_library_share_no_code():
+    """The product package never imports, includes or loads the oracle, and
+    the oracle never imports the package (inputs reach it as arguments);
+    bench.py reaches the oracle only inside its CPU-baseline and reference
+    functions."""
+    import ast
+    pkg = os.path.join(B.ROOT, "paper_1701_01607_gb300")
+    for root, _, files in os.walk(pkg):
+        if "_build" in root or "__pycache__" in root:
+            continue
+        for f in files:
+            path = os.path.join(root, f)
+            with open(path, encoding="utf-8", errors="replace") as fh:
+                src = fh.read()
+            if f.endswith(".py"):
+                for node in ast.walk(ast.parse(src)):
+                    if isinstance(node, (ast.Import, ast.ImportFrom)):
+                        mods = [a.name for a in node.names] if isinstance(node, ast.Import) \
+                            else [node.module or ""]
+                        assert not any(mo.split(".")[0] == "oracle" for mo in mods), path
+            elif f.endswith((".cu", ".cuh", ".h", ".cpp", ".c")):
+                assert not re.search(r'#include\s*[<"][^>"]*oracle', src), path
+                assert "liboracle" not in src, path
+    for f in os.listdir(os.path.join(B.ROOT, "oracle")):
+        if f.endswith((".py", ".c", ".h")):
+            with open(os.path.join(B.ROOT, "oracle", f)) as fh:
+                src = fh.read()
+            assert "paper_1701_01607_gb300" not in src.split('"""', 2)[-1], f
+            assert "libmg3d" not in src and "mg3d.h" not in src, f
+    with open(os.path.join(B.ROOT, "bench.py")) as fh:
+        tree = ast.parse(fh.read())
+    users = set()
+    for fn in ast.walk(tree):
+        if isinstance(fn, ast.FunctionDef):
+            for node in ast.walk(fn):
+                if isinstance(node, ast.ImportFrom) and (node.module or "").startswith("oracle"):
+                    users.add(fn.name)
+    top = [n for n in tree.body if isinstance(n, (ast.Import, ast.ImportFrom))]
+    assert not any(isinstance(n, ast.ImportFrom) and (n.module or "").startswith("oracle")
+                   for n in top)
+    assert users and all("cpu" in u or "reference" in u for u in users), users
