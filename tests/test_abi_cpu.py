@@ -352,3 +352,17 @@ def test_oracle_and_library_share_no_code():
     assert not any(isinstance(n, ast.ImportFrom) and (n.module or "").startswith("oracle")
                    for n in top)
     assert users and all("cpu" in u or "reference" in u for u in users), users
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No fallback: with the library absent every entry point raises before
+    computing anything."""
+    monkeypatch.setattr(m, "_lib", None)
+    monkeypatch.setattr(m, "library_path", lambda: str(tmp_path / "libmg3d.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        m.load()
+    atm, atom = synth.stratified_two_level(8, 8, 17, eps=1e-3)
+    with pytest.raises(RuntimeError, match="not built"):
+        m.mg3d_create(atm, atom, n_grids=1)
+    with pytest.raises(RuntimeError, match="not built"):
+        m.mg3d_check_voigt(0.1, np.zeros(3))
