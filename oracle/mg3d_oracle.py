@@ -1143,8 +1143,6 @@ class MultiLevelProblem(TwoLevelProblem):
                           if getattr(ln, "gamma_prd", 0.0) > 0.0]
         if self.prd_lines and fine.vel is not None:
             raise ValueError("partial redistribution takes a static atmosphere")
-        if any(getattr(atom.lines[ti], "a_damp", 0.0) > 0.0 for ti in self.prd_lines):
-            raise ValueError("partial redistribution of damped lines is not built")
         self._prd_tables = {}
         # the lagged mean intensity per frequency serves background scattering
         # and partial redistribution alike
@@ -1237,22 +1235,38 @@ class MultiLevelProblem(TwoLevelProblem):
     def prd_tables(self, k: int, ti: int):
         """For PRD line ti on grid k, per node: the redistribution matrix
         R[v, f', f] (R_I-A at the node's Doppler width d,
-        R0(x', x) = erfc(max(|x|, |x'|)/d)/(2 d^2), scaled symmetrically so
-        that its discrete marginals sum_f' wq R[f', f] are the node's profile,
-        the fixed point of ``prd_matrix`` node by node), the normalised
-        quadrature weights wq [v, f] and the profile phi [v, f]."""
+        R0(x', x) = erfc(max(|x|, |x'|)/d)/(2 d^2), or for a damped line
+        R_II-A(x/d, x'/d; a/d)/d^2, scaled symmetrically so that its discrete
+        marginals sum_f' wq R[f', f] are the node's profile, the fixed point
+        of ``prd_matrix`` node by node), the normalised quadrature weights
+        wq [v, f] and the profile phi [v, f]."""
         key = (k, ti)
         if key not in self._prd_tables:
             from scipy.special import erfc
             fs = self.line_freqs[ti]
+            a = float(getattr(self.atom.lines[ti], "a_damp", 0.0))
             x = np.array([self.freqs[f][2] for f in fs])
             w = np.array([self.freqs[f][3] for f in fs])
             d = np.sqrt(self.levels[k].T.reshape(-1) / self.atom.t_ref)
-            phi = ml_line_profile(x[None, :], d[:, None])
+            phi = ml_line_profile(x[None, :], d[:, None], a)
             wq = w[None, :] / (w[None, :] * phi).sum(axis=1)[:, None]
             ax = np.abs(x)
             dd = d[:, None, None]
-            R0 = 0.5 * erfc(np.maximum(ax[:, None], ax[None, :])[None, :, :] / dd) / dd ** 2
+            if a > 0.0:
+                # one table per distinct Doppler width (the kernel is costly)
+                R0 = np.empty((d.size, len(x), len(x)))
+                cache = {}
+                for v, dv in enumerate(d):
+                    if dv not in cache:
+                        t = np.empty((len(x), len(x)))
+                        for i in range(len(x)):
+                            for j in range(i, len(x)):
+                                t[i, j] = t[j, i] = redistribution_r2a(
+                                    x[i] / dv, x[j] / dv, a / dv) / dv ** 2
+                        cache[dv] = t
+                    R0[v] = cache[dv]
+            else:
+                R0 = 0.5 * erfc(np.maximum(ax[:, None], ax[None, :])[None, :, :] / dd) / dd ** 2
             c = np.ones_like(phi)
             for _ in range(200):
                 c = np.sqrt(c * phi / np.einsum("vab,va->vb", R0, wq * c))

@@ -401,10 +401,6 @@ def test_ml_prd_refusals():
     vatm = synth.chromosphere(8, 8, 17, atom, seed=2, velocity=1.0)
     with pytest.raises(ValueError, match="static"):
         O.MultiLevelProblem(vatm, atom)
-    damped = synth.hydrogen_like_atom(line_freq=7, cont_freq=4, seed=2, gamma_prd=1.0,
-                                      a_damp=0.01)
-    with pytest.raises(ValueError, match="damped"):
-        O.MultiLevelProblem(atm, damped)
 
 
 def test_ml_prd_with_background_scattering_shares_the_lagged_field():
@@ -424,3 +420,58 @@ def test_ml_prd_with_background_scattering_shares_the_lagged_field():
     n_mali, _ = O.mali_solve(O.MultiLevelProblem(atm, atom, n_grids=2), 1e-11)
     n_fas, _ = O.fas_solve(O.MultiLevelProblem(atm, atom, n_grids=2), 1e-10, params)
     assert O.max_rel_error(n_fas, n_mali) < 1e-8
+
+
+def test_ml_damped_prd_reduces_to_two_level_damped_prd():
+    """One damped PRD line at T = t_ref: the two-level oracle with R_II-A and
+    the Voigt profile, through MALI sweeps and a V-cycle."""
+    a, g = 0.05, 1.0
+    atom2 = synth.TwoLevelAtom(gamma_prd=g, a_damp=a, n_freq=9, x_max=4.0)
+    atm2, atom2 = synth.stratified_two_level(4, 4, 9, eps=1e-2, sigma=0.3, seed=4, atom=atom2)
+    line = synth.Line(0, 1, 1.0, atom2.a_ul, atom2.kappa, atom2.n_freq, atom2.x_max, a, g)
+    ml_atom = synth.MultiLevelAtom(g=np.array([1.0, 1.0]), theta=np.array([0.0, atom2.theta]),
+                                   theta_ref=atom2.theta, lines=[line], continua=[],
+                                   t_ref=5000.0)
+    c = np.zeros((2, 2) + atm2.shape)
+    c[1, 0] = atm2.c_ul
+    c[0, 1] = atm2.c_ul * np.exp(-atom2.theta / atm2.T)
+    ml_atm = synth.MultiLevelAtmosphere(atm2.nx, atm2.ny, atm2.nz, atm2.dx, atm2.dy, atm2.z,
+                                        atm2.T, atm2.n_tot, np.zeros(atm2.shape), c,
+                                        np.zeros((2,) + atm2.shape))
+    p2 = O.TwoLevelProblem(atm2, atom2, n_grids=2)
+    pm = O.MultiLevelProblem(ml_atm, ml_atom, n_grids=2)
+    n2, nm = p2.zero_radiation(2), pm.zero_radiation(2)
+    for _ in range(3):
+        n2, c2 = p2.mali_sweep(2, n2)
+        nm, cm = pm.mali_sweep(2, nm)
+        assert abs(cm - c2) < 1e-12
+    params = dict(nu_fmg=4, nu0=4, nu1=2, nu2=2, nu3=32)
+    n2, _ = p2.fas_cycle(n2, False, params)
+    nm, _ = pm.fas_cycle(nm, False, params)
+    assert O.max_rel_error(nm, n2) < 1e-12
+
+
+def test_ml_damped_prd_table_follows_the_continuous_kernel():
+    """At nodes of different Doppler widths d the damped table is
+    c_a R0(x_a, x_b) c_b with R0 = R_II-A(x/d, x'/d; a/d)/d^2; inside the grid
+    the symmetric factors stay near 1 (1 % here, where the Lorentz wings are
+    cut at 6 Doppler widths; 15 % or more with a wrong width scaling) and
+    the discrete marginals are the node's Voigt profile."""
+    a = 0.05
+    atom = synth.hydrogen_like_atom(line_freq=31, cont_freq=3, seed=2, gamma_prd=1.0,
+                                    a_damp=a, x_max=6.0)
+    atm = synth.chromosphere(1, 1, 3, atom, seed=2, ground_collisions=1e-3)
+    p = O.MultiLevelProblem(atm, atom)
+    ti = p.prd_lines[0]
+    R, wq, phi = p.prd_tables(1, ti)
+    x = np.array([p.freqs[f][2] for f in p.line_freqs[ti]])
+    d = np.sqrt(atm.T.reshape(-1) / atom.t_ref)
+    assert d.min() < 0.95 and d.max() > 1.3
+    kernel = lambda i, j, dv: O.redistribution_r2a(x[i] / dv, x[j] / dv, a / dv) / dv ** 2
+    inner = np.flatnonzero(np.abs(x) <= 3.0)
+    for v, dv in enumerate(d):
+        c = {i: math.sqrt(R[v, i, i] / kernel(i, i, dv)) for i in inner}
+        assert max(abs(ci - 1.0) for ci in c.values()) < 3e-2
+        for i, j in ((inner[0], inner[-1]), (inner[2], inner[len(inner) // 2])):
+            assert abs(R[v, i, j] / (c[i] * c[j] * kernel(i, j, dv)) - 1.0) < 1e-12
+    assert np.allclose(np.einsum("vab,va->vb", R, wq), phi, rtol=1e-12)
