@@ -229,6 +229,26 @@ def formal_solution_raw(z, dx, dy, mu, wray, chi, S, wphi, I_bottom, I_top,
     return Jbar, Jeff, U
 
 
+def read_shifted(v, y, x, outside):
+    """v [nf, nvox] given on the equidistant frequency grid x [nf], read at
+    offsets y [nf, nvox] by linear interpolation; beyond the grid the edge
+    value (outside None) or the constant ``outside``."""
+    nf = len(x)
+    if nf == 1:
+        return v.copy()
+    h = x[1] - x[0]
+    p = (y - x[0]) / h
+    i = np.clip(np.floor(p).astype(np.int64), 0, nf - 2)
+    t = np.clip(p - i, 0.0, 1.0)
+    out = (1.0 - t) * np.take_along_axis(v, i, axis=0) + t * np.take_along_axis(v, i + 1, axis=0)
+    # the end nodes belong to the grid even where rounding puts p a hair
+    # outside [0, nf - 1] (a spacing such as 8/6 is not exact)
+    lo, hi = p < -1e-9, p > nf - 1 + 1e-9
+    if outside is None:
+        return np.where(lo, v[:1], np.where(hi, v[-1:], out))
+    return np.where(lo | hi, outside, out)
+
+
 # --------------------------------------------------------------------------
 # One grid level
 # --------------------------------------------------------------------------
@@ -446,22 +466,8 @@ class TwoLevelProblem:
         return (Jbar.reshape(lev.shape), Jeff.reshape(lev.shape), U.reshape(lev.shape))
 
     def _shifted(self, v, y, outside):
-        """v [nf, nvox] on the frequency grid, read at offsets y [nf, nvox] by
-        linear interpolation; beyond the grid the edge value (outside None)
-        or the constant ``outside``."""
-        nf = len(self.x)
-        if nf == 1:
-            return v.copy()
-        h = self.x[1] - self.x[0]
-        p = (y - self.x[0]) / h
-        i = np.clip(np.floor(p).astype(np.int64), 0, nf - 2)
-        t = p - i
-        out = (1.0 - t) * np.take_along_axis(v, i, axis=0) + \
-            t * np.take_along_axis(v, i + 1, axis=0)
-        lo, hi = p < 0.0, p > nf - 1
-        if outside is None:
-            return np.where(lo, v[:1], np.where(hi, v[-1:], out))
-        return np.where(lo | hi, outside, out)
+        """``read_shifted`` on this atom's frequency grid."""
+        return read_shifted(v, y, self.x, outside)
 
     def _formal_solution_moving_prd(self, k: int, lev, chi0, S, u):
         """Partial redistribution in a flow (reading: redistribution in each
@@ -471,7 +477,11 @@ class TwoLevelProblem:
         I_r read at observer offset y + s by linear interpolation in
         frequency (edge value beyond the grid); rho_cm follows from it as in
         the static case, and the emission of ray r at observer offset x has
-        the ratio rho_cm(x - s) (1 beyond the grid).  Opacity and the
+        the ratio rho_cm(x - s) (1 beyond the grid), scaled per node and ray
+        so that the emission profile keeps sum_f w phi rho = 1 on the ray's
+        renormalised weights (photon conservation, exact in the static
+        case; without it the local operator overshoots where a shifted line
+        meets the grid's edge, and MALI loses positivity).  Opacity and the
         renormalised weights are those of the moving CRD solution; the MALI
         sums treat rho as fixed, as in the static case."""
         nvox = lev.nx * lev.ny * lev.nz
@@ -490,6 +500,9 @@ class TwoLevelProblem:
             wphi = wphi / wphi.sum(axis=0)
             chi = chi0[None, :] * prof
             rho = self._shifted(rho_cm, xs, 1.0)
+            # photons conserved per node and ray: sum_f w phi rho = 1 on the
+            # ray's renormalised weights, as in the static case
+            rho = rho / np.sum(wphi * rho, axis=0)[None, :]
             Sf = rho * S[None, :]
             Jx, Ux, Jm = formal_solution_nu_raw(lev.z, lev.dx, lev.dy, self.mu[r:r + 1],
                                                 self.wray[r:r + 1], chi.reshape(shp),
@@ -1141,8 +1154,9 @@ class MultiLevelProblem(TwoLevelProblem):
         # partial redistribution of lines with a coherence fraction
         self.prd_lines = [ti for ti, ln in enumerate(atom.lines)
                           if getattr(ln, "gamma_prd", 0.0) > 0.0]
-        if self.prd_lines and fine.vel is not None:
-            raise ValueError("partial redistribution takes a static atmosphere")
+        if self.prd_lines and fine.vel is not None and self.scatter:
+            raise ValueError("background scattering with partial redistribution in a flow "
+                             "is not built")
         self._prd_tables = {}
         # the lagged mean intensity per frequency serves background scattering
         # and partial redistribution alike
@@ -1401,6 +1415,12 @@ class MultiLevelProblem(TwoLevelProblem):
             if kind == "line":
                 line_freqs.setdefault(ti, []).append(f)
         shp = (nf,) + lev.shape
+        # partial redistribution in the comoving frame (the two-level reading):
+        # rho_cm per PRD line from the lagged comoving field, read by each ray
+        # at its comoving offsets; the rays' intensities build the new field
+        rho_cm = self.prd_ratios(k, n, terms) if self.prd_lines else {}
+        xgrid = {ti: np.array([self.freqs[f][2] for f in line_freqs[ti]]) for ti in rho_cm}
+        Jcm = {ti: np.zeros((len(line_freqs[ti]), nvox)) for ti in rho_cm}
         for r in range(len(self.wray)):
             ur = self.mu[r] @ u
             chi, S = terms["chi"].copy(), terms["S"].copy()
@@ -1413,13 +1433,21 @@ class MultiLevelProblem(TwoLevelProblem):
                 B = self.planck_rho(ln.rho, T)
                 phis = [ml_line_profile(self.freqs[f][2] - ur, d, ln.a_damp) for f in fs]
                 norm = sum(self.freqs[f][3] * ph for f, ph in zip(fs, phis))
-                for f, ph in zip(fs, phis):
+                if ti in rho_cm:
+                    xl = xgrid[ti]
+                    rho_r = read_shifted(rho_cm[ti], xl[:, None] - ur[None, :], xl, 1.0)
+                    # photons conserved per node and ray (the two-level reading)
+                    wl = np.array([self.freqs[f][3] for f in fs])[:, None] * np.array(phis) / norm
+                    rho_r = rho_r / np.sum(wl * rho_r, axis=0)[None, :]
+                else:
+                    rho_r = np.ones((len(fs), nvox))
+                for j, (f, ph) in enumerate(zip(fs, phis)):
                     chi_t = ln.kappa * ph * (nn[lo] * gr - nn[up])
-                    eta_t = ln.kappa * ln.rho ** 3 * ph * nn[up]
+                    eta_t = ln.kappa * ln.rho ** 3 * ph * nn[up] * rho_r[j]
                     chi[f] = chi_t + chi_c + sigma
                     S[f] = (eta_t + chi_c * B + sigma * self.jbg[k][f]) / chi[f]
                     sl[f] = eta_t / chi[f]
-                    fl[f] = chi_t / chi[f]
+                    fl[f] = rho_r[j] * chi_t / chi[f]
                     w[f] = self.freqs[f][3] * ph / norm
             res = formal_solution_nu_raw(lev.z, lev.dx, lev.dy, self.mu[r:r + 1],
                                          self.wray[r:r + 1], chi.reshape(shp), S.reshape(shp),
@@ -1429,6 +1457,10 @@ class MultiLevelProblem(TwoLevelProblem):
             Jw += w * res[0].reshape(nf, -1)
             Uw += w * res[1].reshape(nf, -1)
             Jm += res[2].reshape(nf, -1)
+            for ti in rho_cm:
+                xl = xgrid[ti]
+                I_r = res[2].reshape(nf, -1)[line_freqs[ti]] / self.wray[r]
+                Jcm[ti] += self.wray[r] * read_shifted(I_r, xl[:, None] + ur[None, :], xl, None)
         for ti, fs in line_freqs.items():
             ln = at.lines[ti]
             gr = at.g[ln.upper] / at.g[ln.lower]
@@ -1439,6 +1471,8 @@ class MultiLevelProblem(TwoLevelProblem):
                 terms["qe"][f] = ln.a_ul
         if self.updates_background(k):
             self.jbg[k] = Jm
+            for ti, jc in Jcm.items():
+                self.jbg[k][line_freqs[ti]] = jc
         self.fs_count[k] += 1
         return Jw, Uw, terms
 

@@ -335,7 +335,7 @@ def test_prd_in_a_uniform_flow_tends_to_static_prd():
         atm.vel[0], atm.vel[1], atm.vel[2] = 0.4, -0.3, 0.6
         n_flow, _ = O.mali_solve(O.TwoLevelProblem(atm, atom), 1e-12)
         gaps.append(O.max_rel_error(n_flow, n_static))
-    assert gaps[1] < 3e-3 and gaps[1] < 0.3 * gaps[0], gaps
+    assert gaps[1] < 1e-3 and gaps[1] < 0.3 * gaps[0], gaps
 
 
 def test_prd_in_a_flow_conserves_and_multigrid_agrees():
@@ -344,3 +344,19 @@ def test_prd_in_a_flow_conserves_and_multigrid_agrees():
     atom.gamma_prd = 0.0
     n_crd = _agreement(atm, atom, interp=0)
     assert O.max_rel_error(n_prd, n_crd) > 1e-4
+
+
+def test_prd_in_a_flow_keeps_mali_positive_when_scattering_dominates():
+    """eps = 1e-3, full coherence, a flow of rms 1 Doppler width on a grid
+    of +-3 widths: with the emission ratio scaled per node and ray to
+    conserve photons, MALI stays positive and converges (without that
+    scaling the second sweep already drives populations negative)."""
+    atm, atom = _box(nx=4, nz=17, eps=1e-3, velocity=1.0, gamma=1.0)
+    p = O.TwoLevelProblem(atm, atom)
+    n = p.zero_radiation(1)
+    for _ in range(200):
+        n, C = p.mali_sweep(1, n)
+        assert np.all(n > 0)
+        if C < 1e-8:
+            break
+    assert C < 1e-8

@@ -398,8 +398,8 @@ def test_ml_prd_conservation_multigrid_and_effect():
 
 def test_ml_prd_refusals():
     atm, atom = _ml_prd_box()
-    vatm = synth.chromosphere(8, 8, 17, atom, seed=2, velocity=1.0)
-    with pytest.raises(ValueError, match="static"):
+    vatm = synth.chromosphere(8, 8, 17, atom, seed=2, velocity=1.0, scattering=1.0)
+    with pytest.raises(ValueError, match="background scattering"):
         O.MultiLevelProblem(vatm, atom)
 
 
@@ -475,3 +475,49 @@ def test_ml_damped_prd_table_follows_the_continuous_kernel():
         for i, j in ((inner[0], inner[-1]), (inner[2], inner[len(inner) // 2])):
             assert abs(R[v, i, j] / (c[i] * c[j] * kernel(i, j, dv)) - 1.0) < 1e-12
     assert np.allclose(np.einsum("vab,va->vb", R, wq), phi, rtol=1e-12)
+
+
+def test_ml_prd_in_a_flow_reduces_to_two_level_moving_prd():
+    """One PRD line at T = t_ref in a flow: the two-level oracle with
+    comoving-frame redistribution (itself pinned by its zero-flow and
+    uniform-flow limits), through MALI sweeps and a V-cycle."""
+    (atm2, atom2), (ml_atm, ml_atom) = _two_level_pair(0.9, nx=4, nz=9)
+    vatm, _ = synth.stratified_two_level(4, 4, 9, eps=1e-2, sigma=0.3, seed=4, atom=atom2,
+                                         velocity=1.0)
+    atm2.vel = vatm.vel
+    ml_atm.vel = vatm.vel.copy()
+    p2 = O.TwoLevelProblem(atm2, atom2, n_grids=2)
+    pm = O.MultiLevelProblem(ml_atm, ml_atom, n_grids=2)
+    n2, nm = p2.zero_radiation(2), pm.zero_radiation(2)
+    for _ in range(3):
+        n2, c2 = p2.mali_sweep(2, n2)
+        nm, cm = pm.mali_sweep(2, nm)
+        assert abs(cm - c2) < 1e-12
+    params = dict(nu_fmg=4, nu0=4, nu1=2, nu2=2, nu3=32)
+    n2, _ = p2.fas_cycle(n2, False, params)
+    nm, _ = pm.fas_cycle(nm, False, params)
+    assert O.max_rel_error(nm, n2) < 1e-12
+
+
+def test_ml_prd_in_a_flow_zero_flow_conservation_and_fas():
+    atm, atom = _ml_prd_box(nx=4, nz=9)
+    ps = O.MultiLevelProblem(atm, atom)
+    ns = ps.zero_radiation(1)
+    atm.vel = np.zeros((3,) + atm.shape)
+    pm = O.MultiLevelProblem(atm, atom)
+    nm = pm.zero_radiation(1)
+    for _ in range(3):
+        ns, _ = ps.mali_sweep(1, ns)
+        nm, _ = pm.mali_sweep(1, nm)
+    assert O.max_rel_error(nm, ns) < 1e-10
+    vatm = synth.chromosphere(4, 4, 9, atom, seed=2, ground_collisions=1e-3, velocity=1.0)
+    p = O.MultiLevelProblem(vatm, atom, n_grids=2)
+    n = p.zero_radiation(2)
+    for _ in range(3):
+        n, _ = p.mali_sweep(2, n)
+        assert np.allclose(n.sum(axis=0), vatm.n_tot, rtol=1e-13)
+        assert np.all(n > 0)
+    params = dict(nu_fmg=8, nu0=10, nu1=2, nu2=4, nu3=16)
+    n_mali, _ = O.mali_solve(O.MultiLevelProblem(vatm, atom, n_grids=2), 1e-11)
+    n_fas, _ = O.fas_solve(O.MultiLevelProblem(vatm, atom, n_grids=2), 1e-10, params)
+    assert O.max_rel_error(n_fas, n_mali) < 1e-8
