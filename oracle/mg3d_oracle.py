@@ -1154,9 +1154,6 @@ class MultiLevelProblem(TwoLevelProblem):
         # partial redistribution of lines with a coherence fraction
         self.prd_lines = [ti for ti, ln in enumerate(atom.lines)
                           if getattr(ln, "gamma_prd", 0.0) > 0.0]
-        if self.prd_lines and fine.vel is not None and self.scatter:
-            raise ValueError("background scattering with partial redistribution in a flow "
-                             "is not built")
         self._prd_tables = {}
         # the lagged mean intensity per frequency serves background scattering
         # and partial redistribution alike
@@ -1167,6 +1164,9 @@ class MultiLevelProblem(TwoLevelProblem):
         nf = len(self.freqs)
         # background radiation field per grid, [nfreq, nvox]
         self.jbg = {k: np.zeros((nf, lev.nx * lev.ny * lev.nz)) for k, lev in self.levels.items()}
+        # in a flow, PRD lines keep their comoving mean intensity apart from
+        # the observer-frame field that background scattering reads
+        self.jcm = {k: {} for k in self.levels}
         # the grid a solve or V-cycle currently treats as its finest: only its
         # formal solutions update its background field (see coarse_entry)
         self.top = n_grids
@@ -1300,6 +1300,10 @@ class MultiLevelProblem(TwoLevelProblem):
         nvox = lev.nx * lev.ny * lev.nz
         nn = n.reshape(N, -1)
         J = self.jbg[k]
+        if self.jcm[k]:
+            J = J.copy()
+            for ti, jc in self.jcm[k].items():
+                J[self.line_freqs[ti]] = jc
         P = lev.c.reshape(N, N, nvox).copy()
         for f, (kind, ti, xv, wv) in enumerate(self.freqs):
             if kind == "line":
@@ -1373,6 +1377,8 @@ class MultiLevelProblem(TwoLevelProblem):
             fine = self.levels[k]
             jf = self.jbg[k].reshape((-1,) + fine.shape)
             self.jbg[k - 1] = restrict_fw(jf).reshape(jf.shape[0], -1)
+            self.jcm[k - 1] = {ti: restrict_fw(jc.reshape((-1,) + fine.shape)).reshape(
+                jc.shape[0], -1) for ti, jc in self.jcm[k].items()}
             self.lambda_iteration(k - 1, n_coarse)
 
     def fmg_prolong(self, k: int):
@@ -1382,6 +1388,8 @@ class MultiLevelProblem(TwoLevelProblem):
             coarse = self.levels[k - 1]
             jc = self.jbg[k - 1].reshape((-1,) + coarse.shape)
             self.jbg[k] = self.prolong(k, jc).reshape(jc.shape[0], -1)
+            self.jcm[k] = {ti: self.prolong(k, v.reshape((-1,) + coarse.shape)).reshape(
+                v.shape[0], -1) for ti, v in self.jcm[k - 1].items()}
 
     def formal_solution_moving(self, k: int, n):
         """Formal solution in a moving atmosphere (the same reading as for the
@@ -1471,8 +1479,7 @@ class MultiLevelProblem(TwoLevelProblem):
                 terms["qe"][f] = ln.a_ul
         if self.updates_background(k):
             self.jbg[k] = Jm
-            for ti, jc in Jcm.items():
-                self.jbg[k][line_freqs[ti]] = jc
+            self.jcm[k] = Jcm
         self.fs_count[k] += 1
         return Jw, Uw, terms
 
@@ -1526,6 +1533,7 @@ class MultiLevelProblem(TwoLevelProblem):
             # the lagged field from nothing: cleared (rho = 1 for partial
             # redistribution); with background scattering one Lambda-iteration
             self.jbg[k] = np.zeros((nf, nvox))
+            self.jcm[k] = {}
             if self.scatter:
                 self.lambda_iteration(k, n)
         return n

@@ -396,11 +396,34 @@ def test_ml_prd_conservation_multigrid_and_effect():
     assert O.max_rel_error(n_crd, n_mali) > 1e-4
 
 
-def test_ml_prd_refusals():
-    atm, atom = _ml_prd_box()
-    vatm = synth.chromosphere(8, 8, 17, atom, seed=2, velocity=1.0, scattering=1.0)
-    with pytest.raises(ValueError, match="background scattering"):
-        O.MultiLevelProblem(vatm, atom)
+def test_ml_prd_in_a_flow_with_background_scattering():
+    """In a flow the PRD lines keep their comoving field apart from the
+    observer-frame field that background scattering reads: zero flow equals
+    the static path, MALI stays positive, FAS meets MALI."""
+    atom = synth.hydrogen_like_atom(line_freq=7, cont_freq=4, seed=2, gamma_prd=1.0)
+    atm = synth.chromosphere(4, 4, 9, atom, seed=2, ground_collisions=1e-3, scattering=1.0)
+    ps = O.MultiLevelProblem(atm, atom)
+    ns = ps.zero_radiation(1)
+    atm.vel = np.zeros((3,) + atm.shape)
+    pm = O.MultiLevelProblem(atm, atom)
+    nm = pm.zero_radiation(1)
+    for _ in range(3):
+        ns, _ = ps.mali_sweep(1, ns)
+        nm, _ = pm.mali_sweep(1, nm)
+    assert O.max_rel_error(nm, ns) < 1e-10
+    assert set(pm.jcm[1]) == set(pm.prd_lines) and not ps.jcm[1]
+    vatm = synth.chromosphere(4, 4, 9, atom, seed=2, ground_collisions=1e-2, scattering=1.0,
+                              velocity=1.0)
+    p = O.MultiLevelProblem(vatm, atom, n_grids=2)
+    n = p.zero_radiation(2)
+    for _ in range(3):
+        n, _ = p.mali_sweep(2, n)
+        assert np.allclose(n.sum(axis=0), vatm.n_tot, rtol=1e-13)
+        assert np.all(n > 0)
+    params = dict(nu_fmg=8, nu0=10, nu1=2, nu2=4, nu3=16)
+    n_mali, _ = O.mali_solve(O.MultiLevelProblem(vatm, atom, n_grids=2), 1e-11)
+    n_fas, _ = O.fas_solve(O.MultiLevelProblem(vatm, atom, n_grids=2), 1e-10, params)
+    assert O.max_rel_error(n_fas, n_mali) < 1e-8
 
 
 def test_ml_prd_with_background_scattering_shares_the_lagged_field():
