@@ -956,10 +956,17 @@ def main():
     ap.add_argument("--profile-ml", choices=["f64", "f32"],
                     help="only run a few multi-level MALI sweeps (for ncu)")
     ap.add_argument("--profile-launches", type=int, default=3)
+    ap.add_argument("--peaks", action="store_true",
+                    help="only measure the FP32/MUFU/FP64 peak rates (mg3d_probe_alu_peaks)")
     ap.add_argument("--profile-shape", default="",
                     help="ng,bands,threads[,lean[,stage]] of the profiled sweep, or "
                          "bands,rays_per_block,threads with --profile-ml")
     args = ap.parse_args()
+    if args.peaks:
+        from paper_1701_01607_gb300 import mg3d as m
+        m.load(build_if_missing=True)
+        print(json.dumps({k: v / 1e12 for k, v in m.mg3d_probe_alu_peaks(5).items()}), flush=True)
+        return
     if args.profile_sweep:
         run_profile_case(args.profile_sweep, args.profile_launches, args.profile_shape)
         return

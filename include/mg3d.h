@@ -534,6 +534,19 @@ int mg3d_set_timing(mg3d_handle *h, int enable);
 int mg3d_get_counters(mg3d_handle *h, mg3d_counters *out);
 int mg3d_reset_counters(mg3d_handle *h);
 
+/* Peak rates of the arithmetic the formal solution runs on, measured on the
+ * current device: out_host[0] FP32 fused multiply-adds, out_host[1] ex2 and
+ * out_host[2] rcp approximations (the FP32 e^-x and 1/x), out_host[3] FP64
+ * fused multiply-adds, each in thread operations per second.  Each kernel
+ * runs eight independent chains per thread on 8 blocks of 256 threads per SM;
+ * one warm-up launch, then the fastest of `reps` (1..100) launches timed with
+ * CUDA events on the legacy default stream (the call synchronises).
+ * Allocates a small device buffer.  The sweep kernels are bound by these
+ * pipes rather than by memory; the rates are the denominators of their
+ * roofline.  Changes no clock or other device setting.
+ * No counterpart in the paper (measurement aid). */
+int mg3d_probe_alu_peaks(int reps, double *out_host);
+
 /* Allocation-free formal solution.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory at the moment
  * they need a formal solution -- code running under another framework's

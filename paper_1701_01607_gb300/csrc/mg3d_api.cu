@@ -28,6 +28,7 @@
 #include "mg3d.h"
 #include "profiles.h"
 #include "mg3d_internal.h"
+#include "sc_step.cuh"
 
 using namespace mg3d;
 
@@ -81,6 +82,7 @@ struct Level {
     // intensity [kRays][nf][nvox]
     void *jnu = nullptr, *jnu_new = nullptr, *rho = nullptr, *rhoS = nullptr;
     StepGeom *geom = nullptr;    // [kRays][nz]
+    void *psteps = nullptr;      // [kRays][nz] PlaneStep<T> of the shifted-plane sweep
     SweepShape shape{};
     // multi-level atom only
     double *chi_c = nullptr;     // [nvox] background opacity
@@ -137,6 +139,9 @@ struct mg3d_handle {
     // frequency tables of the sweep, [order][phi, 1/phi, w phi / 24][n_freq]
     // in the formal-solution precision (see freq_tables)
     void *d_ftab = nullptr;
+    // slot tables of the shifted-plane sweep, one per slot count kPlaneNp[i]:
+    // [ceil(n_freq / (2 np))][np] PlaneSlot<T>
+    void *d_pslot[kPlaneNpCount] = {};
     void *d_vtab = nullptr;      // moving atmospheres: [nf] offsets x, [nf] weights w
     int *d_vline = nullptr;      // multi-level, moving: line index of each frequency or -1
     bool prd = false;            // two-level partial redistribution
@@ -296,6 +301,107 @@ void build_geometry(const mg3d_handle *h, const Level &L, std::vector<StepGeom> 
     }
 }
 
+// Per-step constants of the shifted-plane sweep from the upwind geometry:
+// the bilinear weights and half path of step t, and the corner offsets of
+// step t+1 as the shift of the plane written at step t.
+template <typename T>
+std::vector<PlaneStep<T>> plane_steps(const Level &L, const std::vector<StepGeom> &g) {
+    std::vector<PlaneStep<T>> out((size_t)kRays * L.nz);
+    for (int r = 0; r < kRays; ++r)
+        for (int t = 0; t < L.nz; ++t) {
+            const StepGeom &e = g[(size_t)r * L.nz + t];
+            PlaneStep<T> &p = out[(size_t)r * L.nz + t];
+            p.w00 = (T)((1.0 - e.tx) * (1.0 - e.ty));
+            p.w10 = (T)(e.tx * (1.0 - e.ty));
+            p.w01 = (T)((1.0 - e.tx) * e.ty);
+            p.w11 = (T)(e.tx * e.ty);
+            p.half_s = (T)(0.5 * e.s);
+            const bool last = t + 1 >= L.nz;
+            p.sx = last ? 0 : g[(size_t)r * L.nz + t + 1].ix0;
+            p.sy = last ? 0 : g[(size_t)r * L.nz + t + 1].iy0;
+        }
+    return out;
+}
+
+int plane_np_index(int np) {
+    for (int i = 0; i < kPlaneNpCount; ++i)
+        if (kPlaneNp[i] == np) return i;
+    return -1;
+}
+
+// Launch arguments of the shifted-plane sweep of level L with shape s.
+template <typename T>
+PlaneArgs<T> plane_args(const mg3d_handle *h, const Level &L, const SweepShape &s) {
+    const int nf = h->atom.n_freq;
+    const int last = nf - (s.ngroups - 1) * 2 * s.np;   // frequencies of the last group
+    PlaneArgs<T> a{};
+    a.nx = L.nx;
+    a.ny = L.ny;
+    a.nz = L.nz;
+    a.rows = s.rows;
+    a.bands = s.bands;
+    a.ngroups = s.ngroups;
+    a.nslot_last = (last + 1) / 2;
+    a.up_mask = h->up_mask;
+    a.rmagic = band_magic(s.rows);
+    a.xmagic = band_magic(L.nx);
+    a.chi0 = (const T *)L.chi0;
+    a.S = (const T *)L.S;
+    a.bbot = (const T *)L.bbot;
+    a.steps = (const PlaneStep<T> *)L.psteps;
+    a.slots = (const PlaneSlot<T> *)h->d_pslot[plane_np_index(s.np)];
+    a.pj = (T *)h->pj;
+    a.pu = (T *)h->pu;
+    a.exp_tab = h->d_exp_tab;
+    a.exp_l1 = h->exp_l1;
+    a.exp_l2 = h->exp_l2;
+    return a;
+}
+
+int dev_alloc(void **p, size_t bytes);
+
+// Slot tables of the shifted-plane sweep for every supported slot count:
+// group g takes the table positions [2 np g, 2 np (g + 1)) of mirror order 0
+// (x_0, x_{nf-1}, x_1, x_{nf-2}, ..., centre last), slot p of the group the
+// positions 2p and 2p + 1, so mirror pairs share a slot.
+template <typename T>
+int build_plane_slots(mg3d_handle *h) {
+    const int nf = h->atom.n_freq;
+    for (int i = 0; i < kPlaneNpCount; ++i) {
+        const int np = kPlaneNp[i];
+        const int ngroups = (nf + 2 * np - 1) / (2 * np);
+        std::vector<PlaneSlot<T>> tab((size_t)ngroups * np);
+        for (int g = 0; g < ngroups; ++g)
+            for (int p = 0; p < np; ++p) {
+                PlaneSlot<T> &e = tab[(size_t)g * np + p];
+                e = PlaneSlot<T>{};
+                const int ja = 2 * np * g + 2 * p, jb = ja + 1;
+                if (ja >= nf) continue;   // inactive slot of the last group
+                const int ia = mirror_order(nf, 0, ja);
+                e.phi_a = (T)h->phi[ia];
+                e.iphi_a = (T)(1.0 / h->phi[ia]);
+                e.wphi_a = (T)(h->wphi[ia] / kRays);
+                e.wu_a = e.wphi_a;
+                if (jb < nf) {
+                    const int ib = mirror_order(nf, 0, jb);
+                    e.flags = plane::kHasB;
+                    e.phi_b = (T)h->phi[ib];
+                    e.iphi_b = (T)(1.0 / h->phi[ib]);
+                    e.wphi_b = (T)(h->wphi[ib] / kRays);
+                    e.wu_b = e.wphi_b;
+                    if (h->phi[ib] == h->phi[ia]) {
+                        e.flags |= plane::kShared;
+                        e.wu_a = (T)((h->wphi[ia] + h->wphi[ib]) / kRays);
+                    }
+                }
+            }
+        MG_TRY(dev_alloc(&h->d_pslot[i], tab.size() * sizeof(PlaneSlot<T>)));
+        MG_CUDA(cudaMemcpy(h->d_pslot[i], tab.data(), tab.size() * sizeof(PlaneSlot<T>),
+                           cudaMemcpyHostToDevice));
+    }
+    return MG3D_OK;
+}
+
 // Threads per block for a band of `band` nodes: as few passes of at most
 // kMaxSweepThreads threads as possible, split evenly, rounded to warps.
 int threads_for_band(int band) {
@@ -309,7 +415,76 @@ int threads_for_band(int band) {
 // the number of bands that brings the grid closest to two blocks per SM (the
 // shapes measured fastest on the 64x64 planes of the bench workload, in both
 // precisions, were of this kind); mg3d_autotune replaces it by measurement.
-SweepShape choose_shape(int prec, int nx, int ny, int nfreq, int herm, int vel, int prd) {
+// Slot count of the shifted-plane sweep that takes all n_freq frequencies in
+// one group (0 when more than 16 frequencies need several groups).
+int plane_np_for(int nfreq) {
+    for (int i = 0; i < kPlaneNpCount; ++i)
+        if (2 * kPlaneNp[i] >= nfreq) return kPlaneNp[i];
+    return 0;
+}
+
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            n = 1;
+        }
+    }
+    return n;
+}
+
+// How many clusters of shape s the GPU holds at once (plain launches: blocks).
+int shape_capacity(int prec, const SweepShape &s, int nx) {
+    int n = 0;
+    const cudaError_t e = s.plane ? plane_active_clusters(prec, s, nx, &n)
+                                  : sweep_active_clusters(prec, s, nx, &n);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return s.bands == 1 ? n * sm_count() : n;
+}
+
+// Default shifted-plane shape: all frequencies in one group when they fit in
+// 16 (else groups of 16), and the most bands (up to 8) whose 24 x groups
+// clusters the GPU holds in one wave; mg3d_autotune replaces it by measurement.
+SweepShape choose_plane_shape(int prec, int nx, int ny, int nfreq) {
+    int np = plane_np_for(nfreq);
+    if (np == 0) np = kPlaneNp[kPlaneNpCount - 1];
+    const int ngroups = (nfreq + 2 * np - 1) / (2 * np);
+    SweepShape best{}, fallback{};
+    for (int bands = 1; bands <= kPortableBands && bands <= ny; ++bands) {
+        const int rows = (ny + bands - 1) / bands;
+        if ((long)(bands - 1) * rows >= ny) continue;
+        if (plane_smem_bytes(prec, np, rows, nx) > kMaxPlaneSmem) continue;
+        SweepShape s{2 * np, ngroups, bands, rows, threads_for_band(rows * nx)};
+        if ((long)rows * nx > (long)plane_max_pass(np, prec == MG3D_PREC_F64) * s.threads)
+            continue;
+        s.stage = 0;
+        s.plane = 1;
+        s.np = np;
+        const int cap = shape_capacity(prec, s, nx);
+        if (cap < 1) continue;
+        if (fallback.ng == 0) fallback = s;
+        if (cap >= kRays * ngroups) best = s;
+    }
+    return best.ng ? best : fallback;
+}
+
+// Grids the shifted-plane sweep's 32-bit node indices cover.
+bool plane_grid_ok(int nx, int ny, int nz) {
+    return (long)nx * ny * nx < (1L << 32) && (long)nx * ny * nz < (1L << 31);
+}
+
+SweepShape choose_shape(int prec, int nx, int ny, int nz, int nfreq, int herm, int vel,
+                        int prd) {
+    if (!herm && !vel && !prd && plane_grid_ok(nx, ny, nz)) {
+        const SweepShape s = choose_plane_shape(prec, nx, ny, nfreq);
+        if (s.ng) return s;
+    }
     const int ng = nfreq < 3 ? nfreq : 3;
     const int ngroups = (nfreq + ng - 1) / ng;
     SweepShape best{};
@@ -370,7 +545,7 @@ void free_level(Level &L) {
                     L.r,     L.chi0,  L.S,    L.bbot, L.geom, L.chi_c, L.cmat, L.saha,
                     L.mchi,  L.mS,    L.msl,  L.mfl,  L.mib,  L.sigma_c, L.jbg,
                     L.dchi0, L.dS,   L.mdchi, L.mdS,  L.vel,  L.uproj, L.vnorm, L.dinv,
-                    L.jnu,   L.jnu_new, L.rho, L.rhoS};
+                    L.jnu,   L.jnu_new, L.rho, L.rhoS, L.psteps};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     L = Level{};
@@ -564,6 +739,18 @@ int prd_prepare(mg3d_handle *h, int k) {
     return MG3D_OK;
 }
 
+// The sweep launch of level L with shape s (shifted-plane or band sweep).
+cudaError_t launch_level_sweep(const mg3d_handle *h, const Level &L, const SweepShape &s) {
+    if (s.plane) {
+        if (h->prec == MG3D_PREC_F64)
+            return launch_plane_sweep_f64(plane_args<double>(h, L, s), s, h->stream);
+        return launch_plane_sweep_f32(plane_args<float>(h, L, s), s, h->stream);
+    }
+    if (h->prec == MG3D_PREC_F64)
+        return launch_sweep_f64(sweep_args<double>(h, L, s), s, h->stream);
+    return launch_sweep_f32(sweep_args<float>(h, L, s), s, h->stream);
+}
+
 // Formal solution on level k with its populations: partial sums into pj/pu.
 int formal_solution(mg3d_handle *h, int k) {
     if (h->kind == 1) return ml_formal_solution(h, k);
@@ -582,13 +769,7 @@ int formal_solution(mg3d_handle *h, int k) {
         tl.b = pool_event(h);
         MG_CUDA(record_event(tl.a, h->stream));
     }
-    cudaError_t e;
-    if (h->prec == MG3D_PREC_F64) {
-        e = launch_sweep_f64(sweep_args<double>(h, L, L.shape), L.shape, h->stream);
-    } else {
-        e = launch_sweep_f32(sweep_args<float>(h, L, L.shape), L.shape, h->stream);
-    }
-    MG_TRY(launched(h, e, "sweep"));
+    MG_TRY(launched(h, launch_level_sweep(h, L, L.shape), "sweep"));
     if (h->timing) {
         MG_CUDA(record_event(tl.b, h->stream));
         h->timed.push_back(tl);
@@ -931,15 +1112,65 @@ int make_shape(const mg3d_handle *h, int k, int ng, int bands, int threads, Swee
     return MG3D_OK;
 }
 
+// Shifted-plane shape (stage 2) of the given launch parameters: freq_per_block
+// >= n_freq takes all frequencies in one group (at most 16), else it must be
+// twice a supported slot count (2, 4, 6, 10 or 16).
+static int plane_shape_from_args(const mg3d_handle *h, int level, int freq_per_block, int bands,
+                                 int threads, int lean, SweepShape *out) {
+    const Level &L = h->lev[level];
+    const int nf = h->atom.n_freq;
+    if (h->params.sc_interp || h->moving || h->prd)
+        return fail(MG3D_E_ARG, "the shifted-plane sweep (stage 2) takes static atmospheres in "
+                                "complete redistribution with linear upwind interpolation");
+    if (!plane_grid_ok(L.nx, L.ny, L.nz))
+        return fail(MG3D_E_ARG, "grid too large for the shifted-plane sweep");
+    int np = 0;
+    if (freq_per_block >= nf) {
+        np = plane_np_for(nf);
+        if (np == 0)
+            return fail(MG3D_E_ARG, "more than 16 frequencies: the shifted-plane sweep takes "
+                                    "2, 4, 6, 10 or 16 frequencies per block");
+    } else if (freq_per_block >= 1 && freq_per_block % 2 == 0 &&
+               plane_np_supported(freq_per_block / 2)) {
+        np = freq_per_block / 2;
+    } else {
+        return fail(MG3D_E_ARG, "the shifted-plane sweep takes all frequencies or 2, 4, 6, 10 "
+                                "or 16 per block");
+    }
+    if (bands < 1 || bands > kMaxBands || bands > L.ny || threads < 32 ||
+        threads > kPlaneMaxThreads || threads % 32)
+        return fail(MG3D_E_ARG, "bad sweep shape");
+    if (lean < 0 || lean > 1 || (lean == 1 && h->prec == MG3D_PREC_F64))
+        return fail(MG3D_E_ARG, "the shifted-plane sweep takes lean 0, or 1 in FP32");
+    if (threads > 512 && (h->prec == MG3D_PREC_F64 || lean != 0 || np > 2))
+        return fail(MG3D_E_ARG, "blocks above 512 threads: FP32, lean 0, at most 4 frequencies "
+                                "per block");
+    SweepShape s{2 * np, (nf + 2 * np - 1) / (2 * np), bands, (L.ny + bands - 1) / bands, threads};
+    if ((long)(bands - 1) * s.rows >= L.ny) return fail(MG3D_E_ARG, "empty band");
+    if ((long)s.rows * L.nx > (long)plane_max_pass(np, h->prec == MG3D_PREC_F64) * threads)
+        return fail(MG3D_E_ARG, "too few threads for the band (the shifted-plane sweep takes at "
+                                "most " + std::to_string(plane_max_pass(np, h->prec == MG3D_PREC_F64)) +
+                                " nodes per thread)");
+    s.lean = lean;
+    s.stage = 0;
+    s.plane = 1;
+    s.np = np;
+    if (plane_smem_bytes(h->prec, np, s.rows, L.nx) > kMaxPlaneSmem)
+        return fail(MG3D_E_ARG, "sweep shape exceeds shared memory");
+    *out = s;
+    return MG3D_OK;
+}
+
 // Shape of the given launch parameters on a level, validated except for
 // whether the GPU can schedule it.
 static int shape_from_args(const mg3d_handle *h, int level, int freq_per_block, int bands,
                            int threads, int lean, int stage, SweepShape *out) {
     MG_TRY(check_level(h, level));
     if (h->kind != 0) return fail(MG3D_E_STATE, "sweep shapes apply to two-level handles");
+    if (stage == 2) return plane_shape_from_args(h, level, freq_per_block, bands, threads, lean, out);
     if (lean < 0 || lean > 2 || (lean == 2 && threads > 256))
         return fail(MG3D_E_ARG, "lean must be 0, 1 or (up to 256 threads) 2");
-    if (stage != 0 && stage != 1) return fail(MG3D_E_ARG, "stage must be 0 or 1");
+    if (stage != 0 && stage != 1) return fail(MG3D_E_ARG, "stage must be 0, 1 or 2");
     if (stage && h->params.sc_interp)
         return fail(MG3D_E_ARG, "Hermite upwind interpolation runs unstaged (stage 0)");
     if (stage && h->moving) return fail(MG3D_E_ARG, "moving atmospheres run unstaged (stage 0)");
@@ -959,7 +1190,8 @@ static int shape_from_args(const mg3d_handle *h, int level, int freq_per_block, 
 // k (clusters of more than 8 blocks are not guaranteed to fit).
 int check_schedulable(const mg3d_handle *h, int k, const SweepShape &s) {
     int n = 0;
-    const cudaError_t e = sweep_active_clusters(h->prec, s, h->lev[k].nx, &n);
+    const cudaError_t e = s.plane ? plane_active_clusters(h->prec, s, h->lev[k].nx, &n)
+                                  : sweep_active_clusters(h->prec, s, h->lev[k].nx, &n);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(MG3D_E_ARG,
@@ -1006,11 +1238,7 @@ int time_shape(mg3d_handle *h, int k, const SweepShape &s, int reps, float *ms) 
     int rc = MG3D_OK;
     cudaError_t e = cudaEventRecord(a, h->stream);
     for (int i = 0; i < reps && e == cudaSuccess; ++i) {
-        if (h->prec == MG3D_PREC_F64) {
-            e = launch_sweep_f64(sweep_args<double>(h, L, s), s, h->stream);
-        } else {
-            e = launch_sweep_f32(sweep_args<float>(h, L, s), s, h->stream);
-        }
+        e = launch_level_sweep(h, L, s);
         ++h->launches;
     }
     if (e == cudaSuccess) e = cudaEventRecord(b, h->stream);
@@ -1027,11 +1255,48 @@ int time_shape(mg3d_handle *h, int k, const SweepShape &s, int reps, float *ms) 
 // Time candidate sweep shapes of level k with its current populations and
 // keep the fastest: every (frequencies per block, bands, threads) that fits,
 // one launch each, then the best eight again three times each.
+// Shifted-plane candidates of level k: one group (the fewest slots that take
+// every frequency) and every smaller supported slot count with at most 8
+// groups; 1-16 bands; 32-512 threads in powers of two and the block sizes
+// that cover a band in 1-4 equal passes; in FP32 both register budgets.
+void plane_candidates(mg3d_handle *h, int k, std::vector<SweepShape> &cands) {
+    const Level &L = h->lev[k];
+    const int nf = h->atom.n_freq;
+    for (int i = 0; i < kPlaneNpCount; ++i) {
+        const int np = kPlaneNp[i];
+        const int groups = (nf + 2 * np - 1) / (2 * np);
+        if (groups > 8) continue;
+        if (groups == 1 && np != plane_np_for(nf)) continue;   // one-group: fewest slots
+        const int fpb = groups == 1 ? nf : 2 * np;
+        for (int bands = 1; bands <= kMaxBands && bands <= L.ny; ++bands) {
+            const int band = ((L.ny + bands - 1) / bands) * L.nx;
+            std::vector<int> ths = {32, 64, 128, 256, 512, 1024};
+            for (int passes = 1; passes <= plane_max_pass(np, h->prec == MG3D_PREC_F64); ++passes) {
+                const int th = ((band + passes - 1) / passes + 31) / 32 * 32;
+                if (th <= kPlaneMaxThreads && std::find(ths.begin(), ths.end(), th) == ths.end())
+                    ths.push_back(th);
+            }
+            for (int th : ths)
+                for (int lean = 0; lean < (h->prec == MG3D_PREC_F64 ? 1 : 2); ++lean) {
+                    if (th > 32 && th / 2 >= band) continue;  // a smaller block covers it
+                    SweepShape s;
+                    if (plane_shape_from_args(h, k, fpb, bands, th, lean, &s) != MG3D_OK)
+                        continue;
+                    if (check_schedulable(h, k, s) != MG3D_OK) continue;
+                    cands.push_back(s);
+                }
+        }
+    }
+}
+
 int autotune_level(mg3d_handle *h, int k, int *evaluated) {
     Level &L = h->lev[k];
     const int nf = h->atom.n_freq;
+    const bool plane_ok = !h->params.sc_interp && !h->moving && !h->prd &&
+                          plane_grid_ok(L.nx, L.ny, L.nz);
+    // band-sweep frequency groupings (variants the shifted-plane sweep does not take)
     std::vector<int> ngs;
-    for (int ng = 1; ng <= nf; ++ng) {
+    for (int ng = 1; ng <= nf && !plane_ok; ++ng) {
         const int groups = (nf + ng - 1) / ng;
         if (groups > 64) continue;
         // one ng per distinct group count, the smallest that gives it
@@ -1039,6 +1304,7 @@ int autotune_level(mg3d_handle *h, int k, int *evaluated) {
         ngs.push_back(ng);
     }
     std::vector<SweepShape> cands;
+    if (plane_ok) plane_candidates(h, k, cands);
     for (int ng : ngs)
         for (int bands = 1; bands <= kMaxBands && bands <= L.ny; ++bands) {
             // 32 to 512 threads in powers of two and the block sizes that
@@ -1257,7 +1523,18 @@ int create_impl(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_qu
         std::vector<StepGeom> g;
         build_geometry(h, L, g);
         MG_CUDA(cudaMemcpy(L.geom, g.data(), g.size() * sizeof(StepGeom), cudaMemcpyHostToDevice));
-        L.shape = choose_shape(h->prec, L.nx, L.ny, atom->n_freq, params->sc_interp,
+        if (h->prec == MG3D_PREC_F64) {
+            const auto ps = plane_steps<double>(L, g);
+            MG_TRY(dev_alloc(&L.psteps, ps.size() * sizeof(ps[0])));
+            MG_CUDA(cudaMemcpy(L.psteps, ps.data(), ps.size() * sizeof(ps[0]),
+                               cudaMemcpyHostToDevice));
+        } else {
+            const auto ps = plane_steps<float>(L, g);
+            MG_TRY(dev_alloc(&L.psteps, ps.size() * sizeof(ps[0])));
+            MG_CUDA(cudaMemcpy(L.psteps, ps.data(), ps.size() * sizeof(ps[0]),
+                               cudaMemcpyHostToDevice));
+        }
+        L.shape = choose_shape(h->prec, L.nx, L.ny, L.nz, atom->n_freq, params->sc_interp,
                                atm->vel ? 1 : 0, atom->gamma_prd > 0.0 ? 1 : 0);
         if (atom->gamma_prd > 0.0) {
             void **bufs[3] = {&L.jnu, &L.rho, &L.rhoS};
@@ -1329,6 +1606,8 @@ int create_impl(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_qu
         MG_CUDA(cudaMemcpy(h->d_ftab, t32.data(), t32.size() * es, cudaMemcpyHostToDevice));
     }
     if (h->prd) MG_TRY(setup_prd(h));
+    if (h->prec == MG3D_PREC_F64) MG_TRY(build_plane_slots<double>(h));
+    else MG_TRY(build_plane_slots<float>(h));
     {
         double tab[kExpTab];
         exp_neg_constants(tab, &h->exp_l1, &h->exp_l2);
@@ -2689,6 +2968,8 @@ int mg3d_destroy(mg3d_handle *h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     drop_graphs(h);
     for (int k = 0; k <= MG3D_MAX_GRIDS; ++k) free_level(h->lev[k]);
+    for (void *p : h->d_pslot)
+        if (p) cudaFree(p);
     void *ptrs[] = {h->d_ftab, h->d_vtab, h->d_vline, h->d_kmat, h->d_wphin, h->d_fidx,
                     h->d_exp_tab, h->pj, h->pu, h->scal,
                     h->scratch, h->d_fi, h->d_ti, h->ml_jx, h->ml_ux, h->ml_acc,
@@ -2946,13 +3227,17 @@ int mg3d_get_fs_occupancy(mg3d_handle *h, int level, int freq_per_block, int ban
     SweepShape s;
     MG_TRY(shape_from_args(h, level, freq_per_block, bands, threads, lean, stage, &s));
     int n = 0;
-    const cudaError_t e = sweep_active_clusters(h->prec, s, h->lev[level].nx, &n);
+    const cudaError_t e = s.plane ? plane_active_clusters(h->prec, s, h->lev[level].nx, &n)
+                                  : sweep_active_clusters(h->prec, s, h->lev[level].nx, &n);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(MG3D_E_CUDA, std::string("occupancy query: ") + cudaGetErrorString(e));
     }
     if (max_clusters) *max_clusters = n;
-    if (smem_bytes) *smem_bytes = (long long)sweep_smem_bytes(h->prec, s, h->lev[level].nx);
+    if (smem_bytes)
+        *smem_bytes = (long long)(s.plane ? plane_smem_bytes(h->prec, s.np, s.rows,
+                                                             h->lev[level].nx)
+                                          : sweep_smem_bytes(h->prec, s, h->lev[level].nx));
     return MG3D_OK;
 }
 
@@ -2986,11 +3271,12 @@ int mg3d_get_fs_config(const mg3d_handle *h, int level, int *freq_per_block, int
                        int *threads, int *lean, int *stage) {
     MG_TRY(check_level(h, level));
     const Level &L = h->lev[level];
-    if (freq_per_block) *freq_per_block = L.shape.ng;
+    if (freq_per_block)
+        *freq_per_block = L.shape.plane && L.shape.ngroups == 1 ? h->atom.n_freq : L.shape.ng;
     if (bands) *bands = L.shape.bands;
     if (threads) *threads = L.shape.threads;
     if (lean) *lean = L.shape.lean;
-    if (stage) *stage = L.shape.stage;
+    if (stage) *stage = L.shape.plane ? 2 : L.shape.stage;
     return MG3D_OK;
 }
 

@@ -38,7 +38,71 @@ struct SweepShape {
     int herm = 0;  // 1: monotone cubic Hermite upwind interpolation (unstaged)
     int vel = 0;   // 1: moving atmosphere, ray-dependent profiles (unstaged)
     int prd = 0;   // 1: partial redistribution, frequency-dependent S (unstaged)
+    int plane = 0; // 1: shifted-plane sweep (plane_sweep.cuh) with np slots of two
+    int np = 0;    //    frequencies per group (ng = 2 np table positions per group)
 };
+
+// Per (ray, step t) constants of the shifted-plane sweep (plane_sweep.cuh),
+// in the formal-solution precision: the bilinear weights of the upwind
+// corners and half the path length of step t (t >= 1), and the shift of the
+// plane written at step t, i.e. the corner offsets (ix0, iy0) of step t+1
+// (t <= nz-2).
+template <typename T>
+struct PlaneStep {
+    T w00, w10, w01, w11;
+    T half_s;
+    int sx, sy;
+};
+
+// Slot flags of the shifted-plane sweep.
+namespace plane {
+constexpr int kHasB = 1;    // the slot has a second frequency
+constexpr int kShared = 2;  // the second frequency has the first one's phi
+}  // namespace plane
+
+// One slot of the shifted-plane sweep: two frequencies (a, b) of a group.
+template <typename T>
+struct PlaneSlot {
+    T phi_a, phi_b;      // profile values
+    T iphi_a, iphi_b;    // their inverses
+    T wphi_a, wphi_b;    // ray weight x frequency weight x profile (0: no frequency b)
+    T wu_a, wu_b;        // weight of u: wphi_a + wphi_b when a and b share phi, else own
+    int flags;           // bit 0: frequency b present; bit 1: b has a's phi
+};
+
+// Arguments of the shifted-plane sweep kernel (plane_sweep.cuh).
+template <typename T>
+struct PlaneArgs {
+    int nx, ny, nz, rows, bands, ngroups;
+    int nslot_last;                      // active slots of the last group (0: all NP)
+    unsigned up_mask;                    // bit r set when ray r points up
+    unsigned long long rmagic, xmagic;   // band_magic(rows), band_magic(nx)
+    const T *chi0, *S, *bbot;            // [nvox], [nvox], [nx*ny]
+    const PlaneStep<T> *steps;           // [kRays][nz]
+    const PlaneSlot<T> *slots;           // [ngroups][NP]
+    T *pj, *pu;                          // [kRays*ngroups][nvox] partial Jeff and U
+    const double *exp_tab;               // FP64 exp table (FP64 sweeps)
+    double exp_l1, exp_l2;
+};
+
+// Slot counts (frequency pairs per group) the shifted-plane sweep is built for.
+constexpr int kPlaneNp[] = {1, 2, 3, 5, 8};
+constexpr int kPlaneNpCount = 5;
+constexpr size_t kMaxPlaneSmem = 224 * 1024;   // dynamic; static use stays below 3 KB
+constexpr int kPlaneMaxThreads = 1024;
+// nodes a thread of the shifted-plane sweep takes per step (band <= this x
+// threads): the node loop is unrolled over them, which costs registers where
+// the compiler overlaps them (FP32 with more than two slots: two nodes)
+__host__ __device__ constexpr int plane_max_pass(int np, bool fp64) {
+    return fp64 || np <= 2 ? 4 : 2;
+}
+bool plane_np_supported(int np);
+size_t plane_smem_bytes(int prec, int np, int rows, int nx);
+cudaError_t launch_plane_sweep_f64(const PlaneArgs<double> &a, const SweepShape &s,
+                                   cudaStream_t st);
+cudaError_t launch_plane_sweep_f32(const PlaneArgs<float> &a, const SweepShape &s,
+                                   cudaStream_t st);
+cudaError_t plane_active_clusters(int prec, const SweepShape &s, int nx, int *n);
 
 // Sweep variants: linear upwind interpolation, Hermite, moving atmosphere,
 // partial redistribution.

@@ -1,0 +1,15 @@
+// Shifted-plane sweep (plane_sweep.cuh), FP32 instances.
+#include "plane_sweep.cuh"
+
+namespace mg3d {
+
+cudaError_t launch_plane_sweep_f32(const PlaneArgs<float> &a, const SweepShape &s,
+                                   cudaStream_t st) {
+    return plane_dispatch<float>(&a, s, a.nx, st, nullptr);
+}
+
+cudaError_t plane_active_clusters_f32(const SweepShape &s, int nx, int *n) {
+    return plane_dispatch<float>(nullptr, s, nx, 0, n);
+}
+
+}  // namespace mg3d

@@ -62,6 +62,29 @@ __device__ __forceinline__ double exp_neg(double x, const ExpNegTable e) {
     return flush ? 0.0 : __longlong_as_double(bits);
 }
 
+// exp_neg with the range test on the high word of x (an integer compare on
+// the integer pipe instead of an FP64 compare): x >= 708, infinite or NaN
+// gives 0 (0x40862000 is the high word of 708.0; a non-negative double orders
+// like its bit pattern).  The reduction and polynomial are exp_neg's; for x
+// past the test the intermediate values are discarded.
+__device__ __forceinline__ double exp_neg_hi(double x, const ExpNegTable e) {
+    const bool flush = __double2hiint(x) >= 0x40862000;
+    const double magic = 6755399441055744.0;  // 1.5 * 2^52
+    const double t = fma(x, -369.3299304675746, magic);
+    const int n = __double2loint(t);
+    const double nd = t - magic;
+    double r = fma(-nd, e.l1, -x);
+    r = fma(-nd, e.l2, r);
+    double p = fma(r, 1.0 / 24.0, 1.0 / 6.0);
+    p = fma(p, r, 0.5);
+    p = fma(p, r, 1.0);
+    const double q = p * r;
+    const double tj = e.tab[n & (kExpTab - 1)];
+    const double v = fma(tj, q, tj);
+    const long long bits = __double_as_longlong(v) + ((long long)(n >> 8) << 52);
+    return __longlong_as_double(flush ? 0ll : bits);
+}
+
 // closed() has no branch, so a caller can evaluate several independent steps
 // back to back and patch the small-x ones with series() afterwards; eval()
 // takes one form or the other per lane.

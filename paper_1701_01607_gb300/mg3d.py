@@ -153,6 +153,7 @@ _SIGNATURES = {
                                    ctypes.POINTER(ctypes.c_longlong)]),
     "mg3d_autotune": (_I, [_H, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),
     "mg3d_check_exp": (_I, [_I, _D, _D]),
+    "mg3d_probe_alu_peaks": (_I, [_I, _D]),
     "mg3d_check_profiles": (_I, [_I, ctypes.c_double, _D, _D, _D]),
     "mg3d_check_voigt": (_I, [_I, _D, _D, _D]),
     "mg3d_set_graphs": (_I, [_H, _I]),
@@ -458,6 +459,14 @@ def mg3d_autotune(h, level: int = 0):
     secs = ctypes.c_double()
     _check(load().mg3d_autotune(h, level, ctypes.byref(n), ctypes.byref(secs)))
     return {"evaluated": n.value, "seconds": secs.value}
+
+
+def mg3d_probe_alu_peaks(reps: int = 3):
+    """Measured peak rates (thread operations per second) of FP32 FMA, the ex2
+    and rcp approximations and FP64 FMA on the current device."""
+    out = np.empty(4)
+    _check(load().mg3d_probe_alu_peaks(reps, _dptr(out)))
+    return {"ffma": out[0], "ex2": out[1], "rcp": out[2], "dfma": out[3]}
 
 
 def mg3d_check_exp(x):
