@@ -51,10 +51,19 @@ FS_UNITS_PER_FINE = GRID[0] * GRID[1] * GRID[2] * 24 * 9
 N_DISTINCT_PHI = (9 + 1) // 2
 ALG_FLOPS_PER_UNIT = 7 + 5 + 4 + (1 + 1 + 2 + 1 + 1) * N_DISTINCT_PHI / 9.0 + 16.0 / 9.0
 FP64_NOMINAL_TFLOPS = 1.25      # GB300, at the 2070 MHz maximum SM clock
+# FP32 instructions per unit the FP32 sweep needs (each an FMA-pipe
+# instruction): per frequency the bilinear I_up 4, the new I 2 (one of them
+# the w_up S_up term shared by a mirror pair is counted per distinct phi
+# below), the Jeff sum 1; per distinct phi (5 of 9) the optical path 1, the
+# exp2 argument 1, u 1, w0 1, w_up 1, w_up S_up 1, the U sum 1; per node and
+# ray the chi0/S bilinear 8 and dtau 2.  Plus per distinct phi one ex2 and one
+# rcp on the multi-function unit.
+ALG_FP32_OPS_PER_UNIT = 4 + 2 + 1 + 7 * N_DISTINCT_PHI / 9.0 + 10.0 / 9.0
+MUFU_EX2_PER_UNIT = MUFU_RCP_PER_UNIT = N_DISTINCT_PHI / 9.0
 # DRAM bytes (read + write) of one finest-grid FP64 sweep launch, from one ncu
 # capture of the current kernel at this launch shape (ng, bands, threads,
 # lean, stage); reported only when the autotuner picks the same shape
-FINE_SWEEP_TRAFFIC = {"shape": [9, 5, 512, 0, 0], "bytes": 13261312 + 141663488}
+FINE_SWEEP_TRAFFIC = {"shape": [9, 5, 224, 0, 2], "bytes": 14019072 + 142003968}
 SM_MAX_MHZ = 2070.0
 
 
@@ -196,21 +205,29 @@ def run_gpu(args):
             ms.append(e0.elapsed_time(e1))
         return ms, m.mg3d_get_counters(h)
 
-    # ---- main measurement: FP64 V-cycles
+    # ---- measured peak rates of the ALU pipes the sweeps run on (roofline
+    # denominators): FP32 FMA, ex2, rcp, FP64 FMA, thread operations per second
+    peaks = m.mg3d_probe_alu_peaks(5)
+    torch.cuda.synchronize()
+
+    # ---- main measurement: FP64 V-cycles, no per-launch instrumentation
     h = make(m.MG3D_PREC_F64)
     clocks = ClockSampler(local)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    ms, cnt = timed_cycles(h, args.steps, args.warmup, timing=True)
+    ms, cnt = timed_cycles(h, args.steps, args.warmup, timing=False)
     torch.cuda.synchronize()
     clk = clocks.stop()
     total_ms, units = aggregate_over_ranks(sum(ms), cnt["fs_units"], dist, "cuda")
     value = units / (total_ms * 1e-3) / 1e9
     fine = N_GRIDS
-    fine_ms = cnt["level_fs_kernel_ms"][fine] / max(1, cnt["level_fs_timed_launches"][fine])
-    fine_units = cnt["level_fs_units"][fine] / max(1, cnt["level_fs_launches"][fine])
+    # per-launch sweep times from a separate instrumented pass (event pairs
+    # recorded around every sweep inside the replayed V-cycle graph)
+    _, cnt_t = timed_cycles(h, max(3, args.steps // 2), 1, timing=True)
+    fine_ms = cnt_t["level_fs_kernel_ms"][fine] / max(1, cnt_t["level_fs_timed_launches"][fine])
+    fine_units = cnt_t["level_fs_units"][fine] / max(1, cnt_t["level_fs_launches"][fine])
 
     # ---- end to end: host populations in, V-cycle, host populations out
     nx, ny, nz = GRID
@@ -235,14 +252,16 @@ def run_gpu(args):
 
     # ---- mixed precision (FP32 formal solution, FP64 rates): same step
     h32 = make(m.MG3D_PREC_F32)
-    ms32, cnt32 = timed_cycles(h32, args.steps, args.warmup, timing=True)
+    ms32, cnt32 = timed_cycles(h32, args.steps, args.warmup, timing=False)
+    _, cnt32_t = timed_cycles(h32, max(3, args.steps // 2), 1, timing=True)
     m.mg3d_destroy(h32)
-    fine_ms32 = cnt32["level_fs_kernel_ms"][fine] / max(1, cnt32["level_fs_timed_launches"][fine])
+    fine_ms32 = (cnt32_t["level_fs_kernel_ms"][fine]
+                 / max(1, cnt32_t["level_fs_timed_launches"][fine]))
+    large32 = fp32_sweep_large(m, stream, peaks) if world == 1 and not args.no_large else None
 
     result = None
     if rank == 0:
-        sm_mhz = clk.get("sm_mhz") or SM_MAX_MHZ
-        peak = FP64_NOMINAL_TFLOPS * sm_mhz / SM_MAX_MHZ
+        peak = 2.0 * peaks["dfma"] / 1e12       # measured FP64 TFLOP/s
         achieved = ALG_FLOPS_PER_UNIT * fine_units / (fine_ms * 1e-3) / 1e12
         fine_shape = list(tuning.get("f64", {}).get("shapes", {}).get(fine, ()))
         traffic = (FINE_SWEEP_TRAFFIC["bytes"]
@@ -258,14 +277,26 @@ def run_gpu(args):
                        "parallelism": f"replicas x{world}",
                        "l2": "256 MB buffer written between timed steps",
                        "sweep_autotune": tuning},
-            "roofline": {"kernel": "sweep_kernel<double> (finest grid)", "bound": "alu",
+            "roofline": {"kernel": "plane_sweep_kernel<double> (finest grid)", "bound": "alu",
                          "achieved": round(achieved, 4), "peak": round(peak, 4),
                          "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                          "traffic": traffic,
-                         "peak_source": "nominal FP64 1.25 TFLOP/s x median SM clock / 2070 MHz",
+                         "peak_source": "measured FP64 FMA rate x 2 (mg3d_probe_alu_peaks, "
+                                        "this run); nominal 1.25 TFLOP/s",
+                         "frac_of_nominal": round(achieved / FP64_NOMINAL_TFLOPS, 4),
                          "alg_flops_per_unit": round(ALG_FLOPS_PER_UNIT, 3),
                          "units_per_launch": fine_units,
-                         "ms_per_launch": round(fine_ms, 4)},
+                         "ms_per_launch": round(fine_ms, 4),
+                         "timing": "sweep launches timed in a separate instrumented pass"},
+            "roofline_fp32": roofline_fp32(fine_units, fine_ms32, peaks,
+                                           "plane_sweep_kernel<float> (finest grid)"),
+            "fp32_large_plane": large32,
+            "alu_peaks": {"ffma_tops": round(peaks["ffma"] / 1e12, 3),
+                          "ex2_tops": round(peaks["ex2"] / 1e12, 3),
+                          "rcp_tops": round(peaks["rcp"] / 1e12, 3),
+                          "dfma_tops": round(peaks["dfma"] / 1e12, 4),
+                          "how": "mg3d_probe_alu_peaks: 8 independent chains per thread, "
+                                 "8 blocks of 256 per SM, best of 5 launches"},
             "e2e": {"value": round(e2e_units / (sum(e2e_ms) * 1e-3) / 1e9, 4), "unit": UNIT,
                     "h2d_bytes_per_step": int(pinned_in.nbytes),
                     "d2h_bytes_per_step": int(pinned_out.nbytes)},
@@ -292,6 +323,56 @@ def run_gpu(args):
         dist.barrier()
         dist.destroy_process_group()
     return result
+
+
+def roofline_fp32(units, ms, peaks, kernel):
+    """FP32 sweep against its ALU roofline: per unit the FP32 instructions of
+    the algorithm on the FMA pipes and the ex2/rcp on the multi-function
+    unit, at the rates measured in this run; the roofline throughput is the
+    slower of the two pipes."""
+    t_fma = ALG_FP32_OPS_PER_UNIT / peaks["ffma"]
+    t_mufu = MUFU_EX2_PER_UNIT / peaks["ex2"] + MUFU_RCP_PER_UNIT / peaks["rcp"]
+    peak = 1.0 / max(t_fma, t_mufu) / 1e9
+    achieved = units / (ms * 1e-3) / 1e9
+    return {"kernel": kernel, "bound": "alu", "achieved": round(achieved, 3),
+            "peak": round(peak, 3), "unit": "Gunit/s", "frac": round(achieved / peak, 4),
+            "alg_fp32_ops_per_unit": round(ALG_FP32_OPS_PER_UNIT, 3),
+            "mufu_per_unit": round(MUFU_EX2_PER_UNIT + MUFU_RCP_PER_UNIT, 3),
+            "limiting_pipe": "fma" if t_fma >= t_mufu else "mufu",
+            "units_per_launch": units, "ms_per_launch": round(ms, 4),
+            "peak_source": "measured FFMA, ex2 and rcp rates (mg3d_probe_alu_peaks, this run)"}
+
+
+LARGE_PLANE = (128, 128, 129)
+
+
+def fp32_sweep_large(m, stream, peaks, reps=10):
+    """The FP32 sweep on 128x128 planes (the bench atmosphere's recipe, 129
+    nodes in z): 4 times the work per plane step of the 64x64 box, so the
+    per-plane barrier and latency weigh less; autotuned, then the sweep
+    kernel of `reps` formal solutions timed with CUDA events."""
+    from paper_1701_01607_gb300 import synth
+    nx, ny, nz = LARGE_PLANE
+    atm, atom = synth.stratified_two_level(nx, ny, nz, eps=1e-4, sigma=0.3, seed=1)
+    h = m.mg3d_create(atm, atom, n_grids=1, fs_prec=m.MG3D_PREC_F32)
+    try:
+        m.mg3d_set_stream(h, stream.cuda_stream)
+        m.mg3d_autotune(h, 1)
+        m.mg3d_formal_solve(h, 1, want=False)
+        m.mg3d_set_timing(h, True)
+        m.mg3d_reset_counters(h)
+        for _ in range(reps):
+            m.mg3d_formal_solve(h, 1, want=False)
+        c = m.mg3d_get_counters(h)
+        ms = c["level_fs_kernel_ms"][1] / max(1, c["level_fs_timed_launches"][1])
+        shape = m.mg3d_get_fs_config(h, 1)
+    finally:
+        m.mg3d_destroy(h)
+    out = roofline_fp32(nx * ny * nz * 24 * 9, ms, peaks,
+                        "plane_sweep_kernel<float>, %dx%dx%d" % LARGE_PLANE)
+    out["shape"] = list(shape)
+    out["note"] = "sweep kernel alone (events around each launch); not part of the V-cycle step"
+    return out
 
 
 def time_to_solution(m, atm, atom, stream, tol=1e-3):
@@ -927,6 +1008,8 @@ def main():
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--no-tts", action="store_true", help="skip time-to-solution runs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the FP32 sweep on 128x128 planes")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default sweep shapes")
     ap.add_argument("--shapes", default="",

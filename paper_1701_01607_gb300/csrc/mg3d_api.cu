@@ -448,30 +448,40 @@ int shape_capacity(int prec, const SweepShape &s, int nx) {
     return s.bands == 1 ? n * sm_count() : n;
 }
 
-// Default shifted-plane shape: all frequencies in one group when they fit in
-// 16 (else groups of 16), and the most bands (up to 8) whose 24 x groups
-// clusters the GPU holds in one wave; mg3d_autotune replaces it by measurement.
+// Default shifted-plane shape: the largest slot count that takes all
+// frequencies in one group (or groups of 16 beyond 16 frequencies), and the
+// most bands (up to 8) whose 24 x groups clusters the GPU holds in one wave.
+// Planes too large for that take fewer slots per group and up to 16 bands,
+// the first shape that fits.  mg3d_autotune replaces it by measurement.
 SweepShape choose_plane_shape(int prec, int nx, int ny, int nfreq) {
-    int np = plane_np_for(nfreq);
-    if (np == 0) np = kPlaneNp[kPlaneNpCount - 1];
-    const int ngroups = (nfreq + 2 * np - 1) / (2 * np);
-    SweepShape best{}, fallback{};
-    for (int bands = 1; bands <= kPortableBands && bands <= ny; ++bands) {
-        const int rows = (ny + bands - 1) / bands;
-        if ((long)(bands - 1) * rows >= ny) continue;
-        if (plane_smem_bytes(prec, np, rows, nx) > kMaxPlaneSmem) continue;
-        SweepShape s{2 * np, ngroups, bands, rows, threads_for_band(rows * nx)};
-        if ((long)rows * nx > (long)plane_max_pass(np, prec == MG3D_PREC_F64) * s.threads)
-            continue;
-        s.stage = 0;
-        s.plane = 1;
-        s.np = np;
-        const int cap = shape_capacity(prec, s, nx);
-        if (cap < 1) continue;
-        if (fallback.ng == 0) fallback = s;
-        if (cap >= kRays * ngroups) best = s;
+    int np0 = plane_np_for(nfreq);
+    if (np0 == 0) np0 = kPlaneNp[kPlaneNpCount - 1];
+    SweepShape fallback{};
+    for (int i = kPlaneNpCount - 1; i >= 0; --i) {
+        const int np = kPlaneNp[i];
+        if (np > np0) continue;
+        const int ngroups = (nfreq + 2 * np - 1) / (2 * np);
+        SweepShape best{};
+        for (int bands = 1; bands <= kMaxBands && bands <= ny; ++bands) {
+            const int rows = (ny + bands - 1) / bands;
+            if ((long)(bands - 1) * rows >= ny) continue;
+            if (plane_smem_bytes(prec, np, rows, nx) > kMaxPlaneSmem) continue;
+            // one thread per node up to 512 (1024 for FP32 with one or two slots)
+            const int cap = prec == MG3D_PREC_F32 && np <= 2 ? kPlaneMaxThreads : 512;
+            const int th = std::max(32, std::min(cap, ((rows * nx + 31) / 32) * 32));
+            if ((long)rows * nx > (long)plane_max_pass(np, prec == MG3D_PREC_F64) * th) continue;
+            SweepShape s{2 * np, ngroups, bands, rows, th};
+            s.stage = 0;
+            s.plane = 1;
+            s.np = np;
+            const int held = shape_capacity(prec, s, nx);
+            if (held < 1) continue;
+            if (fallback.ng == 0) fallback = s;
+            if (bands <= kPortableBands && held >= kRays * ngroups) best = s;
+        }
+        if (best.ng) return best;
     }
-    return best.ng ? best : fallback;
+    return fallback;
 }
 
 // Grids the shifted-plane sweep's 32-bit node indices cover.

@@ -48,10 +48,10 @@ struct SweepShape {
 // plane written at step t, i.e. the corner offsets (ix0, iy0) of step t+1
 // (t <= nz-2).
 template <typename T>
-struct PlaneStep {
+struct alignas(16) PlaneStep {
     T w00, w10, w01, w11;
     T half_s;
-    int sx, sy;
+    int sx, sy;   // (16-byte aligned and padded: loaded as whole vectors)
 };
 
 // Slot flags of the shifted-plane sweep.

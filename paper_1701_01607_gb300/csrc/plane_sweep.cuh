@@ -79,23 +79,29 @@ __device__ __forceinline__ unsigned cluster_rank() {
     asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
     return r;
 }
-// 16-byte store of (v[0..VW-1]) at a shared-memory address of this block
-// (local) or of any block of the cluster (cluster address).  No memory
-// clobber: the stores go to the plane being written, which no thread reads
-// before the barrier (whose asm carries the clobber) that ends the step.
-__device__ __forceinline__ void st16(unsigned a, const float *v, bool cl) {
-    if (cl)
-        asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v[0]),
-                     "f"(v[1]), "f"(v[2]), "f"(v[3]));
-    else
-        asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v[0]), "f"(v[1]),
-                     "f"(v[2]), "f"(v[3]));
+// 16-byte store of (v[0..VW-1]) at a shared::cluster address (this block's
+// or another block's shared memory; a launch without clusters is a cluster of
+// one block), unconditional or under a predicate.  No memory clobber: the
+// stores go to the plane being written, which no thread reads before the
+// barrier (whose asm carries the clobber) that ends the step.
+__device__ __forceinline__ void st16(unsigned a, const float *v) {
+    asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v[0]),
+                 "f"(v[1]), "f"(v[2]), "f"(v[3]));
 }
-__device__ __forceinline__ void st16(unsigned a, const double *v, bool cl) {
-    if (cl)
-        asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" ::"r"(a), "d"(v[0]), "d"(v[1]));
-    else
-        asm volatile("st.shared.v2.f64 [%0], {%1, %2};" ::"r"(a), "d"(v[0]), "d"(v[1]));
+__device__ __forceinline__ void st16(unsigned a, const double *v) {
+    asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" ::"r"(a), "d"(v[0]), "d"(v[1]));
+}
+__device__ __forceinline__ void st16_if(bool c, unsigned a, const float *v) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %0, 0;\n\t"
+        "@p st.shared::cluster.v4.f32 [%1], {%2, %3, %4, %5};\n\t}" ::"r"((int)c),
+        "r"(a), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]));
+}
+__device__ __forceinline__ void st16_if(bool c, unsigned a, const double *v) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %0, 0;\n\t"
+        "@p st.shared::cluster.v2.f64 [%1], {%2, %3};\n\t}" ::"r"((int)c),
+        "r"(a), "d"(v[0]), "d"(v[1]));
 }
 // one 16-byte vector of shared memory into registers
 __device__ __forceinline__ void ld16(const float *p, float *o) {
@@ -231,7 +237,7 @@ __device__ __forceinline__ void plane_sweep_body(const PlaneArgs<T> &a) {
     const int r = blockIdx.z, g = blockIdx.y;
     const int nb = a.bands;
     const bool cl = nb > 1;
-    const int rank = cl ? (int)cluster_rank() : 0;
+    const int rank = (int)cluster_rank();   // 0 in a launch without clusters
     const int nx = a.nx, ny = a.ny, nz = a.nz, rows = a.rows;
     const int y0 = rank * rows;
     const int myrows = min(rows, ny - y0);
@@ -316,7 +322,9 @@ __device__ __forceinline__ void plane_sweep_body(const PlaneArgs<T> &a) {
     }
 
     // Stores the channels of node (x, y) into the frame of the next step,
-    // shifted by (sx, sy), in buffer `par`, with its pad and halo copies.
+    // shifted by (sx, sy), in buffer `par`, with its pad and halo copies
+    // (predicated stores: a node of column 0 also fills the pad column, a
+    // node of a band's first row also the halo row of the band before it).
     auto store_node = [&](const T *ch, int x, int y, int sx, int sy, int par) {
         int xs = x - sx;
         xs += xs < 0 ? nx : 0;
@@ -324,30 +332,21 @@ __device__ __forceinline__ void plane_sweep_body(const PlaneArgs<T> &a) {
         ys += ys < 0 ? ny : 0;
         const int ob = band_of(ys, a.rmagic);
         const int lr = ys - ob * rows;
-        const unsigned off =
-            (unsigned)((par * plane_el + lr * pitch + xs * CS) * (int)sizeof(T));
-        const unsigned base = cl ? cluster_addr(buf_addr, (unsigned)ob) : buf_addr;
+        const int hb = ob == 0 ? nb - 1 : ob - 1;   // the band whose halo row is ys
+        const int hr = hb == nb - 1 ? lastrows : rows;
+        const unsigned col = (unsigned)((par * plane_el + xs * CS) * (int)sizeof(T));
+        const unsigned base = cluster_addr(buf_addr, (unsigned)ob) +
+                              col + (unsigned)(lr * pitch * (int)sizeof(T));
+        const unsigned hbase = cluster_addr(buf_addr, (unsigned)hb) +
+                               col + (unsigned)(hr * pitch * (int)sizeof(T));
+        const unsigned padoff = (unsigned)(nx * CS * (int)sizeof(T));
+        const bool pad = xs == 0, halo = lr == 0;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) st16(base + off + v * 16, ch + v * VW, cl);
-        if (xs == 0) {
-#pragma unroll
-            for (int v = 0; v < NV; ++v)
-                st16(base + off + nx * CS * (int)sizeof(T) + v * 16, ch + v * VW, cl);
-        }
-        if (lr == 0) {
-            // the first row of band ob is also the halo row of the band before it
-            const int hb = ob == 0 ? nb - 1 : ob - 1;
-            const int hr = hb == nb - 1 ? lastrows : rows;
-            const unsigned hoff =
-                (unsigned)((par * plane_el + hr * pitch + xs * CS) * (int)sizeof(T));
-            const unsigned hbase = cl ? cluster_addr(buf_addr, (unsigned)hb) : buf_addr;
-#pragma unroll
-            for (int v = 0; v < NV; ++v) st16(hbase + hoff + v * 16, ch + v * VW, cl);
-            if (xs == 0) {
-#pragma unroll
-                for (int v = 0; v < NV; ++v)
-                    st16(hbase + hoff + nx * CS * (int)sizeof(T) + v * 16, ch + v * VW, cl);
-            }
+        for (int v = 0; v < NV; ++v) {
+            st16(base + v * 16, ch + v * VW);
+            st16_if(pad, base + padoff + v * 16, ch + v * VW);
+            st16_if(halo, hbase + v * 16, ch + v * VW);
+            st16_if(halo && pad, hbase + padoff + v * 16, ch + v * VW);
         }
     };
 
@@ -419,11 +418,14 @@ __device__ __forceinline__ void plane_sweep_body(const PlaneArgs<T> &a) {
             const int p = c >> 1;
             return p < nslot && ((c & 1) == 0 || (stab[p].flags & kHasB));
         };
+        // the step constants are loaded one step ahead as well
+        PlaneStep<T> sp_next = a.steps[(long)r * nz + (nz > 1 ? 1 : 0)];
         for (int t = 1; t < nz; ++t) {
             const int kp = (up ? t : nz - 1 - t) * nplane;
             const T *prev = buf + ((t - 1) & 1) * plane_el;
-            const PlaneStep<T> sp = a.steps[(long)r * nz + t];
+            const PlaneStep<T> sp = sp_next;
             const bool write = t + 1 < nz;
+            if (write) sp_next = a.steps[(long)r * nz + t + 1];
             T cchi[MAXP], cS[MAXP];
 #pragma unroll
             for (int i = 0; i < MAXP; ++i) {
