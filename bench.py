@@ -317,6 +317,11 @@ def run_gpu(args):
         }
         if not args.no_tts and world == 1:
             result["time_to_solution"] = time_to_solution(m, atm, atom, stream)
+            result["mixed_precision"]["accuracy"] = dict(
+                result["time_to_solution"]["mixed_precision_fas"],
+                what="3-grid FAS from the zero-radiation start to C < 1e-3: FP32 formal "
+                     "solution against FP64 throughout; e_inf against a FAS solution "
+                     "converged to C < 1e-9")
         if world == 1 and not args.no_cpu:
             result["cpu_baseline"] = cpu_baseline(atm, atom, samples=2)
     if dist:
@@ -397,6 +402,24 @@ def time_to_solution(m, atm, atom, stream, tol=1e-3):
                        "e_inf": float(np.max(np.abs(n - n_ref) / np.abs(n_ref))),
                        "negatives": st["negatives"]}
     out["tol"] = tol
+    # the FP32 formal solution (FP64 rates, residuals and transfers) to the
+    # same stopping point: its error against the FP64 solve of the same
+    # schedule and against the converged reference
+    n64 = None
+    acc = {}
+    for prec, key in ((m.MG3D_PREC_F64, "f64"), (m.MG3D_PREC_F32, "f32")):
+        h = m.mg3d_create(atm, atom, n_grids=N_GRIDS, fs_prec=prec, **NU)
+        m.mg3d_set_stream(h, stream.cuda_stream)
+        st = m.mg3d_fas_solve(h, tol, 400, n_grids=N_GRIDS)
+        n = m.mg3d_get_populations(h, N_GRIDS)
+        m.mg3d_destroy(h)
+        acc[key] = {"cycles": st["iterations"], "seconds": round(st["seconds"], 4),
+                    "e_inf": float(np.max(np.abs(n - n_ref) / np.abs(n_ref)))}
+        if key == "f64":
+            n64 = n
+        else:
+            acc["f32_vs_f64_e_inf"] = float(np.max(np.abs(n - n64) / np.abs(n64)))
+    out["mixed_precision_fas"] = acc
     out["speedup_fas"] = round(out["mali"]["seconds"] / out["fas"]["seconds"], 3)
     out["speedup_fmg"] = round(out["mali"]["seconds"] / out["fmg"]["seconds"], 3)
     out["equal_accuracy"] = equal_accuracy(m, atm, atom, stream, n_ref)

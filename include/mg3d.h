@@ -242,6 +242,37 @@ int mg3d_init_zero_radiation(mg3d_handle *h, int level);
  * of the Lambda operator).  Either pointer may be NULL. */
 int mg3d_formal_solve(mg3d_handle *h, int level, double *jeff_host, double *u_host);
 
+/* The same formal solution (Sec. 2.1: Jeff and U = 1 - Lambda* are what the
+ * MALI update of Eqs. 2-4 takes from it) in a chosen precision prec
+ * (MG3D_PREC_F64 or MG3D_PREC_F32) instead of the handle's fs_prec.  In the
+ * handle's own precision it is mg3d_formal_solve.  In the other precision
+ * (two-level atoms, static, complete redistribution, linear upwind
+ * interpolation; MG3D_E_ARG otherwise) the first call on a level allocates
+ * that precision's opacity, source, bottom-intensity and step buffers for the
+ * level and the handle's partial sums and frequency tables in it, which the
+ * handle keeps until mg3d_destroy; populations, rates and outputs stay FP64.
+ * MG3D_E_STATE for multi-level handles. */
+int mg3d_formal_solve_ex(mg3d_handle *h, int level, int prec, double *jeff_host,
+                         double *u_host);
+
+/* Device-pointer variants for callers whose buffers live on the GPU (for
+ * example PyTorch tensors' data_ptr()), ordered on the caller's CUDA stream
+ * cuda_stream (NULL: the legacy default stream): the work waits for what was
+ * enqueued on that stream before the call, and work enqueued on it after the
+ * call waits for the results.  They return once the work is enqueued and do
+ * not synchronise.  Device buffers are owned by the caller and must stay
+ * valid until the stream reaches the call's work.
+ * mg3d_formal_solve_dev: as mg3d_formal_solve_ex (Sec. 2.1), outputs
+ *   jeff_dev, u_dev [nz][ny][nx] FP64 (either may be NULL);
+ * mg3d_get_populations_dev / mg3d_set_populations_dev: as
+ *   mg3d_get/set_populations, n_dev [n_levels][nz][ny][nx] FP64 (n of Eq. 4;
+ *   checkpoints have no counterpart in the paper). */
+int mg3d_formal_solve_dev(mg3d_handle *h, int level, int prec, double *jeff_dev, double *u_dev,
+                          void *cuda_stream);
+int mg3d_get_populations_dev(mg3d_handle *h, int level, double *n_dev, void *cuda_stream);
+int mg3d_set_populations_dev(mg3d_handle *h, int level, const double *n_dev,
+                             void *cuda_stream);
+
 /* n_sweeps MALI iterations on a level solving W(n) = f for that level's f
  * (f = (n_tot, 0) on the finest grid, the tau-corrected f of Eq. 9 on a
  * coarser one).  *max_rel_change (nullable) receives C of the last sweep:
@@ -570,12 +601,21 @@ int mg3d_probe_alu_peaks(int reps, double *out_host);
  *   stream).  The call returns once the work is enqueued.
  * Limits: at most MG3D_NOALLOC_MAX_NODES nodes, MG3D_NOALLOC_MAX_NZ planes and
  * MG3D_NOALLOC_MAX_FREQ frequencies; larger inputs return MG3D_E_ARG with a
- * message naming the limit.  The first call on each device looks up the
- * array's device address (cudaGetSymbolAddress) while that device is current;
- * make that first call before any stream capture.  All calls share the one
- * array, and each call rewrites all of it that it reads: calls whose work
- * overlaps on the GPU race, so order them on one stream or synchronise
- * between them. */
+ * message naming the limit.  Within them, the sweep keeps every frequency's
+ * intensities of a row band in shared memory, in at most 8 bands of 200 KB:
+ * about 16 (n_freq + 4) nx ceil(ny/8) bytes per band must fit (a 64 x 64
+ * plane takes at most 20 frequencies); a larger plane returns MG3D_E_ARG.
+ * quad_a as in mg3d_quadrature (MG3D_E_ARG unless finite and below
+ * 1/sqrt(2)).
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) while that device is current and writes its
+ * constant table; with CUDA's lazy module loading this is also when the
+ * device reserves the array, so make that first call at start-up, before the
+ * caller's allocator takes the device's memory (otherwise it can fail with
+ * MG3D_E_OOM) and before any stream capture.  All calls share the one array,
+ * and each call rewrites all of it that it reads apart from that table:
+ * calls whose work overlaps on the GPU race, so order them on one stream or
+ * synchronise between them. */
 #define MG3D_NOALLOC_MAX_NODES 65536
 #define MG3D_NOALLOC_MAX_NZ 1024
 #define MG3D_NOALLOC_MAX_FREQ 64

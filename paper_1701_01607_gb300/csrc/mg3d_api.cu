@@ -84,6 +84,11 @@ struct Level {
     StepGeom *geom = nullptr;    // [kRays][nz]
     void *psteps = nullptr;      // [kRays][nz] PlaneStep<T> of the shifted-plane sweep
     SweepShape shape{};
+    // formal solutions in the precision other than the handle's (built on the
+    // first request, two-level static CRD handles): chi0, S, the bottom
+    // intensity, the plane-sweep step table, and the shape
+    void *o_chi0 = nullptr, *o_S = nullptr, *o_bbot = nullptr, *o_psteps = nullptr;
+    SweepShape o_shape{};
     // multi-level atom only
     double *chi_c = nullptr;     // [nvox] background opacity
     double *cmat = nullptr;      // [N][N][nvox] collisional rates
@@ -142,6 +147,11 @@ struct mg3d_handle {
     // slot tables of the shifted-plane sweep, one per slot count kPlaneNp[i]:
     // [ceil(n_freq / (2 np))][np] PlaneSlot<T>
     void *d_pslot[kPlaneNpCount] = {};
+    // the other precision's slot tables and partial sums (see Level::o_chi0)
+    int o_prec = -1;
+    void *o_pslot[kPlaneNpCount] = {};
+    void *o_pj = nullptr, *o_pu = nullptr;
+    size_t partial_elems_o = 0;
     void *d_vtab = nullptr;      // moving atmospheres: [nf] offsets x, [nf] weights w
     int *d_vline = nullptr;      // multi-level, moving: line index of each frequency or -1
     bool prd = false;            // two-level partial redistribution
@@ -331,7 +341,8 @@ int plane_np_index(int np) {
 
 // Launch arguments of the shifted-plane sweep of level L with shape s.
 template <typename T>
-PlaneArgs<T> plane_args(const mg3d_handle *h, const Level &L, const SweepShape &s) {
+PlaneArgs<T> plane_args(const mg3d_handle *h, const Level &L, const SweepShape &s,
+                        bool other = false) {
     const int nf = h->atom.n_freq;
     const int last = nf - (s.ngroups - 1) * 2 * s.np;   // frequencies of the last group
     PlaneArgs<T> a{};
@@ -345,13 +356,13 @@ PlaneArgs<T> plane_args(const mg3d_handle *h, const Level &L, const SweepShape &
     a.up_mask = h->up_mask;
     a.rmagic = band_magic(s.rows);
     a.xmagic = band_magic(L.nx);
-    a.chi0 = (const T *)L.chi0;
-    a.S = (const T *)L.S;
-    a.bbot = (const T *)L.bbot;
-    a.steps = (const PlaneStep<T> *)L.psteps;
-    a.slots = (const PlaneSlot<T> *)h->d_pslot[plane_np_index(s.np)];
-    a.pj = (T *)h->pj;
-    a.pu = (T *)h->pu;
+    a.chi0 = (const T *)(other ? L.o_chi0 : L.chi0);
+    a.S = (const T *)(other ? L.o_S : L.S);
+    a.bbot = (const T *)(other ? L.o_bbot : L.bbot);
+    a.steps = (const PlaneStep<T> *)(other ? L.o_psteps : L.psteps);
+    a.slots = (const PlaneSlot<T> *)(other ? h->o_pslot : h->d_pslot)[plane_np_index(s.np)];
+    a.pj = (T *)(other ? h->o_pj : h->pj);
+    a.pu = (T *)(other ? h->o_pu : h->pu);
     a.exp_tab = h->d_exp_tab;
     a.exp_l1 = h->exp_l1;
     a.exp_l2 = h->exp_l2;
@@ -365,7 +376,7 @@ int dev_alloc(void **p, size_t bytes);
 // (x_0, x_{nf-1}, x_1, x_{nf-2}, ..., centre last), slot p of the group the
 // positions 2p and 2p + 1, so mirror pairs share a slot.
 template <typename T>
-int build_plane_slots(mg3d_handle *h) {
+int build_plane_slots(mg3d_handle *h, void **out) {
     const int nf = h->atom.n_freq;
     for (int i = 0; i < kPlaneNpCount; ++i) {
         const int np = kPlaneNp[i];
@@ -395,8 +406,8 @@ int build_plane_slots(mg3d_handle *h) {
                     }
                 }
             }
-        MG_TRY(dev_alloc(&h->d_pslot[i], tab.size() * sizeof(PlaneSlot<T>)));
-        MG_CUDA(cudaMemcpy(h->d_pslot[i], tab.data(), tab.size() * sizeof(PlaneSlot<T>),
+        MG_TRY(dev_alloc(&out[i], tab.size() * sizeof(PlaneSlot<T>)));
+        MG_CUDA(cudaMemcpy(out[i], tab.data(), tab.size() * sizeof(PlaneSlot<T>),
                            cudaMemcpyHostToDevice));
     }
     return MG3D_OK;
@@ -555,7 +566,8 @@ void free_level(Level &L) {
                     L.r,     L.chi0,  L.S,    L.bbot, L.geom, L.chi_c, L.cmat, L.saha,
                     L.mchi,  L.mS,    L.msl,  L.mfl,  L.mib,  L.sigma_c, L.jbg,
                     L.dchi0, L.dS,   L.mdchi, L.mdS,  L.vel,  L.uproj, L.vnorm, L.dinv,
-                    L.jnu,   L.jnu_new, L.rho, L.rhoS, L.psteps};
+                    L.jnu,   L.jnu_new, L.rho, L.rhoS, L.psteps, L.o_chi0, L.o_S, L.o_bbot,
+                    L.o_psteps};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     L = Level{};
@@ -793,6 +805,98 @@ int formal_solution(mg3d_handle *h, int k) {
     ++h->level_launches[k];
     h->level_units[k] += (double)L.nvox * kRays * h->atom.n_freq;
     ++h->fss[k];
+    return MG3D_OK;
+}
+
+// Formal solutions of level k in the precision other than the handle's (a
+// per-call precision, two-level static CRD handles): on the first request
+// the level's chi0/S/bottom-intensity buffers, step table and shape in that
+// precision, and the handle's slot tables and partial sums, are built; then
+// opacity, shifted-plane sweep and reduction run like the handle's own, with
+// those buffers.  Output: Jeff and U in h->scratch [2][nvox].
+int other_prec_fs(mg3d_handle *h, int k, int prec) {
+    Level &L = h->lev[k];
+    if (h->kind != 0 || h->moving || h->prd || h->params.sc_interp)
+        return fail(MG3D_E_ARG, "a formal solution in another precision than the handle's is "
+                                "built for static two-level atoms in complete redistribution "
+                                "with linear upwind interpolation");
+    if (!plane_grid_ok(L.nx, L.ny, L.nz))
+        return fail(MG3D_E_ARG, "grid too large for the shifted-plane sweep");
+    const size_t es = elem_size(prec);
+    if (h->o_prec != prec) {
+        if (h->o_prec >= 0) return fail(MG3D_E_STATE, "other-precision state mismatch");
+        if (prec == MG3D_PREC_F64) MG_TRY(build_plane_slots<double>(h, h->o_pslot));
+        else MG_TRY(build_plane_slots<float>(h, h->o_pslot));
+        h->o_prec = prec;
+    }
+    if (!L.o_chi0) {
+        MG_TRY(dev_alloc(&L.o_chi0, L.nvox * es));
+        MG_TRY(dev_alloc(&L.o_S, L.nvox * es));
+        MG_TRY(dev_alloc(&L.o_bbot, L.nplane * es));
+        std::vector<StepGeom> g;
+        build_geometry(h, L, g);
+        if (prec == MG3D_PREC_F64) {
+            const auto ps = plane_steps<double>(L, g);
+            MG_TRY(dev_alloc(&L.o_psteps, ps.size() * sizeof(ps[0])));
+            MG_CUDA(cudaMemcpy(L.o_psteps, ps.data(), ps.size() * sizeof(ps[0]),
+                               cudaMemcpyHostToDevice));
+        } else {
+            const auto ps = plane_steps<float>(L, g);
+            MG_TRY(dev_alloc(&L.o_psteps, ps.size() * sizeof(ps[0])));
+            MG_CUDA(cudaMemcpy(L.o_psteps, ps.data(), ps.size() * sizeof(ps[0]),
+                               cudaMemcpyHostToDevice));
+        }
+        L.o_shape = choose_plane_shape(prec, L.nx, L.ny, h->atom.n_freq);
+        if (L.o_shape.ng == 0) return fail(MG3D_E_ARG, "no sweep shape fits in shared memory");
+        MG_TRY(launched(h, launch_planck_bottom(prec, L.nplane, h->atom.theta, L.T, L.o_bbot,
+                                                h->stream),
+                        "planck"));
+    }
+    size_t need = 0;
+    for (int j = 1; j <= h->L; ++j)
+        if (h->lev[j].o_chi0)
+            need = std::max(need, (size_t)kRays * h->lev[j].o_shape.ngroups *
+                                      (size_t)h->lev[j].nvox);
+    static_assert(sizeof(size_t) == 8, "64-bit sizes");
+    if (!h->o_pj || need > h->partial_elems_o) {
+        MG_CUDA(cudaStreamSynchronize(h->stream));
+        if (h->o_pj) cudaFree(h->o_pj);
+        if (h->o_pu) cudaFree(h->o_pu);
+        h->o_pj = h->o_pu = nullptr;
+        h->partial_elems_o = 0;
+        MG_TRY(dev_alloc(&h->o_pj, need * es));
+        MG_TRY(dev_alloc(&h->o_pu, need * es));
+        h->partial_elems_o = need;
+    }
+    MG_TRY(launched(h, launch_opacity(prec, L.nvox, h->atom.g_ratio, h->atom.kappa, L.n,
+                                      L.o_chi0, L.o_S, h->stream),
+                    "opacity"));
+    const cudaError_t e =
+        prec == MG3D_PREC_F64
+            ? launch_plane_sweep_f64(plane_args<double>(h, L, L.o_shape, true), L.o_shape,
+                                     h->stream)
+            : launch_plane_sweep_f32(plane_args<float>(h, L, L.o_shape, true), L.o_shape,
+                                     h->stream);
+    MG_TRY(launched(h, e, "sweep"));
+    ++h->fs_launches;
+    h->fs_units += (double)L.nvox * kRays * h->atom.n_freq;
+    ++h->level_launches[k];
+    h->level_units[k] += (double)L.nvox * kRays * h->atom.n_freq;
+    RateArgs a{};
+    a.nvox = L.nvox;
+    a.nslots = kRays * L.o_shape.ngroups;
+    a.prec = prec;
+    a.pj = h->o_pj;
+    a.pu = h->o_pu;
+    a.a_ul = h->atom.a_ul;
+    a.g_ratio = h->atom.g_ratio;
+    a.c_ul = L.c_ul;
+    a.c_lu = L.c_lu;
+    a.n_tot = L.n_tot;
+    a.n = L.n;
+    a.out = h->scratch;
+    a.mode = kRateReduce;
+    MG_TRY(launched(h, launch_rates(a, h->stream), "reduce"));
     return MG3D_OK;
 }
 
@@ -1616,8 +1720,8 @@ int create_impl(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_qu
         MG_CUDA(cudaMemcpy(h->d_ftab, t32.data(), t32.size() * es, cudaMemcpyHostToDevice));
     }
     if (h->prd) MG_TRY(setup_prd(h));
-    if (h->prec == MG3D_PREC_F64) MG_TRY(build_plane_slots<double>(h));
-    else MG_TRY(build_plane_slots<float>(h));
+    if (h->prec == MG3D_PREC_F64) MG_TRY(build_plane_slots<double>(h, h->d_pslot));
+    else MG_TRY(build_plane_slots<float>(h, h->d_pslot));
     {
         double tab[kExpTab];
         exp_neg_constants(tab, &h->exp_l1, &h->exp_l2);
@@ -2543,11 +2647,23 @@ extern "C" {
 
 const char *mg3d_last_error(void) { return g_last_error.c_str(); }
 
+// The A4 parameter a must leave b = sqrt(1 - 2a^2) real and positive: a <= 0
+// (the default set) or 0 < a < 1/sqrt(2); non-finite values are refused.
+static int check_quadrature(const mg3d_quadrature *quad) {
+    if (!quad) return MG3D_OK;
+    const double a = quad->a;
+    if (!std::isfinite(a) || (a > 0.0 && 2.0 * a * a >= 1.0))
+        return fail(MG3D_E_ARG, "quadrature parameter a must be finite and below 1/sqrt(2) "
+                                "(a <= 0 selects the default A4 set)");
+    return MG3D_OK;
+}
+
 int mg3d_create(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_quadrature *quad,
                 const mg3d_params *params, mg3d_handle **out) {
     if (!out) return fail(MG3D_E_ARG, "null output pointer");
     *out = nullptr;
     if (!atm || !atom || !params) return fail(MG3D_E_ARG, "null argument");
+    MG_TRY(check_quadrature(quad));
     if (!atm->z || !atm->T || !atm->n_tot || !atm->c_ul) return fail(MG3D_E_ARG, "null array");
     if (params->n_grids < 1 || params->n_grids > MG3D_MAX_GRIDS)
         return fail(MG3D_E_ARG, "n_grids out of range");
@@ -2607,6 +2723,7 @@ int mg3d_create_ml(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
     if (!out) return fail(MG3D_E_ARG, "null output pointer");
     *out = nullptr;
     if (!atm || !atom || !params) return fail(MG3D_E_ARG, "null argument");
+    MG_TRY(check_quadrature(quad));
     if (!atm->z || !atm->T || !atm->n_tot || !atm->chi_c || !atm->c || !atm->saha)
         return fail(MG3D_E_ARG, "null atmosphere array");
     const int N = atom->n_levels;
@@ -2980,6 +3097,10 @@ int mg3d_destroy(mg3d_handle *h) {
     for (int k = 0; k <= MG3D_MAX_GRIDS; ++k) free_level(h->lev[k]);
     for (void *p : h->d_pslot)
         if (p) cudaFree(p);
+    for (void *p : h->o_pslot)
+        if (p) cudaFree(p);
+    if (h->o_pj) cudaFree(h->o_pj);
+    if (h->o_pu) cudaFree(h->o_pu);
     void *ptrs[] = {h->d_ftab, h->d_vtab, h->d_vline, h->d_kmat, h->d_wphin, h->d_fidx,
                     h->d_exp_tab, h->pj, h->pu, h->scal,
                     h->scratch, h->d_fi, h->d_ti, h->ml_jx, h->ml_ux, h->ml_acc,
@@ -3048,6 +3169,87 @@ int mg3d_formal_solve(mg3d_handle *h, int level, double *jeff_host, double *u_ho
                                         cudaMemcpyDeviceToHost, h->stream));
     MG_CUDA(cudaStreamSynchronize(h->stream));
     return MG3D_OK;
+}
+
+// Orders stream `to` after the work enqueued so far on stream `from`.
+static int order_after(mg3d_handle *h, cudaStream_t from, cudaStream_t to) {
+    if (from == to) return MG3D_OK;
+    cudaEvent_t e = pool_event(h);
+    const cudaError_t r1 = cudaEventRecord(e, from);
+    const cudaError_t r2 = r1 == cudaSuccess ? cudaStreamWaitEvent(to, e, 0) : r1;
+    h->event_pool.push_back(e);   // the wait holds the recorded state: reusable
+    MG_CUDA(r2);
+    return MG3D_OK;
+}
+
+// Formal solution of a two-level handle's level in precision prec into
+// h->scratch [2][nvox] (Jeff, U), on the handle's stream.
+static int formal_solution_into_scratch(mg3d_handle *h, int level, int prec) {
+    if (prec != h->prec) return other_prec_fs(h, level, prec);
+    MG_TRY(formal_solution(h, level));
+    RateArgs a = rate_args(h, level, kRateReduce);
+    a.out = h->scratch;
+    a.scal = nullptr;
+    MG_TRY(launched(h, launch_rates(a, h->stream), "reduce"));
+    return MG3D_OK;
+}
+
+static int check_fs_call(const mg3d_handle *h, int level, int prec) {
+    MG_TRY(check_level(h, level));
+    if (h->kind != 0) return fail(MG3D_E_STATE, "multi-level handle: use mg3d_formal_solve_ml");
+    if (prec != MG3D_PREC_F64 && prec != MG3D_PREC_F32)
+        return fail(MG3D_E_ARG, "prec must be MG3D_PREC_F64 or MG3D_PREC_F32");
+    return MG3D_OK;
+}
+
+int mg3d_formal_solve_ex(mg3d_handle *h, int level, int prec, double *jeff_host,
+                         double *u_host) {
+    MG_TRY(check_fs_call(h, level, prec));
+    const Level &L = h->lev[level];
+    MG_TRY(formal_solution_into_scratch(h, level, prec));
+    if (jeff_host) MG_CUDA(cudaMemcpyAsync(jeff_host, h->scratch, L.nvox * 8,
+                                           cudaMemcpyDeviceToHost, h->stream));
+    if (u_host) MG_CUDA(cudaMemcpyAsync(u_host, h->scratch + L.nvox, L.nvox * 8,
+                                        cudaMemcpyDeviceToHost, h->stream));
+    MG_CUDA(cudaStreamSynchronize(h->stream));
+    return MG3D_OK;
+}
+
+int mg3d_formal_solve_dev(mg3d_handle *h, int level, int prec, double *jeff_dev, double *u_dev,
+                          void *cuda_stream) {
+    MG_TRY(check_fs_call(h, level, prec));
+    const Level &L = h->lev[level];
+    const cudaStream_t cs = static_cast<cudaStream_t>(cuda_stream);
+    MG_TRY(order_after(h, cs, h->stream));
+    MG_TRY(formal_solution_into_scratch(h, level, prec));
+    if (jeff_dev) MG_CUDA(cudaMemcpyAsync(jeff_dev, h->scratch, L.nvox * 8,
+                                          cudaMemcpyDeviceToDevice, h->stream));
+    if (u_dev) MG_CUDA(cudaMemcpyAsync(u_dev, h->scratch + L.nvox, L.nvox * 8,
+                                       cudaMemcpyDeviceToDevice, h->stream));
+    return order_after(h, h->stream, cs);
+}
+
+int mg3d_get_populations_dev(mg3d_handle *h, int level, double *n_dev, void *cuda_stream) {
+    MG_TRY(check_level(h, level));
+    if (!n_dev) return fail(MG3D_E_ARG, "null buffer");
+    const Level &L = h->lev[level];
+    const cudaStream_t cs = static_cast<cudaStream_t>(cuda_stream);
+    MG_TRY(order_after(h, cs, h->stream));
+    MG_CUDA(cudaMemcpyAsync(n_dev, L.n, (size_t)h->N * L.nvox * sizeof(double),
+                            cudaMemcpyDeviceToDevice, h->stream));
+    return order_after(h, h->stream, cs);
+}
+
+int mg3d_set_populations_dev(mg3d_handle *h, int level, const double *n_dev,
+                             void *cuda_stream) {
+    MG_TRY(check_level(h, level));
+    if (!n_dev) return fail(MG3D_E_ARG, "null buffer");
+    const Level &L = h->lev[level];
+    const cudaStream_t cs = static_cast<cudaStream_t>(cuda_stream);
+    MG_TRY(order_after(h, cs, h->stream));
+    MG_CUDA(cudaMemcpyAsync(L.n, n_dev, (size_t)h->N * L.nvox * sizeof(double),
+                            cudaMemcpyDeviceToDevice, h->stream));
+    return order_after(h, h->stream, cs);
 }
 
 int mg3d_mali_sweep(mg3d_handle *h, int level, int n_sweeps, double *max_rel_change) {

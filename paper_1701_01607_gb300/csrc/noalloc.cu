@@ -12,10 +12,14 @@
 //
 // The array's name is only a host-side stand-in in host code; its device
 // address is obtained once per device with cudaGetSymbolAddress (on the first
-// call made while that device is current) and passed to the kernels.  All
-// calls share the array, so calls whose work overlaps on the GPU race; each
-// call rewrites every scratch entry it reads, so nothing carries over from one
-// call to the next.
+// call made while that device is current) and passed to the kernels.  With
+// lazy module loading (the CUDA default) that first lookup is also when the
+// device reserves the array, so it can fail for lack of memory (MG3D_E_OOM)
+// if the caller's allocator already holds the device's memory; the same
+// one-time set-up fills the exponential table from the host.  All calls share
+// the array, so calls whose work overlaps on the GPU race; each call rewrites
+// every other scratch entry it reads, so nothing carries over from one call to
+// the next.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -70,9 +74,22 @@ int scratch_address(double **out) {
     if (!g_addr[dev]) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e == cudaSuccess) {
+            // the table of 2^(j/256) the sweep's FP64 exp uses, correctly
+            // rounded on the host: written once, read by every call
+            double tab[kExpTab], l1 = 0.0, l2 = 0.0;
+            exp_neg_constants(tab, &l1, &l2);
+            e = cudaMemcpyToSymbol(g_noalloc_scratch, tab, sizeof(tab),
+                                   kOffExpTab * sizeof(double), cudaMemcpyHostToDevice);
+        }
         if (e != cudaSuccess) {
-            record_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-            return MG3D_E_CUDA;
+            const bool oom = e == cudaErrorMemoryAllocation;
+            cudaGetLastError();
+            record_error(std::string(oom ? "allocation-free scratch could not be reserved on "
+                                           "this device (first call, device memory full): "
+                                         : "allocation-free scratch set-up: ") +
+                         cudaGetErrorString(e));
+            return oom ? MG3D_E_OOM : MG3D_E_CUDA;
         }
         g_addr[dev] = static_cast<double *>(p);
     }
@@ -130,9 +147,6 @@ __global__ void noalloc_tables_kernel(int nx, int ny, int nz, double dx, double 
         }
         for (int f = 0; f < nfreq; ++f) wphi[f] /= sum * kRays;
     }
-    if (blockIdx.x == 0)
-        for (int j = threadIdx.x; j < kExpTab; j += blockDim.x)
-            scratch[kOffExpTab + j] = exp2((double)j / kExpTab);
 }
 
 // Jeff and U: the 24 ray partials of every node added in ray order.
@@ -163,6 +177,11 @@ extern "C" int mg3d_formal_solve_noalloc(int nx, int ny, int nz, double dx, doub
                                          double *jeff_dev, double *u_dev, void *cuda_stream) {
     if (!atom || !z_dev || !chi0_dev || !S_dev || !bbot_dev || !jeff_dev || !u_dev) {
         record_error("null argument");
+        return MG3D_E_ARG;
+    }
+    if (!std::isfinite(quad_a) || (quad_a > 0.0 && 2.0 * quad_a * quad_a >= 1.0)) {
+        record_error("quadrature parameter a must be finite and below 1/sqrt(2) "
+                     "(a <= 0 selects the default A4 set)");
         return MG3D_E_ARG;
     }
     if (nx < 1 || ny < 1 || nz < 2 || !(dx > 0.0) || !(dy > 0.0)) {
@@ -199,7 +218,8 @@ extern "C" int mg3d_formal_solve_noalloc(int nx, int ny, int nz, double dx, doub
         }
     }
     if (shape.bands == 0) {
-        record_error("plane too large for the sweep's shared memory on the allocation-free path");
+        record_error("plane too large for the sweep's shared memory on the allocation-free path "
+                     "(all n_freq intensity planes of a row band, at most 8 bands of 200 KB)");
         return MG3D_E_ARG;
     }
     const int band = shape.rows * nx;

@@ -154,6 +154,11 @@ _SIGNATURES = {
     "mg3d_autotune": (_I, [_H, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),
     "mg3d_check_exp": (_I, [_I, _D, _D]),
     "mg3d_probe_alu_peaks": (_I, [_I, _D]),
+    "mg3d_formal_solve_ex": (_I, [_H, _I, _I, _D, _D]),
+    "mg3d_formal_solve_dev": (_I, [_H, _I, _I, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p]),
+    "mg3d_get_populations_dev": (_I, [_H, _I, ctypes.c_void_p, ctypes.c_void_p]),
+    "mg3d_set_populations_dev": (_I, [_H, _I, ctypes.c_void_p, ctypes.c_void_p]),
     "mg3d_check_profiles": (_I, [_I, ctypes.c_double, _D, _D, _D]),
     "mg3d_check_voigt": (_I, [_I, _D, _D, _D]),
     "mg3d_set_graphs": (_I, [_H, _I]),
@@ -345,6 +350,34 @@ def mg3d_formal_solve(h, level: int, want: bool = True):
     u = np.empty((nz, ny, nx)) if want else None
     _check(load().mg3d_formal_solve(h, level, _dptr(jeff), _dptr(u)))
     return jeff, u
+
+
+def mg3d_formal_solve_ex(h, level: int, prec: int, want: bool = True):
+    """Formal solution in precision ``prec``; host outputs like mg3d_formal_solve."""
+    nx, ny, nz = mg3d_level_shape(h, level)
+    jeff = np.empty((nz, ny, nx)) if want else None
+    u = np.empty((nz, ny, nx)) if want else None
+    _check(load().mg3d_formal_solve_ex(h, level, prec, _dptr(jeff), _dptr(u)))
+    return jeff, u
+
+
+def mg3d_formal_solve_dev(h, level: int, prec: int, jeff_dev: int | None, u_dev: int | None,
+                          stream_ptr: int | None = None):
+    """Formal solution into device buffers (addresses, e.g. tensor.data_ptr()),
+    ordered on the CUDA stream ``stream_ptr``; does not synchronise."""
+    return _check(load().mg3d_formal_solve_dev(h, level, prec, ctypes.c_void_p(jeff_dev or 0),
+                                               ctypes.c_void_p(u_dev or 0),
+                                               ctypes.c_void_p(stream_ptr or 0)))
+
+
+def mg3d_get_populations_dev(h, level: int, n_dev: int, stream_ptr: int | None = None):
+    return _check(load().mg3d_get_populations_dev(h, level, ctypes.c_void_p(n_dev),
+                                                  ctypes.c_void_p(stream_ptr or 0)))
+
+
+def mg3d_set_populations_dev(h, level: int, n_dev: int, stream_ptr: int | None = None):
+    return _check(load().mg3d_set_populations_dev(h, level, ctypes.c_void_p(n_dev),
+                                                  ctypes.c_void_p(stream_ptr or 0)))
 
 
 def mg3d_mali_sweep(h, level: int, n_sweeps: int = 1) -> float:

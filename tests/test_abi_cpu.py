@@ -103,6 +103,20 @@ def test_allocation_free_call_refuses_prd_and_damping(lib):
         assert "Doppler" in m.mg3d_last_error()
 
 
+def test_quadrature_parameter_is_checked_before_the_gpu(lib):
+    """a >= 1/sqrt(2) leaves b = sqrt(1 - 2a^2) without a real positive value,
+    and a non-finite a is no quadrature: both entry points refuse them before
+    any CUDA call (the dummy addresses are never touched)."""
+    atm, atom = synth.stratified_two_level(8, 8, 9, eps=1e-3)
+    for a in (0.75, 2.0 ** -0.5, float("nan"), float("inf")):
+        with pytest.raises(m.MG3DError) as ei:
+            m.mg3d_create(atm, atom, quad_a=a, n_grids=1)
+        assert ei.value.code == m.MG3D_E_ARG and "quadrature" in m.mg3d_last_error()
+        rc = m.mg3d_formal_solve_noalloc(4, 4, 5, 1.0, 1.0, 256, synth.TwoLevelAtom(), a, 256,
+                                         256, 256, 256, 256)
+        assert rc == m.MG3D_E_ARG and "quadrature" in m.mg3d_last_error()
+
+
 def test_host_line_tables_match_scipy_and_the_oracle(lib):
     """The Voigt function and R_II-A the library tabulates for damped atoms
     (host code, no GPU) against scipy's Faddeeva function and the oracle's

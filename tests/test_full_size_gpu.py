@@ -1,13 +1,22 @@
 """Multi-level chromospheres at their full sizes, against the oracle.
 
 The oracle cannot run a 128x128x257 or 256x256x385 formal solution with 600
-frequencies in seconds, but a horizontally homogeneous atmosphere pins the
-full-size GPU path all the same: with every plane uniform, the bilinear
-upwind interpolation is exact, so the 3D solution is the same in every column
-and equals the solution on a 2x2 column with the same stratification, which
-the oracle computes in seconds.  The GPU runs in the launch configuration of
-the full size (its row bands, rays per block and frequency chunks).
-Bars: 1e-10 on FP64 populations, 1e-4 with the FP32 formal solution.
+frequencies in seconds.  Two kinds of case pin the full-size GPU path:
+
+* a horizontally homogeneous atmosphere at the full size: with every plane
+  uniform the bilinear upwind interpolation is exact, so the 3D solution is
+  the same in every column and equals the solution on a 2x2 column with the
+  same stratification, which the oracle computes in seconds.  This runs the
+  full size's planes, frequency chunks and launch configuration, but cannot
+  see a wrong upwind row, ray-group slot or wrap;
+* the full width with horizontal structure: 3D-perturbed chromospheres with
+  128- and 256-wide planes, few planes and few frequencies, swept in the
+  launch shapes the full sizes take (their row bands, rays per block and
+  block sizes), compared with the oracle element by element.  A wrong peer
+  band, slot or wrap changes these results.
+
+Bars: per-frequency angle sums 1e-11 (FP64) and 2e-4 (FP32), populations
+1e-10 (FP64) and 1e-4 (FP32 formal solution).
 """
 
 import numpy as np
@@ -139,3 +148,99 @@ def test_bench_box_prd_fp64():
     atom = synth.TwoLevelAtom(n_freq=9, gamma_prd=1.0)
     atm, atom = synth.stratified_two_level(64, 64, 129, eps=1e-4, sigma=0.3, seed=1, atom=atom)
     assert _two_level_sweeps(atm, atom) < 1e-10
+
+
+# ------------------- full width with horizontal structure, full-size shapes
+
+# Launch shapes (bands, rays per block, threads) of the full sizes: the
+# library's defaults at 128x128x257 and 256x256x385 (600 frequencies), and the
+# FP32 shape the autotuner takes at 128x128x257.
+FULL_WIDTH_SHAPES = [
+    (128, m.MG3D_PREC_F64, (8, 6, 256)),
+    (128, m.MG3D_PREC_F32, (8, 12, 256)),
+    (128, m.MG3D_PREC_F32, (8, 3, 512)),
+    (256, m.MG3D_PREC_F64, (6, 1, 256)),
+    (256, m.MG3D_PREC_F32, (8, 3, 256)),
+]
+
+_FS = {}
+
+
+def structured(nx, nz):
+    """A 3D-perturbed chromosphere (temperature perturbations 10 %) with 15
+    frequencies (5 lines x 2, 5 continua x 1)."""
+    atom = synth.hydrogen_like_atom(line_freq=2, cont_freq=1, seed=2)
+    return synth.chromosphere(nx, nx, nz, atom, seed=5), atom
+
+
+def per_frequency_error(got, ref):
+    nf = ref.shape[0]
+    err = np.max(np.abs(got.reshape(nf, -1) - ref), axis=1) / np.max(np.abs(ref), axis=1)
+    return float(err.max())
+
+
+@pytest.mark.parametrize("nx,prec,shape", FULL_WIDTH_SHAPES)
+def test_full_width_structured_formal_solution(nx, prec, shape):
+    nz = 9 if nx == 128 else 5
+    atm, atom = structured(nx, nz)
+    if nx not in _FS:
+        p = O.MultiLevelProblem(atm, atom)
+        Jo, Uo, _ = p.formal_solution(1, p.zero_radiation(1))
+        _FS[nx] = (Jo, Uo)
+    Jo, Uo = _FS[nx]
+    h = m.mg3d_create_ml(atm, atom, n_grids=1, fs_prec=prec)
+    try:
+        m.mg3d_set_ml_shape(h, 1, *shape)
+        assert m.mg3d_get_ml_shape(h, 1) == shape
+        jx, ux = m.mg3d_formal_solve_ml(h, 1)
+    finally:
+        m.mg3d_destroy(h)
+    tol = 1e-11 if prec == m.MG3D_PREC_F64 else 2e-4
+    assert per_frequency_error(jx, Jo) < tol
+    assert per_frequency_error(ux, Uo) < tol
+
+
+def test_full_width_structured_fas_vcycle_fp64():
+    """A 3-grid FAS V-cycle on 128x128x9 with the finest grid in the
+    128x128x257 FP64 launch shape, and the two coarser grids in theirs:
+    populations after the cycle against the oracle's cycle to 1e-10."""
+    atm, atom = structured(128, 9)
+    params = dict(nu_fmg=4, nu0=1, nu1=1, nu2=1, nu3=4)
+    p = O.MultiLevelProblem(atm, atom, n_grids=3)
+    n_o, _ = p.fas_cycle(p.zero_radiation(3), True, params)
+    h = m.mg3d_create_ml(atm, atom, n_grids=3, fs_prec=m.MG3D_PREC_F64, **params)
+    try:
+        for level, shape in ((3, (8, 6, 256)), (2, (4, 12, 256)), (1, (2, 12, 256))):
+            m.mg3d_set_ml_shape(h, level, *shape)
+        m.mg3d_fas_vcycle(h, True)
+        n = m.mg3d_get_populations(h, 3)
+    finally:
+        m.mg3d_destroy(h)
+    assert float(np.max(np.abs(n - n_o) / np.abs(n_o))) < 1e-10
+
+
+# ---------------- mixed precision against the FP64 oracle: FAS and FMG solves
+
+TWO_LEVEL_PARAMS = dict(nu_fmg=16, nu0=0, nu1=2, nu2=2, nu3=32)
+
+
+@pytest.mark.parametrize("method", ["fas", "fmg"])
+def test_two_level_fp32_solve_against_fp64_oracle(method):
+    """The benchmark spec's mixed-precision bar: a two-grid FAS (or FMG) solve to
+    C < 1e-3 with the FP32 formal solution and FP64 rates matches the FP64
+    oracle's solve of the same schedule to 1e-4 relative on the populations,
+    with the same number of V-cycles (16x16x33 box, eps = 1e-4, log-normal
+    sigma = 0.3; the oracle's solves take seconds at this size)."""
+    atm, atom = synth.stratified_two_level(16, 16, 33, eps=1e-4, sigma=0.3, seed=3)
+    prob = O.TwoLevelProblem(atm, atom, n_grids=2)
+    solve_o = O.fas_solve if method == "fas" else O.fmg_solve
+    n_o, cycles_o = solve_o(prob, 1e-3, TWO_LEVEL_PARAMS)
+    h = m.mg3d_create(atm, atom, n_grids=2, fs_prec=m.MG3D_PREC_F32, **TWO_LEVEL_PARAMS)
+    try:
+        solve = m.mg3d_fas_solve if method == "fas" else m.mg3d_fmg_solve
+        st = solve(h, 1e-3, 100, n_grids=2)
+        n = m.mg3d_get_populations(h, 2)
+    finally:
+        m.mg3d_destroy(h)
+    assert st["iterations"] == cycles_o
+    assert float(np.max(np.abs(n - n_o) / np.abs(n_o))) < 1e-4

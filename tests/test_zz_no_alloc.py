@@ -4,10 +4,10 @@ mg3d_formal_solve_noalloc is for callers that cannot allocate device memory
 when they need a formal solution (code under another framework's memory pool,
 allocation-free sections of a pipeline, a process whose device memory is all
 held by a caching allocator).  Here the caller's buffers come from torch; the
-entry point itself must allocate nothing.  Two calls in a row must both give
-the Jeff and U of mg3d_formal_solve to the FP64 formal-solution tolerance of
-the parity tests (1e-12 relative), so nothing left in the shared scratch by
-one call may leak into the next.
+entry point itself must allocate nothing.  Calls in a row on different
+problems must each give the Jeff and U of mg3d_formal_solve on that problem to
+the FP64 formal-solution tolerance of the parity tests (1e-12 relative), so
+nothing left in the shared scratch by one call may leak into the next.
 
 This file is named to be collected last.
 """
@@ -27,35 +27,48 @@ def rel(a, b):
     return float(np.max(np.abs(a - b) / np.abs(b)))
 
 
-def test_noalloc_formal_solution_matches_handle_path_twice():
-    torch = pytest.importorskip("torch")
-    m.load(build_if_missing=True)
-    atm, atom = synth.stratified_two_level(16, 16, 33, eps=1e-3, sigma=0.3, seed=21)
+def _case(nx, ny, nz, seed, sweeps):
+    """A box, its handle-path Jeff and U after `sweeps` MALI sweeps, and the
+    caller's inputs (chi0, S, bottom intensity) from the same populations."""
+    atm, atom = synth.stratified_two_level(nx, ny, nz, eps=1e-3, sigma=0.3, seed=seed)
     h = m.mg3d_create(atm, atom, n_grids=1, fs_prec=m.MG3D_PREC_F64)
     try:
-        m.mg3d_mali_sweep(h, 1, 2)
+        m.mg3d_mali_sweep(h, 1, sweeps)
         n = m.mg3d_get_populations(h, 1)
         j_ref, u_ref = m.mg3d_formal_solve(h, 1)
     finally:
         m.mg3d_destroy(h)
-
-    # the caller's inputs, from the same populations
     diff = n[0] * atom.g_ratio - n[1]
-    chi0 = atom.kappa * diff
-    S = n[1] / diff
-    bbot = 1.0 / np.expm1(atom.theta / atm.T[0])
+    return atm, atom, atom.kappa * diff, n[1] / diff, 1.0 / np.expm1(atom.theta / atm.T[0]), \
+        j_ref, u_ref
+
+
+def test_noalloc_formal_solution_matches_handle_path_twice():
+    """Two calls in a row on different problems (the second on a smaller grid
+    with other opacities and source functions), each against its own
+    handle-path result; outputs start as NaN, and after the first call (which
+    reserves the scratch on this device) the calls change the device's free
+    memory by nothing."""
+    torch = pytest.importorskip("torch")
+    m.load(build_if_missing=True)
     dev = torch.device("cuda")
 
     def d(a):
         return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
 
-    z_d, chi_d, S_d, b_d = d(atm.z), d(chi0), d(S), d(bbot)
-    j_d = torch.empty(atm.shape, dtype=torch.float64, device=dev)
-    u_d = torch.empty(atm.shape, dtype=torch.float64, device=dev)
+    cases = [_case(16, 16, 33, 21, 2), _case(8, 12, 17, 22, 5), _case(16, 16, 33, 21, 2)]
+    bufs = []
+    for atm, atom, chi0, S, bbot, _, _ in cases:
+        bufs.append((d(atm.z), d(chi0), d(S), d(bbot),
+                     torch.empty(atm.shape, dtype=torch.float64, device=dev),
+                     torch.empty(atm.shape, dtype=torch.float64, device=dev)))
+    torch.cuda.synchronize()
     stream = torch.cuda.current_stream().cuda_stream
-    for call in range(2):
+    free_after_first = None
+    for call, ((atm, atom, _, _, _, j_ref, u_ref), (z_d, chi_d, S_d, b_d, j_d, u_d)) in \
+            enumerate(zip(cases, bufs)):
         j_d.fill_(float("nan"))
-        u_d.fill_(-1.0)
+        u_d.fill_(float("nan"))
         torch.cuda.synchronize()
         rc = m.mg3d_formal_solve_noalloc(atm.nx, atm.ny, atm.nz, atm.dx, atm.dy,
                                          z_d.data_ptr(), atom, 0.0, chi_d.data_ptr(),
@@ -63,10 +76,27 @@ def test_noalloc_formal_solution_matches_handle_path_twice():
                                          u_d.data_ptr(), stream)
         torch.cuda.synchronize()
         assert rc == m.MG3D_OK, m.mg3d_last_error()
-        j = j_d.cpu().numpy()
-        u = u_d.cpu().numpy()
-        assert rel(j, j_ref) < TOL_FS64, call
-        assert rel(u, u_ref) < TOL_FS64, call
+        free = torch.cuda.mem_get_info()[0]
+        if call == 0:
+            free_after_first = free
+        else:
+            assert free == free_after_first, call
+        assert rel(j_d.cpu().numpy(), j_ref) < TOL_FS64, call
+        assert rel(u_d.cpu().numpy(), u_ref) < TOL_FS64, call
+
+
+def test_noalloc_refuses_planes_beyond_shared_memory():
+    """Within the node, plane and frequency limits a plane can still be too
+    large for one band's intensities of every frequency: 64 x 64 with 32
+    frequencies is refused with a message, before any work is enqueued."""
+    torch = pytest.importorskip("torch")
+    m.load(build_if_missing=True)
+    atom = synth.TwoLevelAtom(n_freq=32)
+    buf = torch.zeros(16, dtype=torch.float64, device="cuda")
+    p = buf.data_ptr()
+    rc = m.mg3d_formal_solve_noalloc(64, 64, 9, 1.0, 1.0, p, atom, 0.0, p, p, p, p, p, None)
+    assert rc == m.MG3D_E_ARG
+    assert "shared memory" in m.mg3d_last_error()
 
 
 def test_noalloc_rejects_grids_beyond_its_limit():
