@@ -303,6 +303,18 @@ int mg3d_fas_solve(mg3d_handle *h, double tol, int max_cycles, mg3d_stats *stats
  * until C(cycle) < tol. */
 int mg3d_fmg_solve(mg3d_handle *h, double tol, int max_cycles, mg3d_stats *stats);
 
+/* One stage of full multigrid (Sec. 2.3, Fig. 1), for callers that inspect
+ * each grid's solution as FMG builds it: stage 1 starts grid 1 from the
+ * zero-radiation populations and runs nu_fmg MALI sweeps on it; stage k =
+ * 2..n_grids interpolates the full approximation from grid k-1 to grid k
+ * (Sec. 4.5) and, below the finest grid, runs one V-cycle on grid k.  After
+ * stage k, mg3d_get_populations(h, k) reads grid k's approximation.  Stages
+ * run in order (MG3D_E_STATE otherwise; stage 1 restarts);
+ * mg3d_fmg_solve is stages 1..n_grids followed by V-cycles on the finest grid
+ * (mg3d_fas_vcycle, the first with is_first = 1) until C < tol.  Synchronises
+ * the handle's stream. */
+int mg3d_fmg_stage(mg3d_handle *h, int stage);
+
 /* ------------------------------------------------------------------------
  * Multi-level atoms (Sec. 3.2: the paper's 3- and 6-level Ca II and H I atoms;
  * here any atom of 2..8 levels with lines and bound-free continua).

@@ -42,6 +42,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 static long node_index(long x, long y, long k, long nx, long ny)
 {
@@ -225,6 +228,67 @@ int orc_formal_solution(long nx, long ny, long nz, double dx, double dy,
     free(Icur);
     free(W0);
     return 0;
+}
+
+/*
+ * The same formal solution with the rays spread over `nthreads` host threads
+ * (OpenMP, when the file is compiled with it; otherwise one thread): each ray
+ * runs orc_formal_solution above on its own, into its own partial sums, and
+ * the partial sums are then added in ray order.  It exists to time the
+ * oracle on all cores of a host (the bench's CPU baseline); the sums differ
+ * from the serial ones only in their association (rounding).  Same
+ * arguments as orc_formal_solution without I_out; returns 0, or -1 on a bad
+ * argument or a failed allocation.
+ */
+int orc_formal_solution_threads(long nx, long ny, long nz, double dx, double dy,
+                                const double *z, long nrays, const double *mu,
+                                const double *wray, long nfreq, const double *chi,
+                                const double *S, const double *wphi,
+                                const double *I_bottom, const double *I_top,
+                                double *Jbar, double *Jeff, double *U, int interp, int nthreads)
+{
+    if (nrays < 1 || nthreads < 1 || nx < 1 || ny < 1 || nz < 2)
+        return -1;
+    long nvox = nx * ny * nz;
+    double *part = malloc(sizeof(double) * 3 * (size_t)nrays * (size_t)nvox);
+    if (!part)
+        return -1;
+    int bad = 0;
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nthreads) schedule(dynamic, 1) reduction(| : bad)
+#endif
+    for (long r = 0; r < nrays; ++r) {
+        double *p = part + 3 * r * nvox;
+        bad |= orc_formal_solution(nx, ny, nz, dx, dy, z, 1, mu + 3 * r, wray + r, nfreq, chi,
+                                   S, wphi, I_bottom, I_top, p, p + nvox, p + 2 * nvox, NULL,
+                                   interp) != 0;
+    }
+    if (!bad) {
+        for (long v = 0; v < nvox; ++v) {
+            double jb = 0.0, je = 0.0, u = 0.0;
+            for (long r = 0; r < nrays; ++r) {
+                const double *p = part + 3 * r * nvox;
+                jb += p[v];
+                je += p[nvox + v];
+                u += p[2 * nvox + v];
+            }
+            Jbar[v] = jb;
+            Jeff[v] = je;
+            U[v] = u;
+        }
+    }
+    free(part);
+    return bad ? -1 : 0;
+}
+
+/* Threads the OpenMP runtime offers (1 without OpenMP). */
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /*

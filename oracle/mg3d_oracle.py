@@ -85,15 +85,19 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle/fs_oracle.c into oracle/_build/liboracle.so (plain gcc)."""
+    """Compile oracle/fs_oracle.c into oracle/_build/liboracle.so (plain gcc,
+    with OpenMP for the all-cores timing entry when the compiler has it)."""
     src = os.path.join(_HERE, "fs_oracle.c")
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(src)):
         return _LIB_PATH
     os.makedirs(_BUILD, exist_ok=True)
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp,
-                           src, "-lm"])
+    base = ["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, src, "-lm"]
+    try:
+        subprocess.check_call(base + ["-fopenmp"], stderr=subprocess.DEVNULL)
+    except subprocess.CalledProcessError:
+        subprocess.check_call(base)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -107,12 +111,24 @@ def _load():
         lib.orc_formal_solution.argtypes = [
             ctypes.c_long, ctypes.c_long, ctypes.c_long, ctypes.c_double, ctypes.c_double,
             d, ctypes.c_long, d, d, ctypes.c_long, d, d, d, d, d, d, d, d, d, ctypes.c_int]
+        lib.orc_formal_solution_threads.restype = ctypes.c_int
+        lib.orc_formal_solution_threads.argtypes = [
+            ctypes.c_long, ctypes.c_long, ctypes.c_long, ctypes.c_double, ctypes.c_double,
+            d, ctypes.c_long, d, d, ctypes.c_long, d, d, d, d, d, d, d, d, ctypes.c_int,
+            ctypes.c_int]
+        lib.orc_max_threads.restype = ctypes.c_int
+        lib.orc_max_threads.argtypes = []
         lib.orc_formal_solution_nu.restype = ctypes.c_int
         lib.orc_formal_solution_nu.argtypes = [
             ctypes.c_long, ctypes.c_long, ctypes.c_long, ctypes.c_double, ctypes.c_double,
             d, ctypes.c_long, d, d, ctypes.c_long, d, d, d, d, d, d, d, d, d, ctypes.c_int]
         _lib = lib
     return _lib
+
+
+def max_threads() -> int:
+    """Host threads the oracle's OpenMP runtime offers (1 without OpenMP)."""
+    return int(_load().orc_max_threads())
 
 
 def _ptr(a):
@@ -285,6 +301,9 @@ class TwoLevelProblem:
         self.restriction = restriction
         self.interpolation = interpolation
         self.sc_interp = sc_interp
+        # host threads of the static two-level formal solution (1: the plain
+        # serial loop; more: rays in parallel, for timing on all cores)
+        self.threads = 1
         self.mu, self.wray = a4_quadrature(quad_a)
         self.a_damp = float(getattr(atom, "a_damp", 0.0))
         self.x, self.phi, self.wphi = frequency_grid(atom.n_freq, atom.x_max, self.a_damp)
@@ -405,11 +424,19 @@ class TwoLevelProblem:
         Jeff = np.empty(nvox)
         U = np.empty(nvox)
         mu = np.ascontiguousarray(self.mu)
-        rc = _load().orc_formal_solution(
-            lev.nx, lev.ny, lev.nz, lev.dx, lev.dy, _ptr(np.ascontiguousarray(lev.z)),
-            len(self.wray), _ptr(mu), _ptr(self.wray), nf, _ptr(chi), _ptr(Sf),
-            _ptr(wphi), _ptr(Ib), _ptr(It), _ptr(Jbar), _ptr(Jeff), _ptr(U), None,
-            int(self.sc_interp))
+        if self.threads > 1:
+            # rays on several host threads (timing the oracle on all cores)
+            rc = _load().orc_formal_solution_threads(
+                lev.nx, lev.ny, lev.nz, lev.dx, lev.dy, _ptr(np.ascontiguousarray(lev.z)),
+                len(self.wray), _ptr(mu), _ptr(self.wray), nf, _ptr(chi), _ptr(Sf),
+                _ptr(wphi), _ptr(Ib), _ptr(It), _ptr(Jbar), _ptr(Jeff), _ptr(U),
+                int(self.sc_interp), int(self.threads))
+        else:
+            rc = _load().orc_formal_solution(
+                lev.nx, lev.ny, lev.nz, lev.dx, lev.dy, _ptr(np.ascontiguousarray(lev.z)),
+                len(self.wray), _ptr(mu), _ptr(self.wray), nf, _ptr(chi), _ptr(Sf),
+                _ptr(wphi), _ptr(Ib), _ptr(It), _ptr(Jbar), _ptr(Jeff), _ptr(U), None,
+                int(self.sc_interp))
         if rc != 0:
             raise RuntimeError("oracle formal solution failed")
         self.fs_count[k] += 1

@@ -127,6 +127,7 @@ struct mg3d_handle {
     int ml_chunk = 0;
     int ml_chunk_req = 0;        // chunk asked for (0: automatic), kept across retuning
     bool scatter = false;        // background coherent scattering present
+    int fmg_next = 1;            // the FMG stage mg3d_fmg_stage may run next (1 restarts)
     int top = 0;                 // grid being solved (0: the finest); only its formal
                                  // solutions update its background field
     bool force_bg = false;       // the current formal solution is a Lambda-iteration
@@ -3329,41 +3330,63 @@ int mg3d_fas_solve(mg3d_handle *h, double tol, int max_cycles, mg3d_stats *stats
     return MG3D_OK;
 }
 
+// Stage k of full multigrid (Sec. 2.3, Fig. 1): k = 1 starts grid 1 from the
+// zero-radiation populations and runs nu_fmg MALI sweeps on it; k >= 2
+// interpolates the full approximation (and the lagged fields) from grid k-1
+// to grid k and, below the finest grid, runs one V-cycle on grid k.
+int fmg_stage(mg3d_handle *h, int k) {
+    h->top = k;  // each stage solves on its own grid
+    if (k == 1) {
+        MG_TRY(zero_radiation(h, 1));
+        for (int i = 0; i < h->params.nu_fmg; ++i) MG_TRY(sweep(h, 1));
+        return MG3D_OK;
+    }
+    Level &Fk = h->lev[k];
+    Level &Ck = h->lev[k - 1];
+    MG_TRY(launched(h, launch_prolong(h->params.interpolation, h->N, Ck.nx, Ck.ny, Ck.nz,
+                                      Fk.tz, Fk.zf, Ck.n, Fk.n, h->stream),
+                    "prolong full approximation"));
+    if (h->kind == 1 && h->scatter)
+        MG_TRY(launched(h, launch_prolong_prec(h->params.interpolation, h->prec, h->nfreq_ml,
+                                               Ck.nx, Ck.ny, Ck.nz, Fk.tz, Fk.zf, Ck.jbg,
+                                               Fk.jbg, h->stream),
+                        "prolong background field"));
+    if (h->kind == 0 && h->prd)
+        MG_TRY(launched(h, launch_prolong_prec(h->params.interpolation, h->prec,
+                                               h->atom.n_freq, Ck.nx, Ck.ny, Ck.nz, Fk.tz,
+                                               Fk.zf, Ck.jnu, Fk.jnu, h->stream),
+                        "prolong mean intensity"));
+    Fk.f_default = true;
+    if (k < h->L) {
+        MG_TRY(reset_scalars(h));
+        MG_TRY(vcycle(h, k, false));
+        long long neg = 0;
+        MG_TRY(read_scalars(h, nullptr, &neg, nullptr));
+        h->negatives += neg;
+    }
+    return MG3D_OK;
+}
+
+int mg3d_fmg_stage(mg3d_handle *h, int stage) {
+    if (!h) return fail(MG3D_E_ARG, "null handle");
+    if (h->L < 2) return fail(MG3D_E_STATE, "FMG needs n_grids >= 2");
+    if (stage < 1 || stage > h->L) return fail(MG3D_E_ARG, "stage must be 1..n_grids");
+    if (stage != 1 && stage != h->fmg_next)
+        return fail(MG3D_E_STATE, "FMG stages run in order, starting at 1");
+    MG_TRY(fmg_stage(h, stage));
+    h->fmg_next = stage + 1;
+    MG_CUDA(cudaStreamSynchronize(h->stream));
+    return MG3D_OK;
+}
+
 int mg3d_fmg_solve(mg3d_handle *h, double tol, int max_cycles, mg3d_stats *stats) {
     if (!h) return fail(MG3D_E_ARG, "null handle");
     if (!(tol > 0.0) || max_cycles < 1) return fail(MG3D_E_ARG, "bad tol or max_cycles");
     if (h->L < 2) return fail(MG3D_E_STATE, "FMG needs n_grids >= 2");
     auto t0 = std::chrono::steady_clock::now();
     begin_stats(h);
-    h->top = 1;  // each stage solves on its own grid
-    MG_TRY(zero_radiation(h, 1));
-    for (int i = 0; i < h->params.nu_fmg; ++i) MG_TRY(sweep(h, 1));
-    for (int k = 2; k <= h->L; ++k) {
-        Level &Fk = h->lev[k];
-        Level &Ck = h->lev[k - 1];
-        h->top = k;
-        MG_TRY(launched(h, launch_prolong(h->params.interpolation, h->N, Ck.nx, Ck.ny, Ck.nz,
-                                          Fk.tz, Fk.zf, Ck.n, Fk.n, h->stream),
-                        "prolong full approximation"));
-        if (h->kind == 1 && h->scatter)
-            MG_TRY(launched(h, launch_prolong_prec(h->params.interpolation, h->prec, h->nfreq_ml,
-                                                   Ck.nx, Ck.ny, Ck.nz, Fk.tz, Fk.zf, Ck.jbg,
-                                                   Fk.jbg, h->stream),
-                            "prolong background field"));
-        if (h->kind == 0 && h->prd)
-            MG_TRY(launched(h, launch_prolong_prec(h->params.interpolation, h->prec,
-                                                   h->atom.n_freq, Ck.nx, Ck.ny, Ck.nz, Fk.tz,
-                                                   Fk.zf, Ck.jnu, Fk.jnu, h->stream),
-                            "prolong mean intensity"));
-        Fk.f_default = true;
-        if (k < h->L) {
-            MG_TRY(reset_scalars(h));
-            MG_TRY(vcycle(h, k, false));
-            long long neg = 0;
-            MG_TRY(read_scalars(h, nullptr, &neg, nullptr));
-            h->negatives += neg;
-        }
-    }
+    for (int k = 1; k <= h->L; ++k) MG_TRY(fmg_stage(h, k));
+    h->fmg_next = h->L + 1;
     double C = 1.0;
     int cyc = 0;
     while (cyc < max_cycles) {

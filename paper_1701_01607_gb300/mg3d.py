@@ -154,6 +154,7 @@ _SIGNATURES = {
     "mg3d_autotune": (_I, [_H, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),
     "mg3d_check_exp": (_I, [_I, _D, _D]),
     "mg3d_probe_alu_peaks": (_I, [_I, _D]),
+    "mg3d_fmg_stage": (_I, [_H, _I]),
     "mg3d_formal_solve_ex": (_I, [_H, _I, _I, _D, _D]),
     "mg3d_formal_solve_dev": (_I, [_H, _I, _I, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p]),
@@ -423,6 +424,10 @@ def mg3d_fas_solve(h, tol: float, max_cycles: int = 1000, n_grids: int = 1):
 
 def mg3d_fmg_solve(h, tol: float, max_cycles: int = 1000, n_grids: int = 1):
     return _solve(load().mg3d_fmg_solve, h, tol, max_cycles, n_grids)
+
+
+def mg3d_fmg_stage(h, stage: int):
+    return _check(load().mg3d_fmg_stage(h, stage))
 
 
 def mg3d_restrict(h, level_fine: int, fine):

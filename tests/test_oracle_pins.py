@@ -499,3 +499,17 @@ def test_zero_radiation_start_gives_a_smoother_error_than_lte():
             hist[name].append(smoothing_number(n))
     ratio = np.array(hist["lte"]) / np.array(hist["zero"])
     assert np.all(ratio[1:] > 3.0), ratio
+
+
+def test_threaded_formal_solution_equals_the_serial_loop():
+    """The all-cores timing entry (rays on several host threads, partial sums
+    added in ray order) computes the serial loop's Jbar, Jeff and U up to the
+    association of the sums."""
+    atm, atom = synth.stratified_two_level(8, 8, 17, eps=1e-3, sigma=0.3, seed=12)
+    p = O.TwoLevelProblem(atm, atom)
+    n = p.zero_radiation(1)
+    serial = p.formal_solution(1, n)
+    p.threads = 4
+    threaded = p.formal_solution(1, n)
+    for a, b in zip(threaded, serial):
+        assert float(np.max(np.abs(a - b) / np.abs(b))) < 1e-13
