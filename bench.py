@@ -983,7 +983,10 @@ def run_chromosphere(args):
     (nu_0, nu_1, nu_2, nu_3) = (20, 4, 8, 32), sweep shapes autotuned first;
     opt-in, --chromosphere).  ``--scattering`` sets the grey background
     scattering opacity in units of the thermal continuum opacity (Sec. 4.8),
-    ``--ground-collisions`` scales the collisions out of the ground level.
+    ``--ground-collisions`` scales the collisions out of the ground level
+    (default 1e-3: scattering-dominated resonance lines, so that MALI's
+    spectral radius is close to one as in the paper's chromospheres; 1 gives
+    collision-dominated lines that MALI solves in a few sweeps).
     Prints one JSON line."""
     from paper_1701_01607_gb300 import mg3d as m
     from paper_1701_01607_gb300 import synth
@@ -1026,6 +1029,109 @@ def run_chromosphere(args):
     out["value"] = out["fas"].get("seconds")
     out["fine_fs_units"] = units_fine
     return out
+
+
+CONFIG4_PARAMS = dict(nu_fmg=16, nu0=20, nu1=4, nu2=8, nu3=32)
+
+
+def config4_atmosphere(size, freqs):
+    """The 6-level chromosphere of config 4: 256x256x385 nodes (``size``),
+    horizontal spacing 24 km taken as the length unit, heights stretched from
+    13 km in the middle to 60 km at the ends (the paper's Model 2 pattern),
+    seed 3; ``freqs`` (line, continuum) frequencies per transition."""
+    from paper_1701_01607_gb300 import synth
+    nx, ny, nz = size
+    atom = synth.hydrogen_like_atom(line_freq=freqs[0], cont_freq=freqs[1], seed=2)
+    z = synth.stretched_heights(nz, 13.0 / 24.0, 60.0 / 24.0)
+    return synth.chromosphere(nx, ny, nz, atom, seed=3, z=z, dx=1.0), atom
+
+
+def run_config4(args):
+    """Full multigrid on the config-4 chromosphere with 4 grids and
+    (nu_FMG, nu_0, nu_1, nu_2, nu_3) = (16, 20, 4, 8, 32) (Table 1, Model 2
+    row): the FP32 formal solution (FP64 rates) against FP64 throughout, the
+    error of FP32 against FP64 on each grid after each FMG stage (Sec. 2.3:
+    stage 1 solves grid 1, stage k interpolates to grid k and runs a V-cycle
+    there), then V-cycles on the finest grid to C < 1e-3; and FP32 MALI and
+    FAS to the same stopping rule.  Opt-in (--config4); --c4-size and
+    --c4-freqs shrink it.  Prints one JSON line."""
+    from paper_1701_01607_gb300 import mg3d as m
+    m.load(build_if_missing=True)
+    size = tuple(int(v) for v in args.c4_size.split(","))
+    freqs = tuple(int(v) for v in args.c4_freqs.split(","))
+    atm, atom = config4_atmosphere(size, freqs)
+    L = 4
+    runs = {}
+    for prec, key in ((m.MG3D_PREC_F32, "f32"), (m.MG3D_PREC_F64, "f64")):
+        if key == "f64" and args.c4_no_f64:
+            continue
+        h = m.mg3d_create_ml(atm, atom, n_grids=L, fs_prec=prec, **CONFIG4_PARAMS)
+        try:
+            t0 = time.perf_counter()
+            m.mg3d_autotune(h)
+            tune_s = time.perf_counter() - t0
+            stages, pops = [], []
+            m.mg3d_reset_counters(h)
+            t_all = time.perf_counter()
+            for k in range(1, L + 1):
+                t0 = time.perf_counter()
+                m.mg3d_fmg_stage(h, k)
+                stages.append(round(time.perf_counter() - t0, 3))
+                pops.append(m.mg3d_get_populations(h, k))
+            cs, cyc = [], 0
+            while cyc < args.c4_max_cycles:
+                cs.append(m.mg3d_fas_vcycle(h, cyc == 0))
+                cyc += 1
+                if cs[-1] < 1e-3:
+                    break
+            secs = time.perf_counter() - t_all
+            units = m.mg3d_get_counters(h)["fs_units"]
+            final = m.mg3d_get_populations(h, L)
+        finally:
+            m.mg3d_destroy(h)
+        runs[key] = {"autotune_s": round(tune_s, 1), "stage_seconds": stages,
+                     "cycles": cyc, "C": [float(c) for c in cs], "seconds": round(secs, 2),
+                     "fine_fs_equivalents": round(units / (np.prod(size) * 24 * n_freq_of(atom)),
+                                                  1),
+                     "pops": pops, "final": final,
+                     "conservation": float(np.max(np.abs(final.sum(axis=0) / atm.n_tot - 1)))}
+    out = {"metric": "config 4: FMG, FP32 formal solution against FP64, error per grid",
+           "unit": "s", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+           "config": {"workload": "chromosphere %dx%dx%d, 6-level atom, %d frequencies, stretched z "
+                                  "(13-60 km, dx = 24 km), seed 3" % (size + (n_freq_of(atom),)),
+                      "n_grids": L, **CONFIG4_PARAMS}}
+    for key, r in runs.items():
+        out[key] = {k: v for k, v in r.items() if k not in ("pops", "final")}
+    if "f64" in runs:
+        a, b = runs["f32"], runs["f64"]
+        out["f32_vs_f64_e_inf_by_stage"] = {
+            f"stage {k + 1} (grid {k + 1})": float(np.max(np.abs(a["pops"][k] - b["pops"][k])
+                                                       / np.abs(b["pops"][k])))
+            for k in range(L)}
+        out["f32_vs_f64_e_inf_final"] = float(np.max(np.abs(a["final"] - b["final"])
+                                                     / np.abs(b["final"])))
+    if not args.c4_no_mali:
+        for method, grids, fn in (("fas", L, m.mg3d_fas_solve), ("mali", 1, m.mg3d_mali_solve)):
+            h = m.mg3d_create_ml(atm, atom, n_grids=grids, fs_prec=m.MG3D_PREC_F32,
+                                 **CONFIG4_PARAMS)
+            try:
+                m.mg3d_autotune(h)
+                try:
+                    st = fn(h, 1e-3, 40 if method == "fas" else 400, n_grids=grids)
+                    out[method + "_f32"] = {"seconds": round(st["seconds"], 2),
+                                            "iterations": st["iterations"],
+                                            "fine_fs_equivalents": round(st["fine_fs_equivalents"], 1)}
+                except m.MG3DError as e:
+                    out[method + "_f32"] = {"reached": False, "error": str(e)}
+            finally:
+                m.mg3d_destroy(h)
+    out["value"] = out["f32"]["seconds"]
+    return out
+
+
+def n_freq_of(atom):
+    """Frequencies of a multi-level atom: every line's and continuum's."""
+    return sum(t.n_freq for t in atom.lines) + sum(t.n_freq for t in atom.continua)
 
 
 def run_profile_ml(prec_name, launches, shape=""):
@@ -1082,9 +1188,18 @@ def main():
     ap.add_argument("--scattering-experiment", action="store_true",
                     help="MALI and FAS to E_inf <= 1e-3 against background scattering strength")
     ap.add_argument("--chromo-size", default="128,128,257", help="nx,ny,nz of --chromosphere")
+    ap.add_argument("--config4", action="store_true",
+                    help="FMG on the 256x256x385 chromosphere, FP32 against FP64 per grid")
+    ap.add_argument("--c4-size", default="256,256,385", help="nx,ny,nz of --config4")
+    ap.add_argument("--c4-freqs", default="100,20",
+                    help="frequencies per line and per continuum of --config4")
+    ap.add_argument("--c4-max-cycles", type=int, default=20)
+    ap.add_argument("--c4-no-f64", action="store_true", help="--config4 without the FP64 run")
+    ap.add_argument("--c4-no-mali", action="store_true",
+                    help="--config4 without the FP32 MALI and FAS runs")
     ap.add_argument("--scattering", type=float, default=0.0,
                     help="--chromosphere: background scattering opacity / thermal continuum opacity")
-    ap.add_argument("--ground-collisions", type=float, default=1.0,
+    ap.add_argument("--ground-collisions", type=float, default=1e-3,
                     help="--chromosphere: factor on the collisions out of the ground level")
     ap.add_argument("--batch", action="store_true",
                     help="time batched V-cycles of the 32-atmosphere batch instead")
@@ -1110,6 +1225,9 @@ def main():
         return
     if args.batch:
         print(json.dumps(run_batch(args)), flush=True)
+        return
+    if args.config4:
+        print(json.dumps(run_config4(args)), flush=True)
         return
     if args.prd_experiment:
         print(json.dumps(run_prd(args)), flush=True)

@@ -181,6 +181,17 @@ def box_64x64x129_lognormal(seed: int = 1):
     return stratified_two_level(64, 64, 129, eps=1e-4, sigma=0.3, seed=seed)
 
 
+def stretched_heights(nz: int, d_mid: float, d_end: float, sharpness: float = 4.0):
+    """Node heights [nz] whose spacing is d_mid at the middle of the column and
+    grows smoothly (tanh^2 in the node index) to d_end at both ends, the
+    pattern of the paper's Model 2 grid (fine in the middle, coarse at top and
+    bottom).  z[0] = 0."""
+    u = (np.arange(nz - 1) + 0.5) / (nz - 1) - 0.5
+    t = np.tanh(sharpness * u) ** 2 / np.tanh(0.5 * sharpness) ** 2
+    d = d_mid + (d_end - d_mid) * t
+    return np.concatenate(([0.0], np.cumsum(d)))
+
+
 def zero_populations_like(atm: Atmosphere, n_levels: int = 2):
     return np.zeros((n_levels,) + atm.shape)
 

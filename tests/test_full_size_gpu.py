@@ -244,3 +244,37 @@ def test_two_level_fp32_solve_against_fp64_oracle(method):
         m.mg3d_destroy(h)
     assert st["iterations"] == cycles_o
     assert float(np.max(np.abs(n - n_o) / np.abs(n_o))) < 1e-4
+
+
+def test_config4_fmg_stages_fp32_against_fp64():
+    """Config 4 in small: full multigrid with 4 grids and (16, 20, 4, 8, 32) on
+    a stretched-height chromosphere (spacing 13/24 to 60/24 of dx, seed 3) with
+    30 frequencies.  After every FMG stage the FP32 formal solution's
+    approximation on that grid stays within 1e-4 of FP64's, and so do the
+    populations after the V-cycles to C < 1e-3, with the same cycle count."""
+    atom = synth.hydrogen_like_atom(line_freq=4, cont_freq=2, seed=2)
+    z = synth.stretched_heights(49, 13.0 / 24.0, 60.0 / 24.0)
+    atm = synth.chromosphere(32, 32, 49, atom, seed=3, z=z, dx=1.0)
+    params = dict(nu_fmg=16, nu0=20, nu1=4, nu2=8, nu3=32)
+    res = {}
+    for prec in (m.MG3D_PREC_F64, m.MG3D_PREC_F32):
+        h = m.mg3d_create_ml(atm, atom, n_grids=4, fs_prec=prec, **params)
+        try:
+            pops = []
+            for k in range(1, 5):
+                m.mg3d_fmg_stage(h, k)
+                pops.append(m.mg3d_get_populations(h, k))
+            cycles = 0
+            while cycles < 20:
+                c = m.mg3d_fas_vcycle(h, cycles == 0)
+                cycles += 1
+                if c < 1e-3:
+                    break
+            res[prec] = (pops, cycles, m.mg3d_get_populations(h, 4))
+        finally:
+            m.mg3d_destroy(h)
+    (p64, c64, n64), (p32, c32, n32) = res[m.MG3D_PREC_F64], res[m.MG3D_PREC_F32]
+    for k in range(4):
+        assert float(np.max(np.abs(p32[k] - p64[k]) / p64[k])) < 1e-4, k + 1
+    assert c32 == c64
+    assert float(np.max(np.abs(n32 - n64) / n64)) < 1e-4
