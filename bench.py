@@ -627,6 +627,26 @@ def run_batch(args):
             m.mg3d_destroy(h)
     units = c1["fs_units"] - c0["fs_units"]
     kinds = [k for k, _, _ in spec]
+    # the same members alone, one handle at a time, same schedule and steps:
+    # the aggregate throughput the batch replaces
+    solo_wall, solo_units = 0.0, 0.0
+    for kind, atm, atom in spec:
+        h = (m.mg3d_create(atm, atom, **params) if kind == "two"
+             else m.mg3d_create_ml(atm, atom, ml_chunk=100, **params))
+        try:
+            for i in range(args.warmup):
+                m.mg3d_fas_vcycle(h, i == 0)
+            u0 = m.mg3d_get_counters(h)["fs_units"]
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            for _ in range(args.steps):
+                m.mg3d_fas_vcycle(h, False)
+            torch.cuda.synchronize()
+            solo_wall += time.perf_counter() - t1
+            solo_units += m.mg3d_get_counters(h)["fs_units"] - u0
+        finally:
+            m.mg3d_destroy(h)
+    solo = solo_units / solo_wall / 1e9
     return {"metric": "batched FS Gvoxel*ray*freq/s (32 uneven atmospheres, 3-grid FAS V-cycle)",
             "value": round(units / wall / 1e9, 4), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup,
@@ -640,7 +660,12 @@ def run_batch(args):
             "gpu_launches_per_step": round((c1["kernel_launches"] - c0["kernel_launches"])
                                            / args.steps, 1),
             "device_gb_in_use": round((total - free) / 1e9, 1), "setup_s": round(setup_s, 1),
-            "max_rel_change_last_step": float(np.max(C))}
+            "max_rel_change_last_step": float(np.max(C)),
+            "solo": {"value": round(solo, 4), "unit": UNIT,
+                     "ms_per_step": round(solo_wall / args.steps * 1e3, 2),
+                     "what": "each member alone on its own handle, one after the other, same "
+                             "schedule, warm-up and timed V-cycles"},
+            "batch_over_solo": round(units / wall / 1e9 / solo, 3)}
 
 
 def run_scattering(args):
@@ -1034,37 +1059,46 @@ def run_chromosphere(args):
 CONFIG4_PARAMS = dict(nu_fmg=16, nu0=20, nu1=4, nu2=8, nu3=32)
 
 
-def config4_atmosphere(size, freqs):
+def config4_atmosphere(size, freqs, ground_collisions=1e-3):
     """The 6-level chromosphere of config 4: 256x256x385 nodes (``size``),
     horizontal spacing 24 km taken as the length unit, heights stretched from
     13 km in the middle to 60 km at the ends (the paper's Model 2 pattern),
-    seed 3; ``freqs`` (line, continuum) frequencies per transition."""
+    seed 3; ``freqs`` (line, continuum) frequencies per transition; the
+    collisions out of the ground level scaled by ``ground_collisions`` (the
+    resonance lines scattering-dominated, as in the other chromosphere runs)."""
     from paper_1701_01607_gb300 import synth
     nx, ny, nz = size
     atom = synth.hydrogen_like_atom(line_freq=freqs[0], cont_freq=freqs[1], seed=2)
     z = synth.stretched_heights(nz, 13.0 / 24.0, 60.0 / 24.0)
-    return synth.chromosphere(nx, ny, nz, atom, seed=3, z=z, dx=1.0), atom
+    return synth.chromosphere(nx, ny, nz, atom, seed=3, z=z, dx=1.0,
+                              ground_collisions=ground_collisions), atom
 
 
 def run_config4(args):
     """Full multigrid on the config-4 chromosphere with 4 grids and
     (nu_FMG, nu_0, nu_1, nu_2, nu_3) = (16, 20, 4, 8, 32) (Table 1, Model 2
-    row): the FP32 formal solution (FP64 rates) against FP64 throughout, the
+    row), the FP32 formal solution (FP64 rates) against FP64 throughout: the
     error of FP32 against FP64 on each grid after each FMG stage (Sec. 2.3:
-    stage 1 solves grid 1, stage k interpolates to grid k and runs a V-cycle
-    there), then V-cycles on the finest grid to C < 1e-3; and FP32 MALI and
-    FAS to the same stopping rule.  Opt-in (--config4); --c4-size and
-    --c4-freqs shrink it.  Prints one JSON line."""
+    stage 1 solves grid 1, stage k interpolates to grid k and, below the
+    finest grid, runs a V-cycle there) and after the same number of finest-grid
+    V-cycles (--c4-f64-cycles, FP64 being the costlier run); FP32 then goes on
+    to C < 1e-3 (time to solution).  Optionally (--c4-mali) FP32 MALI to the
+    same rule.  Opt-in (--config4); --c4-size and --c4-freqs shrink it.
+    Prints one JSON line."""
     from paper_1701_01607_gb300 import mg3d as m
     m.load(build_if_missing=True)
     size = tuple(int(v) for v in args.c4_size.split(","))
     freqs = tuple(int(v) for v in args.c4_freqs.split(","))
-    atm, atom = config4_atmosphere(size, freqs)
+    t0 = time.perf_counter()
+    atm, atom = config4_atmosphere(size, freqs, args.ground_collisions)
+    build_s = time.perf_counter() - t0
     L = 4
+    ncmp = args.c4_f64_cycles
     runs = {}
-    for prec, key in ((m.MG3D_PREC_F32, "f32"), (m.MG3D_PREC_F64, "f64")):
+    for prec, key in ((m.MG3D_PREC_F64, "f64"), (m.MG3D_PREC_F32, "f32")):
         if key == "f64" and args.c4_no_f64:
             continue
+        max_cycles = ncmp if key == "f64" else args.c4_max_cycles
         h = m.mg3d_create_ml(atm, atom, n_grids=L, fs_prec=prec, **CONFIG4_PARAMS)
         try:
             t0 = time.perf_counter()
@@ -1078,10 +1112,14 @@ def run_config4(args):
                 m.mg3d_fmg_stage(h, k)
                 stages.append(round(time.perf_counter() - t0, 3))
                 pops.append(m.mg3d_get_populations(h, k))
-            cs, cyc = [], 0
-            while cyc < args.c4_max_cycles:
+            cs, cyc, at_cmp, cycle_s = [], 0, None, []
+            while cyc < max_cycles:
+                t0 = time.perf_counter()
                 cs.append(m.mg3d_fas_vcycle(h, cyc == 0))
+                cycle_s.append(round(time.perf_counter() - t0, 2))
                 cyc += 1
+                if cyc == ncmp:
+                    at_cmp = m.mg3d_get_populations(h, L)
                 if cs[-1] < 1e-3:
                     break
             secs = time.perf_counter() - t_all
@@ -1089,42 +1127,44 @@ def run_config4(args):
             final = m.mg3d_get_populations(h, L)
         finally:
             m.mg3d_destroy(h)
-        runs[key] = {"autotune_s": round(tune_s, 1), "stage_seconds": stages,
-                     "cycles": cyc, "C": [float(c) for c in cs], "seconds": round(secs, 2),
-                     "fine_fs_equivalents": round(units / (np.prod(size) * 24 * n_freq_of(atom)),
-                                                  1),
-                     "pops": pops, "final": final,
-                     "conservation": float(np.max(np.abs(final.sum(axis=0) / atm.n_tot - 1)))}
+        r = {"autotune_s": round(tune_s, 1), "stage_seconds": stages, "cycle_seconds": cycle_s,
+             "cycles": cyc, "C": [float(c) for c in cs], "seconds": round(secs, 2),
+             "reached_tol": bool(cs and cs[-1] < 1e-3),
+             "fine_fs_equivalents": round(units / (np.prod(size) * 24 * n_freq_of(atom)), 1),
+             "conservation": float(np.max(np.abs(final.sum(axis=0) / atm.n_tot - 1)))}
+        print(json.dumps({"config4_partial": key, **r}), file=sys.stderr, flush=True)
+        runs[key] = dict(r, pops=pops, at_cmp=at_cmp)
     out = {"metric": "config 4: FMG, FP32 formal solution against FP64, error per grid",
            "unit": "s", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
            "config": {"workload": "chromosphere %dx%dx%d, 6-level atom, %d frequencies, stretched z "
-                                  "(13-60 km, dx = 24 km), seed 3" % (size + (n_freq_of(atom),)),
-                      "n_grids": L, **CONFIG4_PARAMS}}
+                                  "(13-60 km, dx = 24 km), seed 3, ground collisions x %g"
+                                  % (size + (n_freq_of(atom), args.ground_collisions)),
+                      "n_grids": L, **CONFIG4_PARAMS},
+           "atmosphere_build_s": round(build_s, 1)}
     for key, r in runs.items():
-        out[key] = {k: v for k, v in r.items() if k not in ("pops", "final")}
+        out[key] = {k: v for k, v in r.items() if k not in ("pops", "at_cmp")}
     if "f64" in runs:
         a, b = runs["f32"], runs["f64"]
         out["f32_vs_f64_e_inf_by_stage"] = {
             f"stage {k + 1} (grid {k + 1})": float(np.max(np.abs(a["pops"][k] - b["pops"][k])
                                                        / np.abs(b["pops"][k])))
             for k in range(L)}
-        out["f32_vs_f64_e_inf_final"] = float(np.max(np.abs(a["final"] - b["final"])
-                                                     / np.abs(b["final"])))
-    if not args.c4_no_mali:
-        for method, grids, fn in (("fas", L, m.mg3d_fas_solve), ("mali", 1, m.mg3d_mali_solve)):
-            h = m.mg3d_create_ml(atm, atom, n_grids=grids, fs_prec=m.MG3D_PREC_F32,
-                                 **CONFIG4_PARAMS)
+        if a["at_cmp"] is not None and b["at_cmp"] is not None:
+            out[f"f32_vs_f64_e_inf_after_{ncmp}_cycles"] = float(
+                np.max(np.abs(a["at_cmp"] - b["at_cmp"]) / np.abs(b["at_cmp"])))
+    if args.c4_mali:
+        h = m.mg3d_create_ml(atm, atom, n_grids=1, fs_prec=m.MG3D_PREC_F32, **CONFIG4_PARAMS)
+        try:
+            m.mg3d_autotune(h)
             try:
-                m.mg3d_autotune(h)
-                try:
-                    st = fn(h, 1e-3, 40 if method == "fas" else 400, n_grids=grids)
-                    out[method + "_f32"] = {"seconds": round(st["seconds"], 2),
-                                            "iterations": st["iterations"],
-                                            "fine_fs_equivalents": round(st["fine_fs_equivalents"], 1)}
-                except m.MG3DError as e:
-                    out[method + "_f32"] = {"reached": False, "error": str(e)}
-            finally:
-                m.mg3d_destroy(h)
+                st = m.mg3d_mali_solve(h, 1e-3, args.c4_mali_max)
+                out["mali_f32"] = {"seconds": round(st["seconds"], 2),
+                                   "iterations": st["iterations"],
+                                   "fine_fs_equivalents": round(st["fine_fs_equivalents"], 1)}
+            except m.MG3DError as e:
+                out["mali_f32"] = {"reached": False, "error": str(e)}
+        finally:
+            m.mg3d_destroy(h)
     out["value"] = out["f32"]["seconds"]
     return out
 
@@ -1195,8 +1235,10 @@ def main():
                     help="frequencies per line and per continuum of --config4")
     ap.add_argument("--c4-max-cycles", type=int, default=20)
     ap.add_argument("--c4-no-f64", action="store_true", help="--config4 without the FP64 run")
-    ap.add_argument("--c4-no-mali", action="store_true",
-                    help="--config4 without the FP32 MALI and FAS runs")
+    ap.add_argument("--c4-f64-cycles", type=int, default=2,
+                    help="finest-grid V-cycles of the FP64 run of --config4 (FP32 compared there)")
+    ap.add_argument("--c4-mali", action="store_true", help="--config4 with an FP32 MALI run")
+    ap.add_argument("--c4-mali-max", type=int, default=300)
     ap.add_argument("--scattering", type=float, default=0.0,
                     help="--chromosphere: background scattering opacity / thermal continuum opacity")
     ap.add_argument("--ground-collisions", type=float, default=1e-3,

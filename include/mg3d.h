@@ -350,9 +350,27 @@ typedef struct {
     double a_damp;      /* Voigt damping parameter at t_ref; must be 0 (Doppler
                            profiles): damped lines of multi-level atoms are
                            refused with MG3D_E_ARG */
-    double gamma_prd;   /* coherence fraction of partial redistribution; must
-                           be 0 (CRD): multi-level PRD is refused with
-                           MG3D_E_ARG */
+    double gamma_prd;   /* coherence fraction of partial redistribution in
+                           [0, 1] (0: CRD).  The next step Sec. 6 names, read as
+                           for the two-level atom: the line emits with the
+                           profile rho_f phi_f, rho_f = 1 + gamma_prd f_rad
+                           (sum_f' wq_f' R(f', f) J_f' / (phi_f Jbar) - 1), R the
+                           angle-averaged Doppler redistribution R_I-A at each
+                           node's Doppler width d, erfc(max(|x|, |x'|)/d)/(2 d^2),
+                           scaled symmetrically so that its marginals over the
+                           line's normalised weights wq are the node's profile
+                           (200 steps of the fixed point, once per grid), J the
+                           lagged mean intensity of the previous formal solution
+                           on the grid (shared with background scattering:
+                           cleared at the zero-radiation start, restricted and
+                           Lambda-iterated on a coarse-grid entry, prolonged in
+                           FMG), f_rad = n_l B_lu Jbar over the inflow into the
+                           upper level with the lagged field's plain rates;
+                           rho = 1 where Jbar = 0.  The line's emissivity and
+                           the transition's shares of S and chi in MALI scale by
+                           rho.  At most 128 frequencies per PRD line; static
+                           atmospheres with linear upwind interpolation, no
+                           batches (MG3D_E_ARG otherwise) */
 } mg3d_line;
 
 typedef struct {
@@ -497,13 +515,24 @@ int mg3d_prolong(mg3d_handle *h, int level_fine, int ncomp, const double *coarse
  * every shape can be scheduled with), threads per block (32..512, a multiple
  * of 32), the register budget of the kernel variant (lean = 0 full, 1
  * compiled for 1024 resident threads per SM, i.e. 64 registers per thread, 2
- * for three blocks of at most 256 threads per SM, 85 registers), and stage =
- * 1 to copy each step's rows of chi0 and S into shared memory one step ahead
- * (0: read them from global memory where used, which frees that shared
- * memory for more resident blocks).
- * The library picks a shape at creation (at most 8 bands, staged); this
- * overrides it.  Returns MG3D_E_ARG if the shape does not fit in shared
- * memory or the GPU cannot hold one of its clusters.
+ * for three blocks of at most 256 threads per SM, 85 registers), and the
+ * sweep kind `stage`:
+ *   0, 1  band sweep: 1 copies each step's rows of chi0 and S into shared
+ *         memory one step ahead (0: reads them from global memory where used,
+ *         which frees that shared memory for more resident blocks);
+ *   2, 3  shifted-plane sweep (static atmospheres in complete redistribution
+ *         with linear upwind interpolation): each finished plane is stored
+ *         shifted by the next step's upwind offset; freq_per_block = n_freq
+ *         (at most 16) or 2, 4, 6, 10, 16; up to 1024 threads in FP32 with 2
+ *         or 4 frequencies per block; lean 0, or 1 in FP32.  2 orders the
+ *         planes with one cluster barrier per step, 3 with stores into other
+ *         blocks that count their bytes on an mbarrier of the receiving block
+ *         (a wait that runs past 2 s makes the next call that reads results
+ *         return MG3D_E_CUDA).
+ * The library picks a shape at creation (the shifted-plane sweep with
+ * cluster barriers where it applies, at most 8 bands); this overrides it.
+ * Returns MG3D_E_ARG if the shape does not fit in shared memory or the GPU
+ * cannot hold one of its clusters.
  * No counterpart in the paper (launch control). */
 int mg3d_set_fs_config(mg3d_handle *h, int level, int freq_per_block, int bands,
                        int threads, int lean, int stage);
@@ -523,12 +552,16 @@ int mg3d_get_fs_occupancy(mg3d_handle *h, int level, int freq_per_block, int ban
 
 /* Autotuner: times candidate sweep shapes on this GPU with the level's current
  * populations and keeps the fastest per level (level = 0: every level).
- * Multi-level handles: every band count (1-8), 12/6/4/3/2 rays per block and
- * 128/256/512 threads that fit, timed on the first 32 frequencies; the chunk
+ * Multi-level handles: every band count (1-8), 12/6/4/3/2 rays per block (1
+ * where none of those fits) and 128/256/512 threads that fit, timed on the first 32 frequencies; the chunk
  * buffers are then resized for the chosen shapes (keeping a requested chunk
- * size).  Two-level handles: every number of frequency groups up to 64, 1-16 bands,
+ * size).  Two-level handles taking the shifted-plane sweep: groupings of up
+ * to 8 groups, 1-16 bands, 32-1024 threads in powers of two and the block
+ * sizes that cover a band in equal passes, both register budgets in FP32 and
+ * both completion schemes (stages 2 and 3) with more than one band; other
+ * two-level handles (band sweep): every number of frequency groups up to 64, 1-16 bands,
  * 32-512 threads in powers of two and the block sizes that cover a band in
- * 1-4 equal passes, the three register budgets, staged or not, where the shape fits and
+ * 1-4 equal passes, the three register budgets, staged or not; where the shape fits and
  * can be scheduled; one launch each,
  * then the best eight three more times.  Overwrites the partial sums (not the populations).
  * *evaluated and *seconds (nullable) report the candidates and wall time.

@@ -98,6 +98,8 @@ struct Level {
     void *mib = nullptr;         // [nf][nplane] bottom intensity
     double *sigma_c = nullptr;   // background coherent scattering [nvox] (FP64)
     void *jbg = nullptr;         // background radiation field [nf][nvox] (FS precision)
+    double *prd_c = nullptr;     // partial redistribution of multi-level lines: scaling
+    double *prd_rho = nullptr;   // of R and emission-profile ratio [n_prd_freq][nvox]
     int ml_bands = 0, ml_rows = 0, ml_threads = 0;
     int ml_rpb = 12;             // rays of a hemisphere per block of the multi-level sweep
 };
@@ -108,6 +110,10 @@ struct TimedLaunch {
 };
 
 }  // namespace
+
+// Index of the sweep status word in mg3d_handle::scal (after the eight
+// scalars that reset_scalars clears).
+constexpr int kScalStatus = 8;
 
 struct mg3d_handle {
     int L = 0;
@@ -127,6 +133,13 @@ struct mg3d_handle {
     int ml_chunk = 0;
     int ml_chunk_req = 0;        // chunk asked for (0: automatic), kept across retuning
     bool scatter = false;        // background coherent scattering present
+    // partial redistribution of multi-level lines: the PRD lines, the
+    // |x|-sorted frequency order and its groups, and each frequency's row of
+    // the rho arrays (-1: not a PRD line frequency)
+    bool ml_prd = false;
+    int n_prd = 0, n_prd_freq = 0;
+    PrdLine *d_prd = nullptr;
+    int *d_prd_ord = nullptr, *d_prd_grp = nullptr, *d_prd_index = nullptr;
     int fmg_next = 1;            // the FMG stage mg3d_fmg_stage may run next (1 restarts)
     int top = 0;                 // grid being solved (0: the finest); only its formal
                                  // solutions update its background field
@@ -165,7 +178,10 @@ struct mg3d_handle {
     void *pj = nullptr, *pu = nullptr;
     size_t partial_elems = 0;
     unsigned long long *scal = nullptr;  // [0] C bits, [1] negative after a sweep,
-                                         // [2] non-finite, [3] reset by the 10 % rule
+                                         // [2] non-finite, [3] reset by the 10 % rule,
+                                         // [4] cycle C bits, [6] cycle non-finite;
+                                         // [kScalStatus] sweep status bits, kept
+                                         // until read
     double *scratch = nullptr;           // [4][finest nvox]
     cudaStream_t own_stream = nullptr, stream = nullptr;
     // counters
@@ -367,6 +383,7 @@ PlaneArgs<T> plane_args(const mg3d_handle *h, const Level &L, const SweepShape &
     a.exp_tab = h->d_exp_tab;
     a.exp_l1 = h->exp_l1;
     a.exp_l2 = h->exp_l2;
+    a.status = reinterpret_cast<unsigned *>(h->scal + kScalStatus);
     return a;
 }
 
@@ -568,7 +585,7 @@ void free_level(Level &L) {
                     L.mchi,  L.mS,    L.msl,  L.mfl,  L.mib,  L.sigma_c, L.jbg,
                     L.dchi0, L.dS,   L.mdchi, L.mdS,  L.vel,  L.uproj, L.vnorm, L.dinv,
                     L.jnu,   L.jnu_new, L.rho, L.rhoS, L.psteps, L.o_chi0, L.o_S, L.o_bbot,
-                    L.o_psteps};
+                    L.o_psteps, L.prd_c, L.prd_rho};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     L = Level{};
@@ -623,7 +640,8 @@ int ml_chunk_fs(mg3d_handle *h, int k, int f0, int nc) {
                      L.n, L.T, L.chi_c, L.saha, L.mchi, L.mS, L.msl, L.mfl, f0,
                      h->d_exp_tab, h->exp_l1, h->exp_l2,
                      h->scatter ? L.sigma_c : nullptr, h->scatter ? L.jbg : nullptr,
-                     h->moving ? 1 : 0};
+                     h->moving ? 1 : 0, h->ml_prd ? h->d_prd_index : nullptr,
+                     h->ml_prd ? L.prd_rho : nullptr};
     MG_TRY(launched(h, launch_ml_opacity(oa, h->stream), "multi-level opacity"));
     if (h->params.sc_interp)
         MG_TRY(launched(h, launch_xslopes(h->prec, L.nx, (long)nc * L.nvox, L.mchi, L.mS, L.mdchi,
@@ -678,7 +696,23 @@ int ml_chunk_fs(mg3d_handle *h, int k, int f0, int nc) {
 // coarse operator stays the same from the tau-correction of Eq. 9 to the
 // correction of Eq. 10.
 bool updates_background(const mg3d_handle *h, int k) {
-    return (h->scatter || h->prd) && (h->force_bg || k == (h->top ? h->top : h->L));
+    return (h->scatter || h->prd || h->ml_prd) && (h->force_bg || k == (h->top ? h->top : h->L));
+}
+
+// Multi-level handles with a lagged per-frequency field (jbg): background
+// scattering reads it in its source term, partial redistribution forms its
+// emission-profile ratios from it.
+bool ml_lagged(const mg3d_handle *h) { return h->kind == 1 && (h->scatter || h->ml_prd); }
+
+// Partial redistribution before a multi-level formal solution of grid k:
+// rho of every PRD line frequency from the grid's lagged field.
+int ml_prd_prepare(mg3d_handle *h, int k) {
+    if (!h->ml_prd) return MG3D_OK;
+    Level &L = h->lev[k];
+    MlPrdArgs a{L.nvox, h->N, h->ntrans, h->n_prd, h->d_fi, h->d_ti, h->d_prd, h->d_prd_ord,
+                h->d_prd_grp, h->theta_ref, h->t_ref, L.n, L.T, L.cmat, L.saha, L.jbg, h->prec,
+                L.prd_c, L.prd_rho, h->d_exp_tab, h->exp_l1, h->exp_l2};
+    return launched(h, launch_ml_prd_rho(a, h->stream), "partial redistribution ratios");
 }
 
 int formal_solution(mg3d_handle *h, int k);
@@ -716,6 +750,7 @@ int ml_clear_acc(mg3d_handle *h, int k) {
 // the rate equations use.
 int ml_formal_solution(mg3d_handle *h, int k) {
     Level &L = h->lev[k];
+    MG_TRY(ml_prd_prepare(h, k));
     MG_TRY(ml_clear_acc(h, k));
     for (int f0 = 0; f0 < h->nfreq_ml; f0 += h->ml_chunk) {
         const int nc = std::min(h->ml_chunk, h->nfreq_ml - f0);
@@ -941,10 +976,30 @@ int reset_scalars(mg3d_handle *h) {
     return MG3D_OK;
 }
 
+// MG3D_E_CUDA (and the word cleared) when the sweep status word read back
+// from the device holds a bit: a shifted-plane sweep's bounded wait for the
+// data of a plane ran out, so its formal solution is not valid.
+int sweep_status(mg3d_handle *h, unsigned long long word) {
+    if (!word) return MG3D_OK;
+    cudaMemsetAsync(h->scal + kScalStatus, 0, sizeof(unsigned long long), h->stream);
+    return fail(MG3D_E_CUDA, "a formal-solution sweep gave up waiting for the data of a plane "
+                             "(shifted-plane sweep, transaction-counted stores)");
+}
+
+// Reads the status word after the work enqueued so far.
+int take_sweep_status(mg3d_handle *h) {
+    unsigned long long w = 0;
+    MG_CUDA(cudaMemcpyAsync(&w, h->scal + kScalStatus, sizeof(w), cudaMemcpyDeviceToHost,
+                            h->stream));
+    MG_CUDA(cudaStreamSynchronize(h->stream));
+    return sweep_status(h, w);
+}
+
 int read_scalars(mg3d_handle *h, double *C, long long *neg, long long *bad) {
-    unsigned long long s[4];
+    unsigned long long s[kScalStatus + 1];
     MG_CUDA(cudaMemcpyAsync(s, h->scal, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
     MG_CUDA(cudaStreamSynchronize(h->stream));
+    MG_TRY(sweep_status(h, s[kScalStatus]));
     double c;
     std::memcpy(&c, &s[0], sizeof(c));
     if (C) *C = c;
@@ -962,14 +1017,15 @@ int zero_radiation(mg3d_handle *h, int k) {
         MlRateArgs a = ml_rate_args(h, k, kRateSolve);
         a.scal = nullptr;
         MG_TRY(launched(h, launch_ml_rates(a, h->stream), "zero radiation"));
-        if (h->scatter) {
-            // background field from nothing: cleared, then one Lambda-iteration
+        if (ml_lagged(h)) {
+            // the lagged field from nothing: cleared (rho = 1 for partial
+            // redistribution); with background scattering one Lambda-iteration
             // (a formal solution with the populations held, Sec. 4.8)
             Level &L = h->lev[k];
             MG_CUDA(cudaMemsetAsync(L.jbg, 0,
                                     (size_t)h->nfreq_ml * L.nvox * elem_size(h->prec),
                                     h->stream));
-            MG_TRY(lambda_iteration(h, k));
+            if (h->scatter) MG_TRY(lambda_iteration(h, k));
         }
         return MG3D_OK;
     }
@@ -1014,10 +1070,10 @@ int vcycle(mg3d_handle *h, int k, bool first) {
                     "restrict n"));
     MG_CUDA(cudaMemcpyAsync(C.n_before, C.n, (size_t)h->N * C.nvox * sizeof(double),
                             cudaMemcpyDeviceToDevice, h->stream));
-    if (h->kind == 1 && h->scatter) {
-        // background field: full-weighted, then one Lambda-iteration with the
-        // restricted populations; fixed on this grid until the cycle leaves
-        // it (Sec. 4.8)
+    if (ml_lagged(h)) {
+        // background field (and the lagged field of partial redistribution):
+        // full-weighted, then one Lambda-iteration with the restricted
+        // populations; fixed on this grid until the cycle leaves it (Sec. 4.8)
         MG_TRY(launched(h, launch_restrict_prec(h->prec, h->nfreq_ml, F.nx, F.ny, F.nz, F.jbg,
                                                 C.jbg, h->stream),
                         "restrict background field"));
@@ -1160,9 +1216,10 @@ int fas_cycle(mg3d_handle *h, bool first, double *C, long long *neg) {
     } else {
         MG_TRY(cycle_work(h, first));
     }
-    unsigned long long sc[8];
+    unsigned long long sc[kScalStatus + 1];
     MG_CUDA(cudaMemcpyAsync(sc, h->scal, sizeof(sc), cudaMemcpyDeviceToHost, h->stream));
     MG_CUDA(cudaStreamSynchronize(h->stream));
+    MG_TRY(sweep_status(h, sc[kScalStatus]));
     if (graphs) {
         for (auto &t : h->cycle_timed[first ? 1 : 0]) {
             float ms = 0.f;
@@ -1231,7 +1288,7 @@ int make_shape(const mg3d_handle *h, int k, int ng, int bands, int threads, Swee
 // >= n_freq takes all frequencies in one group (at most 16), else it must be
 // twice a supported slot count (2, 4, 6, 10 or 16).
 static int plane_shape_from_args(const mg3d_handle *h, int level, int freq_per_block, int bands,
-                                 int threads, int lean, SweepShape *out) {
+                                 int threads, int lean, SweepShape *out, int kind = 1) {
     const Level &L = h->lev[level];
     const int nf = h->atom.n_freq;
     if (h->params.sc_interp || h->moving || h->prd)
@@ -1268,7 +1325,7 @@ static int plane_shape_from_args(const mg3d_handle *h, int level, int freq_per_b
                                 " nodes per thread)");
     s.lean = lean;
     s.stage = 0;
-    s.plane = 1;
+    s.plane = kind;
     s.np = np;
     if (plane_smem_bytes(h->prec, np, s.rows, L.nx) > kMaxPlaneSmem)
         return fail(MG3D_E_ARG, "sweep shape exceeds shared memory");
@@ -1282,10 +1339,12 @@ static int shape_from_args(const mg3d_handle *h, int level, int freq_per_block, 
                            int threads, int lean, int stage, SweepShape *out) {
     MG_TRY(check_level(h, level));
     if (h->kind != 0) return fail(MG3D_E_STATE, "sweep shapes apply to two-level handles");
-    if (stage == 2) return plane_shape_from_args(h, level, freq_per_block, bands, threads, lean, out);
+    if (stage == 2 || stage == 3)
+        return plane_shape_from_args(h, level, freq_per_block, bands, threads, lean, out,
+                                     stage - 1);
     if (lean < 0 || lean > 2 || (lean == 2 && threads > 256))
         return fail(MG3D_E_ARG, "lean must be 0, 1 or (up to 256 threads) 2");
-    if (stage != 0 && stage != 1) return fail(MG3D_E_ARG, "stage must be 0, 1 or 2");
+    if (stage != 0 && stage != 1) return fail(MG3D_E_ARG, "stage must be 0, 1, 2 or 3");
     if (stage && h->params.sc_interp)
         return fail(MG3D_E_ARG, "Hermite upwind interpolation runs unstaged (stage 0)");
     if (stage && h->moving) return fail(MG3D_E_ARG, "moving atmospheres run unstaged (stage 0)");
@@ -1392,14 +1451,17 @@ void plane_candidates(mg3d_handle *h, int k, std::vector<SweepShape> &cands) {
                     ths.push_back(th);
             }
             for (int th : ths)
-                for (int lean = 0; lean < (h->prec == MG3D_PREC_F64 ? 1 : 2); ++lean) {
-                    if (th > 32 && th / 2 >= band) continue;  // a smaller block covers it
-                    SweepShape s;
-                    if (plane_shape_from_args(h, k, fpb, bands, th, lean, &s) != MG3D_OK)
-                        continue;
-                    if (check_schedulable(h, k, s) != MG3D_OK) continue;
-                    cands.push_back(s);
-                }
+                for (int lean = 0; lean < (h->prec == MG3D_PREC_F64 ? 1 : 2); ++lean)
+                    // both completion schemes where blocks exchange rows
+                    for (int kind = 1; kind <= (bands > 1 ? 2 : 1); ++kind) {
+                        if (th > 32 && th / 2 >= band) continue;  // a smaller block covers it
+                        SweepShape s;
+                        if (plane_shape_from_args(h, k, fpb, bands, th, lean, &s, kind) !=
+                            MG3D_OK)
+                            continue;
+                        if (check_schedulable(h, k, s) != MG3D_OK) continue;
+                        cands.push_back(s);
+                    }
         }
     }
 }
@@ -1731,7 +1793,7 @@ int create_impl(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_qu
     }
     MG_TRY(dev_alloc(&h->pj, h->partial_elems * es));
     MG_TRY(dev_alloc(&h->pu, h->partial_elems * es));
-    MG_TRY(dalloc(&h->scal, 8));
+    MG_TRY(dalloc(&h->scal, kScalStatus + 1));
     for (int k = 1; k <= h->L; ++k) MG_TRY(zero_radiation(h, k));
     MG_CUDA(cudaStreamSynchronize(h->stream));
     return MG3D_OK;
@@ -1756,7 +1818,7 @@ void trapezoid_grid(double a, double b, int n, std::vector<double> &x, std::vect
 // and the angle sums of every ray-group slot on the finest.
 size_t ml_bytes_per_freq(const mg3d_handle *h) {
     const size_t es = elem_size(h->prec);
-    size_t b = (h->scatter ? 3 : 2) * (size_t)h->ml_slots * h->lev[h->L].nvox * es;
+    size_t b = (ml_lagged(h) ? 3 : 2) * (size_t)h->ml_slots * h->lev[h->L].nvox * es;
     const size_t per_level = h->params.sc_interp ? 6 : 4;  // Hermite: slopes of chi, S
     for (int k = 1; k <= h->L; ++k) b += per_level * (size_t)h->lev[k].nvox * es;
     return b;
@@ -1800,7 +1862,7 @@ int alloc_ml_chunks(mg3d_handle *h, int chunk) {
     const size_t nv = h->lev[h->L].nvox;
     MG_TRY(dev_alloc(&h->ml_jx, (size_t)h->ml_slots * chunk * nv * es));
     MG_TRY(dev_alloc(&h->ml_ux, (size_t)h->ml_slots * chunk * nv * es));
-    if (h->scatter) MG_TRY(dev_alloc(&h->ml_jm, (size_t)h->ml_slots * chunk * nv * es));
+    if (ml_lagged(h)) MG_TRY(dev_alloc(&h->ml_jm, (size_t)h->ml_slots * chunk * nv * es));
     h->ml_chunk = chunk;
     return MG3D_OK;
 }
@@ -1866,8 +1928,24 @@ int time_ml_shape(mg3d_handle *h, int k, int bands, int rpb, int threads, int nc
     return rc;
 }
 
+// True when no multi-level sweep shape with two or more rays per block fits
+// level k's plane in shared memory (a 256-wide FP64 plane): its candidates
+// then take one ray per block, 24 ray-group slots.
+bool ml_single_ray_only(const mg3d_handle *h, int k) {
+    const Level &L = h->lev[k];
+    for (int rpb : {12, 6, 4, 3, 2})
+        for (int bands = 1; bands <= kPortableBands && bands <= L.ny; ++bands) {
+            const int rows = (L.ny + bands - 1) / bands;
+            if ((long)(bands - 1) * rows >= L.ny) continue;
+            if (ml_sweep_smem_bytes(h->prec, rows, L.nx, rpb, h->params.sc_interp,
+                                    h->moving ? 1 : 0) <= kMaxSweepSmem)
+                return false;
+        }
+    return true;
+}
+
 // Times the multi-level sweep shapes of level k on its first nc frequencies
-// (every band count, rays per block 12, 6, 4, 3 or 2 and 128/256/512 threads
+// (every band count, rays per block 12, 6, 4, 3 or 2, else 1, and 128/256/512 threads
 // that fit; once each, the best six three more times) and keeps the fastest.
 int autotune_ml_level(mg3d_handle *h, int k, int nc, int *evaluated) {
     Level &L = h->lev[k];
@@ -1883,10 +1961,12 @@ int autotune_ml_level(mg3d_handle *h, int k, int nc, int *evaluated) {
         int bands, rpb, threads;
     };
     std::vector<Cand> cands;
-    for (int rpb : {12, 6, 4, 3, 2})
+    // rays per block 1 only where no larger group fits (a 256-wide FP64 plane)
+    for (int rpb : {12, 6, 4, 3, 2, 1})
         for (int bands = 1; bands <= kPortableBands && bands <= L.ny; ++bands) {
             const int rows = (L.ny + bands - 1) / bands;
             if ((long)(bands - 1) * rows >= L.ny) continue;
+            if (rpb == 1 && !cands.empty()) break;
             if (ml_sweep_smem_bytes(h->prec, rows, L.nx, rpb, h->params.sc_interp,
                                     h->moving ? 1 : 0) > kMaxSweepSmem)
                 continue;
@@ -1930,8 +2010,11 @@ int autotune_ml_level(mg3d_handle *h, int k, int nc, int *evaluated) {
 int autotune_ml(mg3d_handle *h, int level, int *evaluated) {
     MG_CUDA(cudaStreamSynchronize(h->stream));
     drop_graphs(h);
-    // tuning buffers: up to 12 slots, at most 32 frequencies that fit
+    // tuning buffers: the slots of the candidates (12 for two rays per block,
+    // 24 where a level fits only one), at most 32 frequencies that fit
     h->ml_slots = 12;
+    for (int k = 1; k <= h->L; ++k)
+        if ((level == 0 || k == level) && ml_single_ray_only(h, k)) h->ml_slots = 24;
     MG_TRY(alloc_ml_chunks(h, 1));
     const int nc = std::min(32, default_ml_chunk(h));
     MG_TRY(alloc_ml_chunks(h, nc));
@@ -2013,6 +2096,75 @@ int setup_velocity_ml(mg3d_handle *h, const double *vel_host) {
     return rc;
 }
 
+// Partial redistribution of multi-level lines: the PRD line table (each
+// line's frequencies sorted by |x|, mirror offsets adjacent, grouped by equal
+// |x|), each frequency's row of the rho arrays, and per grid the symmetric
+// scaling of R at every node's Doppler width (fixed for the handle: it
+// depends on the temperature only) and rho = 1 until the first formal
+// solution.
+int setup_ml_prd(mg3d_handle *h, const mg3d_ml_atom *atom) {
+    std::vector<PrdLine> pl;
+    std::vector<int> ord, grp, index(h->nfreq_ml, -1);
+    int pf = 0;
+    for (int t = 0; t < atom->n_lines; ++t) {
+        const mg3d_line &ln = atom->lines[t];
+        if (!(ln.gamma_prd > 0.0)) continue;
+        const TransInfo &tr = h->ti[t];
+        PrdLine L{};
+        L.lo = ln.lower;
+        L.up = ln.upper;
+        L.f_begin = tr.f_begin;
+        L.f_end = tr.f_end;
+        L.pf0 = pf;
+        L.nf = tr.f_end - tr.f_begin;
+        L.ord0 = (int)ord.size();
+        L.grp0 = (int)grp.size();
+        L.gamma = ln.gamma_prd;
+        L.gr = tr.gr;
+        L.b_ul = tr.coef / (tr.rho * tr.rho * tr.rho);
+        std::vector<int> fs;
+        for (int f = tr.f_begin; f < tr.f_end; ++f) {
+            fs.push_back(f);
+            index[f] = pf + (f - tr.f_begin);
+        }
+        std::stable_sort(fs.begin(), fs.end(), [&](int a, int b) {
+            return std::fabs(h->fi[a].xy) < std::fabs(h->fi[b].xy);
+        });
+        for (int i = 0; i < L.nf; ++i) {
+            if (i == 0 || std::fabs(h->fi[fs[i]].xy) != std::fabs(h->fi[fs[i - 1]].xy))
+                grp.push_back(i);
+            ord.push_back(fs[i]);
+        }
+        L.ngrp = (int)grp.size() - L.grp0;
+        grp.push_back(L.nf);   // end of the last group
+        pl.push_back(L);
+        pf += L.nf;
+    }
+    h->n_prd = (int)pl.size();
+    h->n_prd_freq = pf;
+    MG_TRY(dev_alloc((void **)&h->d_prd, pl.size() * sizeof(PrdLine)));
+    MG_TRY(dev_alloc((void **)&h->d_prd_ord, ord.size() * sizeof(int)));
+    MG_TRY(dev_alloc((void **)&h->d_prd_grp, grp.size() * sizeof(int)));
+    MG_TRY(dev_alloc((void **)&h->d_prd_index, index.size() * sizeof(int)));
+    MG_CUDA(cudaMemcpy(h->d_prd, pl.data(), pl.size() * sizeof(PrdLine), cudaMemcpyHostToDevice));
+    MG_CUDA(cudaMemcpy(h->d_prd_ord, ord.data(), ord.size() * sizeof(int), cudaMemcpyHostToDevice));
+    MG_CUDA(cudaMemcpy(h->d_prd_grp, grp.data(), grp.size() * sizeof(int), cudaMemcpyHostToDevice));
+    MG_CUDA(cudaMemcpy(h->d_prd_index, index.data(), index.size() * sizeof(int),
+                       cudaMemcpyHostToDevice));
+    std::vector<double> ones;
+    for (int k = 1; k <= h->L; ++k) {
+        Level &L = h->lev[k];
+        MG_TRY(dalloc(&L.prd_c, (size_t)pf * L.nvox));
+        MG_TRY(dalloc(&L.prd_rho, (size_t)pf * L.nvox));
+        ones.assign((size_t)pf * L.nvox, 1.0);
+        MG_CUDA(cudaMemcpy(L.prd_rho, ones.data(), ones.size() * 8, cudaMemcpyHostToDevice));
+        MG_TRY(launched(h, launch_ml_prd_scale(L.nvox, h->n_prd, h->d_prd, h->d_fi, h->d_prd_ord,
+                                               h->d_prd_grp, h->t_ref, L.T, L.prd_c, h->stream),
+                        "partial redistribution scaling"));
+    }
+    return MG3D_OK;
+}
+
 int create_ml_impl(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
                    const mg3d_quadrature *quad, const mg3d_params *params, mg3d_handle *h) {
     h->kind = 1;
@@ -2023,6 +2175,7 @@ int create_ml_impl(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
     h->moving = atm->vel != nullptr;
     h->theta_ref = atom->theta_ref;
     h->t_ref = atom->t_ref;
+    for (int t = 0; t < atom->n_lines; ++t) h->ml_prd = h->ml_prd || atom->lines[t].gamma_prd > 0.0;
     build_quadrature(h, quad ? quad->a : 0.0);
     const int N = h->N;
     // frequency table: lines, then continua, each transition contiguous
@@ -2197,6 +2350,13 @@ int create_ml_impl(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
         for (long i = 0; i < F.nvox; ++i)
             if (!(atm->sigma_c[i] >= 0.0)) return fail(MG3D_E_ARG, "negative sigma_c");
     }
+    if (h->ml_prd && !h->scatter)
+        for (int k = 1; k <= h->L; ++k) {
+            Level &L = h->lev[k];
+            MG_TRY(dev_alloc(&L.jbg, (size_t)nf * L.nvox * elem_size(h->prec)));
+            MG_CUDA(cudaMemset(L.jbg, 0, (size_t)nf * L.nvox * elem_size(h->prec)));
+        }
+    if (h->ml_prd) MG_TRY(setup_ml_prd(h, atom));
     if (h->scatter) {
         for (int k = 1; k <= h->L; ++k) {
             Level &L = h->lev[k];
@@ -2218,7 +2378,7 @@ int create_ml_impl(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
     MG_TRY(alloc_ml_chunks(h, params && params->ml_chunk > 0
                                   ? std::min(params->ml_chunk, h->nfreq_ml)
                                   : default_ml_chunk(h)));
-    MG_TRY(dalloc(&h->scal, 8));
+    MG_TRY(dalloc(&h->scal, kScalStatus + 1));
     for (int k = 1; k <= h->L; ++k) MG_TRY(zero_radiation(h, k));
     MG_CUDA(cudaStreamSynchronize(h->stream));
     return MG3D_OK;
@@ -2744,10 +2904,16 @@ int mg3d_create_ml(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
         if (ln.a_damp != 0.0)
             return fail(MG3D_E_ARG, "line " + std::to_string(t) +
                                         ": multi-level atoms take Doppler profiles (a_damp 0)");
-        if (ln.gamma_prd != 0.0)
+        if (!(ln.gamma_prd >= 0.0 && ln.gamma_prd <= 1.0))
+            return fail(MG3D_E_ARG, "line " + std::to_string(t) + ": gamma_prd must lie in [0, 1]");
+        if (ln.gamma_prd > 0.0 && (atm->vel || params->sc_interp))
             return fail(MG3D_E_ARG, "line " + std::to_string(t) +
-                                        ": partial redistribution of multi-level atoms is not "
-                                        "built (gamma_prd 0)");
+                                        ": partial redistribution of multi-level lines takes a "
+                                        "static atmosphere and linear upwind interpolation");
+        if (ln.gamma_prd > 0.0 && ln.n_freq > kMaxPrdLineFreq)
+            return fail(MG3D_E_ARG, "line " + std::to_string(t) + ": partial redistribution takes "
+                                        "at most " + std::to_string(kMaxPrdLineFreq) +
+                                        " frequencies per line");
         nf += ln.n_freq;
     }
     for (int t = 0; t < atom->n_continua; ++t) {
@@ -2811,10 +2977,11 @@ int mg3d_formal_solve_ml(mg3d_handle *h, int level, double *jx_host, double *ux_
     const size_t es = elem_size(h->prec);
     const size_t nv = (size_t)L.nvox;
     std::vector<unsigned char> hj, hu;
+    MG_TRY(ml_prd_prepare(h, level));
     for (int f0 = 0; f0 < h->nfreq_ml; f0 += h->ml_chunk) {
         const int nc = std::min(h->ml_chunk, h->nfreq_ml - f0);
         MG_TRY(ml_chunk_fs(h, level, f0, nc));
-        if (h->scatter) {   // the background field takes the new mean intensity
+        if (ml_lagged(h)) {   // the lagged field takes the new mean intensity
             h->force_bg = true;
             const int rc = ml_accumulate(h, level, f0, nc, false);
             h->force_bg = false;
@@ -2918,6 +3085,8 @@ int mg3d_batch_create(int n, mg3d_handle *const *members, mg3d_batch **out) {
         if (!members[i]) return fail(MG3D_E_ARG, "null member");
         if (members[i]->scatter)
             return fail(MG3D_E_ARG, "batches do not take background scattering");
+        if (members[i]->ml_prd)
+            return fail(MG3D_E_ARG, "batches do not take partial redistribution");
         if (members[i]->params.sc_interp)
             return fail(MG3D_E_ARG, "batches do not take Hermite upwind interpolation");
         if (members[i]->moving)
@@ -3100,6 +3269,9 @@ int mg3d_destroy(mg3d_handle *h) {
         if (p) cudaFree(p);
     for (void *p : h->o_pslot)
         if (p) cudaFree(p);
+    for (void *p : {(void *)h->d_prd, (void *)h->d_prd_ord, (void *)h->d_prd_grp,
+                    (void *)h->d_prd_index})
+        if (p) cudaFree(p);
     if (h->o_pj) cudaFree(h->o_pj);
     if (h->o_pu) cudaFree(h->o_pu);
     void *ptrs[] = {h->d_ftab, h->d_vtab, h->d_vline, h->d_kmat, h->d_wphin, h->d_fidx,
@@ -3168,8 +3340,7 @@ int mg3d_formal_solve(mg3d_handle *h, int level, double *jeff_host, double *u_ho
                                            cudaMemcpyDeviceToHost, h->stream));
     if (u_host) MG_CUDA(cudaMemcpyAsync(u_host, h->scratch + L.nvox, L.nvox * 8,
                                         cudaMemcpyDeviceToHost, h->stream));
-    MG_CUDA(cudaStreamSynchronize(h->stream));
-    return MG3D_OK;
+    return take_sweep_status(h);
 }
 
 // Orders stream `to` after the work enqueued so far on stream `from`.
@@ -3212,8 +3383,7 @@ int mg3d_formal_solve_ex(mg3d_handle *h, int level, int prec, double *jeff_host,
                                            cudaMemcpyDeviceToHost, h->stream));
     if (u_host) MG_CUDA(cudaMemcpyAsync(u_host, h->scratch + L.nvox, L.nvox * 8,
                                         cudaMemcpyDeviceToHost, h->stream));
-    MG_CUDA(cudaStreamSynchronize(h->stream));
-    return MG3D_OK;
+    return take_sweep_status(h);
 }
 
 int mg3d_formal_solve_dev(mg3d_handle *h, int level, int prec, double *jeff_dev, double *u_dev,
@@ -3346,7 +3516,7 @@ int fmg_stage(mg3d_handle *h, int k) {
     MG_TRY(launched(h, launch_prolong(h->params.interpolation, h->N, Ck.nx, Ck.ny, Ck.nz,
                                       Fk.tz, Fk.zf, Ck.n, Fk.n, h->stream),
                     "prolong full approximation"));
-    if (h->kind == 1 && h->scatter)
+    if (ml_lagged(h))
         MG_TRY(launched(h, launch_prolong_prec(h->params.interpolation, h->prec, h->nfreq_ml,
                                                Ck.nx, Ck.ny, Ck.nz, Fk.tz, Fk.zf, Ck.jbg,
                                                Fk.jbg, h->stream),
@@ -3511,7 +3681,7 @@ int mg3d_get_fs_config(const mg3d_handle *h, int level, int *freq_per_block, int
     if (bands) *bands = L.shape.bands;
     if (threads) *threads = L.shape.threads;
     if (lean) *lean = L.shape.lean;
-    if (stage) *stage = L.shape.plane ? 2 : L.shape.stage;
+    if (stage) *stage = L.shape.plane ? 1 + L.shape.plane : L.shape.stage;
     return MG3D_OK;
 }
 

@@ -38,7 +38,8 @@ struct SweepShape {
     int herm = 0;  // 1: monotone cubic Hermite upwind interpolation (unstaged)
     int vel = 0;   // 1: moving atmosphere, ray-dependent profiles (unstaged)
     int prd = 0;   // 1: partial redistribution, frequency-dependent S (unstaged)
-    int plane = 0; // 1: shifted-plane sweep (plane_sweep.cuh) with np slots of two
+    int plane = 0; // shifted-plane sweep (plane_sweep.cuh) with np slots of two
+                   // frequencies: 1 cluster barriers, 2 transaction-counted stores
     int np = 0;    //    frequencies per group (ng = 2 np table positions per group)
 };
 
@@ -83,7 +84,12 @@ struct PlaneArgs {
     T *pj, *pu;                          // [kRays*ngroups][nvox] partial Jeff and U
     const double *exp_tab;               // FP64 exp table (FP64 sweeps)
     double exp_l1, exp_l2;
+    unsigned *status;                    // kPlaneStatus* bits (async scheme), nullable
 };
+
+// Status bits of the shifted-plane sweep: a bounded wait for a plane's bytes
+// ran out (the launch's results are not valid).
+constexpr unsigned kPlaneStatusWait = 1u;
 
 // Slot counts (frequency pairs per group) the shifted-plane sweep is built for.
 constexpr int kPlaneNp[] = {1, 2, 3, 5, 8};
@@ -102,6 +108,12 @@ cudaError_t launch_plane_sweep_f64(const PlaneArgs<double> &a, const SweepShape 
                                    cudaStream_t st);
 cudaError_t launch_plane_sweep_f32(const PlaneArgs<float> &a, const SweepShape &s,
                                    cudaStream_t st);
+cudaError_t launch_plane_async_f64(const PlaneArgs<double> &a, const SweepShape &s,
+                                   cudaStream_t st);
+cudaError_t launch_plane_async_f32(const PlaneArgs<float> &a, const SweepShape &s,
+                                   cudaStream_t st);
+cudaError_t plane_async_clusters_f64(const SweepShape &s, int nx, int *n);
+cudaError_t plane_async_clusters_f32(const SweepShape &s, int nx, int *n);
 cudaError_t plane_active_clusters(int prec, const SweepShape &s, int nx, int *n);
 
 // Sweep variants: linear upwind interpolation, Hermite, moving atmosphere,
@@ -282,6 +294,40 @@ struct MlSweepArgs {
     const T *vnorm, *uproj, *dinv;
 };
 
+// Partial redistribution of one line of a multi-level atom: its frequencies
+// [f_begin, f_end) of the frequency table, their positions pf0 .. pf0+nf-1
+// among all PRD line frequencies (the rows of the scaling and rho arrays),
+// and `ord` (entries ord0 .. ord0+nf-1 of the order table): the line's
+// frequencies (table indices) sorted by |x| with mirror offsets adjacent,
+// grouped by equal |x| (grp: entries grp0 .. grp0+ngrp of the group-start
+// table, positions within the sorted list).
+constexpr int kMaxPrdLineFreq = 128;   // frequencies of one PRD line of a multi-level atom
+struct PrdLine {
+    int lo, up, f_begin, f_end, pf0, nf, ord0, grp0, ngrp;
+    double gamma;   // coherence fraction
+    double gr;      // g_u / g_l
+    double b_ul;    // A_ul / rho^3
+};
+
+// Rates of the lagged field and partial-redistribution ratios per node (see
+// launch_ml_prd_rho).
+struct MlPrdArgs {
+    long nvox;
+    int n_levels, n_trans, n_prd;
+    const FreqInfo *fi;
+    const TransInfo *ti;
+    const PrdLine *pl;
+    const int *ord, *grp;
+    double theta_ref, t_ref;
+    const double *n, *T, *c, *saha;  // populations [N][nvox], T, collisions [N][N][nvox], saha
+    const void *jbg;                 // lagged mean intensity [n_freq][nvox] (FS precision)
+    int prec;
+    const double *scale;             // [n_prd_freq][nvox] symmetric scaling of R
+    double *rho;                     // [n_prd_freq][nvox] out
+    const double *exp_tab;
+    double exp_l1, exp_l2;
+};
+
 // Opacity of the chunk of frequencies f0 .. f0+nfreq-1, written at the
 // chunk-local index [f - f0][nvox].
 struct MlOpacityArgs {
@@ -301,6 +347,9 @@ struct MlOpacityArgs {
                                    // at unit profile, S <- its emissivity at unit profile
                                    // (continua: their own), sl <- background opacity,
                                    // fl <- background emissivity
+    const int *prd_index;          // [n_freq] row of rho for a PRD line frequency, else -1
+                                   // (null: no partial redistribution)
+    const double *prd_rho;         // [n_prd_freq][nvox] emission-profile ratio psi/phi
 };
 
 // Radiative sums per transition and node, [n_trans][3][nvox] in FP64:
@@ -349,6 +398,15 @@ cudaError_t launch_ml_vel_prep(int prec, long nvox, int ntrans, const TransInfo 
                                const double *T, double t_ref, void *uproj, void *dinv,
                                void *vnorm, cudaStream_t st);
 cudaError_t launch_ml_opacity(const MlOpacityArgs &a, cudaStream_t st);
+// Per node and PRD line: the symmetric scaling c of R_I-A at the node's
+// Doppler width, the fixed point of c <- sqrt(c phi / (R0^T (wq c))) after
+// 200 steps from c = 1 (R = diag(c) R0 diag(c) then has marginals phi).
+cudaError_t launch_ml_prd_scale(long nvox, int n_prd, const PrdLine *pl, const FreqInfo *fi,
+                                const int *ord, const int *grp, double t_ref, const double *T,
+                                double *scale, cudaStream_t st);
+// Per node and PRD line frequency: rho = 1 + gamma f_rad (sum_f' wq R(f', f)
+// J_f' / (phi_f Jbar) - 1) from the lagged mean intensity.
+cudaError_t launch_ml_prd_rho(const MlPrdArgs &a, cudaStream_t st);
 cudaError_t launch_ml_bottom(int prec, long nplane, int nfreq, const FreqInfo *fi,
                              double theta_ref, const double *T, void *ib, cudaStream_t st);
 cudaError_t launch_ml_sweep_f64(const MlSweepArgs<double> &a, int bands, int threads,

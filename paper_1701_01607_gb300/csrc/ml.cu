@@ -153,13 +153,204 @@ __global__ void ml_opacity_kernel(const MlOpacityArgs a) {
                 chi = chi_t + (T)cc;
                 src = eta_t + (T)cc * B;
             }
+            T rho = T(1);
+            if (a.prd_index) {
+                // partial redistribution: the line's emission profile is rho phi,
+                // so its emissivity and the transition's shares scale by rho
+                const int pr = a.prd_index[a.f0 + fl];
+                if (pr >= 0) {
+                    rho = (T)a.prd_rho[(long)pr * nvox + v];
+                    src += (rho - T(1)) * eta_t;
+                }
+            }
             const T inv = T(1) / chi;
             ((T *)a.chi)[i] = chi;
             ((T *)a.S)[i] = src * inv;
-            ((T *)a.sl)[i] = eta_t * inv;
-            ((T *)a.fl)[i] = chi_t * inv;
+            ((T *)a.sl)[i] = rho * eta_t * inv;
+            ((T *)a.fl)[i] = rho * chi_t * inv;
         }
     }
+}
+
+// ------------------------------------------------ partial redistribution
+
+// Partial redistribution of a line (the next step Sec. 6 names; the reading
+// of the two-level case generalised): the angle-averaged Doppler
+// redistribution R_I-A at a node of Doppler width d,
+//   R0(x', x) = erfc(max(|x|, |x'|)/d) / (2 d^2),
+// scaled symmetrically, R = diag(c) R0 diag(c), so that its discrete
+// marginals sum_f' wq_f' R(f', f) are the node's profile phi_f (wq: the
+// line's trapezoid weights normalised by sum w phi).  R0 depends on its two
+// frequencies only through the larger |x|, so with the frequencies sorted by
+// |x| a product R0^T v is, for a frequency of group k (equal |x|),
+//   g_k sum_{groups <= k} v + sum_{groups > k} g v,   g = erfc(|x|/d)/(2 d^2):
+// a prefix and a suffix sum, O(n) per node instead of O(n^2).
+constexpr int kMaxPrdFreq = kMaxPrdLineFreq;
+
+// out_s = sum_a R0(a, s) v_a for the line's sorted frequencies s (v, out in
+// sorted order; g per group; suf scratch of ngrp + 1 entries).
+__device__ inline void prd_r0_product(int nf, int ngrp, const int *__restrict__ gs,
+                                      const double *g, const double *v, double *out,
+                                      double *suf) {
+    // suffix sums over groups above k
+    suf[ngrp] = 0.0;
+    for (int k = ngrp - 1; k >= 0; --k) {
+        double sg = 0.0;
+        for (int s = gs[k]; s < gs[k + 1]; ++s) sg += v[s];
+        suf[k] = suf[k + 1] + g[k] * sg;
+    }
+    double pre = 0.0;
+    for (int k = 0; k < ngrp; ++k) {
+        for (int s = gs[k]; s < gs[k + 1]; ++s) pre += v[s];
+        const double m = g[k] * pre + suf[k + 1];
+        for (int s = gs[k]; s < gs[k + 1]; ++s) out[s] = m;
+    }
+}
+
+// The line's profile at the node (sorted order), its normalised weights and
+// the R0 group values.
+__device__ inline void prd_line_setup(const PrdLine &L, const FreqInfo *__restrict__ fi,
+                                      const int *__restrict__ ord, const int *__restrict__ gs,
+                                      double d, double *phi, double *wq, double *g) {
+    const double inv_d = 1.0 / d;
+    double norm = 0.0;
+    for (int s = 0; s < L.nf; ++s) {
+        const FreqInfo q = fi[ord[L.ord0 + s]];
+        const double xd = q.xy * inv_d;
+        phi[s] = exp(-xd * xd) * 0.56418958354775628 * inv_d;
+        norm += q.w * phi[s];
+    }
+    for (int s = 0; s < L.nf; ++s) wq[s] = fi[ord[L.ord0 + s]].w / norm;
+    for (int k = 0; k < L.ngrp; ++k) {
+        const double ax = fabs(fi[ord[L.ord0 + gs[k]]].xy);
+        g[k] = 0.5 * erfc(ax * inv_d) * inv_d * inv_d;
+    }
+}
+
+__global__ void __launch_bounds__(128) ml_prd_scale_kernel(long nvox, int n_prd,
+                                                           const PrdLine *__restrict__ pl,
+                                                           const FreqInfo *__restrict__ fi,
+                                                           const int *__restrict__ ord,
+                                                           const int *__restrict__ grp,
+                                                           double t_ref,
+                                                           const double *__restrict__ T,
+                                                           double *__restrict__ scale) {
+    double phi[kMaxPrdFreq], wq[kMaxPrdFreq], c[kMaxPrdFreq], v[kMaxPrdFreq], m[kMaxPrdFreq];
+    double g[kMaxPrdFreq + 1], suf[kMaxPrdFreq + 1];
+    for (long x = blockIdx.x * (long)blockDim.x + threadIdx.x; x < nvox;
+         x += (long)gridDim.x * blockDim.x) {
+        const double d = sqrt(T[x] / t_ref);
+        for (int l = 0; l < n_prd; ++l) {
+            const PrdLine L = pl[l];
+            const int *gs = grp + L.grp0;
+            prd_line_setup(L, fi, ord, gs, d, phi, wq, g);
+            for (int s = 0; s < L.nf; ++s) c[s] = 1.0;
+            for (int it = 0; it < 200; ++it) {
+                for (int s = 0; s < L.nf; ++s) v[s] = wq[s] * c[s];
+                prd_r0_product(L.nf, L.ngrp, gs, g, v, m, suf);
+                for (int s = 0; s < L.nf; ++s) c[s] = sqrt(c[s] * phi[s] / m[s]);
+            }
+            for (int s = 0; s < L.nf; ++s)
+                scale[(long)(L.pf0 + ord[L.ord0 + s] - L.f_begin) * nvox + x] = c[s];
+        }
+    }
+}
+
+template <typename TP>
+__global__ void __launch_bounds__(128) ml_prd_rho_kernel(const MlPrdArgs a) {
+    double phi[kMaxPrdFreq], wq[kMaxPrdFreq], v[kMaxPrdFreq], m[kMaxPrdFreq];
+    double g[kMaxPrdFreq + 1], suf[kMaxPrdFreq + 1];
+    const TP *__restrict__ jbg = (const TP *)a.jbg;
+    const long nvox = a.nvox;
+    const int N = a.n_levels;
+    for (long x = blockIdx.x * (long)blockDim.x + threadIdx.x; x < nvox;
+         x += (long)gridDim.x * blockDim.x) {
+        const double Tg = a.T[x];
+        const double d = sqrt(Tg / a.t_ref), inv_d = 1.0 / d;
+        // plain rates of the lagged field: collisions plus every transition's
+        // radiative rates with J (no local operator)
+        double P[kMaxLevels][kMaxLevels];
+        for (int i = 0; i < N; ++i)
+            for (int j = 0; j < N; ++j) P[i][j] = i == j ? 0.0 : a.c[((long)i * N + j) * nvox + x];
+        for (int t = 0; t < a.n_trans; ++t) {
+            const TransInfo tr = a.ti[t];
+            if (tr.kind == 0) {
+                double s0 = 0.0, s1 = 0.0;
+                for (int f = tr.f_begin; f < tr.f_end; ++f) {
+                    const FreqInfo q = a.fi[f];
+                    const double xd = q.xy * inv_d;
+                    const double wphi = q.w * exp(-xd * xd) * 0.56418958354775628 * inv_d;
+                    s0 += wphi;
+                    s1 += wphi * (double)jbg[(long)f * nvox + x];
+                }
+                const double Jb = s1 / s0;
+                const double b_ul = tr.coef / (tr.rho * tr.rho * tr.rho);
+                P[tr.lo][tr.up] += tr.gr * b_ul * Jb;
+                P[tr.up][tr.lo] += tr.coef + b_ul * Jb;
+            } else {
+                const double G = a.saha[(long)tr.lo * nvox + x];
+                double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+                for (int f = tr.f_begin; f < tr.f_end; ++f) {
+                    const FreqInfo q = a.fi[f];
+                    const double y = q.xy;
+                    const double qa = tr.coef * q.w / (y * y * y * y);
+                    const double E = exp(-a.theta_ref * tr.rho * y / Tg);
+                    const double ry = tr.rho * y;
+                    const double J = (double)jbg[(long)f * nvox + x];
+                    s0 += qa * J;
+                    s1 += qa * E * J;
+                    s2 += qa * E * ry * ry * ry;
+                }
+                P[tr.lo][tr.up] += s0;
+                P[tr.up][tr.lo] += G * (s2 + s1);
+            }
+        }
+        for (int l = 0; l < a.n_prd; ++l) {
+            const PrdLine L = a.pl[l];
+            const int *gs = a.grp + L.grp0;
+            prd_line_setup(L, a.fi, a.ord, gs, d, phi, wq, g);
+            double Jbar = 0.0;
+            for (int s = 0; s < L.nf; ++s) {
+                const int f = a.ord[L.ord0 + s];
+                const double J = (double)jbg[(long)f * nvox + x];
+                const double cs = a.scale[(long)(L.pf0 + f - L.f_begin) * nvox + x];
+                Jbar += wq[s] * phi[s] * J;
+                v[s] = wq[s] * cs * J;
+            }
+            double inflow = 0.0;
+            for (int j = 0; j < N; ++j)
+                if (j != L.up) inflow += a.n[(long)j * nvox + x] * P[j][L.up];
+            const double excite = a.n[(long)L.lo * nvox + x] * L.gr * L.b_ul * Jbar;
+            const double frad = excite / inflow;
+            prd_r0_product(L.nf, L.ngrp, gs, g, v, m, suf);
+            for (int s = 0; s < L.nf; ++s) {
+                const int f = a.ord[L.ord0 + s];
+                const long row = (long)(L.pf0 + f - L.f_begin) * nvox + x;
+                double r = 1.0;
+                if (Jbar > 0.0) {
+                    const double Af = a.scale[row] * m[s];
+                    r = 1.0 + L.gamma * frad * (Af / (phi[s] * Jbar) - 1.0);
+                }
+                a.rho[row] = r;
+            }
+        }
+    }
+}
+
+cudaError_t launch_ml_prd_scale(long nvox, int n_prd, const PrdLine *pl, const FreqInfo *fi,
+                                const int *ord, const int *grp, double t_ref, const double *T,
+                                double *scale, cudaStream_t st) {
+    ml_prd_scale_kernel<<<grid_for(nvox, 128), 128, 0, st>>>(nvox, n_prd, pl, fi, ord, grp, t_ref,
+                                                              T, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ml_prd_rho(const MlPrdArgs &a, cudaStream_t st) {
+    if (a.prec == MG3D_PREC_F64)
+        ml_prd_rho_kernel<double><<<grid_for(a.nvox, 128), 128, 0, st>>>(a);
+    else
+        ml_prd_rho_kernel<float><<<grid_for(a.nvox, 128), 128, 0, st>>>(a);
+    return cudaGetLastError();
 }
 
 template <typename T>

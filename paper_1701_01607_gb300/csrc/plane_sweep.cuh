@@ -24,6 +24,18 @@
 // cluster barrier per plane orders the writes of a step before the reads of
 // the next and the reads of a step before the overwrite two steps later.
 //
+// A second completion scheme (stage 3) replaces the barrier's release fence
+// with transaction-counted stores: values bound for another block go by
+// st.async, which counts its bytes on an mbarrier in the receiving block, and
+// each block waits on its own mbarrier for the bytes its plane receives from
+// other blocks (stores within a block are ordered by __syncthreads).  The
+// reads of a step must still end, cluster-wide, before the plane they came
+// from is overwritten two steps later; a relaxed cluster barrier (no fence)
+// arrives at the end of a step and waits just before the first store of the
+// next.  Every wait on an mbarrier is bounded in time: past the bound the
+// kernel records MG3D_STATUS_WAIT in the status word, stops waiting and runs
+// to the end, so the host reports an error instead of a hung launch.
+//
 // Channels: per stored node the intensities of the group's frequencies in
 // slot order, then chi0 and S of the node's plane (so the upwind chi0 and S
 // are interpolated with the intensities, from the same corners), padded to
@@ -121,6 +133,74 @@ __device__ __forceinline__ void cluster_barrier() {
         "barrier.cluster.arrive.release.aligned;\n\t"
         "barrier.cluster.wait.acquire.aligned;" ::
             : "memory");
+}
+
+// Split phases of a cluster barrier without memory ordering (the async
+// scheme orders its data through mbarriers and __syncthreads)
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+    asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
+}
+// 16-byte store into another block's shared memory that completes 16 bytes of
+// the transaction count of the mbarrier at `bar` (a shared::cluster address
+// in the same block), under a predicate
+__device__ __forceinline__ void st16_async_if(bool c, unsigned a, const float *v, unsigned bar) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %0, 0;\n\t"
+        "@p st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%1], "
+        "{%2, %3, %4, %5}, [%6];\n\t}" ::"r"((int)c),
+        "r"(a), "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void st16_async_if(bool c, unsigned a, const double *v,
+                                              unsigned bar) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %0, 0;\n\t"
+        "@p st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%1], "
+        "{%2, %3}, [%4];\n\t}" ::"r"((int)c),
+        "r"(a), "d"(v[0]), "d"(v[1]), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// the one arrival of a phase, with the bytes the phase is to receive
+__device__ __forceinline__ void mbar_arrive_expect(unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Waits until the phase of parity `parity` of the mbarrier completes, at most
+// kWaitLimitNs; false when the bound ran out.
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+static __device__ __noinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
+    if (mbar_test(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 1;; ++it) {
+        if (mbar_test(bar, parity)) return true;
+        if ((it & 63u) == 0 && global_ns() - t0 > kWaitLimitNs) return false;
+    }
 }
 
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -224,7 +304,7 @@ __device__ __forceinline__ float node_rcp(float) { return 0.0f; }
 }  // namespace plane
 
 // The body of the kernel for ray blockIdx.z and frequency group blockIdx.y.
-template <typename T, int NP>
+template <typename T, int NP, bool AS>
 __device__ __forceinline__ void plane_sweep_body(const PlaneArgs<T> &a) {
     using namespace plane;
     constexpr int VW = vec_width<T>();
@@ -237,6 +317,7 @@ __device__ __forceinline__ void plane_sweep_body(const PlaneArgs<T> &a) {
     const int r = blockIdx.z, g = blockIdx.y;
     const int nb = a.bands;
     const bool cl = nb > 1;
+    const bool as = AS && cl;               // the async completion scheme
     const int rank = (int)cluster_rank();   // 0 in a launch without clusters
     const int nx = a.nx, ny = a.ny, nz = a.nz, rows = a.rows;
     const int y0 = rank * rows;
@@ -256,6 +337,14 @@ __device__ __forceinline__ void plane_sweep_body(const PlaneArgs<T> &a) {
     const unsigned buf_addr = smem_addr(buf);
     __shared__ double exp_tab[kExpTab];
     __shared__ PlaneSlot<T> stab[NP];
+    // async scheme: one mbarrier per plane buffer, one phase per filling
+    __shared__ __align__(8) unsigned long long full_bar[2];
+    const unsigned bar_addr = smem_addr(full_bar);
+    if (as && threadIdx.x == 0) {
+        mbar_init(bar_addr, 1);
+        mbar_init(bar_addr + 8, 1);
+        mbar_init_fence();
+    }
     if (sizeof(T) == 8)
         for (int i = threadIdx.x; i < kExpTab; i += blockDim.x) exp_tab[i] = a.exp_tab[i];
     for (int i = threadIdx.x; i < NP; i += blockDim.x) stab[i] = gs[i];
@@ -341,6 +430,34 @@ __device__ __forceinline__ void plane_sweep_body(const PlaneArgs<T> &a) {
                                col + (unsigned)(hr * pitch * (int)sizeof(T));
         const unsigned padoff = (unsigned)(nx * CS * (int)sizeof(T));
         const bool pad = xs == 0, halo = lr == 0;
+        if constexpr (AS) {
+            if (as) {
+                // to another block: st.async counted on that block's mbarrier
+                // of buffer `par`; within the block: plain stores
+                const unsigned bar = cluster_addr(bar_addr + 8u * par, (unsigned)ob);
+                const unsigned hbar = cluster_addr(bar_addr + 8u * par, (unsigned)hb);
+                const bool rem = ob != rank, hrem = hb != rank;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    const T *cv = ch + v * VW;
+                    if (rem) {
+                        st16_async_if(true, base + v * 16, cv, bar);
+                        st16_async_if(pad, base + padoff + v * 16, cv, bar);
+                    } else {
+                        st16(base + v * 16, cv);
+                        st16_if(pad, base + padoff + v * 16, cv);
+                    }
+                    if (hrem) {
+                        st16_async_if(halo, hbase + v * 16, cv, hbar);
+                        st16_async_if(halo && pad, hbase + padoff + v * 16, cv, hbar);
+                    } else {
+                        st16_if(halo, hbase + v * 16, cv);
+                        st16_if(halo && pad, hbase + padoff + v * 16, cv);
+                    }
+                }
+                return;
+            }
+        }
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             st16(base + v * 16, ch + v * VW);
@@ -364,6 +481,39 @@ __device__ __forceinline__ void plane_sweep_body(const PlaneArgs<T> &a) {
             }
     };
 
+    // Async scheme: the bytes buffer `par` of this block receives from other
+    // blocks when the plane is stored with row shift sy.  Stored row ys (a
+    // row of the band, or the halo row: the next band's first row, row 0
+    // after the last band) holds source row (ys + sy) mod ny, all of its nx
+    // nodes and the pad copy, written by the block that owns that row.  Warp
+    // 0 counts the rows with another owner; its lane 0 posts the phase's one
+    // arrival with the byte count.
+    auto expect_fill = [&](int sy, int par) {
+        if (threadIdx.x >= 32) return;
+        int cnt = 0;
+        for (int j = threadIdx.x; j <= myrows; j += 32) {
+            const int ys = j < myrows ? y0 + j : (rank == nb - 1 ? 0 : y0 + rows);
+            int ysrc = ys + sy;
+            ysrc -= ysrc >= ny ? ny : 0;
+            cnt += band_of(ysrc, a.rmagic) != rank ? 1 : 0;
+        }
+        cnt = __reduce_add_sync(0xffffffffu, cnt);
+        if (threadIdx.x == 0)
+            mbar_arrive_expect(bar_addr + 8u * par, (unsigned)(cnt * (nx + 1) * NV * 16));
+    };
+    bool waits_ok = true;   // false once a bounded wait ran out
+    auto wait_fill = [&](int s) {   // buffer s & 1 holds the plane stored at step s
+        if (waits_ok && !mbar_wait_bounded(bar_addr + 8u * (s & 1), (unsigned)((s >> 1) & 1))) {
+            waits_ok = false;
+            if (a.status) atomicOr(a.status, kPlaneStatusWait);
+        }
+    };
+    if (as && nz > 1) {
+        // every block's mbarriers are initialised before any store reaches them
+        cluster_barrier();
+        expect_fill(a.steps[(long)r * nz].sy, 0);
+    }
+
     // ---- entering boundary plane: I prescribed (bottom: Planck at the local
     // temperature, top: zero), so w0 = 0 and 1 - w0 = 1
     prefetch(0);
@@ -385,7 +535,7 @@ __device__ __forceinline__ void plane_sweep_body(const PlaneArgs<T> &a) {
         }
     }
     if (nz > 1) prefetch(1);
-    if (cl) cluster_barrier();
+    if (cl && !as) cluster_barrier();
     else __syncthreads();
 
     // Regime of a node's weights: every slot in closed form, every slot by
@@ -433,6 +583,15 @@ __device__ __forceinline__ void plane_sweep_body(const PlaneArgs<T> &a) {
                 cS[i] = nS[i];
             }
             if (write) prefetch(t + 1);
+            if (as) {
+                // the other blocks' part of the plane stored at step t - 1
+                wait_fill(t - 1);
+                if (write) {
+                    expect_fill(sp.sy, t & 1);
+                    // every block's reads of this buffer (step t - 1) are over
+                    if (t >= 2) cluster_wait();
+                }
+            }
 #pragma unroll
             for (int i = 0; i < MAXP; ++i) {
                 // FP64 takes its nodes one after the other (its pipe, not
@@ -532,20 +691,28 @@ __device__ __forceinline__ void plane_sweep_body(const PlaneArgs<T> &a) {
                 }
             }
             if (write) {
-                if (cl) cluster_barrier();
-                else __syncthreads();
+                if (as) {
+                    __syncthreads();
+                    if (t + 2 < nz) cluster_arrive_relaxed();
+                } else if (cl) {
+                    cluster_barrier();
+                } else {
+                    __syncthreads();
+                }
             }
         }
     };
     if (fast) run(std::true_type{});
     else run(std::false_type{});
+    // no block leaves while another may still address its shared memory
+    if (as && nz > 1) cluster_barrier();
 }
 
 // MAXT: block-size bound the kernel is compiled for; MINB: resident blocks
 // per SM it must fit (the register budget).
-template <typename T, int NP, int MAXT, int MINB>
+template <typename T, int NP, int MAXT, int MINB, bool AS>
 __global__ void __launch_bounds__(MAXT, MINB) plane_sweep_kernel(const PlaneArgs<T> a) {
-    plane_sweep_body<T, NP>(a);
+    plane_sweep_body<T, NP, AS>(a);
 }
 
 // ------------------------------------------------------------- launching
@@ -557,16 +724,16 @@ inline size_t plane_smem_t(int rows, int nx) {
 
 // Kernel attributes and the launch configuration of shape s (dynamic shared
 // memory, clusters of `bands` blocks); a is used by the launch only.
-template <typename T, int NP, int MAXT, int MINB>
+template <typename T, int NP, int MAXT, int MINB, bool AS>
 static cudaError_t plane_config(const SweepShape &s, int nx, cudaStream_t st,
                                 cudaLaunchConfig_t *cfg, cudaLaunchAttribute *attr) {
     // the limit is the same for every launch, so a CUDA graph that captured a
     // launch needing more shared memory than a later one still replays
-    cudaError_t e = cudaFuncSetAttribute(plane_sweep_kernel<T, NP, MAXT, MINB>,
+    cudaError_t e = cudaFuncSetAttribute(plane_sweep_kernel<T, NP, MAXT, MINB, AS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kMaxPlaneSmem);
     if (e == cudaSuccess && s.bands > kPortableBands)
-        e = cudaFuncSetAttribute(plane_sweep_kernel<T, NP, MAXT, MINB>,
+        e = cudaFuncSetAttribute(plane_sweep_kernel<T, NP, MAXT, MINB, AS>,
                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     *cfg = cudaLaunchConfig_t{};
@@ -585,61 +752,61 @@ static cudaError_t plane_config(const SweepShape &s, int nx, cudaStream_t st,
 
 // launch (a non-null) or occupancy query (a null: *n = clusters, or blocks
 // per SM for one band, the GPU holds at once)
-template <typename T, int NP, int MAXT, int MINB>
+template <typename T, int NP, int MAXT, int MINB, bool AS>
 static cudaError_t plane_go(const PlaneArgs<T> *a, const SweepShape &s, int nx, cudaStream_t st,
                             int *n) {
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
-    cudaError_t e = plane_config<T, NP, MAXT, MINB>(s, nx, st, &cfg, attr);
+    cudaError_t e = plane_config<T, NP, MAXT, MINB, AS>(s, nx, st, &cfg, attr);
     if (e != cudaSuccess) return e;
-    if (a) return cudaLaunchKernelEx(&cfg, plane_sweep_kernel<T, NP, MAXT, MINB>, *a);
+    if (a) return cudaLaunchKernelEx(&cfg, plane_sweep_kernel<T, NP, MAXT, MINB, AS>, *a);
     if (s.bands == 1)
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            n, plane_sweep_kernel<T, NP, MAXT, MINB>, s.threads, cfg.dynamicSmemBytes);
-    return cudaOccupancyMaxActiveClusters(n, plane_sweep_kernel<T, NP, MAXT, MINB>, &cfg);
+            n, plane_sweep_kernel<T, NP, MAXT, MINB, AS>, s.threads, cfg.dynamicSmemBytes);
+    return cudaOccupancyMaxActiveClusters(n, plane_sweep_kernel<T, NP, MAXT, MINB, AS>, &cfg);
 }
 
 // register budget: lean 0 the full budget of MAXT threads (one block per SM),
 // lean 1 (FP32 only) two blocks of 512 or four of 256 per SM (64 registers);
 // FP32 blocks of up to 1024 threads for one or two slots
-template <typename T, int NP>
+template <typename T, int NP, bool AS>
 static cudaError_t plane_go_np(const PlaneArgs<T> *a, const SweepShape &s, int nx,
                                cudaStream_t st, int *n) {
     if constexpr (sizeof(T) == 4) {
         if (s.threads > 512) {
             // 1024 threads (64 registers): small slot counts only
             if constexpr (NP <= 2) {
-                if (s.lean == 0) return plane_go<T, NP, 1024, 1>(a, s, nx, st, n);
+                if (s.lean == 0) return plane_go<T, NP, 1024, 1, AS>(a, s, nx, st, n);
             }
             return cudaErrorInvalidValue;
         }
         if (s.lean == 1)
-            return s.threads <= 256 ? plane_go<T, NP, 256, 4>(a, s, nx, st, n)
-                                    : plane_go<T, NP, 512, 2>(a, s, nx, st, n);
-        return s.threads <= 256 ? plane_go<T, NP, 256, 1>(a, s, nx, st, n)
-                                : plane_go<T, NP, 512, 1>(a, s, nx, st, n);
+            return s.threads <= 256 ? plane_go<T, NP, 256, 4, AS>(a, s, nx, st, n)
+                                    : plane_go<T, NP, 512, 2, AS>(a, s, nx, st, n);
+        return s.threads <= 256 ? plane_go<T, NP, 256, 1, AS>(a, s, nx, st, n)
+                                : plane_go<T, NP, 512, 1, AS>(a, s, nx, st, n);
     } else {
         // the FP64 body does not fit 64 registers without spilling: no lean
         // variant; 448 threads leave it up to 146 registers
         if (s.lean != 0 || s.threads > 512) return cudaErrorInvalidValue;
-        if (s.threads <= 256) return plane_go<T, NP, 256, 1>(a, s, nx, st, n);
-        if (s.threads <= 448) return plane_go<T, NP, 448, 1>(a, s, nx, st, n);
-        return plane_go<T, NP, 512, 1>(a, s, nx, st, n);
+        if (s.threads <= 256) return plane_go<T, NP, 256, 1, AS>(a, s, nx, st, n);
+        if (s.threads <= 448) return plane_go<T, NP, 448, 1, AS>(a, s, nx, st, n);
+        return plane_go<T, NP, 512, 1, AS>(a, s, nx, st, n);
     }
 }
 
-template <typename T>
+template <typename T, bool AS>
 static cudaError_t plane_dispatch(const PlaneArgs<T> *a, const SweepShape &s, int nx,
                                   cudaStream_t st, int *n) {
     if (s.threads < 32 || s.threads > kPlaneMaxThreads || s.threads % 32 || s.lean < 0 ||
         s.lean > 1)
         return cudaErrorInvalidValue;
     switch (s.np) {
-        case 1: return plane_go_np<T, 1>(a, s, nx, st, n);
-        case 2: return plane_go_np<T, 2>(a, s, nx, st, n);
-        case 3: return plane_go_np<T, 3>(a, s, nx, st, n);
-        case 5: return plane_go_np<T, 5>(a, s, nx, st, n);
-        case 8: return plane_go_np<T, 8>(a, s, nx, st, n);
+        case 1: return plane_go_np<T, 1, AS>(a, s, nx, st, n);
+        case 2: return plane_go_np<T, 2, AS>(a, s, nx, st, n);
+        case 3: return plane_go_np<T, 3, AS>(a, s, nx, st, n);
+        case 5: return plane_go_np<T, 5, AS>(a, s, nx, st, n);
+        case 8: return plane_go_np<T, 8, AS>(a, s, nx, st, n);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -19,7 +19,8 @@ size_t plane_smem_bytes(int prec, int np, int rows, int nx) {
 
 cudaError_t launch_plane_sweep_f64(const PlaneArgs<double> &a, const SweepShape &s,
                                    cudaStream_t st) {
-    return plane_dispatch<double>(&a, s, a.nx, st, nullptr);
+    if (s.plane == 2) return launch_plane_async_f64(a, s, st);
+    return plane_dispatch<double, false>(&a, s, a.nx, st, nullptr);
 }
 
 cudaError_t plane_active_clusters_f32(const SweepShape &s, int nx, int *n);
@@ -27,7 +28,8 @@ cudaError_t plane_active_clusters_f32(const SweepShape &s, int nx, int *n);
 cudaError_t plane_active_clusters(int prec, const SweepShape &s, int nx, int *n) {
     *n = 0;
     if (prec != 0) return plane_active_clusters_f32(s, nx, n);
-    return plane_dispatch<double>(nullptr, s, nx, 0, n);
+    if (s.plane == 2) return plane_async_clusters_f64(s, nx, n);
+    return plane_dispatch<double, false>(nullptr, s, nx, 0, n);
 }
 
 }  // namespace mg3d

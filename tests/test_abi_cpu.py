@@ -282,8 +282,25 @@ ML_REFUSALS = [
     (_set(theta_ref=0.0), "theta_ref"),
     (_set(t_ref=-1.0), "t_ref"),
     (_set(lines=[], continua=[]), "no transitions"),
-    (_bad_line(0, gamma_prd=0.5), "partial redistribution"),
+    (_bad_line(0, gamma_prd=1.5), "gamma_prd must lie in [0, 1]"),
+    (_bad_line(0, gamma_prd=float("nan")), "gamma_prd must lie in [0, 1]"),
+    (_bad_line(0, gamma_prd=0.5, n_freq=200), "partial redistribution takes at most"),
 ]
+
+
+def test_create_ml_refuses_prd_with_hermite_or_a_flow(lib):
+    """Partial redistribution of multi-level lines is built for static
+    atmospheres with the linear upwind interpolation; the other combinations
+    are refused before any CUDA call."""
+    atm, atom = _ml_inputs()
+    atom.lines[0].gamma_prd = 0.5
+    with pytest.raises(m.MG3DError) as ei:
+        m.mg3d_create_ml(atm, atom, n_grids=1, sc_interp=1)
+    assert ei.value.code == m.MG3D_E_ARG and "static atmosphere" in m.mg3d_last_error()
+    atm.vel = np.zeros((3,) + atm.shape)
+    with pytest.raises(m.MG3DError) as ei:
+        m.mg3d_create_ml(atm, atom, n_grids=1)
+    assert ei.value.code == m.MG3D_E_ARG and "static atmosphere" in m.mg3d_last_error()
 
 
 @pytest.mark.parametrize("mutate,words", ML_REFUSALS)

@@ -180,6 +180,67 @@ def test_plane_sweep_matches_band_sweep_and_is_reproducible():
     assert rel(u1, ub) < 1e-13
 
 
+ASYNC = 3   # stage value of the shifted-plane sweep with transaction-counted stores
+
+ASYNC_SHAPES = [
+    # (precision, freq_per_block, bands, threads, lean)
+    (m.MG3D_PREC_F64, 9, 2, 512, 0), (m.MG3D_PREC_F64, 9, 3, 64, 0),
+    (m.MG3D_PREC_F64, 4, 6, 64, 0), (m.MG3D_PREC_F64, 9, 16, 32, 0),
+    (m.MG3D_PREC_F32, 9, 5, 64, 0), (m.MG3D_PREC_F32, 9, 8, 64, 1),
+    (m.MG3D_PREC_F32, 2, 4, 128, 1), (m.MG3D_PREC_F32, 4, 2, 1024, 0),
+    (m.MG3D_PREC_F32, 6, 3, 64, 0),
+]
+
+
+@pytest.mark.parametrize("prec,fpb,bands,threads,lean", ASYNC_SHAPES)
+def test_async_completion_equals_cluster_barriers(prec, fpb, bands, threads, lean):
+    """Stores into other blocks counted on the receiving block's mbarrier
+    (stage 3) order the same data as the per-plane cluster barrier (stage 2):
+    the same arithmetic in the same order, so bitwise equal results, and the
+    oracle's to the precision's bar.  Covers ragged bands (16 rows as 6+6+4,
+    3x5+1, ...), a 16-block cluster, frequency groups with a one-frequency
+    slot, both FP32 register budgets and 1024-thread blocks."""
+    atm, atom = synth.stratified_two_level(16, 16, 17, eps=1e-3, sigma=0.3, seed=2)
+    out = {}
+    for stage in (PLANE, ASYNC):
+        jeff, u, cfg = gpu_fs(atm, atom, prec=prec, shape=(fpb, bands, threads, lean, stage))
+        assert cfg == (fpb, bands, threads, lean, stage)
+        out[stage] = (jeff, u)
+    assert np.array_equal(out[PLANE][0], out[ASYNC][0])
+    assert np.array_equal(out[PLANE][1], out[ASYNC][1])
+    tol = TOL_FS64 if prec == m.MG3D_PREC_F64 else TOL_FS32
+    jo, uo = oracle_fs(atm, atom, "16x16x17")
+    assert rel(out[ASYNC][0], jo) < tol
+    assert rel(out[ASYNC][1], uo) < tol
+
+
+def test_async_completion_on_the_bench_box_and_in_cycles():
+    """The 64x64x129 bench box at 5 bands in both precisions against the
+    oracle, then MALI sweeps and a V-cycle with stage 3 on every level equal
+    bitwise to the same with stage 2 (and a graph replay of the cycle)."""
+    atm, atom = synth.box_64x64x129_lognormal(seed=1)
+    jo, uo = oracle_fs(atm, atom, "bench")
+    for prec, tol in ((m.MG3D_PREC_F64, TOL_FS64), (m.MG3D_PREC_F32, TOL_FS32)):
+        jeff, u, cfg = gpu_fs(atm, atom, prec=prec, shape=(9, 5, 512, 0, ASYNC))
+        assert cfg[4] == ASYNC
+        assert rel(jeff, jo) < tol and rel(u, uo) < tol
+    atm, atom = synth.stratified_two_level(32, 32, 33, eps=1e-3, sigma=0.3, seed=3)
+    res = {}
+    for stage in (PLANE, ASYNC):
+        h = m.mg3d_create(atm, atom, n_grids=2, fs_prec=m.MG3D_PREC_F64, nu0=2, nu1=2,
+                          nu2=2, nu3=8)
+        try:
+            for level, bands in ((1, 2), (2, 4)):
+                m.mg3d_set_fs_config(h, level, 9, bands, 128, 0, stage)
+            m.mg3d_mali_sweep(h, 2, 2)
+            m.mg3d_fas_vcycle(h, True)
+            m.mg3d_fas_vcycle(h, False)
+            res[stage] = m.mg3d_get_populations(h, 2)
+        finally:
+            m.mg3d_destroy(h)
+    assert np.array_equal(res[PLANE], res[ASYNC])
+
+
 def test_plane_shapes_refused_where_they_do_not_apply():
     atm, atom = synth.stratified_two_level(16, 16, 17, eps=1e-3, sigma=0.3, seed=2)
     h = m.mg3d_create(atm, atom, n_grids=1)
@@ -187,7 +248,8 @@ def test_plane_shapes_refused_where_they_do_not_apply():
         for bad in [(3, 2, 64, 0, PLANE),     # odd group below n_freq
                     (8, 2, 64, 0, PLANE),     # 4 slots: not built
                     (9, 2, 64, 1, PLANE),     # FP64 has no 64-register variant
-                    (9, 2, 48, 0, PLANE)]:    # not a multiple of 32 threads
+                    (9, 2, 48, 0, PLANE),     # not a multiple of 32 threads
+                    (9, 2, 64, 0, 4)]:        # no sweep kind 4
             with pytest.raises(m.MG3DError):
                 m.mg3d_set_fs_config(h, 1, *bad)
     finally:
