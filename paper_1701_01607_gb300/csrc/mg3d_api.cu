@@ -93,13 +93,14 @@ struct Level {
     double *chi_c = nullptr;     // [nvox] background opacity
     double *cmat = nullptr;      // [N][N][nvox] collisional rates
     double *saha = nullptr;      // [N][nvox] LTE ratios to the continuum
-    void *mchi = nullptr, *mS = nullptr, *msl = nullptr, *mfl = nullptr;  // [nf][nvox]
+    void *mchi = nullptr, *mS = nullptr, *msc = nullptr, *moc = nullptr;  // [nf][nvox]
     void *mdchi = nullptr, *mdS = nullptr;  // [nf][nvox] x-slopes of mchi, mS (Hermite)
     void *mib = nullptr;         // [nf][nplane] bottom intensity
     double *sigma_c = nullptr;   // background coherent scattering [nvox] (FP64)
     void *jbg = nullptr;         // background radiation field [nf][nvox] (FS precision)
     double *prd_c = nullptr;     // partial redistribution of multi-level lines: scaling
-    double *prd_rho = nullptr;   // of R and emission-profile ratio [n_prd_freq][nvox]
+    double *prd_rho = nullptr;   // of R and emission-profile ratio [n_prd_freq][nvox],
+    double *prd_oc = nullptr;    // and 1 - rho chi_t/chi in FP64 [n_prd_freq][nvox]
     int ml_bands = 0, ml_rows = 0, ml_threads = 0;
     int ml_rpb = 12;             // rays of a hemisphere per block of the multi-level sweep
 };
@@ -582,10 +583,10 @@ int dalloc(P **p, size_t count) {
 void free_level(Level &L) {
     void *ptrs[] = {L.T,     L.n_tot, L.c_ul, L.c_lu, L.tz,   L.zf,   L.n,    L.f,   L.n_before,
                     L.r,     L.chi0,  L.S,    L.bbot, L.geom, L.chi_c, L.cmat, L.saha,
-                    L.mchi,  L.mS,    L.msl,  L.mfl,  L.mib,  L.sigma_c, L.jbg,
+                    L.mchi,  L.mS,    L.msc,  L.moc,  L.mib,  L.sigma_c, L.jbg,
                     L.dchi0, L.dS,   L.mdchi, L.mdS,  L.vel,  L.uproj, L.vnorm, L.dinv,
                     L.jnu,   L.jnu_new, L.rho, L.rhoS, L.psteps, L.o_chi0, L.o_S, L.o_bbot,
-                    L.o_psteps, L.prd_c, L.prd_rho};
+                    L.o_psteps, L.prd_c, L.prd_rho, L.prd_oc};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     L = Level{};
@@ -637,7 +638,7 @@ cudaEvent_t pool_event(mg3d_handle *h) {
 int ml_chunk_fs(mg3d_handle *h, int k, int f0, int nc) {
     Level &L = h->lev[k];
     MlOpacityArgs oa{L.nvox, nc, h->N, h->prec, h->d_fi, h->theta_ref, h->t_ref,
-                     L.n, L.T, L.chi_c, L.saha, L.mchi, L.mS, L.msl, L.mfl, f0,
+                     L.n, L.T, L.chi_c, L.saha, L.mchi, L.mS, L.msc, L.moc, f0,
                      h->d_exp_tab, h->exp_l1, h->exp_l2,
                      h->scatter ? L.sigma_c : nullptr, h->scatter ? L.jbg : nullptr,
                      h->moving ? 1 : 0, h->ml_prd ? h->d_prd_index : nullptr,
@@ -659,7 +660,7 @@ int ml_chunk_fs(mg3d_handle *h, int k, int f0, int nc) {
     if (h->prec == MG3D_PREC_F64) {
         MlSweepArgs<double> a{L.nx, L.ny, L.nz, nc, L.ml_rows,
                               (const double *)L.mchi, (const double *)L.mS,
-                              (const double *)L.msl, (const double *)L.mfl,
+                              (const double *)L.msc, (const double *)L.moc,
                               (const double *)ib, L.geom, h->d_exp_tab, h->exp_l1, h->exp_l2,
                               (double *)h->ml_jx, (double *)h->ml_ux, L.ml_rpb,
                               (double *)h->ml_jm, (const double *)L.mdchi, (const double *)L.mdS,
@@ -671,7 +672,7 @@ int ml_chunk_fs(mg3d_handle *h, int k, int f0, int nc) {
     } else {
         MlSweepArgs<float> a{L.nx, L.ny, L.nz, nc, L.ml_rows,
                              (const float *)L.mchi, (const float *)L.mS,
-                             (const float *)L.msl, (const float *)L.mfl,
+                             (const float *)L.msc, (const float *)L.moc,
                              (const float *)ib, L.geom, h->d_exp_tab, h->exp_l1, h->exp_l2,
                              (float *)h->ml_jx, (float *)h->ml_ux, L.ml_rpb,
                              (float *)h->ml_jm, (const float *)L.mdchi, (const float *)L.mdS,
@@ -711,7 +712,8 @@ int ml_prd_prepare(mg3d_handle *h, int k) {
     Level &L = h->lev[k];
     MlPrdArgs a{L.nvox, h->N, h->ntrans, h->n_prd, h->d_fi, h->d_ti, h->d_prd, h->d_prd_ord,
                 h->d_prd_grp, h->theta_ref, h->t_ref, L.n, L.T, L.cmat, L.saha, L.jbg, h->prec,
-                L.prd_c, L.prd_rho, h->d_exp_tab, h->exp_l1, h->exp_l2};
+                L.prd_c, L.prd_rho, h->d_exp_tab, h->exp_l1, h->exp_l2, L.chi_c, L.sigma_c,
+                L.prd_oc};
     return launched(h, launch_ml_prd_rho(a, h->stream), "partial redistribution ratios");
 }
 
@@ -735,7 +737,8 @@ int ml_accumulate(mg3d_handle *h, int k, int f0, int nc, bool zero_rad) {
     MlAccumArgs a{L.nvox, f0, nc, h->ntrans, h->prec, h->d_fi, h->d_ti, h->theta_ref,
                   h->t_ref, L.T, h->ml_jx, h->ml_ux, 2 * (12 / L.ml_rpb), zero_rad ? 1 : 0,
                   h->ml_acc, h->d_exp_tab, h->exp_l1, h->exp_l2, bg ? h->ml_jm : nullptr,
-                  bg ? L.jbg : nullptr, h->moving ? 1 : 0};
+                  bg ? L.jbg : nullptr, h->moving ? 1 : 0,
+                  h->ml_prd ? h->d_prd_index : nullptr, h->ml_prd ? L.prd_oc : nullptr};
     return launched(h, launch_ml_accum(a, h->stream), "radiative sums");
 }
 
@@ -1794,6 +1797,7 @@ int create_impl(const mg3d_atmosphere *atm, const mg3d_atom *atom, const mg3d_qu
     MG_TRY(dev_alloc(&h->pj, h->partial_elems * es));
     MG_TRY(dev_alloc(&h->pu, h->partial_elems * es));
     MG_TRY(dalloc(&h->scal, kScalStatus + 1));
+    MG_CUDA(cudaMemset(h->scal, 0, (kScalStatus + 1) * sizeof(unsigned long long)));
     for (int k = 1; k <= h->L; ++k) MG_TRY(zero_radiation(h, k));
     MG_CUDA(cudaStreamSynchronize(h->stream));
     return MG3D_OK;
@@ -1842,7 +1846,7 @@ int alloc_ml_chunks(mg3d_handle *h, int chunk) {
     const size_t es = elem_size(h->prec);
     for (int k = 1; k <= h->L; ++k) {
         Level &L = h->lev[k];
-        void **bufs[6] = {&L.mchi, &L.mS, &L.msl, &L.mfl, &L.mdchi, &L.mdS};
+        void **bufs[6] = {&L.mchi, &L.mS, &L.msc, &L.moc, &L.mdchi, &L.mdS};
         for (void **p : bufs) {
             if (*p) cudaFree(*p);
             *p = nullptr;
@@ -1855,7 +1859,7 @@ int alloc_ml_chunks(mg3d_handle *h, int chunk) {
     h->ml_chunk = 0;
     for (int k = 1; k <= h->L; ++k) {
         Level &L = h->lev[k];
-        void **bufs[6] = {&L.mchi, &L.mS, &L.msl, &L.mfl, &L.mdchi, &L.mdS};
+        void **bufs[6] = {&L.mchi, &L.mS, &L.msc, &L.moc, &L.mdchi, &L.mdS};
         const int nbufs = h->params.sc_interp ? 6 : 4;
         for (int i = 0; i < nbufs; ++i) MG_TRY(dev_alloc(bufs[i], (size_t)chunk * L.nvox * es));
     }
@@ -1886,7 +1890,7 @@ int time_ml_shape(mg3d_handle *h, int k, int bands, int rpb, int threads, int nc
         if (h->prec == MG3D_PREC_F64) {
             MlSweepArgs<double> sa{L.nx, L.ny, L.nz, nc, L.ml_rows,
                                    (const double *)L.mchi, (const double *)L.mS,
-                                   (const double *)L.msl, (const double *)L.mfl,
+                                   (const double *)L.msc, (const double *)L.moc,
                                    (const double *)L.mib, L.geom, h->d_exp_tab, h->exp_l1,
                                    h->exp_l2, (double *)h->ml_jx, (double *)h->ml_ux, rpb,
                                    nullptr, (const double *)L.mdchi, (const double *)L.mdS,
@@ -1899,7 +1903,7 @@ int time_ml_shape(mg3d_handle *h, int k, int bands, int rpb, int threads, int nc
         } else {
             MlSweepArgs<float> sa{L.nx, L.ny, L.nz, nc, L.ml_rows,
                                   (const float *)L.mchi, (const float *)L.mS,
-                                  (const float *)L.msl, (const float *)L.mfl,
+                                  (const float *)L.msc, (const float *)L.moc,
                                   (const float *)L.mib, L.geom, h->d_exp_tab, h->exp_l1,
                                   h->exp_l2, (float *)h->ml_jx, (float *)h->ml_ux, rpb,
                                   nullptr, (const float *)L.mdchi, (const float *)L.mdS,
@@ -1950,7 +1954,7 @@ bool ml_single_ray_only(const mg3d_handle *h, int k) {
 int autotune_ml_level(mg3d_handle *h, int k, int nc, int *evaluated) {
     Level &L = h->lev[k];
     MlOpacityArgs oa{L.nvox, nc, h->N, h->prec, h->d_fi, h->theta_ref, h->t_ref,
-                     L.n, L.T, L.chi_c, L.saha, L.mchi, L.mS, L.msl, L.mfl, 0,
+                     L.n, L.T, L.chi_c, L.saha, L.mchi, L.mS, L.msc, L.moc, 0,
                      h->d_exp_tab, h->exp_l1, h->exp_l2, nullptr, nullptr, h->moving ? 1 : 0};
     MG_TRY(launched(h, launch_ml_opacity(oa, h->stream), "multi-level opacity"));
     if (h->params.sc_interp)
@@ -2156,6 +2160,8 @@ int setup_ml_prd(mg3d_handle *h, const mg3d_ml_atom *atom) {
         Level &L = h->lev[k];
         MG_TRY(dalloc(&L.prd_c, (size_t)pf * L.nvox));
         MG_TRY(dalloc(&L.prd_rho, (size_t)pf * L.nvox));
+        MG_TRY(dalloc(&L.prd_oc, (size_t)pf * L.nvox));
+        MG_CUDA(cudaMemset(L.prd_oc, 0, (size_t)pf * L.nvox * sizeof(double)));
         ones.assign((size_t)pf * L.nvox, 1.0);
         MG_CUDA(cudaMemcpy(L.prd_rho, ones.data(), ones.size() * 8, cudaMemcpyHostToDevice));
         MG_TRY(launched(h, launch_ml_prd_scale(L.nvox, h->n_prd, h->d_prd, h->d_fi, h->d_prd_ord,
@@ -2379,6 +2385,7 @@ int create_ml_impl(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
                                   ? std::min(params->ml_chunk, h->nfreq_ml)
                                   : default_ml_chunk(h)));
     MG_TRY(dalloc(&h->scal, kScalStatus + 1));
+    MG_CUDA(cudaMemset(h->scal, 0, (kScalStatus + 1) * sizeof(unsigned long long)));
     for (int k = 1; k <= h->L; ++k) MG_TRY(zero_radiation(h, k));
     MG_CUDA(cudaStreamSynchronize(h->stream));
     return MG3D_OK;
@@ -2467,7 +2474,7 @@ int batch_fs(mg3d_batch *b, int k) {
             Level &L = h->lev[k];
             const int f0 = (int)c * h->ml_chunk, nc = std::min(h->ml_chunk, h->nfreq_ml - f0);
             MlOpacityArgs oa{L.nvox, nc, h->N, h->prec, h->d_fi, h->theta_ref, h->t_ref,
-                             L.n, L.T, L.chi_c, L.saha, L.mchi, L.mS, L.msl, L.mfl, f0,
+                             L.n, L.T, L.chi_c, L.saha, L.mchi, L.mS, L.msc, L.moc, f0,
                              h->d_exp_tab, h->exp_l1, h->exp_l2};
             MG_TRY(batch_launched(b, launch_ml_opacity(oa, b->stream), "batch opacity"));
         }
@@ -2761,7 +2768,7 @@ int batch_build_level(mg3d_batch *b, int k) {
                 if (b->prec == MG3D_PREC_F64) {
                     MlSweepArgs<double> a{L.nx, L.ny, L.nz, nc, L.ml_rows,
                                           (const double *)L.mchi, (const double *)L.mS,
-                                          (const double *)L.msl, (const double *)L.mfl,
+                                          (const double *)L.msc, (const double *)L.moc,
                                           (const double *)ib, L.geom, h->d_exp_tab, h->exp_l1,
                                           h->exp_l2, (double *)h->ml_jx, (double *)h->ml_ux,
                                           L.ml_rpb};
@@ -2769,7 +2776,7 @@ int batch_build_level(mg3d_batch *b, int k) {
                 } else {
                     MlSweepArgs<float> a{L.nx, L.ny, L.nz, nc, L.ml_rows,
                                          (const float *)L.mchi, (const float *)L.mS,
-                                         (const float *)L.msl, (const float *)L.mfl,
+                                         (const float *)L.msc, (const float *)L.moc,
                                          (const float *)ib, L.geom, h->d_exp_tab, h->exp_l1,
                                          h->exp_l2, (float *)h->ml_jx, (float *)h->ml_ux,
                                          L.ml_rpb};

@@ -273,7 +273,7 @@ struct TransInfo {
 template <typename T>
 struct MlSweepArgs {
     int nx, ny, nz, nfreq, rows;
-    const T *chi, *S, *sl, *fl;   // [nfreq][nvox]
+    const T *chi, *S, *sc, *oc;   // [nfreq][nvox]
     const T *ib;                  // [nfreq][nx*ny] intensity entering at the bottom
     const StepGeom *geom;         // [kRays][nz]
     const double *exp_tab;
@@ -283,7 +283,7 @@ struct MlSweepArgs {
     T *jm;                        // mean intensity sum_r w_r I per slot, or null
     const T *dchi, *dS;           // [nfreq][nvox] x-slopes of chi and S (herm only)
     int herm;                     // 1: monotone cubic Hermite upwind interpolation
-    // moving atmospheres (moving = 1): chi, S, sl, fl hold the parts the
+    // moving atmospheres (moving = 1): chi, S, sc, oc hold the parts the
     // opacity kernel writes in moving mode; per global frequency f0 + f the
     // line offset, quadrature weight and line index (-1: continuum); per
     // line, ray and node the inverse profile sum [nlines][kRays][nvox]; per
@@ -326,6 +326,8 @@ struct MlPrdArgs {
     double *rho;                     // [n_prd_freq][nvox] out
     const double *exp_tab;
     double exp_l1, exp_l2;
+    const double *chi_c, *sigma_c;   // background opacity [nvox] and scattering (nullable)
+    double *oc;                      // [n_prd_freq][nvox] out: 1 - rho chi_t/chi
 };
 
 // Opacity of the chunk of frequencies f0 .. f0+nfreq-1, written at the
@@ -336,7 +338,7 @@ struct MlOpacityArgs {
     const FreqInfo *fi;
     double theta_ref, t_ref;
     const double *n, *T, *chi_c, *saha;
-    void *chi, *S, *sl, *fl;
+    void *chi, *S, *sc, *oc;       // sc = S - rho eta_t/chi, oc = 1 - rho chi_t/chi
     int f0;
     const double *exp_tab;         // FP64 exp table of the sweep
     double exp_l1, exp_l2;
@@ -345,8 +347,8 @@ struct MlOpacityArgs {
     int moving;                    // 1: write the ray-independent parts instead (a
                                    // moving atmosphere): chi <- the transition's opacity
                                    // at unit profile, S <- its emissivity at unit profile
-                                   // (continua: their own), sl <- background opacity,
-                                   // fl <- background emissivity
+                                   // (continua: their own), oc <- background opacity,
+                                   // sc <- background emissivity
     const int *prd_index;          // [n_freq] row of rho for a PRD line frequency, else -1
                                    // (null: no partial redistribution)
     const double *prd_rho;         // [n_prd_freq][nvox] emission-profile ratio psi/phi
@@ -375,6 +377,9 @@ struct MlAccumArgs {
     void *jbg;                     // background field [n_freq][nvox] written from jm
     int moving;                    // 1: line sums already carry their per-ray profile
                                    // weights (sum 1 over a line), so they add as they are
+    const int *prd_index;          // [n_freq] PRD row of a frequency, else -1 (null: none)
+    const double *prd_oc;          // [n_prd_freq][nvox] 1 - rho chi_t/chi in FP64: U of a
+                                   // PRD frequency is oc + (1 - oc) sum_r w_r u_r
 };
 
 struct MlRateArgs {

@@ -4,8 +4,10 @@
 // Opacity (Eq. 1, Sec. 2.1, Sec. 3).  Every frequency point belongs to one
 // transition (lower l, upper u); with the grey LTE background chi_c:
 //   chi = chi_t + chi_c,  S = (eta_t + chi_c B_nu) / chi,
-//   sl = eta_t / chi (the part of S the transition's populations set),
-//   fl = chi_t / chi (its share of the opacity).
+//   sc = chi_c B_nu / chi = S - eta_t / chi (the part of S the transition's
+//        populations do not set),
+//   oc = chi_c / chi = 1 - chi_t / chi (the opacity share they do not set),
+// each formed directly, not as a difference.
 // Line:        chi_t = kappa (n_l g_u/g_l - n_u) phi,  eta_t = kappa rho^3 n_u phi,
 //              phi = exp(-(x/d)^2)/(sqrt(pi) d), d = sqrt(T/t_ref), B at line centre.
 // Bound-free:  chi_t = kappa y^-3 (n_l - n_u G E),  eta_t = kappa y^-3 n_u G E (rho y)^3,
@@ -16,10 +18,16 @@
 // bands and each holds the intensity planes of the group's rays, double
 // buffered.  A thread owns a node and walks the group's rays, so the angle
 // sums
-//   Jx = sum_r w_r (I - w0 sl),   Ux = sum_r w_r (1 - w0 fl)
-// over the group are complete in registers (as sum I - sl sum w0 and
-// rays - fl sum w0, sl and fl being the node's) and written once per group;
-// the radiative sums below add the groups in order.
+//   Jx = sum_r w_r (I - w0 eta_t/chi),   Ux = sum_r w_r (1 - w0 chi_t/chi)
+// over the group are complete in registers and written once per group; the
+// radiative sums below add the groups in order.  They are accumulated as
+//   Jx = sum (I - w0 S) + sc sum w0,   Ux = sum (1 - w0) + oc sum w0,
+// where I - w0 S = I_up e^-x + w_up S_up and 1 - w0 = u come from the step
+// itself: every term is non-negative, so in FP32 no cancellation between
+// I and w0 eta_t/chi (nearly equal in an optically thick line) degrades
+// them.  The MALI rates of a scattering-dominated line depend on the small
+// difference J - Lambda* S, so this order keeps the FP32 formal solution
+// accurate there.
 //
 // Rates (Rybicki & Hummer 1992, diagonal operator).  Per node, for a line:
 //   Jbar = sum wphi Jx, Ubar = sum wphi Ux (wphi: trapezoid x profile,
@@ -138,36 +146,41 @@ __global__ void ml_opacity_kernel(const MlOpacityArgs a) {
                 }
                 ((T *)a.chi)[i] = ca;
                 ((T *)a.S)[i] = ea;
-                ((T *)a.sl)[i] = cb;
-                ((T *)a.fl)[i] = eb;
+                ((T *)a.oc)[i] = cb;
+                ((T *)a.sc)[i] = eb;
                 continue;
             }
-            T chi, src;
+            // the background's opacity and emissivity (continuum, and
+            // coherent scattering of the previous mean intensity)
+            T chi_b = (T)cc, eta_b = (T)cc * B;
             if (a.sigma_c) {
-                // background coherent scattering with the previous mean intensity
                 const T sg = (T)a.sigma_c[v];
-                const T jb = ((const T *)a.jbg)[(long)(a.f0 + fl) * nvox + v];
-                chi = chi_t + (T)cc + sg;
-                src = eta_t + (T)cc * B + sg * jb;
-            } else {
-                chi = chi_t + (T)cc;
-                src = eta_t + (T)cc * B;
+                chi_b += sg;
+                eta_b += sg * ((const T *)a.jbg)[(long)(a.f0 + fl) * nvox + v];
             }
             T rho = T(1);
+            bool prd = false;
             if (a.prd_index) {
                 // partial redistribution: the line's emission profile is rho phi,
                 // so its emissivity and the transition's shares scale by rho
                 const int pr = a.prd_index[a.f0 + fl];
                 if (pr >= 0) {
                     rho = (T)a.prd_rho[(long)pr * nvox + v];
-                    src += (rho - T(1)) * eta_t;
+                    prd = true;
                 }
             }
+            const T chi = chi_t + chi_b;
             const T inv = T(1) / chi;
             ((T *)a.chi)[i] = chi;
-            ((T *)a.S)[i] = src * inv;
-            ((T *)a.sl)[i] = rho * eta_t * inv;
-            ((T *)a.fl)[i] = rho * chi_t * inv;
+            ((T *)a.S)[i] = (rho * eta_t + eta_b) * inv;
+            // the parts of S and chi the transition does not set, formed
+            // directly: S - rho eta_t/chi and 1 - chi_t/chi.  For a PRD
+            // frequency oc = 1 - rho chi_t/chi takes either sign and its
+            // weighted sum over the line nearly cancels, so the sweep gets
+            // oc = 0 (Ux = sum w u) and the radiative sums add the local
+            // term in FP64 (prd_oc)
+            ((T *)a.sc)[i] = eta_b * inv;
+            ((T *)a.oc)[i] = prd ? T(0) : chi_b * inv;
         }
     }
 }
@@ -323,6 +336,10 @@ __global__ void __launch_bounds__(128) ml_prd_rho_kernel(const MlPrdArgs a) {
             const double excite = a.n[(long)L.lo * nvox + x] * L.gr * L.b_ul * Jbar;
             const double frad = excite / inflow;
             prd_r0_product(L.nf, L.ngrp, gs, g, v, m, suf);
+            // the line's opacity at the node (as the opacity step forms it)
+            // for 1 - rho chi_t/chi, the local term of the line's U
+            const double nlo = a.n[(long)L.lo * nvox + x], nup = a.n[(long)L.up * nvox + x];
+            const double chi_b = a.chi_c[x] + (a.sigma_c ? a.sigma_c[x] : 0.0);
             for (int s = 0; s < L.nf; ++s) {
                 const int f = a.ord[L.ord0 + s];
                 const long row = (long)(L.pf0 + f - L.f_begin) * nvox + x;
@@ -332,6 +349,9 @@ __global__ void __launch_bounds__(128) ml_prd_rho_kernel(const MlPrdArgs a) {
                     r = 1.0 + L.gamma * frad * (Af / (phi[s] * Jbar) - 1.0);
                 }
                 a.rho[row] = r;
+                const FreqInfo q = a.fi[f];
+                const double chi_t = q.kappa * phi[s] * (q.gr * nlo - nup);
+                a.oc[row] = (chi_b + (1.0 - r) * chi_t) / (chi_t + chi_b);
             }
         }
     }
@@ -401,8 +421,8 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
     const long nvox = nplane * nz;
     const T *__restrict__ chif = a.chi + (long)f * nvox;
     const T *__restrict__ Sf = a.S + (long)f * nvox;
-    const T *__restrict__ slf = a.sl + (long)f * nvox;
-    const T *__restrict__ flf = a.fl + (long)f * nvox;
+    const T *__restrict__ scf = a.sc + (long)f * nvox;
+    const T *__restrict__ ocf = a.oc + (long)f * nvox;
     T *__restrict__ jxo = a.jx + ((long)slot * a.nfreq + f) * nvox;
     T *__restrict__ uxo = a.ux + ((long)slot * a.nfreq + f) * nvox;
     T *__restrict__ jmo = a.jm ? a.jm + ((long)slot * a.nfreq + f) * nvox : nullptr;
@@ -447,9 +467,9 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
     // VEL: this frequency's line (or -1), offset and weight
     const int vl = VEL ? a.vline[a.f0 + f] : -1;
     const T vxf = VEL ? a.vx[a.f0 + f] : T(0), vwf = VEL ? a.vwq[a.f0 + f] : T(0);
-    // chi, S, sl, fl and the profile weight of node v for ray r0 + j
-    auto moving_terms = [&](long v, int j, T &chi, T &S, T &sl, T &fl, T &wr) {
-        const T A = chif[v], E = Sf[v], cb = slf[v], eb = flf[v];
+    // chi, S, sc, oc and the profile weight of node v for ray r0 + j
+    auto moving_terms = [&](long v, int j, T &chi, T &S, T &sc, T &oc, T &wr) {
+        const T A = chif[v], E = Sf[v], cb = ocf[v], eb = scf[v];
         T prof = T(1);
         wr = T(1);
         if (vl >= 0) {
@@ -463,8 +483,8 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
         chi = ct + cb;
         const T inv = T(1) / chi;
         S = (et_ + eb) * inv;
-        sl = et_ * inv;
-        fl = ct * inv;
+        sc = eb * inv;
+        oc = cb * inv;
     };
 
     for (int t = 0; t < nz; ++t) {
@@ -478,8 +498,8 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
                 const long v = (long)k * nplane + (long)y * nx + x;
                 T jacc = 0, uacc = 0;
                 for (int j = 0; j < rpb; ++j) {
-                    T chi, S, sl, fl, wr;
-                    moving_terms(v, j, chi, S, sl, fl, wr);
+                    T chi, S, sc, oc, wr;
+                    moving_terms(v, j, chi, S, sc, oc, wr);
                     const long i = j * raystride + (long)yl * nx + x;
                     cur[i] = Ib;
                     cur[coff + i] = chi;
@@ -563,10 +583,11 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
                 const int yl = q / nx, x = q - yl * nx;
                 const int y = y0 + yl;
                 const long v = (long)k * nplane + (long)y * nx + x;
-                const T chi_loc = chif[v], S_loc = Sf[v], sl = slf[v], fl = flf[v];
-                // sl and fl are the node's: sum I and w0 over the rays and
-                // form Jx = sum I - sl sum w0, Ux = rays - fl sum w0 once
-                T sum_i = 0, sum_w0 = 0;
+                const T chi_loc = chif[v], S_loc = Sf[v], sc = scf[v], oc = ocf[v];
+                // sc and oc are the node's: sum I - w0 S, 1 - w0, w0 (and I
+                // for the mean intensity) over the rays, then
+                // Jx = sum (I - w0 S) + sc sum w0, Ux = sum u + oc sum w0
+                T sum_i = 0, sum_p = 0, sum_u = 0, sum_w0 = 0;
                 if constexpr (VEL) {
                     T jacc = 0, uacc = 0;
                     for (int j = 0; j < rpb; ++j) {
@@ -582,19 +603,20 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
                                    w11 * Pb[o + xb];
                         };
                         const T I_up = bil(0), chi_up = bil(coff), S_up = bil(soff);
-                        T chi, S, sl_r, fl_r, wr;
-                        moving_terms(v, j, chi, S, sl_r, fl_r, wr);
+                        T chi, S, sc_r, oc_r, wr;
+                        moving_terms(v, j, chi, S, sc_r, oc_r, wr);
                         const T x_tau = (chi_up + chi) * g_hs[j];
                         T ex, w0, wup, u;
                         ScWeights<T>::eval(x_tau, rcp(x_tau), et, ex, w0, wup, u);
-                        const T I = I_up * ex + wup * S_up + w0 * S;
+                        const T part = I_up * ex + wup * S_up;   // I - w0 S
+                        const T I = part + w0 * S;
                         const long i = j * raystride + (long)yl * nx + x;
                         cur[i] = I;
                         cur[coff + i] = chi;
                         cur[soff + i] = S;
                         sum_i += I;
-                        jacc += wr * (I - w0 * sl_r);
-                        uacc += wr * (T(1) - w0 * fl_r);
+                        jacc += wr * (part + w0 * sc_r);
+                        uacc += wr * (u + w0 * oc_r);
                     }
                     jxo[v] = wray * jacc;
                     uxo[v] = wray * uacc;
@@ -630,9 +652,12 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
                         const T x_tau = (chi_up + chi_loc) * g_hs[j];
                         T ex, w0, wup, u;
                         ScWeights<T>::eval(x_tau, rcp(x_tau), et, ex, w0, wup, u);
-                        const T I = I_up * ex + wup * S_up + w0 * S_loc;
+                        const T part = I_up * ex + wup * S_up;   // I - w0 S
+                        const T I = part + w0 * S_loc;
                         cur[j * raystride + (long)yl * nx + x] = I;
                         sum_i += I;
+                        sum_p += part;
+                        sum_u += u;
                         sum_w0 += w0;
                     }
                 } else
@@ -651,13 +676,16 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
                     const T x_tau = (chi_up + chi_loc) * g_hs[j];
                     T ex, w0, wup, u;
                     ScWeights<T>::eval(x_tau, rcp(x_tau), et, ex, w0, wup, u);
-                    const T I = I_up * ex + wup * S_up + w0 * S_loc;
+                    const T part = I_up * ex + wup * S_up;   // I - w0 S
+                    const T I = part + w0 * S_loc;
                     cur[j * raystride + (long)yl * nx + x] = I;
                     sum_i += I;
+                    sum_p += part;
+                    sum_u += u;
                     sum_w0 += w0;
                 }
-                jxo[v] = wray * (sum_i - sl * sum_w0);
-                uxo[v] = wray * (T(rpb) - fl * sum_w0);
+                jxo[v] = wray * (sum_p + sc * sum_w0);
+                uxo[v] = wray * (sum_u + oc * sum_w0);
                 if (jmo) jmo[v] = wray * sum_i;
             }
         }
@@ -905,7 +933,15 @@ __global__ void ml_accum_kernel(const MlAccumArgs a) {
                     // profile in the formal-solution precision, sums in FP64
                     const double wphi = q.w * (double)opac_exp((TP)(xd * xd), et) * rsqpi * inv_d;
                     double J = 0.0, U = 1.0;
-                    if (!a.zero_radiation) sums(f, v, J, U);
+                    if (!a.zero_radiation) {
+                        sums(f, v, J, U);
+                        const int pr = a.prd_index ? a.prd_index[f] : -1;
+                        if (pr >= 0) {
+                            // U = sum_r w_r (1 - w0 (1 - oc)) = oc + (1 - oc) sum_r w_r u_r
+                            const double oc = a.prd_oc[(long)pr * nvox + v];
+                            U = oc + (1.0 - oc) * U;
+                        }
+                    }
                     s0 += wphi;
                     s1 += wphi * J;
                     s2 += wphi * U;

@@ -164,6 +164,36 @@ def test_ml_fp32_sweeps():
         m.mg3d_destroy(h)
 
 
+def test_ml_fp32_scattering_dominated_lines():
+    """Resonance lines scattering-dominated (collisions out of the ground
+    level 1e3 times weaker): the MALI populations follow the small
+    difference J - Lambda* S of a thick line, so the sweep accumulates
+    Jx = sum (I - w0 S) + sc sum w0 and Ux = sum u + oc sum w0 from
+    non-negative terms (sc, oc: the background's shares, formed directly).
+    With Jx = sum I - sl sum w0 in FP32 the populations were 3e-4 off after
+    one sweep; the FP32 formal solution now keeps them within 1e-5 of the
+    oracle after sweeps and converged."""
+    atom = synth.hydrogen_like_atom(line_freq=7, cont_freq=4, seed=2)
+    atm = synth.chromosphere(8, 8, 17, atom, seed=2, ground_collisions=1e-3)
+    p = O.MultiLevelProblem(atm, atom)
+    n = p.zero_radiation(1)
+    h = m.mg3d_create_ml(atm, atom, n_grids=1, fs_prec=m.MG3D_PREC_F32)
+    try:
+        for _ in range(6):
+            m.mg3d_mali_sweep(h, 1, 1)
+            n, _ = p.mali_sweep(1, n)
+            assert rel(m.mg3d_get_populations(h, 1), n) < 1e-5
+    finally:
+        m.mg3d_destroy(h)
+    n_c, _ = O.mali_solve(O.MultiLevelProblem(atm, atom), 1e-8)
+    h = m.mg3d_create_ml(atm, atom, n_grids=1, fs_prec=m.MG3D_PREC_F32)
+    try:
+        m.mg3d_mali_solve(h, 1e-6, 500)
+        assert rel(m.mg3d_get_populations(h, 1), n_c) < 1e-5
+    finally:
+        m.mg3d_destroy(h)
+
+
 def test_ml_six_level_atom_600_frequencies():
     """The 6-level atom at full spectral resolution (5 lines x 100 and
     5 continua x 20 frequencies) on a 16x16x33 chromosphere: one formal

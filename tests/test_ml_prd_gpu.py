@@ -10,7 +10,8 @@ on the grid and f_rad the radiative share of the inflow into the upper
 level.  The GPU computes the scaling once per grid and rho before each
 formal solution; the opacity step applies it to the source function and to
 the transition's shares.  Bars: populations to 1e-10 after a fixed number of
-FP64 sweeps, V-cycles or an FMG solve; 1e-4 with the FP32 formal solution.
+FP64 sweeps, V-cycles or an FMG solve; 1e-5 with the FP32 formal solution
+(after sweeps, and converged against the converged oracle).
 """
 
 import numpy as np
@@ -128,6 +129,14 @@ def test_ml_prd_chunks_and_ray_groups():
 
 
 def test_ml_prd_fp32_formal_solution():
+    """FP32 formal solution, FP64 rates.  The line's local operator U sums
+    1 - w0 rho chi_t/chi over frequencies whose terms take both signs (rho
+    above and below 1) and nearly cancel in a thick line, while the MALI
+    populations of a scattering-dominated line follow the small difference
+    between U and the Lambda* implicit in Jx: that term stays in FP64
+    (1 - rho chi_t/chi from the ratios kernel, U = oc + (1 - oc) sum w u).
+    Formed in FP32 it put the populations 1e-4 off after a few sweeps; they
+    now stay within a few FP32 ulps, after sweeps and converged."""
     atm, atom = prd_box(1.0)
     p = O.MultiLevelProblem(atm, atom)
     n = p.zero_radiation(1)
@@ -136,7 +145,14 @@ def test_ml_prd_fp32_formal_solution():
     h = m.mg3d_create_ml(atm, atom, n_grids=1, fs_prec=m.MG3D_PREC_F32)
     try:
         m.mg3d_mali_sweep(h, 1, 4)
-        assert rel(m.mg3d_get_populations(h, 1), n) < 1e-4
+        assert rel(m.mg3d_get_populations(h, 1), n) < 1e-5
+    finally:
+        m.mg3d_destroy(h)
+    n_c, _ = O.mali_solve(O.MultiLevelProblem(atm, atom), 1e-8)
+    h = m.mg3d_create_ml(atm, atom, n_grids=1, fs_prec=m.MG3D_PREC_F32)
+    try:
+        m.mg3d_mali_solve(h, 1e-6, 500)
+        assert rel(m.mg3d_get_populations(h, 1), n_c) < 1e-5
     finally:
         m.mg3d_destroy(h)
 

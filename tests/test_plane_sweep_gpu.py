@@ -186,7 +186,7 @@ ASYNC_SHAPES = [
     # (precision, freq_per_block, bands, threads, lean)
     (m.MG3D_PREC_F64, 9, 2, 512, 0), (m.MG3D_PREC_F64, 9, 3, 64, 0),
     (m.MG3D_PREC_F64, 4, 6, 64, 0), (m.MG3D_PREC_F64, 9, 16, 32, 0),
-    (m.MG3D_PREC_F32, 9, 5, 64, 0), (m.MG3D_PREC_F32, 9, 8, 64, 1),
+    (m.MG3D_PREC_F32, 9, 6, 64, 0), (m.MG3D_PREC_F32, 9, 8, 64, 1),
     (m.MG3D_PREC_F32, 2, 4, 128, 1), (m.MG3D_PREC_F32, 4, 2, 1024, 0),
     (m.MG3D_PREC_F32, 6, 3, 64, 0),
 ]
