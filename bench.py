@@ -1178,8 +1178,10 @@ def run_profile_ml(prec_name, launches, shape=""):
     """A few multi-level formal solutions for ncu: the 6-level atom with 120
     frequencies (lines 5 x 20, continua 5 x 4) on a 64x64x129 chromosphere,
     about 2 GB on the device in FP32.  ``shape`` "bands,rays_per_block,threads"
-    fixes the multi-level sweep's shape (e.g. an autotuned one); no tuning
-    runs here, so every sweep launch is a profiled one."""
+    fixes the multi-level sweep's shape (e.g. an autotuned one), and
+    "bands,rays_per_block,threads,kind,freq_per_block" its kind as well (1:
+    the shifted-plane form); no tuning runs here, so every sweep launch is a
+    profiled one."""
     from paper_1701_01607_gb300 import mg3d as m
     from paper_1701_01607_gb300 import synth
     m.load(build_if_missing=True)
@@ -1189,10 +1191,14 @@ def run_profile_ml(prec_name, launches, shape=""):
     h = m.mg3d_create_ml(atm, atom, n_grids=1, fs_prec=prec)
     try:
         if shape:
-            m.mg3d_set_ml_shape(h, 1, *[int(v) for v in shape.split(",")])
+            v = [int(x) for x in shape.split(",")]
+            if len(v) == 5:
+                m.mg3d_set_ml_shape_ex(h, 1, *v)
+            else:
+                m.mg3d_set_ml_shape(h, 1, *v)
         for _ in range(launches):
             m.mg3d_mali_sweep(h, 1, 1)
-        print("profile case: multi-level", prec_name, m.mg3d_get_ml_shape(h, 1),
+        print("profile case: multi-level", prec_name, m.mg3d_get_ml_shape_ex(h, 1),
               "chunk", m.mg3d_get_ml_chunk(h), flush=True)
     finally:
         m.mg3d_destroy(h)

@@ -468,6 +468,22 @@ int mg3d_set_ml_shape(mg3d_handle *h, int level, int bands, int rays_per_block, 
 int mg3d_get_ml_shape(const mg3d_handle *h, int level, int *bands, int *rays_per_block,
                       int *threads);
 
+/* Multi-level sweep shape with its kind: kind 0 as mg3d_set_ml_shape (any
+ * atmosphere; freq_per_block 1); kind 1 the shifted-plane form (static
+ * atmospheres with the linear upwind interpolation, Sec. 3 and Sec. 4.2):
+ * each ray's finished plane is stored shifted by the offset of the step that
+ * reads it, so every node finds its upwind corners at fixed offsets, and the
+ * opacity and source function of freq_per_block (1, 2 or 4; FP64: 1)
+ * frequencies ride along with the intensities; bands 1..16 (above 8 a
+ * non-portable cluster size), threads 32..512 covering the band in at most 4
+ * nodes per thread (2 with 4 frequencies per block).  MG3D_E_ARG for shapes
+ * that do not fit in shared memory or cannot be scheduled; the autotuner
+ * times both kinds.  No counterpart in the paper (launch control). */
+int mg3d_set_ml_shape_ex(mg3d_handle *h, int level, int bands, int rays_per_block, int threads,
+                         int kind, int freq_per_block);
+int mg3d_get_ml_shape_ex(const mg3d_handle *h, int level, int *bands, int *rays_per_block,
+                         int *threads, int *kind, int *freq_per_block);
+
 /* ------------------------------------------------------------------------
  * Batches: many independent atmospheres of uneven size (two-level and
  * multi-level atoms mixed) iterated in lockstep.  Every formal solution of
@@ -553,7 +569,10 @@ int mg3d_get_fs_occupancy(mg3d_handle *h, int level, int freq_per_block, int ban
 /* Autotuner: times candidate sweep shapes on this GPU with the level's current
  * populations and keeps the fastest per level (level = 0: every level).
  * Multi-level handles: every band count (1-8), 12/6/4/3/2 rays per block (1
- * where none of those fits) and 128/256/512 threads that fit, timed on the first 32 frequencies; the chunk
+ * where none of those fits) and 128/256/512 threads that fit, and for static
+ * atmospheres with the linear upwind interpolation the shifted-plane shapes
+ * (1, 2 or 4 frequencies per block, 1-16 bands, 12..1 rays per block), timed
+ * on the first 32 frequencies; the chunk
  * buffers are then resized for the chosen shapes (keeping a requested chunk
  * size).  Two-level handles taking the shifted-plane sweep: groupings of up
  * to 8 groups, 1-16 bands, 32-1024 threads in powers of two and the block

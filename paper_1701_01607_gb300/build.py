@@ -18,9 +18,9 @@ LIB = os.path.join(BUILD, "libmg3d.so")
 INCLUDE = os.path.join(ROOT, "include")
 SOURCES = ["fs_sweep.cu", "rates_transfer.cu", "mg3d_api.cu", "noalloc.cu", "ml.cu",
            "plane_sweep_f64.cu", "plane_sweep_f32.cu", "plane_async_f64.cu", "plane_async_f32.cu",
-           "probe.cu"]
+           "ml_plane.cu", "probe.cu"]
 HEADERS = [os.path.join(CSRC, h) for h in ("mg3d_internal.h", "sc_step.cuh", "profiles.h",
-                                            "voigt.cuh", "plane_sweep.cuh")] + [os.path.join(INCLUDE, "mg3d.h")]
+                                            "voigt.cuh", "plane_sweep.cuh", "ml_plane.cuh")] + [os.path.join(INCLUDE, "mg3d.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "-I", INCLUDE, "-I", CSRC]

@@ -103,6 +103,8 @@ struct Level {
     double *prd_oc = nullptr;    // and 1 - rho chi_t/chi in FP64 [n_prd_freq][nvox]
     int ml_bands = 0, ml_rows = 0, ml_threads = 0;
     int ml_rpb = 12;             // rays of a hemisphere per block of the multi-level sweep
+    int ml_plane = 0;            // 1: the shifted-plane form (ml_plane.cuh), ml_nf
+    int ml_nf = 1;               //    frequencies per block
 };
 
 struct TimedLaunch {
@@ -633,6 +635,29 @@ cudaEvent_t pool_event(mg3d_handle *h) {
 
 // Multi-level formal solution on level k: per-frequency angle sums per
 // hemisphere into ml_jx/ml_ux.
+// The multi-level shifted-plane sweep of level L over the chunk's nc
+// frequencies (opacity already formed; ib: the chunk's bottom intensities).
+cudaError_t launch_ml_level_plane(const mg3d_handle *h, const Level &L, int nc, const void *ib,
+                                  int bands, int rpb, int nf, int threads) {
+    const int rows = (L.ny + bands - 1) / bands;
+    if (h->prec == MG3D_PREC_F64) {
+        MlPlaneArgs<double> a{L.nx, L.ny, L.nz, nc, rows, bands, rpb, band_magic(rows),
+                              band_magic(L.nx), (const double *)L.mchi, (const double *)L.mS,
+                              (const double *)L.msc, (const double *)L.moc, (const double *)ib,
+                              (const PlaneStep<double> *)L.psteps, (double *)h->ml_jx,
+                              (double *)h->ml_ux, (double *)h->ml_jm, h->d_exp_tab, h->exp_l1,
+                              h->exp_l2};
+        return launch_ml_plane_f64(a, nf, threads, h->stream);
+    }
+    MlPlaneArgs<float> a{L.nx, L.ny, L.nz, nc, rows, bands, rpb, band_magic(rows),
+                         band_magic(L.nx), (const float *)L.mchi, (const float *)L.mS,
+                         (const float *)L.msc, (const float *)L.moc, (const float *)ib,
+                         (const PlaneStep<float> *)L.psteps, (float *)h->ml_jx,
+                         (float *)h->ml_ux, (float *)h->ml_jm, h->d_exp_tab, h->exp_l1,
+                         h->exp_l2};
+    return launch_ml_plane_f32(a, nf, threads, h->stream);
+}
+
 // Opacity and sweep of the chunk of frequencies f0 .. f0+nc-1 on level k:
 // per-frequency angle sums of both hemispheres into ml_jx/ml_ux.
 int ml_chunk_fs(mg3d_handle *h, int k, int f0, int nc) {
@@ -657,7 +682,9 @@ int ml_chunk_fs(mg3d_handle *h, int k, int f0, int nc) {
     const size_t es = elem_size(h->prec);
     const void *ib = static_cast<const unsigned char *>(L.mib) + (size_t)f0 * L.nplane * es;
     cudaError_t e;
-    if (h->prec == MG3D_PREC_F64) {
+    if (L.ml_plane) {
+        e = launch_ml_level_plane(h, L, nc, ib, L.ml_bands, L.ml_rpb, L.ml_nf, L.ml_threads);
+    } else if (h->prec == MG3D_PREC_F64) {
         MlSweepArgs<double> a{L.nx, L.ny, L.nz, nc, L.ml_rows,
                               (const double *)L.mchi, (const double *)L.mS,
                               (const double *)L.msc, (const double *)L.moc,
@@ -1875,8 +1902,46 @@ int alloc_ml_chunks(mg3d_handle *h, int chunk) {
 // nc frequencies with shape (bands, rpb, threads); the opacity of those
 // frequencies must be in place and the angle-sum buffers hold 2 x 12 / rpb
 // slots.
+// Checks a shifted-plane shape of the multi-level sweep on level k.
+int ml_plane_shape_check(const mg3d_handle *h, int k, int bands, int rpb, int threads, int nf) {
+    const Level &L = h->lev[k];
+    if (h->moving || h->params.sc_interp || !L.psteps)
+        return fail(MG3D_E_ARG, "the shifted-plane multi-level sweep takes static atmospheres "
+                                "and the linear upwind interpolation");
+    if (!plane_grid_ok(L.nx, L.ny, L.nz))
+        return fail(MG3D_E_ARG, "grid too large for the shifted-plane multi-level sweep");
+    if (bands < 1 || bands > kMaxBands || bands > L.ny)
+        return fail(MG3D_E_ARG, "bands must be 1..16 and at most ny");
+    const int rows = (L.ny + bands - 1) / bands;
+    if ((long)(bands - 1) * rows >= L.ny) return fail(MG3D_E_ARG, "empty band");
+    if (rpb < 1 || 12 % rpb) return fail(MG3D_E_ARG, "rays_per_block must divide 12");
+    if (threads < 32 || threads > 512 || threads % 32)
+        return fail(MG3D_E_ARG, "threads must be a multiple of 32 up to 512");
+    if (nf != 1 && nf != 2 && nf != 4)
+        return fail(MG3D_E_ARG, "freq_per_block must be 1, 2 or 4");
+    if (nf > 1 && h->prec == MG3D_PREC_F64)
+        return fail(MG3D_E_ARG, "the FP64 shifted-plane multi-level sweep takes one frequency "
+                                "per block");
+    if ((long)rows * L.nx > (long)ml_plane_max_pass(nf) * threads)
+        return fail(MG3D_E_ARG, "too few threads for the band (at most " +
+                                    std::to_string(ml_plane_max_pass(nf)) + " nodes per thread)");
+    if (ml_plane_smem_bytes(h->prec, nf, rows, L.nx, rpb) > kMlPlaneMaxSmem)
+        return fail(MG3D_E_ARG, "multi-level sweep shape exceeds shared memory");
+    int n = 0;
+    const cudaError_t e = ml_plane_active_clusters(h->prec, nf, bands, rows, L.nx, rpb,
+                                                   std::min(h->ml_chunk, h->nfreq_ml), threads,
+                                                   &n);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MG3D_E_ARG, std::string("multi-level sweep shape cannot be scheduled: ") +
+                                    cudaGetErrorString(e));
+    }
+    if (n < 1) return fail(MG3D_E_ARG, "multi-level sweep shape cannot be scheduled");
+    return MG3D_OK;
+}
+
 int time_ml_shape(mg3d_handle *h, int k, int bands, int rpb, int threads, int nc, int reps,
-                  float *ms) {
+                  float *ms, int plane = 0, int nf = 1) {
     Level &L = h->lev[k];
     const int sb = L.ml_bands, sr = L.ml_rows, sp = L.ml_rpb, sth = L.ml_threads;
     L.ml_bands = bands;
@@ -1887,7 +1952,9 @@ int time_ml_shape(mg3d_handle *h, int k, int bands, int rpb, int threads, int nc
     int rc = MG3D_OK;
     cudaError_t e = cudaEventRecord(a, h->stream);
     for (int i = 0; i < reps && e == cudaSuccess; ++i) {
-        if (h->prec == MG3D_PREC_F64) {
+        if (plane) {
+            e = launch_ml_level_plane(h, L, nc, L.mib, bands, rpb, nf, threads);
+        } else if (h->prec == MG3D_PREC_F64) {
             MlSweepArgs<double> sa{L.nx, L.ny, L.nz, nc, L.ml_rows,
                                    (const double *)L.mchi, (const double *)L.mS,
                                    (const double *)L.msc, (const double *)L.moc,
@@ -1962,7 +2029,7 @@ int autotune_ml_level(mg3d_handle *h, int k, int nc, int *evaluated) {
                                           L.mdS, h->stream),
                         "x-slopes"));
     struct Cand {
-        int bands, rpb, threads;
+        int bands, rpb, threads, plane = 0, nf = 1;
     };
     std::vector<Cand> cands;
     // rays per block 1 only where no larger group fits (a 256-wide FP64 plane)
@@ -1979,13 +2046,36 @@ int autotune_ml_level(mg3d_handle *h, int k, int nc, int *evaluated) {
                 cands.push_back(Cand{bands, rpb, th});
             }
         }
+    // shifted-plane shapes (static atmospheres, linear upwind interpolation)
+    // whose ray-group slots the tuning buffers hold
+    if (!h->moving && !h->params.sc_interp && L.psteps)
+        for (int nf : {1, 2, 4})
+            for (int rpb : {12, 6, 4, 3, 2, 1}) {
+                if (2 * (12 / rpb) > h->ml_slots) continue;
+                for (int bands = 1; bands <= kMaxBands && bands <= L.ny; ++bands) {
+                    const int rows = (L.ny + bands - 1) / bands;
+                    if ((long)(bands - 1) * rows >= L.ny) continue;
+                    for (int th : {128, 256, 512}) {
+                        if (th > 128 && th / 2 >= rows * L.nx) continue;
+                        if (ml_plane_shape_check(h, k, bands, rpb, th, nf) != MG3D_OK) continue;
+                        Cand c{bands, rpb, th};
+                        c.plane = 1;
+                        c.nf = nf;
+                        cands.push_back(c);
+                    }
+                }
+            }
+    g_last_error.clear();
     if (cands.empty()) return fail(MG3D_E_ARG, "no multi-level sweep shape fits");
     float warm = 0.f;
-    MG_TRY(time_ml_shape(h, k, L.ml_bands, L.ml_rpb, L.ml_threads, nc, 1, &warm));
+    if (2 * (12 / L.ml_rpb) <= h->ml_slots)
+        MG_TRY(time_ml_shape(h, k, L.ml_bands, L.ml_rpb, L.ml_threads, nc, 1, &warm, L.ml_plane,
+                             L.ml_nf));
     std::vector<std::pair<float, size_t>> t1;
     for (size_t i = 0; i < cands.size(); ++i) {
         float ms = 0.f;
-        MG_TRY(time_ml_shape(h, k, cands[i].bands, cands[i].rpb, cands[i].threads, nc, 1, &ms));
+        MG_TRY(time_ml_shape(h, k, cands[i].bands, cands[i].rpb, cands[i].threads, nc, 1, &ms,
+                             cands[i].plane, cands[i].nf));
         t1.push_back({ms, i});
     }
     std::sort(t1.begin(), t1.end());
@@ -1994,7 +2084,7 @@ int autotune_ml_level(mg3d_handle *h, int k, int nc, int *evaluated) {
     for (size_t j = 0; j < std::min<size_t>(6, t1.size()); ++j) {
         const Cand &c = cands[t1[j].second];
         float ms = 0.f;
-        MG_TRY(time_ml_shape(h, k, c.bands, c.rpb, c.threads, nc, 3, &ms));
+        MG_TRY(time_ml_shape(h, k, c.bands, c.rpb, c.threads, nc, 3, &ms, c.plane, c.nf));
         if (ms < best_ms) {
             best_ms = ms;
             best = t1[j].second;
@@ -2004,6 +2094,8 @@ int autotune_ml_level(mg3d_handle *h, int k, int nc, int *evaluated) {
     L.ml_rows = (L.ny + L.ml_bands - 1) / L.ml_bands;
     L.ml_rpb = cands[best].rpb;
     L.ml_threads = cands[best].threads;
+    L.ml_plane = cands[best].plane;
+    L.ml_nf = cands[best].nf;
     if (evaluated) *evaluated = (int)cands.size();
     return MG3D_OK;
 }
@@ -2015,10 +2107,14 @@ int autotune_ml(mg3d_handle *h, int level, int *evaluated) {
     MG_CUDA(cudaStreamSynchronize(h->stream));
     drop_graphs(h);
     // tuning buffers: the slots of the candidates (12 for two rays per block,
-    // 24 where a level fits only one), at most 32 frequencies that fit
+    // 24 where a level fits only one, or where the shifted-plane form applies:
+    // wide planes take it with one ray per block), at most 32 frequencies
+    // that fit
     h->ml_slots = 12;
     for (int k = 1; k <= h->L; ++k)
-        if ((level == 0 || k == level) && ml_single_ray_only(h, k)) h->ml_slots = 24;
+        if ((level == 0 || k == level) &&
+            (ml_single_ray_only(h, k) || (!h->moving && !h->params.sc_interp && h->lev[k].psteps)))
+            h->ml_slots = 24;
     MG_TRY(alloc_ml_chunks(h, 1));
     const int nc = std::min(32, default_ml_chunk(h));
     MG_TRY(alloc_ml_chunks(h, nc));
@@ -2255,6 +2351,20 @@ int create_ml_impl(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
         std::vector<StepGeom> g;
         build_geometry(h, L, g);
         MG_CUDA(cudaMemcpy(L.geom, g.data(), g.size() * sizeof(StepGeom), cudaMemcpyHostToDevice));
+        // per-step constants of the shifted-plane form (static, linear upwind)
+        if (!atm->vel && !params->sc_interp) {
+            if (h->prec == MG3D_PREC_F64) {
+                const auto ps = plane_steps<double>(L, g);
+                MG_TRY(dev_alloc(&L.psteps, ps.size() * sizeof(ps[0])));
+                MG_CUDA(cudaMemcpy(L.psteps, ps.data(), ps.size() * sizeof(ps[0]),
+                                   cudaMemcpyHostToDevice));
+            } else {
+                const auto ps = plane_steps<float>(L, g);
+                MG_TRY(dev_alloc(&L.psteps, ps.size() * sizeof(ps[0])));
+                MG_CUDA(cudaMemcpy(L.psteps, ps.data(), ps.size() * sizeof(ps[0]),
+                                   cudaMemcpyHostToDevice));
+            }
+        }
         // rays per block: all 12 of a hemisphere if some band count fits in
         // shared memory, else the largest divisor of 12 that does; bands: the
         // fewest that fit and give >= 300 blocks, else the most that fit
@@ -3057,12 +3167,52 @@ int mg3d_set_ml_shape(mg3d_handle *h, int level, int bands, int rays_per_block, 
     L.ml_rows = rows;
     L.ml_rpb = rays_per_block;
     L.ml_threads = threads;
+    L.ml_plane = 0;
+    L.ml_nf = 1;
     drop_graphs(h);
     const int slots = 2 * (12 / rays_per_block);
     if (slots > h->ml_slots) {
         h->ml_slots = slots;
         MG_TRY(alloc_ml_chunks(h, h->ml_chunk));
     }
+    return MG3D_OK;
+}
+
+int mg3d_set_ml_shape_ex(mg3d_handle *h, int level, int bands, int rays_per_block, int threads,
+                         int kind, int freq_per_block) {
+    MG_TRY(check_level(h, level));
+    if (h->kind != 1) return fail(MG3D_E_STATE, "not a multi-level handle");
+    if (kind == 0) {
+        if (freq_per_block != 1) return fail(MG3D_E_ARG, "kind 0 takes freq_per_block 1");
+        MG_TRY(mg3d_set_ml_shape(h, level, bands, rays_per_block, threads));
+        h->lev[level].ml_plane = 0;
+        h->lev[level].ml_nf = 1;
+        return MG3D_OK;
+    }
+    if (kind != 1) return fail(MG3D_E_ARG, "kind must be 0 or 1");
+    MG_TRY(ml_plane_shape_check(h, level, bands, rays_per_block, threads, freq_per_block));
+    Level &L = h->lev[level];
+    MG_CUDA(cudaStreamSynchronize(h->stream));
+    L.ml_bands = bands;
+    L.ml_rows = (L.ny + bands - 1) / bands;
+    L.ml_rpb = rays_per_block;
+    L.ml_threads = threads;
+    L.ml_plane = 1;
+    L.ml_nf = freq_per_block;
+    drop_graphs(h);
+    const int slots = 2 * (12 / rays_per_block);
+    if (slots > h->ml_slots) {
+        h->ml_slots = slots;
+        MG_TRY(alloc_ml_chunks(h, h->ml_chunk));
+    }
+    return MG3D_OK;
+}
+
+int mg3d_get_ml_shape_ex(const mg3d_handle *h, int level, int *bands, int *rays_per_block,
+                         int *threads, int *kind, int *freq_per_block) {
+    MG_TRY(mg3d_get_ml_shape(h, level, bands, rays_per_block, threads));
+    if (kind) *kind = h->lev[level].ml_plane;
+    if (freq_per_block) *freq_per_block = h->lev[level].ml_nf;
     return MG3D_OK;
 }
 

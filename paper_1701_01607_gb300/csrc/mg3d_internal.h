@@ -294,6 +294,37 @@ struct MlSweepArgs {
     const T *vnorm, *uproj, *dinv;
 };
 
+// Arguments of the multi-level shifted-plane sweep (ml_plane.cuh), one chunk
+// of nfreq frequencies.
+template <typename T>
+struct MlPlaneArgs {
+    int nx, ny, nz, nfreq, rows, bands, rpb;
+    unsigned long long rmagic, xmagic;   // band_magic(rows), band_magic(nx)
+    const T *chi, *S, *sc, *oc;          // [nfreq][nvox]
+    const T *ib;                         // [nfreq][nx*ny] intensity entering at the bottom
+    const PlaneStep<T> *steps;           // [kRays][nz]
+    T *jx, *ux, *jm;                     // [2 * 12 / rpb slots][nfreq][nvox]; jm nullable
+    const double *exp_tab;
+    double exp_l1, exp_l2;
+};
+
+// Frequencies per block the multi-level shifted-plane sweep is built for,
+// and the nodes a thread takes per step (band <= this x threads).
+constexpr int kMlPlaneNf[] = {1, 2, 4};
+// dynamic shared memory limit of the multi-level shifted-plane sweep: its
+// static part (the FP64 exp table and the rays' step constants, 3.2 KB) and
+// this stay within the 227 KB a block may take
+constexpr size_t kMlPlaneMaxSmem = 220 * 1024;
+constexpr int kMlPlaneNfCount = 3;
+__host__ __device__ constexpr int ml_plane_max_pass(int nf) { return nf <= 2 ? 4 : 2; }
+size_t ml_plane_smem_bytes(int prec, int nf, int rows, int nx, int rpb);
+cudaError_t launch_ml_plane_f64(const MlPlaneArgs<double> &a, int nf_block, int threads,
+                                cudaStream_t st);
+cudaError_t launch_ml_plane_f32(const MlPlaneArgs<float> &a, int nf_block, int threads,
+                                cudaStream_t st);
+cudaError_t ml_plane_active_clusters(int prec, int nf_block, int bands, int rows, int nx,
+                                     int rpb, int nfreq, int threads, int *n);
+
 // Partial redistribution of one line of a multi-level atom: its frequencies
 // [f_begin, f_end) of the frequency table, their positions pf0 .. pf0+nf-1
 // among all PRD line frequencies (the rows of the scaling and rho arrays),

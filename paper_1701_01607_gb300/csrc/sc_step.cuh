@@ -101,9 +101,11 @@ struct ScWeights<double> {
         wup = u - ex;
     }
     static __device__ __forceinline__ bool small(double x) { return x < 1e-3; }
+    // coefficients as products with rounded reciprocals (a division would
+    // expand to an iteration with a slow-path branch per evaluation)
     static __device__ __forceinline__ void series(double x, double &w0, double &wup, double &u) {
-        w0 = x * (0.5 - x * (1.0 / 6.0 - x * (1.0 / 24.0 - x * (1.0 / 120.0 - x / 720.0))));
-        wup = x * (0.5 - x * (1.0 / 3.0 - x * (1.0 / 8.0 - x * (1.0 / 30.0 - x / 144.0))));
+        w0 = x * (0.5 - x * (1.0 / 6.0 - x * (1.0 / 24.0 - x * (1.0 / 120.0 - x * (1.0 / 720.0)))));
+        wup = x * (0.5 - x * (1.0 / 3.0 - x * (1.0 / 8.0 - x * (1.0 / 30.0 - x * (1.0 / 144.0)))));
         u = 1.0 - w0;
     }
     // one of the two forms per lane (the closed form's three operations are
@@ -132,8 +134,8 @@ struct ScWeights<float> {
     }
     static __device__ __forceinline__ bool small(float x) { return x < 0.1f; }
     static __device__ __forceinline__ void series(float x, float &w0, float &wup, float &u) {
-        w0 = x * (0.5f - x * (1.0f / 6.0f - x * (1.0f / 24.0f - x * (1.0f / 120.0f - x / 720.0f))));
-        wup = x * (0.5f - x * (1.0f / 3.0f - x * (1.0f / 8.0f - x * (1.0f / 30.0f - x / 144.0f))));
+        w0 = x * (0.5f - x * (1.0f / 6.0f - x * (1.0f / 24.0f - x * (1.0f / 120.0f - x * (1.0f / 720.0f)))));
+        wup = x * (0.5f - x * (1.0f / 3.0f - x * (1.0f / 8.0f - x * (1.0f / 30.0f - x * (1.0f / 144.0f)))));
         u = 1.0f - w0;
     }
     static __device__ __forceinline__ void eval(float x, float inv_x, const ExpNegTable et,

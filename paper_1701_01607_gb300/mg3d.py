@@ -147,6 +147,9 @@ _SIGNATURES = {
     "mg3d_set_ml_chunk": (_I, [_H, _I]),
     "mg3d_get_ml_chunk": (_I, [_H, ctypes.POINTER(_I)]),
     "mg3d_set_ml_shape": (_I, [_H, _I, _I, _I, _I]),
+    "mg3d_set_ml_shape_ex": (_I, [_H, _I, _I, _I, _I, _I, _I]),
+    "mg3d_get_ml_shape_ex": (_I, [_H, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                 ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "mg3d_get_ml_shape": (_I, [_H, _I, ctypes.POINTER(_I), ctypes.POINTER(_I),
                                ctypes.POINTER(_I)]),
     "mg3d_get_fs_occupancy": (_I, [_H, _I, _I, _I, _I, _I, _I, ctypes.POINTER(_I),
@@ -481,6 +484,19 @@ def mg3d_get_ml_shape(h, level: int):
     v = [_I() for _ in range(3)]
     _check(load().mg3d_get_ml_shape(h, level, *[ctypes.byref(x) for x in v]))
     return tuple(x.value for x in v)
+
+
+def mg3d_set_ml_shape_ex(h, level: int, bands: int, rays_per_block: int, threads: int,
+                         kind: int, freq_per_block: int = 1):
+    return _check(load().mg3d_set_ml_shape_ex(h, level, bands, rays_per_block, threads, kind,
+                                              freq_per_block))
+
+
+def mg3d_get_ml_shape_ex(h, level: int):
+    b, r, t, k, f = _I(), _I(), _I(), _I(), _I()
+    _check(load().mg3d_get_ml_shape_ex(h, level, ctypes.byref(b), ctypes.byref(r),
+                                       ctypes.byref(t), ctypes.byref(k), ctypes.byref(f)))
+    return b.value, r.value, t.value, k.value, f.value
 
 
 def mg3d_get_fs_occupancy(h, level: int, freq_per_block: int, bands: int, threads: int = 256,

@@ -324,7 +324,7 @@ def test_ml_autotuned_shapes_keep_parity():
         assert info["evaluated"] > 10
         for k in (1, 2):
             bands, rpb, threads = m.mg3d_get_ml_shape(h, k)
-            assert 12 % rpb == 0 and 1 <= bands <= 8
+            assert 12 % rpb == 0 and 1 <= bands <= 16
         _, nf = m.mg3d_n_levels(h)
         assert m.mg3d_get_ml_chunk(h) == nf
         for _ in range(3):
