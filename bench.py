@@ -60,10 +60,11 @@ FP64_NOMINAL_TFLOPS = 1.25      # GB300, at the 2070 MHz maximum SM clock
 # rcp on the multi-function unit.
 ALG_FP32_OPS_PER_UNIT = 4 + 2 + 1 + 7 * N_DISTINCT_PHI / 9.0 + 10.0 / 9.0
 MUFU_EX2_PER_UNIT = MUFU_RCP_PER_UNIT = N_DISTINCT_PHI / 9.0
-# DRAM bytes (read + write) of one finest-grid FP64 sweep launch, from one ncu
-# capture of the current kernel at this launch shape (ng, bands, threads,
-# lean, stage); reported only when the autotuner picks the same shape
-FINE_SWEEP_TRAFFIC = {"shape": [9, 5, 224, 0, 2], "bytes": 14019072 + 142003968}
+# DRAM bytes (read + write) of one finest-grid FP64 sweep launch on the bench
+# atmosphere per launch shape (ng, bands, threads, lean, stage), from ncu
+# captures of the current kernel; a shape the autotuner picks that is not
+# listed reports traffic null
+FINE_SWEEP_TRAFFIC = {(9, 5, 224, 0, 2): 14019072 + 142003968}
 SM_MAX_MHZ = 2070.0
 
 
@@ -264,8 +265,7 @@ def run_gpu(args):
         peak = 2.0 * peaks["dfma"] / 1e12       # measured FP64 TFLOP/s
         achieved = ALG_FLOPS_PER_UNIT * fine_units / (fine_ms * 1e-3) / 1e12
         fine_shape = list(tuning.get("f64", {}).get("shapes", {}).get(fine, ()))
-        traffic = (FINE_SWEEP_TRAFFIC["bytes"]
-                   if fine_shape == FINE_SWEEP_TRAFFIC["shape"] else None)
+        traffic = FINE_SWEEP_TRAFFIC.get(tuple(fine_shape))
         result = {
             "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
