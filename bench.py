@@ -64,7 +64,10 @@ MUFU_EX2_PER_UNIT = MUFU_RCP_PER_UNIT = N_DISTINCT_PHI / 9.0
 # atmosphere per launch shape (ng, bands, threads, lean, stage), from ncu
 # captures of the current kernel; a shape the autotuner picks that is not
 # listed reports traffic null
-FINE_SWEEP_TRAFFIC = {(9, 5, 224, 0, 2): 14019072 + 142003968}
+FINE_SWEEP_TRAFFIC = {(9, 5, 224, 0, 2): 14835968 + 141922048,
+                      (9, 5, 256, 0, 2): 14634752 + 141857536,
+                      (9, 5, 448, 0, 2): 13970944 + 144993536,
+                      (9, 5, 512, 0, 2): 13957888 + 143129856}
 SM_MAX_MHZ = 2070.0
 
 
