@@ -151,7 +151,7 @@ __device__ __forceinline__ void hermite_step(
         const T chi_loc = a.chi0[pk + x];
         const T S_loc = a.S[pk + x];
         const T dtau0 = (chi_up + chi_loc) * half_s;
-        const T inv_dtau0 = rcp(dtau0);
+        const T inv_dtau0 = sc_rcp(dtau0);
         // the four upwind rows of the intensity and slope planes
         const T *P[4], *D[4];
 #pragma unroll
@@ -252,7 +252,7 @@ __device__ __forceinline__ void moving_step(
                            w11 * Pb[off + xb];
             const T dtau = (chi_up + chi_loc) * half_s;
             T ex, w0, wup, uu;
-            ScWeights<T>::eval(dtau, rcp(dtau), et, ex, w0, wup, uu);
+            ScWeights<T>::eval(dtau, sc_rcp(dtau), et, ex, w0, wup, uu);
             const T part = I_up * ex + wup * S_up;
             const long i = off + (long)yl * nx + x;
             cur[i] = part + w0 * S_loc;
@@ -304,7 +304,7 @@ __device__ __forceinline__ void prd_step(
         const T chi_up = w00 * ca[xa] + w10 * ca[xb] + w01 * cb[xa] + w11 * cb[xb];
         const long v = (long)k * nplane + (long)y * nx + x;
         const T dtau0 = (chi_up + a.chi0[v]) * half_s;
-        const T inv_dtau0 = rcp(dtau0);
+        const T inv_dtau0 = sc_rcp(dtau0);
         const int ba = band_of(ya, rmagic), bb = band_of(yb, rmagic);
         const T *Pa = (ba == rank ? prev : cluster.map_shared_rank(prev, ba)) +
                       (long)(ya - ba * rows) * nx;
@@ -542,7 +542,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T> &a, int g, int r) 
                 const T dtau0 = (chi_up + chi_loc) * half_s;
                 // 1/dtau0 is only used where dtau0 phi >= the series threshold,
                 // so dtau0 > 0 there
-                const T inv_dtau0 = rcp(dtau0);
+                const T inv_dtau0 = sc_rcp(dtau0);
                 // upwind rows of the intensity planes: local or in a peer block
                 const int ba = band_of(ya, rmagic), bb = band_of(yb, rmagic);
                 const T *Pa = (ba == rank) ? prev : cluster.map_shared_rank(prev, ba);

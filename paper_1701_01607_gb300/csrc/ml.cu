@@ -607,7 +607,7 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
                         moving_terms(v, j, chi, S, sc_r, oc_r, wr);
                         const T x_tau = (chi_up + chi) * g_hs[j];
                         T ex, w0, wup, u;
-                        ScWeights<T>::eval(x_tau, rcp(x_tau), et, ex, w0, wup, u);
+                        ScWeights<T>::eval(x_tau, sc_rcp(x_tau), et, ex, w0, wup, u);
                         const T part = I_up * ex + wup * S_up;   // I - w0 S
                         const T I = part + w0 * S;
                         const long i = j * raystride + (long)yl * nx + x;
@@ -651,7 +651,7 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
                                             [&](int m) { return r4.d[m]; });
                         const T x_tau = (chi_up + chi_loc) * g_hs[j];
                         T ex, w0, wup, u;
-                        ScWeights<T>::eval(x_tau, rcp(x_tau), et, ex, w0, wup, u);
+                        ScWeights<T>::eval(x_tau, sc_rcp(x_tau), et, ex, w0, wup, u);
                         const T part = I_up * ex + wup * S_up;   // I - w0 S
                         const T I = part + w0 * S_loc;
                         cur[j * raystride + (long)yl * nx + x] = I;
@@ -675,7 +675,7 @@ __device__ __forceinline__ void ml_sweep_body(const MlSweepArgs<T> &a, int f, in
                     const T I_up = w00 * Pa[xa] + w10 * Pa[xb] + w01 * Pb[xa] + w11 * Pb[xb];
                     const T x_tau = (chi_up + chi_loc) * g_hs[j];
                     T ex, w0, wup, u;
-                    ScWeights<T>::eval(x_tau, rcp(x_tau), et, ex, w0, wup, u);
+                    ScWeights<T>::eval(x_tau, sc_rcp(x_tau), et, ex, w0, wup, u);
                     const T part = I_up * ex + wup * S_up;   // I - w0 S
                     const T I = part + w0 * S_loc;
                     cur[j * raystride + (long)yl * nx + x] = I;

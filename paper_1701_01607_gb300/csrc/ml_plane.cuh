@@ -228,7 +228,7 @@ __device__ __forceinline__ void ml_plane_body(const MlPlaneArgs<T> &a) {
                     const T I_up = ch[3 * k], chi_up = ch[3 * k + 1], S_up = ch[3 * k + 2];
                     const T x = (chi_up + cchi[i][k]) * st.half_s;
                     T ex, w0, wup, u;
-                    ScWeights<T>::eval(x, rcp(x), et, ex, w0, wup, u);
+                    ScWeights<T>::eval(x, sc_rcp(x), et, ex, w0, wup, u);
                     const T part = I_up * ex + wup * S_up;   // I - w0 S
                     const T I = part + w0 * cS[i][k];
                     sp[k] += part;

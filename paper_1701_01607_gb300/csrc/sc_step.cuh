@@ -30,6 +30,20 @@ __device__ __forceinline__ int band_of(int ya, unsigned long long magic) {
 // hardware approximation (within 2 ulp), ample for the FP32 formal solution.
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+// 1/x of an optical path for the closed-form weights, which use it only where
+// x is above the series threshold (far from 0 and from overflow).  FP64: the
+// hardware approximation (about 23 correct bits) refined by two Newton-Raphson
+// steps r <- r + r (1 - x r), each of which doubles the correct bits, in place
+// of an IEEE division with its range checks.
+__device__ __forceinline__ float sc_rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double sc_rcp(double x) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+}
 
 // e^{-x} for x >= 0 by the table-driven method of Tang (ACM TOMS 15, 1989):
 // -x = (256 m + j) ln2/256 + r with integer m, j in [0, 256) and
