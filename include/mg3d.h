@@ -438,7 +438,9 @@ int mg3d_n_levels(const mg3d_handle *h, int *n_levels, int *n_freq);
 
 /* One multi-level formal solution: per frequency and node the angle sums
  * Jx = sum_r w_r (I - w0 S_t) and Ux = sum_r w_r (1 - w0 chi_t/chi), with S_t
- * the transition's part of the source function; host outputs
+ * the transition's part of the source function (for a partial-redistribution
+ * line S_t = rho eta_t/chi and Ux = sum_r w_r (1 - w0 rho chi_t/chi), with
+ * rho from the grid's lagged mean intensity); host outputs
  * [n_freq][nz][ny][nx] (nullable).  MG3D_E_STATE on a two-level handle.
  * The formal solution of Sec. 3 at every frequency of every transition. */
 int mg3d_formal_solve_ml(mg3d_handle *h, int level, double *jx_host, double *ux_host);

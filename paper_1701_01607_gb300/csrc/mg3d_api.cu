@@ -143,6 +143,7 @@ struct mg3d_handle {
     int n_prd = 0, n_prd_freq = 0;
     PrdLine *d_prd = nullptr;
     int *d_prd_ord = nullptr, *d_prd_grp = nullptr, *d_prd_index = nullptr;
+    std::vector<int> prd_index;  // host copy of d_prd_index
     int fmg_next = 1;            // the FMG stage mg3d_fmg_stage may run next (1 restarts)
     int top = 0;                 // grid being solved (0: the finest); only its formal
                                  // solutions update its background field
@@ -2251,6 +2252,7 @@ int setup_ml_prd(mg3d_handle *h, const mg3d_ml_atom *atom) {
     MG_CUDA(cudaMemcpy(h->d_prd_grp, grp.data(), grp.size() * sizeof(int), cudaMemcpyHostToDevice));
     MG_CUDA(cudaMemcpy(h->d_prd_index, index.data(), index.size() * sizeof(int),
                        cudaMemcpyHostToDevice));
+    h->prd_index = index;
     std::vector<double> ones;
     for (int k = 1; k <= h->L; ++k) {
         Level &L = h->lev[k];
@@ -3095,6 +3097,14 @@ int mg3d_formal_solve_ml(mg3d_handle *h, int level, double *jx_host, double *ux_
     const size_t nv = (size_t)L.nvox;
     std::vector<unsigned char> hj, hu;
     MG_TRY(ml_prd_prepare(h, level));
+    // a PRD frequency's sweep sums u alone; its U adds the local term in FP64
+    // (1 - rho chi_t/chi of the ratios kernel), as the radiative sums do
+    std::vector<double> prd_oc;
+    if (h->ml_prd) {
+        prd_oc.resize((size_t)h->n_prd_freq * nv);
+        MG_CUDA(cudaMemcpyAsync(prd_oc.data(), L.prd_oc, prd_oc.size() * sizeof(double),
+                                cudaMemcpyDeviceToHost, h->stream));
+    }
     for (int f0 = 0; f0 < h->nfreq_ml; f0 += h->ml_chunk) {
         const int nc = std::min(h->ml_chunk, h->nfreq_ml - f0);
         MG_TRY(ml_chunk_fs(h, level, f0, nc));
@@ -3124,6 +3134,13 @@ int mg3d_formal_solve_ml(mg3d_handle *h, int level, double *jx_host, double *ux_
                 U += at(hu, sl * cnt + i);
             }
             const size_t o = (size_t)f0 * nv + i;
+            if (h->ml_prd) {
+                const int pr = h->prd_index[f0 + i / nv];
+                if (pr >= 0) {
+                    const double oc = prd_oc[(size_t)pr * nv + i % nv];
+                    U = oc + (1.0 - oc) * U;
+                }
+            }
             if (jx_host) jx_host[o] = J;
             if (ux_host) ux_host[o] = U;
         }

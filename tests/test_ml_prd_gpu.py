@@ -166,3 +166,28 @@ def test_ml_prd_batches_refused():
         assert ei.value.code == m.MG3D_E_ARG and "partial redistribution" in m.mg3d_last_error()
     finally:
         m.mg3d_destroy(h)
+
+
+def test_ml_prd_formal_solution_angle_sums():
+    """mg3d_formal_solve_ml returns the angle sums the rates use: for a PRD
+    frequency Ux = sum_r w (1 - w0 rho chi_t/chi), whose local term the
+    library adds in FP64 to the sweep's sum of u.  After two MALI sweeps on
+    both sides (the same lagged field), every frequency's Jx and Ux against
+    the oracle on its own scale."""
+    atm, atom = prd_box(1.0)
+    p = O.MultiLevelProblem(atm, atom)
+    n = p.zero_radiation(1)
+    h = m.mg3d_create_ml(atm, atom, n_grids=1)
+    try:
+        for _ in range(2):
+            m.mg3d_mali_sweep(h, 1, 1)
+            n, _ = p.mali_sweep(1, n)
+        jx, ux = m.mg3d_formal_solve_ml(h, 1)
+    finally:
+        m.mg3d_destroy(h)
+    Jo, Uo, _ = p.formal_solution(1, n)
+    nf = Jo.shape[0]
+    for got, ref in ((jx, Jo), (ux, Uo)):
+        g2, r2 = got.reshape(nf, -1), ref.reshape(nf, -1)
+        err = np.max(np.abs(g2 - r2), axis=1) / np.max(np.abs(r2), axis=1)
+        assert float(np.max(err)) < 1e-10
