@@ -369,7 +369,9 @@ struct MlOpacityArgs {
     const FreqInfo *fi;
     double theta_ref, t_ref;
     const double *n, *T, *chi_c, *saha;
-    void *chi, *S, *sc, *oc;       // sc = S - rho eta_t/chi, oc = 1 - rho chi_t/chi
+    void *chi, *S, *sc, *oc;       // sc = S - rho eta_t/chi, oc = 1 - chi_t/chi (0 for a
+                                   // PRD frequency: its 1 - rho chi_t/chi goes in FP64
+                                   // to the radiative sums, MlAccumArgs::prd_oc)
     int f0;
     const double *exp_tab;         // FP64 exp table of the sweep
     double exp_l1, exp_l2;
