@@ -226,7 +226,7 @@ TWO_LEVEL_PARAMS = dict(nu_fmg=16, nu0=0, nu1=2, nu2=2, nu3=32)
 
 @pytest.mark.parametrize("method", ["fas", "fmg"])
 def test_two_level_fp32_solve_against_fp64_oracle(method):
-    """The benchmark spec's mixed-precision bar: a two-grid FAS (or FMG) solve to
+    """The mixed-precision bar on converged populations: a two-grid FAS (or FMG) solve to
     C < 1e-3 with the FP32 formal solution and FP64 rates matches the FP64
     oracle's solve of the same schedule to 1e-4 relative on the populations,
     with the same number of V-cycles (16x16x33 box, eps = 1e-4, log-normal
