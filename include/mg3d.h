@@ -347,9 +347,16 @@ typedef struct {
     double kappa;       /* opacity coefficient at unit profile */
     int n_freq;
     double x_max;
-    double a_damp;      /* Voigt damping parameter at t_ref; must be 0 (Doppler
-                           profiles): damped lines of multi-level atoms are
-                           refused with MG3D_E_ARG */
+    double a_damp;      /* Voigt damping parameter at t_ref in [0, 1000) (0:
+                           Doppler profile).  The damping width does not scale
+                           with temperature while the Doppler width d =
+                           sqrt(T/t_ref) does, so a node's profile is
+                           H(a/d, x/d)/(sqrt(pi) d), from the rational Voigt
+                           function (mg3d_check_voigt) in FP64 per node and
+                           frequency, rounded once to the formal-solution
+                           precision.  MG3D_E_ARG with a velocity field, in an
+                           atom with partial-redistribution lines, or in a
+                           batch */
     double gamma_prd;   /* coherence fraction of partial redistribution in
                            [0, 1] (0: CRD).  The next step Sec. 6 names, read as
                            for the two-level atom: the line emits with the

@@ -144,6 +144,7 @@ struct mg3d_handle {
     PrdLine *d_prd = nullptr;
     int *d_prd_ord = nullptr, *d_prd_grp = nullptr, *d_prd_index = nullptr;
     std::vector<int> prd_index;  // host copy of d_prd_index
+    VoigtTable *d_voigt = nullptr;   // Voigt coefficients when a multi-level line is damped
     int fmg_next = 1;            // the FMG stage mg3d_fmg_stage may run next (1 restarts)
     int top = 0;                 // grid being solved (0: the finest); only its formal
                                  // solutions update its background field
@@ -668,7 +669,7 @@ int ml_chunk_fs(mg3d_handle *h, int k, int f0, int nc) {
                      h->d_exp_tab, h->exp_l1, h->exp_l2,
                      h->scatter ? L.sigma_c : nullptr, h->scatter ? L.jbg : nullptr,
                      h->moving ? 1 : 0, h->ml_prd ? h->d_prd_index : nullptr,
-                     h->ml_prd ? L.prd_rho : nullptr};
+                     h->ml_prd ? L.prd_rho : nullptr, h->d_voigt};
     MG_TRY(launched(h, launch_ml_opacity(oa, h->stream), "multi-level opacity"));
     if (h->params.sc_interp)
         MG_TRY(launched(h, launch_xslopes(h->prec, L.nx, (long)nc * L.nvox, L.mchi, L.mS, L.mdchi,
@@ -766,7 +767,8 @@ int ml_accumulate(mg3d_handle *h, int k, int f0, int nc, bool zero_rad) {
                   h->t_ref, L.T, h->ml_jx, h->ml_ux, 2 * (12 / L.ml_rpb), zero_rad ? 1 : 0,
                   h->ml_acc, h->d_exp_tab, h->exp_l1, h->exp_l2, bg ? h->ml_jm : nullptr,
                   bg ? L.jbg : nullptr, h->moving ? 1 : 0,
-                  h->ml_prd ? h->d_prd_index : nullptr, h->ml_prd ? L.prd_oc : nullptr};
+                  h->ml_prd ? h->d_prd_index : nullptr, h->ml_prd ? L.prd_oc : nullptr,
+                  h->d_voigt};
     return launched(h, launch_ml_accum(a, h->stream), "radiative sums");
 }
 
@@ -2023,7 +2025,8 @@ int autotune_ml_level(mg3d_handle *h, int k, int nc, int *evaluated) {
     Level &L = h->lev[k];
     MlOpacityArgs oa{L.nvox, nc, h->N, h->prec, h->d_fi, h->theta_ref, h->t_ref,
                      L.n, L.T, L.chi_c, L.saha, L.mchi, L.mS, L.msc, L.moc, 0,
-                     h->d_exp_tab, h->exp_l1, h->exp_l2, nullptr, nullptr, h->moving ? 1 : 0};
+                     h->d_exp_tab, h->exp_l1, h->exp_l2, nullptr, nullptr, h->moving ? 1 : 0,
+                     nullptr, nullptr, h->d_voigt};
     MG_TRY(launched(h, launch_ml_opacity(oa, h->stream), "multi-level opacity"));
     if (h->params.sc_interp)
         MG_TRY(launched(h, launch_xslopes(h->prec, L.nx, (long)nc * L.nvox, L.mchi, L.mS, L.mdchi,
@@ -2280,6 +2283,14 @@ int create_ml_impl(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
     h->theta_ref = atom->theta_ref;
     h->t_ref = atom->t_ref;
     for (int t = 0; t < atom->n_lines; ++t) h->ml_prd = h->ml_prd || atom->lines[t].gamma_prd > 0.0;
+    for (int t = 0; t < atom->n_lines; ++t)
+        if (atom->lines[t].a_damp > 0.0 && !h->d_voigt) {
+            // damped lines: the opacity step and the radiative sums evaluate
+            // the Voigt function per node and frequency
+            MG_TRY(dev_alloc((void **)&h->d_voigt, sizeof(VoigtTable)));
+            MG_CUDA(cudaMemcpy(h->d_voigt, &voigt_coefficients(), sizeof(VoigtTable),
+                               cudaMemcpyHostToDevice));
+        }
     build_quadrature(h, quad ? quad->a : 0.0);
     const int N = h->N;
     // frequency table: lines, then continua, each transition contiguous
@@ -2291,7 +2302,8 @@ int create_ml_impl(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
         TransInfo tr{0, ln.lower, ln.upper, (int)h->fi.size(), 0, ln.rho, ln.a_ul,
                      atom->g[ln.upper] / atom->g[ln.lower]};
         for (int i = 0; i < ln.n_freq; ++i)
-            h->fi.push_back(FreqInfo{0, ln.lower, ln.upper, x[i], w[i], ln.rho, ln.kappa, tr.gr});
+            h->fi.push_back(
+                FreqInfo{0, ln.lower, ln.upper, x[i], w[i], ln.rho, ln.kappa, tr.gr, ln.a_damp});
         tr.f_end = (int)h->fi.size();
         h->ti.push_back(tr);
     }
@@ -3020,9 +3032,11 @@ int mg3d_create_ml(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
         if (ln.lower < 0 || ln.upper >= N || ln.lower >= ln.upper || ln.n_freq < 1 ||
             !(ln.rho > 0) || !(ln.a_ul > 0) || !(ln.kappa >= 0) || !(ln.x_max >= 0))
             return fail(MG3D_E_ARG, "bad line " + std::to_string(t));
-        if (ln.a_damp != 0.0)
+        if (!(ln.a_damp >= 0.0 && ln.a_damp < 1e3))
+            return fail(MG3D_E_ARG, "line " + std::to_string(t) + ": a_damp must lie in [0, 1000)");
+        if (ln.a_damp > 0.0 && atm->vel)
             return fail(MG3D_E_ARG, "line " + std::to_string(t) +
-                                        ": multi-level atoms take Doppler profiles (a_damp 0)");
+                                        ": damped lines take a static atmosphere");
         if (!(ln.gamma_prd >= 0.0 && ln.gamma_prd <= 1.0))
             return fail(MG3D_E_ARG, "line " + std::to_string(t) + ": gamma_prd must lie in [0, 1]");
         if (ln.gamma_prd > 0.0 && (atm->vel || params->sc_interp))
@@ -3034,6 +3048,17 @@ int mg3d_create_ml(const mg3d_ml_atmosphere *atm, const mg3d_ml_atom *atom,
                                         "at most " + std::to_string(kMaxPrdLineFreq) +
                                         " frequencies per line");
         nf += ln.n_freq;
+    }
+    {
+        bool damped = false, prd = false;
+        for (int t = 0; t < atom->n_lines; ++t) {
+            damped = damped || atom->lines[t].a_damp > 0.0;
+            prd = prd || atom->lines[t].gamma_prd > 0.0;
+        }
+        if (damped && prd)
+            return fail(MG3D_E_ARG, "damped lines and partial redistribution in one multi-level "
+                                    "atom are not built (the ratios' plain rates take Doppler "
+                                    "profiles)");
     }
     for (int t = 0; t < atom->n_continua; ++t) {
         const mg3d_continuum &ct = atom->continua[t];
@@ -3259,6 +3284,8 @@ int mg3d_batch_create(int n, mg3d_handle *const *members, mg3d_batch **out) {
         if (!members[i]) return fail(MG3D_E_ARG, "null member");
         if (members[i]->scatter)
             return fail(MG3D_E_ARG, "batches do not take background scattering");
+        if (members[i]->d_voigt)
+            return fail(MG3D_E_ARG, "batches do not take damped multi-level lines");
         if (members[i]->ml_prd)
             return fail(MG3D_E_ARG, "batches do not take partial redistribution");
         if (members[i]->params.sc_interp)
@@ -3444,7 +3471,7 @@ int mg3d_destroy(mg3d_handle *h) {
     for (void *p : h->o_pslot)
         if (p) cudaFree(p);
     for (void *p : {(void *)h->d_prd, (void *)h->d_prd_ord, (void *)h->d_prd_grp,
-                    (void *)h->d_prd_index})
+                    (void *)h->d_prd_index, (void *)h->d_voigt})
         if (p) cudaFree(p);
     if (h->o_pj) cudaFree(h->o_pj);
     if (h->o_pu) cudaFree(h->o_pu);

@@ -7,6 +7,8 @@
 
 namespace mg3d {
 
+struct VoigtTable;   // voigt.cuh
+
 constexpr int kRays = 24;          // A4 quadrature, 12 up and 12 down
 constexpr int kMaxBands = 16;      // thread blocks per cluster sharing a plane (beyond
                                    // 8: non-portable cluster size, checked per shape)
@@ -260,6 +262,7 @@ struct FreqInfo {
     double rho;     // line: nu/nu_ref; continuum: threshold nu/nu_ref
     double kappa;   // opacity coefficient
     double gr;      // line: g_u/g_l (unused for continua)
+    double adamp;   // line: Voigt damping parameter at t_ref (0: Doppler profile)
 };
 
 // One transition: its frequencies are [f_begin, f_end) of the table.
@@ -385,6 +388,7 @@ struct MlOpacityArgs {
     const int *prd_index;          // [n_freq] row of rho for a PRD line frequency, else -1
                                    // (null: no partial redistribution)
     const double *prd_rho;         // [n_prd_freq][nvox] emission-profile ratio psi/phi
+    const VoigtTable *voigt;       // coefficients of the Voigt function (damped lines), or null
 };
 
 // Radiative sums per transition and node, [n_trans][3][nvox] in FP64:
@@ -413,6 +417,7 @@ struct MlAccumArgs {
     const int *prd_index;          // [n_freq] PRD row of a frequency, else -1 (null: none)
     const double *prd_oc;          // [n_prd_freq][nvox] 1 - rho chi_t/chi in FP64: U of a
                                    // PRD frequency is oc + (1 - oc) sum_r w_r u_r
+    const VoigtTable *voigt;       // coefficients of the Voigt function (damped lines), or null
 };
 
 struct MlRateArgs {

@@ -44,6 +44,7 @@
 #include "mg3d.h"
 #include "mg3d_internal.h"
 #include "sc_step.cuh"
+#include "voigt.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -75,6 +76,20 @@ __device__ __forceinline__ double ml_doppler(double dd2, double di, const ExpNeg
 }
 __device__ __forceinline__ float ml_doppler(float dd2, float di, const ExpNegTable &) {
     return __expf(-dd2) * di * 0.564189584f;
+}
+
+// A line's profile at a node of Doppler width d = 1/inv_d reference widths,
+// per reference width: the Doppler profile in the formal-solution precision,
+// or for a damped line (damping a at t_ref; the node's parameter a/d, since
+// the damping width does not scale with temperature) H(a/d, x/d)/(sqrt(pi) d)
+// from the rational Voigt function in FP64, rounded once.
+template <typename T>
+__device__ __forceinline__ T ml_line_phi(const FreqInfo &q, double inv_d, T pnorm,
+                                         const VoigtTable *vt, const ExpNegTable &et) {
+    const double xd = q.xy * inv_d;
+    if (q.adamp > 0.0)
+        return (T)(voigt_H_rational(*vt, q.adamp * inv_d, xd) * 0.5641895835477563 * inv_d);
+    return opac_exp((T)(xd * xd), et) * pnorm;
 }
 
 // One thread per node walks the chunk's frequencies, so per-node quantities
@@ -115,8 +130,7 @@ __global__ void ml_opacity_kernel(const MlOpacityArgs a) {
                     rho_b = q.rho;
                     B = (T)planck_rho(q.rho, a.theta_ref, Tg);
                 }
-                const double xd = q.xy * inv_d;
-                const T phi = opac_exp((T)(xd * xd), et) * pnorm;
+                const T phi = ml_line_phi<T>(q, inv_d, pnorm, a.voigt, et);
                 chi_t = (T)q.kappa * phi * (T)(q.gr * nl - nu);
                 eta_t = (T)(q.kappa * q.rho * q.rho * q.rho) * (T)nu * phi;
             } else {
@@ -929,9 +943,14 @@ __global__ void ml_accum_kernel(const MlAccumArgs a) {
                         continue;
                     }
                     const FreqInfo q = a.fi[f];
-                    const double xd = q.xy * inv_d;
                     // profile in the formal-solution precision, sums in FP64
-                    const double wphi = q.w * (double)opac_exp((TP)(xd * xd), et) * rsqpi * inv_d;
+                    double wphi;
+                    if (q.adamp > 0.0) {
+                        wphi = q.w * (double)ml_line_phi<TP>(q, inv_d, TP(0), a.voigt, et);
+                    } else {
+                        const double xd = q.xy * inv_d;
+                        wphi = q.w * (double)opac_exp((TP)(xd * xd), et) * rsqpi * inv_d;
+                    }
                     double J = 0.0, U = 1.0;
                     if (!a.zero_radiation) {
                         sums(f, v, J, U);

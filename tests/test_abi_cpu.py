@@ -86,12 +86,21 @@ def test_create_rejects_bad_grids_before_touching_the_gpu(lib):
     with pytest.raises(m.MG3DError) as ei:
         m.mg3d_create(vatm, synth.TwoLevelAtom(a_damp=0.05), n_grids=1)
     assert ei.value.code == m.MG3D_E_ARG and "Doppler" in m.mg3d_last_error()
-    # damped lines of a multi-level atom are not built
-    ml_atom = synth.hydrogen_like_atom(line_freq=5, cont_freq=3, a_damp=0.01)
+    # damped lines of a multi-level atom: non-negative, static, not with PRD
+    ml_atom = synth.hydrogen_like_atom(line_freq=5, cont_freq=3, a_damp=-0.01)
     ml_atm = synth.chromosphere(8, 8, 17, ml_atom)
     with pytest.raises(m.MG3DError) as ei:
         m.mg3d_create_ml(ml_atm, ml_atom, n_grids=1)
-    assert ei.value.code == m.MG3D_E_ARG and "Doppler" in m.mg3d_last_error()
+    assert ei.value.code == m.MG3D_E_ARG and "a_damp" in m.mg3d_last_error()
+    ml_atom = synth.hydrogen_like_atom(line_freq=5, cont_freq=3, a_damp=0.01)
+    vml = synth.chromosphere(8, 8, 17, ml_atom, velocity=0.5)
+    with pytest.raises(m.MG3DError) as ei:
+        m.mg3d_create_ml(vml, ml_atom, n_grids=1)
+    assert ei.value.code == m.MG3D_E_ARG and "static" in m.mg3d_last_error()
+    ml_atom = synth.hydrogen_like_atom(line_freq=5, cont_freq=3, a_damp=0.01, gamma_prd=0.5)
+    with pytest.raises(m.MG3DError) as ei:
+        m.mg3d_create_ml(ml_atm, ml_atom, n_grids=1)
+    assert ei.value.code == m.MG3D_E_ARG and "damped" in m.mg3d_last_error()
 
 
 def test_allocation_free_call_refuses_prd_and_damping(lib):
